@@ -1,0 +1,188 @@
+/*
+ * pgb -- treecode-accelerated boundary-element Poisson-Boltzmann solver for a
+ * molecule near surfaces of imposed charge or potential (Cooper & Barba,
+ * arXiv 1506.03745), for NVIDIA GB300 (sm_103a).
+ *
+ * C ABI.  Every call returns 0 (PGB_OK) or a negative status; no exception
+ * crosses the boundary.  pgb_last_error() gives a one-line message for the
+ * last failing call on a context.  All device pointers are plain CUDA device
+ * addresses on the context's device, used on the context's stream; the
+ * caller owns them.  Host pointers are only read during the call.
+ *
+ * Units (Section 2 of the paper): lengths in Angstrom, charges in e,
+ * permittivities relative, kappa in 1/Angstrom, imposed surface charge in
+ * C/m^2, imposed potential in volts, energies in kcal/mol.  Internally the
+ * library works in e, Angstrom and eps0 = 1.
+ *
+ * Unknown vector layout (Eq. 6 / Eq. 7): bodies in load order; a dielectric
+ * body (molecule) contributes [phi (N), dphi/dn (N)] -- the interior potential
+ * and its normal derivative at its panel centroids -- and a surface body
+ * contributes one block of N values: dphi/dn (imposed potential, Eq. 6) or
+ * phi (imposed charge, Eq. 7).  Within a block, panels are in the order of
+ * the triangles given to pgb_mesh_load.
+ */
+#ifndef PGB_H
+#define PGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define PGB_OK 0
+#define PGB_EINVAL (-1)     /* bad argument; nothing changed */
+#define PGB_ENOMEM (-2)     /* device allocation failed */
+#define PGB_ECUDA (-3)      /* CUDA runtime error (message in pgb_last_error) */
+#define PGB_ENOCONV (-4)    /* GMRES did not reach tol; solution and stats still written */
+#define PGB_ETIMEOUT (-5)   /* a bounded device-side wait gave up */
+#define PGB_ESTATE (-6)     /* call out of order (e.g. matvec before pgb_tree_build) */
+
+/* body kinds (Eq. 1): molecule interface Gamma_1, or surface Gamma_2 */
+#define PGB_DIELECTRIC 0
+#define PGB_SET_CHARGE 1
+#define PGB_SET_POTENTIAL 2
+
+/* precisions / solve modes */
+#define PGB_FP32 0          /* P2P/M2P/P2M in FP32 with compensated accumulation */
+#define PGB_FP64 1          /* every treecode kernel in FP64 */
+#define PGB_FP32_REFINE 2   /* solve: FP32 inner GMRES, FP64 outer residual */
+
+/* Numerical parameters: the seven columns of the paper's parameter tables
+ * (Tables 1, 2, 4: Gauss points in-element per edge, close-by, far-away;
+ * treecode N_crit, P, theta; GMRES tol -- tol is passed to pgb_solve) plus
+ * the target group size of the interaction lists. */
+typedef struct pgb_params {
+    int32_t K;            /* far-field points per panel: 1, 3, 4 or 7 (Section 3.1) */
+    int32_t K_near;       /* fine rule inside 2L: 19 (Section 3.1) */
+    int32_t n_edge;       /* Gauss points per edge for the self panel: 3, 6, 9 or 12 */
+    int32_t P;            /* Taylor order, 0..8 (Section 3.2) */
+    double theta;         /* multipole acceptance criterion; 0 = direct sum */
+    int32_t leaf_size;    /* N_crit: max panels per octree leaf, 1..1024 */
+    int32_t group_size;   /* targets per interaction list: 32 (one warp) */
+} pgb_params;
+
+typedef struct pgb_solve_stats {
+    int32_t iterations;        /* total inner GMRES iterations */
+    int32_t outer_steps;       /* refinement steps (1 for PGB_FP64) */
+    int32_t matvecs;           /* operator applications, all precisions */
+    int32_t matvecs_fp64;      /* of which FP64 */
+    double rel_residual;       /* final ||b - A x|| / ||b|| (FP64 operator) */
+} pgb_solve_stats;
+
+typedef struct pgb_energies {
+    double coulomb;            /* Coulomb energy of the point charges */
+    double solvation;          /* Eq. 12 with the 1/2 kept */
+    double surface;            /* Eq. 15 */
+    double total;              /* Eq. 16 */
+} pgb_energies;
+
+typedef struct pgb_tree_info {
+    int64_t n_panels;          /* all bodies */
+    int64_t n_unknowns;
+    int64_t n_nodes;
+    int64_t n_leaves;
+    int64_t n_groups;
+    int64_t n_near;            /* (group, leaf) near pairs */
+    int64_t n_far;             /* (group, node) far pairs */
+    int64_t p2p_pairs;         /* target x source-point P2P interactions per matvec */
+    int64_t p2p_laplace_pairs; /* of which also need the Laplace kernel */
+    int64_t m2p_pairs;         /* target x node M2P evaluations per matvec */
+    int64_t m2p_laplace_pairs;
+    int64_t n_corrections;     /* near-field correction entries */
+} pgb_tree_info;
+
+/* Device time per stage of the hot path, accumulated with CUDA events on
+ * the context's stream while timing is enabled (pgb_timing). */
+#define PGB_STAGE_SOURCES 0   /* panel densities and per-point source terms */
+#define PGB_STAGE_UPWARD 1    /* P2M at the leaves + moment shifts to the root */
+#define PGB_STAGE_EVAL 2      /* P2P over near leaves + M2P over far nodes */
+#define PGB_STAGE_ASSEMBLE 3  /* near-field corrections + block rows */
+#define PGB_STAGE_KRYLOV 4    /* Arnoldi (CGS2), Givens, updates */
+#define PGB_STAGE_TREE 5      /* pgb_tree_build */
+#define PGB_STAGE_ENERGY 6    /* pgb_energy */
+#define PGB_STAGE_RHS 7       /* right-hand side */
+#define PGB_N_STAGES 8
+typedef struct pgb_stage_times {
+    double ms[PGB_N_STAGES];        /* summed device milliseconds */
+    int64_t calls[PGB_N_STAGES];    /* timed intervals */
+    int64_t kernel_launches;        /* kernels the library launched (all stages) */
+} pgb_stage_times;
+
+/* Create a context on the current CUDA device.  p may be NULL (defaults:
+ * K=7, K_near=19, n_edge=9, P=6, theta=0.5, leaf_size=32, group_size=32).
+ * cuda_stream is a cudaStream_t (NULL = legacy default stream).  Returns
+ * PGB_EINVAL for out-of-range parameters. */
+int pgb_create(struct pgb_ctx** ctx, const pgb_params* p, void* cuda_stream);
+int pgb_destroy(struct pgb_ctx* ctx);
+const char* pgb_last_error(const struct pgb_ctx* ctx);
+int pgb_default_params(pgb_params* p);
+
+/* Load one body (Section 2, Eq. 1; Section 3.1 discretisation).
+ * verts: nv*3 doubles (Angstrom), tris: nt*3 int32, counter-clockwise seen
+ * from the solvent so the normal points into the solvent.  For
+ * PGB_DIELECTRIC: eps_in > 0 and nq >= 0 charges (charge_xyz nq*3, charge_q
+ * nq, in e); bc_value ignored.  For PGB_SET_CHARGE: bc_value = sigma0 (C/m^2);
+ * for PGB_SET_POTENTIAL: bc_value = phi0 (V); charges must be empty.
+ * Host arrays are copied.  *body_id_out receives the body index.  Loading a
+ * body invalidates the tree (call pgb_tree_build again). */
+int pgb_mesh_load(struct pgb_ctx* ctx, int32_t kind, const double* verts, int64_t nv,
+                  const int32_t* tris, int64_t nt, double eps_in,
+                  const double* charge_xyz, const double* charge_q, int64_t nq,
+                  double bc_value, int32_t* body_id_out);
+
+/* Solvent permittivity and inverse Debye length (Eq. 1); kappa >= 0. */
+int pgb_set_solvent(struct pgb_ctx* ctx, double eps_out, double kappa);
+
+/* Rigid pose of a body: world = R * body + t (R row-major 3x3, proper
+ * rotation within 1e-9).  Invalidates interaction lists and cross-body
+ * near-field entries (pgb_tree_build again). */
+int pgb_set_pose(struct pgb_ctx* ctx, int32_t body_id, const double R[9], const double t[3]);
+
+/* Geometry, octree, interaction lists and near-field corrections for the
+ * current bodies and poses (Section 3.1 tiers, Section 3.2 treecode). */
+int pgb_tree_build(struct pgb_ctx* ctx);
+int pgb_tree_stats(struct pgb_ctx* ctx, pgb_tree_info* info);
+
+/* Number of unknowns 2*N_dielectric + N_surface. */
+int pgb_num_unknowns(struct pgb_ctx* ctx, int64_t* n);
+
+/* y = A x, the block operator of Eq. 6 / Eq. 7 applied by the treecode
+ * (Section 3.2): x, y device arrays of n_unknowns floats (PGB_FP32) or
+ * doubles (PGB_FP64).  x and y must not overlap. */
+int pgb_matvec(struct pgb_ctx* ctx, const void* x, void* y, int32_t precision);
+
+/* Right-hand side of Eq. 6 / Eq. 7 (Coulomb rows with the 1/eps_in of Eq. 5,
+ * imposed-boundary terms moved to the right) into device doubles b. */
+int pgb_rhs(struct pgb_ctx* ctx, double* b);
+
+/* GMRES solve of Eq. 6 / Eq. 7 (Section 3.2).  mode PGB_FP64 or
+ * PGB_FP32_REFINE; tol on ||b - A x||/||b||; max_iter total inner iterations;
+ * restart = Krylov dimension (1..256).  x_out: device doubles, n_unknowns.
+ * Returns PGB_ENOCONV (x_out and stats still written) when tol is not met. */
+int pgb_solve(struct pgb_ctx* ctx, int32_t mode, double tol, int32_t max_iter, int32_t restart,
+              double* x_out, pgb_solve_stats* stats);
+
+/* Energies (Section 3.3, Eq. 11-16) of a solution x (device doubles):
+ * Coulomb, solvation (phi_reac of Eq. 13 at the charges with the three-tier
+ * rule), surface (Eq. 15) and total, summed over bodies.  per_body may be
+ * NULL or an array of n_bodies entries. */
+int pgb_energy(struct pgb_ctx* ctx, const double* x, pgb_energies* e, pgb_energies* per_body);
+
+/* Enable (1) or disable (0) stage timing.  If out is not NULL the stream
+ * is synchronised and the times and launch count accumulated since the last
+ * read are written to out and reset.  Launch counting is always on. */
+int pgb_timing(struct pgb_ctx* ctx, int32_t enable, pgb_stage_times* out);
+
+/* Debug/test export of the tree (host arrays sized from pgb_tree_stats):
+ * perm[n_panels] (sorted position -> panel index within its body, bodies
+ * concatenated), near_off[n_groups+1], near_node[n_near], far_off[n_groups+1],
+ * far_node[n_far].  Any pointer may be NULL. */
+int pgb_tree_export(struct pgb_ctx* ctx, int32_t* perm, int64_t* near_off, int32_t* near_node,
+                    int64_t* far_off, int32_t* far_node);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,233 @@
+"""ctypes binding of libpgb (include/pgb.h): one Python function per C entry
+point, with the same name, doing argument marshalling only.  Device arrays are
+passed as torch CUDA tensors (their data_ptr is handed to the library);
+host arrays as numpy arrays.  A negative status raises PgbError, except
+PGB_ENOCONV from pgb_solve, which is returned with the stats."""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpgb.so")
+
+PGB_OK, PGB_EINVAL, PGB_ENOMEM, PGB_ECUDA, PGB_ENOCONV, PGB_ETIMEOUT, PGB_ESTATE = 0, -1, -2, -3, -4, -5, -6
+PGB_DIELECTRIC, PGB_SET_CHARGE, PGB_SET_POTENTIAL = 0, 1, 2
+PGB_FP32, PGB_FP64, PGB_FP32_REFINE = 0, 1, 2
+
+c_i32, c_i64, c_dbl, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+
+
+class pgb_params(ctypes.Structure):
+    _fields_ = [("K", c_i32), ("K_near", c_i32), ("n_edge", c_i32), ("P", c_i32), ("theta", c_dbl),
+                ("leaf_size", c_i32), ("group_size", c_i32)]
+
+
+class pgb_solve_stats(ctypes.Structure):
+    _fields_ = [("iterations", c_i32), ("outer_steps", c_i32), ("matvecs", c_i32), ("matvecs_fp64", c_i32),
+                ("rel_residual", c_dbl)]
+
+
+class pgb_energies(ctypes.Structure):
+    _fields_ = [("coulomb", c_dbl), ("solvation", c_dbl), ("surface", c_dbl), ("total", c_dbl)]
+
+
+class pgb_tree_info(ctypes.Structure):
+    _fields_ = [(n, c_i64) for n in ("n_panels", "n_unknowns", "n_nodes", "n_leaves", "n_groups", "n_near",
+                                     "n_far", "p2p_pairs", "p2p_laplace_pairs", "m2p_pairs", "m2p_laplace_pairs",
+                                     "n_corrections")]
+
+
+N_STAGES = 8
+STAGES = ("sources", "upward", "eval", "assemble", "krylov", "tree", "energy", "rhs")
+
+
+class pgb_stage_times(ctypes.Structure):
+    _fields_ = [("ms", c_dbl * N_STAGES), ("calls", c_i64 * N_STAGES), ("kernel_launches", c_i64)]
+
+
+class PgbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pgb error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+_SIGS = {
+    "pgb_create": (c_i32, [ctypes.POINTER(c_vp), ctypes.POINTER(pgb_params), c_vp]),
+    "pgb_destroy": (c_i32, [c_vp]),
+    "pgb_last_error": (ctypes.c_char_p, [c_vp]),
+    "pgb_default_params": (c_i32, [ctypes.POINTER(pgb_params)]),
+    "pgb_mesh_load": (c_i32, [c_vp, c_i32, c_vp, c_i64, c_vp, c_i64, c_dbl, c_vp, c_vp, c_i64, c_dbl,
+                              ctypes.POINTER(c_i32)]),
+    "pgb_set_solvent": (c_i32, [c_vp, c_dbl, c_dbl]),
+    "pgb_set_pose": (c_i32, [c_vp, c_i32, c_vp, c_vp]),
+    "pgb_tree_build": (c_i32, [c_vp]),
+    "pgb_tree_stats": (c_i32, [c_vp, ctypes.POINTER(pgb_tree_info)]),
+    "pgb_num_unknowns": (c_i32, [c_vp, ctypes.POINTER(c_i64)]),
+    "pgb_matvec": (c_i32, [c_vp, c_vp, c_vp, c_i32]),
+    "pgb_rhs": (c_i32, [c_vp, c_vp]),
+    "pgb_solve": (c_i32, [c_vp, c_i32, c_dbl, c_i32, c_i32, c_vp, ctypes.POINTER(pgb_solve_stats)]),
+    "pgb_energy": (c_i32, [c_vp, c_vp, ctypes.POINTER(pgb_energies), c_vp]),
+    "pgb_tree_export": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "pgb_timing": (c_i32, [c_vp, c_i32, ctypes.POINTER(pgb_stage_times)]),
+}
+
+
+def lib():
+    """The loaded CDLL; raises if the library has not been built (there is no
+    fallback path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with python -m paper_1506_03745_gb300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(ctx, st, allow=()):
+    if st < 0 and st not in allow:
+        msg = lib().pgb_last_error(ctx).decode() if ctx else ""
+        raise PgbError(st, msg)
+    return st
+
+
+def _dptr(t, dtype_name, n=None):
+    """Device pointer of a contiguous CUDA tensor (torch), checked."""
+    if not (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous()):
+        raise TypeError("expected a contiguous CUDA tensor")
+    if str(t.dtype) != "torch." + dtype_name:
+        raise TypeError(f"expected torch.{dtype_name}, got {t.dtype}")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"expected {n} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(c_vp)
+
+
+def default_params(**kw):
+    p = pgb_params()
+    lib().pgb_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def pgb_create(params=None, stream=None):
+    """stream: a torch.cuda.Stream, a raw cudaStream_t integer or None."""
+    h = c_vp()
+    s = getattr(stream, "cuda_stream", stream)
+    st = lib().pgb_create(ctypes.byref(h), ctypes.byref(params) if params is not None else None,
+                          c_vp(s) if s else None)
+    _check(None, st)
+    return h
+
+
+def pgb_destroy(ctx):
+    return _check(None, lib().pgb_destroy(ctx))
+
+
+def pgb_last_error(ctx):
+    return lib().pgb_last_error(ctx).decode()
+
+
+def pgb_mesh_load(ctx, kind, verts, tris, eps_in=1.0, charge_xyz=None, charge_q=None, bc_value=0.0):
+    v, vp = _hptr(verts, np.float64)
+    t, tp = _hptr(tris, np.int32)
+    nq = 0 if charge_q is None else len(charge_q)
+    if nq:
+        qx, qxp = _hptr(charge_xyz, np.float64)
+        qq, qqp = _hptr(charge_q, np.float64)
+    else:
+        qxp = qqp = None
+    bid = c_i32()
+    _check(ctx, lib().pgb_mesh_load(ctx, kind, vp, v.shape[0], tp, t.shape[0], eps_in, qxp, qqp, nq,
+                                    bc_value, ctypes.byref(bid)))
+    return bid.value
+
+
+def pgb_set_solvent(ctx, eps_out, kappa):
+    return _check(ctx, lib().pgb_set_solvent(ctx, eps_out, kappa))
+
+
+def pgb_set_pose(ctx, body_id, R, t):
+    R_, Rp = _hptr(np.asarray(R).reshape(9), np.float64)
+    t_, tp = _hptr(np.asarray(t).reshape(3), np.float64)
+    return _check(ctx, lib().pgb_set_pose(ctx, body_id, Rp, tp))
+
+
+def pgb_tree_build(ctx):
+    return _check(ctx, lib().pgb_tree_build(ctx))
+
+
+def pgb_tree_stats(ctx):
+    info = pgb_tree_info()
+    _check(ctx, lib().pgb_tree_stats(ctx, ctypes.byref(info)))
+    return {n: getattr(info, n) for n, _ in pgb_tree_info._fields_}
+
+
+def pgb_num_unknowns(ctx):
+    n = c_i64()
+    _check(ctx, lib().pgb_num_unknowns(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def pgb_matvec(ctx, x, y, precision):
+    n = pgb_num_unknowns(ctx)
+    dt = "float32" if precision == PGB_FP32 else "float64"
+    return _check(ctx, lib().pgb_matvec(ctx, _dptr(x, dt, n), _dptr(y, dt, n), precision))
+
+
+def pgb_rhs(ctx, b):
+    return _check(ctx, lib().pgb_rhs(ctx, _dptr(b, "float64", pgb_num_unknowns(ctx))))
+
+
+def pgb_solve(ctx, mode, tol, max_iter, restart, x_out):
+    st = pgb_solve_stats()
+    code = _check(ctx, lib().pgb_solve(ctx, mode, tol, max_iter, restart,
+                                       _dptr(x_out, "float64", pgb_num_unknowns(ctx)), ctypes.byref(st)),
+                  allow=(PGB_ENOCONV,))
+    return code, {n: getattr(st, n) for n, _ in pgb_solve_stats._fields_}
+
+
+def pgb_energy(ctx, x, n_bodies=None):
+    e = pgb_energies()
+    per = (pgb_energies * n_bodies)() if n_bodies else None
+    _check(ctx, lib().pgb_energy(ctx, _dptr(x, "float64", pgb_num_unknowns(ctx)), ctypes.byref(e), per))
+    d = {n: getattr(e, n) for n, _ in pgb_energies._fields_}
+    if per is not None:
+        d["per_body"] = [{n: getattr(p, n) for n, _ in pgb_energies._fields_} for p in per]
+    return d
+
+
+def pgb_timing(ctx, enable, read=True):
+    """Enable/disable stage timing; when read, return and reset the
+    accumulated {stage: (ms, calls)} and the kernel launch count."""
+    t = pgb_stage_times()
+    _check(ctx, lib().pgb_timing(ctx, 1 if enable else 0, ctypes.byref(t) if read else None))
+    if not read:
+        return None
+    d = {STAGES[i]: (t.ms[i], t.calls[i]) for i in range(N_STAGES)}
+    d["kernel_launches"] = t.kernel_launches
+    return d
+
+
+def pgb_tree_export(ctx):
+    s = pgb_tree_stats(ctx)
+    perm = np.zeros(s["n_panels"], np.int32)
+    noff = np.zeros(s["n_groups"] + 1, np.int64)
+    foff = np.zeros(s["n_groups"] + 1, np.int64)
+    near = np.zeros(max(1, s["n_near"]), np.int32)
+    far = np.zeros(max(1, s["n_far"]), np.int32)
+    p = lambda a: a.ctypes.data_as(c_vp)
+    _check(ctx, lib().pgb_tree_export(ctx, p(perm), p(noff), p(near), p(foff), p(far)))
+    return perm, noff, near[:s["n_near"]], foff, far[:s["n_far"]]

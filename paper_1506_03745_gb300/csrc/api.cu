@@ -1,0 +1,377 @@
+// C entry points of libpgb (declared in include/pgb.h).
+#include <math.h>
+
+#include <cstring>
+#include <exception>
+#include <new>
+
+#include "pgb_internal.cuh"
+
+namespace pgb {
+void cuda_check(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        throw Error{PGB_ECUDA, std::string(what) + ": " + cudaGetErrorString(e)};
+    }
+}
+void fail(int code, const std::string& msg) { throw Error{code, msg}; }
+
+static cudaEvent_t get_event(pgb_ctx* c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cuda_check(cudaEventCreate(&e), "cudaEventCreate");
+    return e;
+}
+
+StageTimer::StageTimer(pgb_ctx* ctx, int st) : c(ctx), stage(st) {
+    if (!c->timing) return;
+    e0 = get_event(c);
+    e1 = get_event(c);
+    cudaEventRecord(e0, c->stream);
+}
+
+StageTimer::~StageTimer() {
+    if (!e0) return;
+    cudaEventRecord(e1, c->stream);
+    c->ev_pending.push_back({stage, {e0, e1}});
+}
+
+void collect_timing(pgb_ctx* c) {
+    if (c->ev_pending.empty()) return;
+    cuda_check(cudaStreamSynchronize(c->stream), "timing sync");
+    for (auto& p : c->ev_pending) {
+        float ms = 0;
+        cuda_check(cudaEventElapsedTime(&ms, p.second.first, p.second.second), "cudaEventElapsedTime");
+        c->stage_ms[p.first] += ms;
+        c->stage_calls[p.first] += 1;
+        c->ev_pool.push_back(p.second.first);
+        c->ev_pool.push_back(p.second.second);
+    }
+    c->ev_pending.clear();
+}
+void convert_f32_f64(const float* a, double* b, int64_t n, cudaStream_t s);
+void convert_f64_f32(const double* a, float* b, int64_t n, cudaStream_t s);
+}  // namespace pgb
+
+using namespace pgb;
+
+template <class F>
+static int guard(pgb_ctx* c, F f) {
+    try {
+        int r = f();
+        if (c && r == PGB_OK) c->err.clear();
+        return r;
+    } catch (const Error& e) {
+        if (c) c->err = e.msg;
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        if (c) c->err = "host allocation failed";
+        return PGB_ENOMEM;
+    } catch (const std::exception& e) {
+        if (c) c->err = e.what();
+        return PGB_EINVAL;
+    }
+}
+
+static int check_params(const pgb_params* p, std::string& why) {
+    if (!(p->K == 1 || p->K == 3 || p->K == 4 || p->K == 7)) why = "K must be 1, 3, 4 or 7";
+    else if (p->K_near != 19) why = "K_near must be 19";
+    else if (!(p->n_edge == 3 || p->n_edge == 6 || p->n_edge == 9 || p->n_edge == 12)) why = "n_edge must be 3, 6, 9 or 12";
+    else if (p->P < 0 || p->P > PGB_MAX_P) why = "P must be in 0..8";
+    else if (!(p->theta >= 0 && p->theta < 1)) why = "theta must be in [0, 1)";
+    else if (p->leaf_size < 1 || p->leaf_size > 1024) why = "leaf_size must be in 1..1024";
+    else if (p->group_size != 32) why = "group_size must be 32";
+    else return PGB_OK;
+    return PGB_EINVAL;
+}
+
+extern "C" {
+
+int pgb_default_params(pgb_params* p) {
+    if (!p) return PGB_EINVAL;
+    p->K = 7;
+    p->K_near = 19;
+    p->n_edge = 9;
+    p->P = 6;
+    p->theta = 0.5;
+    p->leaf_size = 32;
+    p->group_size = 32;
+    return PGB_OK;
+}
+
+int pgb_create(pgb_ctx** out, const pgb_params* p, void* stream) {
+    if (!out) return PGB_EINVAL;
+    *out = nullptr;
+    pgb_params q;
+    pgb_default_params(&q);
+    if (p) q = *p;
+    std::string why;
+    if (check_params(&q, why) != PGB_OK) return PGB_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        (void)cudaGetLastError();
+        return PGB_ECUDA;
+    }
+    pgb_ctx* c = new (std::nothrow) pgb_ctx;
+    if (!c) return PGB_ENOMEM;
+    c->p = q;
+    c->stream = (cudaStream_t)stream;
+    if (cudaMallocHost(&c->h_pinned, 64) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete c;
+        return PGB_ENOMEM;
+    }
+    *out = c;
+    return PGB_OK;
+}
+
+int pgb_destroy(pgb_ctx* c) {
+    if (!c) return PGB_EINVAL;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto& p : c->ev_pending) {
+        cudaEventDestroy(p.second.first);
+        cudaEventDestroy(p.second.second);
+    }
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    delete c;
+    return PGB_OK;
+}
+
+const char* pgb_last_error(const pgb_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int pgb_mesh_load(pgb_ctx* c, int32_t kind, const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                  double eps_in, const double* charge_xyz, const double* charge_q, int64_t nq, double bc_value,
+                  int32_t* body_id_out) {
+    if (!c) return PGB_EINVAL;
+    return guard(c, [&]() -> int {
+        if (kind != PGB_DIELECTRIC && kind != PGB_SET_CHARGE && kind != PGB_SET_POTENTIAL) fail(PGB_EINVAL, "bad kind");
+        if (!verts || !tris || nv < 3 || nt < 1) fail(PGB_EINVAL, "empty mesh");
+        if (nt > (int64_t)1 << 26) fail(PGB_EINVAL, "too many panels");
+        if ((int)c->bodies.size() >= PGB_MAX_BODIES) fail(PGB_EINVAL, "too many bodies");
+        if (nq < 0 || (nq > 0 && (!charge_xyz || !charge_q))) fail(PGB_EINVAL, "bad charges");
+        if (kind != PGB_DIELECTRIC && nq != 0) fail(PGB_EINVAL, "surfaces carry no point charges");
+        if (kind == PGB_DIELECTRIC && !(eps_in > 0 && isfinite(eps_in))) fail(PGB_EINVAL, "eps_in must be > 0");
+        if (!isfinite(bc_value)) fail(PGB_EINVAL, "bc_value must be finite");
+        Body b;
+        b.kind = kind;
+        b.eps_in = kind == PGB_DIELECTRIC ? eps_in : 1.0;
+        b.N = nt;
+        b.nv = nv;
+        b.nq = nq;
+        b.verts.assign(verts, verts + 3 * nv);
+        b.tris.assign(tris, tris + 3 * nt);
+        for (double v : b.verts)
+            if (!isfinite(v)) fail(PGB_EINVAL, "non-finite vertex coordinate");
+        for (int32_t t : b.tris)
+            if (t < 0 || t >= nv) fail(PGB_EINVAL, "triangle index out of range");
+        for (int64_t i = 0; i < nt; ++i) {
+            const double* v0 = &b.verts[3 * b.tris[3 * i]];
+            const double* v1 = &b.verts[3 * b.tris[3 * i + 1]];
+            const double* v2 = &b.verts[3 * b.tris[3 * i + 2]];
+            double e1[3] = {v1[0] - v0[0], v1[1] - v0[1], v1[2] - v0[2]};
+            double e2[3] = {v2[0] - v0[0], v2[1] - v0[1], v2[2] - v0[2]};
+            double cx = e1[1] * e2[2] - e1[2] * e2[1], cy = e1[2] * e2[0] - e1[0] * e2[2], cz = e1[0] * e2[1] - e1[1] * e2[0];
+            if (!(cx * cx + cy * cy + cz * cz > 0)) fail(PGB_EINVAL, "degenerate triangle " + std::to_string(i));
+        }
+        if (nq) {
+            b.qxyz.assign(charge_xyz, charge_xyz + 3 * nq);
+            b.qval.assign(charge_q, charge_q + nq);
+            for (double v : b.qxyz)
+                if (!isfinite(v)) fail(PGB_EINVAL, "non-finite charge position");
+            for (double v : b.qval)
+                if (!isfinite(v)) fail(PGB_EINVAL, "non-finite charge");
+        }
+        const double e = 1.602176634e-19, eps0 = 8.8541878128e-12;
+        if (kind == PGB_SET_CHARGE) b.bc = bc_value * 1e-20 / e;          // C/m^2 -> e/A^2
+        if (kind == PGB_SET_POTENTIAL) b.bc = bc_value * eps0 * 1e-10 / e;  // V -> e/(eps0 A)
+        c->bodies.push_back(std::move(b));
+        c->tree_valid = false;
+        c->order_valid = false;
+        if (body_id_out) *body_id_out = (int32_t)c->bodies.size() - 1;
+        return PGB_OK;
+    });
+}
+
+int pgb_set_solvent(pgb_ctx* c, double eps_out, double kappa) {
+    if (!c) return PGB_EINVAL;
+    if (!(eps_out > 0 && isfinite(eps_out)) || !(kappa >= 0 && isfinite(kappa))) {
+        c->err = "eps_out must be > 0 and kappa >= 0";
+        return PGB_EINVAL;
+    }
+    c->eps_out = eps_out;
+    c->kappa = kappa;
+    c->tree_valid = false;
+    return PGB_OK;
+}
+
+int pgb_set_pose(pgb_ctx* c, int32_t id, const double R[9], const double t[3]) {
+    if (!c) return PGB_EINVAL;
+    if (id < 0 || id >= (int32_t)c->bodies.size() || !R || !t) {
+        c->err = "bad body id or pose";
+        return PGB_EINVAL;
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0;
+            for (int k = 0; k < 3; ++k) s += R[3 * i + k] * R[3 * j + k];
+            if (!(fabs(s - (i == j ? 1.0 : 0.0)) < 1e-9)) {
+                c->err = "R is not orthonormal";
+                return PGB_EINVAL;
+            }
+        }
+    double det = R[0] * (R[4] * R[8] - R[5] * R[7]) - R[1] * (R[3] * R[8] - R[5] * R[6]) + R[2] * (R[3] * R[7] - R[4] * R[6]);
+    if (!(det > 0) || !isfinite(t[0]) || !isfinite(t[1]) || !isfinite(t[2])) {
+        c->err = "R must be a proper rotation and t finite";
+        return PGB_EINVAL;
+    }
+    auto& b = c->bodies[id];
+    memcpy(b.R, R, sizeof(b.R));
+    memcpy(b.t, t, sizeof(b.t));
+    c->tree_valid = false;
+    return PGB_OK;
+}
+
+int pgb_tree_build(pgb_ctx* c) {
+    if (!c) return PGB_EINVAL;
+    return guard(c, [&]() -> int {
+        if (c->bodies.empty()) fail(PGB_ESTATE, "no bodies loaded");
+        StageTimer tm(c, PGB_STAGE_TREE);
+        if (!c->order_valid) {
+            upload_bodies(c);
+            build_order(c);
+        }
+        build_geometry(c);
+        build_lists(c);
+        build_corrections(c);
+        c->tree_valid = true;
+        return PGB_OK;
+    });
+}
+
+int pgb_tree_stats(pgb_ctx* c, pgb_tree_info* info) {
+    if (!c || !info) return PGB_EINVAL;
+    if (!c->tree_valid) {
+        c->err = "pgb_tree_build has not run";
+        return PGB_ESTATE;
+    }
+    info->n_panels = c->n_pan;
+    info->n_unknowns = c->n_unk;
+    info->n_nodes = c->n_nodes;
+    info->n_leaves = c->n_leaves;
+    info->n_groups = c->n_groups;
+    info->n_near = c->n_near;
+    info->n_far = c->n_far;
+    info->p2p_pairs = c->p2p_pairs;
+    info->p2p_laplace_pairs = c->p2p_lap;
+    info->m2p_pairs = c->m2p_pairs;
+    info->m2p_laplace_pairs = c->m2p_lap;
+    info->n_corrections = c->n_corr;
+    return PGB_OK;
+}
+
+int pgb_num_unknowns(pgb_ctx* c, int64_t* n) {
+    if (!c || !n) return PGB_EINVAL;
+    int64_t s = 0;
+    for (auto& b : c->bodies) s += b.kind == PGB_DIELECTRIC ? 2 * b.N : b.N;
+    *n = s;
+    return PGB_OK;
+}
+
+int pgb_matvec(pgb_ctx* c, const void* x, void* y, int32_t precision) {
+    if (!c) return PGB_EINVAL;
+    return guard(c, [&]() -> int {
+        if (!x || !y) fail(PGB_EINVAL, "null vector");
+        if (precision != PGB_FP32 && precision != PGB_FP64) fail(PGB_EINVAL, "precision must be PGB_FP32 or PGB_FP64");
+        if (!c->tree_valid) fail(PGB_ESTATE, "pgb_tree_build has not run for the current bodies and poses");
+        if (precision == PGB_FP64) {
+            apply_operator(c, (const double*)x, (double*)y, PGB_FP64, false);
+        } else {
+            c->d_xtmp.resize(c->n_unk);
+            c->d_ytmp.resize(c->n_unk);
+            convert_f32_f64((const float*)x, c->d_xtmp, c->n_unk, c->stream);
+            apply_operator(c, c->d_xtmp, c->d_ytmp, PGB_FP32, false);
+            convert_f64_f32(c->d_ytmp, (float*)y, c->n_unk, c->stream);
+        }
+        PGB_CUDA(cudaGetLastError());
+        return PGB_OK;
+    });
+}
+
+int pgb_rhs(pgb_ctx* c, double* b) {
+    if (!c) return PGB_EINVAL;
+    return guard(c, [&]() -> int {
+        if (!b) fail(PGB_EINVAL, "null vector");
+        if (!c->tree_valid) fail(PGB_ESTATE, "pgb_tree_build has not run");
+        build_rhs(c, b);
+        return PGB_OK;
+    });
+}
+
+int pgb_solve(pgb_ctx* c, int32_t mode, double tol, int32_t max_iter, int32_t restart, double* x,
+              pgb_solve_stats* st) {
+    if (!c) return PGB_EINVAL;
+    return guard(c, [&]() -> int {
+        if (!x) fail(PGB_EINVAL, "null x_out");
+        if (!(tol > 0 && tol < 1)) fail(PGB_EINVAL, "tol must be in (0, 1)");
+        if (max_iter < 1 || restart < 1 || restart > 256) fail(PGB_EINVAL, "max_iter >= 1 and restart in 1..256");
+        if (!c->tree_valid) fail(PGB_ESTATE, "pgb_tree_build has not run");
+        int r = solve(c, mode, tol, max_iter, restart, x, st);
+        PGB_CUDA(cudaStreamSynchronize(c->stream));
+        if (r == PGB_ENOCONV) c->err = "GMRES did not reach tol";
+        return r;
+    });
+}
+
+int pgb_energy(pgb_ctx* c, const double* x, pgb_energies* e, pgb_energies* per_body) {
+    if (!c) return PGB_EINVAL;
+    return guard(c, [&]() -> int {
+        if (!x || !e) fail(PGB_EINVAL, "null argument");
+        {
+            StageTimer tm(c, PGB_STAGE_ENERGY);
+            energies(c, x, e, per_body);
+        }
+        return PGB_OK;
+    });
+}
+
+int pgb_timing(pgb_ctx* c, int32_t enable, pgb_stage_times* out) {
+    if (!c) return PGB_EINVAL;
+    return guard(c, [&]() -> int {
+        if (out) {
+            collect_timing(c);
+            for (int i = 0; i < PGB_N_STAGES; ++i) {
+                out->ms[i] = c->stage_ms[i];
+                out->calls[i] = c->stage_calls[i];
+                c->stage_ms[i] = 0;
+                c->stage_calls[i] = 0;
+            }
+            out->kernel_launches = c->launches;
+            c->launches = 0;
+        }
+        c->timing = enable != 0;
+        return PGB_OK;
+    });
+}
+
+int pgb_tree_export(pgb_ctx* c, int32_t* perm, int64_t* near_off, int32_t* near_node, int64_t* far_off,
+                    int32_t* far_node) {
+    if (!c) return PGB_EINVAL;
+    return guard(c, [&]() -> int {
+        if (!c->tree_valid) fail(PGB_ESTATE, "pgb_tree_build has not run");
+        cudaStream_t s = c->stream;
+        if (perm) PGB_CUDA(cudaMemcpyAsync(perm, c->d_perm.p, 4 * c->n_pan, cudaMemcpyDeviceToHost, s));
+        if (near_off) PGB_CUDA(cudaMemcpyAsync(near_off, c->d_near_off.p, 8 * (c->n_groups + 1), cudaMemcpyDeviceToHost, s));
+        if (far_off) PGB_CUDA(cudaMemcpyAsync(far_off, c->d_far_off.p, 8 * (c->n_groups + 1), cudaMemcpyDeviceToHost, s));
+        if (near_node && c->n_near) PGB_CUDA(cudaMemcpyAsync(near_node, c->d_near.p, 4 * c->n_near, cudaMemcpyDeviceToHost, s));
+        if (far_node && c->n_far) PGB_CUDA(cudaMemcpyAsync(far_node, c->d_far.p, 4 * c->n_far, cudaMemcpyDeviceToHost, s));
+        PGB_CUDA(cudaStreamSynchronize(s));
+        return PGB_OK;
+    });
+}
+
+}  // extern "C"

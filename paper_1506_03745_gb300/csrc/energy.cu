@@ -1,0 +1,141 @@
+// Energies of Section 3.3 (Eq. 11-16) from a solution vector, FP64.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "pgb_internal.cuh"
+
+namespace pgb {
+
+// phi_reac(r_k) = -K_L(phi) + V_L(dphi) at each charge of a dielectric body
+// (Eq. 13), three-tier rule with r_k as target: 19-point rule when
+// |r_k - c_j| < 2 L_j, the K-point rule otherwise.  One block per charge.
+__global__ void k_phi_reac(Geo g, BodyDev bd, Rules r, const double* qxyz, const int32_t* qbody, const double* x,
+                           double* out) {
+    __shared__ double sh[32];
+    const int64_t k = blockIdx.x;
+    const int b = qbody[k];
+    const double xq[3] = {qxyz[3 * k], qxyz[3 * k + 1], qxyz[3 * k + 2]};
+    const int64_t s0 = bd.pan_off[b], s1 = bd.pan_off[b + 1], N = s1 - s0, o = bd.unk_off[b];
+    double acc = 0;
+    for (int64_t j = s0 + threadIdx.x; j < s1; j += blockDim.x) {
+        const int64_t loc = g.perm[j] - s0;
+        const double phi = x[o + loc], dphi = x[o + N + loc];
+        const double* cj = g.c + 3 * j;
+        const double* nj = g.n + 3 * j;
+        double dx = xq[0] - cj[0], dy = xq[1] - cj[1], dz = xq[2] - cj[2];
+        double d2 = dx * dx + dy * dy + dz * dz;
+        double vl = 0, kl = 0;
+        if (d2 < 8.0 * g.A[j]) {
+            const double* v = g.v + 9 * j;
+            for (int m = 0; m < r.Kn; ++m) {
+                double y[3];
+                for (int a = 0; a < 3; ++a)
+                    y[a] = cj[a] + ((r.mun[m][0] * (v[a] - cj[a]) + r.mun[m][1] * (v[3 + a] - cj[a])) +
+                                    r.mun[m][2] * (v[6 + a] - cj[a]));
+                double ex = xq[0] - y[0], ey = xq[1] - y[1], ez = xq[2] - y[2];
+                double rr = sqrt(ex * ex + ey * ey + ez * ez), ri = 1.0 / rr;
+                double w = r.wn[m] * g.A[j];
+                vl += w * ri;
+                kl += w * (nj[0] * ex + nj[1] * ey + nj[2] * ez) * ri * ri * ri;
+            }
+        } else {
+            for (int m = 0; m < g.K; ++m) {
+                const double* y = g.y + 3 * (j * g.K + m);
+                double ex = xq[0] - y[0], ey = xq[1] - y[1], ez = xq[2] - y[2];
+                double rr = sqrt(ex * ex + ey * ey + ez * ez), ri = 1.0 / rr;
+                double w = g.w[j * g.K + m];
+                vl += w * ri;
+                kl += w * (nj[0] * ex + nj[1] * ey + nj[2] * ez) * ri * ri * ri;
+            }
+        }
+        acc += vl * dphi - kl * phi;
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) out[k] = acc / PGB_FOUR_PI;
+}
+
+// per-body sums: [0] sum q phi_reac, [1] Coulomb sum_{k<l} q_k q_l / r_kl,
+// [2] sum_j u_j A_j (surfaces).  One block per body.
+__global__ void k_body_sums(Geo g, BodyDev bd, const double* qxyz, const double* qv, const int64_t* qoff,
+                            const double* phir, const double* x, double* out) {
+    __shared__ double sh[32];
+    const int b = blockIdx.x;
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int64_t k = qoff[b] + threadIdx.x; k < qoff[b + 1]; k += blockDim.x) {
+        s0 += qv[k] * phir[k];
+        for (int64_t l = k + 1; l < qoff[b + 1]; ++l) {
+            double dx = qxyz[3 * k] - qxyz[3 * l], dy = qxyz[3 * k + 1] - qxyz[3 * l + 1],
+                   dz = qxyz[3 * k + 2] - qxyz[3 * l + 2];
+            s1 += qv[k] * qv[l] / sqrt(dx * dx + dy * dy + dz * dz);
+        }
+    }
+    if (bd.kind[b] != PGB_DIELECTRIC) {
+        const int64_t p0 = bd.pan_off[b], p1 = bd.pan_off[b + 1];
+        for (int64_t j = p0 + threadIdx.x; j < p1; j += blockDim.x)
+            s2 += x[bd.unk_off[b] + (g.perm[j] - p0)] * g.A[j];
+    }
+    s0 = block_sum(s0, sh);
+    s1 = block_sum(s1, sh);
+    s2 = block_sum(s2, sh);
+    if (threadIdx.x == 0) {
+        out[3 * b] = s0;
+        out[3 * b + 1] = s1;
+        out[3 * b + 2] = s2;
+    }
+}
+
+// e^2/(eps0 Angstrom) in kcal/mol from CODATA 2018
+static double energy_unit_kcal() {
+    const double e = 1.602176634e-19, eps0 = 8.8541878128e-12, NA = 6.02214076e23;
+    return e * e / (eps0 * 1e-10) * NA / 4184.0;
+}
+
+void energies(pgb_ctx* c, const double* x, pgb_energies* e, pgb_energies* per_body) {
+    if (!c->tree_valid) fail(PGB_ESTATE, "pgb_tree_build has not run");
+    cudaStream_t s = c->stream;
+    const int nb = (int)c->bodies.size();
+    DBuf<double> phir, sums;
+    DBuf<int64_t> qoff;
+    phir.resize(std::max<int64_t>(1, c->n_q));
+    sums.resize(3 * nb);
+    std::vector<int64_t> qo(nb + 1);
+    for (int b = 0; b < nb; ++b) qo[b] = c->bodies[b].q_off;
+    qo[nb] = c->n_q;
+    qoff.resize(nb + 1);
+    PGB_CUDA(cudaMemcpyAsync(qoff.p, qo.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
+    Rules r = make_rules(c->p.K, c->p.K_near, c->p.n_edge);
+    if (c->n_q) k_phi_reac<<<(unsigned)c->n_q, 128, 0, s>>>(geo(c), body_dev(c), r, c->d_qxyz, c->d_q_body, x, phir);
+    k_body_sums<<<nb, 128, 0, s>>>(geo(c), body_dev(c), c->d_qxyz, c->d_qval, qoff, phir, x, sums);
+    PGB_CUDA(cudaGetLastError());
+    PGB_LAUNCHED(c, c->n_q ? 2 : 1);
+    std::vector<double> h(3 * nb);
+    PGB_CUDA(cudaMemcpyAsync(h.data(), sums.p, 8 * 3 * nb, cudaMemcpyDeviceToHost, s));
+    PGB_CUDA(cudaStreamSynchronize(s));
+    const double U = energy_unit_kcal();
+    pgb_energies tot{0, 0, 0, 0};
+    for (int b = 0; b < nb; ++b) {
+        const auto& bd = c->bodies[b];
+        pgb_energies eb{0, 0, 0, 0};
+        if (bd.kind == PGB_DIELECTRIC) {
+            eb.solvation = 0.5 * h[3 * b] * U;
+            eb.coulomb = h[3 * b + 1] / (PGB_FOUR_PI * bd.eps_in) * U;
+        } else if (bd.kind == PGB_SET_CHARGE) {
+            eb.surface = 0.5 * bd.bc * h[3 * b + 2] * U;  // 1/2 sum phi_j sigma0 A_j
+        } else {
+            // -1/2 sum phi0 sigma_j A_j with sigma_j = -eps_out dphi_j
+            eb.surface = 0.5 * c->eps_out * bd.bc * h[3 * b + 2] * U;
+        }
+        eb.total = eb.coulomb + eb.solvation + eb.surface;
+        tot.coulomb += eb.coulomb;
+        tot.solvation += eb.solvation;
+        tot.surface += eb.surface;
+        tot.total += eb.total;
+        if (per_body) per_body[b] = eb;
+    }
+    if (e) *e = tot;
+}
+
+}  // namespace pgb

@@ -1,0 +1,181 @@
+// Treecode matvec driver: source densities, upward pass + evaluation,
+// near-field corrections and the block rows of Eq. 6 / Eq. 7.
+#include <algorithm>
+
+#include "treecode.cuh"
+
+namespace pgb {
+
+void treecode_launch_f32(int stage, int P, const UpArgs& up, const EvalArgs& ev, const void* src, const void* xrel,
+                         void* mom, cudaStream_t s);
+void treecode_launch_f64(int stage, int P, const UpArgs& up, const EvalArgs& ev, const void* src, const void* xrel,
+                         void* mom, cudaStream_t s);
+
+static inline int nblk(int64_t n, int t) { return (int)std::max<int64_t>(1, (n + t - 1) / t); }
+
+// Panel densities (psi_L, psi_Y, phi) of the combined potential U = S_V - S_K
+// for every sorted panel, and the per-point source terms
+// A = {y - c_leaf, w psi_L}, B = {w phi n, w psi_Y}.
+//   dielectric: psi_L = dphi, psi_Y = (eps_in/eps_out) dphi, phi = phi
+//   imposed potential: psi_Y = u; imposed charge: phi = u
+// known == true builds the imposed-boundary densities instead: phi0 as the
+// double-layer density of an imposed-potential surface, dphi = -sigma0/eps_out
+// as the single layer of an imposed-charge surface, zero on molecules.
+template <typename real>
+__global__ void k_src_prep(Geo g, BodyDev bd, const double* __restrict__ x, bool known,
+                           const typename V4<real>::t* __restrict__ yrel, typename V4<real>::t* __restrict__ src,
+                           double* __restrict__ dens, double eps_out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= g.n_pan) return;
+    const int b = g.pbody[i];
+    const int64_t loc = g.perm[i] - bd.pan_off[b];
+    const int64_t N = bd.pan_off[b + 1] - bd.pan_off[b];
+    const int64_t o = bd.unk_off[b];
+    double psiL = 0, psiY = 0, phi = 0;
+    const int kind = bd.kind[b];
+    if (!known) {
+        if (kind == PGB_DIELECTRIC) {
+            phi = x[o + loc];
+            psiL = x[o + N + loc];
+            psiY = bd.eps_ratio[b] * psiL;
+        } else if (kind == PGB_SET_POTENTIAL) {
+            psiY = x[o + loc];
+        } else {
+            phi = x[o + loc];
+        }
+    } else {
+        if (kind == PGB_SET_POTENTIAL) phi = bd.bc[b];
+        else if (kind == PGB_SET_CHARGE) psiY = -bd.bc[b] / eps_out;
+    }
+    dens[3 * i] = psiL;
+    dens[3 * i + 1] = psiY;
+    dens[3 * i + 2] = phi;
+    const double nx = g.n[3 * i], ny = g.n[3 * i + 1], nz = g.n[3 * i + 2];
+    for (int m = 0; m < g.K; ++m) {
+        const int64_t p = i * g.K + m;
+        const double w = g.w[p];
+        typename V4<real>::t A = yrel[p], B;
+        A.w = (real)(w * psiL);
+        B.x = (real)(w * phi * nx);
+        B.y = (real)(w * phi * ny);
+        B.z = (real)(w * phi * nz);
+        B.w = (real)(w * psiY);
+        src[2 * p] = A;
+        src[2 * p + 1] = B;
+    }
+}
+
+// U += near-field corrections (FP64), then the rows of Eq. 6 / Eq. 7 in the
+// caller's layout.  mode 0: y = A x.  mode 1: right-hand side of the imposed
+// boundary terms, -(U + jump) on exterior and surface rows.
+__global__ void k_assemble(Geo g, BodyDev bd, const double* __restrict__ U, const double* __restrict__ dens,
+                           const int64_t* __restrict__ coff, const int32_t* __restrict__ cj,
+                           const dbl4* __restrict__ cval, int mode, double* __restrict__ y) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= g.n_pan) return;
+    const double inv4pi = 1.0 / PGB_FOUR_PI;
+    double UL = U[2 * i] * inv4pi, UY = U[2 * i + 1] * inv4pi;
+    for (int64_t e = coff[i]; e < coff[i + 1]; ++e) {
+        const int64_t j = cj[e];
+        const dbl4 d = cval[e];
+        const double psiL = dens[3 * j], psiY = dens[3 * j + 1], phi = dens[3 * j + 2];
+        UL += d.x * psiL - d.y * phi;
+        UY += d.z * psiY - d.w * phi;
+    }
+    const int b = g.pbody[i];
+    const int64_t loc = g.perm[i] - bd.pan_off[b];
+    const int64_t N = bd.pan_off[b + 1] - bd.pan_off[b];
+    const int64_t o = bd.unk_off[b];
+    const int kind = bd.kind[b];
+    if (mode == 0) {
+        const double phi = dens[3 * i + 2];
+        if (kind == PGB_DIELECTRIC) {
+            y[o + loc] = 0.5 * phi - UL;
+            y[o + N + loc] = 0.5 * phi + UY;
+        } else if (kind == PGB_SET_CHARGE) {
+            y[o + loc] = UY + 0.5 * phi;
+        } else {
+            y[o + loc] = UY;
+        }
+    } else {
+        if (kind == PGB_DIELECTRIC) y[o + N + loc] = -UY;
+        else if (kind == PGB_SET_CHARGE) y[o + loc] = -UY;
+        else y[o + loc] = -(UY + 0.5 * bd.bc[b]);
+    }
+}
+
+__global__ void k_f32_to_f64(const float* a, double* b, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[i];
+}
+__global__ void k_f64_to_f32(const double* a, float* b, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+void convert_f32_f64(const float* a, double* b, int64_t n, cudaStream_t s) {
+    k_f32_to_f64<<<nblk(n, 256), 256, 0, s>>>(a, b, n);
+}
+void convert_f64_f32(const double* a, float* b, int64_t n, cudaStream_t s) {
+    k_f64_to_f32<<<nblk(n, 256), 256, 0, s>>>(a, b, n);
+}
+
+void apply_operator(pgb_ctx* c, const double* x, double* y, int precision, bool known_only) {
+    if (!c->tree_valid) fail(PGB_ESTATE, "pgb_tree_build has not run for the current bodies and poses");
+    cudaStream_t s = c->stream;
+    Geo g = geo(c);
+    BodyDev bd = body_dev(c);
+    const int P = c->p.P;
+    const int T = n_terms(P);
+    const int64_t nsrc = g.n_src;
+    c->d_dens.resize(3 * c->n_pan);
+    c->d_U.resize(2 * c->n_pan);
+    UpArgs up;
+    up.n_leaves = c->n_leaves;
+    up.leaf_node = c->d_leaf_node; up.nstart = c->d_node_start; up.nend = c->d_node_end;
+    up.parent = c->d_node_parent; up.child = c->d_node_child; up.nchild = c->d_node_nchild;
+    up.ncenter = c->d_node_center; up.K = c->p.K; up.counter = c->d_up_counter;
+    EvalArgs ev;
+    ev.n_groups = c->n_groups;
+    ev.gstart = c->d_group_start; ev.gend = c->d_group_end; ev.gbody = c->d_group_body;
+    ev.gcenter = c->d_group_center; ev.near_off = c->d_near_off; ev.far_off = c->d_far_off;
+    ev.near_l = c->d_near; ev.far_l = c->d_far; ev.nstart = c->d_node_start; ev.nend = c->d_node_end;
+    ev.nbody = c->d_node_body; ev.ncenter = c->d_node_center; ev.K = c->p.K; ev.kappa = c->kappa;
+    for (int b = 0; b < PGB_MAX_BODIES; ++b) ev.lap_body[b] = 0;
+    for (size_t b = 0; b < c->bodies.size(); ++b) ev.lap_body[b] = c->bodies[b].kind == PGB_DIELECTRIC;
+    ev.U = c->d_U;
+    const bool f32 = precision == PGB_FP32;
+    if (f32) {
+        c->d_src32.resize(2 * nsrc);
+        c->d_mom32.resize((size_t)c->n_nodes * 2 * T);
+    } else {
+        c->d_src64.resize(2 * nsrc);
+        c->d_mom64.resize((size_t)c->n_nodes * 2 * T);
+    }
+    {
+        StageTimer tm(c, PGB_STAGE_SOURCES);
+        if (f32)
+            k_src_prep<float><<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, x, known_only, c->d_y32, c->d_src32,
+                                                                  c->d_dens, c->eps_out);
+        else
+            k_src_prep<double><<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, x, known_only, c->d_y64, c->d_src64,
+                                                                   c->d_dens, c->eps_out);
+        PGB_CUDA(cudaGetLastError());
+        PGB_LAUNCHED(c, 1);
+    }
+    for (int stage : {PGB_STAGE_UPWARD, PGB_STAGE_EVAL}) {
+        StageTimer tm(c, stage);
+        if (f32) treecode_launch_f32(stage, P, up, ev, c->d_src32, c->d_x32, c->d_mom32, s);
+        else treecode_launch_f64(stage, P, up, ev, c->d_src64, c->d_x64, c->d_mom64, s);
+        PGB_CUDA(cudaGetLastError());
+        PGB_LAUNCHED(c, 1);
+    }
+    {
+        StageTimer tm(c, PGB_STAGE_ASSEMBLE);
+        k_assemble<<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, c->d_U, c->d_dens, c->d_corr_off, c->d_corr_j,
+                                                       c->d_corr_val, known_only ? 1 : 0, y);
+        PGB_CUDA(cudaGetLastError());
+        PGB_LAUNCHED(c, 1);
+    }
+}
+
+}  // namespace pgb

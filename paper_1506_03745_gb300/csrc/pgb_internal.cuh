@@ -1,0 +1,219 @@
+// Internal declarations shared by the translation units of libpgb.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pgb.h"
+
+#define PGB_MAX_P 8
+#define PGB_MAX_BODIES 64
+#define PGB_LIST_STACK 96
+
+namespace pgb {
+
+struct __align__(32) dbl4 {
+    double x, y, z, w;
+};
+
+// Status carried through host code as an exception inside the library only;
+// the C entry points turn it into a return code.
+struct Error {
+    int code;
+    std::string msg;
+};
+
+void cuda_check(cudaError_t e, const char* what);
+#define PGB_CUDA(call) ::pgb::cuda_check((call), #call)
+void fail(int code, const std::string& msg);
+
+template <typename T>
+struct DBuf {  // owning device buffer
+    T* p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    ~DBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    void resize(size_t count) {  // contents undefined after growth
+        if (count <= n && p) return;
+        release();
+        size_t c = count ? count : 1;
+        cudaError_t e = cudaMalloc(&p, c * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            (void)cudaGetLastError();
+            fail(PGB_ENOMEM, "cudaMalloc of " + std::to_string(c * sizeof(T)) + " bytes failed");
+        }
+        n = c;
+    }
+    operator T*() const { return p; }
+};
+
+// Taylor term count of total degree <= P in three variables.
+constexpr int n_terms(int P) { return (P + 1) * (P + 2) * (P + 3) / 6; }
+
+struct Body {
+    int kind = PGB_DIELECTRIC;
+    double eps_in = 1.0;
+    double bc = 0.0;  // internal units: sigma0 in e/A^2, phi0 in e/(eps0 A)
+    int64_t N = 0, nv = 0, nq = 0;
+    std::vector<double> verts;  // body frame
+    std::vector<int32_t> tris;
+    std::vector<double> qxyz, qval;
+    double R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    double t[3] = {0, 0, 0};
+    bool identity_pose = true;
+    // offsets into global arrays
+    int64_t pan_off = 0, unk_off = 0, q_off = 0, v_off = 0;
+    // tree frame
+    double lo[3] = {0, 0, 0}, ext = 1.0;
+    int32_t root = 0;
+};
+
+// Device-side view of the problem passed by value to kernels.
+struct Geo {
+    int64_t n_pan, n_src;
+    int K;
+    // per sorted panel
+    const int32_t* perm;       // sorted -> global original panel index
+    const int32_t* pbody;      // body id
+    const double* v;           // 9 per panel, world
+    const double* c;           // 3 per panel (world centroid)
+    const double* n;           // 3 per panel (unit normal)
+    const double* A;           // area
+    const int32_t* pleaf;      // leaf index of the panel
+    // per source point
+    const double* y;           // 3 per point
+    const double* w;           // weight * area
+};
+
+struct BodyDev {  // per-body constants for kernels
+    int kind[PGB_MAX_BODIES];
+    double eps_ratio[PGB_MAX_BODIES];  // eps_in / eps_out (dielectric)
+    double bc[PGB_MAX_BODIES];
+    int64_t pan_off[PGB_MAX_BODIES + 1];
+    int64_t unk_off[PGB_MAX_BODIES];
+    int n_bodies;
+};
+
+}  // namespace pgb
+
+struct pgb_ctx {
+    pgb_params p;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    double eps_out = 80.0, kappa = 0.0;
+    std::vector<pgb::Body> bodies;
+    bool tree_valid = false;
+    bool order_valid = false;  // Morton order / octree structure (body frame)
+    int64_t n_pan = 0, n_unk = 0, n_q = 0, n_verts = 0;
+
+    // inputs on the device
+    pgb::DBuf<double> d_vb;      // body-frame vertices, all bodies
+    pgb::DBuf<int32_t> d_tris;   // global vertex ids, original panel order
+    pgb::DBuf<int32_t> d_pan_body;
+    pgb::DBuf<double> d_qxyz_body, d_qval, d_qxyz;  // charges (body frame / world)
+    pgb::DBuf<int32_t> d_q_body;
+    pgb::DBuf<double> d_pose;    // 12 per body (R row-major, t)
+
+    // ordering and tree structure (body frame; rebuilt when meshes change)
+    pgb::DBuf<int32_t> d_perm, d_inv;    // sorted -> original global, and inverse
+    pgb::DBuf<uint32_t> d_key;           // sorted keys
+    pgb::DBuf<int32_t> d_qcell;          // 3 per sorted panel
+    int64_t n_nodes = 0, n_leaves = 0;
+    pgb::DBuf<int32_t> d_node_start, d_node_end, d_node_level, d_node_child, d_node_nchild, d_node_body;
+    pgb::DBuf<int32_t> d_node_leaf0, d_node_leaf1, d_leaf_node, d_node_parent;
+    pgb::DBuf<unsigned int> d_up_counter;
+    std::vector<int32_t> h_node_level;   // for per-level passes
+    std::vector<int64_t> level_begin;    // node id ranges by level
+    pgb::DBuf<int32_t> d_pan_leaf;
+
+    // world geometry (per pose)
+    pgb::DBuf<double> d_v, d_c, d_n, d_A, d_y, d_w;
+    pgb::DBuf<int32_t> d_pbody;          // body of sorted panel
+    pgb::DBuf<double> d_node_center, d_node_r2, d_node_clo, d_node_chi, d_node_a8;
+    pgb::DBuf<float4> d_y32;             // point - leaf centre, weight
+    pgb::DBuf<pgb::dbl4> d_y64;
+    // target groups
+    int64_t n_groups = 0;
+    pgb::DBuf<int32_t> d_group_start, d_group_end, d_group_body;
+    pgb::DBuf<double> d_group_lo, d_group_hi, d_group_center;
+    pgb::DBuf<float4> d_x32;             // centroid - group centre
+    pgb::DBuf<pgb::dbl4> d_x64;
+    // lists
+    int64_t n_near = 0, n_far = 0;
+    pgb::DBuf<int64_t> d_near_off, d_far_off;
+    pgb::DBuf<int32_t> d_near, d_far;
+    // near-field corrections (CSR over sorted targets)
+    int64_t n_corr = 0;
+    pgb::DBuf<int64_t> d_corr_off;
+    pgb::DBuf<int32_t> d_corr_j;
+    pgb::DBuf<pgb::dbl4> d_corr_val;       // dVL, dKL, dVY, dKY
+
+    // matvec work buffers
+    pgb::DBuf<float4> d_src32;           // 2 per point
+    pgb::DBuf<pgb::dbl4> d_src64;
+    pgb::DBuf<double> d_dens;            // 3 per sorted panel: psiL, psiY, phi
+    pgb::DBuf<float> d_mom32;            // 2*T per node
+    pgb::DBuf<double> d_mom64;
+    pgb::DBuf<double> d_U;               // 2 per sorted panel: UL, UY
+    pgb::DBuf<double> d_xtmp, d_ytmp;    // FP64 staging for FP32 matvec API
+    // scratch
+    pgb::DBuf<int64_t> d_scan_tmp;
+    pgb::DBuf<unsigned char> d_scratch;
+
+    // solver
+    pgb::DBuf<double> d_V, d_H, d_red, d_gv, d_b, d_r, d_wk, d_xs, d_small;
+    double* h_pinned = nullptr;
+
+    // statistics and stage timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+    double stage_ms[PGB_N_STAGES] = {0};
+    int64_t stage_calls[PGB_N_STAGES] = {0};
+    int64_t launches = 0;
+    pgb_tree_info info{};
+    int64_t p2p_pairs = 0, p2p_lap = 0, m2p_pairs = 0, m2p_lap = 0;
+};
+
+namespace pgb {
+// CUDA-event interval on the context stream around one stage (no-op when
+// timing is off).
+struct StageTimer {
+    pgb_ctx* c;
+    int stage;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    StageTimer(pgb_ctx* ctx, int st);
+    ~StageTimer();
+};
+void collect_timing(pgb_ctx* c);
+#define PGB_LAUNCHED(c, k) ((c)->launches += (k))
+// geometry / tree (tree.cu)
+void upload_bodies(pgb_ctx* c);
+void build_order(pgb_ctx* c);
+void build_geometry(pgb_ctx* c);
+void build_lists(pgb_ctx* c);
+void build_corrections(pgb_ctx* c);
+BodyDev body_dev(const pgb_ctx* c);
+Geo geo(const pgb_ctx* c);
+// scans (tree.cu)
+void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s, int64_t* total_host);
+// matvec (matvec.cu)
+void apply_operator(pgb_ctx* c, const double* x, double* y, int precision, bool known_only);
+// solver (solver.cu)
+void build_rhs(pgb_ctx* c, double* b);
+int solve(pgb_ctx* c, int mode, double tol, int max_iter, int restart, double* x, pgb_solve_stats* st);
+// energy (energy.cu)
+void energies(pgb_ctx* c, const double* x, pgb_energies* e, pgb_energies* per_body);
+// quadrature tables on the device (geometry.cu)
+void rule_host(int K, const double** mu, const double** w);
+}  // namespace pgb

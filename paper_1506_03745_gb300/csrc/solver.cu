@@ -1,0 +1,333 @@
+// Right-hand side and GMRES (Section 3.2 of the paper): FP64 Arnoldi with
+// classical Gram-Schmidt applied twice, Givens rotations on the device, the
+// restarted iteration driven from the host; optional FP32 inner solves with
+// FP64 residual refinement.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "pgb_internal.cuh"
+
+namespace pgb {
+
+static inline int nblk(int64_t n, int t) { return (int)std::max<int64_t>(1, (n + t - 1) / t); }
+
+// Coulomb rows (first line of Eq. 5, with its 1/eps_in kept -- reading of
+// Eq. 6/7): (1/eps_in) sum_k q_k / (4 pi |c_i - r_k|) over the body's charges.
+__global__ void k_coulomb_rows(Geo g, BodyDev bd, const double* qxyz, const double* qv, const int64_t* qoff,
+                               const double* eps_in, double* b) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= g.n_pan) return;
+    const int bi = g.pbody[i];
+    if (bd.kind[bi] != PGB_DIELECTRIC) return;
+    const double x = g.c[3 * i], y = g.c[3 * i + 1], z = g.c[3 * i + 2];
+    double s = 0;
+    for (int64_t k = qoff[bi]; k < qoff[bi + 1]; ++k) {
+        double dx = x - qxyz[3 * k], dy = y - qxyz[3 * k + 1], dz = z - qxyz[3 * k + 2];
+        s += qv[k] / sqrt(dx * dx + dy * dy + dz * dz);
+    }
+    const int64_t loc = g.perm[i] - bd.pan_off[bi];
+    b[bd.unk_off[bi] + loc] = s / (PGB_FOUR_PI * eps_in[bi]);
+}
+
+void build_rhs(pgb_ctx* c, double* b) {
+    cudaStream_t s = c->stream;
+    StageTimer tm(c, PGB_STAGE_RHS);
+    PGB_CUDA(cudaMemsetAsync(b, 0, 8 * c->n_unk, s));
+    bool any_known = false;
+    for (auto& bd : c->bodies) any_known |= bd.kind != PGB_DIELECTRIC;
+    if (any_known) apply_operator(c, nullptr, b, PGB_FP64, true);
+    std::vector<int64_t> qoff(c->bodies.size() + 1, 0);
+    std::vector<double> eps(c->bodies.size());
+    for (size_t i = 0; i < c->bodies.size(); ++i) {
+        qoff[i] = c->bodies[i].q_off;
+        eps[i] = c->bodies[i].eps_in;
+    }
+    qoff.back() = c->n_q;
+    DBuf<int64_t> dq;
+    DBuf<double> de;
+    dq.resize(qoff.size());
+    de.resize(eps.size());
+    PGB_CUDA(cudaMemcpyAsync(dq.p, qoff.data(), 8 * qoff.size(), cudaMemcpyHostToDevice, s));
+    PGB_CUDA(cudaMemcpyAsync(de.p, eps.data(), 8 * eps.size(), cudaMemcpyHostToDevice, s));
+    k_coulomb_rows<<<nblk(c->n_pan, 128), 128, 0, s>>>(geo(c), body_dev(c), c->d_qxyz, c->d_qval, dq, de, b);
+    PGB_CUDA(cudaGetLastError());
+    PGB_LAUNCHED(c, 2);
+    PGB_CUDA(cudaStreamSynchronize(s));
+}
+
+// ---------------------------------------------------------------- BLAS-1/2
+#define DOT_BLOCKS 304
+#define DOT_THREADS 256
+
+// partial[i * nb + blk] = sum over this block's rows of V_i . w, i < m
+__global__ void k_multi_dot(const double* __restrict__ V, int64_t ld, int m, const double* __restrict__ w, int64_t n,
+                            double* partial) {
+    __shared__ double sh[DOT_THREADS / 32];
+    for (int i = 0; i < m; ++i) {
+        const double* v = V + i * ld;
+        double s = 0;
+        for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+            s += v[r] * w[r];
+        s = block_sum(s, sh);
+        if (threadIdx.x == 0) partial[(int64_t)i * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+// out[i] = (accumulate ? out[i] : 0) + sum_b partial[i*nb + b]   (one block per i)
+__global__ void k_reduce_partials(const double* partial, int nb, double* out, int accumulate, int sqrt_out) {
+    __shared__ double sh[32];
+    int i = blockIdx.x;
+    double s = 0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partial[(int64_t)i * nb + b];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) {
+        if (sqrt_out) s = sqrt(s);
+        out[i] = accumulate ? out[i] + s : s;
+    }
+}
+
+// w -= sum_i h[i] V_i   (sign = -1)  or  x += sum_i h[i] V_i (sign = +1)
+__global__ void k_multi_axpy(const double* __restrict__ V, int64_t ld, int m, const double* __restrict__ h, double sign,
+                             double* __restrict__ w, int64_t n) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0;
+        for (int i = 0; i < m; ++i) s += h[i] * V[i * ld + r];
+        w[r] += sign * s;
+    }
+}
+
+// v = w / *nrm
+__global__ void k_scale_by(const double* w, const double* nrm, double* v, int64_t n) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double a = *nrm;
+    if (r < n) v[r] = a > 0 ? w[r] / a : 0.0;
+}
+
+__global__ void k_axpby(double a, const double* x, double b, const double* y, double* out, int64_t n) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r < n) out[r] = a * x[r] + b * y[r];
+}
+
+// Givens step on column j of H (column-major, ld = m+1): apply the previous
+// rotations, form the new one, rotate g; out[0] = |g_{j+1}|, out[1] = h_{j+1,j}.
+__global__ void k_givens(double* H, int ld, double* cs, double* sn, double* g, int j, double* out) {
+    if (threadIdx.x || blockIdx.x) return;
+    double* h = H + (int64_t)j * ld;
+    for (int i = 0; i < j; ++i) {
+        double a = cs[i] * h[i] + sn[i] * h[i + 1];
+        double b = -sn[i] * h[i] + cs[i] * h[i + 1];
+        h[i] = a;
+        h[i + 1] = b;
+    }
+    out[1] = h[j + 1];
+    double a = h[j], b = h[j + 1];
+    double r = hypot(a, b);
+    double c = r > 0 ? a / r : 1.0, s = r > 0 ? b / r : 0.0;
+    cs[j] = c;
+    sn[j] = s;
+    h[j] = r;
+    h[j + 1] = 0;
+    g[j + 1] = -s * g[j];
+    g[j] = c * g[j];
+    out[0] = fabs(g[j + 1]);
+}
+
+// y = H(0:k,0:k)^{-1} g(0:k) (upper triangular)
+__global__ void k_backsolve(const double* H, int ld, const double* g, int k, double* y) {
+    if (threadIdx.x || blockIdx.x) return;
+    for (int i = k - 1; i >= 0; --i) {
+        double s = g[i];
+        for (int j = i + 1; j < k; ++j) s -= H[(int64_t)j * ld + i] * y[j];
+        y[i] = H[(int64_t)i * ld + i] != 0 ? s / H[(int64_t)i * ld + i] : 0.0;
+    }
+}
+
+__global__ void k_init_g(double* g, int m1, const double* beta) {
+    int i = threadIdx.x + blockIdx.x * blockDim.x;
+    if (i < m1) g[i] = (i == 0) ? *beta : 0.0;
+}
+
+struct Krylov {
+    pgb_ctx* c;
+    int64_t n;
+    int m;
+    cudaStream_t s;
+
+    void norm(const double* w, double* out) {
+        k_multi_dot<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(w, n, 1, w, n, c->d_red);
+        k_reduce_partials<<<1, 256, 0, s>>>(c->d_red, DOT_BLOCKS, out, 0, 1);
+    }
+    double host_read(const double* d) {
+        PGB_CUDA(cudaMemcpyAsync(c->h_pinned, d, 8, cudaMemcpyDeviceToHost, s));
+        PGB_CUDA(cudaStreamSynchronize(s));
+        return c->h_pinned[0];
+    }
+};
+
+// Restarted GMRES on A x = b from the given x; precision of the operator
+// `prec`; stops when the (estimated) residual <= abs_tol or after max_it
+// iterations.  Returns iterations done; *matvecs counts operator uses.
+static int gmres(pgb_ctx* c, int prec, const double* b, double* x, double abs_tol, int max_it, int restart,
+                 int* matvecs, double* est_out, bool x_zero) {
+    const int64_t n = c->n_unk;
+    const int m = restart;
+    cudaStream_t s = c->stream;
+    Krylov K{c, n, m, s};
+    c->d_V.resize((size_t)(m + 1) * n);
+    c->d_H.resize((size_t)(m + 1) * m);
+    c->d_red.resize((size_t)DOT_BLOCKS * (m + 1));
+    c->d_gv.resize(3 * (m + 1) + 8);
+    c->d_wk.resize(n);
+    c->d_small.resize(2 * (m + 1) + 8);
+    double* cs = c->d_gv.p;
+    double* sn = cs + (m + 1);
+    double* g = sn + (m + 1);
+    double* hcol = c->d_small.p;       // m+1 (current H column tail workspace)
+    double* yv = hcol + (m + 1);       // m+1
+    DBuf<double> misc;
+    misc.resize(8);
+    int it = 0;
+    double est = INFINITY;
+    while (it < max_it) {
+        // r = b - A x (x = 0 on entry needs no product)
+        if (x_zero) {
+            PGB_CUDA(cudaMemcpyAsync(c->d_wk.p, b, 8 * n, cudaMemcpyDeviceToDevice, s));
+            x_zero = false;
+        } else {
+            apply_operator(c, x, c->d_wk, prec, false);
+            ++*matvecs;
+            k_axpby<<<nblk(n, 256), 256, 0, s>>>(1.0, b, -1.0, c->d_wk, c->d_wk, n);
+        }
+        K.norm(c->d_wk, misc.p);
+        PGB_LAUNCHED(c, 3);
+        double beta = K.host_read(misc.p);
+        est = beta;
+        if (beta <= abs_tol || beta == 0) break;
+        k_scale_by<<<nblk(n, 256), 256, 0, s>>>(c->d_wk, misc.p, c->d_V, n);
+        k_init_g<<<1, 256, 0, s>>>(g, m + 1, misc.p);
+        int j = 0;
+        for (; j < m && it < max_it; ++j, ++it) {
+            double* vj = c->d_V.p + (size_t)j * n;
+            double* w = c->d_wk.p;
+            apply_operator(c, vj, w, prec, false);
+            ++*matvecs;
+            double* h = c->d_H.p + (size_t)j * (m + 1);
+            {
+                StageTimer tm(c, PGB_STAGE_KRYLOV);
+                for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+                    k_multi_dot<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(c->d_V, n, j + 1, w, n, c->d_red);
+                    k_reduce_partials<<<j + 1, 256, 0, s>>>(c->d_red, DOT_BLOCKS, pass ? hcol : h, 0, 0);
+                    k_multi_axpy<<<nblk(n, 256), 256, 0, s>>>(c->d_V, n, j + 1, pass ? hcol : h, -1.0, w, n);
+                    if (pass) k_axpby<<<1, 256, 0, s>>>(1.0, h, 1.0, hcol, h, j + 1);
+                }
+                K.norm(w, h + j + 1);
+                k_scale_by<<<nblk(n, 256), 256, 0, s>>>(w, h + j + 1, c->d_V.p + (size_t)(j + 1) * n, n);
+                k_givens<<<1, 1, 0, s>>>(c->d_H, m + 1, cs, sn, g, j, misc.p + 2);
+                PGB_CUDA(cudaGetLastError());
+                PGB_LAUNCHED(c, 12);
+            }
+            PGB_CUDA(cudaMemcpyAsync(c->h_pinned, misc.p + 2, 16, cudaMemcpyDeviceToHost, s));
+            PGB_CUDA(cudaStreamSynchronize(s));
+            est = c->h_pinned[0];
+            double hnext = c->h_pinned[1];
+            if (est <= abs_tol || !(hnext > 0)) {
+                ++j;
+                ++it;
+                break;
+            }
+        }
+        k_backsolve<<<1, 1, 0, s>>>(c->d_H, m + 1, g, j, yv);
+        k_multi_axpy<<<nblk(n, 256), 256, 0, s>>>(c->d_V, n, j, yv, 1.0, x, n);
+        PGB_CUDA(cudaGetLastError());
+        PGB_LAUNCHED(c, 2);
+        if (est <= abs_tol) break;
+    }
+    if (est_out) *est_out = est;
+    return it;
+}
+
+static double vec_norm(pgb_ctx* c, const double* v) {
+    PGB_LAUNCHED(c, 2);
+    Krylov K{c, c->n_unk, 0, c->stream};
+    DBuf<double> t;
+    t.resize(1);
+    c->d_red.resize(std::max<size_t>(c->d_red.n, DOT_BLOCKS));
+    K.norm(v, t);
+    return K.host_read(t);
+}
+
+int solve(pgb_ctx* c, int mode, double tol, int max_iter, int restart, double* x, pgb_solve_stats* st) {
+    const int64_t n = c->n_unk;
+    cudaStream_t s = c->stream;
+    c->d_b.resize(n);
+    c->d_r.resize(n);
+    c->d_xs.resize(n);
+    c->d_red.resize((size_t)DOT_BLOCKS * (restart + 1));
+    build_rhs(c, c->d_b);
+    pgb_solve_stats z{};
+    int fp64_mv = 0;
+    for (auto& b : c->bodies)
+        if (b.kind != PGB_DIELECTRIC) {
+            fp64_mv = 1;  // imposed-boundary terms of the right-hand side
+            break;
+        }
+    z.matvecs = fp64_mv;
+    z.matvecs_fp64 = fp64_mv;
+    const double bnorm = vec_norm(c, c->d_b);
+    PGB_CUDA(cudaMemsetAsync(x, 0, 8 * n, s));
+    if (bnorm == 0) {
+        z.outer_steps = 0;
+        z.rel_residual = 0;
+        if (st) *st = z;
+        return PGB_OK;
+    }
+    double rel = 1.0;
+    if (mode == PGB_FP64) {
+        int mv = 0;
+        z.iterations = gmres(c, PGB_FP64, c->d_b, x, tol * bnorm, max_iter, restart, &mv, nullptr, true);
+        z.matvecs += mv;
+        z.matvecs_fp64 += mv;
+        z.outer_steps = 1;
+        apply_operator(c, x, c->d_r, PGB_FP64, false);
+        ++z.matvecs;
+        ++z.matvecs_fp64;
+        k_axpby<<<nblk(n, 256), 256, 0, s>>>(1.0, c->d_b, -1.0, c->d_r, c->d_r, n);
+        rel = vec_norm(c, c->d_r) / bnorm;
+    } else if (mode == PGB_FP32_REFINE) {
+        // r = b (x = 0); outer: solve A32 d = r, x += d, r = b - A64 x
+        PGB_CUDA(cudaMemcpyAsync(c->d_r.p, c->d_b.p, 8 * n, cudaMemcpyDeviceToDevice, s));
+        double rn = bnorm;
+        while (rel > tol && z.iterations < max_iter && z.outer_steps < 50) {
+            double inner = std::max(tol * bnorm / rn, 1e-4);
+            PGB_CUDA(cudaMemsetAsync(c->d_xs.p, 0, 8 * n, s));
+            int mv = 0;
+            int it = gmres(c, PGB_FP32, c->d_r, c->d_xs, inner * rn, max_iter - z.iterations, restart, &mv, nullptr, true);
+            z.iterations += it;
+            z.matvecs += mv;
+            ++z.outer_steps;
+            k_axpby<<<nblk(n, 256), 256, 0, s>>>(1.0, x, 1.0, c->d_xs, x, n);
+            apply_operator(c, x, c->d_r, PGB_FP64, false);
+            ++z.matvecs;
+            ++z.matvecs_fp64;
+            k_axpby<<<nblk(n, 256), 256, 0, s>>>(1.0, c->d_b, -1.0, c->d_r, c->d_r, n);
+            double rn_new = vec_norm(c, c->d_r);
+            rel = rn_new / bnorm;
+            if (it == 0 || !(rn_new < rn)) {  // no progress: stop
+                rn = rn_new;
+                break;
+            }
+            rn = rn_new;
+        }
+    } else {
+        fail(PGB_EINVAL, "mode must be PGB_FP64 or PGB_FP32_REFINE");
+    }
+    PGB_CUDA(cudaGetLastError());
+    z.rel_residual = rel;
+    if (st) *st = z;
+    return rel <= tol ? PGB_OK : PGB_ENOCONV;
+}
+
+}  // namespace pgb

@@ -1,0 +1,1021 @@
+// Geometry, Morton ordering, octree, target groups, interaction lists and
+// near-field corrections (Sections 3.1 and 3.2 of the paper).
+#include <math.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "common.cuh"
+#include "pgb_internal.cuh"
+
+namespace pgb {
+
+Rules make_rules(int K, int Kn, int ne) {
+    Rules r;
+    memset(&r, 0, sizeof(r));
+    r.K = K;
+    r.Kn = Kn;
+    r.ne = ne;
+    const double(*mu)[3] = nullptr;
+    const double* w = nullptr;
+    switch (K) {
+        case 1: mu = PGB_TRI1_MU; w = PGB_TRI1_W; break;
+        case 3: mu = PGB_TRI3_MU; w = PGB_TRI3_W; break;
+        case 4: mu = PGB_TRI4_MU; w = PGB_TRI4_W; break;
+        case 7: mu = PGB_TRI7_MU; w = PGB_TRI7_W; break;
+        default: fail(PGB_EINVAL, "K must be 1, 3, 4 or 7");
+    }
+    for (int i = 0; i < K; ++i) {
+        for (int a = 0; a < 3; ++a) r.mu[i][a] = mu[i][a];
+        r.w[i] = w[i];
+    }
+    if (Kn != 19) fail(PGB_EINVAL, "K_near must be 19");
+    for (int i = 0; i < 19; ++i) {
+        for (int a = 0; a < 3; ++a) r.mun[i][a] = PGB_TRI19_MU[i][a];
+        r.wn[i] = PGB_TRI19_W[i];
+    }
+    const double *ex = nullptr, *ew = nullptr;
+    switch (ne) {
+        case 3: ex = PGB_GL3_X; ew = PGB_GL3_W; break;
+        case 6: ex = PGB_GL6_X; ew = PGB_GL6_W; break;
+        case 9: ex = PGB_GL9_X; ew = PGB_GL9_W; break;
+        case 12: ex = PGB_GL12_X; ew = PGB_GL12_W; break;
+        default: fail(PGB_EINVAL, "n_edge must be 3, 6, 9 or 12");
+    }
+    for (int i = 0; i < ne; ++i) {
+        r.ex[i] = ex[i];
+        r.ew[i] = ew[i];
+    }
+    return r;
+}
+
+static inline int nblk(int64_t n, int t) { return (int)std::max<int64_t>(1, (n + t - 1) / t); }
+
+// ---------------------------------------------------------------- scan
+// Exclusive scan of n int64 values by one block: each thread scans a
+// contiguous chunk, the chunk totals are scanned across the block.
+__global__ void k_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total) {
+    __shared__ int64_t sh[1024];
+    int t = threadIdx.x;
+    int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
+    int64_t b = t * chunk, e = min(n, b + chunk);
+    int64_t s = 0;
+    for (int64_t i = b; i < e; ++i) s += in[i];
+    sh[t] = s;
+    __syncthreads();
+    for (int off = 1; off < blockDim.x; off <<= 1) {
+        int64_t v = (t >= off) ? sh[t - off] : 0;
+        __syncthreads();
+        sh[t] += v;
+        __syncthreads();
+    }
+    int64_t run = sh[t] - s;
+    for (int64_t i = b; i < e; ++i) {
+        int64_t v = in[i];
+        out[i] = run;
+        run += v;
+    }
+    if (t == blockDim.x - 1) *total = sh[t];
+}
+
+void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s, int64_t* total_host) {
+    static thread_local DBuf<int64_t> tot;
+    tot.resize(1);
+    k_scan_i64<<<1, 1024, 0, s>>>(in, out, n, tot);
+    PGB_CUDA(cudaGetLastError());
+    if (total_host) {
+        PGB_CUDA(cudaMemcpyAsync(total_host, tot.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        PGB_CUDA(cudaStreamSynchronize(s));
+    }
+}
+
+// ---------------------------------------------------------------- upload
+void upload_bodies(pgb_ctx* c) {
+    int64_t np = 0, nv = 0, nq = 0, nu = 0;
+    for (auto& b : c->bodies) {
+        b.pan_off = np;
+        b.v_off = nv;
+        b.q_off = nq;
+        b.unk_off = nu;
+        np += b.N;
+        nv += b.nv;
+        nq += b.nq;
+        nu += (b.kind == PGB_DIELECTRIC) ? 2 * b.N : b.N;
+    }
+    c->n_pan = np;
+    c->n_verts = nv;
+    c->n_q = nq;
+    c->n_unk = nu;
+    std::vector<double> vb(3 * nv), qb(3 * nq), qv(nq), pose(12 * c->bodies.size());
+    std::vector<int32_t> tr(3 * np), pb(np), qbody(nq);
+    for (size_t bi = 0; bi < c->bodies.size(); ++bi) {
+        auto& b = c->bodies[bi];
+        std::copy(b.verts.begin(), b.verts.end(), vb.begin() + 3 * b.v_off);
+        for (int64_t i = 0; i < 3 * b.N; ++i) tr[3 * b.pan_off + i] = b.tris[i] + (int32_t)b.v_off;
+        for (int64_t i = 0; i < b.N; ++i) pb[b.pan_off + i] = (int32_t)bi;
+        std::copy(b.qxyz.begin(), b.qxyz.end(), qb.begin() + 3 * b.q_off);
+        std::copy(b.qval.begin(), b.qval.end(), qv.begin() + b.q_off);
+        for (int64_t i = 0; i < b.nq; ++i) qbody[b.q_off + i] = (int32_t)bi;
+        for (int a = 0; a < 9; ++a) pose[12 * bi + a] = b.R[a];
+        for (int a = 0; a < 3; ++a) pose[12 * bi + 9 + a] = b.t[a];
+    }
+    cudaStream_t s = c->stream;
+    c->d_vb.resize(vb.size());
+    c->d_tris.resize(tr.size());
+    c->d_pan_body.resize(np);
+    c->d_qxyz_body.resize(qb.size());
+    c->d_qval.resize(qv.size());
+    c->d_q_body.resize(qbody.size());
+    c->d_qxyz.resize(qb.size());
+    c->d_pose.resize(pose.size());
+    PGB_CUDA(cudaMemcpyAsync(c->d_vb.p, vb.data(), vb.size() * 8, cudaMemcpyHostToDevice, s));
+    PGB_CUDA(cudaMemcpyAsync(c->d_tris.p, tr.data(), tr.size() * 4, cudaMemcpyHostToDevice, s));
+    PGB_CUDA(cudaMemcpyAsync(c->d_pan_body.p, pb.data(), pb.size() * 4, cudaMemcpyHostToDevice, s));
+    if (nq) {
+        PGB_CUDA(cudaMemcpyAsync(c->d_qxyz_body.p, qb.data(), qb.size() * 8, cudaMemcpyHostToDevice, s));
+        PGB_CUDA(cudaMemcpyAsync(c->d_qval.p, qv.data(), qv.size() * 8, cudaMemcpyHostToDevice, s));
+        PGB_CUDA(cudaMemcpyAsync(c->d_q_body.p, qbody.data(), qbody.size() * 4, cudaMemcpyHostToDevice, s));
+    }
+    PGB_CUDA(cudaMemcpyAsync(c->d_pose.p, pose.data(), pose.size() * 8, cudaMemcpyHostToDevice, s));
+    PGB_CUDA(cudaStreamSynchronize(s));
+}
+
+// ---------------------------------------------------------------- ordering
+// Body-frame centroids ((v0 + v1) + v2) / 3, evaluated without fused products.
+__global__ void k_body_centroids(const double* vb, const int32_t* tris, int64_t n, double* cen) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double* v0 = vb + 3 * (int64_t)tris[3 * i];
+    const double* v1 = vb + 3 * (int64_t)tris[3 * i + 1];
+    const double* v2 = vb + 3 * (int64_t)tris[3 * i + 2];
+    for (int a = 0; a < 3; ++a) cen[3 * i + a] = __ddiv_rn(dadd(dadd(v0[a], v1[a]), v2[a]), 3.0);
+}
+
+// Per body min/max of the centroids (one block per body).
+__global__ void k_bbox(const double* cen, const int64_t* off, double* out) {
+    __shared__ double sh[6][32];
+    int b = blockIdx.x;
+    int64_t s = off[b], e = off[b + 1];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = s + threadIdx.x; i < e; i += blockDim.x)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fmin(lo[a], cen[3 * i + a]);
+            hi[a] = fmax(hi[a], cen[3 * i + a]);
+        }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fmin(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = fmax(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int a = 0; a < 3; ++a) {
+            sh[a][w] = lo[a];
+            sh[3 + a][w] = hi[a];
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int nw = blockDim.x / 32;
+        for (int k = 1; k < nw; ++k)
+            for (int a = 0; a < 3; ++a) {
+                sh[a][0] = fmin(sh[a][0], sh[a][k]);
+                sh[3 + a][0] = fmax(sh[3 + a][0], sh[3 + a][k]);
+            }
+        for (int a = 0; a < 6; ++a) out[6 * b + a] = sh[a][0];
+    }
+}
+
+struct BodyFrame {
+    double lo[PGB_MAX_BODIES][3];
+    double scale[PGB_MAX_BODIES];  // 1024 / ext
+};
+
+// 30-bit Morton key of the 10-bit cell q = floor((c - lo) * (1024/ext)),
+// x bit highest in each triple; the body index goes above bit 30 so one sort
+// orders all bodies.
+__global__ void k_morton(const double* cen, const int32_t* pbody, int64_t n, BodyFrame f,
+                         uint64_t* key, int32_t* idx, int32_t* qc) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int b = pbody[i];
+    uint32_t q[3];
+    for (int a = 0; a < 3; ++a) {
+        double u = dmul(dsub(cen[3 * i + a], f.lo[b][a]), f.scale[b]);
+        double fl = floor(u);
+        int v = (int)fl;
+        v = v < 0 ? 0 : (v > 1023 ? 1023 : v);
+        q[a] = (uint32_t)v;
+        qc[3 * i + a] = v;
+    }
+    uint64_t k = 0;
+    for (int bit = 0; bit < 10; ++bit) {
+        k |= (uint64_t)((q[0] >> bit) & 1u) << (3 * bit + 2);
+        k |= (uint64_t)((q[1] >> bit) & 1u) << (3 * bit + 1);
+        k |= (uint64_t)((q[2] >> bit) & 1u) << (3 * bit);
+    }
+    key[i] = k | ((uint64_t)b << 30);
+    idx[i] = (int32_t)i;
+}
+
+// Stable LSD radix sort, 4 bits per pass.  Tiles of 1024 elements.
+#define RS_TILE 1024
+__global__ void k_rs_hist(const uint64_t* key, int64_t n, int shift, int64_t* hist, int ntiles) {
+    __shared__ int cnt[16];
+    if (threadIdx.x < 16) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int i = threadIdx.x; i < RS_TILE; i += blockDim.x) {
+        int64_t g = base + i;
+        if (g < n) atomicAdd(&cnt[(key[g] >> shift) & 15], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 16) hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void k_rs_scatter(const uint64_t* key, const int32_t* val, int64_t n, int shift, const int64_t* off,
+                             int ntiles, uint64_t* okey, int32_t* oval) {
+    __shared__ uint64_t sk[RS_TILE];
+    __shared__ int32_t sv[RS_TILE];
+    int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    int cnt = (int)min((int64_t)RS_TILE, n - base);
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        sk[i] = key[base + i];
+        sv[i] = val[base + i];
+    }
+    __syncthreads();
+    if (threadIdx.x < 16) {  // one thread per digit walks the tile in order (stable)
+        int d = threadIdx.x;
+        int64_t pos = off[(int64_t)d * ntiles + blockIdx.x];
+        for (int i = 0; i < cnt; ++i)
+            if (((sk[i] >> shift) & 15) == (uint64_t)d) {
+                okey[pos] = sk[i];
+                oval[pos] = sv[i];
+                ++pos;
+            }
+    }
+}
+
+__global__ void k_gather_i32x3(const int32_t* src, const int32_t* perm, int64_t n, int32_t* dst) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t j = perm[i];
+    for (int a = 0; a < 3; ++a) dst[3 * i + a] = src[3 * j + a];
+}
+
+__global__ void k_invert(const int32_t* perm, int64_t n, int32_t* inv) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) inv[perm[i]] = (int32_t)i;
+}
+
+__global__ void k_key30(const uint64_t* k64, int64_t n, uint32_t* k32) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) k32[i] = (uint32_t)(k64[i] & 0x3fffffffull);
+}
+
+// Octree split: a node at depth l with more than leaf_size panels splits into
+// its non-empty octants (key order), depth limited to 10.
+__device__ __forceinline__ int octant_of(const uint32_t* key, int64_t i, int child_level) {
+    return (int)((key[i] >> (3 * (10 - child_level))) & 7u);
+}
+__device__ int64_t lower_oct(const uint32_t* key, int64_t s, int64_t e, int child_level, int o) {
+    while (s < e) {
+        int64_t m = (s + e) >> 1;
+        if (octant_of(key, m, child_level) < o) s = m + 1;
+        else e = m;
+    }
+    return s;
+}
+
+__global__ void k_split_count(const int32_t* start, const int32_t* end, int64_t n, int level, int leaf_size,
+                              const uint32_t* key, int64_t* nchild) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t s = start[i], e = end[i];
+    int64_t cnt = 0;
+    if (e - s > leaf_size && level < 10) {
+        for (int o = 0; o < 8; ++o) {
+            int64_t a = lower_oct(key, s, e, level + 1, o), b = lower_oct(key, s, e, level + 1, o + 1);
+            cnt += (b > a);
+        }
+    }
+    nchild[i] = cnt;
+}
+
+__global__ void k_split_write(const int32_t* start, const int32_t* end, const int32_t* body, int64_t n, int level,
+                              const uint32_t* key, const int64_t* nchild, const int64_t* coff, int64_t child_base,
+                              int32_t* first_child, int32_t* nch, int32_t* cstart, int32_t* cend, int32_t* cbody) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    nch[i] = (int32_t)nchild[i];
+    first_child[i] = nchild[i] ? (int32_t)(child_base + coff[i]) : -1;
+    if (!nchild[i]) return;
+    int64_t s = start[i], e = end[i];
+    int64_t k = coff[i];
+    for (int o = 0; o < 8; ++o) {
+        int64_t a = lower_oct(key, s, e, level + 1, o), b = lower_oct(key, s, e, level + 1, o + 1);
+        if (b > a) {
+            cstart[k] = (int32_t)a;
+            cend[k] = (int32_t)b;
+            cbody[k] = body[i];
+            ++k;
+        }
+    }
+}
+
+__global__ void k_parents(const int32_t* child, const int32_t* nch, int64_t n, int32_t* parent) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int k = 0; k < nch[i]; ++k) parent[child[i] + k] = (int32_t)i;
+}
+
+__global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+// leaves in key order: mark leaf starts over panels, scan gives leaf index.
+__global__ void k_mark_leaves(const int32_t* start, const int32_t* nch, int64_t n, int64_t* mark) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n && nch[i] == 0) mark[start[i]] = 1;
+}
+__global__ void k_leaf_ids(const int32_t* start, const int32_t* end, const int32_t* nch, int64_t n,
+                           const int64_t* lscan, int64_t n_pan, int64_t n_leaves, int32_t* leaf0, int32_t* leaf1,
+                           int32_t* leaf_node) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t s = start[i], e = end[i];
+    leaf0[i] = (int32_t)lscan[s];
+    leaf1[i] = (int32_t)(e < n_pan ? lscan[e] : n_leaves);
+    if (nch[i] == 0) leaf_node[lscan[s]] = (int32_t)i;
+}
+__global__ void k_pan_leaf(const int32_t* leaf_node, const int32_t* start, const int32_t* end, int64_t nl,
+                           int32_t* pan_leaf) {
+    int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (l >= nl) return;
+    int nd = leaf_node[l];
+    for (int64_t p = start[nd]; p < end[nd]; ++p) pan_leaf[p] = (int32_t)l;
+}
+
+void build_order(pgb_ctx* c) {
+    cudaStream_t s = c->stream;
+    int64_t n = c->n_pan;
+    int nb = (int)c->bodies.size();
+    DBuf<double> cen;
+    cen.resize(3 * n);
+    k_body_centroids<<<nblk(n, 256), 256, 0, s>>>(c->d_vb, c->d_tris, n, cen);
+    PGB_CUDA(cudaGetLastError());
+    std::vector<int64_t> off(nb + 1);
+    for (int b = 0; b < nb; ++b) off[b] = c->bodies[b].pan_off;
+    off[nb] = n;
+    DBuf<int64_t> d_off;
+    d_off.resize(nb + 1);
+    DBuf<double> d_bb;
+    d_bb.resize(6 * nb);
+    PGB_CUDA(cudaMemcpyAsync(d_off.p, off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
+    k_bbox<<<nb, 256, 0, s>>>(cen, d_off, d_bb);
+    PGB_CUDA(cudaGetLastError());
+    std::vector<double> bb(6 * nb);
+    PGB_CUDA(cudaMemcpyAsync(bb.data(), d_bb.p, 8 * 6 * nb, cudaMemcpyDeviceToHost, s));
+    PGB_CUDA(cudaStreamSynchronize(s));
+    BodyFrame f;
+    for (int b = 0; b < nb; ++b) {
+        double ext = 0;
+        for (int a = 0; a < 3; ++a) ext = std::max(ext, bb[6 * b + 3 + a] - bb[6 * b + a]);
+        if (!(ext > 0)) ext = 1.0;
+        c->bodies[b].ext = ext;
+        for (int a = 0; a < 3; ++a) c->bodies[b].lo[a] = f.lo[b][a] = bb[6 * b + a];
+        f.scale[b] = 1024.0 / ext;
+    }
+    DBuf<uint64_t> k0, k1;
+    DBuf<int32_t> v0, v1, qc;
+    k0.resize(n); k1.resize(n); v0.resize(n); v1.resize(n); qc.resize(3 * n);
+    k_morton<<<nblk(n, 256), 256, 0, s>>>(cen, c->d_pan_body, n, f, k0, v0, qc);
+    PGB_CUDA(cudaGetLastError());
+    int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
+    DBuf<int64_t> hist, hoff;
+    hist.resize(16 * (int64_t)ntiles);
+    hoff.resize(16 * (int64_t)ntiles);
+    int top = 30;
+    while ((1 << (top - 30)) < nb) ++top;  // bits needed for the body index
+    uint64_t *ka = k0.p, *kb = k1.p;
+    int32_t *va = v0.p, *vb = v1.p;
+    for (int shift = 0; shift < top; shift += 4) {
+        k_rs_hist<<<ntiles, 256, 0, s>>>(ka, n, shift, hist, ntiles);
+        exclusive_scan_i64(hist, hoff, 16 * (int64_t)ntiles, s, nullptr);
+        k_rs_scatter<<<ntiles, 64, 0, s>>>(ka, va, n, shift, hoff, ntiles, kb, vb);
+        PGB_CUDA(cudaGetLastError());
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    c->d_perm.resize(n);
+    c->d_inv.resize(n);
+    c->d_key.resize(n);
+    c->d_qcell.resize(3 * n);
+    PGB_CUDA(cudaMemcpyAsync(c->d_perm.p, va, 4 * n, cudaMemcpyDeviceToDevice, s));
+    k_key30<<<nblk(n, 256), 256, 0, s>>>(ka, n, c->d_key);
+    k_gather_i32x3<<<nblk(n, 256), 256, 0, s>>>(qc, c->d_perm, n, c->d_qcell);
+    k_invert<<<nblk(n, 256), 256, 0, s>>>(c->d_perm, n, c->d_inv);
+    PGB_CUDA(cudaGetLastError());
+
+    // octree, level by level (all bodies together); roots first
+    std::vector<DBuf<int32_t>*> lv_start, lv_end, lv_body, lv_fc, lv_nch;
+    std::vector<int64_t> lv_n;
+    auto alloc = [&](int64_t m) {
+        lv_start.push_back(new DBuf<int32_t>); lv_start.back()->resize(m);
+        lv_end.push_back(new DBuf<int32_t>); lv_end.back()->resize(m);
+        lv_body.push_back(new DBuf<int32_t>); lv_body.back()->resize(m);
+        lv_fc.push_back(new DBuf<int32_t>); lv_fc.back()->resize(m);
+        lv_nch.push_back(new DBuf<int32_t>); lv_nch.back()->resize(m);
+        lv_n.push_back(m);
+    };
+    alloc(nb);
+    {
+        std::vector<int32_t> rs(nb), re(nb), rb(nb);
+        for (int b = 0; b < nb; ++b) {
+            rs[b] = (int32_t)off[b];
+            re[b] = (int32_t)off[b + 1];
+            rb[b] = b;
+        }
+        PGB_CUDA(cudaMemcpyAsync(lv_start[0]->p, rs.data(), 4 * nb, cudaMemcpyHostToDevice, s));
+        PGB_CUDA(cudaMemcpyAsync(lv_end[0]->p, re.data(), 4 * nb, cudaMemcpyHostToDevice, s));
+        PGB_CUDA(cudaMemcpyAsync(lv_body[0]->p, rb.data(), 4 * nb, cudaMemcpyHostToDevice, s));
+        PGB_CUDA(cudaStreamSynchronize(s));
+    }
+    int64_t base = nb;
+    DBuf<int64_t> nchild, coff;
+    for (int level = 0; level <= 10; ++level) {
+        int64_t m = lv_n[level];
+        nchild.resize(m);
+        coff.resize(m);
+        k_split_count<<<nblk(m, 128), 128, 0, s>>>(*lv_start[level], *lv_end[level], m, level, c->p.leaf_size,
+                                                   c->d_key, nchild);
+        PGB_CUDA(cudaGetLastError());
+        int64_t total = 0;
+        exclusive_scan_i64(nchild, coff, m, s, &total);
+        alloc(std::max<int64_t>(total, 1));
+        lv_n.back() = total;
+        k_split_write<<<nblk(m, 128), 128, 0, s>>>(*lv_start[level], *lv_end[level], *lv_body[level], m, level,
+                                                   c->d_key, nchild, coff, base, *lv_fc[level], *lv_nch[level],
+                                                   *lv_start[level + 1], *lv_end[level + 1], *lv_body[level + 1]);
+        PGB_CUDA(cudaGetLastError());
+        base += total;
+        if (total == 0) break;
+    }
+    int nlev = 0;
+    while (nlev < (int)lv_n.size() && lv_n[nlev] > 0) ++nlev;
+    int64_t nn = 0;
+    c->level_begin.assign(nlev + 1, 0);
+    for (int l = 0; l < nlev; ++l) {
+        c->level_begin[l] = nn;
+        nn += lv_n[l];
+    }
+    c->level_begin[nlev] = nn;
+    c->n_nodes = nn;
+    c->d_node_start.resize(nn); c->d_node_end.resize(nn); c->d_node_body.resize(nn);
+    c->d_node_child.resize(nn); c->d_node_nchild.resize(nn); c->d_node_level.resize(nn);
+    c->h_node_level.assign(nn, 0);
+    for (int l = 0; l < nlev; ++l) {
+        int64_t o = c->level_begin[l], m = lv_n[l];
+        PGB_CUDA(cudaMemcpyAsync(c->d_node_start.p + o, lv_start[l]->p, 4 * m, cudaMemcpyDeviceToDevice, s));
+        PGB_CUDA(cudaMemcpyAsync(c->d_node_end.p + o, lv_end[l]->p, 4 * m, cudaMemcpyDeviceToDevice, s));
+        PGB_CUDA(cudaMemcpyAsync(c->d_node_body.p + o, lv_body[l]->p, 4 * m, cudaMemcpyDeviceToDevice, s));
+        PGB_CUDA(cudaMemcpyAsync(c->d_node_child.p + o, lv_fc[l]->p, 4 * m, cudaMemcpyDeviceToDevice, s));
+        PGB_CUDA(cudaMemcpyAsync(c->d_node_nchild.p + o, lv_nch[l]->p, 4 * m, cudaMemcpyDeviceToDevice, s));
+        k_fill_i32<<<nblk(m, 256), 256, 0, s>>>(c->d_node_level.p + o, m, l);
+        for (int64_t i = o; i < o + m; ++i) c->h_node_level[i] = l;
+    }
+    PGB_CUDA(cudaGetLastError());
+    PGB_CUDA(cudaStreamSynchronize(s));
+    for (size_t l = 0; l < lv_start.size(); ++l) {
+        delete lv_start[l]; delete lv_end[l]; delete lv_body[l]; delete lv_fc[l]; delete lv_nch[l];
+    }
+    for (int b = 0; b < nb; ++b) c->bodies[b].root = b;
+    c->d_node_parent.resize(nn);
+    k_fill_i32<<<nblk(nn, 256), 256, 0, s>>>(c->d_node_parent, nn, -1);
+    k_parents<<<nblk(nn, 256), 256, 0, s>>>(c->d_node_child, c->d_node_nchild, nn, c->d_node_parent);
+    c->d_up_counter.resize(nn);
+    PGB_CUDA(cudaMemsetAsync(c->d_up_counter.p, 0, 4 * nn, s));
+    // leaves
+    DBuf<int64_t> mark, lscan;
+    mark.resize(n);
+    lscan.resize(n);
+    PGB_CUDA(cudaMemsetAsync(mark.p, 0, 8 * n, s));
+    k_mark_leaves<<<nblk(nn, 256), 256, 0, s>>>(c->d_node_start, c->d_node_nchild, nn, mark);
+    int64_t nl = 0;
+    exclusive_scan_i64(mark, lscan, n, s, &nl);
+    c->n_leaves = nl;
+    c->d_node_leaf0.resize(nn);
+    c->d_node_leaf1.resize(nn);
+    c->d_leaf_node.resize(nl);
+    c->d_pan_leaf.resize(n);
+    k_leaf_ids<<<nblk(nn, 256), 256, 0, s>>>(c->d_node_start, c->d_node_end, c->d_node_nchild, nn, lscan, n, nl,
+                                             c->d_node_leaf0, c->d_node_leaf1, c->d_leaf_node);
+    k_pan_leaf<<<nblk(nl, 128), 128, 0, s>>>(c->d_leaf_node, c->d_node_start, c->d_node_end, nl, c->d_pan_leaf);
+    PGB_CUDA(cudaGetLastError());
+    PGB_CUDA(cudaStreamSynchronize(s));
+    c->order_valid = true;
+}
+
+// ---------------------------------------------------------------- geometry
+// World-frame panel geometry in sorted order and the K-point quadrature nodes
+// y = c + sum_a mu_a (v_a - c), weights w_m A (Section 3.1).
+__global__ void k_geometry(const double* vb, const int32_t* tris, const int32_t* perm, const int32_t* pan_body,
+                           const double* pose, int64_t n, Rules r, double* V, double* C, double* Nn, double* A,
+                           double* Y, double* W, int32_t* pbody) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t g = perm[i];
+    int b = pan_body[g];
+    pbody[i] = b;
+    const double* P = pose + 12 * b;
+    double v[3][3];
+    for (int k = 0; k < 3; ++k) rigid(P, vb + 3 * (int64_t)tris[3 * g + k], v[k]);
+    double c[3];
+    for (int a = 0; a < 3; ++a) c[a] = __ddiv_rn(dadd(dadd(v[0][a], v[1][a]), v[2][a]), 3.0);
+    double e1[3], e2[3], cr[3];
+    for (int a = 0; a < 3; ++a) {
+        e1[a] = v[1][a] - v[0][a];
+        e2[a] = v[2][a] - v[0][a];
+    }
+    cr[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    cr[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    cr[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    double nr = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+    for (int k = 0; k < 3; ++k)
+        for (int a = 0; a < 3; ++a) V[9 * i + 3 * k + a] = v[k][a];
+    for (int a = 0; a < 3; ++a) {
+        C[3 * i + a] = c[a];
+        Nn[3 * i + a] = cr[a] / nr;
+    }
+    double area = 0.5 * nr;
+    A[i] = area;
+    for (int m = 0; m < r.K; ++m) {
+        for (int a = 0; a < 3; ++a)
+            Y[3 * (i * r.K + m) + a] =
+                c[a] + ((r.mu[m][0] * (v[0][a] - c[a]) + r.mu[m][1] * (v[1][a] - c[a])) + r.mu[m][2] * (v[2][a] - c[a]));
+        W[i * r.K + m] = r.w[m] * area;
+    }
+}
+
+// Node centre (cube cell centre, world frame), radius^2 over its quadrature
+// nodes, centroid box and max 8*A of its panels.  One block per node.
+__global__ void k_node_geometry(const int32_t* nstart, const int32_t* nend, const int32_t* nlevel,
+                                const int32_t* nbody, const int32_t* qcell, BodyFrame f, const double* ext,
+                                const double* pose, const double* Y, const double* C, const double* A, int K,
+                                double* center, double* r2, double* clo, double* chi, double* a8) {
+    __shared__ double cw[3];
+    __shared__ double sh[32];
+    int nd = blockIdx.x;
+    int64_t s = nstart[nd], e = nend[nd];
+    int b = nbody[nd], l = nlevel[nd];
+    if (threadIdx.x == 0) {
+        double h = ldexp(ext[b], -(l + 1));
+        double cb[3];
+        for (int a = 0; a < 3; ++a) {
+            int cell = qcell[3 * s + a] >> (10 - l);
+            cb[a] = dadd(f.lo[b][a], dmul(h, (double)(2 * cell + 1)));
+        }
+        rigid(pose + 12 * b, cb, cw);
+        for (int a = 0; a < 3; ++a) center[3 * nd + a] = cw[a];
+    }
+    __syncthreads();
+    double m = 0;
+    for (int64_t p = s * K + threadIdx.x; p < e * K; p += blockDim.x) {
+        double dx = dsub(Y[3 * p], cw[0]), dy = dsub(Y[3 * p + 1], cw[1]), dz = dsub(Y[3 * p + 2], cw[2]);
+        double d2 = dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz));
+        m = fmax(m, d2);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mm = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) mm = fmax(mm, sh[k]);
+        r2[nd] = mm;
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY}, am = 0;
+        for (int64_t p = s; p < e; ++p) {
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = fmin(lo[a], C[3 * p + a]);
+                hi[a] = fmax(hi[a], C[3 * p + a]);
+            }
+            am = fmax(am, 8.0 * A[p]);
+        }
+        for (int a = 0; a < 3; ++a) {
+            clo[3 * nd + a] = lo[a];
+            chi[3 * nd + a] = hi[a];
+        }
+        a8[nd] = am;
+    }
+}
+
+// Target groups: consecutive runs of group_size panels (key order) per body.
+__global__ void k_groups(const int32_t* gstart, const int32_t* gend, int64_t ng, const double* C, double* glo,
+                         double* ghi, double* gcen) {
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t p = gstart[g]; p < gend[g]; ++p)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fmin(lo[a], C[3 * p + a]);
+            hi[a] = fmax(hi[a], C[3 * p + a]);
+        }
+    for (int a = 0; a < 3; ++a) {
+        glo[3 * g + a] = lo[a];
+        ghi[3 * g + a] = hi[a];
+        gcen[3 * g + a] = 0.5 * (lo[a] + hi[a]);
+    }
+}
+
+__global__ void k_rel_targets(const int32_t* gstart, const int32_t* gend, int64_t ng, const double* C,
+                              const double* gcen, float4* x32, dbl4* x64) {
+    int64_t g = blockIdx.x;
+    if (g >= ng) return;
+    for (int64_t p = gstart[g] + threadIdx.x; p < gend[g]; p += blockDim.x) {
+        double dx = C[3 * p] - gcen[3 * g], dy = C[3 * p + 1] - gcen[3 * g + 1], dz = C[3 * p + 2] - gcen[3 * g + 2];
+        x32[p] = make_float4((float)dx, (float)dy, (float)dz, 0.f);
+        x64[p] = dbl4{dx, dy, dz, 0.0};
+    }
+}
+
+__global__ void k_rel_sources(const int32_t* pan_leaf, const int32_t* leaf_node, const double* ncen, int64_t n, int K,
+                              const double* Y, const double* W, float4* y32, dbl4* y64) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n * K) return;
+    int64_t i = p / K;
+    int nd = leaf_node[pan_leaf[i]];
+    double dx = Y[3 * p] - ncen[3 * nd], dy = Y[3 * p + 1] - ncen[3 * nd + 1], dz = Y[3 * p + 2] - ncen[3 * nd + 2];
+    y32[p] = make_float4((float)dx, (float)dy, (float)dz, (float)W[p]);
+    y64[p] = dbl4{dx, dy, dz, W[p]};
+}
+
+void build_geometry(pgb_ctx* c) {
+    cudaStream_t s = c->stream;
+    int64_t n = c->n_pan;
+    int K = c->p.K;
+    Rules r = make_rules(K, c->p.K_near, c->p.n_edge);
+    // poses
+    std::vector<double> pose(12 * c->bodies.size());
+    for (size_t b = 0; b < c->bodies.size(); ++b) {
+        for (int a = 0; a < 9; ++a) pose[12 * b + a] = c->bodies[b].R[a];
+        for (int a = 0; a < 3; ++a) pose[12 * b + 9 + a] = c->bodies[b].t[a];
+    }
+    PGB_CUDA(cudaMemcpyAsync(c->d_pose.p, pose.data(), 8 * pose.size(), cudaMemcpyHostToDevice, s));
+    c->d_v.resize(9 * n); c->d_c.resize(3 * n); c->d_n.resize(3 * n); c->d_A.resize(n);
+    c->d_y.resize(3 * n * K); c->d_w.resize(n * K); c->d_pbody.resize(n);
+    k_geometry<<<nblk(n, 128), 128, 0, s>>>(c->d_vb, c->d_tris, c->d_perm, c->d_pan_body, c->d_pose, n, r, c->d_v,
+                                            c->d_c, c->d_n, c->d_A, c->d_y, c->d_w, c->d_pbody);
+    PGB_CUDA(cudaGetLastError());
+    // charges in the world frame
+    if (c->n_q) {
+        std::vector<double> qw(3 * c->n_q);
+        for (auto& b : c->bodies) {
+            for (int64_t k = 0; k < b.nq; ++k) {
+                const double* v = &b.qxyz[3 * k];
+                for (int a = 0; a < 3; ++a)
+                    qw[3 * (b.q_off + k) + a] = ((b.R[3 * a] * v[0] + b.R[3 * a + 1] * v[1]) + b.R[3 * a + 2] * v[2]) + b.t[a];
+            }
+        }
+        PGB_CUDA(cudaMemcpyAsync(c->d_qxyz.p, qw.data(), 8 * qw.size(), cudaMemcpyHostToDevice, s));
+        PGB_CUDA(cudaStreamSynchronize(s));
+    }
+    BodyFrame f;
+    std::vector<double> ext(c->bodies.size());
+    for (size_t b = 0; b < c->bodies.size(); ++b) {
+        for (int a = 0; a < 3; ++a) f.lo[b][a] = c->bodies[b].lo[a];
+        f.scale[b] = 1024.0 / c->bodies[b].ext;
+        ext[b] = c->bodies[b].ext;
+    }
+    DBuf<double> d_ext;
+    d_ext.resize(ext.size());
+    PGB_CUDA(cudaMemcpyAsync(d_ext.p, ext.data(), 8 * ext.size(), cudaMemcpyHostToDevice, s));
+    int64_t nn = c->n_nodes;
+    c->d_node_center.resize(3 * nn); c->d_node_r2.resize(nn); c->d_node_clo.resize(3 * nn);
+    c->d_node_chi.resize(3 * nn); c->d_node_a8.resize(nn);
+    k_node_geometry<<<(int)nn, 128, 0, s>>>(c->d_node_start, c->d_node_end, c->d_node_level, c->d_node_body,
+                                            c->d_qcell, f, d_ext, c->d_pose, c->d_y, c->d_c, c->d_A, K,
+                                            c->d_node_center, c->d_node_r2, c->d_node_clo, c->d_node_chi,
+                                            c->d_node_a8);
+    PGB_CUDA(cudaGetLastError());
+    // target groups
+    std::vector<int32_t> gs, ge, gb;
+    int G = c->p.group_size;
+    for (size_t b = 0; b < c->bodies.size(); ++b) {
+        auto& bd = c->bodies[b];
+        for (int64_t o = 0; o < bd.N; o += G) {
+            gs.push_back((int32_t)(bd.pan_off + o));
+            ge.push_back((int32_t)(bd.pan_off + std::min<int64_t>(bd.N, o + G)));
+            gb.push_back((int32_t)b);
+        }
+    }
+    int64_t ng = (int64_t)gs.size();
+    c->n_groups = ng;
+    c->d_group_start.resize(ng); c->d_group_end.resize(ng); c->d_group_body.resize(ng);
+    c->d_group_lo.resize(3 * ng); c->d_group_hi.resize(3 * ng); c->d_group_center.resize(3 * ng);
+    PGB_CUDA(cudaMemcpyAsync(c->d_group_start.p, gs.data(), 4 * ng, cudaMemcpyHostToDevice, s));
+    PGB_CUDA(cudaMemcpyAsync(c->d_group_end.p, ge.data(), 4 * ng, cudaMemcpyHostToDevice, s));
+    PGB_CUDA(cudaMemcpyAsync(c->d_group_body.p, gb.data(), 4 * ng, cudaMemcpyHostToDevice, s));
+    k_groups<<<nblk(ng, 128), 128, 0, s>>>(c->d_group_start, c->d_group_end, ng, c->d_c, c->d_group_lo,
+                                           c->d_group_hi, c->d_group_center);
+    c->d_x32.resize(n);
+    c->d_x64.resize(n);
+    k_rel_targets<<<(int)ng, 32, 0, s>>>(c->d_group_start, c->d_group_end, ng, c->d_c, c->d_group_center, c->d_x32,
+                                         c->d_x64);
+    c->d_y32.resize(n * K);
+    c->d_y64.resize(n * K);
+    k_rel_sources<<<nblk(n * K, 256), 256, 0, s>>>(c->d_pan_leaf, c->d_leaf_node, c->d_node_center, n, K, c->d_y,
+                                                   c->d_w, c->d_y32, c->d_y64);
+    PGB_CUDA(cudaGetLastError());
+    PGB_CUDA(cudaStreamSynchronize(s));
+}
+
+// ---------------------------------------------------------------- lists
+// Acceptance: node far for a group when theta > 0 and r_b^2 <= theta^2 d^2,
+// d = distance from the node centre to the group's box (Section 3.2).
+__device__ __forceinline__ bool mac_far(double theta2, double r2, const double* cc, const double* lo, const double* hi) {
+    double d2 = 0;
+    double e[3];
+    for (int a = 0; a < 3; ++a) {
+        double u = fmax(fmax(dsub(lo[a], cc[a]), dsub(cc[a], hi[a])), 0.0);
+        e[a] = u;
+    }
+    d2 = dadd(dadd(dmul(e[0], e[0]), dmul(e[1], e[1])), dmul(e[2], e[2]));
+    return r2 <= dmul(theta2, d2);
+}
+
+struct ListArgs {
+    const int32_t *nchild, *child, *nstart, *nend, *nbody, *gstart, *gend, *gbody;
+    const double *center, *r2, *glo, *ghi;
+    int n_bodies;
+    int kind[PGB_MAX_BODIES];
+    double theta, theta2;
+    int K;
+};
+
+// count (fill == false) or write the near/far lists of each group; depth
+// first, children in key order, bodies in order.
+__global__ void k_lists(ListArgs a, int64_t ng, bool fill, int64_t* ncnt, int64_t* fcnt, const int64_t* noff,
+                        const int64_t* foff, int32_t* nearl, int32_t* farl, unsigned long long* stats) {
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    int32_t stack[PGB_LIST_STACK];
+    int64_t nn = 0, nf = 0;
+    int64_t wn = fill ? noff[g] : 0, wf = fill ? foff[g] : 0;
+    const double* lo = a.glo + 3 * g;
+    const double* hi = a.ghi + 3 * g;
+    int gb = a.gbody[g];
+    int64_t gsize = a.gend[g] - a.gstart[g];
+    unsigned long long p2p = 0, p2pl = 0, m2p = 0, m2pl = 0;
+    for (int b = 0; b < a.n_bodies; ++b) {
+        bool lap = (b == gb) && a.kind[b] == PGB_DIELECTRIC;
+        int sp = 0;
+        stack[sp++] = b;  // roots are nodes 0..n_bodies-1
+        while (sp > 0) {
+            int nd = stack[--sp];
+            bool far = a.theta > 0 && mac_far(a.theta2, a.r2[nd], a.center + 3 * nd, lo, hi);
+            if (far) {
+                if (fill) farl[wf++] = nd;
+                ++nf;
+                m2p += gsize;
+                if (lap) m2pl += gsize;
+            } else if (a.nchild[nd] == 0) {
+                if (fill) nearl[wn++] = nd;
+                ++nn;
+                unsigned long long pts = (unsigned long long)(a.nend[nd] - a.nstart[nd]) * a.K;
+                p2p += pts * gsize;
+                if (lap) p2pl += pts * gsize;
+            } else {
+                int fc = a.child[nd], k = a.nchild[nd];
+                if (sp + k > PGB_LIST_STACK) {
+                    atomicAdd(&stats[4], 1ull);  // overflow flag (cannot happen for depth <= 10)
+                    continue;
+                }
+                for (int j = k - 1; j >= 0; --j) stack[sp++] = fc + j;
+            }
+        }
+    }
+    if (!fill) {
+        ncnt[g] = nn;
+        fcnt[g] = nf;
+    } else {
+        atomicAdd(&stats[0], p2p);
+        atomicAdd(&stats[1], p2pl);
+        atomicAdd(&stats[2], m2p);
+        atomicAdd(&stats[3], m2pl);
+    }
+}
+
+void build_lists(pgb_ctx* c) {
+    cudaStream_t s = c->stream;
+    int64_t ng = c->n_groups;
+    ListArgs a;
+    a.nchild = c->d_node_nchild; a.child = c->d_node_child; a.nstart = c->d_node_start; a.nend = c->d_node_end;
+    a.nbody = c->d_node_body; a.gstart = c->d_group_start; a.gend = c->d_group_end; a.gbody = c->d_group_body;
+    a.center = c->d_node_center; a.r2 = c->d_node_r2; a.glo = c->d_group_lo; a.ghi = c->d_group_hi;
+    a.n_bodies = (int)c->bodies.size();
+    for (int b = 0; b < a.n_bodies; ++b) a.kind[b] = c->bodies[b].kind;
+    a.theta = c->p.theta;
+    a.theta2 = c->p.theta * c->p.theta;
+    a.K = c->p.K;
+    DBuf<int64_t> nc, fc;
+    nc.resize(ng); fc.resize(ng);
+    c->d_near_off.resize(ng + 1);
+    c->d_far_off.resize(ng + 1);
+    DBuf<unsigned long long> st;
+    st.resize(5);
+    PGB_CUDA(cudaMemsetAsync(st.p, 0, 40, s));
+    k_lists<<<nblk(ng, 64), 64, 0, s>>>(a, ng, false, nc, fc, nullptr, nullptr, nullptr, nullptr, st);
+    PGB_CUDA(cudaGetLastError());
+    int64_t tn = 0, tf = 0;
+    exclusive_scan_i64(nc, c->d_near_off, ng, s, &tn);
+    exclusive_scan_i64(fc, c->d_far_off, ng, s, &tf);
+    PGB_CUDA(cudaMemcpyAsync(c->d_near_off.p + ng, &tn, 8, cudaMemcpyHostToDevice, s));
+    PGB_CUDA(cudaMemcpyAsync(c->d_far_off.p + ng, &tf, 8, cudaMemcpyHostToDevice, s));
+    c->n_near = tn;
+    c->n_far = tf;
+    c->d_near.resize(tn);
+    c->d_far.resize(tf);
+    k_lists<<<nblk(ng, 64), 64, 0, s>>>(a, ng, true, nullptr, nullptr, c->d_near_off, c->d_far_off, c->d_near,
+                                        c->d_far, st);
+    PGB_CUDA(cudaGetLastError());
+    unsigned long long h[5];
+    PGB_CUDA(cudaMemcpyAsync(h, st.p, 40, cudaMemcpyDeviceToHost, s));
+    PGB_CUDA(cudaStreamSynchronize(s));
+    if (h[4]) fail(PGB_EINVAL, "octree traversal stack overflow");
+    c->p2p_pairs = (int64_t)h[0];
+    c->p2p_lap = (int64_t)h[1];
+    c->m2p_pairs = (int64_t)h[2];
+    c->m2p_lap = (int64_t)h[3];
+}
+
+// ---------------------------------------------------------------- corrections
+struct CorrArgs {
+    const int32_t *nchild, *child, *nstart, *nend;
+    const double *clo, *chi, *a8, *C, *A;
+    int n_bodies;
+};
+
+// candidates j of target i: |c_i - c_j|^2 < 8 A_j (|x - c_j| < 2 L_j), or j == i
+__global__ void k_corr_find(CorrArgs a, int64_t n, bool fill, int64_t* cnt, const int64_t* off, int32_t* cj) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x[3] = {a.C[3 * i], a.C[3 * i + 1], a.C[3 * i + 2]};
+    int32_t stack[PGB_LIST_STACK];
+    int64_t k = 0, w = fill ? off[i] : 0;
+    for (int b = 0; b < a.n_bodies; ++b) {
+        int sp = 0;
+        stack[sp++] = b;
+        while (sp > 0) {
+            int nd = stack[--sp];
+            double d2 = 0;
+            for (int q = 0; q < 3; ++q) {
+                double u = fmax(fmax(a.clo[3 * nd + q] - x[q], x[q] - a.chi[3 * nd + q]), 0.0);
+                d2 += u * u;
+            }
+            if (!(d2 < a.a8[nd]) && !(d2 == 0.0)) continue;
+            if (a.nchild[nd] == 0) {
+                for (int64_t j = a.nstart[nd]; j < a.nend[nd]; ++j) {
+                    double dx = x[0] - a.C[3 * j], dy = x[1] - a.C[3 * j + 1], dz = x[2] - a.C[3 * j + 2];
+                    double dd = dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz));
+                    if (j == i || dd < 8.0 * a.A[j]) {
+                        if (fill) cj[w++] = (int32_t)j;
+                        ++k;
+                    }
+                }
+            } else {
+                int fc = a.child[nd], m = a.nchild[nd];
+                if (sp + m > PGB_LIST_STACK) continue;
+                for (int q = m - 1; q >= 0; --q) stack[sp++] = fc + q;
+            }
+        }
+    }
+    if (!fill) cnt[i] = k;
+}
+
+// Kernel values at a target x from a source point y with normal n (no 1/4pi).
+__device__ __forceinline__ void kern4(const double* x, const double* y, const double* n, double kappa, double w,
+                                      double& vl, double& kl, double& vy, double& ky) {
+    double dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
+    double r2 = dx * dx + dy * dy + dz * dz;
+    if (!(r2 > 0)) return;
+    double r = sqrt(r2);
+    double ri = 1.0 / r;
+    double nd = n[0] * dx + n[1] * dy + n[2] * dz;
+    double e = exp(-kappa * r);
+    vl += w * ri;
+    kl += w * nd * ri * ri * ri;
+    vy += w * e * ri;
+    ky += w * nd * (1.0 + kappa * r) * e * ri * ri * ri;
+}
+
+// Correction entry (i, j): tiered value minus the K-point value (FP64), for
+// V_L, K_L, V_Y, K_Y (Section 3.1).  Self panel: semi-analytical single layer
+// (three sub-triangles about the centroid, radial integral in closed form,
+// n_edge Gauss points along each edge), K_ii = 0.  Otherwise the 19-point rule.
+__global__ void k_corr_values(int64_t n, const int64_t* off, const int32_t* cj, const double* V, const double* C,
+                              const double* Nn, const double* A, const double* Y, const double* W,
+                              const int32_t* pbody, BodyDev bd, Rules r, double kappa, dbl4* out) {
+    int64_t i = blockIdx.x;
+    if (i >= n) return;
+    for (int64_t e = off[i] + threadIdx.x; e < off[i + 1]; e += blockDim.x) {
+        int64_t j = cj[e];
+        const double* x = C + 3 * i;
+        const double* nj = Nn + 3 * j;
+        double tv[4] = {0, 0, 0, 0};
+        if (j == i) {
+            const double* v = V + 9 * j;
+            for (int ed = 0; ed < 3; ++ed) {
+                const double* pa = v + 3 * ed;
+                const double* pb = v + 3 * ((ed + 1) % 3);
+                double ev[3] = {pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2]};
+                double ell = sqrt(ev[0] * ev[0] + ev[1] * ev[1] + ev[2] * ev[2]);
+                double u[3] = {ev[0] / ell, ev[1] / ell, ev[2] / ell};
+                double cpa[3] = {x[0] - pa[0], x[1] - pa[1], x[2] - pa[2]};
+                double proj = cpa[0] * u[0] + cpa[1] * u[1] + cpa[2] * u[2];
+                double hv[3] = {cpa[0] - proj * u[0], cpa[1] - proj * u[1], cpa[2] - proj * u[2]};
+                double h = sqrt(hv[0] * hv[0] + hv[1] * hv[1] + hv[2] * hv[2]);
+                for (int g = 0; g < r.ne; ++g) {
+                    double sg = r.ex[g] * ell;
+                    double p[3] = {pa[0] + sg * u[0] - x[0], pa[1] + sg * u[1] - x[1], pa[2] + sg * u[2] - x[2]};
+                    double rho = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+                    double jac = h / (rho * rho) * ell * r.ew[g];
+                    tv[0] += rho * jac;
+                    tv[2] += (kappa > 0 ? (1.0 - exp(-kappa * rho)) / kappa : rho) * jac;
+                }
+            }
+        } else {
+            const double* v = V + 9 * j;
+            const double* cjp = C + 3 * j;
+            for (int m = 0; m < r.Kn; ++m) {
+                double y[3];
+                for (int a = 0; a < 3; ++a)
+                    y[a] = cjp[a] + ((r.mun[m][0] * (v[a] - cjp[a]) + r.mun[m][1] * (v[3 + a] - cjp[a])) +
+                                     r.mun[m][2] * (v[6 + a] - cjp[a]));
+                kern4(x, y, nj, kappa, r.wn[m] * A[j], tv[0], tv[1], tv[2], tv[3]);
+            }
+        }
+        // the treecode sums leave out the target's own panel, so the self entry
+        // is the whole semi-analytical value; other entries replace the K-point sum
+        double kv[4] = {0, 0, 0, 0};
+        if (j != i)
+            for (int m = 0; m < r.K; ++m) kern4(x, Y + 3 * (j * r.K + m), nj, kappa, W[j * r.K + m], kv[0], kv[1], kv[2], kv[3]);
+        double d[4];
+        for (int q = 0; q < 4; ++q) d[q] = (tv[q] - kv[q]) / PGB_FOUR_PI;
+        int bi = pbody[i], bj = pbody[j];
+        if (bi != bj || bd.kind[bi] != PGB_DIELECTRIC) d[0] = d[1] = 0.0;
+        out[e] = dbl4{d[0], d[1], d[2], d[3]};
+    }
+}
+
+BodyDev body_dev(const pgb_ctx* c) {
+    BodyDev b;
+    memset(&b, 0, sizeof(b));
+    b.n_bodies = (int)c->bodies.size();
+    for (int i = 0; i < b.n_bodies; ++i) {
+        const auto& bb = c->bodies[i];
+        b.kind[i] = bb.kind;
+        b.eps_ratio[i] = bb.eps_in / c->eps_out;
+        b.bc[i] = bb.bc;
+        b.pan_off[i] = bb.pan_off;
+        b.unk_off[i] = bb.unk_off;
+    }
+    b.pan_off[b.n_bodies] = c->n_pan;
+    return b;
+}
+
+void build_corrections(pgb_ctx* c) {
+    cudaStream_t s = c->stream;
+    int64_t n = c->n_pan;
+    CorrArgs a;
+    a.nchild = c->d_node_nchild; a.child = c->d_node_child; a.nstart = c->d_node_start; a.nend = c->d_node_end;
+    a.clo = c->d_node_clo; a.chi = c->d_node_chi; a.a8 = c->d_node_a8; a.C = c->d_c; a.A = c->d_A;
+    a.n_bodies = (int)c->bodies.size();
+    DBuf<int64_t> cnt;
+    cnt.resize(n);
+    c->d_corr_off.resize(n + 1);
+    k_corr_find<<<nblk(n, 64), 64, 0, s>>>(a, n, false, cnt, nullptr, nullptr);
+    PGB_CUDA(cudaGetLastError());
+    int64_t tot = 0;
+    exclusive_scan_i64(cnt, c->d_corr_off, n, s, &tot);
+    PGB_CUDA(cudaMemcpyAsync(c->d_corr_off.p + n, &tot, 8, cudaMemcpyHostToDevice, s));
+    c->n_corr = tot;
+    c->d_corr_j.resize(tot);
+    c->d_corr_val.resize(tot);
+    k_corr_find<<<nblk(n, 64), 64, 0, s>>>(a, n, true, nullptr, c->d_corr_off, c->d_corr_j);
+    Rules r = make_rules(c->p.K, c->p.K_near, c->p.n_edge);
+    k_corr_values<<<(int)n, 32, 0, s>>>(n, c->d_corr_off, c->d_corr_j, c->d_v, c->d_c, c->d_n, c->d_A, c->d_y, c->d_w,
+                                        c->d_pbody, body_dev(c), r, c->kappa, c->d_corr_val);
+    PGB_CUDA(cudaGetLastError());
+    PGB_CUDA(cudaStreamSynchronize(s));
+}
+
+Geo geo(const pgb_ctx* c) {
+    Geo g;
+    g.n_pan = c->n_pan;
+    g.n_src = c->n_pan * c->p.K;
+    g.K = c->p.K;
+    g.perm = c->d_perm; g.pbody = c->d_pbody; g.v = c->d_v; g.c = c->d_c; g.n = c->d_n; g.A = c->d_A;
+    g.pleaf = c->d_pan_leaf; g.y = c->d_y; g.w = c->d_w;
+    return g;
+}
+
+}  // namespace pgb

@@ -1,0 +1,173 @@
+"""GPU parity of the CUDA path (through the C ABI) against the CPU oracle."""
+import numpy as np
+import pytest
+
+from oracle.energy import energies
+from oracle.treecode import TreecodeOperator
+from problems import gpu_context, oracle_system, spheres, star_molecule
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no GPU", allow_module_level=True)
+
+import paper_1506_03745_gb300 as pgb  # noqa: E402
+
+
+def _matvec(ctx, x, prec):
+    dt = torch.float32 if prec == pgb.PGB_FP32 else torch.float64
+    xt = torch.tensor(x, dtype=dt, device="cuda")
+    yt = torch.empty_like(xt)
+    pgb.pgb_matvec(ctx, xt, yt, prec)
+    torch.cuda.synchronize()
+    return yt.double().cpu().numpy()
+
+
+CASES = {
+    "molecule_only": dict(surface=False, level_mol=3),
+    "sigma_pair": dict(kind="sigma", level_mol=2, level_srf=2),
+    "phi_pair": dict(kind="phi", level_mol=2, level_srf=1, r_srf=3.0, sep=9.0),
+    "ragged_geodesic": dict(kind="sigma", mol_nu=5, level_srf=1, sep=10.0),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_direct_sum_matvec_matches_oracle(case):
+    bodies = spheres(**CASES[case])
+    so = oracle_system(bodies, theta=0.0)
+    ctx = gpu_context(bodies, theta=0.0, leaf_size=16)
+    try:
+        x = np.random.default_rng(1).normal(size=so.n)
+        ref = so.apply(x)
+        scale = np.abs(ref).max()
+        y64 = _matvec(ctx, x, pgb.PGB_FP64)
+        assert np.abs(y64 - ref).max() / scale < 1e-11
+        y32 = _matvec(ctx, x, pgb.PGB_FP32)
+        assert np.abs(y32 - ref).max() / scale < 2e-6
+    finally:
+        pgb.pgb_destroy(ctx)
+
+
+@pytest.mark.parametrize("case,theta,P", [("sigma_pair", 0.5, 6), ("phi_pair", 0.6, 3), ("molecule_only", 0.5, 4)])
+def test_treecode_matches_oracle_treecode(case, theta, P):
+    kw = dict(CASES[case])
+    if case == "molecule_only":
+        kw["level_mol"] = 2
+    bodies = spheres(**kw)
+    so = oracle_system(bodies, theta=theta, P=P, leaf_size=8)
+    ctx = gpu_context(bodies, theta=theta, P=P, leaf_size=8)
+    try:
+        tc = TreecodeOperator(so)
+        # identical ordering and interaction lists (integer work: bit-exact)
+        perm, noff, near, foff, far = pgb.pgb_tree_export(ctx)
+        offs = np.cumsum([0] + [p.N for p in so.panels])
+        operm = np.concatenate([tr.perm + o for tr, o in zip(tc.trees, offs[:-1])])
+        assert np.array_equal(perm, operm)
+        node_base = _node_ids(tc)
+        assert len(noff) - 1 == len(tc.groups)
+        for gi in range(len(tc.groups)):
+            on, of = [], []
+            for b in range(len(so.bodies)):
+                n_, f_ = tc.lists[(gi, b)]
+                on += [node_base[b][i] for i in n_]
+                of += [node_base[b][i] for i in f_]
+            assert sorted(near[noff[gi]:noff[gi + 1]]) == sorted(on)
+            assert sorted(far[foff[gi]:foff[gi + 1]]) == sorted(of)
+        x = np.random.default_rng(2).normal(size=so.n)
+        ref = tc.apply(x)
+        scale = np.abs(ref).max()
+        y64 = _matvec(ctx, x, pgb.PGB_FP64)
+        assert np.abs(y64 - ref).max() / scale < 1e-10
+        y32 = _matvec(ctx, x, pgb.PGB_FP32)
+        assert np.abs(y32 - ref).max() / scale < 5e-6
+    finally:
+        pgb.pgb_destroy(ctx)
+
+
+def _node_ids(tc):
+    """Map oracle per-body DFS node indices to the library's level-order ids
+    (roots first, then each level's children in parent order, key order)."""
+    levels = []
+    for b, tr in enumerate(tc.trees):
+        levels.append([(b, 0)])
+    ids = [dict() for _ in tc.trees]
+    cur = [(b, 0) for b in range(len(tc.trees))]
+    nid = 0
+    while cur:
+        nxt = []
+        for b, i in cur:
+            ids[b][i] = nid
+            nid += 1
+        for b, i in cur:
+            nxt += [(b, ch) for ch in tc.trees[b].nodes[i]["children"]]
+        cur = nxt
+    return ids
+
+
+@pytest.mark.parametrize("kind", ["sigma", "phi"])
+@pytest.mark.parametrize("mode", ["fp64", "refine"])
+def test_solve_and_energies_match_dense_oracle(kind, mode):
+    bodies = spheres(kind=kind, level_mol=2, level_srf=2)
+    so = oracle_system(bodies, theta=0.0)
+    ctx = gpu_context(bodies, theta=0.0)
+    try:
+        n = pgb.pgb_num_unknowns(ctx)
+        x = torch.empty(n, dtype=torch.float64, device="cuda")
+        m = pgb.PGB_FP64 if mode == "fp64" else pgb.PGB_FP32_REFINE
+        code, st = pgb.pgb_solve(ctx, m, 1e-10, 2000, 100, x)
+        assert code == 0 and st["rel_residual"] <= 1e-10
+        xo = so.solve()
+        assert np.abs(x.cpu().numpy() - xo).max() / np.abs(xo).max() < 1e-8
+        e = pgb.pgb_energy(ctx, x, 2)
+        eo = energies(so, xo)
+        for k in ("coulomb", "solvation", "surface", "total"):
+            assert e[k] == pytest.approx(eo[k], rel=1e-8, abs=1e-12)
+    finally:
+        pgb.pgb_destroy(ctx)
+
+
+def test_star_molecule_charges_and_rhs():
+    bodies = star_molecule(nu=6, nq=40)
+    so = oracle_system(bodies, theta=0.0)
+    ctx = gpu_context(bodies, theta=0.0)
+    try:
+        n = pgb.pgb_num_unknowns(ctx)
+        b = torch.empty(n, dtype=torch.float64, device="cuda")
+        pgb.pgb_rhs(ctx, b)
+        _, bo = so.assemble()
+        assert np.abs(b.cpu().numpy() - bo).max() / np.abs(bo).max() < 1e-12
+        x = torch.empty(n, dtype=torch.float64, device="cuda")
+        code, st = pgb.pgb_solve(ctx, pgb.PGB_FP64, 1e-10, 2000, 100, x)
+        assert code == 0
+        e = pgb.pgb_energy(ctx, x)
+        eo = energies(so, so.solve())
+        assert e["coulomb"] == pytest.approx(eo["coulomb"], rel=1e-12)
+        assert e["solvation"] == pytest.approx(eo["solvation"], rel=1e-8)
+    finally:
+        pgb.pgb_destroy(ctx)
+
+
+def test_state_and_argument_errors():
+    ctx = pgb.pgb_create(pgb.default_params(), torch.cuda.current_stream())
+    try:
+        x = torch.zeros(4, dtype=torch.float64, device="cuda")
+        assert pgb.lib().pgb_tree_build(ctx) == pgb.PGB_ESTATE
+        import synth
+        v, f = synth.icosphere(1, 2.0)
+        bad = f.copy()
+        bad[0, 0] = 10_000
+        with pytest.raises(pgb.PgbError) as ei:
+            pgb.pgb_mesh_load(ctx, pgb.PGB_DIELECTRIC, v, bad, 4.0)
+        assert ei.value.code == pgb.PGB_EINVAL
+        vnan = v.copy()
+        vnan[3, 1] = np.nan
+        with pytest.raises(pgb.PgbError):
+            pgb.pgb_mesh_load(ctx, pgb.PGB_DIELECTRIC, vnan, f, 4.0)
+        with pytest.raises(pgb.PgbError):
+            pgb.pgb_set_solvent(ctx, 80.0, -1.0)
+        pgb.pgb_mesh_load(ctx, pgb.PGB_DIELECTRIC, v, f, 4.0)
+        st = pgb.lib().pgb_matvec(ctx, x.data_ptr(), x.data_ptr(), pgb.PGB_FP64)
+        assert st == pgb.PGB_ESTATE
+    finally:
+        pgb.pgb_destroy(ctx)
