@@ -1,0 +1,408 @@
+#!/usr/bin/env python
+"""Benchmark of the treecode BEM hot path on one GB300 (or N replicas).
+
+Workload (the two-sphere configuration the metric is quoted on): a spherical
+molecule of radius 4 A (icosphere, 20480 panels) with a central +1e charge,
+eps_in 4, next to a sphere of radius 4 A (20480 panels) with imposed charge
+0.05 C/m^2, centres 12 A apart, eps_out 80, kappa 0.125 1/A; K=7, 19-point
+near rule, 9 points per edge, treecode theta 0.5, P 6; GMRES tol 1e-6 with
+FP32 inner solves and FP64 residual refinement.
+
+One step = the whole hot path: geometry + octree + lists + near-field
+precompute (pgb_tree_build), the FP32+refinement GMRES solve (pgb_solve) and
+the energies (pgb_energy), inputs resident on the device.  value = treecode
+matvecs per second inside those steps (all operator applications of the solve,
+FP32 and FP64, divided by the step time).  L2 is flushed (512 MB write)
+before each timed step; the flush is outside the timed intervals.
+
+--impl reference times the CPU FP64 oracle (direct-sum rows of the same
+operator) on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "treecode matvecs/sec and GMRES solve ms at 1e-5 energy err, FP32+refine vs FP64"
+UNIT = "matvecs/s"
+WORKLOAD = "two spheres r=4 A, 2 x 20480 panels, sigma=0.05 C/m^2, R=12 A"
+PARAMS = dict(K=7, K_near=19, n_edge=9, P=6, theta=0.5, leaf_size=32, group_size=32)
+TOL = 1e-6
+RESTART = 100
+MAX_ITER = 2000
+FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)"
+
+
+def workload_bodies(level=5):
+    import synth
+    v, f = synth.icosphere(level, 4.0)
+    mol = dict(kind="dielectric", verts=v, tris=f, eps_in=4.0, qxyz=np.zeros((1, 3)), q=np.array([1.0]), bc=0.0)
+    srf = dict(kind="sigma", verts=v + np.array([12.0, 0.0, 0.0]), tris=f, eps_in=1.0, qxyz=np.zeros((0, 3)),
+               q=np.zeros(0), bc=0.05)
+    return [mol, srf]
+
+
+# ------------------------------------------------------------------ flops
+def p2p_flops(laplace):
+    """FP32 operations per target x source-point pair of the P2P tile loop
+    (rsqrt and exp counted as one each): difference 3, r^2 5, rsqrt 1, n.d 5,
+    1/r^2 and t 2, Yukawa 10, Laplace 3."""
+    return 26 + (3 if laplace else 0)
+
+
+def m2p_flops(P, laplace):
+    """Operations per (target, far node) of the Taylor recurrences and the
+    contraction with the moments, counted term by term."""
+    terms = [(x, y, n - x - y) for n in range(P + 1) for x in range(n, -1, -1) for y in range(n - x, -1, -1)]
+    yuk = 3 + 5 + 1 + 1 + 1 + 2 + 1 + 1   # R, r^2, rsqrt, 1/r^2, rho, exp, G0, G0*M0
+    lap = 1
+    for k in terms[1:]:
+        a1 = sum(1 for c in k if c >= 1)
+        a2 = sum(1 for c in k if c >= 2)
+        s1 = 2 * a1 - 1
+        s2 = max(a2 - 1, 0)
+        yuk += 2 * s1 + 2 * s2 + (1 if a2 else 0) + 1 + 1 + (2 if a2 else 0) + (1 if a2 else 0) + 2 + 1 + 2
+        lap += s1 + s2 + 1 + (2 if a2 else 0) + 1 + 2
+    return yuk + (lap if laplace else 0)
+
+
+def eval_flops(info, P):
+    yp = info["p2p_pairs"] - info["p2p_laplace_pairs"]
+    lp = info["p2p_laplace_pairs"]
+    ym = info["m2p_pairs"] - info["m2p_laplace_pairs"]
+    lm = info["m2p_laplace_pairs"]
+    return yp * p2p_flops(False) + lp * p2p_flops(True) + ym * m2p_flops(P, False) + lm * m2p_flops(P, True)
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.FIELDS,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for nm, val in zip(names, r[5:9]):
+                if "Active" in val and "Not" not in val:
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ profile
+def recorded_traffic():
+    """dram bytes per launch of the FP32 evaluation kernel from the committed
+    ncu summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "k_eval_fp32_two_sphere.txt")
+    src = os.path.join(ROOT, "paper_1506_03745_gb300", "csrc", "treecode.cuh")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    kv = {}
+    for line in open(path):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.split("=", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("treecode_cuh_sha256_16") != h or "dram_bytes_per_launch_full" not in kv:
+        return None
+    return float(kv["dram_bytes_per_launch_full"])
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ------------------------------------------------------------------ reference (oracle)
+def oracle_rate(bodies, n_targets, seed=0):
+    """Direct-sum FP64 oracle rows for n_targets molecule panels: returns
+    (seconds, matvec fraction)."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from problems import oracle_system
+    so = oracle_system(bodies, theta=0.0)
+    x = np.random.default_rng(seed).normal(size=so.n)
+    rows = np.arange(n_targets)
+    t0 = time.perf_counter()
+    so.apply_rows(x, 0, rows)
+    dt = time.perf_counter() - t0
+    n_pan = sum(p.N for p in so.panels)
+    return dt, n_targets / n_pan
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    bodies = workload_bodies()
+    per_step = 24
+    for _ in range(args.warmup):
+        oracle_rate(bodies, 4)
+    tot, frac = 0.0, 0.0
+    for _ in range(args.steps):
+        dt, f = oracle_rate(bodies, per_step)
+        tot += dt
+        frac += f
+    value = frac / tot
+    sample = (f"{per_step} of 40960 target panels per step (both rows of each), direct-sum FP64 oracle "
+              f"over all 286720 source points, extrapolated to whole matvecs")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+    import paper_1506_03745_gb300 as pgb
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from problems import gpu_context
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    bodies = workload_bodies()
+    ctx = gpu_context(bodies, **PARAMS)
+    n = pgb.pgb_num_unknowns(ctx)
+    x = torch.empty(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def step(mode):
+        pgb.pgb_tree_build(ctx)
+        code, st = pgb.pgb_solve(ctx, mode, TOL, MAX_ITER, RESTART, x)
+        if code != 0:
+            raise RuntimeError(f"solve did not converge: {st}")
+        e = pgb.pgb_energy(ctx, x)
+        return st, e
+
+    for _ in range(args.warmup):
+        step(pgb.PGB_FP32_REFINE)
+    torch.cuda.synchronize()
+    # ---- timed region
+    pgb.pgb_timing(ctx, True, read=True)      # reset counters, timing on
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms, matvecs, stats = 0.0, 0, []
+    for _ in range(args.steps):
+        flush.zero_()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        st, e32 = step(pgb.PGB_FP32_REFINE)
+        s1.record(stream)
+        s1.synchronize()
+        total_ms += s0.elapsed_time(s1)
+        matvecs += st["matvecs"]
+        stats.append(st)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    timing = pgb.pgb_timing(ctx, False, read=True)
+    t_max = total_ms
+    mv_all = matvecs
+    if dist:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        m = torch.tensor([matvecs], device=dev, dtype=torch.float64)
+        dist.all_reduce(m)
+        mv_all = int(m.item())
+    value = mv_all / (t_max / 1e3)
+
+    # ---- FP64 reference solve on the same GPU (reported beside the value)
+    flush.zero_()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    st64, e64 = step(pgb.PGB_FP64)
+    f1.record(stream)
+    f1.synchronize()
+    fp64_ms = f0.elapsed_time(f1)
+    x64 = x.clone()
+    step(pgb.PGB_FP32_REFINE)
+    e_err = {k: abs(e32[k] - e64[k]) / max(abs(e64[k]), 1e-300) for k in ("solvation", "surface", "total")}
+
+    info = pgb.pgb_tree_stats(ctx)
+    ev_ms, ev_calls = timing["eval"]
+    flops = eval_flops(info, PARAMS["P"])
+    peaks = load_peaks()
+    peak_tflops = 152 * 128 * 2 * 2.07e9 / 1e12
+    achieved = flops / (ev_ms / ev_calls / 1e3) / 1e12 if ev_calls else None
+    traffic = recorded_traffic()
+
+    # ---- end to end through the public API with host inputs
+    e2e_ms = []
+    h2d = sum(b["verts"].nbytes + b["tris"].astype(np.int32).nbytes + b["qxyz"].nbytes + b["q"].nbytes
+              for b in bodies)
+    d2h = 32 + 24  # energies + solve stats
+    e2e_mv = 0
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c2 = gpu_context(bodies, **PARAMS)
+        xx = torch.empty(n, dtype=torch.float64, device=dev)
+        code, st = pgb.pgb_solve(c2, pgb.PGB_FP32_REFINE, TOL, MAX_ITER, RESTART, xx)
+        ee = pgb.pgb_energy(c2, xx)
+        pgb.pgb_destroy(c2)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+            e2e_mv += st["matvecs"]
+    e2e_value = e2e_mv / (sum(e2e_ms) / 1e3) * (mv_all / max(matvecs, 1))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, frac = 0.0, 0.0
+        while dt < 10.0:
+            d, f = oracle_rate(bodies, 32)
+            dt += d
+            frac += f
+        cpu = {"value": frac / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{int(round(frac * 40960))} of 40960 target panels, direct-sum FP64 oracle rows "
+                         f"(dense O(N^2) operator, not a treecode), extrapolated to whole matvecs"}
+
+    st0 = stats[0]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_unknowns": n, "theta": PARAMS["theta"], "P": PARAMS["P"],
+                   "leaf_size": PARAMS["leaf_size"], "K": PARAMS["K"], "tol": TOL, "restart": RESTART,
+                   "step": "tree build + FP32/FP64-refined GMRES solve + energies",
+                   "l2": "flushed (512 MB write) before every timed step",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "solve": {"fp32_refine_ms": t_max / args.steps, "fp64_ms": fp64_ms,
+                  "speedup_vs_fp64": fp64_ms / (t_max / args.steps),
+                  "iterations": st0["iterations"], "outer_steps": st0["outer_steps"],
+                  "matvecs": st0["matvecs"], "matvecs_fp64": st0["matvecs_fp64"],
+                  "fp64_iterations": st64["iterations"], "rel_residual": st0["rel_residual"],
+                  "energy_rel_err_vs_fp64": e_err, "energies_kcal_mol": e32},
+        "stage_ms_per_step": {k: v[0] / args.steps for k, v in timing.items() if k != "kernel_launches"},
+        "gpu_launches": timing["kernel_launches"],
+        "roofline": {"kernel": "k_eval<float,6> (P2P + M2P)", "bound": "alu", "achieved": achieved,
+                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": (achieved / peak_tflops) if achieved else None,
+                     "traffic": traffic, "flops_per_launch": flops, "launches": ev_calls,
+                     "avg_launch_ms": ev_ms / ev_calls if ev_calls else None,
+                     "peak_source": FP32_PEAK_NOTE + " (derived, not in MEASURED_PEAKS.json)"},
+        "tree": info,
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h,
+                "ms_per_step": statistics.mean(e2e_ms)},
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    pgb.pgb_destroy(ctx)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_matvec(args):
+    """Operator applications only: W + K FP32 treecode matvecs of the
+    workload (tree built once, untimed); prints matvecs/s and per-stage times."""
+    import torch
+    import paper_1506_03745_gb300 as pgb
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from problems import gpu_context
+    dev = torch.device("cuda", 0)
+    ctx = gpu_context(workload_bodies(), **PARAMS)
+    n = pgb.pgb_num_unknowns(ctx)
+    prec = pgb.PGB_FP64 if args.precision == "fp64" else pgb.PGB_FP32
+    dt = torch.float64 if prec == pgb.PGB_FP64 else torch.float32
+    x = torch.randn(n, dtype=dt, device=dev)
+    y = torch.empty_like(x)
+    for _ in range(args.warmup):
+        pgb.pgb_matvec(ctx, x, y, prec)
+    torch.cuda.synchronize()
+    pgb.pgb_timing(ctx, True, read=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        pgb.pgb_matvec(ctx, x, y, prec)
+    e1.record()
+    torch.cuda.synchronize()
+    t = pgb.pgb_timing(ctx, False, read=True)
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"mode": "matvec", "precision": args.precision, "ms_per_matvec": ms,
+                      "matvecs_per_s": 1e3 / ms,
+                      "stage_ms_per_matvec": {k: v[0] / args.steps for k, v in t.items() if k != "kernel_launches"},
+                      "tree": pgb.pgb_tree_stats(ctx)}), flush=True)
+    pgb.pgb_destroy(ctx)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--mode", default="solve", choices=["solve", "matvec"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    elif args.mode == "matvec":
+        run_matvec(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()
