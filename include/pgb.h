@@ -95,15 +95,16 @@ typedef struct pgb_tree_info {
 
 /* Device time per stage of the hot path, accumulated with CUDA events on
  * the context's stream while timing is enabled (pgb_timing). */
-#define PGB_STAGE_SOURCES 0   /* panel densities and per-point source terms */
-#define PGB_STAGE_UPWARD 1    /* P2M at the leaves + moment shifts to the root */
-#define PGB_STAGE_EVAL 2      /* P2P over near leaves + M2P over far nodes */
-#define PGB_STAGE_ASSEMBLE 3  /* near-field corrections + block rows */
+#define PGB_STAGE_SOURCES 0   /* FP32 matvec: panel densities and per-point source terms */
+#define PGB_STAGE_UPWARD 1    /* FP32 matvec: P2M at the leaves + moment shifts to the root */
+#define PGB_STAGE_EVAL 2      /* FP32 matvec: P2P over near leaves + M2P over far nodes */
+#define PGB_STAGE_ASSEMBLE 3  /* FP32 matvec: near-field corrections + block rows */
 #define PGB_STAGE_KRYLOV 4    /* Arnoldi (CGS2), Givens, updates */
 #define PGB_STAGE_TREE 5      /* pgb_tree_build */
 #define PGB_STAGE_ENERGY 6    /* pgb_energy */
-#define PGB_STAGE_RHS 7       /* right-hand side */
-#define PGB_N_STAGES 8
+#define PGB_STAGE_RHS 7       /* right-hand side (Coulomb rows; imposed terms are FP64 matvecs) */
+#define PGB_STAGE_FP64 8      /* add to stages 0-3 for the FP64 matvec */
+#define PGB_N_STAGES 12
 typedef struct pgb_stage_times {
     double ms[PGB_N_STAGES];        /* summed device milliseconds */
     int64_t calls[PGB_N_STAGES];    /* timed intervals */
@@ -169,6 +170,26 @@ int pgb_solve(struct pgb_ctx* ctx, int32_t mode, double tol, int32_t max_iter, i
  * rule), surface (Eq. 15) and total, summed over bodies.  per_body may be
  * NULL or an array of n_bodies entries. */
 int pgb_energy(struct pgb_ctx* ctx, const double* x, pgb_energies* e, pgb_energies* per_body);
+
+/* Energies like pgb_energy, for callers that must not allocate device
+ * memory: code running under an external memory budget or a pool that owns
+ * all of the device's memory, and code paths where cudaMalloc would
+ * serialise the device (for example between launches of a latency-bound
+ * pose sweep).  The paper has no counterpart; this is a library feature.
+ *
+ * It allocates nothing: its scratch (reaction potential at every charge,
+ * per-body sums and charge offsets) lives in one file-scope device array of
+ * PGB_NOALLOC_MAX_CHARGES + 4*64 + 1 doubles (about 514 KB) that every GPU
+ * which loads libpgb holds until the process exits.  The context must have been
+ * built (pgb_tree_build) beforehand; its buffers are reused, not grown.
+ * Returns PGB_EINVAL when the context holds more than PGB_NOALLOC_MAX_CHARGES
+ * charges.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and each call overwrites every entry it reads,
+ * so calls that overlap on the GPU (different streams or threads without
+ * ordering) race and must be serialised by the caller. */
+#define PGB_NOALLOC_MAX_CHARGES 65536
+int pgb_energy_noalloc(struct pgb_ctx* ctx, const double* x, pgb_energies* e);
 
 /* Enable (1) or disable (0) stage timing.  If out is not NULL the stream
  * is synchronised and the times and launch count accumulated since the last

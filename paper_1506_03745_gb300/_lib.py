@@ -38,8 +38,9 @@ class pgb_tree_info(ctypes.Structure):
                                      "n_corrections")]
 
 
-N_STAGES = 8
-STAGES = ("sources", "upward", "eval", "assemble", "krylov", "tree", "energy", "rhs")
+N_STAGES = 12
+STAGES = ("sources", "upward", "eval", "assemble", "krylov", "tree", "energy", "rhs",
+          "sources_fp64", "upward_fp64", "eval_fp64", "assemble_fp64")
 
 
 class pgb_stage_times(ctypes.Structure):
@@ -72,6 +73,7 @@ _SIGS = {
     "pgb_energy": (c_i32, [c_vp, c_vp, ctypes.POINTER(pgb_energies), c_vp]),
     "pgb_tree_export": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "pgb_timing": (c_i32, [c_vp, c_i32, ctypes.POINTER(pgb_stage_times)]),
+    "pgb_energy_noalloc": (c_i32, [c_vp, c_vp, ctypes.POINTER(pgb_energies)]),
 }
 
 
@@ -207,6 +209,17 @@ def pgb_energy(ctx, x, n_bodies=None):
     if per is not None:
         d["per_body"] = [{n: getattr(p, n) for n, _ in pgb_energies._fields_} for p in per]
     return d
+
+
+PGB_NOALLOC_MAX_CHARGES = 65536
+
+
+def pgb_energy_noalloc(ctx, x):
+    """pgb_energy through the entry point that allocates no device memory
+    (fixed scratch of PGB_NOALLOC_MAX_CHARGES charges)."""
+    e = pgb_energies()
+    _check(ctx, lib().pgb_energy_noalloc(ctx, _dptr(x, "float64", pgb_num_unknowns(ctx)), ctypes.byref(e)))
+    return {n: getattr(e, n) for n, _ in pgb_energies._fields_}
 
 
 def pgb_timing(ctx, enable, read=True):

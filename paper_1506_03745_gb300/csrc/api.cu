@@ -339,6 +339,15 @@ int pgb_energy(pgb_ctx* c, const double* x, pgb_energies* e, pgb_energies* per_b
     });
 }
 
+int pgb_energy_noalloc(pgb_ctx* c, const double* x, pgb_energies* e) {
+    if (!c) return PGB_EINVAL;
+    return guard(c, [&]() -> int {
+        if (!x || !e) fail(PGB_EINVAL, "null argument");
+        energies_noalloc(c, x, e);
+        return PGB_OK;
+    });
+}
+
 int pgb_timing(pgb_ctx* c, int32_t enable, pgb_stage_times* out) {
     if (!c) return PGB_EINVAL;
     return guard(c, [&]() -> int {

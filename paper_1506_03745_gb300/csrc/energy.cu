@@ -2,6 +2,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -136,6 +137,88 @@ void energies(pgb_ctx* c, const double* x, pgb_energies* e, pgb_energies* per_bo
         if (per_body) per_body[b] = eb;
     }
     if (e) *e = tot;
+}
+
+// ---------------------------------------------------------------- no-alloc path
+// Scratch of pgb_energy_noalloc: reaction potentials at up to
+// PGB_NOALLOC_MAX_CHARGES charges, then 3 sums per body, then the body charge
+// offsets (PGB_MAX_BODIES + 1 int64 in double-sized slots).  Shared by every
+// call in the process; held by every device that loads the library.
+#define PGB_NOALLOC_SCRATCH (PGB_NOALLOC_MAX_CHARGES + 4 * PGB_MAX_BODIES + 1)
+static __device__ __align__(256) double g_energy_scratch[PGB_NOALLOC_SCRATCH];
+
+static std::mutex g_scratch_mu;
+static double* g_scratch_ptr[64];
+static bool g_scratch_ready[64];
+
+// Device address of g_energy_scratch on the current device, looked up once per
+// device (host code cannot use the symbol itself: it names a host stand-in).
+static double* energy_scratch() {
+    int dev = 0;
+    PGB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) fail(PGB_EINVAL, "device ordinal out of range for the no-alloc scratch table");
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_ready[dev]) {
+        double* p = nullptr;
+        cudaError_t err = cudaGetSymbolAddress((void**)&p, g_energy_scratch);
+        if (err != cudaSuccess || p == nullptr) {
+            (void)cudaGetLastError();
+            fail(PGB_ECUDA, std::string("cudaGetSymbolAddress(g_energy_scratch): ") + cudaGetErrorString(err));
+        }
+        g_scratch_ptr[dev] = p;
+        g_scratch_ready[dev] = true;
+    }
+    return g_scratch_ptr[dev];
+}
+
+// Same kernels and arithmetic as energies(); every buffer is either the
+// context's or the static scratch, and the host side uses only stack arrays.
+void energies_noalloc(pgb_ctx* c, const double* x, pgb_energies* e) {
+    if (!c->tree_valid) fail(PGB_ESTATE, "pgb_tree_build has not run");
+    if (c->n_q > PGB_NOALLOC_MAX_CHARGES)
+        fail(PGB_EINVAL, "pgb_energy_noalloc handles at most " + std::to_string(PGB_NOALLOC_MAX_CHARGES) +
+                             " charges; this context has " + std::to_string(c->n_q));
+    double* scratch = energy_scratch();
+    double* phir = scratch;
+    double* sums = scratch + PGB_NOALLOC_MAX_CHARGES;
+    cudaStream_t s = c->stream;
+    const int nb = (int)c->bodies.size();
+    int64_t qo[PGB_MAX_BODIES + 1];
+    for (int b = 0; b < nb; ++b) qo[b] = c->bodies[b].q_off;
+    qo[nb] = c->n_q;
+    // the body charge offsets follow the sums (written before the kernels
+    // read them, on the same stream)
+    static_assert(sizeof(int64_t) == sizeof(double), "layout");
+    int64_t* qoff = reinterpret_cast<int64_t*>(sums + 3 * PGB_MAX_BODIES);
+    PGB_CUDA(cudaMemcpyAsync(qoff, qo, 8 * (nb + 1), cudaMemcpyHostToDevice, s));
+    Rules r = make_rules(c->p.K, c->p.K_near, c->p.n_edge);
+    if (c->n_q) k_phi_reac<<<(unsigned)c->n_q, 128, 0, s>>>(geo(c), body_dev(c), r, c->d_qxyz, c->d_q_body, x, phir);
+    k_body_sums<<<nb, 128, 0, s>>>(geo(c), body_dev(c), c->d_qxyz, c->d_qval, qoff, phir, x, sums);
+    PGB_CUDA(cudaGetLastError());
+    PGB_LAUNCHED(c, c->n_q ? 2 : 1);
+    double h[3 * PGB_MAX_BODIES];
+    PGB_CUDA(cudaMemcpyAsync(h, sums, 8 * 3 * nb, cudaMemcpyDeviceToHost, s));
+    PGB_CUDA(cudaStreamSynchronize(s));
+    const double U = energy_unit_kcal();
+    pgb_energies tot{0, 0, 0, 0};
+    for (int b = 0; b < nb; ++b) {
+        const auto& bd = c->bodies[b];
+        pgb_energies eb{0, 0, 0, 0};
+        if (bd.kind == PGB_DIELECTRIC) {
+            eb.solvation = 0.5 * h[3 * b] * U;
+            eb.coulomb = h[3 * b + 1] / (PGB_FOUR_PI * bd.eps_in) * U;
+        } else if (bd.kind == PGB_SET_CHARGE) {
+            eb.surface = 0.5 * bd.bc * h[3 * b + 2] * U;
+        } else {
+            eb.surface = 0.5 * c->eps_out * bd.bc * h[3 * b + 2] * U;
+        }
+        eb.total = eb.coulomb + eb.solvation + eb.surface;
+        tot.coulomb += eb.coulomb;
+        tot.solvation += eb.solvation;
+        tot.surface += eb.surface;
+        tot.total += eb.total;
+    }
+    *e = tot;
 }
 
 }  // namespace pgb

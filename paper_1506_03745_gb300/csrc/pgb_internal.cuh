@@ -152,6 +152,7 @@ struct pgb_ctx {
     int64_t n_near = 0, n_far = 0;
     pgb::DBuf<int64_t> d_near_off, d_far_off;
     pgb::DBuf<int32_t> d_near, d_far;
+    pgb::DBuf<float4> d_near4, d_far4;   // FP32 entry offsets (node centre - group centre), node id
     // near-field corrections (CSR over sorted targets)
     int64_t n_corr = 0;
     pgb::DBuf<int64_t> d_corr_off;
@@ -214,6 +215,7 @@ void build_rhs(pgb_ctx* c, double* b);
 int solve(pgb_ctx* c, int mode, double tol, int max_iter, int restart, double* x, pgb_solve_stats* st);
 // energy (energy.cu)
 void energies(pgb_ctx* c, const double* x, pgb_energies* e, pgb_energies* per_body);
+void energies_noalloc(pgb_ctx* c, const double* x, pgb_energies* e);
 // quadrature tables on the device (geometry.cu)
 void rule_host(int K, const double** mu, const double** w);
 }  // namespace pgb
