@@ -80,12 +80,14 @@ def m2p_flops(P, laplace):
     return yuk + (lap if laplace else 0)
 
 
-def eval_flops(info, P):
+def p2p_kernel_flops(info):
     yp = info["p2p_pairs"] - info["p2p_laplace_pairs"]
-    lp = info["p2p_laplace_pairs"]
+    return yp * p2p_flops(False) + info["p2p_laplace_pairs"] * p2p_flops(True)
+
+
+def m2p_kernel_flops(info, P):
     ym = info["m2p_pairs"] - info["m2p_laplace_pairs"]
-    lm = info["m2p_laplace_pairs"]
-    return yp * p2p_flops(False) + lp * p2p_flops(True) + ym * m2p_flops(P, False) + lm * m2p_flops(P, True)
+    return ym * m2p_flops(P, False) + info["m2p_laplace_pairs"] * m2p_flops(P, True)
 
 
 # ------------------------------------------------------------------ clocks
@@ -132,10 +134,12 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ profile
-def recorded_traffic():
-    """dram bytes per launch of the FP32 evaluation kernel from the committed
-    ncu summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "k_eval_fp32_two_sphere.txt")
+def recorded_traffic(kernel):
+    """dram bytes per launch of `kernel` from the committed ncu summary
+    (profiles/<kernel>_two_sphere.txt), if it was taken on the current kernel
+    source."""
+    name = kernel.split("<")[0]
+    path = os.path.join(ROOT, "profiles", f"{name}_fp32_two_sphere.txt")
     src = os.path.join(ROOT, "paper_1506_03745_gb300", "csrc", "treecode.cuh")
     if not os.path.exists(path):
         return None
@@ -279,12 +283,16 @@ def run_gpu(args):
     e_err = {k: abs(e32[k] - e64[k]) / max(abs(e64[k]), 1e-300) for k in ("solvation", "surface", "total")}
 
     info = pgb.pgb_tree_stats(ctx)
-    ev_ms, ev_calls = timing["eval"]
-    flops = eval_flops(info, PARAMS["P"])
-    peaks = load_peaks()
     peak_tflops = 152 * 128 * 2 * 2.07e9 / 1e12
-    achieved = flops / (ev_ms / ev_calls / 1e3) / 1e12 if ev_calls else None
-    traffic = recorded_traffic()
+    kern = {}
+    for name, stage, fl in (("k_p2p<float> (P2P, near leaves)", "p2p", p2p_kernel_flops(info)),
+                            ("k_m2p<float,6> (M2P, far nodes)", "m2p", m2p_kernel_flops(info, PARAMS["P"]))):
+        ms, calls = timing[stage]
+        kern[stage] = dict(kernel=name, total_ms=ms, calls=calls, flops=fl,
+                           avg_ms=ms / calls if calls else None,
+                           achieved=fl / (ms / calls / 1e3) / 1e12 if calls else None)
+    dom = max(kern.values(), key=lambda k: k["total_ms"])
+    traffic = recorded_traffic(dom["kernel"].split(" ")[0])
 
     # ---- end to end through the public API with host inputs
     e2e_ms = []
@@ -335,11 +343,14 @@ def run_gpu(args):
                   "energy_rel_err_vs_fp64": e_err, "energies_kcal_mol": e32},
         "stage_ms_per_step": {k: v[0] / args.steps for k, v in timing.items() if k != "kernel_launches"},
         "gpu_launches": timing["kernel_launches"],
-        "roofline": {"kernel": "k_eval<float,6> (P2P + M2P)", "bound": "alu", "achieved": achieved,
-                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": (achieved / peak_tflops) if achieved else None,
-                     "traffic": traffic, "flops_per_launch": flops, "launches": ev_calls,
-                     "avg_launch_ms": ev_ms / ev_calls if ev_calls else None,
-                     "peak_source": FP32_PEAK_NOTE + " (derived, not in MEASURED_PEAKS.json)"},
+        "roofline": {"kernel": dom["kernel"], "bound": "alu", "achieved": dom["achieved"],
+                     "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": (dom["achieved"] / peak_tflops) if dom["achieved"] else None,
+                     "traffic": traffic, "flops_per_launch": dom["flops"], "launches": dom["calls"],
+                     "avg_launch_ms": dom["avg_ms"],
+                     "peak_source": FP32_PEAK_NOTE + " (derived, not in MEASURED_PEAKS.json)",
+                     "other_kernels": {k: {kk: vv for kk, vv in v.items() if kk != "kernel"} | {"kernel": v["kernel"]}
+                                       for k, v in kern.items() if v is not dom}},
         "tree": info,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h,
@@ -395,7 +406,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--leaf", type=int, default=None, help="override leaf_size (parameter sweeps)")
+    ap.add_argument("--P", type=int, default=None, help="override the Taylor order (parameter sweeps)")
+    ap.add_argument("--theta", type=float, default=None, help="override theta (parameter sweeps)")
     args = ap.parse_args()
+    for k, v in (("leaf_size", args.leaf), ("P", args.P), ("theta", args.theta)):
+        if v is not None:
+            PARAMS[k] = v
     if args.impl == "reference":
         run_reference(args)
     elif args.mode == "matvec":

@@ -97,14 +97,15 @@ typedef struct pgb_tree_info {
  * the context's stream while timing is enabled (pgb_timing). */
 #define PGB_STAGE_SOURCES 0   /* FP32 matvec: panel densities and per-point source terms */
 #define PGB_STAGE_UPWARD 1    /* FP32 matvec: P2M at the leaves + moment shifts to the root */
-#define PGB_STAGE_EVAL 2      /* FP32 matvec: P2P over near leaves + M2P over far nodes */
-#define PGB_STAGE_ASSEMBLE 3  /* FP32 matvec: near-field corrections + block rows */
-#define PGB_STAGE_KRYLOV 4    /* Arnoldi (CGS2), Givens, updates */
-#define PGB_STAGE_TREE 5      /* pgb_tree_build */
-#define PGB_STAGE_ENERGY 6    /* pgb_energy */
-#define PGB_STAGE_RHS 7       /* right-hand side (Coulomb rows; imposed terms are FP64 matvecs) */
-#define PGB_STAGE_FP64 8      /* add to stages 0-3 for the FP64 matvec */
-#define PGB_N_STAGES 12
+#define PGB_STAGE_P2P 2       /* FP32 matvec: P2P over the near leaves */
+#define PGB_STAGE_M2P 3       /* FP32 matvec: M2P over the far nodes */
+#define PGB_STAGE_ASSEMBLE 4  /* FP32 matvec: near-field corrections + block rows */
+#define PGB_STAGE_KRYLOV 5    /* Arnoldi (CGS2), Givens, updates */
+#define PGB_STAGE_TREE 6      /* pgb_tree_build */
+#define PGB_STAGE_ENERGY 7    /* pgb_energy */
+#define PGB_STAGE_RHS 8       /* right-hand side (Coulomb rows; imposed terms are FP64 matvecs) */
+#define PGB_STAGE_FP64 9      /* add to stages 0-4 for the FP64 matvec */
+#define PGB_N_STAGES 14
 typedef struct pgb_stage_times {
     double ms[PGB_N_STAGES];        /* summed device milliseconds */
     int64_t calls[PGB_N_STAGES];    /* timed intervals */

@@ -38,9 +38,9 @@ class pgb_tree_info(ctypes.Structure):
                                      "n_corrections")]
 
 
-N_STAGES = 12
-STAGES = ("sources", "upward", "eval", "assemble", "krylov", "tree", "energy", "rhs",
-          "sources_fp64", "upward_fp64", "eval_fp64", "assemble_fp64")
+N_STAGES = 14
+STAGES = ("sources", "upward", "p2p", "m2p", "assemble", "krylov", "tree", "energy", "rhs",
+          "sources_fp64", "upward_fp64", "p2p_fp64", "m2p_fp64", "assemble_fp64")
 
 
 class pgb_stage_times(ctypes.Structure):

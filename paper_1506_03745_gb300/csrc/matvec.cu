@@ -6,10 +6,10 @@
 
 namespace pgb {
 
-void treecode_launch_f32(int stage, int P, const UpArgs& up, const EvalArgs& ev, const void* src, const void* xrel,
-                         void* mom, cudaStream_t s);
-void treecode_launch_f64(int stage, int P, const UpArgs& up, const EvalArgs& ev, const void* src, const void* xrel,
-                         void* mom, cudaStream_t s);
+void treecode_launch_f32(int stage, int P, const UpArgs& up, const std::vector<int64_t>& lv, const EvalArgs& ev,
+                         const void* src, const void* xrel, void* mom, cudaStream_t s);
+void treecode_launch_f64(int stage, int P, const UpArgs& up, const std::vector<int64_t>& lv, const EvalArgs& ev,
+                         const void* src, const void* xrel, void* mom, cudaStream_t s);
 
 static inline int nblk(int64_t n, int t) { return (int)std::max<int64_t>(1, (n + t - 1) / t); }
 
@@ -132,16 +132,26 @@ void apply_operator(pgb_ctx* c, const double* x, double* y, int precision, bool 
     UpArgs up;
     up.n_leaves = c->n_leaves;
     up.leaf_node = c->d_leaf_node; up.nstart = c->d_node_start; up.nend = c->d_node_end;
-    up.parent = c->d_node_parent; up.child = c->d_node_child; up.nchild = c->d_node_nchild;
-    up.ncenter = c->d_node_center; up.K = c->p.K; up.counter = c->d_up_counter;
+    up.child = c->d_node_child; up.nchild = c->d_node_nchild;
+    up.ncenter = c->d_node_center; up.K = c->p.K; up.nbody = c->d_node_body;
+    up.lvl_begin = up.lvl_end = 0;
     EvalArgs ev;
     ev.n_groups = c->n_groups;
     ev.gstart = c->d_group_start; ev.gend = c->d_group_end; ev.gbody = c->d_group_body;
     ev.gcenter = c->d_group_center; ev.near_off = c->d_near_off; ev.far_off = c->d_far_off;
     ev.near_l = c->d_near; ev.far_l = c->d_far; ev.nstart = c->d_node_start; ev.nend = c->d_node_end;
     ev.nbody = c->d_node_body; ev.ncenter = c->d_node_center; ev.K = c->p.K; ev.kappa = c->kappa;
-    for (int b = 0; b < PGB_MAX_BODIES; ++b) ev.lap_body[b] = 0;
-    for (size_t b = 0; b < c->bodies.size(); ++b) ev.lap_body[b] = c->bodies[b].kind == PGB_DIELECTRIC;
+    for (int b = 0; b < PGB_MAX_BODIES; ++b) ev.lap_body[b] = ev.src_active[b] = up.src_active[b] = 0;
+    for (size_t b = 0; b < c->bodies.size(); ++b) {
+        ev.lap_body[b] = c->bodies[b].kind == PGB_DIELECTRIC;
+        // imposed-boundary terms: molecules carry no known density
+        ev.src_active[b] = up.src_active[b] = known_only ? (c->bodies[b].kind != PGB_DIELECTRIC) : 1;
+    }
+    ev.near4 = c->d_near4;
+    ev.far4 = c->d_far4;
+    ev.tile_off = c->d_tile_off;
+    ev.tile_d = c->d_tile_d;
+    ev.tile_m = c->d_tile_m;
     ev.U = c->d_U;
     const bool f32 = precision == PGB_FP32;
     if (f32) {
@@ -152,7 +162,7 @@ void apply_operator(pgb_ctx* c, const double* x, double* y, int precision, bool 
         c->d_mom64.resize((size_t)c->n_nodes * 2 * T);
     }
     {
-        StageTimer tm(c, PGB_STAGE_SOURCES);
+        StageTimer tm(c, PGB_STAGE_SOURCES + (f32 ? 0 : PGB_STAGE_FP64));
         if (f32)
             k_src_prep<float><<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, x, known_only, c->d_y32, c->d_src32,
                                                                   c->d_dens, c->eps_out);
@@ -162,15 +172,15 @@ void apply_operator(pgb_ctx* c, const double* x, double* y, int precision, bool 
         PGB_CUDA(cudaGetLastError());
         PGB_LAUNCHED(c, 1);
     }
-    for (int stage : {PGB_STAGE_UPWARD, PGB_STAGE_EVAL}) {
-        StageTimer tm(c, stage);
-        if (f32) treecode_launch_f32(stage, P, up, ev, c->d_src32, c->d_x32, c->d_mom32, s);
-        else treecode_launch_f64(stage, P, up, ev, c->d_src64, c->d_x64, c->d_mom64, s);
+    for (int stage : {PGB_STAGE_UPWARD, PGB_STAGE_P2P, PGB_STAGE_M2P}) {
+        StageTimer tm(c, stage + (f32 ? 0 : PGB_STAGE_FP64));
+        if (f32) treecode_launch_f32(stage, P, up, c->level_begin, ev, c->d_src32, c->d_x32, c->d_mom32, s);
+        else treecode_launch_f64(stage, P, up, c->level_begin, ev, c->d_src64, c->d_x64, c->d_mom64, s);
         PGB_CUDA(cudaGetLastError());
-        PGB_LAUNCHED(c, 1);
+        PGB_LAUNCHED(c, stage == PGB_STAGE_UPWARD ? (int64_t)c->level_begin.size() - 2 : 1);
     }
     {
-        StageTimer tm(c, PGB_STAGE_ASSEMBLE);
+        StageTimer tm(c, PGB_STAGE_ASSEMBLE + (f32 ? 0 : PGB_STAGE_FP64));
         k_assemble<<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, c->d_U, c->d_dens, c->d_corr_off, c->d_corr_j,
                                                        c->d_corr_val, known_only ? 1 : 0, y);
         PGB_CUDA(cudaGetLastError());

@@ -153,6 +153,10 @@ struct pgb_ctx {
     pgb::DBuf<int64_t> d_near_off, d_far_off;
     pgb::DBuf<int32_t> d_near, d_far;
     pgb::DBuf<float4> d_near4, d_far4;   // FP32 entry offsets (node centre - group centre), node id
+    int64_t n_tiles = 0;                 // P2P tiles (<= 32 points of one near leaf) over all groups
+    pgb::DBuf<int64_t> d_tile_off;
+    pgb::DBuf<float4> d_tile_d;
+    pgb::DBuf<int4> d_tile_m;
     // near-field corrections (CSR over sorted targets)
     int64_t n_corr = 0;
     pgb::DBuf<int64_t> d_corr_off;

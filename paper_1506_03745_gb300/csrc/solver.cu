@@ -301,7 +301,10 @@ int solve(pgb_ctx* c, int mode, double tol, int max_iter, int restart, double* x
         PGB_CUDA(cudaMemcpyAsync(c->d_r.p, c->d_b.p, 8 * n, cudaMemcpyDeviceToDevice, s));
         double rn = bnorm;
         while (rel > tol && z.iterations < max_iter && z.outer_steps < 50) {
-            double inner = std::max(tol * bnorm / rn, 1e-4);
+            // aim each inner FP32 solve at the final tolerance (the FP32
+            // operator itself is accurate to ~1e-7), so that one FP64 residual
+            // usually confirms convergence
+            double inner = std::max(0.5 * tol * bnorm / rn, 1e-7);
             PGB_CUDA(cudaMemsetAsync(c->d_xs.p, 0, 8 * n, s));
             int mv = 0;
             int it = gmres(c, PGB_FP32, c->d_r, c->d_xs, inner * rn, max_iter - z.iterations, restart, &mv, nullptr, true);

@@ -579,32 +579,87 @@ __global__ void k_node_geometry(const int32_t* nstart, const int32_t* nend, cons
         for (int a = 0; a < 3; ++a) center[3 * nd + a] = cw[a];
     }
     __syncthreads();
-    double m = 0;
-    for (int64_t p = s * K + threadIdx.x; p < e * K; p += blockDim.x) {
-        double dx = dsub(Y[3 * p], cw[0]), dy = dsub(Y[3 * p + 1], cw[1]), dz = dsub(Y[3 * p + 2], cw[2]);
-        double d2 = dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz));
-        m = fmax(m, d2);
+    __shared__ double sred[7][32];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY}, am = 0;
+    for (int64_t p = s + threadIdx.x; p < e; p += blockDim.x) {
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fmin(lo[a], C[3 * p + a]);
+            hi[a] = fmax(hi[a], C[3 * p + a]);
+        }
+        am = fmax(am, 8.0 * A[p]);
     }
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    for (int o = 16; o > 0; o >>= 1) {
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fmin(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = fmax(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+        am = fmax(am, __shfl_xor_sync(0xffffffffu, am, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        int wi = threadIdx.x >> 5;
+        for (int a = 0; a < 3; ++a) {
+            sred[a][wi] = lo[a];
+            sred[3 + a][wi] = hi[a];
+        }
+        sred[6][wi] = am;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double mm = 0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) mm = fmax(mm, sh[k]);
-        r2[nd] = mm;
-        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY}, am = 0;
-        for (int64_t p = s; p < e; ++p) {
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
             for (int a = 0; a < 3; ++a) {
-                lo[a] = fmin(lo[a], C[3 * p + a]);
-                hi[a] = fmax(hi[a], C[3 * p + a]);
+                lo[a] = fmin(lo[a], sred[a][k]);
+                hi[a] = fmax(hi[a], sred[3 + a][k]);
             }
-            am = fmax(am, 8.0 * A[p]);
+            am = fmax(am, sred[6][k]);
         }
         for (int a = 0; a < 3; ++a) {
             clo[3 * nd + a] = lo[a];
             chi[3 * nd + a] = hi[a];
         }
         a8[nd] = am;
+    }
+}
+
+// Node radius^2 = max over the node's quadrature nodes of |y - c|^2 (unfused
+// FP64).  Nodes are cut into chunks of R2_CHUNK points, one block per chunk;
+// chunk maxima combine by an integer atomicMax on the bit pattern (valid for
+// non-negative doubles, and order-independent).
+#define R2_CHUNK 4096
+__global__ void k_chunk_count(const int32_t* nstart, const int32_t* nend, int64_t nn, int K, int64_t* cnt) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < nn) cnt[i] = ((int64_t)(nend[i] - nstart[i]) * K + R2_CHUNK - 1) / R2_CHUNK;
+}
+__global__ void k_node_r2(const int32_t* nstart, const int32_t* nend, int64_t nn, const int64_t* coff,
+                          const double* center, const double* Y, int K, unsigned long long* r2bits) {
+    __shared__ double sh[32];
+    __shared__ int64_t s_nd;
+    const int64_t chunk = blockIdx.x;
+    if (threadIdx.x == 0) {  // node owning this chunk: last coff <= chunk
+        int64_t lo = 0, hi = nn;
+        while (hi - lo > 1) {
+            int64_t m = (lo + hi) >> 1;
+            if (coff[m] <= chunk) lo = m;
+            else hi = m;
+        }
+        while (lo + 1 < nn && coff[lo + 1] <= chunk) ++lo;
+        s_nd = lo;
+    }
+    __syncthreads();
+    const int64_t nd = s_nd;
+    const int64_t p0 = (int64_t)nstart[nd] * K + (chunk - coff[nd]) * R2_CHUNK;
+    const int64_t p1 = min((int64_t)nend[nd] * K, p0 + R2_CHUNK);
+    const double c0 = center[3 * nd], c1 = center[3 * nd + 1], c2 = center[3 * nd + 2];
+    double m = 0;
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        double dx = dsub(Y[3 * p], c0), dy = dsub(Y[3 * p + 1], c1), dz = dsub(Y[3 * p + 2], c2);
+        m = fmax(m, dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz)));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, sh[k]);
+        atomicMax(r2bits + nd, (unsigned long long)__double_as_longlong(m));
     }
 }
 
@@ -696,6 +751,19 @@ void build_geometry(pgb_ctx* c) {
                                             c->d_node_center, c->d_node_r2, c->d_node_clo, c->d_node_chi,
                                             c->d_node_a8);
     PGB_CUDA(cudaGetLastError());
+    {
+        DBuf<int64_t> cnt, coff;
+        cnt.resize(nn);
+        coff.resize(nn);
+        k_chunk_count<<<nblk(nn, 256), 256, 0, s>>>(c->d_node_start, c->d_node_end, nn, K, cnt);
+        int64_t nchunks = 0;
+        exclusive_scan_i64(cnt, coff, nn, s, &nchunks);
+        PGB_CUDA(cudaMemsetAsync(c->d_node_r2.p, 0, 8 * nn, s));
+        k_node_r2<<<(unsigned)nchunks, 256, 0, s>>>(c->d_node_start, c->d_node_end, nn, coff, c->d_node_center,
+                                                    c->d_y, K, (unsigned long long*)c->d_node_r2.p);
+        PGB_CUDA(cudaGetLastError());
+        PGB_CUDA(cudaStreamSynchronize(s));
+    }
     // target groups
     std::vector<int32_t> gs, ge, gb;
     int G = c->p.group_size;
@@ -804,6 +872,56 @@ __global__ void k_lists(ListArgs a, int64_t ng, bool fill, int64_t* ncnt, int64_
     }
 }
 
+// FP32 offset of every list entry: node centre - group centre (FP64
+// difference, rounded once), with the node id in the .w bits.
+__global__ void k_list_offsets(int64_t ng, const int64_t* off, const int32_t* ids, const double* ncen,
+                               const double* gcen, float4* out) {
+    int64_t g = blockIdx.x;
+    if (g >= ng) return;
+    for (int64_t e = off[g] + threadIdx.x; e < off[g + 1]; e += blockDim.x) {
+        int nd = ids[e];
+        out[e] = make_float4((float)(ncen[3 * nd] - gcen[3 * g]), (float)(ncen[3 * nd + 1] - gcen[3 * g + 1]),
+                             (float)(ncen[3 * nd + 2] - gcen[3 * g + 2]), __int_as_float(nd));
+    }
+}
+
+// P2P tiles: every near leaf of a group cut into runs of at most 32
+// quadrature points; descriptor = (leaf centre - group centre in FP32, first
+// point) and (leaf, count, flags: 1 Laplace pair, 2 leaf holds group targets, body).
+__global__ void k_tile_count(int64_t ng, const int64_t* noff, const int32_t* nearl, const int32_t* nstart,
+                             const int32_t* nend, int K, int64_t* cnt) {
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    int64_t c = 0;
+    for (int64_t e = noff[g]; e < noff[g + 1]; ++e) {
+        int nd = nearl[e];
+        c += ((int64_t)(nend[nd] - nstart[nd]) * K + 31) / 32;
+    }
+    cnt[g] = c;
+}
+__global__ void k_tile_fill(int64_t ng, const int64_t* noff, const int32_t* nearl, const float4* near4,
+                            const int32_t* nstart, const int32_t* nend, const int32_t* nbody, const int32_t* gstart,
+                            const int32_t* gend, const int32_t* gbody, BodyDev bd, int K, const int64_t* toff,
+                            float4* td, int4* tm) {
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    int64_t w = toff[g];
+    const int gb = gbody[g];
+    for (int64_t e = noff[g]; e < noff[g + 1]; ++e) {
+        const int nd = nearl[e];
+        const int nb = nbody[nd];
+        const int flags = ((nb == gb && bd.kind[gb] == PGB_DIELECTRIC) ? 1 : 0) |
+                          ((nstart[nd] < gend[g] && nend[nd] > gstart[g]) ? 2 : 0);
+        const int64_t s0 = (int64_t)nstart[nd] * K, s1 = (int64_t)nend[nd] * K;
+        for (int64_t q = s0; q < s1; q += 32) {
+            const float4 o = near4[e];
+            td[w] = make_float4(o.x, o.y, o.z, __int_as_float((int)q));
+            tm[w] = make_int4(nd, (int)min((int64_t)32, s1 - q), flags, nb);
+            ++w;
+        }
+    }
+}
+
 void build_lists(pgb_ctx* c) {
     cudaStream_t s = c->stream;
     int64_t ng = c->n_groups;
@@ -837,6 +955,33 @@ void build_lists(pgb_ctx* c) {
     k_lists<<<nblk(ng, 64), 64, 0, s>>>(a, ng, true, nullptr, nullptr, c->d_near_off, c->d_far_off, c->d_near,
                                         c->d_far, st);
     PGB_CUDA(cudaGetLastError());
+    c->d_near4.resize(tn);
+    c->d_far4.resize(tf);
+    k_list_offsets<<<(unsigned)ng, 64, 0, s>>>(ng, c->d_near_off, c->d_near, c->d_node_center, c->d_group_center,
+                                               c->d_near4);
+    k_list_offsets<<<(unsigned)ng, 64, 0, s>>>(ng, c->d_far_off, c->d_far, c->d_node_center, c->d_group_center,
+                                               c->d_far4);
+    PGB_CUDA(cudaGetLastError());
+    {
+        DBuf<int64_t> tc;
+        tc.resize(ng);
+        c->d_tile_off.resize(ng + 1);
+        k_tile_count<<<nblk(ng, 128), 128, 0, s>>>(ng, c->d_near_off, c->d_near, c->d_node_start, c->d_node_end,
+                                                   c->p.K, tc);
+        int64_t nt = 0;
+        exclusive_scan_i64(tc, c->d_tile_off, ng, s, &nt);
+        PGB_CUDA(cudaMemcpyAsync(c->d_tile_off.p + ng, &nt, 8, cudaMemcpyHostToDevice, s));
+        c->n_tiles = nt;
+        c->d_tile_d.resize(nt);
+        c->d_tile_m.resize(nt);
+        k_tile_fill<<<nblk(ng, 128), 128, 0, s>>>(ng, c->d_near_off, c->d_near, c->d_near4, c->d_node_start,
+                                                  c->d_node_end, c->d_node_body, c->d_group_start, c->d_group_end,
+                                                  c->d_group_body, body_dev(c), c->p.K, c->d_tile_off, c->d_tile_d,
+                                                  c->d_tile_m);
+        PGB_CUDA(cudaGetLastError());
+        PGB_CUDA(cudaStreamSynchronize(s));
+    }
+    PGB_LAUNCHED(c, 6);
     unsigned long long h[5];
     PGB_CUDA(cudaMemcpyAsync(h, st.p, 40, cudaMemcpyDeviceToHost, s));
     PGB_CUDA(cudaStreamSynchronize(s));

@@ -38,6 +38,20 @@ __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
 __device__ __forceinline__ float exp_(float x) { return __expf(x); }
 __device__ __forceinline__ double exp_(double x) { return exp(x); }
+// 2^x (the P2P loop folds log2(e) into its constant).  FP32: the SFU's
+// approximate forms (relative error about 2^-22), one instruction each.
+__device__ __forceinline__ float exp2_(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ double exp2_(double x) { return exp2(x); }
+__device__ __forceinline__ float rsqrt_fast(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ double rsqrt_fast(double x) { return rsqrt(x); }
 
 // Neumaier-compensated accumulation s + c += v.
 template <typename T>
@@ -120,21 +134,38 @@ struct EvalArgs {
     int K;
     double kappa;
     int lap_body[PGB_MAX_BODIES];  // 1 when the body is dielectric
+    int src_active[PGB_MAX_BODIES];  // 0: the body's densities are all zero (skip)
+    const float4* near4;           // per near entry: leaf centre - group centre, node id bits
+    const float4* far4;            // per far entry: node centre - group centre, node id bits
+    const int64_t* tile_off;       // per group: its P2P tiles [tile_off[g], tile_off[g+1])
+    const float4* tile_d;          // per tile: leaf centre - group centre (FP32), first point (int bits)
+    const int4* tile_m;            // per tile: leaf node, point count, flags (1 Laplace, 2 own panel), body
     double* U;                     // 2 per sorted panel
 };
 
 // Far-field contraction sum_k G_k(R) M_k for one target (returns Yukawa and,
-// when lap, Laplace).
+// when lap, Laplace).  Per level n the recurrence constants are folded into
+// a_n = -(2n-1)/(n rho^2), b_n = -(n-1)/(n rho^2), e_n = -kappa/(n rho^2) and
+// h_n = -kappa/n; H is not formed at the last level.
 template <typename real, int P>
 __device__ __forceinline__ void m2p_eval(real Rx, real Ry, real Rz, real kappa, const real* ML, const real* MY,
                                          bool lap, real& uL, real& uY) {
     constexpr MI<P> mi{};
     constexpr int T = MI<P>::T;
-    real R[3] = {Rx, Ry, Rz};
-    real r2 = Rx * Rx + Ry * Ry + Rz * Rz;
-    real ri = rsqrt_(r2);
-    real i2 = ri * ri;
-    real rho = r2 * ri;
+    const real R[3] = {Rx, Ry, Rz};
+    const real r2 = Rx * Rx + Ry * Ry + Rz * Rz;
+    const real ri = rsqrt_(r2);
+    const real i2 = ri * ri;
+    const real rho = r2 * ri;
+    real an[P + 1], bn[P + 1], en[P + 1], hn[P + 1];
+#pragma unroll
+    for (int n = 1; n <= P; ++n) {
+        const real inv_n = real(1) / real(n);
+        an[n] = -(real(2 * n - 1) * inv_n) * i2;
+        bn[n] = -(real(n - 1) * inv_n) * i2;
+        hn[n] = -kappa * inv_n;
+        en[n] = hn[n] * i2;
+    }
     real G[T], H[T];
     H[0] = exp_(-kappa * rho);
     G[0] = H[0] * ri;
@@ -142,23 +173,40 @@ __device__ __forceinline__ void m2p_eval(real Rx, real Ry, real Rz, real kappa, 
 #pragma unroll
     for (int k = 1; k < T; ++k) {
         const int n = mi.lvl[k];
+        // S1 = sum_a R_a G_{k-e_a}, S2 = sum_a G_{k-2e_a} (T1, T2 with H); the
+        // parent sets are compile-time, so the sums start at their first term
         real S1 = 0, S2 = 0, T1 = 0, T2 = 0;
+        bool h1 = false, h2 = false;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             if (mi.m1[k][a] >= 0) {
-                S1 += R[a] * G[mi.m1[k][a]];
-                T1 += R[a] * H[mi.m1[k][a]];
+                if (h1) {
+                    S1 += R[a] * G[mi.m1[k][a]];
+                    T1 += R[a] * H[mi.m1[k][a]];
+                } else {
+                    S1 = R[a] * G[mi.m1[k][a]];
+                    T1 = R[a] * H[mi.m1[k][a]];
+                    h1 = true;
+                }
             }
             if (mi.m2[k][a] >= 0) {
-                S2 += G[mi.m2[k][a]];
-                T2 += H[mi.m2[k][a]];
+                if (h2) {
+                    S2 += G[mi.m2[k][a]];
+                    T2 += H[mi.m2[k][a]];
+                } else {
+                    S2 = G[mi.m2[k][a]];
+                    T2 = H[mi.m2[k][a]];
+                    h2 = true;
+                }
             }
         }
-        const real inv_n = real(1) / real(n);
-        const real c1 = real(2 * n - 1) * inv_n, c2 = real(n - 1) * inv_n;
-        real kn = kappa * inv_n;
-        H[k] = -kn * (S1 + S2);
-        G[k] = -(c1 * S1 + c2 * S2 + kn * (T1 + T2)) * i2;
+        if (h2) {
+            if (n < P) H[k] = hn[n] * (S1 + S2);
+            G[k] = an[n] * S1 + bn[n] * S2 + en[n] * (T1 + T2);
+        } else {
+            if (n < P) H[k] = hn[n] * S1;
+            G[k] = an[n] * S1 + en[n] * T1;
+        }
         accY += G[k] * MY[k];
     }
     uY = accY;
@@ -170,14 +218,19 @@ __device__ __forceinline__ void m2p_eval(real Rx, real Ry, real Rz, real kappa, 
         for (int k = 1; k < T; ++k) {
             const int n = mi.lvl[k];
             real S1 = 0, S2 = 0;
+            bool h1 = false, h2 = false;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                if (mi.m1[k][a] >= 0) S1 += R[a] * L[mi.m1[k][a]];
-                if (mi.m2[k][a] >= 0) S2 += L[mi.m2[k][a]];
+                if (mi.m1[k][a] >= 0) {
+                    S1 = h1 ? S1 + R[a] * L[mi.m1[k][a]] : R[a] * L[mi.m1[k][a]];
+                    h1 = true;
+                }
+                if (mi.m2[k][a] >= 0) {
+                    S2 = h2 ? S2 + L[mi.m2[k][a]] : L[mi.m2[k][a]];
+                    h2 = true;
+                }
             }
-            const real inv_n = real(1) / real(n);
-            const real c1 = real(2 * n - 1) * inv_n, c2 = real(n - 1) * inv_n;
-            L[k] = -(c1 * S1 + c2 * S2) * i2;
+            L[k] = h2 ? an[n] * S1 + bn[n] * S2 : an[n] * S1;
             accL += L[k] * ML[k];
         }
         uL = accL;
@@ -194,133 +247,277 @@ __device__ __forceinline__ void p2p_tile(const typename V4<real>::t* sA, const t
                                          int64_t t, int64_t own_lo, int64_t own_hi, real r0x, real r0y, real r0z,
                                          real kappa, real& sumL, real& sumY) {
     using v4 = typename V4<real>::t;
-    const real nkl = -kappa;
+    const real nkl = -kappa * real(1.4426950408889634);  // -kappa log2(e)
+    real sL2 = 0, sY2 = 0;  // second accumulator pair: two independent chains
 #pragma unroll 4
     for (int j = 0; j < cnt; ++j) {
         const v4 A = sA[j], B = sB[j];
         const real dx = r0x - A.x, dy = r0y - A.y, dz = r0z - A.z;
         const real r2 = dx * dx + dy * dy + dz * dz;
-        bool keep = r2 > real(0);
-        if (OWN) keep = keep && !(t + j >= own_lo && t + j < own_hi);
-        const real ri = keep ? rsqrt_(r2) : real(0);
+        // a quadrature node of another panel never coincides with a target
+        // centroid on a valid (non-overlapping) mesh; only the target's own
+        // panel, in the leaf that holds the group, needs the exclusion
+        real ri = rsqrt_fast(r2);
+        if (OWN) ri = (r2 > real(0) && !(t + j >= own_lo && t + j < own_hi)) ? ri : real(0);
         const real pd = B.x * dx + B.y * dy + B.z * dz;
         const real tt = pd * (ri * ri);
-        if (LAP) sumL += ri * (A.w - tt);
         const real r = r2 * ri;
-        const real ex = exp_(nkl * r);
+        const real ex = exp2_(nkl * r);
         const real gg = kappa * r + real(1);
-        sumY += (ex * ri) * (B.w - gg * tt);
+        if (j & 1) {
+            if (LAP) sL2 += ri * (A.w - tt);
+            sY2 += (ex * ri) * (B.w - gg * tt);
+        } else {
+            if (LAP) sumL += ri * (A.w - tt);
+            sumY += (ex * ri) * (B.w - gg * tt);
+        }
     }
+    sumL += sL2;
+    sumY += sY2;
 }
 
-// One warp per target group: P2P over the near leaves, M2P over the far nodes.
-template <typename real, int P>
-__global__ void __launch_bounds__(128) k_eval(EvalArgs a, const typename V4<real>::t* __restrict__ src,
-                                              const typename V4<real>::t* __restrict__ xrel,
-                                              const real* __restrict__ mom) {
+// One block of NW warps per target group (32 targets, one per lane): the
+// warps share out the near leaves (P2P) and far nodes (M2P) of the group's
+// lists round robin, and their partial sums are combined in warp order.
+template <typename real>
+__device__ __forceinline__ void entry_offset(const EvalArgs& a, int64_t e, bool is_far, double gc0, double gc1,
+                                             double gc2, int& nd, real& ox, real& oy, real& oz);
+template <>
+__device__ __forceinline__ void entry_offset<float>(const EvalArgs& a, int64_t e, bool is_far, double, double, double,
+                                                    int& nd, float& ox, float& oy, float& oz) {
+    const float4 q = is_far ? a.far4[e] : a.near4[e];
+    nd = __float_as_int(q.w);
+    ox = q.x;
+    oy = q.y;
+    oz = q.z;
+}
+template <>
+__device__ __forceinline__ void entry_offset<double>(const EvalArgs& a, int64_t e, bool is_far, double gc0, double gc1,
+                                                     double gc2, int& nd, double& ox, double& oy, double& oz) {
+    nd = is_far ? a.far_l[e] : a.near_l[e];
+    ox = a.ncenter[3 * nd] - gc0;
+    oy = a.ncenter[3 * nd + 1] - gc1;
+    oz = a.ncenter[3 * nd + 2] - gc2;
+}
+
+// P2P: one block of NW warps per target group (32 targets, one per lane); the
+// group's source tiles (up to 32 quadrature points of one near leaf) are dealt
+// round robin to the warps, the next tile prefetched into registers.  Partial
+// sums are combined in warp order and written to U (the far field is added by
+// k_m2p afterwards).
+template <typename real, int NW>
+__global__ void __launch_bounds__(NW * 32) k_p2p(EvalArgs a,
+                                                                    const typename V4<real>::t* __restrict__ src,
+                                                                    const typename V4<real>::t* __restrict__ xrel) {
     using v4 = typename V4<real>::t;
-    constexpr int T = MI<P>::T;
-    __shared__ v4 sA[4][32], sB[4][32];
-    __shared__ real sM[4][2 * T];
+    __shared__ v4 sA[NW][32], sB[NW][32];
+    __shared__ real red[NW][4][32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t g = (int64_t)blockIdx.x * 4 + w;
+    const int64_t g = blockIdx.x;
     if (g >= a.n_groups) return;
     const int64_t p0 = a.gstart[g], p1 = a.gend[g];
     const int64_t p = p0 + lane;
     const bool active = p < p1;
-    v4 xr = active ? xrel[p] : xrel[p0];
+    const v4 xr = active ? xrel[p] : xrel[p0];
+    const double gc0 = a.gcenter[3 * g], gc1 = a.gcenter[3 * g + 1], gc2 = a.gcenter[3 * g + 2];
+    const real kappa = (real)a.kappa;
+    const int64_t own_lo = p * a.K, own_hi = own_lo + a.K;
+    real UL = 0, cL = 0, UY = 0, cY = 0;
+    const int64_t t1 = a.tile_off[g + 1];
+    int64_t t = a.tile_off[g] + w;
+    v4 pa = v4(), pb = v4();
+    int4 m = make_int4(0, 0, 0, 0);
+    float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (t < t1) {
+        d = a.tile_d[t];
+        m = a.tile_m[t];
+        if (lane < m.y) {
+            const int64_t q = (int64_t)__float_as_int(d.w) + lane;
+            pa = src[2 * q];
+            pb = src[2 * q + 1];
+        }
+    }
+    while (t < t1) {
+        const int cnt = m.y, flags = m.z | (a.src_active[m.w] ? 0 : 4);
+        const int64_t first = (int64_t)__float_as_int(d.w);
+        real ox, oy, oz;
+        if (sizeof(real) == sizeof(float)) {
+            ox = (real)d.x;
+            oy = (real)d.y;
+            oz = (real)d.z;
+        } else {
+            const int nd = m.x;
+            ox = (real)(a.ncenter[3 * nd] - gc0);
+            oy = (real)(a.ncenter[3 * nd + 1] - gc1);
+            oz = (real)(a.ncenter[3 * nd + 2] - gc2);
+        }
+        __syncwarp();
+        if (lane < cnt) {
+            sA[w][lane] = pa;
+            sB[w][lane] = pb;
+        }
+        __syncwarp();
+        t += NW;
+        if (t < t1) {  // prefetch this warp's next tile
+            d = a.tile_d[t];
+            m = a.tile_m[t];
+            if (lane < m.y) {
+                const int64_t q = (int64_t)__float_as_int(d.w) + lane;
+                pa = src[2 * q];
+                pb = src[2 * q + 1];
+            }
+        }
+        const real r0x = xr.x - ox, r0y = xr.y - oy, r0z = xr.z - oz;
+        real sumL = 0, sumY = 0;
+        if (flags & 4) {
+            // source body without density in this product (imposed-boundary terms)
+        } else if (flags & 2) {
+            if (flags & 1) p2p_tile<real, true, true>(sA[w], sB[w], cnt, first, own_lo, own_hi, r0x, r0y, r0z, kappa, sumL, sumY);
+            else p2p_tile<real, false, true>(sA[w], sB[w], cnt, first, own_lo, own_hi, r0x, r0y, r0z, kappa, sumL, sumY);
+        } else {
+            if (flags & 1) p2p_tile<real, true, false>(sA[w], sB[w], cnt, first, own_lo, own_hi, r0x, r0y, r0z, kappa, sumL, sumY);
+            else p2p_tile<real, false, false>(sA[w], sB[w], cnt, first, own_lo, own_hi, r0x, r0y, r0z, kappa, sumL, sumY);
+        }
+        kadd(UL, cL, sumL);
+        kadd(UY, cY, sumY);
+    }
+    red[w][0][lane] = UL;
+    red[w][1][lane] = cL;
+    red[w][2][lane] = UY;
+    red[w][3][lane] = cY;
+    __syncthreads();
+    if (w == 0 && active) {
+        real sL = 0, eL = 0, sY = 0, eY = 0;
+        for (int k = 0; k < NW; ++k) {
+            kadd(sL, eL, red[k][0][lane]);
+            kadd(sL, eL, red[k][1][lane]);
+            kadd(sY, eY, red[k][2][lane]);
+            kadd(sY, eY, red[k][3][lane]);
+        }
+        a.U[2 * p] = (double)sL + (double)eL;
+        a.U[2 * p + 1] = (double)sY + (double)eY;
+    }
+}
+
+// M2P: one block of NW warps per target group; far nodes round robin over the
+// warps with the next node's moments prefetched; adds to the P2P result in U.
+template <typename real, int P, int NW>
+__global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a, const typename V4<real>::t* __restrict__ xrel,
+                                                  const real* __restrict__ mom) {
+    using v4 = typename V4<real>::t;
+    constexpr int T = MI<P>::T;
+    constexpr int MW = (2 * T + 31) / 32;  // moment words per lane
+    __shared__ real sM[NW][2 * T];
+    __shared__ real red[NW][4][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t g = blockIdx.x;
+    if (g >= a.n_groups) return;
+    const int64_t p0 = a.gstart[g], p1 = a.gend[g];
+    const int64_t p = p0 + lane;
+    const bool active = p < p1;
+    const v4 xr = active ? xrel[p] : xrel[p0];
     const double gc0 = a.gcenter[3 * g], gc1 = a.gcenter[3 * g + 1], gc2 = a.gcenter[3 * g + 2];
     const int gb = a.gbody[g];
     const real kappa = (real)a.kappa;
     real UL = 0, cL = 0, UY = 0, cY = 0;
-    // ---- near field: direct K-point sums
-    for (int64_t e = a.near_off[g]; e < a.near_off[g + 1]; ++e) {
-        const int nd = a.near_l[e];
-        const bool lap = (a.nbody[nd] == gb) && a.lap_body[gb];
-        const real r0x = xr.x - (real)(a.ncenter[3 * nd] - gc0);
-        const real r0y = xr.y - (real)(a.ncenter[3 * nd + 1] - gc1);
-        const real r0z = xr.z - (real)(a.ncenter[3 * nd + 2] - gc2);
-        const int64_t s0 = (int64_t)a.nstart[nd] * a.K, s1 = (int64_t)a.nend[nd] * a.K;
-        // the target's own panel is left to the near-field correction (its
-        // centroid node is singular); only a leaf overlapping the group needs the test
-        const bool own = (a.nstart[nd] < p1) && (a.nend[nd] > p0);
-        const int64_t own_lo = p * a.K, own_hi = own_lo + a.K;
-        for (int64_t t = s0; t < s1; t += 32) {
-            const int cnt = (int)min((int64_t)32, s1 - t);
-            __syncwarp();
-            if (lane < cnt) {
-                sA[w][lane] = src[2 * (t + lane)];
-                sB[w][lane] = src[2 * (t + lane) + 1];
-            }
-            __syncwarp();
-            real sumL = 0, sumY = 0;
-            if (own) {
-                if (lap) p2p_tile<real, true, true>(sA[w], sB[w], cnt, t, own_lo, own_hi, r0x, r0y, r0z, kappa, sumL, sumY);
-                else p2p_tile<real, false, true>(sA[w], sB[w], cnt, t, own_lo, own_hi, r0x, r0y, r0z, kappa, sumL, sumY);
-            } else {
-                if (lap) p2p_tile<real, true, false>(sA[w], sB[w], cnt, t, own_lo, own_hi, r0x, r0y, r0z, kappa, sumL, sumY);
-                else p2p_tile<real, false, false>(sA[w], sB[w], cnt, t, own_lo, own_hi, r0x, r0y, r0z, kappa, sumL, sumY);
-            }
-            kadd(UL, cL, sumL);
-            kadd(UY, cY, sumY);
+    const int64_t f1 = a.far_off[g + 1];
+    auto seek = [&](int64_t ee) -> int64_t {  // next active entry of this warp
+        while (ee < f1) {
+            int nn;
+            real qx, qy, qz;
+            entry_offset<real>(a, ee, true, gc0, gc1, gc2, nn, qx, qy, qz);
+            if (a.src_active[a.nbody[nn]]) return ee;
+            ee += NW;
+        }
+        return ee;
+    };
+    real pm[MW];
+    int nd = -1;
+    real ox = 0, oy = 0, oz = 0;
+    int64_t e = seek(a.far_off[g] + w);
+    if (e < f1) {
+        entry_offset<real>(a, e, true, gc0, gc1, gc2, nd, ox, oy, oz);
+#pragma unroll
+        for (int q = 0; q < MW; ++q) {
+            const int k = lane + 32 * q;
+            pm[q] = k < 2 * T ? mom[(int64_t)nd * 2 * T + k] : real(0);
         }
     }
-    // ---- far field: Taylor expansions about node centres
-    for (int64_t e = a.far_off[g]; e < a.far_off[g + 1]; ++e) {
-        const int nd = a.far_l[e];
+    while (e < f1) {
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < MW; ++q) {
+            const int k = lane + 32 * q;
+            if (k < 2 * T) sM[w][k] = pm[q];
+        }
+        __syncwarp();
         const bool lap = (a.nbody[nd] == gb) && a.lap_body[gb];
-        __syncwarp();
-        for (int k = lane; k < 2 * T; k += 32) sM[w][k] = mom[(int64_t)nd * 2 * T + k];
-        __syncwarp();
-        const real Rx = xr.x - (real)(a.ncenter[3 * nd] - gc0);
-        const real Ry = xr.y - (real)(a.ncenter[3 * nd + 1] - gc1);
-        const real Rz = xr.z - (real)(a.ncenter[3 * nd + 2] - gc2);
+        const real Rx = xr.x - ox, Ry = xr.y - oy, Rz = xr.z - oz;
+        e = seek(e + NW);
+        if (e < f1) {  // prefetch the next node
+            entry_offset<real>(a, e, true, gc0, gc1, gc2, nd, ox, oy, oz);
+#pragma unroll
+            for (int q = 0; q < MW; ++q) {
+                const int k = lane + 32 * q;
+                pm[q] = k < 2 * T ? mom[(int64_t)nd * 2 * T + k] : real(0);
+            }
+        }
         real uL, uY;
         m2p_eval<real, P>(Rx, Ry, Rz, kappa, sM[w], sM[w] + T, lap, uL, uY);
         kadd(UL, cL, uL);
         kadd(UY, cY, uY);
     }
-    if (active) {
-        a.U[2 * p] = (double)UL + (double)cL;
-        a.U[2 * p + 1] = (double)UY + (double)cY;
+    red[w][0][lane] = UL;
+    red[w][1][lane] = cL;
+    red[w][2][lane] = UY;
+    red[w][3][lane] = cY;
+    __syncthreads();
+    if (w == 0 && active) {
+        real sL = 0, eL = 0, sY = 0, eY = 0;
+        for (int k = 0; k < NW; ++k) {
+            kadd(sL, eL, red[k][0][lane]);
+            kadd(sL, eL, red[k][1][lane]);
+            kadd(sY, eY, red[k][2][lane]);
+            kadd(sY, eY, red[k][3][lane]);
+        }
+        a.U[2 * p] += (double)sL + (double)eL;
+        a.U[2 * p + 1] += (double)sY + (double)eY;
     }
 }
 
 struct UpArgs {
     int64_t n_leaves;
-    const int32_t *leaf_node, *nstart, *nend, *parent, *child, *nchild;
+    const int32_t *leaf_node, *nstart, *nend, *child, *nchild, *nbody;
+    int src_active[PGB_MAX_BODIES];
     const double* ncenter;
     int K;
-    unsigned int* counter;  // per node, zero between launches
+    int64_t lvl_begin, lvl_end;  // node ids of the level for k_m2m_level
 };
 
-// Upward pass in one launch: each block forms the moments of one leaf from its
-// points, then the block that completes the last child of a node forms the
-// node from its children by the binomial shift, and so on to the root.  No
-// block waits on another; the child order of every sum is fixed.
+__device__ __constant__ const int kBinom[9][9] = {
+    {1, 0, 0, 0, 0, 0, 0, 0, 0},      {1, 1, 0, 0, 0, 0, 0, 0, 0},      {1, 2, 1, 0, 0, 0, 0, 0, 0},
+    {1, 3, 3, 1, 0, 0, 0, 0, 0},      {1, 4, 6, 4, 1, 0, 0, 0, 0},      {1, 5, 10, 10, 5, 1, 0, 0, 0},
+    {1, 6, 15, 20, 15, 6, 1, 0, 0},   {1, 7, 21, 35, 35, 21, 7, 1, 0}, {1, 8, 28, 56, 70, 56, 28, 8, 1}};
+
+// P2M: moments of every leaf about its centre, u = c - y (one block per leaf).
 template <typename real, int P>
-__global__ void __launch_bounds__(128) k_upward(UpArgs a, const typename V4<real>::t* __restrict__ src,
-                                                real* __restrict__ mom) {
+__global__ void __launch_bounds__(128) k_p2m_leaves(UpArgs a, const typename V4<real>::t* __restrict__ src,
+                                                    real* __restrict__ mom) {
     using v4 = typename V4<real>::t;
     constexpr int T = MI<P>::T;
     __shared__ real pw[128][3][P + 1];
     __shared__ real sq[128][5];
-    __shared__ real dp[3][P + 1];
-    __shared__ short idx3[P + 1][P + 1][P + 1];
-    __shared__ int last;
     const int tid = threadIdx.x;
     const int64_t leaf = blockIdx.x;
     if (leaf >= a.n_leaves) return;
-    int nd = a.leaf_node[leaf];
-    int kx = 0, ky = 0, kz = 0;
-    if (tid < T) {
-        decode_mi(tid, kx, ky, kz);
-        idx3[kx][ky][kz] = (short)tid;
-    }
-    // ---- P2M at the leaf centre: u = c - y = -(y - c)
-    {
+    const int nd = a.leaf_node[leaf];
+    if (!a.src_active[a.nbody[nd]]) return;
+    const int64_t s0 = (int64_t)a.nstart[nd] * a.K, s1 = (int64_t)a.nend[nd] * a.K;
+    for (int k0 = 0; k0 < T; k0 += 128) {
+        const int k = k0 + tid;
+        int kx = 0, ky = 0, kz = 0;
+        if (k < T) decode_mi(k, kx, ky, kz);
         real accL = 0, accY = 0;
-        const int64_t s0 = (int64_t)a.nstart[nd] * a.K, s1 = (int64_t)a.nend[nd] * a.K;
         for (int64_t t = s0; t < s1; t += 128) {
             const int cnt = (int)min((int64_t)128, s1 - t);
             __syncthreads();
@@ -336,81 +533,103 @@ __global__ void __launch_bounds__(128) k_upward(UpArgs a, const typename V4<real
                 }
                 sq[tid][0] = A.w;  // qL
                 sq[tid][1] = B.w;  // qY
-                sq[tid][2] = B.x;  // p
+                sq[tid][2] = B.x;  // p = w phi n
                 sq[tid][3] = B.y;
                 sq[tid][4] = B.z;
             }
             __syncthreads();
-            if (tid < T) {
+            if (k < T) {
                 for (int j = 0; j < cnt; ++j) {
-                    const real mono = pw[j][0][kx] * pw[j][1][ky] * pw[j][2][kz];
+                    const real px = pw[j][0][kx], py = pw[j][1][ky], pz = pw[j][2][kz];
+                    const real mono = px * py * pz;
+                    // (q + p . grad_u) u^k
                     real dl = 0;
-                    if (kx) dl += sq[j][2] * real(kx) * pw[j][0][kx - 1] * pw[j][1][ky] * pw[j][2][kz];
-                    if (ky) dl += sq[j][3] * real(ky) * pw[j][0][kx] * pw[j][1][ky - 1] * pw[j][2][kz];
-                    if (kz) dl += sq[j][4] * real(kz) * pw[j][0][kx] * pw[j][1][ky] * pw[j][2][kz - 1];
+                    if (kx) dl += sq[j][2] * real(kx) * pw[j][0][kx - 1] * py * pz;
+                    if (ky) dl += sq[j][3] * real(ky) * px * pw[j][1][ky - 1] * pz;
+                    if (kz) dl += sq[j][4] * real(kz) * px * py * pw[j][2][kz - 1];
                     accL += sq[j][0] * mono + dl;
                     accY += sq[j][1] * mono + dl;
                 }
             }
         }
-        if (tid < T) {
-            mom[(int64_t)nd * 2 * T + tid] = accL;
-            mom[(int64_t)nd * 2 * T + T + tid] = accY;
+        if (k < T) {
+            mom[(int64_t)nd * 2 * T + k] = accL;
+            mom[(int64_t)nd * 2 * T + T + k] = accY;
         }
     }
-    // ---- walk up while this block completed the last child
-    while (true) {
-        __threadfence();
-        __syncthreads();
-        const int par = a.parent[nd];
-        if (par < 0) break;
-        if (tid == 0) {
-            unsigned int prev = atomicAdd(&a.counter[par], 1u);
-            last = (prev + 1 == (unsigned int)a.nchild[par]);
-            if (last) a.counter[par] = 0;  // leave the counter clean for the next launch
+}
+
+// Moment shift for every inner node of one level from its (at most eight)
+// children: M_k(c) = sum_{j<=k} C(k,j) (c - c_child)^{k-j} M_j(c_child).  The
+// shift is separable, so it is applied as three one-axis passes
+// A -> B (x) -> C (y) -> D (z), each output summing at most P+1 terms; all
+// children are shifted at once, then summed in child order.
+template <typename real, int P>
+__global__ void __launch_bounds__(256) k_m2m_level(UpArgs a, real* __restrict__ mom) {
+    constexpr int T = MI<P>::T;
+    __shared__ real bufA[8][2 * T], bufB[8][2 * T];
+    __shared__ real cd[8][3][P + 1];
+    __shared__ real binom[P + 1][P + 1];
+    __shared__ short idx3[P + 1][P + 1][P + 1];
+    __shared__ signed char kk[T][3];
+    const int tid = threadIdx.x;
+    const int64_t nd = a.lvl_begin + blockIdx.x;
+    if (nd >= a.lvl_end) return;
+    const int nc = a.nchild[nd];
+    if (nc == 0 || !a.src_active[a.nbody[nd]]) return;
+    const int fc = a.child[nd];
+    for (int k = tid; k < T; k += blockDim.x) {
+        int x, y, z;
+        decode_mi(k, x, y, z);
+        idx3[x][y][z] = (short)k;
+        kk[k][0] = (signed char)x;
+        kk[k][1] = (signed char)y;
+        kk[k][2] = (signed char)z;
+    }
+    for (int q = tid; q < (P + 1) * (P + 1); q += blockDim.x) {
+        const int n = q / (P + 1), m = q - n * (P + 1);
+        binom[n][m] = (real)kBinom[n][m];
+    }
+    for (int q = tid; q < nc * 2 * T; q += blockDim.x) {
+        const int ci = q / (2 * T), k = q - ci * 2 * T;
+        bufA[ci][k] = mom[(int64_t)(fc + ci) * 2 * T + k];
+    }
+    if (tid < 3 * nc) {
+        const int ci = tid / 3, ax = tid - 3 * ci;
+        const real d = (real)(a.ncenter[3 * nd + ax] - a.ncenter[3 * (fc + ci) + ax]);
+        real v = 1;
+        for (int m = 0; m <= P; ++m) {
+            cd[ci][ax][m] = v;
+            v *= d;
         }
-        __syncthreads();
-        if (!last) break;
-        __threadfence();
-        nd = par;
-        real accL = 0, accY = 0;
-        const int fc = a.child[nd], nc = a.nchild[nd];
-        for (int ci = 0; ci < nc; ++ci) {
-            const int ch = fc + ci;
-            __syncthreads();
-            if (tid < 3) {
-                const real d = (real)(a.ncenter[3 * nd + tid] - a.ncenter[3 * ch + tid]);
-                real v = 1;
-                for (int m = 0; m <= P; ++m) {
-                    dp[tid][m] = v;
-                    v *= d;
-                }
+    }
+    __syncthreads();
+    // three passes, alternating the two buffers: x (A->B), y (B->A), z (A->B)
+#pragma unroll 1
+    for (int ax = 0; ax < 3; ++ax) {
+        real(*src)[2 * T] = (ax == 1) ? bufB : bufA;
+        real(*dst)[2 * T] = (ax == 1) ? bufA : bufB;
+        for (int it = tid; it < nc * T; it += blockDim.x) {
+            const int ci = it / T, k = it - ci * T;
+            const int k0 = kk[k][0], k1 = kk[k][1], k2 = kk[k][2];
+            const int ka = kk[k][ax];
+            real sL = 0, sY = 0;
+            for (int j = 0; j <= ka; ++j) {
+                const int jx = ax == 0 ? j : k0, jy = ax == 1 ? j : k1, jz = ax == 2 ? j : k2;
+                const int jj = idx3[jx][jy][jz];
+                const real coef = binom[ka][j] * cd[ci][ax][ka - j];
+                sL += coef * src[ci][jj];
+                sY += coef * src[ci][T + jj];
             }
-            __syncthreads();
-            if (tid < T) {
-                const volatile real* mc = mom + (int64_t)ch * 2 * T;
-                real bx = 1;
-                for (int jx = 0; jx <= kx; ++jx) {
-                    real by = 1;
-                    for (int jy = 0; jy <= ky; ++jy) {
-                        real bz = 1;
-                        for (int jz = 0; jz <= kz; ++jz) {
-                            const int j = idx3[jx][jy][jz];
-                            const real coef = bx * by * bz * dp[0][kx - jx] * dp[1][ky - jy] * dp[2][kz - jz];
-                            accL += coef * mc[j];
-                            accY += coef * mc[T + j];
-                            bz = bz * real(kz - jz) / real(jz + 1);
-                        }
-                        by = by * real(ky - jy) / real(jy + 1);
-                    }
-                    bx = bx * real(kx - jx) / real(jx + 1);
-                }
-            }
+            dst[ci][k] = sL;
+            dst[ci][T + k] = sY;
         }
-        if (tid < T) {
-            mom[(int64_t)nd * 2 * T + tid] = accL;
-            mom[(int64_t)nd * 2 * T + T + tid] = accY;
-        }
+        __syncthreads();
+    }
+    for (int k = tid; k < 2 * T; k += blockDim.x) {
+        real acc = 0;
+        for (int ci = 0; ci < nc; ++ci) acc += bufB[ci][k];
+        mom[nd * 2 * T + k] = acc;
     }
 }
 

@@ -5,14 +5,25 @@
 namespace pgb {
 
 template <typename real, int P>
-static void launch_p(int stage, const UpArgs& up, const EvalArgs& ev, const void* src, const void* xrel, void* mom,
-                     cudaStream_t s) {
+static void launch_p(int stage, const UpArgs& up, const std::vector<int64_t>& up_levels, const EvalArgs& ev,
+                     const void* src, const void* xrel, void* mom, cudaStream_t s) {
     using v4 = typename V4<real>::t;
-    if (stage == PGB_STAGE_UPWARD && up.n_leaves > 0)
-        k_upward<real, P><<<(unsigned)up.n_leaves, 128, 0, s>>>(up, (const v4*)src, (real*)mom);
-    if (stage == PGB_STAGE_EVAL && ev.n_groups > 0)
-        k_eval<real, P><<<(unsigned)((ev.n_groups + 3) / 4), 128, 0, s>>>(ev, (const v4*)src, (const v4*)xrel,
-                                                                         (const real*)mom);
+    if (stage == PGB_STAGE_UPWARD && up.n_leaves > 0) {
+        k_p2m_leaves<real, P><<<(unsigned)up.n_leaves, 128, 0, s>>>(up, (const v4*)src, (real*)mom);
+        // inner nodes level by level, deepest first
+        for (int l = (int)up_levels.size() - 3; l >= 0; --l) {  // the deepest level holds only leaves
+            UpArgs u = up;
+            u.lvl_begin = up_levels[l];
+            u.lvl_end = up_levels[l + 1];
+            if (u.lvl_end > u.lvl_begin)
+                k_m2m_level<real, P><<<(unsigned)(u.lvl_end - u.lvl_begin), 256, 0, s>>>(u, (real*)mom);
+        }
+    }
+    constexpr int NW = 8;
+    if (stage == PGB_STAGE_P2P && ev.n_groups > 0)
+        k_p2p<real, 8><<<(unsigned)ev.n_groups, 8 * 32, 0, s>>>(ev, (const v4*)src, (const v4*)xrel);
+    if (stage == PGB_STAGE_M2P && ev.n_groups > 0)
+        k_m2p<real, P, NW><<<(unsigned)ev.n_groups, NW * 32, 0, s>>>(ev, (const v4*)xrel, (const real*)mom);
 }
 
 }  // namespace pgb
