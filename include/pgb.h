@@ -45,9 +45,11 @@ extern "C" {
 #define PGB_SET_POTENTIAL 2
 
 /* precisions / solve modes */
-#define PGB_FP32 0          /* P2P/M2P/P2M in FP32 with compensated accumulation */
+#define PGB_FP32 0          /* matvec: P2P/M2P/P2M in FP32 with compensated accumulation;
+                               solve: FP32 operator throughout (right-hand side included),
+                               FP64 Arnoldi/Givens, no FP64 matvec */
 #define PGB_FP64 1          /* every treecode kernel in FP64 */
-#define PGB_FP32_REFINE 2   /* solve: FP32 inner GMRES, FP64 outer residual */
+#define PGB_FP32_REFINE 2   /* solve: FP32 inner GMRES, FP64 right-hand side and outer residual */
 
 /* Numerical parameters: the seven columns of the paper's parameter tables
  * (Tables 1, 2, 4: Gauss points in-element per edge, close-by, far-away;
@@ -159,12 +161,24 @@ int pgb_matvec(struct pgb_ctx* ctx, const void* x, void* y, int32_t precision);
  * imposed-boundary terms moved to the right) into device doubles b. */
 int pgb_rhs(struct pgb_ctx* ctx, double* b);
 
-/* GMRES solve of Eq. 6 / Eq. 7 (Section 3.2).  mode PGB_FP64 or
- * PGB_FP32_REFINE; tol on ||b - A x||/||b||; max_iter total inner iterations;
+/* GMRES solve of Eq. 6 / Eq. 7 (Section 3.2).  mode PGB_FP64, PGB_FP32_REFINE
+ * or PGB_FP32; tol on ||b - A x||/||b|| (measured with the FP64 operator,
+ * except in PGB_FP32 mode where the FP32 operator is used); max_iter total inner iterations;
  * restart = Krylov dimension (1..256).  x_out: device doubles, n_unknowns.
  * Returns PGB_ENOCONV (x_out and stats still written) when tol is not met. */
 int pgb_solve(struct pgb_ctx* ctx, int32_t mode, double tol, int32_t max_iter, int32_t restart,
               double* x_out, pgb_solve_stats* stats);
+
+/* Rigid-pose sweep (the orientation studies of Section 1): for each of B
+ * poses (R: B x 9 row-major, t: B x 3) of body body_id, set the pose,
+ * rebuild what the pose changes (world geometry, lists, cross-body near-field
+ * entries; each body's own near-field entries and tree are reused), solve
+ * (mode, tol, max_iter, restart as pgb_solve) and evaluate the energies:
+ * F_out[4b..4b+3] = Coulomb, solvation, surface, total (kcal/mol); stats may be
+ * NULL or hold B entries.  The body keeps the last pose.  Returns PGB_ENOCONV
+ * if any pose missed tol (all poses are still written). */
+int pgb_solve_batch(struct pgb_ctx* ctx, int32_t body_id, const double* R, const double* t, int64_t B, int32_t mode,
+                    double tol, int32_t max_iter, int32_t restart, double* F_out, pgb_solve_stats* stats);
 
 /* Energies (Section 3.3, Eq. 11-16) of a solution x (device doubles):
  * Coulomb, solvation (phi_reac of Eq. 13 at the charges with the three-tier

@@ -71,6 +71,7 @@ _SIGS = {
     "pgb_rhs": (c_i32, [c_vp, c_vp]),
     "pgb_solve": (c_i32, [c_vp, c_i32, c_dbl, c_i32, c_i32, c_vp, ctypes.POINTER(pgb_solve_stats)]),
     "pgb_energy": (c_i32, [c_vp, c_vp, ctypes.POINTER(pgb_energies), c_vp]),
+    "pgb_solve_batch": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_i64, c_i32, c_dbl, c_i32, c_i32, c_vp, c_vp]),
     "pgb_tree_export": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "pgb_timing": (c_i32, [c_vp, c_i32, ctypes.POINTER(pgb_stage_times)]),
     "pgb_energy_noalloc": (c_i32, [c_vp, c_vp, ctypes.POINTER(pgb_energies)]),
@@ -199,6 +200,21 @@ def pgb_solve(ctx, mode, tol, max_iter, restart, x_out):
                                        _dptr(x_out, "float64", pgb_num_unknowns(ctx)), ctypes.byref(st)),
                   allow=(PGB_ENOCONV,))
     return code, {n: getattr(st, n) for n, _ in pgb_solve_stats._fields_}
+
+
+def pgb_solve_batch(ctx, body_id, R, t, mode, tol, max_iter, restart):
+    """R: (B,3,3), t: (B,3) host arrays.  Returns (status, F (B,4) numpy
+    [coulomb, solvation, surface, total], list of stats dicts)."""
+    R_, Rp = _hptr(np.asarray(R).reshape(-1, 9), np.float64)
+    t_, tp = _hptr(np.asarray(t).reshape(-1, 3), np.float64)
+    B = R_.shape[0]
+    if t_.shape[0] != B:
+        raise ValueError("R and t batch sizes differ")
+    F = np.zeros((B, 4))
+    st = (pgb_solve_stats * max(1, B))()
+    code = _check(ctx, lib().pgb_solve_batch(ctx, body_id, Rp, tp, B, mode, tol, max_iter, restart,
+                                             F.ctypes.data_as(c_vp), st), allow=(PGB_ENOCONV,))
+    return code, F, [{n: getattr(s, n) for n, _ in pgb_solve_stats._fields_} for s in st[:B]]
 
 
 def pgb_energy(ctx, x, n_bodies=None):

@@ -192,6 +192,7 @@ int pgb_mesh_load(pgb_ctx* c, int32_t kind, const double* verts, int64_t nv, con
         c->bodies.push_back(std::move(b));
         c->tree_valid = false;
         c->order_valid = false;
+        c->intra_valid = false;
         if (body_id_out) *body_id_out = (int32_t)c->bodies.size() - 1;
         return PGB_OK;
     });
@@ -203,6 +204,7 @@ int pgb_set_solvent(pgb_ctx* c, double eps_out, double kappa) {
         c->err = "eps_out must be > 0 and kappa >= 0";
         return PGB_EINVAL;
     }
+    if (kappa != c->kappa) c->intra_valid = false;
     c->eps_out = eps_out;
     c->kappa = kappa;
     c->tree_valid = false;
@@ -244,6 +246,7 @@ int pgb_tree_build(pgb_ctx* c) {
         if (!c->order_valid) {
             upload_bodies(c);
             build_order(c);
+            c->intra_valid = false;
         }
         build_geometry(c);
         build_lists(c);
@@ -270,7 +273,7 @@ int pgb_tree_stats(pgb_ctx* c, pgb_tree_info* info) {
     info->p2p_laplace_pairs = c->p2p_lap;
     info->m2p_pairs = c->m2p_pairs;
     info->m2p_laplace_pairs = c->m2p_lap;
-    info->n_corrections = c->n_corr;
+    info->n_corrections = c->n_corr + c->n_xcorr;
     return PGB_OK;
 }
 
@@ -307,7 +310,7 @@ int pgb_rhs(pgb_ctx* c, double* b) {
     return guard(c, [&]() -> int {
         if (!b) fail(PGB_EINVAL, "null vector");
         if (!c->tree_valid) fail(PGB_ESTATE, "pgb_tree_build has not run");
-        build_rhs(c, b);
+        build_rhs(c, b, PGB_FP64);
         return PGB_OK;
     });
 }
@@ -324,6 +327,51 @@ int pgb_solve(pgb_ctx* c, int32_t mode, double tol, int32_t max_iter, int32_t re
         PGB_CUDA(cudaStreamSynchronize(c->stream));
         if (r == PGB_ENOCONV) c->err = "GMRES did not reach tol";
         return r;
+    });
+}
+
+int pgb_solve_batch(pgb_ctx* c, int32_t body_id, const double* R, const double* t, int64_t B, int32_t mode, double tol,
+                    int32_t max_iter, int32_t restart, double* F_out, pgb_solve_stats* stats) {
+    if (!c) return PGB_EINVAL;
+    return guard(c, [&]() -> int {
+        if (!R || !t || !F_out || B < 0) fail(PGB_EINVAL, "null argument or negative batch");
+        if (body_id < 0 || body_id >= (int32_t)c->bodies.size()) fail(PGB_EINVAL, "bad body id");
+        if (!(tol > 0 && tol < 1)) fail(PGB_EINVAL, "tol must be in (0, 1)");
+        if (max_iter < 1 || restart < 1 || restart > 256) fail(PGB_EINVAL, "max_iter >= 1 and restart in 1..256");
+        int first_err = PGB_OK;
+        for (int64_t b = 0; b < B; ++b) {
+            int r = pgb_set_pose(c, body_id, R + 9 * b, t + 3 * b);
+            if (r != PGB_OK) fail(r, "pose " + std::to_string(b) + ": " + c->err);
+            {
+                StageTimer tm(c, PGB_STAGE_TREE);
+                if (!c->order_valid) {
+                    upload_bodies(c);
+                    build_order(c);
+                    c->intra_valid = false;
+                }
+                build_geometry(c);
+                build_lists(c);
+                build_corrections(c);  // intra-body entries are reused across poses
+                c->tree_valid = true;
+            }
+            c->d_xbatch.resize(c->n_unk);
+            pgb_solve_stats st{};
+            int rs = solve(c, mode, tol, max_iter, restart, c->d_xbatch, &st);
+            if (rs != PGB_OK && first_err == PGB_OK) first_err = rs;
+            pgb_energies e{};
+            {
+                StageTimer tm(c, PGB_STAGE_ENERGY);
+                energies(c, c->d_xbatch, &e, nullptr);
+            }
+            F_out[4 * b] = e.coulomb;
+            F_out[4 * b + 1] = e.solvation;
+            F_out[4 * b + 2] = e.surface;
+            F_out[4 * b + 3] = e.total;
+            if (stats) stats[b] = st;
+        }
+        PGB_CUDA(cudaStreamSynchronize(c->stream));
+        if (first_err == PGB_ENOCONV) c->err = "GMRES did not reach tol for at least one pose";
+        return first_err;
     });
 }
 

@@ -70,7 +70,9 @@ __global__ void k_src_prep(Geo g, BodyDev bd, const double* __restrict__ x, bool
 // boundary terms, -(U + jump) on exterior and surface rows.
 __global__ void k_assemble(Geo g, BodyDev bd, const double* __restrict__ U, const double* __restrict__ dens,
                            const int64_t* __restrict__ coff, const int32_t* __restrict__ cj,
-                           const dbl4* __restrict__ cval, int mode, double* __restrict__ y) {
+                           const dbl4* __restrict__ cval, const int64_t* __restrict__ xoff,
+                           const int32_t* __restrict__ xj, const dbl4* __restrict__ xval, int mode,
+                           double* __restrict__ y) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= g.n_pan) return;
     const double inv4pi = 1.0 / PGB_FOUR_PI;
@@ -81,6 +83,11 @@ __global__ void k_assemble(Geo g, BodyDev bd, const double* __restrict__ U, cons
         const double psiL = dens[3 * j], psiY = dens[3 * j + 1], phi = dens[3 * j + 2];
         UL += d.x * psiL - d.y * phi;
         UY += d.z * psiY - d.w * phi;
+    }
+    for (int64_t e = xoff[i]; e < xoff[i + 1]; ++e) {  // cross-body entries (Yukawa only)
+        const int64_t j = xj[e];
+        const dbl4 d = xval[e];
+        UY += d.z * dens[3 * j + 1] - d.w * dens[3 * j + 2];
     }
     const int b = g.pbody[i];
     const int64_t loc = g.perm[i] - bd.pan_off[b];
@@ -182,7 +189,8 @@ void apply_operator(pgb_ctx* c, const double* x, double* y, int precision, bool 
     {
         StageTimer tm(c, PGB_STAGE_ASSEMBLE + (f32 ? 0 : PGB_STAGE_FP64));
         k_assemble<<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, c->d_U, c->d_dens, c->d_corr_off, c->d_corr_j,
-                                                       c->d_corr_val, known_only ? 1 : 0, y);
+                                                       c->d_corr_val, c->d_xcorr_off, c->d_xcorr_j, c->d_xcorr_val,
+                                                       known_only ? 1 : 0, y);
         PGB_CUDA(cudaGetLastError());
         PGB_LAUNCHED(c, 1);
     }

@@ -158,10 +158,14 @@ struct pgb_ctx {
     pgb::DBuf<float4> d_tile_d;
     pgb::DBuf<int4> d_tile_m;
     // near-field corrections (CSR over sorted targets)
-    int64_t n_corr = 0;
-    pgb::DBuf<int64_t> d_corr_off;
-    pgb::DBuf<int32_t> d_corr_j;
-    pgb::DBuf<pgb::dbl4> d_corr_val;       // dVL, dKL, dVY, dKY
+    // intra-body entries depend only on each body's own geometry and kappa, so
+    // they survive pose changes; cross-body entries are rebuilt per pose
+    bool intra_valid = false;
+    int64_t n_corr = 0, n_xcorr = 0;
+    pgb::DBuf<int64_t> d_corr_off, d_xcorr_off;
+    pgb::DBuf<int32_t> d_corr_j, d_xcorr_j;
+    pgb::DBuf<pgb::dbl4> d_corr_val, d_xcorr_val;  // dVL, dKL, dVY, dKY
+    pgb::DBuf<double> d_xbatch;            // solution buffer of pgb_solve_batch
 
     // matvec work buffers
     pgb::DBuf<float4> d_src32;           // 2 per point
@@ -215,7 +219,7 @@ void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t
 // matvec (matvec.cu)
 void apply_operator(pgb_ctx* c, const double* x, double* y, int precision, bool known_only);
 // solver (solver.cu)
-void build_rhs(pgb_ctx* c, double* b);
+void build_rhs(pgb_ctx* c, double* b, int precision);
 int solve(pgb_ctx* c, int mode, double tol, int max_iter, int restart, double* x, pgb_solve_stats* st);
 // energy (energy.cu)
 void energies(pgb_ctx* c, const double* x, pgb_energies* e, pgb_energies* per_body);

@@ -999,14 +999,18 @@ struct CorrArgs {
     int n_bodies;
 };
 
-// candidates j of target i: |c_i - c_j|^2 < 8 A_j (|x - c_j| < 2 L_j), or j == i
-__global__ void k_corr_find(CorrArgs a, int64_t n, bool fill, int64_t* cnt, const int64_t* off, int32_t* cj) {
+// candidates j of target i: |c_i - c_j|^2 < 8 A_j (|x - c_j| < 2 L_j), or j == i;
+// cross == false: sources of the target's own body, true: of the other bodies
+__global__ void k_corr_find(CorrArgs a, int64_t n, bool fill, bool cross, const int32_t* pbody, int64_t* cnt,
+                            const int64_t* off, int32_t* cj) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     double x[3] = {a.C[3 * i], a.C[3 * i + 1], a.C[3 * i + 2]};
     int32_t stack[PGB_LIST_STACK];
     int64_t k = 0, w = fill ? off[i] : 0;
+    const int ib = pbody[i];
     for (int b = 0; b < a.n_bodies; ++b) {
+        if ((b != ib) != cross) continue;
         int sp = 0;
         stack[sp++] = b;
         while (sp > 0) {
@@ -1127,7 +1131,8 @@ BodyDev body_dev(const pgb_ctx* c) {
     return b;
 }
 
-void build_corrections(pgb_ctx* c) {
+static void build_corr_part(pgb_ctx* c, bool cross, DBuf<int64_t>& off, DBuf<int32_t>& cj, DBuf<dbl4>& val,
+                            int64_t& count) {
     cudaStream_t s = c->stream;
     int64_t n = c->n_pan;
     CorrArgs a;
@@ -1136,21 +1141,32 @@ void build_corrections(pgb_ctx* c) {
     a.n_bodies = (int)c->bodies.size();
     DBuf<int64_t> cnt;
     cnt.resize(n);
-    c->d_corr_off.resize(n + 1);
-    k_corr_find<<<nblk(n, 64), 64, 0, s>>>(a, n, false, cnt, nullptr, nullptr);
+    off.resize(n + 1);
+    k_corr_find<<<nblk(n, 64), 64, 0, s>>>(a, n, false, cross, c->d_pbody, cnt, nullptr, nullptr);
     PGB_CUDA(cudaGetLastError());
     int64_t tot = 0;
-    exclusive_scan_i64(cnt, c->d_corr_off, n, s, &tot);
-    PGB_CUDA(cudaMemcpyAsync(c->d_corr_off.p + n, &tot, 8, cudaMemcpyHostToDevice, s));
-    c->n_corr = tot;
-    c->d_corr_j.resize(tot);
-    c->d_corr_val.resize(tot);
-    k_corr_find<<<nblk(n, 64), 64, 0, s>>>(a, n, true, nullptr, c->d_corr_off, c->d_corr_j);
-    Rules r = make_rules(c->p.K, c->p.K_near, c->p.n_edge);
-    k_corr_values<<<(int)n, 32, 0, s>>>(n, c->d_corr_off, c->d_corr_j, c->d_v, c->d_c, c->d_n, c->d_A, c->d_y, c->d_w,
-                                        c->d_pbody, body_dev(c), r, c->kappa, c->d_corr_val);
+    exclusive_scan_i64(cnt, off, n, s, &tot);
+    PGB_CUDA(cudaMemcpyAsync(off.p + n, &tot, 8, cudaMemcpyHostToDevice, s));
+    count = tot;
+    cj.resize(tot);
+    val.resize(tot);
+    if (tot) {
+        k_corr_find<<<nblk(n, 64), 64, 0, s>>>(a, n, true, cross, c->d_pbody, nullptr, off, cj);
+        Rules r = make_rules(c->p.K, c->p.K_near, c->p.n_edge);
+        k_corr_values<<<(int)n, 32, 0, s>>>(n, off, cj, c->d_v, c->d_c, c->d_n, c->d_A, c->d_y, c->d_w, c->d_pbody,
+                                            body_dev(c), r, c->kappa, val);
+    }
     PGB_CUDA(cudaGetLastError());
     PGB_CUDA(cudaStreamSynchronize(s));
+    PGB_LAUNCHED(c, tot ? 4 : 2);
+}
+
+void build_corrections(pgb_ctx* c) {
+    if (!c->intra_valid) {
+        build_corr_part(c, false, c->d_corr_off, c->d_corr_j, c->d_corr_val, c->n_corr);
+        c->intra_valid = true;
+    }
+    build_corr_part(c, true, c->d_xcorr_off, c->d_xcorr_j, c->d_xcorr_val, c->n_xcorr);
 }
 
 Geo geo(const pgb_ctx* c) {
