@@ -169,6 +169,25 @@ int pgb_rhs(struct pgb_ctx* ctx, double* b);
 int pgb_solve(struct pgb_ctx* ctx, int32_t mode, double tol, int32_t max_iter, int32_t restart,
               double* x_out, pgb_solve_stats* stats);
 
+/* Gradients of the total free energy (Eq. 16) of the solved system by the
+ * discrete adjoint (the paper has no gradient; this is the adjoint of
+ * Eq. 6 / Eq. 7): solves A^T lam = dF/dx with the transposed treecode
+ * (GMRES, FP64 Arnoldi; operator in `precision` = PGB_FP32 or PGB_FP64, tol
+ * relative to ||dF/dx||), then
+ *   dF_dq[n_q]      dF/dq_k for every charge (kcal/mol/e), bodies in load order;
+ *   dF_dbc[n_bodies] dF/dsigma0 (kcal/mol per C/m^2) or dF/dphi0 (per V) for
+ *                   surfaces, 0 for molecules;
+ *   dF_dt[3 n_bodies] dF/dt for a rigid translation of each body (kcal/mol/A).
+ * x: the solution of pgb_solve (device doubles).  Host output pointers may be
+ * NULL.  Needs P <= 7 and the bodies farther apart than 2L (no cross-body
+ * near-field entries), else PGB_EINVAL.  adj (may be NULL) receives the
+ * adjoint iterations and the relative residual of A^T lam = dF/dx. */
+int pgb_grad(struct pgb_ctx* ctx, const double* x, int32_t precision, double tol, int32_t max_iter, int32_t restart,
+             double* dF_dq, double* dF_dbc, double* dF_dt, pgb_solve_stats* adj);
+
+/* y = A^T lam, the transposed operator (device doubles, n_unknowns each). */
+int pgb_matvec_transpose(struct pgb_ctx* ctx, const double* lam, double* y, int32_t precision);
+
 /* Rigid-pose sweep (the orientation studies of Section 1): for each of B
  * poses (R: B x 9 row-major, t: B x 3) of body body_id, set the pose,
  * rebuild what the pose changes (world geometry, lists, cross-body near-field

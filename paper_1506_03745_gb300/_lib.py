@@ -72,6 +72,8 @@ _SIGS = {
     "pgb_solve": (c_i32, [c_vp, c_i32, c_dbl, c_i32, c_i32, c_vp, ctypes.POINTER(pgb_solve_stats)]),
     "pgb_energy": (c_i32, [c_vp, c_vp, ctypes.POINTER(pgb_energies), c_vp]),
     "pgb_solve_batch": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_i64, c_i32, c_dbl, c_i32, c_i32, c_vp, c_vp]),
+    "pgb_grad": (c_i32, [c_vp, c_vp, c_i32, c_dbl, c_i32, c_i32, c_vp, c_vp, c_vp, ctypes.POINTER(pgb_solve_stats)]),
+    "pgb_matvec_transpose": (c_i32, [c_vp, c_vp, c_vp, c_i32]),
     "pgb_tree_export": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "pgb_timing": (c_i32, [c_vp, c_i32, ctypes.POINTER(pgb_stage_times)]),
     "pgb_energy_noalloc": (c_i32, [c_vp, c_vp, ctypes.POINTER(pgb_energies)]),
@@ -215,6 +217,24 @@ def pgb_solve_batch(ctx, body_id, R, t, mode, tol, max_iter, restart):
     code = _check(ctx, lib().pgb_solve_batch(ctx, body_id, Rp, tp, B, mode, tol, max_iter, restart,
                                              F.ctypes.data_as(c_vp), st), allow=(PGB_ENOCONV,))
     return code, F, [{n: getattr(s, n) for n, _ in pgb_solve_stats._fields_} for s in st[:B]]
+
+
+def pgb_grad(ctx, x, n_charges, n_bodies, precision=PGB_FP32, tol=1e-8, max_iter=1000, restart=100):
+    """Adjoint gradients: returns (status, dF_dq (n_charges,), dF_dbc (n_bodies,),
+    dF_dt (n_bodies, 3), adjoint stats)."""
+    dq = np.zeros(max(1, n_charges))
+    dbc = np.zeros(max(1, n_bodies))
+    dt = np.zeros((max(1, n_bodies), 3))
+    st = pgb_solve_stats()
+    code = _check(ctx, lib().pgb_grad(ctx, _dptr(x, "float64", pgb_num_unknowns(ctx)), precision, tol, max_iter,
+                                      restart, dq.ctypes.data_as(c_vp), dbc.ctypes.data_as(c_vp),
+                                      dt.ctypes.data_as(c_vp), ctypes.byref(st)), allow=(PGB_ENOCONV,))
+    return code, dq[:n_charges], dbc[:n_bodies], dt[:n_bodies], {n: getattr(st, n) for n, _ in pgb_solve_stats._fields_}
+
+
+def pgb_matvec_transpose(ctx, lam, y, precision):
+    n = pgb_num_unknowns(ctx)
+    return _check(ctx, lib().pgb_matvec_transpose(ctx, _dptr(lam, "float64", n), _dptr(y, "float64", n), precision))
 
 
 def pgb_energy(ctx, x, n_bodies=None):

@@ -375,6 +375,36 @@ int pgb_solve_batch(pgb_ctx* c, int32_t body_id, const double* R, const double* 
     });
 }
 
+int pgb_grad(pgb_ctx* c, const double* x, int32_t precision, double tol, int32_t max_iter, int32_t restart,
+             double* dq, double* dbc, double* dt, pgb_solve_stats* adj) {
+    if (!c) return PGB_EINVAL;
+    return guard(c, [&]() -> int {
+        if (!x) fail(PGB_EINVAL, "null x");
+        if (!(tol > 0 && tol < 1)) fail(PGB_EINVAL, "tol must be in (0, 1)");
+        if (max_iter < 1 || restart < 1 || restart > 256) fail(PGB_EINVAL, "max_iter >= 1 and restart in 1..256");
+        pgb_solve_stats st{};
+        grad(c, x, precision, tol, max_iter, restart, dq, dbc, dt, &st);
+        if (adj) *adj = st;
+        if (st.rel_residual > tol) {
+            c->err = "adjoint GMRES did not reach tol";
+            return PGB_ENOCONV;
+        }
+        return PGB_OK;
+    });
+}
+
+int pgb_matvec_transpose(pgb_ctx* c, const double* lam, double* y, int32_t precision) {
+    if (!c) return PGB_EINVAL;
+    return guard(c, [&]() -> int {
+        if (!lam || !y) fail(PGB_EINVAL, "null vector");
+        if (precision != PGB_FP32 && precision != PGB_FP64) fail(PGB_EINVAL, "precision must be PGB_FP32 or PGB_FP64");
+        if (c->p.P > 7) fail(PGB_EINVAL, "the adjoint supports P <= 7");
+        apply_transpose(c, lam, y, precision);
+        PGB_CUDA(cudaGetLastError());
+        return PGB_OK;
+    });
+}
+
 int pgb_energy(pgb_ctx* c, const double* x, pgb_energies* e, pgb_energies* per_body) {
     if (!c) return PGB_EINVAL;
     return guard(c, [&]() -> int {

@@ -89,7 +89,7 @@ __global__ void k_body_sums(Geo g, BodyDev bd, const double* qxyz, const double*
 }
 
 // e^2/(eps0 Angstrom) in kcal/mol from CODATA 2018
-static double energy_unit_kcal() {
+double energy_unit_kcal() {
     const double e = 1.602176634e-19, eps0 = 8.8541878128e-12, NA = 6.02214076e23;
     return e * e / (eps0 * 1e-10) * NA / 4184.0;
 }
@@ -219,6 +219,15 @@ void energies_noalloc(pgb_ctx* c, const double* x, pgb_energies* e) {
         tot.total += eb.total;
     }
     *e = tot;
+}
+
+// phi_reac (Eq. 13) at every charge into device doubles `out` (n_q entries).
+void phi_reac(pgb_ctx* c, const double* x, double* out) {
+    if (!c->n_q) return;
+    Rules r = make_rules(c->p.K, c->p.K_near, c->p.n_edge);
+    k_phi_reac<<<(unsigned)c->n_q, 128, 0, c->stream>>>(geo(c), body_dev(c), r, c->d_qxyz, c->d_q_body, x, out);
+    PGB_CUDA(cudaGetLastError());
+    PGB_LAUNCHED(c, 1);
 }
 
 }  // namespace pgb

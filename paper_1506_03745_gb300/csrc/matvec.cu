@@ -126,11 +126,14 @@ void convert_f64_f32(const double* a, float* b, int64_t n, cudaStream_t s) {
     k_f64_to_f32<<<nblk(n, 256), 256, 0, s>>>(a, b, n);
 }
 
-void apply_operator(pgb_ctx* c, const double* x, double* y, int precision, bool known_only) {
+void apply_operator(pgb_ctx* c, const double* x, double* y, int precision, bool known_only, const int* known_mask) {
     if (!c->tree_valid) fail(PGB_ESTATE, "pgb_tree_build has not run for the current bodies and poses");
     cudaStream_t s = c->stream;
     Geo g = geo(c);
     BodyDev bd = body_dev(c);
+    if (known_only && known_mask)  // imposed terms of the selected surfaces only
+        for (int b = 0; b < bd.n_bodies; ++b)
+            if (!known_mask[b]) bd.bc[b] = 0.0;
     const int P = c->p.P;
     const int T = n_terms(P);
     const int64_t nsrc = g.n_src;
@@ -152,7 +155,8 @@ void apply_operator(pgb_ctx* c, const double* x, double* y, int precision, bool 
     for (size_t b = 0; b < c->bodies.size(); ++b) {
         ev.lap_body[b] = c->bodies[b].kind == PGB_DIELECTRIC;
         // imposed-boundary terms: molecules carry no known density
-        ev.src_active[b] = up.src_active[b] = known_only ? (c->bodies[b].kind != PGB_DIELECTRIC) : 1;
+        ev.src_active[b] = up.src_active[b] =
+            known_only ? (known_mask ? known_mask[b] : (c->bodies[b].kind != PGB_DIELECTRIC)) : 1;
     }
     ev.near4 = c->d_near4;
     ev.far4 = c->d_far4;

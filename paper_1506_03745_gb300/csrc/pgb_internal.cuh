@@ -166,6 +166,21 @@ struct pgb_ctx {
     pgb::DBuf<int32_t> d_corr_j, d_xcorr_j;
     pgb::DBuf<pgb::dbl4> d_corr_val, d_xcorr_val;  // dVL, dKL, dVY, dKY
     pgb::DBuf<double> d_xbatch;            // solution buffer of pgb_solve_batch
+    // adjoint (transposed treecode): built on first use after each tree build
+    bool adj_valid = false;
+    std::vector<int64_t> group_begin;      // first group of each body (+ total)
+    pgb::DBuf<float4> d_yT32, d_n32, d_cT32;
+    pgb::DBuf<pgb::dbl4> d_yT64, d_n64, d_cT64;
+    pgb::DBuf<double> d_rT2, d_gTlo, d_gThi;
+    int64_t n_Tnear = 0, n_Tfar = 0;
+    pgb::DBuf<int64_t> d_Tnear_off, d_Tfar_off, d_ct_off;
+    pgb::DBuf<int32_t> d_Tnear, d_Tfar, d_ct_i;
+    pgb::DBuf<float4> d_Tnear4, d_Tfar4;
+    pgb::DBuf<pgb::dbl4> d_ct_val;
+    pgb::DBuf<float4> d_srcT32;
+    pgb::DBuf<pgb::dbl4> d_srcT64;
+    pgb::DBuf<float> d_momT32;
+    pgb::DBuf<double> d_momT64, d_Tout, d_sT, d_lam, d_gx, d_bu;
 
     // matvec work buffers
     pgb::DBuf<float4> d_src32;           // 2 per point
@@ -211,13 +226,25 @@ void upload_bodies(pgb_ctx* c);
 void build_order(pgb_ctx* c);
 void build_geometry(pgb_ctx* c);
 void build_lists(pgb_ctx* c);
+void make_lists(pgb_ctx* c, const double* r2, const double* glo, const double* ghi, DBuf<int64_t>& noff,
+                DBuf<int32_t>& nearl, DBuf<int64_t>& foff, DBuf<int32_t>& farl, DBuf<float4>& near4,
+                DBuf<float4>& far4, int64_t& n_near, int64_t& n_far, unsigned long long* stats4);
 void build_corrections(pgb_ctx* c);
 BodyDev body_dev(const pgb_ctx* c);
 Geo geo(const pgb_ctx* c);
 // scans (tree.cu)
 void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s, int64_t* total_host);
 // matvec (matvec.cu)
-void apply_operator(pgb_ctx* c, const double* x, double* y, int precision, bool known_only);
+void apply_operator(pgb_ctx* c, const double* x, double* y, int precision, bool known_only,
+                    const int* known_mask = nullptr);
+void apply_transpose(pgb_ctx* c, const double* lam, double* y, int precision);
+void grad(pgb_ctx* c, const double* x, int precision, double tol, int max_iter, int restart, double* dq, double* dbc,
+          double* dt, pgb_solve_stats* st);
+int gmres_op(pgb_ctx* c, int prec, bool transpose, const double* b, double* x, double abs_tol, int max_it,
+             int restart, int* matvecs, double* est_out, bool x_zero);
+double vec_dot(pgb_ctx* c, const double* a, const double* b);
+double energy_unit_kcal();
+void phi_reac(pgb_ctx* c, const double* x, double* out);
 // solver (solver.cu)
 void build_rhs(pgb_ctx* c, double* b, int precision);
 int solve(pgb_ctx* c, int mode, double tol, int max_iter, int restart, double* x, pgb_solve_stats* st);

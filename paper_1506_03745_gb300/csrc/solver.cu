@@ -170,8 +170,12 @@ struct Krylov {
 // Restarted GMRES on A x = b from the given x; precision of the operator
 // `prec`; stops when the (estimated) residual <= abs_tol or after max_it
 // iterations.  Returns iterations done; *matvecs counts operator uses.
-static int gmres(pgb_ctx* c, int prec, const double* b, double* x, double abs_tol, int max_it, int restart,
-                 int* matvecs, double* est_out, bool x_zero) {
+int gmres_op(pgb_ctx* c, int prec, bool transpose, const double* b, double* x, double abs_tol, int max_it,
+             int restart, int* matvecs, double* est_out, bool x_zero) {
+    auto apply = [&](const double* in, double* out) {
+        if (transpose) apply_transpose(c, in, out, prec);
+        else apply_operator(c, in, out, prec, false);
+    };
     const int64_t n = c->n_unk;
     const int m = restart;
     cudaStream_t s = c->stream;
@@ -197,7 +201,7 @@ static int gmres(pgb_ctx* c, int prec, const double* b, double* x, double abs_to
             PGB_CUDA(cudaMemcpyAsync(c->d_wk.p, b, 8 * n, cudaMemcpyDeviceToDevice, s));
             x_zero = false;
         } else {
-            apply_operator(c, x, c->d_wk, prec, false);
+            apply(x, c->d_wk);
             ++*matvecs;
             k_axpby<<<nblk(n, 256), 256, 0, s>>>(1.0, b, -1.0, c->d_wk, c->d_wk, n);
         }
@@ -212,7 +216,7 @@ static int gmres(pgb_ctx* c, int prec, const double* b, double* x, double abs_to
         for (; j < m && it < max_it; ++j, ++it) {
             double* vj = c->d_V.p + (size_t)j * n;
             double* w = c->d_wk.p;
-            apply_operator(c, vj, w, prec, false);
+            apply(vj, w);
             ++*matvecs;
             double* h = c->d_H.p + (size_t)j * (m + 1);
             {
@@ -247,6 +251,22 @@ static int gmres(pgb_ctx* c, int prec, const double* b, double* x, double abs_to
     }
     if (est_out) *est_out = est;
     return it;
+}
+
+static int gmres(pgb_ctx* c, int prec, const double* b, double* x, double abs_tol, int max_it, int restart,
+                 int* matvecs, double* est_out, bool x_zero) {
+    return gmres_op(c, prec, false, b, x, abs_tol, max_it, restart, matvecs, est_out, x_zero);
+}
+
+double vec_dot(pgb_ctx* c, const double* a, const double* b) {
+    PGB_LAUNCHED(c, 2);
+    Krylov K{c, c->n_unk, 0, c->stream};
+    DBuf<double> t;
+    t.resize(1);
+    c->d_red.resize(std::max<size_t>(c->d_red.n, DOT_BLOCKS));
+    k_multi_dot<<<DOT_BLOCKS, DOT_THREADS, 0, c->stream>>>(a, c->n_unk, 1, b, c->n_unk, c->d_red);
+    k_reduce_partials<<<1, 256, 0, c->stream>>>(c->d_red, DOT_BLOCKS, t, 0, 0);
+    return K.host_read(t);
 }
 
 static double vec_norm(pgb_ctx* c, const double* v) {

@@ -777,6 +777,11 @@ void build_geometry(pgb_ctx* c) {
     }
     int64_t ng = (int64_t)gs.size();
     c->n_groups = ng;
+    c->group_begin.assign(c->bodies.size() + 1, 0);
+    for (int64_t k = 0; k < ng; ++k) c->group_begin[gb[k] + 1] = k + 1;
+    for (size_t b = 1; b <= c->bodies.size(); ++b)
+        c->group_begin[b] = std::max(c->group_begin[b], c->group_begin[b - 1]);
+    c->adj_valid = false;
     c->d_group_start.resize(ng); c->d_group_end.resize(ng); c->d_group_body.resize(ng);
     c->d_group_lo.resize(3 * ng); c->d_group_hi.resize(3 * ng); c->d_group_center.resize(3 * ng);
     PGB_CUDA(cudaMemcpyAsync(c->d_group_start.p, gs.data(), 4 * ng, cudaMemcpyHostToDevice, s));
@@ -922,13 +927,15 @@ __global__ void k_tile_fill(int64_t ng, const int64_t* noff, const int32_t* near
     }
 }
 
-void build_lists(pgb_ctx* c) {
+void make_lists(pgb_ctx* c, const double* r2, const double* glo, const double* ghi, DBuf<int64_t>& noff,
+                DBuf<int32_t>& nearl, DBuf<int64_t>& foff, DBuf<int32_t>& farl, DBuf<float4>& near4,
+                DBuf<float4>& far4, int64_t& n_near, int64_t& n_far, unsigned long long* stats4) {
     cudaStream_t s = c->stream;
     int64_t ng = c->n_groups;
     ListArgs a;
     a.nchild = c->d_node_nchild; a.child = c->d_node_child; a.nstart = c->d_node_start; a.nend = c->d_node_end;
     a.nbody = c->d_node_body; a.gstart = c->d_group_start; a.gend = c->d_group_end; a.gbody = c->d_group_body;
-    a.center = c->d_node_center; a.r2 = c->d_node_r2; a.glo = c->d_group_lo; a.ghi = c->d_group_hi;
+    a.center = c->d_node_center; a.r2 = r2; a.glo = glo; a.ghi = ghi;
     a.n_bodies = (int)c->bodies.size();
     for (int b = 0; b < a.n_bodies; ++b) a.kind[b] = c->bodies[b].kind;
     a.theta = c->p.theta;
@@ -936,32 +943,48 @@ void build_lists(pgb_ctx* c) {
     a.K = c->p.K;
     DBuf<int64_t> nc, fc;
     nc.resize(ng); fc.resize(ng);
-    c->d_near_off.resize(ng + 1);
-    c->d_far_off.resize(ng + 1);
+    noff.resize(ng + 1);
+    foff.resize(ng + 1);
     DBuf<unsigned long long> st;
     st.resize(5);
     PGB_CUDA(cudaMemsetAsync(st.p, 0, 40, s));
     k_lists<<<nblk(ng, 64), 64, 0, s>>>(a, ng, false, nc, fc, nullptr, nullptr, nullptr, nullptr, st);
     PGB_CUDA(cudaGetLastError());
     int64_t tn = 0, tf = 0;
-    exclusive_scan_i64(nc, c->d_near_off, ng, s, &tn);
-    exclusive_scan_i64(fc, c->d_far_off, ng, s, &tf);
-    PGB_CUDA(cudaMemcpyAsync(c->d_near_off.p + ng, &tn, 8, cudaMemcpyHostToDevice, s));
-    PGB_CUDA(cudaMemcpyAsync(c->d_far_off.p + ng, &tf, 8, cudaMemcpyHostToDevice, s));
-    c->n_near = tn;
-    c->n_far = tf;
-    c->d_near.resize(tn);
-    c->d_far.resize(tf);
-    k_lists<<<nblk(ng, 64), 64, 0, s>>>(a, ng, true, nullptr, nullptr, c->d_near_off, c->d_far_off, c->d_near,
-                                        c->d_far, st);
+    exclusive_scan_i64(nc, noff, ng, s, &tn);
+    exclusive_scan_i64(fc, foff, ng, s, &tf);
+    PGB_CUDA(cudaMemcpyAsync(noff.p + ng, &tn, 8, cudaMemcpyHostToDevice, s));
+    PGB_CUDA(cudaMemcpyAsync(foff.p + ng, &tf, 8, cudaMemcpyHostToDevice, s));
+    n_near = tn;
+    n_far = tf;
+    nearl.resize(tn);
+    farl.resize(tf);
+    k_lists<<<nblk(ng, 64), 64, 0, s>>>(a, ng, true, nullptr, nullptr, noff, foff, nearl, farl, st);
     PGB_CUDA(cudaGetLastError());
-    c->d_near4.resize(tn);
-    c->d_far4.resize(tf);
-    k_list_offsets<<<(unsigned)ng, 64, 0, s>>>(ng, c->d_near_off, c->d_near, c->d_node_center, c->d_group_center,
-                                               c->d_near4);
-    k_list_offsets<<<(unsigned)ng, 64, 0, s>>>(ng, c->d_far_off, c->d_far, c->d_node_center, c->d_group_center,
-                                               c->d_far4);
+    near4.resize(tn);
+    far4.resize(tf);
+    k_list_offsets<<<(unsigned)ng, 64, 0, s>>>(ng, noff, nearl, c->d_node_center, c->d_group_center, near4);
+    k_list_offsets<<<(unsigned)ng, 64, 0, s>>>(ng, foff, farl, c->d_node_center, c->d_group_center, far4);
     PGB_CUDA(cudaGetLastError());
+    unsigned long long h[5];
+    PGB_CUDA(cudaMemcpyAsync(h, st.p, 40, cudaMemcpyDeviceToHost, s));
+    PGB_CUDA(cudaStreamSynchronize(s));
+    if (h[4]) fail(PGB_EINVAL, "octree traversal stack overflow");
+    if (stats4)
+        for (int k = 0; k < 4; ++k) stats4[k] = h[k];
+    PGB_LAUNCHED(c, 6);
+}
+
+void build_lists(pgb_ctx* c) {
+    cudaStream_t s = c->stream;
+    int64_t ng = c->n_groups;
+    unsigned long long h[4];
+    make_lists(c, c->d_node_r2, c->d_group_lo, c->d_group_hi, c->d_near_off, c->d_near, c->d_far_off, c->d_far,
+               c->d_near4, c->d_far4, c->n_near, c->n_far, h);
+    c->p2p_pairs = (int64_t)h[0];
+    c->p2p_lap = (int64_t)h[1];
+    c->m2p_pairs = (int64_t)h[2];
+    c->m2p_lap = (int64_t)h[3];
     {
         DBuf<int64_t> tc;
         tc.resize(ng);
@@ -981,15 +1004,7 @@ void build_lists(pgb_ctx* c) {
         PGB_CUDA(cudaGetLastError());
         PGB_CUDA(cudaStreamSynchronize(s));
     }
-    PGB_LAUNCHED(c, 6);
-    unsigned long long h[5];
-    PGB_CUDA(cudaMemcpyAsync(h, st.p, 40, cudaMemcpyDeviceToHost, s));
-    PGB_CUDA(cudaStreamSynchronize(s));
-    if (h[4]) fail(PGB_EINVAL, "octree traversal stack overflow");
-    c->p2p_pairs = (int64_t)h[0];
-    c->p2p_lap = (int64_t)h[1];
-    c->m2p_pairs = (int64_t)h[2];
-    c->m2p_lap = (int64_t)h[3];
+    PGB_LAUNCHED(c, 2);
 }
 
 // ---------------------------------------------------------------- corrections

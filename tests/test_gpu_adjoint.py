@@ -1,0 +1,140 @@
+"""Adjoint path on the GPU (pgb_matvec_transpose, pgb_grad) against the
+dense oracle, the dot-product identity and finite differences."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import units
+from oracle.bem import SET_CHARGE
+from oracle.gradient import gradients
+from problems import gpu_context, oracle_system
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no GPU", allow_module_level=True)
+
+import paper_1506_03745_gb300 as pgb  # noqa: E402
+
+
+def _bodies(kind="sigma", nu=4, level=2, t=(10.5, 0.4, -0.3)):
+    v, f = synth.star_surface(4, nu, 3.5)
+    rng = np.random.default_rng(2)
+    mol = dict(kind="dielectric", verts=v, tris=f, eps_in=4.0, qxyz=rng.uniform(-1.0, 1.0, size=(6, 3)),
+               q=rng.uniform(-1, 1, 6), bc=0.0)
+    v2, f2 = synth.icosphere(level, 3.0)
+    srf = dict(kind=kind, verts=v2, tris=f2, eps_in=1.0, qxyz=np.zeros((0, 3)), q=np.zeros(0),
+               bc=-0.05 if kind == "sigma" else 0.05, R=np.eye(3), t=np.asarray(t, dtype=float))
+    return [mol, srf]
+
+
+def _tmv(ctx, lam, prec):
+    lt = torch.tensor(lam, device="cuda")
+    yt = torch.empty_like(lt)
+    pgb.pgb_matvec_transpose(ctx, lt, yt, prec)
+    torch.cuda.synchronize()
+    return yt.cpu().numpy()
+
+
+@pytest.mark.parametrize("kind", ["sigma", "phi"])
+def test_transposed_product_matches_dense_transpose(kind):
+    bodies = _bodies(kind)
+    so = oracle_system(bodies, theta=0.0)
+    ctx = gpu_context(bodies, theta=0.0, leaf_size=16)
+    try:
+        A, _ = so.assemble()
+        lam = np.random.default_rng(5).normal(size=so.n)
+        ref = A.T @ lam
+        scale = np.abs(ref).max()
+        assert np.abs(_tmv(ctx, lam, pgb.PGB_FP64) - ref).max() / scale < 1e-11
+        assert np.abs(_tmv(ctx, lam, pgb.PGB_FP32) - ref).max() / scale < 5e-6
+    finally:
+        pgb.pgb_destroy(ctx)
+
+
+def test_transposed_treecode_accuracy():
+    bodies = _bodies("sigma", nu=6, level=3)
+    so = oracle_system(bodies, theta=0.0)
+    ctx = gpu_context(bodies, theta=0.5, P=6, leaf_size=16)
+    try:
+        A, _ = so.assemble()
+        lam = np.random.default_rng(6).normal(size=so.n)
+        ref = A.T @ lam
+        for prec in (pgb.PGB_FP64, pgb.PGB_FP32):
+            err = np.abs(_tmv(ctx, lam, prec) - ref).max() / np.abs(ref).max()
+            assert err < 2e-3
+        stats = pgb.pgb_tree_stats(ctx)
+        assert stats["n_far"] > 0
+    finally:
+        pgb.pgb_destroy(ctx)
+
+
+def test_dot_product_identity_direct_sum():
+    bodies = _bodies("phi")
+    ctx = gpu_context(bodies, theta=0.0)
+    try:
+        n = pgb.pgb_num_unknowns(ctx)
+        rng = np.random.default_rng(7)
+        x, lam = rng.normal(size=n), rng.normal(size=n)
+        xt = torch.tensor(x, device="cuda")
+        yt = torch.empty_like(xt)
+        pgb.pgb_matvec(ctx, xt, yt, pgb.PGB_FP64)
+        ax = yt.cpu().numpy()
+        atl = _tmv(ctx, lam, pgb.PGB_FP64)
+        assert lam @ ax == pytest.approx(atl @ x, rel=1e-12)
+    finally:
+        pgb.pgb_destroy(ctx)
+
+
+def _solve(ctx, tol=1e-11):
+    n = pgb.pgb_num_unknowns(ctx)
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    code, _ = pgb.pgb_solve(ctx, pgb.PGB_FP64, tol, 3000, 100, x)
+    assert code == 0
+    return x
+
+
+@pytest.mark.parametrize("kind", ["sigma", "phi"])
+def test_gradients_match_dense_adjoint(kind):
+    bodies = _bodies(kind)
+    so = oracle_system(bodies, theta=0.0)
+    ref = gradients(so)
+    ctx = gpu_context(bodies, theta=0.0)
+    try:
+        x = _solve(ctx)
+        code, dq, dbc, dt, st = pgb.pgb_grad(ctx, x, 6, 2, pgb.PGB_FP64, 1e-11, 2000, 100)
+        assert code == 0
+        np.testing.assert_allclose(dq, ref["dq"][0], rtol=1e-8, atol=1e-10)
+        assert dbc[1] == pytest.approx(ref["dbc"][1], rel=1e-8)
+        np.testing.assert_allclose(dt, np.array(ref["dt"]), rtol=1e-5, atol=1e-8)
+        # Euler's identity of the quadratic form and translation invariance
+        e = pgb.pgb_energy(ctx, x)
+        bc = bodies[1]["bc"]
+        assert bodies[0]["q"] @ dq + bc * dbc[1] == pytest.approx(2 * e["total"], rel=1e-8)
+        np.testing.assert_allclose(dt[0], -dt[1], rtol=1e-6, atol=1e-10)
+    finally:
+        pgb.pgb_destroy(ctx)
+
+
+def test_translation_gradient_matches_finite_differences_treecode():
+    bodies = _bodies("sigma", nu=6, level=3)
+    ctx = gpu_context(bodies, theta=0.5, P=6, leaf_size=16)
+    try:
+        x = _solve(ctx)
+        code, dq, dbc, dt, st = pgb.pgb_grad(ctx, x, 6, 2, pgb.PGB_FP32, 1e-6, 2000, 100)
+        assert code == 0
+        h = 1e-3
+        t0 = np.asarray(bodies[1]["t"])
+        for ax in range(3):
+            f = []
+            for sgn in (1, -1):
+                tt = t0.copy()
+                tt[ax] += sgn * h
+                pgb.pgb_set_pose(ctx, 1, np.eye(3), tt)
+                pgb.pgb_tree_build(ctx)
+                f.append(pgb.pgb_energy(ctx, _solve(ctx))["total"])
+            fd = (f[0] - f[1]) / (2 * h)
+            assert dt[1, ax] == pytest.approx(fd, rel=1e-3, abs=2e-5)
+    finally:
+        pgb.pgb_destroy(ctx)
