@@ -202,6 +202,17 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def reduce_across_ranks(dist, total_ms, matvecs, device):
+    """Whole-job numbers of N replicas: the slowest rank's time and the sum of
+    the operator applications of all ranks."""
+    import torch
+    t = torch.tensor([total_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    m = torch.tensor([float(matvecs)], device=device, dtype=torch.float64)
+    dist.all_reduce(m)
+    return float(t.item()), int(round(m.item()))
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import torch
@@ -258,15 +269,7 @@ def run_gpu(args):
         dist.barrier()
     clk = clocks.stop()
     timing = pgb.pgb_timing(ctx, False, read=True)
-    t_max = total_ms
-    mv_all = matvecs
-    if dist:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        m = torch.tensor([matvecs], device=dev, dtype=torch.float64)
-        dist.all_reduce(m)
-        mv_all = int(m.item())
+    t_max, mv_all = reduce_across_ranks(dist, total_ms, matvecs, dev) if dist else (total_ms, matvecs)
     value = mv_all / (t_max / 1e3)
 
     # ---- FP64 reference solve on the same GPU (reported beside the value)

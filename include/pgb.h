@@ -136,6 +136,14 @@ int pgb_mesh_load(struct pgb_ctx* ctx, int32_t kind, const double* verts, int64_
                   const double* charge_xyz, const double* charge_q, int64_t nq,
                   double bc_value, int32_t* body_id_out);
 
+/* Replace the charge values of dielectric body body_id (nq must equal the
+ * loaded count; positions are kept).  Does not invalidate the tree. */
+int pgb_set_charges(struct pgb_ctx* ctx, int32_t body_id, const double* charge_q, int64_t nq);
+
+/* Replace the imposed sigma0 (C/m^2) or phi0 (V) of surface body body_id.
+ * Does not invalidate the tree. */
+int pgb_set_bc(struct pgb_ctx* ctx, int32_t body_id, double bc_value);
+
 /* Solvent permittivity and inverse Debye length (Eq. 1); kappa >= 0. */
 int pgb_set_solvent(struct pgb_ctx* ctx, double eps_out, double kappa);
 

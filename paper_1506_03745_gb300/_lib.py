@@ -63,6 +63,8 @@ _SIGS = {
     "pgb_mesh_load": (c_i32, [c_vp, c_i32, c_vp, c_i64, c_vp, c_i64, c_dbl, c_vp, c_vp, c_i64, c_dbl,
                               ctypes.POINTER(c_i32)]),
     "pgb_set_solvent": (c_i32, [c_vp, c_dbl, c_dbl]),
+    "pgb_set_charges": (c_i32, [c_vp, c_i32, c_vp, c_i64]),
+    "pgb_set_bc": (c_i32, [c_vp, c_i32, c_dbl]),
     "pgb_set_pose": (c_i32, [c_vp, c_i32, c_vp, c_vp]),
     "pgb_tree_build": (c_i32, [c_vp]),
     "pgb_tree_stats": (c_i32, [c_vp, ctypes.POINTER(pgb_tree_info)]),
@@ -162,6 +164,15 @@ def pgb_mesh_load(ctx, kind, verts, tris, eps_in=1.0, charge_xyz=None, charge_q=
 
 def pgb_set_solvent(ctx, eps_out, kappa):
     return _check(ctx, lib().pgb_set_solvent(ctx, eps_out, kappa))
+
+
+def pgb_set_charges(ctx, body_id, q):
+    q_, qp = _hptr(np.asarray(q).reshape(-1), np.float64)
+    return _check(ctx, lib().pgb_set_charges(ctx, body_id, qp, q_.shape[0]))
+
+
+def pgb_set_bc(ctx, body_id, bc_value):
+    return _check(ctx, lib().pgb_set_bc(ctx, body_id, float(bc_value)))
 
 
 def pgb_set_pose(ctx, body_id, R, t):

@@ -198,6 +198,36 @@ int pgb_mesh_load(pgb_ctx* c, int32_t kind, const double* verts, int64_t nv, con
     });
 }
 
+int pgb_set_charges(pgb_ctx* c, int32_t id, const double* q, int64_t nq) {
+    if (!c) return PGB_EINVAL;
+    return guard(c, [&]() -> int {
+        if (id < 0 || id >= (int32_t)c->bodies.size()) fail(PGB_EINVAL, "bad body id");
+        auto& b = c->bodies[id];
+        if (b.kind != PGB_DIELECTRIC) fail(PGB_EINVAL, "only molecules carry charges");
+        if (nq != b.nq || (nq && !q)) fail(PGB_EINVAL, "charge count differs from the loaded body");
+        for (int64_t k = 0; k < nq; ++k)
+            if (!isfinite(q[k])) fail(PGB_EINVAL, "non-finite charge");
+        b.qval.assign(q, q + nq);
+        if (c->order_valid && nq)  // device copy exists: update it in place
+            PGB_CUDA(cudaMemcpyAsync(c->d_qval.p + b.q_off, q, 8 * nq, cudaMemcpyHostToDevice, c->stream));
+        PGB_CUDA(cudaStreamSynchronize(c->stream));
+        return PGB_OK;
+    });
+}
+
+int pgb_set_bc(pgb_ctx* c, int32_t id, double bc_value) {
+    if (!c) return PGB_EINVAL;
+    return guard(c, [&]() -> int {
+        if (id < 0 || id >= (int32_t)c->bodies.size()) fail(PGB_EINVAL, "bad body id");
+        auto& b = c->bodies[id];
+        if (b.kind == PGB_DIELECTRIC) fail(PGB_EINVAL, "molecules have no imposed boundary value");
+        if (!isfinite(bc_value)) fail(PGB_EINVAL, "bc_value must be finite");
+        const double e = 1.602176634e-19, eps0 = 8.8541878128e-12;
+        b.bc = b.kind == PGB_SET_CHARGE ? bc_value * 1e-20 / e : bc_value * eps0 * 1e-10 / e;
+        return PGB_OK;
+    });
+}
+
 int pgb_set_solvent(pgb_ctx* c, double eps_out, double kappa) {
     if (!c) return PGB_EINVAL;
     if (!(eps_out > 0 && isfinite(eps_out)) || !(kappa >= 0 && isfinite(kappa))) {

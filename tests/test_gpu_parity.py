@@ -171,3 +171,24 @@ def test_state_and_argument_errors():
         assert st == pgb.PGB_ESTATE
     finally:
         pgb.pgb_destroy(ctx)
+
+
+@pytest.mark.parametrize("kind", ["sigma", "phi"])
+def test_treecode_energies_within_1e3_of_dense(kind):
+    """theta 0.5, P 6 treecode with FP32+refinement against the dense FP64
+    oracle: energies within 1e-3 relative."""
+    bodies = spheres(kind=kind, level_mol=3, level_srf=3)
+    so = oracle_system(bodies, theta=0.0)
+    ctx = gpu_context(bodies, theta=0.5, P=6, leaf_size=32)
+    try:
+        n = pgb.pgb_num_unknowns(ctx)
+        x = torch.empty(n, dtype=torch.float64, device="cuda")
+        code, st = pgb.pgb_solve(ctx, pgb.PGB_FP32_REFINE, 1e-6, 2000, 100, x)
+        assert code == 0
+        e = pgb.pgb_energy(ctx, x, 2)
+        eo = energies(so, so.solve())
+        assert e["solvation"] == pytest.approx(eo["solvation"], rel=1e-3)
+        assert e["surface"] == pytest.approx(eo["surface"], rel=1e-3)
+        assert e["total"] == pytest.approx(eo["total"], rel=1e-3)
+    finally:
+        pgb.pgb_destroy(ctx)
