@@ -367,6 +367,161 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ other workloads
+def star_bodies(density, seed=3, nq=900):
+    """Star-shaped molecule r = 15 A (1 + sum_{l<=6} a_lm Y_lm), `density`
+    panels per A^2, nq charges inside (>= 1.5 A from the mesh), eps_in 4."""
+    import synth
+    nu = synth.nu_for_density(seed, density)
+    v, f = synth.star_surface(seed, nu)
+    coeffs = synth.star_coefficients(seed)
+    xyz, q = synth.interior_charges(seed, nq, v, f, radius_fn=lambda d: synth.star_radius(d, coeffs, 15.0))
+    return dict(kind="dielectric", verts=v, tris=f, eps_in=4.0, qxyz=xyz, q=q, bc=0.0)
+
+
+def sphere_body(radius=40.0, nu=39, sigma=-0.05):
+    import synth
+    u, f = synth.geodesic_sphere(nu)
+    return dict(kind="sigma", verts=u * radius, tris=f, eps_in=1.0, qxyz=np.zeros((0, 3)), q=np.zeros(0), bc=sigma)
+
+
+def place_for_gap(verts, R, radius, gap):
+    """x offset D of the rotated molecule so that its closest vertex is `gap`
+    from a sphere of `radius` at the origin (bisection)."""
+    v = np.asarray(verts) @ np.asarray(R).T
+    lo, hi = radius + gap - v[:, 0].min() - 50.0, radius + gap - v[:, 0].min() + 50.0
+    for _ in range(80):
+        mid = 0.5 * (lo + hi)
+        d = np.sqrt(((v + np.array([mid, 0, 0])) ** 2).sum(1)).min() - radius
+        lo, hi = (mid, hi) if d < gap else (lo, mid)
+    return 0.5 * (lo + hi)
+
+
+def _timed(fn):
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = fn()
+    e1.record()
+    e1.synchronize()
+    return out, e0.elapsed_time(e1)
+
+
+def run_star(args):
+    """Config: star molecule at 2, 4, 8 panels/A^2 with 900 charges, FP32 +
+    refinement (tol 1e-6) against the plain FP64 solve on the same GPU."""
+    import torch
+    import paper_1506_03745_gb300 as pgb
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from problems import gpu_context
+    rows = []
+    for dens in (2, 4, 8):
+        body = star_bodies(dens)
+        ctx = gpu_context([body], **PARAMS)
+        n = pgb.pgb_num_unknowns(ctx)
+        x = torch.empty(n, dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup):
+            pgb.pgb_solve(ctx, pgb.PGB_FP32_REFINE, TOL, MAX_ITER, RESTART, x)
+        ms = []
+        for _ in range(args.steps):
+            (code, st), t = _timed(lambda: (pgb.pgb_tree_build(ctx),
+                                            pgb.pgb_solve(ctx, pgb.PGB_FP32_REFINE, TOL, MAX_ITER, RESTART, x))[1])
+            (e32), te = _timed(lambda: pgb.pgb_energy(ctx, x))
+            ms.append(t + te)
+        (c64, st64), t64 = _timed(lambda: pgb.pgb_solve(ctx, pgb.PGB_FP64, TOL, MAX_ITER, RESTART, x))
+        e64 = pgb.pgb_energy(ctx, x)
+        info = pgb.pgb_tree_stats(ctx)
+        rows.append({"density": dens, "panels": info["n_panels"], "ms_per_step": statistics.median(ms),
+                     "fp64_solve_ms": t64, "iterations": st["iterations"], "matvecs": st["matvecs"],
+                     "matvecs_per_s": st["matvecs"] / (statistics.median(ms) / 1e3),
+                     "solvation_kcal_mol": e32["solvation"], "solvation_rel_err_vs_fp64":
+                         abs(e32["solvation"] - e64["solvation"]) / abs(e64["solvation"]),
+                     "coulomb_kcal_mol": e32["coulomb"]})
+        pgb.pgb_destroy(ctx)
+    print(json.dumps({"workload": "star molecule r=15 A, 900 charges, 2/4/8 panels/A^2, single body",
+                      "step": "tree build + FP32/FP64-refined solve (tol 1e-6) + energies", "params": PARAMS,
+                      "results": rows}), flush=True)
+
+
+def run_gradient(args):
+    """Config: star molecule (2 panels/A^2, 900 charges) 10 A from a sphere
+    r = 40 A (30420 panels, sigma -0.05 C/m^2): adjoint gradient time."""
+    import torch
+    import paper_1506_03745_gb300 as pgb
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from problems import gpu_context
+    mol = star_bodies(2)
+    srf = sphere_body()
+    D = place_for_gap(mol["verts"], np.eye(3), 40.0, 10.0)
+    mol["R"], mol["t"] = np.eye(3), np.array([D, 0.0, 0.0])
+    prm = dict(PARAMS)
+    ctx = gpu_context([mol, srf], **prm)
+    n = pgb.pgb_num_unknowns(ctx)
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    nq = len(mol["q"])
+    for _ in range(args.warmup):
+        pgb.pgb_solve(ctx, pgb.PGB_FP32_REFINE, TOL, MAX_ITER, RESTART, x)
+        pgb.pgb_grad(ctx, x, nq, 2, pgb.PGB_FP32, 1e-6, MAX_ITER, RESTART)
+    ts, tg = [], []
+    for _ in range(args.steps):
+        (code, st), t1 = _timed(lambda: pgb.pgb_solve(ctx, pgb.PGB_FP32_REFINE, TOL, MAX_ITER, RESTART, x))
+        res, t2 = _timed(lambda: pgb.pgb_grad(ctx, x, nq, 2, pgb.PGB_FP32, 1e-6, MAX_ITER, RESTART))
+        ts.append(t1)
+        tg.append(t2)
+    _, dq, dbc, dt, ast = res
+    e = pgb.pgb_energy(ctx, x, 2)
+    print(json.dumps({"workload": "star molecule (2 panels/A^2, 900 charges) 10 A from a sphere r=40 A "
+                                  "(30420 panels, sigma -0.05 C/m^2)",
+                      "panels": pgb.pgb_tree_stats(ctx)["n_panels"], "solve_ms": statistics.median(ts),
+                      "grad_ms": statistics.median(tg), "solve_iterations": st["iterations"],
+                      "adjoint_iterations": ast["iterations"], "adjoint_rel_residual": ast["rel_residual"],
+                      "F_total_kcal_mol": e["total"], "dF_dt_molecule": dt[0].tolist(),
+                      "dF_dsigma": float(dbc[1]), "sum_q_dFdq_plus_sigma_dFdsigma_over_2F":
+                          float((mol["q"] @ dq + srf["bc"] * dbc[1]) / (2 * e["total"]))}), flush=True)
+    pgb.pgb_destroy(ctx)
+
+
+def run_poses(args):
+    """Config subset: one synthetic molecule (~5000 panels, 900 charges) in
+    `--poses` orientations x 4 gaps (6, 8, 10, 14 A) near a sphere r = 40 A
+    (30420 panels, sigma -0.05 C/m^2), batched with pgb_solve_batch in pure
+    FP32 (tol 1e-5); the energy error against FP64 is measured on 2 poses."""
+    import torch
+    import synth
+    import paper_1506_03745_gb300 as pgb
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from problems import gpu_context
+    nu = int(round(math.sqrt(5000 / 20)))
+    v, f = synth.star_surface(100, nu)
+    coeffs = synth.star_coefficients(100)
+    xyz, q = synth.interior_charges(100, 900, v, f, radius_fn=lambda d: synth.star_radius(d, coeffs, 15.0))
+    mol = dict(kind="dielectric", verts=v, tris=f, eps_in=4.0, qxyz=xyz, q=q, bc=0.0)
+    srf = sphere_body()
+    Rs = synth.random_rotations(7, args.poses)
+    poses_R, poses_t = [], []
+    for R in Rs:
+        for gap in (6.0, 8.0, 10.0, 14.0):
+            poses_R.append(R)
+            poses_t.append([place_for_gap(v, R, 40.0, gap), 0.0, 0.0])
+    poses_R, poses_t = np.array(poses_R), np.array(poses_t)
+    mol["R"], mol["t"] = poses_R[0], poses_t[0]
+    ctx = gpu_context([mol, srf], **PARAMS)
+    B = len(poses_R)
+    pgb.pgb_solve_batch(ctx, 0, poses_R[:2], poses_t[:2], pgb.PGB_FP32, 1e-5, MAX_ITER, RESTART)  # warm-up
+    (code, F, st), ms = _timed(lambda: pgb.pgb_solve_batch(ctx, 0, poses_R, poses_t, pgb.PGB_FP32, 1e-5,
+                                                           MAX_ITER, RESTART))
+    code64, F64, _ = pgb.pgb_solve_batch(ctx, 0, poses_R[:2], poses_t[:2], pgb.PGB_FP64, 1e-9, MAX_ITER, RESTART)
+    err = [abs(F[i, 3] - F64[i, 3]) / abs(F64[i, 3]) for i in range(2)]
+    print(json.dumps({"workload": f"1 molecule ({pgb.pgb_tree_stats(ctx)['n_panels'] - 30420} panels, 900 "
+                                  f"charges) x {args.poses} orientations x 4 gaps near a sphere r=40 A "
+                                  f"(30420 panels)", "poses": B, "ms": ms, "poses_per_s": B / (ms / 1e3),
+                      "mean_iterations": float(np.mean([s["iterations"] for s in st])),
+                      "energy_rel_err_vs_fp64_first_2_poses": err, "status": code,
+                      "F_total_range_kcal_mol": [float(F[:, 3].min()), float(F[:, 3].max())]}), flush=True)
+    pgb.pgb_destroy(ctx)
+
+
 def run_matvec(args):
     """Operator applications only: W + K FP32 treecode matvecs of the
     workload (tree built once, untimed); prints matvecs/s and per-stage times."""
@@ -403,6 +558,8 @@ def run_matvec(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--mode", default="solve", choices=["solve", "matvec"])
+    ap.add_argument("--workload", default="two_sphere", choices=["two_sphere", "star", "gradient", "poses"])
+    ap.add_argument("--poses", type=int, default=8, help="orientations for --workload poses")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -418,6 +575,12 @@ def main():
             PARAMS[k] = v
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "star":
+        run_star(args)
+    elif args.workload == "gradient":
+        run_gradient(args)
+    elif args.workload == "poses":
+        run_poses(args)
     elif args.mode == "matvec":
         run_matvec(args)
     else:
