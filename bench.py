@@ -8,8 +8,8 @@ eps_in 4, next to a sphere of radius 4 A (20480 panels) with imposed charge
 near rule, 9 points per edge, treecode theta 0.5, P 6; GMRES tol 1e-6 with
 FP32 inner solves and FP64 residual refinement.
 
-One step = the whole hot path: geometry + octree + lists + near-field
-precompute (pgb_tree_build), the FP32+refinement GMRES solve (pgb_solve) and
+One step = the whole hot path: Morton sort + octree + geometry + lists +
+near-field precompute (pgb_tree_reset + pgb_tree_build, nothing cached), the FP32+refinement GMRES solve (pgb_solve) and
 the energies (pgb_energy), inputs resident on the device.  value = treecode
 matvecs per second inside those steps (all operator applications of the solve,
 FP32 and FP64, divided by the step time).  L2 is flushed (512 MB write)
@@ -237,6 +237,7 @@ def run_gpu(args):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
     def step(mode):
+        pgb.pgb_tree_reset(ctx)   # the whole geometry pipeline runs in every step
         pgb.pgb_tree_build(ctx)
         code, st = pgb.pgb_solve(ctx, mode, TOL, MAX_ITER, RESTART, x)
         if code != 0:
@@ -335,7 +336,8 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_unknowns": n, "theta": PARAMS["theta"], "P": PARAMS["P"],
                    "leaf_size": PARAMS["leaf_size"], "K": PARAMS["K"], "tol": TOL, "restart": RESTART,
-                   "step": "tree build + FP32/FP64-refined GMRES solve + energies",
+                   "step": "full tree build (sort, octree, lists, near field; nothing cached) + "
+                           "FP32/FP64-refined GMRES solve + energies",
                    "l2": "flushed (512 MB write) before every timed step",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "solve": {"fp32_refine_ms": t_max / args.steps, "fp64_ms": fp64_ms,
@@ -509,8 +511,10 @@ def run_poses(args):
     ctx = gpu_context([mol, srf], **PARAMS)
     B = len(poses_R)
     pgb.pgb_solve_batch(ctx, 0, poses_R[:2], poses_t[:2], pgb.PGB_FP32, 1e-5, MAX_ITER, RESTART)  # warm-up
+    pgb.pgb_timing(ctx, True, read=True)
     (code, F, st), ms = _timed(lambda: pgb.pgb_solve_batch(ctx, 0, poses_R, poses_t, pgb.PGB_FP32, 1e-5,
                                                            MAX_ITER, RESTART))
+    tim = pgb.pgb_timing(ctx, False, read=True)
     code64, F64, _ = pgb.pgb_solve_batch(ctx, 0, poses_R[:2], poses_t[:2], pgb.PGB_FP64, 1e-9, MAX_ITER, RESTART)
     err = [abs(F[i, 3] - F64[i, 3]) / abs(F64[i, 3]) for i in range(2)]
     print(json.dumps({"workload": f"1 molecule ({pgb.pgb_tree_stats(ctx)['n_panels'] - 30420} panels, 900 "
@@ -518,6 +522,8 @@ def run_poses(args):
                                   f"(30420 panels)", "poses": B, "ms": ms, "poses_per_s": B / (ms / 1e3),
                       "mean_iterations": float(np.mean([s["iterations"] for s in st])),
                       "energy_rel_err_vs_fp64_first_2_poses": err, "status": code,
+                      "stage_ms_per_pose": {k: v[0] / B for k, v in tim.items() if k != "kernel_launches" and v[0]},
+                      "kernel_launches_per_pose": tim["kernel_launches"] / B,
                       "F_total_range_kcal_mol": [float(F[:, 3].min()), float(F[:, 3].max())]}), flush=True)
     pgb.pgb_destroy(ctx)
 

@@ -157,6 +157,12 @@ int pgb_set_pose(struct pgb_ctx* ctx, int32_t body_id, const double R[9], const 
 int pgb_tree_build(struct pgb_ctx* ctx);
 int pgb_tree_stats(struct pgb_ctx* ctx, pgb_tree_info* info);
 
+/* Drop every cached geometric structure (Morton order, octree, each body's
+ * own near-field entries), so that the next pgb_tree_build recomputes all of
+ * them (pgb_tree_build otherwise rebuilds only what loads, poses and the
+ * solvent changed). */
+int pgb_tree_reset(struct pgb_ctx* ctx);
+
 /* Number of unknowns 2*N_dielectric + N_surface. */
 int pgb_num_unknowns(struct pgb_ctx* ctx, int64_t* n);
 
@@ -232,6 +238,21 @@ int pgb_energy(struct pgb_ctx* ctx, const double* x, pgb_energies* e, pgb_energi
  * ordering) race and must be serialised by the caller. */
 #define PGB_NOALLOC_MAX_CHARGES 65536
 int pgb_energy_noalloc(struct pgb_ctx* ctx, const double* x, pgb_energies* e);
+
+/* Treecode parameter autotuner (a library feature; the paper fixes its
+ * parameters by hand, Tables 1, 2, 4).  For every candidate (theta, P,
+ * leaf_size) of the given lists it builds the tree, times `reps` FP32
+ * matvecs with CUDA events and solves in PGB_FP32 mode to `tol` for the total
+ * energy.  The reference is the candidate with the smallest theta, largest P
+ * and first leaf size; among the candidates whose total energy is within
+ * target_rel_err of the reference, the one with the shortest solve time
+ * (tree build + solve) is chosen.  The context keeps the chosen parameters and
+ * a built tree; *chosen receives them.  report (may be NULL) receives, per
+ * candidate in loop order theta-major, then P, then leaf: matvec ms, solve ms,
+ * relative energy difference to the reference. */
+int pgb_autotune(struct pgb_ctx* ctx, const double* thetas, int32_t n_theta, const int32_t* Ps, int32_t n_P,
+                 const int32_t* leaves, int32_t n_leaf, int32_t reps, double tol, double target_rel_err,
+                 pgb_params* chosen, double* report);
 
 /* Enable (1) or disable (0) stage timing.  If out is not NULL the stream
  * is synchronised and the times and launch count accumulated since the last

@@ -65,8 +65,11 @@ _SIGS = {
     "pgb_set_solvent": (c_i32, [c_vp, c_dbl, c_dbl]),
     "pgb_set_charges": (c_i32, [c_vp, c_i32, c_vp, c_i64]),
     "pgb_set_bc": (c_i32, [c_vp, c_i32, c_dbl]),
+    "pgb_autotune": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_i32, c_vp, c_i32, c_i32, c_dbl, c_dbl,
+                             ctypes.POINTER(pgb_params), c_vp]),
     "pgb_set_pose": (c_i32, [c_vp, c_i32, c_vp, c_vp]),
     "pgb_tree_build": (c_i32, [c_vp]),
+    "pgb_tree_reset": (c_i32, [c_vp]),
     "pgb_tree_stats": (c_i32, [c_vp, ctypes.POINTER(pgb_tree_info)]),
     "pgb_num_unknowns": (c_i32, [c_vp, ctypes.POINTER(c_i64)]),
     "pgb_matvec": (c_i32, [c_vp, c_vp, c_vp, c_i32]),
@@ -175,6 +178,18 @@ def pgb_set_bc(ctx, body_id, bc_value):
     return _check(ctx, lib().pgb_set_bc(ctx, body_id, float(bc_value)))
 
 
+def pgb_autotune(ctx, thetas, Ps, leaves, reps=5, tol=1e-6, target_rel_err=1e-5):
+    """Returns (chosen params dict, report (n, 3): matvec ms, solve ms, energy rel. diff)."""
+    th, thp = _hptr(thetas, np.float64)
+    pp, ppp = _hptr(Ps, np.int32)
+    lv, lvp = _hptr(leaves, np.int32)
+    rep = np.zeros((len(th) * len(pp) * len(lv), 3))
+    ch = pgb_params()
+    _check(ctx, lib().pgb_autotune(ctx, thp, len(th), ppp, len(pp), lvp, len(lv), reps, tol, target_rel_err,
+                                   ctypes.byref(ch), rep.ctypes.data_as(c_vp)))
+    return {n: getattr(ch, n) for n, _ in pgb_params._fields_}, rep
+
+
 def pgb_set_pose(ctx, body_id, R, t):
     R_, Rp = _hptr(np.asarray(R).reshape(9), np.float64)
     t_, tp = _hptr(np.asarray(t).reshape(3), np.float64)
@@ -183,6 +198,10 @@ def pgb_set_pose(ctx, body_id, R, t):
 
 def pgb_tree_build(ctx):
     return _check(ctx, lib().pgb_tree_build(ctx))
+
+
+def pgb_tree_reset(ctx):
+    return _check(ctx, lib().pgb_tree_reset(ctx))
 
 
 def pgb_tree_stats(ctx):

@@ -286,6 +286,15 @@ int pgb_tree_build(pgb_ctx* c) {
     });
 }
 
+int pgb_tree_reset(pgb_ctx* c) {
+    if (!c) return PGB_EINVAL;
+    c->order_valid = false;
+    c->intra_valid = false;
+    c->tree_valid = false;
+    c->adj_valid = false;
+    return PGB_OK;
+}
+
 int pgb_tree_stats(pgb_ctx* c, pgb_tree_info* info) {
     if (!c || !info) return PGB_EINVAL;
     if (!c->tree_valid) {
@@ -452,6 +461,94 @@ int pgb_energy_noalloc(pgb_ctx* c, const double* x, pgb_energies* e) {
     return guard(c, [&]() -> int {
         if (!x || !e) fail(PGB_EINVAL, "null argument");
         energies_noalloc(c, x, e);
+        return PGB_OK;
+    });
+}
+
+int pgb_autotune(pgb_ctx* c, const double* thetas, int32_t n_theta, const int32_t* Ps, int32_t n_P,
+                 const int32_t* leaves, int32_t n_leaf, int32_t reps, double tol, double target, pgb_params* chosen,
+                 double* report) {
+    if (!c) return PGB_EINVAL;
+    return guard(c, [&]() -> int {
+        if (!thetas || !Ps || !leaves || n_theta < 1 || n_P < 1 || n_leaf < 1 || reps < 1)
+            fail(PGB_EINVAL, "empty candidate list");
+        if (!(tol > 0 && tol < 1) || !(target > 0)) fail(PGB_EINVAL, "tol in (0,1) and target > 0");
+        if (c->bodies.empty()) fail(PGB_ESTATE, "no bodies loaded");
+        const pgb_params base = c->p;
+        struct Cand {
+            pgb_params p;
+            double mv_ms, solve_ms, E;
+        };
+        std::vector<Cand> cands;
+        for (int it = 0; it < n_theta; ++it)
+            for (int ip = 0; ip < n_P; ++ip)
+                for (int il = 0; il < n_leaf; ++il) {
+                    pgb_params q = base;
+                    q.theta = thetas[it];
+                    q.P = Ps[ip];
+                    q.leaf_size = leaves[il];
+                    std::string why;
+                    if (check_params(&q, why) != PGB_OK) fail(PGB_EINVAL, "bad candidate: " + why);
+                    cands.push_back({q, 0, 0, 0});
+                }
+        int ref = 0;
+        for (size_t k = 1; k < cands.size(); ++k) {
+            const auto &a = cands[k].p, &b = cands[ref].p;
+            if (a.theta < b.theta || (a.theta == b.theta && a.P > b.P)) ref = (int)k;
+        }
+        cudaEvent_t e0, e1;
+        PGB_CUDA(cudaEventCreate(&e0));
+        PGB_CUDA(cudaEventCreate(&e1));
+        DBuf<double> x, y;
+        for (auto& cd : cands) {
+            const bool tree_changes = cd.p.leaf_size != c->p.leaf_size;
+            c->p = cd.p;
+            if (tree_changes) c->order_valid = false;
+            c->tree_valid = false;
+            PGB_CUDA(cudaEventRecord(e0, c->stream));
+            int r = pgb_tree_build(c);
+            if (r != PGB_OK) fail(r, c->err);
+            x.resize(c->n_unk);
+            y.resize(c->n_unk);
+            pgb_solve_stats st{};
+            r = solve(c, PGB_FP32, tol, 5000, 100, x, &st);
+            if (r != PGB_OK && r != PGB_ENOCONV) fail(r, c->err);
+            PGB_CUDA(cudaEventRecord(e1, c->stream));
+            PGB_CUDA(cudaEventSynchronize(e1));
+            float ms = 0;
+            PGB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            cd.solve_ms = ms;
+            pgb_energies en{};
+            energies(c, x, &en, nullptr);
+            cd.E = en.total;
+            apply_operator(c, x, y, PGB_FP32, false);  // warm
+            PGB_CUDA(cudaEventRecord(e0, c->stream));
+            for (int k = 0; k < reps; ++k) apply_operator(c, x, y, PGB_FP32, false);
+            PGB_CUDA(cudaEventRecord(e1, c->stream));
+            PGB_CUDA(cudaEventSynchronize(e1));
+            PGB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            cd.mv_ms = ms / reps;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        const double Eref = cands[ref].E;
+        int best = ref;
+        for (size_t k = 0; k < cands.size(); ++k) {
+            const double err = fabs(cands[k].E - Eref) / std::max(fabs(Eref), 1e-300);
+            if (report) {
+                report[3 * k] = cands[k].mv_ms;
+                report[3 * k + 1] = cands[k].solve_ms;
+                report[3 * k + 2] = err;
+            }
+            if (err <= target && cands[k].solve_ms < cands[best].solve_ms) best = (int)k;
+        }
+        const bool tree_changes = cands[best].p.leaf_size != c->p.leaf_size;
+        c->p = cands[best].p;
+        if (tree_changes) c->order_valid = false;
+        c->tree_valid = false;
+        int r = pgb_tree_build(c);
+        if (r != PGB_OK) fail(r, c->err);
+        if (chosen) *chosen = c->p;
         return PGB_OK;
     });
 }

@@ -58,34 +58,49 @@ __global__ void k_phi_reac(Geo g, BodyDev bd, Rules r, const double* qxyz, const
     if (threadIdx.x == 0) out[k] = acc / PGB_FOUR_PI;
 }
 
-// per-body sums: [0] sum q phi_reac, [1] Coulomb sum_{k<l} q_k q_l / r_kl,
-// [2] sum_j u_j A_j (surfaces).  One block per body.
+// per-body sums: [0] sum q phi_reac, [2] sum_j u_j A_j (surfaces).  One
+// block per body.  The Coulomb pair sum is k_coulomb_pairs.
 __global__ void k_body_sums(Geo g, BodyDev bd, const double* qxyz, const double* qv, const int64_t* qoff,
                             const double* phir, const double* x, double* out) {
     __shared__ double sh[32];
     const int b = blockIdx.x;
-    double s0 = 0, s1 = 0, s2 = 0;
-    for (int64_t k = qoff[b] + threadIdx.x; k < qoff[b + 1]; k += blockDim.x) {
-        s0 += qv[k] * phir[k];
-        for (int64_t l = k + 1; l < qoff[b + 1]; ++l) {
-            double dx = qxyz[3 * k] - qxyz[3 * l], dy = qxyz[3 * k + 1] - qxyz[3 * l + 1],
-                   dz = qxyz[3 * k + 2] - qxyz[3 * l + 2];
-            s1 += qv[k] * qv[l] / sqrt(dx * dx + dy * dy + dz * dz);
-        }
-    }
+    double s0 = 0, s2 = 0;
+    for (int64_t k = qoff[b] + threadIdx.x; k < qoff[b + 1]; k += blockDim.x) s0 += qv[k] * phir[k];
     if (bd.kind[b] != PGB_DIELECTRIC) {
         const int64_t p0 = bd.pan_off[b], p1 = bd.pan_off[b + 1];
         for (int64_t j = p0 + threadIdx.x; j < p1; j += blockDim.x)
             s2 += x[bd.unk_off[b] + (g.perm[j] - p0)] * g.A[j];
     }
     s0 = block_sum(s0, sh);
-    s1 = block_sum(s1, sh);
     s2 = block_sum(s2, sh);
     if (threadIdx.x == 0) {
         out[3 * b] = s0;
-        out[3 * b + 1] = s1;
         out[3 * b + 2] = s2;
     }
+}
+
+// Coulomb sum_{l>k} q_k q_l / r_kl of each body: one block per charge k,
+// partial sums pair[k], then a per-body reduction.
+__global__ void k_coulomb_pairs(const double* qxyz, const double* qv, const int32_t* qbody, const int64_t* qoff,
+                                double* pair) {
+    __shared__ double sh[32];
+    const int64_t k = blockIdx.x;
+    const int b = qbody[k];
+    double s = 0;
+    for (int64_t l = k + 1 + threadIdx.x; l < qoff[b + 1]; l += blockDim.x) {
+        double dx = qxyz[3 * k] - qxyz[3 * l], dy = qxyz[3 * k + 1] - qxyz[3 * l + 1], dz = qxyz[3 * k + 2] - qxyz[3 * l + 2];
+        s += qv[l] / sqrt(dx * dx + dy * dy + dz * dz);
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) pair[k] = qv[k] * s;
+}
+__global__ void k_coulomb_reduce(const int64_t* qoff, const double* pair, double* out) {
+    __shared__ double sh[32];
+    const int b = blockIdx.x;
+    double s = 0;
+    for (int64_t k = qoff[b] + threadIdx.x; k < qoff[b + 1]; k += blockDim.x) s += pair[k];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) out[3 * b + 1] = s;
 }
 
 // e^2/(eps0 Angstrom) in kcal/mol from CODATA 2018
@@ -110,8 +125,18 @@ void energies(pgb_ctx* c, const double* x, pgb_energies* e, pgb_energies* per_bo
     Rules r = make_rules(c->p.K, c->p.K_near, c->p.n_edge);
     if (c->n_q) k_phi_reac<<<(unsigned)c->n_q, 128, 0, s>>>(geo(c), body_dev(c), r, c->d_qxyz, c->d_q_body, x, phir);
     k_body_sums<<<nb, 128, 0, s>>>(geo(c), body_dev(c), c->d_qxyz, c->d_qval, qoff, phir, x, sums);
-    PGB_CUDA(cudaGetLastError());
-    PGB_LAUNCHED(c, c->n_q ? 2 : 1);
+    {
+        DBuf<double> pair;
+        pair.resize(std::max<int64_t>(1, c->n_q));
+        if (c->n_q)
+            k_coulomb_pairs<<<(unsigned)c->n_q, 128, 0, s>>>(c->d_qxyz, c->d_qval, c->d_q_body, qoff, pair);
+        else
+            PGB_CUDA(cudaMemsetAsync(pair.p, 0, 8, s));
+        k_coulomb_reduce<<<nb, 128, 0, s>>>(qoff, pair, sums);
+        PGB_CUDA(cudaGetLastError());
+        PGB_CUDA(cudaStreamSynchronize(s));
+    }
+    PGB_LAUNCHED(c, c->n_q ? 4 : 2);
     std::vector<double> h(3 * nb);
     PGB_CUDA(cudaMemcpyAsync(h.data(), sums.p, 8 * 3 * nb, cudaMemcpyDeviceToHost, s));
     PGB_CUDA(cudaStreamSynchronize(s));
@@ -195,7 +220,15 @@ void energies_noalloc(pgb_ctx* c, const double* x, pgb_energies* e) {
     if (c->n_q) k_phi_reac<<<(unsigned)c->n_q, 128, 0, s>>>(geo(c), body_dev(c), r, c->d_qxyz, c->d_q_body, x, phir);
     k_body_sums<<<nb, 128, 0, s>>>(geo(c), body_dev(c), c->d_qxyz, c->d_qval, qoff, phir, x, sums);
     PGB_CUDA(cudaGetLastError());
-    PGB_LAUNCHED(c, c->n_q ? 2 : 1);
+    // Coulomb pair sums, one block per charge, accumulated into the scratch
+    // after the per-body sums (pair sums reuse the reaction-potential slots
+    // only after k_body_sums has read them: same stream, in order)
+    if (c->n_q) {
+        k_coulomb_pairs<<<(unsigned)c->n_q, 128, 0, s>>>(c->d_qxyz, c->d_qval, c->d_q_body, qoff, phir);
+    }
+    k_coulomb_reduce<<<nb, 128, 0, s>>>(qoff, phir, sums);
+    PGB_CUDA(cudaGetLastError());
+    PGB_LAUNCHED(c, c->n_q ? 4 : 2);
     double h[3 * PGB_MAX_BODIES];
     PGB_CUDA(cudaMemcpyAsync(h, sums, 8 * 3 * nb, cudaMemcpyDeviceToHost, s));
     PGB_CUDA(cudaStreamSynchronize(s));

@@ -62,17 +62,27 @@ void build_rhs(pgb_ctx* c, double* b, int precision) {
 #define DOT_BLOCKS 304
 #define DOT_THREADS 256
 
-// partial[i * nb + blk] = sum over this block's rows of V_i . w, i < m
+// partial[i * nb + blk] = sum over this block's rows of V_i . w, i < m.
+// Each warp reduces its rows by shuffles and the warps' sums meet in shared
+// memory, so the m products cost one block barrier in total.
 __global__ void k_multi_dot(const double* __restrict__ V, int64_t ld, int m, const double* __restrict__ w, int64_t n,
                             double* partial) {
-    __shared__ double sh[DOT_THREADS / 32];
+    extern __shared__ double shd[];  // m x (warps)
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t r0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     for (int i = 0; i < m; ++i) {
         const double* v = V + i * ld;
         double s = 0;
-        for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
-            s += v[r] * w[r];
-        s = block_sum(s, sh);
-        if (threadIdx.x == 0) partial[(int64_t)i * gridDim.x + blockIdx.x] = s;
+        for (int64_t r = r0; r < n; r += stride) s += v[r] * w[r];
+        s = warp_sum(s);
+        if (lane == 0) shd[i * nw + wi] = s;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        double s = 0;
+        for (int k = 0; k < nw; ++k) s += shd[i * nw + k];
+        partial[(int64_t)i * gridDim.x + blockIdx.x] = s;
     }
 }
 
@@ -157,7 +167,7 @@ struct Krylov {
     cudaStream_t s;
 
     void norm(const double* w, double* out) {
-        k_multi_dot<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(w, n, 1, w, n, c->d_red);
+        k_multi_dot<<<DOT_BLOCKS, DOT_THREADS, 8 * (DOT_THREADS / 32), s>>>(w, n, 1, w, n, c->d_red);
         k_reduce_partials<<<1, 256, 0, s>>>(c->d_red, DOT_BLOCKS, out, 0, 1);
     }
     double host_read(const double* d) {
@@ -222,7 +232,8 @@ int gmres_op(pgb_ctx* c, int prec, bool transpose, const double* b, double* x, d
             {
                 StageTimer tm(c, PGB_STAGE_KRYLOV);
                 for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
-                    k_multi_dot<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(c->d_V, n, j + 1, w, n, c->d_red);
+                    k_multi_dot<<<DOT_BLOCKS, DOT_THREADS, 8 * (DOT_THREADS / 32) * (j + 1), s>>>(c->d_V, n, j + 1, w, n,
+                                                                                            c->d_red);
                     k_reduce_partials<<<j + 1, 256, 0, s>>>(c->d_red, DOT_BLOCKS, pass ? hcol : h, 0, 0);
                     k_multi_axpy<<<nblk(n, 256), 256, 0, s>>>(c->d_V, n, j + 1, pass ? hcol : h, -1.0, w, n);
                     if (pass) k_axpby<<<1, 256, 0, s>>>(1.0, h, 1.0, hcol, h, j + 1);
@@ -264,7 +275,8 @@ double vec_dot(pgb_ctx* c, const double* a, const double* b) {
     DBuf<double> t;
     t.resize(1);
     c->d_red.resize(std::max<size_t>(c->d_red.n, DOT_BLOCKS));
-    k_multi_dot<<<DOT_BLOCKS, DOT_THREADS, 0, c->stream>>>(a, c->n_unk, 1, b, c->n_unk, c->d_red);
+    k_multi_dot<<<DOT_BLOCKS, DOT_THREADS, 8 * (DOT_THREADS / 32), c->stream>>>(a, c->n_unk, 1, b, c->n_unk,
+                                                                                   c->d_red);
     k_reduce_partials<<<1, 256, 0, c->stream>>>(c->d_red, DOT_BLOCKS, t, 0, 0);
     return K.host_read(t);
 }
