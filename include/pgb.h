@@ -49,7 +49,8 @@ extern "C" {
                                solve: FP32 operator throughout (right-hand side included),
                                FP64 Arnoldi/Givens, no FP64 matvec */
 #define PGB_FP64 1          /* every treecode kernel in FP64 */
-#define PGB_FP32_REFINE 2   /* solve: FP32 inner GMRES, FP64 right-hand side and outer residual */
+#define PGB_FP32_REFINE 2   /* solve: FP32 inner GMRES, FP64 outer residual b - A x (one FP64
+                               product with the imposed densities folded in per outer step) */
 
 /* Numerical parameters: the seven columns of the paper's parameter tables
  * (Tables 1, 2, 4: Gauss points in-element per edge, close-by, far-away;

@@ -21,10 +21,13 @@ static inline int nblk(int64_t n, int t) { return (int)std::max<int64_t>(1, (n +
 // known == true builds the imposed-boundary densities instead: phi0 as the
 // double-layer density of an imposed-potential surface, dphi = -sigma0/eps_out
 // as the single layer of an imposed-charge surface, zero on molecules.
+// mode 0: densities of the unknowns x; 1: imposed parts only; 2: both (the
+// unknowns plus the imposed sigma0 / phi0 of every surface).
 template <typename real>
-__global__ void k_src_prep(Geo g, BodyDev bd, const double* __restrict__ x, bool known,
+__global__ void k_src_prep(Geo g, BodyDev bd, const double* __restrict__ x, int mode,
                            const typename V4<real>::t* __restrict__ yrel, typename V4<real>::t* __restrict__ src,
                            double* __restrict__ dens, double eps_out) {
+    const bool known = mode == 1;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= g.n_pan) return;
     const int b = g.pbody[i];
@@ -44,6 +47,10 @@ __global__ void k_src_prep(Geo g, BodyDev bd, const double* __restrict__ x, bool
             phi = x[o + loc];
         }
     } else {
+        if (kind == PGB_SET_POTENTIAL) phi = bd.bc[b];
+        else if (kind == PGB_SET_CHARGE) psiY = -bd.bc[b] / eps_out;
+    }
+    if (mode == 2) {
         if (kind == PGB_SET_POTENTIAL) phi = bd.bc[b];
         else if (kind == PGB_SET_CHARGE) psiY = -bd.bc[b] / eps_out;
     }
@@ -67,7 +74,8 @@ __global__ void k_src_prep(Geo g, BodyDev bd, const double* __restrict__ x, bool
 
 // U += near-field corrections (FP64), then the rows of Eq. 6 / Eq. 7 in the
 // caller's layout.  mode 0: y = A x.  mode 1: right-hand side of the imposed
-// boundary terms, -(U + jump) on exterior and surface rows.
+// boundary terms, -(U + jump) on exterior and surface rows.  mode 2: the rows
+// with the imposed densities included, so that b - A x = b_Coulomb - y.
 __global__ void k_assemble(Geo g, BodyDev bd, const double* __restrict__ U, const double* __restrict__ dens,
                            const int64_t* __restrict__ coff, const int32_t* __restrict__ cj,
                            const dbl4* __restrict__ cval, const int64_t* __restrict__ xoff,
@@ -94,7 +102,7 @@ __global__ void k_assemble(Geo g, BodyDev bd, const double* __restrict__ U, cons
     const int64_t N = bd.pan_off[b + 1] - bd.pan_off[b];
     const int64_t o = bd.unk_off[b];
     const int kind = bd.kind[b];
-    if (mode == 0) {
+    if (mode == 0 || mode == 2) {
         const double phi = dens[3 * i + 2];
         if (kind == PGB_DIELECTRIC) {
             y[o + loc] = 0.5 * phi - UL;
@@ -102,7 +110,7 @@ __global__ void k_assemble(Geo g, BodyDev bd, const double* __restrict__ U, cons
         } else if (kind == PGB_SET_CHARGE) {
             y[o + loc] = UY + 0.5 * phi;
         } else {
-            y[o + loc] = UY;
+            y[o + loc] = UY + (mode == 2 ? 0.5 * bd.bc[b] : 0.0);  // jump of the imposed phi0
         }
     } else {
         if (kind == PGB_DIELECTRIC) y[o + N + loc] = -UY;
@@ -126,7 +134,16 @@ void convert_f64_f32(const double* a, float* b, int64_t n, cudaStream_t s) {
     k_f64_to_f32<<<nblk(n, 256), 256, 0, s>>>(a, b, n);
 }
 
+void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode, const int* known_mask);
+
 void apply_operator(pgb_ctx* c, const double* x, double* y, int precision, bool known_only, const int* known_mask) {
+    apply_mode(c, x, y, precision, known_only ? 1 : 0, known_mask);
+}
+
+void apply_full(pgb_ctx* c, const double* x, double* y, int precision) { apply_mode(c, x, y, precision, 2, nullptr); }
+
+void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode, const int* known_mask) {
+    const bool known_only = mode == 1;
     if (!c->tree_valid) fail(PGB_ESTATE, "pgb_tree_build has not run for the current bodies and poses");
     cudaStream_t s = c->stream;
     Geo g = geo(c);
@@ -175,10 +192,10 @@ void apply_operator(pgb_ctx* c, const double* x, double* y, int precision, bool 
     {
         StageTimer tm(c, PGB_STAGE_SOURCES + (f32 ? 0 : PGB_STAGE_FP64));
         if (f32)
-            k_src_prep<float><<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, x, known_only, c->d_y32, c->d_src32,
+            k_src_prep<float><<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, x, mode, c->d_y32, c->d_src32,
                                                                   c->d_dens, c->eps_out);
         else
-            k_src_prep<double><<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, x, known_only, c->d_y64, c->d_src64,
+            k_src_prep<double><<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, x, mode, c->d_y64, c->d_src64,
                                                                    c->d_dens, c->eps_out);
         PGB_CUDA(cudaGetLastError());
         PGB_LAUNCHED(c, 1);
@@ -194,7 +211,7 @@ void apply_operator(pgb_ctx* c, const double* x, double* y, int precision, bool 
         StageTimer tm(c, PGB_STAGE_ASSEMBLE + (f32 ? 0 : PGB_STAGE_FP64));
         k_assemble<<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, c->d_U, c->d_dens, c->d_corr_off, c->d_corr_j,
                                                        c->d_corr_val, c->d_xcorr_off, c->d_xcorr_j, c->d_xcorr_val,
-                                                       known_only ? 1 : 0, y);
+                                                       mode, y);
         PGB_CUDA(cudaGetLastError());
         PGB_LAUNCHED(c, 1);
     }

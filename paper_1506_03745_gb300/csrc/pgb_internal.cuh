@@ -195,7 +195,7 @@ struct pgb_ctx {
     pgb::DBuf<unsigned char> d_scratch;
 
     // solver
-    pgb::DBuf<double> d_V, d_H, d_red, d_gv, d_b, d_r, d_wk, d_xs, d_small;
+    pgb::DBuf<double> d_V, d_H, d_red, d_gv, d_b, d_bc, d_r, d_wk, d_xs, d_small;
     double* h_pinned = nullptr;
 
     // statistics and stage timing
@@ -238,6 +238,8 @@ void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t
 void apply_operator(pgb_ctx* c, const double* x, double* y, int precision, bool known_only,
                     const int* known_mask = nullptr);
 void apply_transpose(pgb_ctx* c, const double* lam, double* y, int precision);
+void apply_full(pgb_ctx* c, const double* x, double* y, int precision);
+void coulomb_rows(pgb_ctx* c, double* b);
 void grad(pgb_ctx* c, const double* x, int precision, double tol, int max_iter, int restart, double* dq, double* dbc,
           double* dt, pgb_solve_stats* st);
 int gmres_op(pgb_ctx* c, int prec, bool transpose, const double* b, double* x, double abs_tol, int max_it,

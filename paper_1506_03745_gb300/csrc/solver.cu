@@ -32,6 +32,29 @@ __global__ void k_coulomb_rows(Geo g, BodyDev bd, const double* qxyz, const doub
     b[bd.unk_off[bi] + loc] = s / (PGB_FOUR_PI * eps_in[bi]);
 }
 
+// b = 0 except the Coulomb rows of the molecules.
+void coulomb_rows(pgb_ctx* c, double* b) {
+    cudaStream_t s = c->stream;
+    PGB_CUDA(cudaMemsetAsync(b, 0, 8 * c->n_unk, s));
+    std::vector<int64_t> qoff(c->bodies.size() + 1, 0);
+    std::vector<double> eps(c->bodies.size());
+    for (size_t i = 0; i < c->bodies.size(); ++i) {
+        qoff[i] = c->bodies[i].q_off;
+        eps[i] = c->bodies[i].eps_in;
+    }
+    qoff.back() = c->n_q;
+    DBuf<int64_t> dq;
+    DBuf<double> de;
+    dq.resize(qoff.size());
+    de.resize(eps.size());
+    PGB_CUDA(cudaMemcpyAsync(dq.p, qoff.data(), 8 * qoff.size(), cudaMemcpyHostToDevice, s));
+    PGB_CUDA(cudaMemcpyAsync(de.p, eps.data(), 8 * eps.size(), cudaMemcpyHostToDevice, s));
+    k_coulomb_rows<<<nblk(c->n_pan, 128), 128, 0, s>>>(geo(c), body_dev(c), c->d_qxyz, c->d_qval, dq, de, b);
+    PGB_CUDA(cudaGetLastError());
+    PGB_CUDA(cudaStreamSynchronize(s));
+    PGB_LAUNCHED(c, 1);
+}
+
 void build_rhs(pgb_ctx* c, double* b, int precision) {
     cudaStream_t s = c->stream;
     StageTimer tm(c, PGB_STAGE_RHS);
@@ -300,7 +323,7 @@ int solve(pgb_ctx* c, int mode, double tol, int max_iter, int restart, double* x
     c->d_red.resize((size_t)DOT_BLOCKS * (restart + 1));
     if (mode != PGB_FP64 && mode != PGB_FP32_REFINE && mode != PGB_FP32)
         fail(PGB_EINVAL, "mode must be PGB_FP64, PGB_FP32_REFINE or PGB_FP32");
-    const int rhs_prec = mode == PGB_FP32 ? PGB_FP32 : PGB_FP64;
+    const int rhs_prec = mode == PGB_FP64 ? PGB_FP64 : PGB_FP32;
     build_rhs(c, c->d_b, rhs_prec);
     pgb_solve_stats z{};
     int known_mv = 0;
@@ -332,7 +355,11 @@ int solve(pgb_ctx* c, int mode, double tol, int max_iter, int restart, double* x
         k_axpby<<<nblk(n, 256), 256, 0, s>>>(1.0, c->d_b, -1.0, c->d_r, c->d_r, n);
         rel = vec_norm(c, c->d_r) / bnorm;
     } else if (mode == PGB_FP32_REFINE) {
-        // r = b (x = 0); outer: solve A32 d = r, x += d, r = b - A64 x
+        // Inner FP32 solves take the right-hand side from the FP32 operator;
+        // the outer residual is FP64 throughout: r = b_Coulomb - A64(x + imposed
+        // densities), one FP64 product per outer step.
+        c->d_bc.resize(n);
+        coulomb_rows(c, c->d_bc);
         PGB_CUDA(cudaMemcpyAsync(c->d_r.p, c->d_b.p, 8 * n, cudaMemcpyDeviceToDevice, s));
         double rn = bnorm;
         while (rel > tol && z.iterations < max_iter && z.outer_steps < 50) {
@@ -347,10 +374,10 @@ int solve(pgb_ctx* c, int mode, double tol, int max_iter, int restart, double* x
             z.matvecs += mv;
             ++z.outer_steps;
             k_axpby<<<nblk(n, 256), 256, 0, s>>>(1.0, x, 1.0, c->d_xs, x, n);
-            apply_operator(c, x, c->d_r, PGB_FP64, false);
+            apply_full(c, x, c->d_r, PGB_FP64);
             ++z.matvecs;
             ++z.matvecs_fp64;
-            k_axpby<<<nblk(n, 256), 256, 0, s>>>(1.0, c->d_b, -1.0, c->d_r, c->d_r, n);
+            k_axpby<<<nblk(n, 256), 256, 0, s>>>(1.0, c->d_bc, -1.0, c->d_r, c->d_r, n);
             double rn_new = vec_norm(c, c->d_r);
             rel = rn_new / bnorm;
             if (it == 0 || !(rn_new < rn)) {  // no progress: stop

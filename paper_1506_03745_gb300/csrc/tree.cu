@@ -1061,73 +1061,95 @@ __device__ __forceinline__ void kern4(const double* x, const double* y, const do
     double dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
     double r2 = dx * dx + dy * dy + dz * dz;
     if (!(r2 > 0)) return;
-    double r = sqrt(r2);
-    double ri = 1.0 / r;
+    double ri = rsqrt(r2);
+    double r = r2 * ri;
     double nd = n[0] * dx + n[1] * dy + n[2] * dz;
     double e = exp(-kappa * r);
+    double ri3 = ri * ri * ri;
     vl += w * ri;
-    kl += w * nd * ri * ri * ri;
+    kl += w * nd * ri3;
     vy += w * e * ri;
-    ky += w * nd * (1.0 + kappa * r) * e * ri * ri * ri;
+    ky += w * nd * (1.0 + kappa * r) * e * ri3;
 }
 
-// Correction entry (i, j): tiered value minus the K-point value (FP64), for
-// V_L, K_L, V_Y, K_Y (Section 3.1).  Self panel: semi-analytical single layer
-// (three sub-triangles about the centroid, radial integral in closed form,
-// n_edge Gauss points along each edge), K_ii = 0.  Otherwise the 19-point rule.
-__global__ void k_corr_values(int64_t n, const int64_t* off, const int32_t* cj, const double* V, const double* C,
-                              const double* Nn, const double* A, const double* Y, const double* W,
-                              const int32_t* pbody, BodyDev bd, Rules r, double kappa, dbl4* out) {
-    int64_t i = blockIdx.x;
-    if (i >= n) return;
-    for (int64_t e = off[i] + threadIdx.x; e < off[i + 1]; e += blockDim.x) {
-        int64_t j = cj[e];
-        const double* x = C + 3 * i;
-        const double* nj = Nn + 3 * j;
-        double tv[4] = {0, 0, 0, 0};
-        if (j == i) {
-            const double* v = V + 9 * j;
-            for (int ed = 0; ed < 3; ++ed) {
-                const double* pa = v + 3 * ed;
-                const double* pb = v + 3 * ((ed + 1) % 3);
-                double ev[3] = {pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2]};
-                double ell = sqrt(ev[0] * ev[0] + ev[1] * ev[1] + ev[2] * ev[2]);
-                double u[3] = {ev[0] / ell, ev[1] / ell, ev[2] / ell};
-                double cpa[3] = {x[0] - pa[0], x[1] - pa[1], x[2] - pa[2]};
-                double proj = cpa[0] * u[0] + cpa[1] * u[1] + cpa[2] * u[2];
-                double hv[3] = {cpa[0] - proj * u[0], cpa[1] - proj * u[1], cpa[2] - proj * u[2]};
-                double h = sqrt(hv[0] * hv[0] + hv[1] * hv[1] + hv[2] * hv[2]);
-                for (int g = 0; g < r.ne; ++g) {
-                    double sg = r.ex[g] * ell;
-                    double p[3] = {pa[0] + sg * u[0] - x[0], pa[1] + sg * u[1] - x[1], pa[2] + sg * u[2] - x[2]};
-                    double rho = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
-                    double jac = h / (rho * rho) * ell * r.ew[g];
-                    tv[0] += rho * jac;
-                    tv[2] += (kappa > 0 ? (1.0 - exp(-kappa * rho)) / kappa : rho) * jac;
-                }
-            }
-        } else {
-            const double* v = V + 9 * j;
-            const double* cjp = C + 3 * j;
-            for (int m = 0; m < r.Kn; ++m) {
-                double y[3];
-                for (int a = 0; a < 3; ++a)
-                    y[a] = cjp[a] + ((r.mun[m][0] * (v[a] - cjp[a]) + r.mun[m][1] * (v[3 + a] - cjp[a])) +
-                                     r.mun[m][2] * (v[6 + a] - cjp[a]));
-                kern4(x, y, nj, kappa, r.wn[m] * A[j], tv[0], tv[1], tv[2], tv[3]);
-            }
-        }
-        // the treecode sums leave out the target's own panel, so the self entry
-        // is the whole semi-analytical value; other entries replace the K-point sum
-        double kv[4] = {0, 0, 0, 0};
-        if (j != i)
-            for (int m = 0; m < r.K; ++m) kern4(x, Y + 3 * (j * r.K + m), nj, kappa, W[j * r.K + m], kv[0], kv[1], kv[2], kv[3]);
-        double d[4];
-        for (int q = 0; q < 4; ++q) d[q] = (tv[q] - kv[q]) / PGB_FOUR_PI;
-        int bi = pbody[i], bj = pbody[j];
-        if (bi != bj || bd.kind[bi] != PGB_DIELECTRIC) d[0] = d[1] = 0.0;
-        out[e] = dbl4{d[0], d[1], d[2], d[3]};
+__device__ __forceinline__ int64_t owner_row(const int64_t* off, int64_t n, int64_t e) {
+    int64_t lo = 0, hi = n;  // last row with off[row] <= e
+    while (hi - lo > 1) {
+        const int64_t m = (lo + hi) >> 1;
+        if (off[m] <= e) lo = m;
+        else hi = m;
     }
+    return lo;
+}
+
+// Correction entries (i, j), j != i: 19-point rule minus the K-point sum,
+// for V_L, K_L, V_Y, K_Y (Section 3.1), FP64, one thread per entry.
+__global__ void k_corr_values(int64_t n, int64_t tot, const int64_t* off, const int32_t* cj, const double* V,
+                              const double* C, const double* Nn, const double* A, const double* Y, const double* W,
+                              const int32_t* pbody, BodyDev bd, Rules r, double kappa, dbl4* out) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= tot) return;
+    const int64_t i = owner_row(off, n, e);
+    const int64_t j = cj[e];
+    if (j == i) return;  // self entries: k_corr_self
+    const double* x = C + 3 * i;
+    const double* nj = Nn + 3 * j;
+    const double* v = V + 9 * j;
+    const double* cjp = C + 3 * j;
+    double tv[4] = {0, 0, 0, 0};
+    for (int m = 0; m < r.Kn; ++m) {
+        double y[3];
+        for (int a = 0; a < 3; ++a)
+            y[a] = cjp[a] + ((r.mun[m][0] * (v[a] - cjp[a]) + r.mun[m][1] * (v[3 + a] - cjp[a])) +
+                             r.mun[m][2] * (v[6 + a] - cjp[a]));
+        kern4(x, y, nj, kappa, r.wn[m] * A[j], tv[0], tv[1], tv[2], tv[3]);
+    }
+    double kv[4] = {0, 0, 0, 0};
+    for (int m = 0; m < r.K; ++m) kern4(x, Y + 3 * (j * r.K + m), nj, kappa, W[j * r.K + m], kv[0], kv[1], kv[2], kv[3]);
+    double d[4];
+    for (int q = 0; q < 4; ++q) d[q] = (tv[q] - kv[q]) / PGB_FOUR_PI;
+    const int bi = pbody[i], bj = pbody[j];
+    if (bi != bj || bd.kind[bi] != PGB_DIELECTRIC) d[0] = d[1] = 0.0;
+    out[e] = dbl4{d[0], d[1], d[2], d[3]};
+}
+
+// Self entries: the whole semi-analytical single layer (the treecode sums
+// leave out the target's own panel): three sub-triangles about the centroid,
+// radial integral in closed form, n_edge Gauss points along each edge; K_ii = 0.
+// One thread per target; the self entry is located by its column.
+__global__ void k_corr_self(int64_t n, const int64_t* off, const int32_t* cj, const double* V, const double* C,
+                            const int32_t* pbody, BodyDev bd, Rules r, double kappa, dbl4* out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t e = -1;
+    for (int64_t k = off[i]; k < off[i + 1]; ++k)
+        if (cj[k] == i) e = k;
+    if (e < 0) return;
+    const double* x = C + 3 * i;
+    const double* v = V + 9 * i;
+    double vl = 0, vy = 0;
+    for (int ed = 0; ed < 3; ++ed) {
+        const double* pa = v + 3 * ed;
+        const double* pb = v + 3 * ((ed + 1) % 3);
+        double ev[3] = {pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2]};
+        double ell = sqrt(ev[0] * ev[0] + ev[1] * ev[1] + ev[2] * ev[2]);
+        double u[3] = {ev[0] / ell, ev[1] / ell, ev[2] / ell};
+        double cpa[3] = {x[0] - pa[0], x[1] - pa[1], x[2] - pa[2]};
+        double proj = cpa[0] * u[0] + cpa[1] * u[1] + cpa[2] * u[2];
+        double hv[3] = {cpa[0] - proj * u[0], cpa[1] - proj * u[1], cpa[2] - proj * u[2]};
+        double h = sqrt(hv[0] * hv[0] + hv[1] * hv[1] + hv[2] * hv[2]);
+        for (int g = 0; g < r.ne; ++g) {
+            double sg = r.ex[g] * ell;
+            double p[3] = {pa[0] + sg * u[0] - x[0], pa[1] + sg * u[1] - x[1], pa[2] + sg * u[2] - x[2]};
+            double rho = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+            double jac = h / (rho * rho) * ell * r.ew[g];
+            vl += rho * jac;
+            vy += (kappa > 0 ? (1.0 - exp(-kappa * rho)) / kappa : rho) * jac;
+        }
+    }
+    const int bi = pbody[i];
+    const bool lap = bd.kind[bi] == PGB_DIELECTRIC;
+    out[e] = dbl4{lap ? vl / PGB_FOUR_PI : 0.0, 0.0, vy / PGB_FOUR_PI, 0.0};
 }
 
 BodyDev body_dev(const pgb_ctx* c) {
@@ -1168,8 +1190,11 @@ static void build_corr_part(pgb_ctx* c, bool cross, DBuf<int64_t>& off, DBuf<int
     if (tot) {
         k_corr_find<<<nblk(n, 64), 64, 0, s>>>(a, n, true, cross, c->d_pbody, nullptr, off, cj);
         Rules r = make_rules(c->p.K, c->p.K_near, c->p.n_edge);
-        k_corr_values<<<(int)n, 32, 0, s>>>(n, off, cj, c->d_v, c->d_c, c->d_n, c->d_A, c->d_y, c->d_w, c->d_pbody,
-                                            body_dev(c), r, c->kappa, val);
+        k_corr_values<<<nblk(tot, 128), 128, 0, s>>>(n, tot, off, cj, c->d_v, c->d_c, c->d_n, c->d_A, c->d_y,
+                                                     c->d_w, c->d_pbody, body_dev(c), r, c->kappa, val);
+        if (!cross)
+            k_corr_self<<<nblk(n, 128), 128, 0, s>>>(n, off, cj, c->d_v, c->d_c, c->d_pbody, body_dev(c), r,
+                                                     c->kappa, val);
     }
     PGB_CUDA(cudaGetLastError());
     PGB_CUDA(cudaStreamSynchronize(s));
