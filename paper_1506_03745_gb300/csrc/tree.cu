@@ -232,26 +232,60 @@ __global__ void k_rs_hist(const uint64_t* key, int64_t n, int shift, int64_t* hi
     if (threadIdx.x < 16) hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
 }
 
-__global__ void k_rs_scatter(const uint64_t* key, const int32_t* val, int64_t n, int shift, const int64_t* off,
-                             int ntiles, uint64_t* okey, int32_t* oval) {
-    __shared__ uint64_t sk[RS_TILE];
-    __shared__ int32_t sv[RS_TILE];
-    int64_t base = (int64_t)blockIdx.x * RS_TILE;
-    int cnt = (int)min((int64_t)RS_TILE, n - base);
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        sk[i] = key[base + i];
-        sv[i] = val[base + i];
+// Stable scatter of one 4-bit pass: thread t owns the tile's items 4t..4t+3;
+// its offset for digit d = tile base of d + number of d-items held by the
+// threads before it (per-digit exclusive scan over the block) + its own
+// earlier d-items.
+__global__ void __launch_bounds__(256) k_rs_scatter(const uint64_t* key, const int32_t* val, int64_t n, int shift,
+                                                    const int64_t* off, int ntiles, uint64_t* okey, int32_t* oval) {
+    __shared__ int cnt[16][256];
+    const int t = threadIdx.x;
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE + 4 * t;
+    uint64_t k[4];
+    int32_t v[4];
+    int d[4];
+    int mine[16];
+    for (int q = 0; q < 16; ++q) mine[q] = 0;
+    for (int q = 0; q < 4; ++q) {
+        const int64_t g = base + q;
+        if (g < n) {
+            k[q] = key[g];
+            v[q] = val[g];
+            d[q] = (int)((k[q] >> shift) & 15);
+        } else {
+            d[q] = -1;
+        }
+    }
+    for (int q = 0; q < 16; ++q) {
+        int c = 0;
+        for (int r = 0; r < 4; ++r) c += d[r] == q;
+        cnt[q][t] = c;
     }
     __syncthreads();
-    if (threadIdx.x < 16) {  // one thread per digit walks the tile in order (stable)
-        int d = threadIdx.x;
-        int64_t pos = off[(int64_t)d * ntiles + blockIdx.x];
-        for (int i = 0; i < cnt; ++i)
-            if (((sk[i] >> shift) & 15) == (uint64_t)d) {
-                okey[pos] = sk[i];
-                oval[pos] = sv[i];
-                ++pos;
-            }
+    // exclusive scan of every digit row: warp w scans rows 2w and 2w+1, each
+    // lane holding 8 consecutive entries
+    const int w = t >> 5, lane = t & 31;
+    for (int row = 2 * w; row < 2 * w + 2; ++row) {
+        int loc[8], s = 0;
+        for (int e = 0; e < 8; ++e) {
+            loc[e] = s;
+            s += cnt[row][8 * lane + e];
+        }
+        int inc = s;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const int excl = inc - s;
+        for (int e = 0; e < 8; ++e) cnt[row][8 * lane + e] = excl + loc[e];
+    }
+    __syncthreads();
+    for (int q = 0; q < 4; ++q) {
+        if (d[q] < 0) continue;
+        const int64_t pos = off[(int64_t)d[q] * ntiles + blockIdx.x] + cnt[d[q]][t] + mine[d[q]];
+        ++mine[d[q]];
+        okey[pos] = k[q];
+        oval[pos] = v[q];
     }
 }
 
@@ -402,7 +436,7 @@ void build_order(pgb_ctx* c) {
     for (int shift = 0; shift < top; shift += 4) {
         k_rs_hist<<<ntiles, 256, 0, s>>>(ka, n, shift, hist, ntiles);
         exclusive_scan_i64(hist, hoff, 16 * (int64_t)ntiles, s, nullptr);
-        k_rs_scatter<<<ntiles, 64, 0, s>>>(ka, va, n, shift, hoff, ntiles, kb, vb);
+        k_rs_scatter<<<ntiles, 256, 0, s>>>(ka, va, n, shift, hoff, ntiles, kb, vb);
         PGB_CUDA(cudaGetLastError());
         std::swap(ka, kb);
         std::swap(va, vb);
@@ -825,47 +859,80 @@ struct ListArgs {
 };
 
 // count (fill == false) or write the near/far lists of each group; depth
-// first, children in key order, bodies in order.
-__global__ void k_lists(ListArgs a, int64_t ng, bool fill, int64_t* ncnt, int64_t* fcnt, const int64_t* noff,
-                        const int64_t* foff, int32_t* nearl, int32_t* farl, unsigned long long* stats) {
-    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// first, children in key order, bodies in order.  One warp per group: when a
+// node is opened its children are classified (far / near leaf / to open) by
+// one lane each, then pushed on the warp's stack in reverse order with their
+// class, so the entries come out in the sequential depth-first order.
+#define LIST_WARPS 4
+__global__ void __launch_bounds__(32 * LIST_WARPS) k_lists(ListArgs a, int64_t ng, bool fill, int64_t* ncnt,
+                                                            int64_t* fcnt, const int64_t* noff, const int64_t* foff,
+                                                            int32_t* nearl, int32_t* farl, unsigned long long* stats) {
+    __shared__ int32_t st_node[LIST_WARPS][PGB_LIST_STACK];
+    __shared__ int8_t st_cls[LIST_WARPS][PGB_LIST_STACK];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t g = (int64_t)blockIdx.x * LIST_WARPS + w;
     if (g >= ng) return;
-    int32_t stack[PGB_LIST_STACK];
     int64_t nn = 0, nf = 0;
     int64_t wn = fill ? noff[g] : 0, wf = fill ? foff[g] : 0;
-    const double* lo = a.glo + 3 * g;
-    const double* hi = a.ghi + 3 * g;
-    int gb = a.gbody[g];
-    int64_t gsize = a.gend[g] - a.gstart[g];
+    double lo[3], hi[3];
+    for (int q = 0; q < 3; ++q) {
+        lo[q] = a.glo[3 * g + q];
+        hi[q] = a.ghi[3 * g + q];
+    }
+    const int gb = a.gbody[g];
+    const int64_t gsize = a.gend[g] - a.gstart[g];
     unsigned long long p2p = 0, p2pl = 0, m2p = 0, m2pl = 0;
+    bool overflow = false;
+    // class of a node: 0 far, 1 near leaf, 2 open
+    auto classify = [&](int nd) -> int {
+        if (a.theta > 0 && mac_far(a.theta2, a.r2[nd], a.center + 3 * nd, lo, hi)) return 0;
+        return a.nchild[nd] == 0 ? 1 : 2;
+    };
     for (int b = 0; b < a.n_bodies; ++b) {
-        bool lap = (b == gb) && a.kind[b] == PGB_DIELECTRIC;
+        const bool lap = (b == gb) && a.kind[b] == PGB_DIELECTRIC;
         int sp = 0;
-        stack[sp++] = b;  // roots are nodes 0..n_bodies-1
+        if (lane == 0) {
+            st_node[w][0] = b;  // roots are nodes 0..n_bodies-1
+            st_cls[w][0] = (int8_t)classify(b);
+        }
+        sp = 1;
+        __syncwarp();
         while (sp > 0) {
-            int nd = stack[--sp];
-            bool far = a.theta > 0 && mac_far(a.theta2, a.r2[nd], a.center + 3 * nd, lo, hi);
-            if (far) {
-                if (fill) farl[wf++] = nd;
+            --sp;
+            const int nd = st_node[w][sp];
+            const int cls = st_cls[w][sp];
+            __syncwarp();
+            if (cls == 0) {
+                if (fill && lane == 0) farl[wf] = nd;
+                ++wf;
                 ++nf;
                 m2p += gsize;
                 if (lap) m2pl += gsize;
-            } else if (a.nchild[nd] == 0) {
-                if (fill) nearl[wn++] = nd;
+            } else if (cls == 1) {
+                if (fill && lane == 0) nearl[wn] = nd;
+                ++wn;
                 ++nn;
-                unsigned long long pts = (unsigned long long)(a.nend[nd] - a.nstart[nd]) * a.K;
+                const unsigned long long pts = (unsigned long long)(a.nend[nd] - a.nstart[nd]) * a.K;
                 p2p += pts * gsize;
                 if (lap) p2pl += pts * gsize;
             } else {
-                int fc = a.child[nd], k = a.nchild[nd];
+                const int fc = a.child[nd], k = a.nchild[nd];
                 if (sp + k > PGB_LIST_STACK) {
-                    atomicAdd(&stats[4], 1ull);  // overflow flag (cannot happen for depth <= 10)
+                    overflow = true;
                     continue;
                 }
-                for (int j = k - 1; j >= 0; --j) stack[sp++] = fc + j;
+                if (lane < k) {  // child `lane` goes to stack slot sp + (k - 1 - lane)
+                    const int ch = fc + lane;
+                    st_node[w][sp + k - 1 - lane] = ch;
+                    st_cls[w][sp + k - 1 - lane] = (int8_t)classify(ch);
+                }
+                __syncwarp();
+                sp += k;
             }
         }
     }
+    if (lane != 0) return;
+    if (overflow) atomicAdd(&stats[4], 1ull);  // cannot happen for depth <= 10
     if (!fill) {
         ncnt[g] = nn;
         fcnt[g] = nf;
@@ -948,7 +1015,8 @@ void make_lists(pgb_ctx* c, const double* r2, const double* glo, const double* g
     DBuf<unsigned long long> st;
     st.resize(5);
     PGB_CUDA(cudaMemsetAsync(st.p, 0, 40, s));
-    k_lists<<<nblk(ng, 64), 64, 0, s>>>(a, ng, false, nc, fc, nullptr, nullptr, nullptr, nullptr, st);
+    k_lists<<<nblk(ng, LIST_WARPS), 32 * LIST_WARPS, 0, s>>>(a, ng, false, nc, fc, nullptr, nullptr, nullptr, nullptr,
+                                                              st);
     PGB_CUDA(cudaGetLastError());
     int64_t tn = 0, tf = 0;
     exclusive_scan_i64(nc, noff, ng, s, &tn);
@@ -959,7 +1027,8 @@ void make_lists(pgb_ctx* c, const double* r2, const double* glo, const double* g
     n_far = tf;
     nearl.resize(tn);
     farl.resize(tf);
-    k_lists<<<nblk(ng, 64), 64, 0, s>>>(a, ng, true, nullptr, nullptr, noff, foff, nearl, farl, st);
+    k_lists<<<nblk(ng, LIST_WARPS), 32 * LIST_WARPS, 0, s>>>(a, ng, true, nullptr, nullptr, noff, foff, nearl, farl,
+                                                              st);
     PGB_CUDA(cudaGetLastError());
     near4.resize(tn);
     far4.resize(tf);

@@ -192,3 +192,30 @@ def test_treecode_energies_within_1e3_of_dense(kind):
         assert e["total"] == pytest.approx(eo["total"], rel=1e-3)
     finally:
         pgb.pgb_destroy(ctx)
+
+
+def test_morton_order_and_lists_at_size():
+    """Multi-tile radix sort and warp-parallel traversals: the permutation and
+    the interaction-list sizes of the 2 x 20480-panel workload match the oracle."""
+    from oracle.treecode import BodyTree, interaction_lists
+    import bench
+    bodies = bench.workload_bodies()
+    so = oracle_system(bodies, theta=0.5, P=6, leaf_size=32)
+    ctx = gpu_context(bodies, theta=0.5, P=6, leaf_size=32)
+    try:
+        perm, noff, near, foff, far = pgb.pgb_tree_export(ctx)
+        trees = [BodyTree(b, pn, 7, 32) for b, pn in zip(so.bodies, so.panels)]
+        operm = np.concatenate([trees[0].perm, trees[1].perm + so.panels[0].N])
+        assert np.array_equal(perm, operm)
+        g = 0
+        for a, (tr, pn) in enumerate(zip(trees, so.panels)):
+            for g0 in range(0, pn.N, 32):
+                if g % 97 == 0:   # sampled groups
+                    idx = tr.perm[g0:g0 + 32]
+                    x = pn.c[idx]
+                    nn = sum(len(interaction_lists(tb, x.min(0), x.max(0), 0.5)[0]) for tb in trees)
+                    nf = sum(len(interaction_lists(tb, x.min(0), x.max(0), 0.5)[1]) for tb in trees)
+                    assert noff[g + 1] - noff[g] == nn and foff[g + 1] - foff[g] == nf
+                g += 1
+    finally:
+        pgb.pgb_destroy(ctx)
