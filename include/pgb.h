@@ -76,7 +76,7 @@ typedef struct pgb_solve_stats {
 
 typedef struct pgb_energies {
     double coulomb;            /* Coulomb energy of the point charges */
-    double solvation;          /* Eq. 12 with the 1/2 kept */
+    double solvation;          /* Eq. 11: 1/2 sum_k q_k phi_reac(r_k) */
     double surface;            /* Eq. 15 */
     double total;              /* Eq. 16 */
 } pgb_energies;

@@ -3,8 +3,8 @@ system, in kcal/mol.
 
   F_coul(a)  = 1/2 sum_{k != l} q_k q_l / (4 pi eps_a r_kl)              (Coulomb)
   phi_reac(r_k) = -K_L^{r_k}(phi_a) + V_L^{r_k}(dphi_a)                  (Eq. 13)
-  F_solv(a)  = 1/2 sum_k q_k phi_reac(r_k)     (Eq. 12; reading G1 keeps the
-               1/2 of its first line, as Eq. 27 of Section 4 does)
+  F_solv(a)  = 1/2 sum_k q_k phi_reac(r_k)     (Eq. 11-12; reading G1 keeps
+               the 1/2 of Eq. 11, as Eq. 32 (energy_phi) of Section 4 does)
   F_surf(s)  = 1/2 sum_j phi_j sigma0 A_j       imposed charge (Eq. 15)
              = -1/2 sum_j phi0 sigma_j A_j      imposed potential, with
                sigma_j = -eps_out dphi_j/dn (reading G3, the sign of Eq. 1)

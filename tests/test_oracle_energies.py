@@ -49,7 +49,7 @@ def test_isolated_limits_are_textbook_forms():
 
 @pytest.mark.parametrize("n", [0, 1, 2, 3])
 def test_addition_theorem(n):
-    # k_n(kappa r2) P_n(cos th2) = sum_m (2m+1) B_nm i_m(kappa r1) P_m(cos th1), Eq. 19,
+    # k_n(kappa r2) P_n(cos th2) = sum_m (2m+1) B_nm i_m(kappa r1) P_m(cos th1), Eq. 19 (addition_formula),
     # each angle measured from the line of centres towards the other centre
     kappa, R = 0.125, 12.0
     B = B_matrix(50, kappa * R)
