@@ -267,6 +267,15 @@ int pgb_timing(struct pgb_ctx* ctx, int32_t enable, pgb_stage_times* out);
 int pgb_tree_export(struct pgb_ctx* ctx, int32_t* perm, int64_t* near_off, int32_t* near_node,
                     int64_t* far_off, int32_t* far_node);
 
+/* Diagnostic: evaluate the device's FP64 elementary functions of the
+ * near-field sums at n host points x (no context; the current device, its
+ * default stream, synchronous).  out (host, n x 5, row-major) receives per
+ * point: the one-step and two-step Newton reciprocal square roots (valid for
+ * 1e-30 < x < 1e30), the Taylor 2^x (valid for -2^30 < x <= 1020), and the CUDA
+ * library's rsqrt(x) and exp2(x) for comparison.  PGB_EINVAL for n < 0 or a
+ * NULL pointer with n > 0; PGB_ECUDA on a CUDA error. */
+int pgb_math_check(const double* x, int64_t n, double* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -82,6 +82,7 @@ _SIGS = {
     "pgb_tree_export": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "pgb_timing": (c_i32, [c_vp, c_i32, ctypes.POINTER(pgb_stage_times)]),
     "pgb_energy_noalloc": (c_i32, [c_vp, c_vp, ctypes.POINTER(pgb_energies)]),
+    "pgb_math_check": (c_i32, [c_vp, c_i64, c_vp]),
 }
 
 
@@ -310,3 +311,12 @@ def pgb_tree_export(ctx):
     p = lambda a: a.ctypes.data_as(c_vp)
     _check(ctx, lib().pgb_tree_export(ctx, p(perm), p(noff), p(near), p(foff), p(far)))
     return perm, noff, near[:s["n_near"]], foff, far[:s["n_far"]]
+
+
+def pgb_math_check(x):
+    """Device FP64 functions at the points x (host array): columns one-step
+    and two-step Newton rsqrt, Taylor exp2, library rsqrt, library exp2."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros((len(x), 5), np.float64)
+    _check(None, lib().pgb_math_check(x.ctypes.data_as(c_vp), len(x), out.ctypes.data_as(c_vp)))
+    return out

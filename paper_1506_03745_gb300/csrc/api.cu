@@ -5,6 +5,7 @@
 #include <exception>
 #include <new>
 
+#include "common.cuh"
 #include "pgb_internal.cuh"
 
 namespace pgb {
@@ -15,6 +16,17 @@ void cuda_check(cudaError_t e, const char* what) {
     }
 }
 void fail(int code, const std::string& msg) { throw Error{code, msg}; }
+
+__global__ void k_math_check(int64_t n, const double* x, double* y) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = x[i];
+    y[5 * i] = rsqrt_nr<1>(v);
+    y[5 * i + 1] = rsqrt_nr<2>(v);
+    y[5 * i + 2] = exp2_taylor(v);
+    y[5 * i + 3] = rsqrt(v);
+    y[5 * i + 4] = exp2(v);
+}
 
 static cudaEvent_t get_event(pgb_ctx* c) {
     if (!c->ev_pool.empty()) {
@@ -586,6 +598,24 @@ int pgb_tree_export(pgb_ctx* c, int32_t* perm, int64_t* near_off, int32_t* near_
         PGB_CUDA(cudaStreamSynchronize(s));
         return PGB_OK;
     });
+}
+
+int pgb_math_check(const double* x, int64_t n, double* out) {
+    if (n < 0 || (n > 0 && (!x || !out))) return PGB_EINVAL;
+    if (n == 0) return PGB_OK;
+    double *dx = nullptr, *dy = nullptr;
+    int rc = PGB_OK;
+    if (cudaMalloc(&dx, 8 * n) != cudaSuccess || cudaMalloc(&dy, 40 * n) != cudaSuccess) rc = PGB_ECUDA;
+    if (rc == PGB_OK && cudaMemcpy(dx, x, 8 * n, cudaMemcpyHostToDevice) != cudaSuccess) rc = PGB_ECUDA;
+    if (rc == PGB_OK) {
+        pgb::k_math_check<<<(unsigned)((n + 255) / 256), 256>>>(n, dx, dy);
+        if (cudaGetLastError() != cudaSuccess || cudaMemcpy(out, dy, 40 * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = PGB_ECUDA;
+    }
+    if (rc != PGB_OK) (void)cudaGetLastError();
+    cudaFree(dx);
+    cudaFree(dy);
+    return rc;
 }
 
 }  // extern "C"

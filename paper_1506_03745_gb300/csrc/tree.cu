@@ -1124,16 +1124,17 @@ __global__ void k_corr_find(CorrArgs a, int64_t n, bool fill, bool cross, const 
     if (!fill) cnt[i] = k;
 }
 
-// Kernel values at a target x from a source point y with normal n (no 1/4pi).
+// Kernel values at a target x from a source point y with normal n (no 1/4pi);
+// 1/r by two Newton steps (FP64 rounding), e^{-kappa r} by exp2_taylor.
 __device__ __forceinline__ void kern4(const double* x, const double* y, const double* n, double kappa, double w,
                                       double& vl, double& kl, double& vy, double& ky) {
     double dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
     double r2 = dx * dx + dy * dy + dz * dz;
     if (!(r2 > 0)) return;
-    double ri = rsqrt(r2);
+    double ri = rsqrt_nr<2>(r2);
     double r = r2 * ri;
     double nd = n[0] * dx + n[1] * dy + n[2] * dz;
-    double e = exp(-kappa * r);
+    double e = exp2_taylor(-kappa * 1.4426950408889634 * r);
     double ri3 = ri * ri * ri;
     vl += w * ri;
     kl += w * nd * ri3;

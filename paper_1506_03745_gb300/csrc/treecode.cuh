@@ -38,20 +38,24 @@ __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
 __device__ __forceinline__ float exp_(float x) { return __expf(x); }
 __device__ __forceinline__ double exp_(double x) { return exp(x); }
-// 2^x (the P2P loop folds log2(e) into its constant).  FP32: the SFU's
-// approximate forms (relative error about 2^-22), one instruction each.
+// 2^x (the P2P loop folds log2(e) into its constant) and 1/sqrt(x) of the
+// P2P loop.  FP32: the SFU's approximate forms (relative error about 2^-22),
+// one instruction each.  FP64: exp2_taylor and one Newton step on the SFU
+// estimate (relative errors below 1e-14 and 1e-13), about a third of the FP64
+// operations of the library's correctly rounded forms on a part whose FP64
+// rate is 1/64 of its FP32 rate.
 __device__ __forceinline__ float exp2_(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-__device__ __forceinline__ double exp2_(double x) { return exp2(x); }
+__device__ __forceinline__ double exp2_(double x) { return exp2_taylor(x); }
 __device__ __forceinline__ float rsqrt_fast(float x) {
     float y;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-__device__ __forceinline__ double rsqrt_fast(double x) { return rsqrt(x); }
+__device__ __forceinline__ double rsqrt_fast(double x) { return rsqrt_nr<1>(x); }
 
 // Neumaier-compensated accumulation s + c += v.
 template <typename T>

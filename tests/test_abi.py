@@ -52,3 +52,11 @@ def test_argument_errors_need_no_device(libpgb):
     assert lib.pgb_destroy(None) == L.PGB_EINVAL
     assert lib.pgb_matvec(None, None, None, 0) == L.PGB_EINVAL
     assert lib.pgb_last_error(None) == b"null context"
+
+
+def test_math_check_argument_errors(libpgb):
+    import paper_1506_03745_gb300._lib as L
+    lib = L.lib()
+    assert lib.pgb_math_check(None, -1, None) == L.PGB_EINVAL
+    assert lib.pgb_math_check(None, 4, None) == L.PGB_EINVAL
+    assert lib.pgb_math_check(None, 0, None) == L.PGB_OK
