@@ -40,7 +40,8 @@ import numpy as np  # noqa: E402
 METRIC = "treecode matvecs/sec and GMRES solve ms at 1e-5 energy err, FP32+refine vs FP64"
 UNIT = "matvecs/s"
 WORKLOAD = "two spheres r=4 A, 2 x 20480 panels, sigma=0.05 C/m^2, R=12 A"
-PARAMS = dict(K=7, K_near=19, n_edge=9, P=6, theta=0.5, leaf_size=32, group_size=32)
+PARAMS = dict(K=7, K_near=19, n_edge=9, P=6, theta=0.5, leaf_size=32, group_size=32, p2p_item=64, m2p_item=64,
+              precond=0)
 TOL = 1e-6
 RESTART = 100
 MAX_ITER = 2000
@@ -285,6 +286,7 @@ def run_gpu(args):
     x64 = x.clone()
     step(pgb.PGB_FP32_REFINE)
     e_err = {k: abs(e32[k] - e64[k]) / max(abs(e64[k]), 1e-300) for k in ("solvation", "surface", "total")}
+    pc = precond_solve(pgb, bodies, dev, stream, flush, e64) if not PARAMS.get("precond") else None
 
     info = pgb.pgb_tree_stats(ctx)
     peak_tflops = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -335,7 +337,8 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_unknowns": n, "theta": PARAMS["theta"], "P": PARAMS["P"],
-                   "leaf_size": PARAMS["leaf_size"], "K": PARAMS["K"], "tol": TOL, "restart": RESTART,
+                   "leaf_size": PARAMS["leaf_size"], "p2p_item": PARAMS["p2p_item"], "m2p_item": PARAMS["m2p_item"],
+                   "precond": PARAMS["precond"], "K": PARAMS["K"], "tol": TOL, "restart": RESTART,
                    "step": "full tree build (sort, octree, lists, near field; nothing cached) + "
                            "FP32/FP64-refined GMRES solve + energies",
                    "l2": "flushed (512 MB write) before every timed step",
@@ -345,7 +348,8 @@ def run_gpu(args):
                   "iterations": st0["iterations"], "outer_steps": st0["outer_steps"],
                   "matvecs": st0["matvecs"], "matvecs_fp64": st0["matvecs_fp64"],
                   "fp64_iterations": st64["iterations"], "rel_residual": st0["rel_residual"],
-                  "energy_rel_err_vs_fp64": e_err, "energies_kcal_mol": e32},
+                  "energy_rel_err_vs_fp64": e_err, "energies_kcal_mol": e32,
+                  "block_diagonal_precond": pc},
         "stage_ms_per_step": {k: v[0] / args.steps for k, v in timing.items() if k != "kernel_launches"},
         "gpu_launches": timing["kernel_launches"],
         "roofline": {"kernel": dom["kernel"], "bound": "alu", "achieved": dom["achieved"],
@@ -528,6 +532,35 @@ def run_poses(args):
     pgb.pgb_destroy(ctx)
 
 
+def precond_solve(pgb, bodies, dev, stream, flush, e64, steps=3):
+    """The same step with the block-diagonal right preconditioner (precond=1):
+    median device ms over `steps` steps after one warm-up, its iterations and
+    the energy difference to the unpreconditioned FP64 solve."""
+    import torch
+    ctx = gpu_context(bodies, **dict(PARAMS, precond=1))
+    n = pgb.pgb_num_unknowns(ctx)
+    x = torch.empty(n, dtype=torch.float64, device=dev)
+    ms, st, e = [], None, None
+    for i in range(steps + 1):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pgb.pgb_tree_reset(ctx)
+        pgb.pgb_tree_build(ctx)
+        code, st = pgb.pgb_solve(ctx, pgb.PGB_FP32_REFINE, TOL, MAX_ITER, RESTART, x)
+        e = pgb.pgb_energy(ctx, x)
+        b.record(stream)
+        b.synchronize()
+        if code != 0:
+            raise RuntimeError(f"preconditioned solve did not converge: {st}")
+        if i:
+            ms.append(a.elapsed_time(b))
+    pgb.pgb_destroy(ctx)
+    return {"ms_per_step": statistics.median(ms), "iterations": st["iterations"], "matvecs": st["matvecs"],
+            "energy_rel_err_vs_fp64": {k: abs(e[k] - e64[k]) / max(abs(e64[k]), 1e-300)
+                                       for k in ("solvation", "surface", "total")}}
+
+
 def run_matvec(args):
     """Operator applications only: W + K FP32 treecode matvecs of the
     workload (tree built once, untimed); prints matvecs/s and per-stage times."""
@@ -575,8 +608,12 @@ def main():
     ap.add_argument("--leaf", type=int, default=None, help="override leaf_size (parameter sweeps)")
     ap.add_argument("--P", type=int, default=None, help="override the Taylor order (parameter sweeps)")
     ap.add_argument("--theta", type=float, default=None, help="override theta (parameter sweeps)")
+    ap.add_argument("--p2p-item", type=int, default=None, help="override P2P tiles per work item (sweeps)")
+    ap.add_argument("--m2p-item", type=int, default=None, help="override far nodes per M2P work item (sweeps)")
+    ap.add_argument("--precond", type=int, default=None, help="1: block-diagonal GMRES preconditioner")
     args = ap.parse_args()
-    for k, v in (("leaf_size", args.leaf), ("P", args.P), ("theta", args.theta)):
+    for k, v in (("leaf_size", args.leaf), ("P", args.P), ("theta", args.theta), ("p2p_item", args.p2p_item),
+                 ("m2p_item", args.m2p_item), ("precond", args.precond)):
         if v is not None:
             PARAMS[k] = v
     if args.impl == "reference":

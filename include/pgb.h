@@ -64,6 +64,11 @@ typedef struct pgb_params {
     double theta;         /* multipole acceptance criterion; 0 = direct sum */
     int32_t leaf_size;    /* N_crit: max panels per octree leaf, 1..1024 */
     int32_t group_size;   /* targets per interaction list: 32 (one warp) */
+    int32_t p2p_item;     /* P2P work item: at most this many 32-point tiles of one group, 1..4096 (0 = 64) */
+    int32_t m2p_item;     /* M2P work item: at most this many far nodes of one group, 1..4096 (0 = 64) */
+    int32_t precond;      /* GMRES preconditioner: 0 none (the paper's solver), 1 block-diagonal: per
+                             panel, the inverse of the 2x2 (molecule) or 1x1 (surface) block of its own
+                             self terms, applied on the right so the residual test is unchanged */
 } pgb_params;
 
 typedef struct pgb_solve_stats {
@@ -116,7 +121,8 @@ typedef struct pgb_stage_times {
 } pgb_stage_times;
 
 /* Create a context on the current CUDA device.  p may be NULL (defaults:
- * K=7, K_near=19, n_edge=9, P=6, theta=0.5, leaf_size=32, group_size=32).
+ * K=7, K_near=19, n_edge=9, P=6, theta=0.5, leaf_size=32, group_size=32,
+ * p2p_item=64, m2p_item=64, precond=0).
  * cuda_stream is a cudaStream_t (NULL = legacy default stream).  Returns
  * PGB_EINVAL for out-of-range parameters. */
 int pgb_create(struct pgb_ctx** ctx, const pgb_params* p, void* cuda_stream);

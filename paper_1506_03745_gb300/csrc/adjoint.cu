@@ -545,6 +545,7 @@ void grad(pgb_ctx* c, const double* x, int precision, double tol, int max_iter, 
     c->d_V.resize((size_t)(restart + 1) * n);
     c->d_red.resize((size_t)304 * (restart + 1));
     PGB_CUDA(cudaMemsetAsync(c->d_lam.p, 0, 8 * n, s));
+    precond_prepare(c);
     double gnorm = sqrt(vec_dot(c, c->d_gx, c->d_gx));
     pgb_solve_stats z{};
     if (gnorm > 0) {

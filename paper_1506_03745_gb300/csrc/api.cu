@@ -97,6 +97,9 @@ static int check_params(const pgb_params* p, std::string& why) {
     else if (!(p->theta >= 0 && p->theta < 1)) why = "theta must be in [0, 1)";
     else if (p->leaf_size < 1 || p->leaf_size > 1024) why = "leaf_size must be in 1..1024";
     else if (p->group_size != 32) why = "group_size must be 32";
+    else if (p->p2p_item < 0 || p->p2p_item > 4096) why = "p2p_item must be in 1..4096 (0 = default)";
+    else if (p->m2p_item < 0 || p->m2p_item > 4096) why = "m2p_item must be in 1..4096 (0 = default)";
+    else if (p->precond != 0 && p->precond != 1) why = "precond must be 0 or 1";
     else return PGB_OK;
     return PGB_EINVAL;
 }
@@ -112,6 +115,9 @@ int pgb_default_params(pgb_params* p) {
     p->theta = 0.5;
     p->leaf_size = 32;
     p->group_size = 32;
+    p->p2p_item = 64;
+    p->m2p_item = 64;
+    p->precond = 0;
     return PGB_OK;
 }
 
@@ -130,6 +136,8 @@ int pgb_create(pgb_ctx** out, const pgb_params* p, void* stream) {
     }
     pgb_ctx* c = new (std::nothrow) pgb_ctx;
     if (!c) return PGB_ENOMEM;
+    if (q.p2p_item == 0) q.p2p_item = 64;
+    if (q.m2p_item == 0) q.m2p_item = 64;
     c->p = q;
     c->stream = (cudaStream_t)stream;
     if (cudaMallocHost(&c->h_pinned, 64) != cudaSuccess) {

@@ -76,7 +76,16 @@ __global__ void k_src_prep(Geo g, BodyDev bd, const double* __restrict__ x, int 
 // caller's layout.  mode 0: y = A x.  mode 1: right-hand side of the imposed
 // boundary terms, -(U + jump) on exterior and surface rows.  mode 2: the rows
 // with the imposed densities included, so that b - A x = b_Coulomb - y.
-__global__ void k_assemble(Geo g, BodyDev bd, const double* __restrict__ U, const double* __restrict__ dens,
+// Treecode sums of panel i: the partial sums of its group's P2P items, then
+// of its M2P items, in item order (a fixed order: the result does not depend
+// on the schedule).
+struct Parts {
+    const int32_t *pan_group, *gstart;
+    const int64_t *pitem_off, *fitem_off;
+    const double *Up, *Uf;
+};
+
+__global__ void k_assemble(Geo g, BodyDev bd, Parts u, const double* __restrict__ dens,
                            const int64_t* __restrict__ coff, const int32_t* __restrict__ cj,
                            const dbl4* __restrict__ cval, const int64_t* __restrict__ xoff,
                            const int32_t* __restrict__ xj, const dbl4* __restrict__ xval, int mode,
@@ -84,7 +93,18 @@ __global__ void k_assemble(Geo g, BodyDev bd, const double* __restrict__ U, cons
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= g.n_pan) return;
     const double inv4pi = 1.0 / PGB_FOUR_PI;
-    double UL = U[2 * i] * inv4pi, UY = U[2 * i + 1] * inv4pi;
+    const int gi = u.pan_group[i];
+    const int lane = (int)(i - u.gstart[gi]);
+    double sL = 0, sY = 0;
+    for (int64_t it = u.pitem_off[gi]; it < u.pitem_off[gi + 1]; ++it) {
+        sL += u.Up[64 * it + lane];
+        sY += u.Up[64 * it + 32 + lane];
+    }
+    for (int64_t it = u.fitem_off[gi]; it < u.fitem_off[gi + 1]; ++it) {
+        sL += u.Uf[64 * it + lane];
+        sY += u.Uf[64 * it + 32 + lane];
+    }
+    double UL = sL * inv4pi, UY = sY * inv4pi;
     for (int64_t e = coff[i]; e < coff[i + 1]; ++e) {
         const int64_t j = cj[e];
         const dbl4 d = cval[e];
@@ -155,7 +175,8 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
     const int T = n_terms(P);
     const int64_t nsrc = g.n_src;
     c->d_dens.resize(3 * c->n_pan);
-    c->d_U.resize(2 * c->n_pan);
+    c->d_Up.resize(64 * std::max<int64_t>(c->n_pitems, 1));
+    c->d_Uf.resize(64 * std::max<int64_t>(c->n_fitems, 1));
     UpArgs up;
     up.n_leaves = c->n_leaves;
     up.leaf_node = c->d_leaf_node; up.nstart = c->d_node_start; up.nend = c->d_node_end;
@@ -180,7 +201,16 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
     ev.tile_off = c->d_tile_off;
     ev.tile_d = c->d_tile_d;
     ev.tile_m = c->d_tile_m;
-    ev.U = c->d_U;
+    ev.n_pitems = c->n_pitems;
+    ev.n_fitems = c->n_fitems;
+    ev.pitem_off = c->d_pitem_off;
+    ev.fitem_off = c->d_fitem_off;
+    ev.pitem_group = c->d_pitem_group;
+    ev.fitem_group = c->d_fitem_group;
+    ev.p2p_item = c->p.p2p_item;
+    ev.m2p_item = c->p.m2p_item;
+    ev.Up = c->d_Up;
+    ev.Uf = c->d_Uf;
     const bool f32 = precision == PGB_FP32;
     if (f32) {
         c->d_src32.resize(2 * nsrc);
@@ -209,7 +239,8 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
     }
     {
         StageTimer tm(c, PGB_STAGE_ASSEMBLE + (f32 ? 0 : PGB_STAGE_FP64));
-        k_assemble<<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, c->d_U, c->d_dens, c->d_corr_off, c->d_corr_j,
+        Parts u{c->d_pan_group, c->d_group_start, c->d_pitem_off, c->d_fitem_off, c->d_Up, c->d_Uf};
+        k_assemble<<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, u, c->d_dens, c->d_corr_off, c->d_corr_j,
                                                        c->d_corr_val, c->d_xcorr_off, c->d_xcorr_j, c->d_xcorr_val,
                                                        mode, y);
         PGB_CUDA(cudaGetLastError());

@@ -157,6 +157,13 @@ struct pgb_ctx {
     pgb::DBuf<int64_t> d_tile_off;
     pgb::DBuf<float4> d_tile_d;
     pgb::DBuf<int4> d_tile_m;
+    // work items: a group's P2P tiles and its far entries in runs of at most
+    // p.p2p_item / p.m2p_item, one block each, so that no block carries a
+    // whole heavy group; each item leaves 32 (L) + 32 (Y) partial sums
+    int64_t n_pitems = 0, n_fitems = 0;
+    pgb::DBuf<int64_t> d_pitem_off, d_fitem_off;  // per group (+ total)
+    pgb::DBuf<int32_t> d_pitem_group, d_fitem_group;
+    pgb::DBuf<int32_t> d_pan_group;                // sorted panel -> its group
     // near-field corrections (CSR over sorted targets)
     // intra-body entries depend only on each body's own geometry and kappa, so
     // they survive pose changes; cross-body entries are rebuilt per pose
@@ -188,7 +195,7 @@ struct pgb_ctx {
     pgb::DBuf<double> d_dens;            // 3 per sorted panel: psiL, psiY, phi
     pgb::DBuf<float> d_mom32;            // 2*T per node
     pgb::DBuf<double> d_mom64;
-    pgb::DBuf<double> d_U;               // 2 per sorted panel: UL, UY
+    pgb::DBuf<double> d_Up, d_Uf;        // P2P / M2P partial sums: 64 per work item (32 L, then 32 Y)
     pgb::DBuf<double> d_xtmp, d_ytmp;    // FP64 staging for FP32 matvec API
     // scratch
     pgb::DBuf<int64_t> d_scan_tmp;
@@ -196,6 +203,9 @@ struct pgb_ctx {
 
     // solver
     pgb::DBuf<double> d_V, d_H, d_red, d_gv, d_b, d_bc, d_r, d_wk, d_xs, d_small;
+    pgb::DBuf<pgb::dbl4> d_pc;           // block-diagonal preconditioner, per sorted panel
+    pgb::DBuf<double> d_pz;              // its work vector
+    bool pc_ready = false;
     double* h_pinned = nullptr;
 
     // statistics and stage timing
@@ -250,6 +260,7 @@ void phi_reac(pgb_ctx* c, const double* x, double* out);
 // solver (solver.cu)
 void build_rhs(pgb_ctx* c, double* b, int precision);
 int solve(pgb_ctx* c, int mode, double tol, int max_iter, int restart, double* x, pgb_solve_stats* st);
+void precond_prepare(pgb_ctx* c);
 // energy (energy.cu)
 void energies(pgb_ctx* c, const double* x, pgb_energies* e, pgb_energies* per_body);
 void energies_noalloc(pgb_ctx* c, const double* x, pgb_energies* e);

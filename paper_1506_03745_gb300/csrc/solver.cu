@@ -183,6 +183,82 @@ __global__ void k_init_g(double* g, int m1, const double* beta) {
     if (i < m1) g[i] = (i == 0) ? *beta : 0.0;
 }
 
+// Block-diagonal preconditioner from the self terms (no equation of the
+// paper: an addition to its GMRES).  The self entry of panel i holds
+// a = V_L,ii and V_Y,ii (K_ii = 0 on a flat panel), so its own unknowns enter
+// its own rows as
+//   molecule (phi, dphi):  [[1/2, -a], [1/2, r b]],  r = eps_in/eps_out, b = V_Y,ii
+//   imposed potential (dphi2):  b;   imposed charge (phi2):  1/2.
+// pc[i] holds the inverse block (m00, m01, m10, m11).
+__global__ void k_precond_build(Geo g, BodyDev bd, const int64_t* __restrict__ coff, const int32_t* __restrict__ cj,
+                                const dbl4* __restrict__ cval, dbl4* __restrict__ pc) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= g.n_pan) return;
+    dbl4 d{0, 0, 0, 0};
+    bool found = false;
+    for (int64_t e = coff[i]; e < coff[i + 1]; ++e)
+        if (cj[e] == i) {
+            d = cval[e];
+            found = true;
+        }
+    const int b = g.pbody[i];
+    const int kind = bd.kind[b];
+    dbl4 m{1, 0, 0, 1};
+    if (found) {
+        if (kind == PGB_DIELECTRIC) {
+            const double a = d.x, rb = bd.eps_ratio[b] * d.z;
+            const double det = 0.5 * (a + rb);
+            if (det > 0) m = dbl4{rb / det, a / det, -0.5 / det, 0.5 / det};
+        } else if (kind == PGB_SET_POTENTIAL) {
+            if (d.z > 0) m = dbl4{1.0 / d.z, 0, 0, 0};
+        } else {
+            m = dbl4{2.0, 0, 0, 0};
+        }
+    }
+    pc[i] = m;
+}
+
+// z = M^{-1} v (or M^{-T} v), add: z += instead of z =; vectors in the caller's layout.
+__global__ void k_precond_apply(Geo g, BodyDev bd, const dbl4* __restrict__ pc, const double* __restrict__ v,
+                                double* __restrict__ z, int transpose, int add) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= g.n_pan) return;
+    const int b = g.pbody[i];
+    const int64_t loc = g.perm[i] - bd.pan_off[b];
+    const int64_t N = bd.pan_off[b + 1] - bd.pan_off[b];
+    const int64_t o = bd.unk_off[b];
+    const dbl4 m = pc[i];
+    if (bd.kind[b] == PGB_DIELECTRIC) {
+        const double v1 = v[o + loc], v2 = v[o + N + loc];
+        const double m01 = transpose ? m.z : m.y, m10 = transpose ? m.y : m.z;
+        const double z1 = m.x * v1 + m01 * v2, z2 = m10 * v1 + m.w * v2;
+        z[o + loc] = add ? z[o + loc] + z1 : z1;
+        z[o + N + loc] = add ? z[o + N + loc] + z2 : z2;
+    } else {
+        const double z1 = m.x * v[o + loc];
+        z[o + loc] = add ? z[o + loc] + z1 : z1;
+    }
+}
+
+void precond_prepare(pgb_ctx* c) {
+    c->pc_ready = false;
+    if (!c->p.precond) return;
+    c->d_pc.resize(c->n_pan);
+    c->d_pz.resize(c->n_unk);
+    k_precond_build<<<nblk(c->n_pan, 128), 128, 0, c->stream>>>(geo(c), body_dev(c), c->d_corr_off, c->d_corr_j,
+                                                                c->d_corr_val, c->d_pc);
+    PGB_CUDA(cudaGetLastError());
+    PGB_LAUNCHED(c, 1);
+    c->pc_ready = true;
+}
+
+static void precond_apply(pgb_ctx* c, const double* v, double* z, bool transpose, bool add) {
+    k_precond_apply<<<nblk(c->n_pan, 128), 128, 0, c->stream>>>(geo(c), body_dev(c), c->d_pc, v, z,
+                                                                transpose ? 1 : 0, add ? 1 : 0);
+    PGB_CUDA(cudaGetLastError());
+    PGB_LAUNCHED(c, 1);
+}
+
 struct Krylov {
     pgb_ctx* c;
     int64_t n;
@@ -205,9 +281,17 @@ struct Krylov {
 // iterations.  Returns iterations done; *matvecs counts operator uses.
 int gmres_op(pgb_ctx* c, int prec, bool transpose, const double* b, double* x, double abs_tol, int max_it,
              int restart, int* matvecs, double* est_out, bool x_zero) {
+    const bool pc = c->p.precond && c->pc_ready;
     auto apply = [&](const double* in, double* out) {
         if (transpose) apply_transpose(c, in, out, prec);
         else apply_operator(c, in, out, prec, false);
+    };
+    // right preconditioning: the Krylov space is built on A M^{-1}, the
+    // residual b - A x (and so the stopping test) is the unpreconditioned one
+    auto apply_pc = [&](const double* in, double* out) {
+        if (!pc) return apply(in, out);
+        precond_apply(c, in, c->d_pz, transpose, false);
+        apply(c->d_pz, out);
     };
     const int64_t n = c->n_unk;
     const int m = restart;
@@ -249,7 +333,7 @@ int gmres_op(pgb_ctx* c, int prec, bool transpose, const double* b, double* x, d
         for (; j < m && it < max_it; ++j, ++it) {
             double* vj = c->d_V.p + (size_t)j * n;
             double* w = c->d_wk.p;
-            apply(vj, w);
+            apply_pc(vj, w);
             ++*matvecs;
             double* h = c->d_H.p + (size_t)j * (m + 1);
             {
@@ -278,7 +362,13 @@ int gmres_op(pgb_ctx* c, int prec, bool transpose, const double* b, double* x, d
             }
         }
         k_backsolve<<<1, 1, 0, s>>>(c->d_H, m + 1, g, j, yv);
-        k_multi_axpy<<<nblk(n, 256), 256, 0, s>>>(c->d_V, n, j, yv, 1.0, x, n);
+        if (pc) {  // x += M^{-1} V y
+            PGB_CUDA(cudaMemsetAsync(c->d_pz.p, 0, 8 * n, s));
+            k_multi_axpy<<<nblk(n, 256), 256, 0, s>>>(c->d_V, n, j, yv, 1.0, c->d_pz, n);
+            precond_apply(c, c->d_pz, x, transpose, true);
+        } else {
+            k_multi_axpy<<<nblk(n, 256), 256, 0, s>>>(c->d_V, n, j, yv, 1.0, x, n);
+        }
         PGB_CUDA(cudaGetLastError());
         PGB_LAUNCHED(c, 2);
         if (est <= abs_tol) break;
@@ -325,6 +415,7 @@ int solve(pgb_ctx* c, int mode, double tol, int max_iter, int restart, double* x
         fail(PGB_EINVAL, "mode must be PGB_FP64, PGB_FP32_REFINE or PGB_FP32");
     const int rhs_prec = mode == PGB_FP64 ? PGB_FP64 : PGB_FP32;
     build_rhs(c, c->d_b, rhs_prec);
+    precond_prepare(c);
     pgb_solve_stats z{};
     int known_mv = 0;
     for (auto& b : c->bodies)

@@ -994,6 +994,24 @@ __global__ void k_tile_fill(int64_t ng, const int64_t* noff, const int32_t* near
     }
 }
 
+// Work items per group: ceil(tiles / p2p_item) for P2P and
+// ceil(far entries / m2p_item) for M2P.
+__global__ void k_item_count(int64_t ng, const int64_t* toff, const int64_t* foff, int pi, int fi, int64_t* pc,
+                             int64_t* fc) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    pc[g] = (toff[g + 1] - toff[g] + pi - 1) / pi;
+    fc[g] = (foff[g + 1] - foff[g] + fi - 1) / fi;
+}
+__global__ void k_item_fill(int64_t ng, const int64_t* poff, const int64_t* foff, const int32_t* gstart,
+                            const int32_t* gend, int32_t* pg, int32_t* fg, int32_t* pan_group) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    for (int64_t i = poff[g]; i < poff[g + 1]; ++i) pg[i] = (int32_t)g;
+    for (int64_t i = foff[g]; i < foff[g + 1]; ++i) fg[i] = (int32_t)g;
+    for (int32_t p = gstart[g]; p < gend[g]; ++p) pan_group[p] = (int32_t)g;
+}
+
 void make_lists(pgb_ctx* c, const double* r2, const double* glo, const double* ghi, DBuf<int64_t>& noff,
                 DBuf<int32_t>& nearl, DBuf<int64_t>& foff, DBuf<int32_t>& farl, DBuf<float4>& near4,
                 DBuf<float4>& far4, int64_t& n_near, int64_t& n_far, unsigned long long* stats4) {
@@ -1071,9 +1089,31 @@ void build_lists(pgb_ctx* c) {
                                                   c->d_group_body, body_dev(c), c->p.K, c->d_tile_off, c->d_tile_d,
                                                   c->d_tile_m);
         PGB_CUDA(cudaGetLastError());
+    }
+    {
+        DBuf<int64_t> pc, fc;
+        pc.resize(ng);
+        fc.resize(ng);
+        c->d_pitem_off.resize(ng + 1);
+        c->d_fitem_off.resize(ng + 1);
+        k_item_count<<<nblk(ng, 128), 128, 0, s>>>(ng, c->d_tile_off, c->d_far_off, c->p.p2p_item, c->p.m2p_item,
+                                                   pc, fc);
+        int64_t np = 0, nf = 0;
+        exclusive_scan_i64(pc, c->d_pitem_off, ng, s, &np);
+        exclusive_scan_i64(fc, c->d_fitem_off, ng, s, &nf);
+        PGB_CUDA(cudaMemcpyAsync(c->d_pitem_off.p + ng, &np, 8, cudaMemcpyHostToDevice, s));
+        PGB_CUDA(cudaMemcpyAsync(c->d_fitem_off.p + ng, &nf, 8, cudaMemcpyHostToDevice, s));
+        c->n_pitems = np;
+        c->n_fitems = nf;
+        c->d_pitem_group.resize(std::max<int64_t>(np, 1));
+        c->d_fitem_group.resize(std::max<int64_t>(nf, 1));
+        c->d_pan_group.resize(c->n_pan);
+        k_item_fill<<<nblk(ng, 128), 128, 0, s>>>(ng, c->d_pitem_off, c->d_fitem_off, c->d_group_start,
+                                                  c->d_group_end, c->d_pitem_group, c->d_fitem_group, c->d_pan_group);
+        PGB_CUDA(cudaGetLastError());
         PGB_CUDA(cudaStreamSynchronize(s));
     }
-    PGB_LAUNCHED(c, 2);
+    PGB_LAUNCHED(c, 4);
 }
 
 // ---------------------------------------------------------------- corrections

@@ -144,7 +144,12 @@ struct EvalArgs {
     const int64_t* tile_off;       // per group: its P2P tiles [tile_off[g], tile_off[g+1])
     const float4* tile_d;          // per tile: leaf centre - group centre (FP32), first point (int bits)
     const int4* tile_m;            // per tile: leaf node, point count, flags (1 Laplace, 2 own panel), body
-    double* U;                     // 2 per sorted panel
+    // work items (a group's tiles / far entries in runs of p2p_item / m2p_item)
+    int64_t n_pitems, n_fitems;
+    const int64_t *pitem_off, *fitem_off;  // per group
+    const int32_t *pitem_group, *fitem_group;
+    int p2p_item, m2p_item;
+    double *Up, *Uf;               // per item: 32 Laplace then 32 Yukawa partial sums (one per lane)
 };
 
 // Far-field contraction sum_k G_k(R) M_k for one target (returns Yukawa and,
@@ -304,11 +309,33 @@ __device__ __forceinline__ void entry_offset<double>(const EvalArgs& a, int64_t 
     oz = a.ncenter[3 * nd + 2] - gc2;
 }
 
-// P2P: one block of NW warps per target group (32 targets, one per lane); the
-// group's source tiles (up to 32 quadrature points of one near leaf) are dealt
-// round robin to the warps, the next tile prefetched into registers.  Partial
-// sums are combined in warp order and written to U (the far field is added by
-// k_m2p afterwards).
+// Partial sums of the NW warps of a block combined in warp order (each warp
+// carries a compensated pair per kernel) and stored per lane for the item.
+template <typename real, int NW>
+__device__ __forceinline__ void store_item(real (*red)[4][32], int w, int lane, real UL, real cL, real UY, real cY,
+                                           double* out) {
+    red[w][0][lane] = UL;
+    red[w][1][lane] = cL;
+    red[w][2][lane] = UY;
+    red[w][3][lane] = cY;
+    __syncthreads();
+    if (w == 0) {
+        real sL = 0, eL = 0, sY = 0, eY = 0;
+        for (int k = 0; k < NW; ++k) {
+            kadd(sL, eL, red[k][0][lane]);
+            kadd(sL, eL, red[k][1][lane]);
+            kadd(sY, eY, red[k][2][lane]);
+            kadd(sY, eY, red[k][3][lane]);
+        }
+        out[lane] = (double)sL + (double)eL;
+        out[32 + lane] = (double)sY + (double)eY;
+    }
+}
+
+// P2P: one block of NW warps per work item, i.e. up to p2p_item source tiles
+// (up to 32 quadrature points of one near leaf each) of one target group (32
+// targets, one per lane); the tiles are dealt round robin to the warps, the
+// next tile prefetched into registers.  The item's partial sums go to Up.
 template <typename real, int NW>
 __global__ void __launch_bounds__(NW * 32) k_p2p(EvalArgs a,
                                                                     const typename V4<real>::t* __restrict__ src,
@@ -317,8 +344,9 @@ __global__ void __launch_bounds__(NW * 32) k_p2p(EvalArgs a,
     __shared__ v4 sA[NW][32], sB[NW][32];
     __shared__ real red[NW][4][32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t g = blockIdx.x;
-    if (g >= a.n_groups) return;
+    const int64_t it = blockIdx.x;
+    if (it >= a.n_pitems) return;
+    const int64_t g = a.pitem_group[it];
     const int64_t p0 = a.gstart[g], p1 = a.gend[g];
     const int64_t p = p0 + lane;
     const bool active = p < p1;
@@ -327,8 +355,9 @@ __global__ void __launch_bounds__(NW * 32) k_p2p(EvalArgs a,
     const real kappa = (real)a.kappa;
     const int64_t own_lo = p * a.K, own_hi = own_lo + a.K;
     real UL = 0, cL = 0, UY = 0, cY = 0;
-    const int64_t t1 = a.tile_off[g + 1];
-    int64_t t = a.tile_off[g] + w;
+    const int64_t tb = a.tile_off[g] + (it - a.pitem_off[g]) * a.p2p_item;
+    const int64_t t1 = min(a.tile_off[g + 1], tb + a.p2p_item);
+    int64_t t = tb + w;
     v4 pa = v4(), pb = v4();
     int4 m = make_int4(0, 0, 0, 0);
     float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -385,26 +414,12 @@ __global__ void __launch_bounds__(NW * 32) k_p2p(EvalArgs a,
         kadd(UL, cL, sumL);
         kadd(UY, cY, sumY);
     }
-    red[w][0][lane] = UL;
-    red[w][1][lane] = cL;
-    red[w][2][lane] = UY;
-    red[w][3][lane] = cY;
-    __syncthreads();
-    if (w == 0 && active) {
-        real sL = 0, eL = 0, sY = 0, eY = 0;
-        for (int k = 0; k < NW; ++k) {
-            kadd(sL, eL, red[k][0][lane]);
-            kadd(sL, eL, red[k][1][lane]);
-            kadd(sY, eY, red[k][2][lane]);
-            kadd(sY, eY, red[k][3][lane]);
-        }
-        a.U[2 * p] = (double)sL + (double)eL;
-        a.U[2 * p + 1] = (double)sY + (double)eY;
-    }
+    store_item<real, NW>(red, w, lane, UL, cL, UY, cY, a.Up + 64 * it);
 }
 
-// M2P: one block of NW warps per target group; far nodes round robin over the
-// warps with the next node's moments prefetched; adds to the P2P result in U.
+// M2P: one block of NW warps per work item, i.e. up to m2p_item far entries of
+// one target group; the nodes go round robin to the warps with the next
+// node's moments prefetched.  The item's partial sums go to Uf.
 template <typename real, int P, int NW>
 __global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a, const typename V4<real>::t* __restrict__ xrel,
                                                   const real* __restrict__ mom) {
@@ -414,8 +429,9 @@ __global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a, const typename V4<r
     __shared__ real sM[NW][2 * T];
     __shared__ real red[NW][4][32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t g = blockIdx.x;
-    if (g >= a.n_groups) return;
+    const int64_t it = blockIdx.x;
+    if (it >= a.n_fitems) return;
+    const int64_t g = a.fitem_group[it];
     const int64_t p0 = a.gstart[g], p1 = a.gend[g];
     const int64_t p = p0 + lane;
     const bool active = p < p1;
@@ -424,7 +440,8 @@ __global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a, const typename V4<r
     const int gb = a.gbody[g];
     const real kappa = (real)a.kappa;
     real UL = 0, cL = 0, UY = 0, cY = 0;
-    const int64_t f1 = a.far_off[g + 1];
+    const int64_t fb = a.far_off[g] + (it - a.fitem_off[g]) * a.m2p_item;
+    const int64_t f1 = min(a.far_off[g + 1], fb + a.m2p_item);
     auto seek = [&](int64_t ee) -> int64_t {  // next active entry of this warp
         while (ee < f1) {
             int nn;
@@ -438,7 +455,7 @@ __global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a, const typename V4<r
     real pm[MW];
     int nd = -1;
     real ox = 0, oy = 0, oz = 0;
-    int64_t e = seek(a.far_off[g] + w);
+    int64_t e = seek(fb + w);
     if (e < f1) {
         entry_offset<real>(a, e, true, gc0, gc1, gc2, nd, ox, oy, oz);
 #pragma unroll
@@ -471,22 +488,7 @@ __global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a, const typename V4<r
         kadd(UL, cL, uL);
         kadd(UY, cY, uY);
     }
-    red[w][0][lane] = UL;
-    red[w][1][lane] = cL;
-    red[w][2][lane] = UY;
-    red[w][3][lane] = cY;
-    __syncthreads();
-    if (w == 0 && active) {
-        real sL = 0, eL = 0, sY = 0, eY = 0;
-        for (int k = 0; k < NW; ++k) {
-            kadd(sL, eL, red[k][0][lane]);
-            kadd(sL, eL, red[k][1][lane]);
-            kadd(sY, eY, red[k][2][lane]);
-            kadd(sY, eY, red[k][3][lane]);
-        }
-        a.U[2 * p] += (double)sL + (double)eL;
-        a.U[2 * p + 1] += (double)sY + (double)eY;
-    }
+    store_item<real, NW>(red, w, lane, UL, cL, UY, cY, a.Uf + 64 * it);
 }
 
 struct UpArgs {

@@ -20,10 +20,10 @@ static void launch_p(int stage, const UpArgs& up, const std::vector<int64_t>& up
         }
     }
     constexpr int NW = 8;
-    if (stage == PGB_STAGE_P2P && ev.n_groups > 0)
-        k_p2p<real, 8><<<(unsigned)ev.n_groups, 8 * 32, 0, s>>>(ev, (const v4*)src, (const v4*)xrel);
-    if (stage == PGB_STAGE_M2P && ev.n_groups > 0)
-        k_m2p<real, P, NW><<<(unsigned)ev.n_groups, NW * 32, 0, s>>>(ev, (const v4*)xrel, (const real*)mom);
+    if (stage == PGB_STAGE_P2P && ev.n_pitems > 0)
+        k_p2p<real, 8><<<(unsigned)ev.n_pitems, 8 * 32, 0, s>>>(ev, (const v4*)src, (const v4*)xrel);
+    if (stage == PGB_STAGE_M2P && ev.n_fitems > 0)
+        k_m2p<real, P, NW><<<(unsigned)ev.n_fitems, NW * 32, 0, s>>>(ev, (const v4*)xrel, (const real*)mom);
 }
 
 }  // namespace pgb

@@ -45,6 +45,13 @@ def test_argument_errors_need_no_device(libpgb):
     p = L.pgb_params()
     assert lib.pgb_default_params(ctypes.byref(p)) == 0
     assert (p.K, p.K_near, p.n_edge, p.P, p.theta, p.leaf_size) == (7, 19, 9, 6, 0.5, 32)
+    assert (p.p2p_item, p.m2p_item) == (64, 64)
+    for f, v in (("p2p_item", 5000), ("m2p_item", -1)):
+        q = L.pgb_params()
+        lib.pgb_default_params(ctypes.byref(q))
+        setattr(q, f, v)
+        h0 = ctypes.c_void_p()
+        assert lib.pgb_create(ctypes.byref(h0), ctypes.byref(q), None) == L.PGB_EINVAL
     bad = L.pgb_params(K=5, K_near=19, n_edge=9, P=6, theta=0.5, leaf_size=32, group_size=32)
     h = ctypes.c_void_p()
     assert lib.pgb_create(ctypes.byref(h), ctypes.byref(bad), None) == L.PGB_EINVAL

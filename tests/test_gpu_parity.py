@@ -85,6 +85,28 @@ def test_treecode_matches_oracle_treecode(case, theta, P):
         pgb.pgb_destroy(ctx)
 
 
+@pytest.mark.parametrize("items", [(1, 1), (3, 5)])
+def test_work_items_split_groups(items):
+    """Groups cut into many P2P / M2P work items (down to one tile or one far
+    node per block) give the oracle treecode's product."""
+    bodies = spheres(**CASES["sigma_pair"])
+    so = oracle_system(bodies, theta=0.5, P=6, leaf_size=8)
+    ctx = gpu_context(bodies, theta=0.5, P=6, leaf_size=8, p2p_item=items[0], m2p_item=items[1])
+    ref_ctx = gpu_context(bodies, theta=0.5, P=6, leaf_size=8)
+    try:
+        x = np.random.default_rng(5).normal(size=so.n)
+        ref = TreecodeOperator(so).apply(x)
+        scale = np.abs(ref).max()
+        y64 = _matvec(ctx, x, pgb.PGB_FP64)
+        assert np.abs(y64 - ref).max() / scale < 1e-10
+        assert np.abs(y64 - _matvec(ref_ctx, x, pgb.PGB_FP64)).max() / scale < 1e-13
+        y32 = _matvec(ctx, x, pgb.PGB_FP32)
+        assert np.abs(y32 - ref).max() / scale < 5e-6
+    finally:
+        pgb.pgb_destroy(ctx)
+        pgb.pgb_destroy(ref_ctx)
+
+
 def _node_ids(tc):
     """Map oracle per-body DFS node indices to the library's level-order ids
     (roots first, then each level's children in parent order, key order)."""
