@@ -218,8 +218,7 @@ def reduce_across_ranks(dist, total_ms, matvecs, device):
 def run_gpu(args):
     import torch
     import paper_1506_03745_gb300 as pgb
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from problems import gpu_context
+    from paper_1506_03745_gb300.context import context as gpu_context
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -419,8 +418,7 @@ def run_star(args):
     refinement (tol 1e-6) against the plain FP64 solve on the same GPU."""
     import torch
     import paper_1506_03745_gb300 as pgb
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from problems import gpu_context
+    from paper_1506_03745_gb300.context import context as gpu_context
     rows = []
     for dens in (2, 4, 8):
         body = star_bodies(dens)
@@ -455,8 +453,7 @@ def run_gradient(args):
     r = 40 A (30420 panels, sigma -0.05 C/m^2): adjoint gradient time."""
     import torch
     import paper_1506_03745_gb300 as pgb
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from problems import gpu_context
+    from paper_1506_03745_gb300.context import context as gpu_context
     mol = star_bodies(2)
     srf = sphere_body()
     D = place_for_gap(mol["verts"], np.eye(3), 40.0, 10.0)
@@ -496,8 +493,7 @@ def run_poses(args):
     import torch
     import synth
     import paper_1506_03745_gb300 as pgb
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from problems import gpu_context
+    from paper_1506_03745_gb300.context import context as gpu_context
     nu = int(round(math.sqrt(5000 / 20)))
     v, f = synth.star_surface(100, nu)
     coeffs = synth.star_coefficients(100)
@@ -537,6 +533,7 @@ def precond_solve(pgb, bodies, dev, stream, flush, e64, steps=3):
     median device ms over `steps` steps after one warm-up, its iterations and
     the energy difference to the unpreconditioned FP64 solve."""
     import torch
+    from paper_1506_03745_gb300.context import context as gpu_context
     ctx = gpu_context(bodies, **dict(PARAMS, precond=1))
     n = pgb.pgb_num_unknowns(ctx)
     x = torch.empty(n, dtype=torch.float64, device=dev)
@@ -566,8 +563,7 @@ def run_matvec(args):
     workload (tree built once, untimed); prints matvecs/s and per-stage times."""
     import torch
     import paper_1506_03745_gb300 as pgb
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from problems import gpu_context
+    from paper_1506_03745_gb300.context import context as gpu_context
     dev = torch.device("cuda", 0)
     ctx = gpu_context(workload_bodies(), **PARAMS)
     n = pgb.pgb_num_unknowns(ctx)
@@ -611,9 +607,11 @@ def main():
     ap.add_argument("--p2p-item", type=int, default=None, help="override P2P tiles per work item (sweeps)")
     ap.add_argument("--m2p-item", type=int, default=None, help="override far nodes per M2P work item (sweeps)")
     ap.add_argument("--precond", type=int, default=None, help="1: block-diagonal GMRES preconditioner")
+    ap.add_argument("--graphs", type=int, default=None, help="0: plain launches instead of the upward-pass graph")
     args = ap.parse_args()
     for k, v in (("leaf_size", args.leaf), ("P", args.P), ("theta", args.theta), ("p2p_item", args.p2p_item),
-                 ("m2p_item", args.m2p_item), ("precond", args.precond)):
+                 ("m2p_item", args.m2p_item), ("precond", args.precond),
+                 ("graphs", args.graphs)):
         if v is not None:
             PARAMS[k] = v
     if args.impl == "reference":

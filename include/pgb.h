@@ -69,6 +69,8 @@ typedef struct pgb_params {
     int32_t precond;      /* GMRES preconditioner: 0 none (the paper's solver), 1 block-diagonal: per
                              panel, the inverse of the 2x2 (molecule) or 1x1 (surface) block of its own
                              self terms, applied on the right so the residual test is unchanged */
+    int32_t graphs;       /* 1 (default): the upward pass (P2M + one launch per tree level) is captured
+                             once per tree as a CUDA graph and replayed; 0: plain launches */
 } pgb_params;
 
 typedef struct pgb_solve_stats {
@@ -122,7 +124,7 @@ typedef struct pgb_stage_times {
 
 /* Create a context on the current CUDA device.  p may be NULL (defaults:
  * K=7, K_near=19, n_edge=9, P=6, theta=0.5, leaf_size=32, group_size=32,
- * p2p_item=64, m2p_item=64, precond=0).
+ * p2p_item=64, m2p_item=64, precond=0, graphs=1).
  * cuda_stream is a cudaStream_t (NULL = legacy default stream).  Returns
  * PGB_EINVAL for out-of-range parameters. */
 int pgb_create(struct pgb_ctx** ctx, const pgb_params* p, void* cuda_stream);

@@ -21,7 +21,7 @@ c_i32, c_i64, c_dbl, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, cty
 class pgb_params(ctypes.Structure):
     _fields_ = [("K", c_i32), ("K_near", c_i32), ("n_edge", c_i32), ("P", c_i32), ("theta", c_dbl),
                 ("leaf_size", c_i32), ("group_size", c_i32), ("p2p_item", c_i32), ("m2p_item", c_i32),
-                ("precond", c_i32)]
+                ("precond", c_i32), ("graphs", c_i32)]
 
 
 class pgb_solve_stats(ctypes.Structure):

@@ -100,6 +100,7 @@ static int check_params(const pgb_params* p, std::string& why) {
     else if (p->p2p_item < 0 || p->p2p_item > 4096) why = "p2p_item must be in 1..4096 (0 = default)";
     else if (p->m2p_item < 0 || p->m2p_item > 4096) why = "m2p_item must be in 1..4096 (0 = default)";
     else if (p->precond != 0 && p->precond != 1) why = "precond must be 0 or 1";
+    else if (p->graphs != 0 && p->graphs != 1) why = "graphs must be 0 or 1";
     else return PGB_OK;
     return PGB_EINVAL;
 }
@@ -118,6 +119,7 @@ int pgb_default_params(pgb_params* p) {
     p->p2p_item = 64;
     p->m2p_item = 64;
     p->precond = 0;
+    p->graphs = 1;
     return PGB_OK;
 }
 
@@ -157,6 +159,9 @@ int pgb_destroy(pgb_ctx* c) {
         cudaEventDestroy(p.second.second);
     }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
+    for (auto& gr : c->up_graph)
+        if (gr.exec) cudaGraphExecDestroy(gr.exec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     delete c;
     return PGB_OK;

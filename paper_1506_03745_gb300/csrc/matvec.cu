@@ -162,6 +162,50 @@ void apply_operator(pgb_ctx* c, const double* x, double* y, int precision, bool 
 
 void apply_full(pgb_ctx* c, const double* x, double* y, int precision) { apply_mode(c, x, y, precision, 2, nullptr); }
 
+// Upward pass as a CUDA graph: captured (on a private stream; nothing runs
+// there) the first time a tree / buffer / source-activity combination is
+// used, then one cudaGraphLaunch on the context stream per product.
+static void upward_graph(pgb_ctx* c, bool f32, const UpArgs& up, const EvalArgs& ev, const void* src, void* mom) {
+    auto& gr = c->up_graph[f32 ? 0 : 1];
+    bool ok = gr.exec && gr.tree_gen == c->tree_gen && gr.src == src && gr.mom == mom && gr.ncenter == up.ncenter;
+    for (int b = 0; ok && b < PGB_MAX_BODIES; ++b) ok = gr.src_active[b] == up.src_active[b];
+    if (!ok) {
+        if (gr.exec) {
+            PGB_CUDA(cudaGraphExecDestroy(gr.exec));
+            gr.exec = nullptr;
+        }
+        if (!c->cap_stream) PGB_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        PGB_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        std::string why;
+        try {
+            if (f32) treecode_launch_f32(PGB_STAGE_UPWARD, c->p.P, up, c->level_begin, ev, src, nullptr, mom, c->cap_stream);
+            else treecode_launch_f64(PGB_STAGE_UPWARD, c->p.P, up, c->level_begin, ev, src, nullptr, mom, c->cap_stream);
+        } catch (const Error& e) {
+            why = e.msg;
+        }
+        const cudaError_t le = cudaGetLastError();
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &graph);
+        if (!why.empty() || le != cudaSuccess || ce != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            (void)cudaGetLastError();
+            fail(PGB_ECUDA, "upward-pass graph capture: " + (why.empty() ? std::string(cudaGetErrorString(
+                                                                               le != cudaSuccess ? le : ce))
+                                                                          : why));
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&gr.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) gr.exec = nullptr;
+        PGB_CUDA(ie);
+        gr.tree_gen = c->tree_gen;
+        gr.src = src;
+        gr.mom = mom;
+        gr.ncenter = up.ncenter;
+        for (int b = 0; b < PGB_MAX_BODIES; ++b) gr.src_active[b] = up.src_active[b];
+    }
+    PGB_CUDA(cudaGraphLaunch(gr.exec, c->stream));
+}
+
 void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode, const int* known_mask) {
     const bool known_only = mode == 1;
     if (!c->tree_valid) fail(PGB_ESTATE, "pgb_tree_build has not run for the current bodies and poses");
@@ -232,7 +276,10 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
     }
     for (int stage : {PGB_STAGE_UPWARD, PGB_STAGE_P2P, PGB_STAGE_M2P}) {
         StageTimer tm(c, stage + (f32 ? 0 : PGB_STAGE_FP64));
-        if (f32) treecode_launch_f32(stage, P, up, c->level_begin, ev, c->d_src32, c->d_x32, c->d_mom32, s);
+        if (stage == PGB_STAGE_UPWARD && c->p.graphs)
+            upward_graph(c, f32, up, ev, f32 ? (const void*)c->d_src32.p : (const void*)c->d_src64.p,
+                         f32 ? (void*)c->d_mom32.p : (void*)c->d_mom64.p);
+        else if (f32) treecode_launch_f32(stage, P, up, c->level_begin, ev, c->d_src32, c->d_x32, c->d_mom32, s);
         else treecode_launch_f64(stage, P, up, c->level_begin, ev, c->d_src64, c->d_x64, c->d_mom64, s);
         PGB_CUDA(cudaGetLastError());
         PGB_LAUNCHED(c, stage == PGB_STAGE_UPWARD ? (int64_t)c->level_begin.size() - 2 : 1);

@@ -172,6 +172,7 @@ struct pgb_ctx {
     pgb::DBuf<int64_t> d_corr_off, d_xcorr_off;
     pgb::DBuf<int32_t> d_corr_j, d_xcorr_j;
     pgb::DBuf<pgb::dbl4> d_corr_val, d_xcorr_val;  // dVL, dKL, dVY, dKY
+    pgb::DBuf<double> d_yfine;             // 19-point nodes per panel (3 each), for the corrections
     pgb::DBuf<double> d_xbatch;            // solution buffer of pgb_solve_batch
     // adjoint (transposed treecode): built on first use after each tree build
     bool adj_valid = false;
@@ -207,6 +208,19 @@ struct pgb_ctx {
     pgb::DBuf<double> d_pz;              // its work vector
     bool pc_ready = false;
     double* h_pinned = nullptr;
+
+    // upward pass captured as a CUDA graph per precision, replayed on the
+    // context stream; recaptured when the tree or a buffer it uses changes
+    struct UpGraph {
+        cudaGraphExec_t exec = nullptr;
+        uint64_t tree_gen = 0;
+        const void* src = nullptr;
+        void* mom = nullptr;
+        const double* ncenter = nullptr;
+        int src_active[PGB_MAX_BODIES] = {0};
+    } up_graph[2];
+    cudaStream_t cap_stream = nullptr;   // capture only (nothing runs on it)
+    uint64_t tree_gen = 0;               // bumped whenever the octree structure is rebuilt
 
     // statistics and stage timing
     bool timing = false;

@@ -391,6 +391,7 @@ __global__ void k_pan_leaf(const int32_t* leaf_node, const int32_t* start, const
 }
 
 void build_order(pgb_ctx* c) {
+    ++c->tree_gen;  // node structure and level ranges change: recapture graphs
     cudaStream_t s = c->stream;
     int64_t n = c->n_pan;
     int nb = (int)c->bodies.size();
@@ -1166,6 +1167,8 @@ __global__ void k_corr_find(CorrArgs a, int64_t n, bool fill, bool cross, const 
 
 // Kernel values at a target x from a source point y with normal n (no 1/4pi);
 // 1/r by two Newton steps (FP64 rounding), e^{-kappa r} by exp2_taylor.
+// Without LAP only the Yukawa pair (vy, ky) is formed.
+template <bool LAP>
 __device__ __forceinline__ void kern4(const double* x, const double* y, const double* n, double kappa, double w,
                                       double& vl, double& kl, double& vy, double& ky) {
     double dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
@@ -1176,10 +1179,35 @@ __device__ __forceinline__ void kern4(const double* x, const double* y, const do
     double nd = n[0] * dx + n[1] * dy + n[2] * dz;
     double e = exp2_taylor(-kappa * 1.4426950408889634 * r);
     double ri3 = ri * ri * ri;
-    vl += w * ri;
-    kl += w * nd * ri3;
+    if (LAP) {
+        vl += w * ri;
+        kl += w * nd * ri3;
+    }
     vy += w * e * ri;
     ky += w * nd * (1.0 + kappa * r) * e * ri3;
+}
+
+// Fine-rule (19-point) nodes of every panel, mapped like the K-point nodes.
+__global__ void k_fine_nodes(int64_t n, const double* V, const double* C, Rules r, double* YF) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n * r.Kn) return;
+    const int64_t j = t / r.Kn;
+    const int m = (int)(t - j * r.Kn);
+    const double* v = V + 9 * j;
+    const double* cjp = C + 3 * j;
+    for (int a = 0; a < 3; ++a)
+        YF[3 * t + a] = cjp[a] + ((r.mun[m][0] * (v[a] - cjp[a]) + r.mun[m][1] * (v[3 + a] - cjp[a])) +
+                                  r.mun[m][2] * (v[6 + a] - cjp[a]));
+}
+
+template <bool LAP>
+__device__ __forceinline__ void corr_sums(const double* x, const double* nj, int64_t j, const double* YF,
+                                          const double* Y, const double* W, double Aj, const Rules& r, double kappa,
+                                          double* tv, double* kv) {
+    for (int m = 0; m < r.Kn; ++m)
+        kern4<LAP>(x, YF + 3 * (j * r.Kn + m), nj, kappa, r.wn[m] * Aj, tv[0], tv[1], tv[2], tv[3]);
+    for (int m = 0; m < r.K; ++m)
+        kern4<LAP>(x, Y + 3 * (j * r.K + m), nj, kappa, W[j * r.K + m], kv[0], kv[1], kv[2], kv[3]);
 }
 
 __device__ __forceinline__ int64_t owner_row(const int64_t* off, int64_t n, int64_t e) {
@@ -1193,8 +1221,9 @@ __device__ __forceinline__ int64_t owner_row(const int64_t* off, int64_t n, int6
 }
 
 // Correction entries (i, j), j != i: 19-point rule minus the K-point sum,
-// for V_L, K_L, V_Y, K_Y (Section 3.1), FP64, one thread per entry.
-__global__ void k_corr_values(int64_t n, int64_t tot, const int64_t* off, const int32_t* cj, const double* V,
+// for V_L, K_L, V_Y, K_Y (Section 3.1), FP64, one thread per entry; the
+// Laplace pair only where it enters a row (same dielectric body).
+__global__ void k_corr_values(int64_t n, int64_t tot, const int64_t* off, const int32_t* cj, const double* YF,
                               const double* C, const double* Nn, const double* A, const double* Y, const double* W,
                               const int32_t* pbody, BodyDev bd, Rules r, double kappa, dbl4* out) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1204,22 +1233,13 @@ __global__ void k_corr_values(int64_t n, int64_t tot, const int64_t* off, const 
     if (j == i) return;  // self entries: k_corr_self
     const double* x = C + 3 * i;
     const double* nj = Nn + 3 * j;
-    const double* v = V + 9 * j;
-    const double* cjp = C + 3 * j;
-    double tv[4] = {0, 0, 0, 0};
-    for (int m = 0; m < r.Kn; ++m) {
-        double y[3];
-        for (int a = 0; a < 3; ++a)
-            y[a] = cjp[a] + ((r.mun[m][0] * (v[a] - cjp[a]) + r.mun[m][1] * (v[3 + a] - cjp[a])) +
-                             r.mun[m][2] * (v[6 + a] - cjp[a]));
-        kern4(x, y, nj, kappa, r.wn[m] * A[j], tv[0], tv[1], tv[2], tv[3]);
-    }
-    double kv[4] = {0, 0, 0, 0};
-    for (int m = 0; m < r.K; ++m) kern4(x, Y + 3 * (j * r.K + m), nj, kappa, W[j * r.K + m], kv[0], kv[1], kv[2], kv[3]);
+    const int bi = pbody[i], bj = pbody[j];
+    const bool lap = bi == bj && bd.kind[bi] == PGB_DIELECTRIC;
+    double tv[4] = {0, 0, 0, 0}, kv[4] = {0, 0, 0, 0};
+    if (lap) corr_sums<true>(x, nj, j, YF, Y, W, A[j], r, kappa, tv, kv);
+    else corr_sums<false>(x, nj, j, YF, Y, W, A[j], r, kappa, tv, kv);
     double d[4];
     for (int q = 0; q < 4; ++q) d[q] = (tv[q] - kv[q]) / PGB_FOUR_PI;
-    const int bi = pbody[i], bj = pbody[j];
-    if (bi != bj || bd.kind[bi] != PGB_DIELECTRIC) d[0] = d[1] = 0.0;
     out[e] = dbl4{d[0], d[1], d[2], d[3]};
 }
 
@@ -1300,7 +1320,9 @@ static void build_corr_part(pgb_ctx* c, bool cross, DBuf<int64_t>& off, DBuf<int
     if (tot) {
         k_corr_find<<<nblk(n, 64), 64, 0, s>>>(a, n, true, cross, c->d_pbody, nullptr, off, cj);
         Rules r = make_rules(c->p.K, c->p.K_near, c->p.n_edge);
-        k_corr_values<<<nblk(tot, 128), 128, 0, s>>>(n, tot, off, cj, c->d_v, c->d_c, c->d_n, c->d_A, c->d_y,
+        c->d_yfine.resize(3 * n * r.Kn);
+        k_fine_nodes<<<nblk(n * r.Kn, 256), 256, 0, s>>>(n, c->d_v, c->d_c, r, c->d_yfine);
+        k_corr_values<<<nblk(tot, 128), 128, 0, s>>>(n, tot, off, cj, c->d_yfine, c->d_c, c->d_n, c->d_A, c->d_y,
                                                      c->d_w, c->d_pbody, body_dev(c), r, c->kappa, val);
         if (!cross)
             k_corr_self<<<nblk(n, 128), 128, 0, s>>>(n, off, cj, c->d_v, c->d_c, c->d_pbody, body_dev(c), r,
@@ -1308,7 +1330,7 @@ static void build_corr_part(pgb_ctx* c, bool cross, DBuf<int64_t>& off, DBuf<int
     }
     PGB_CUDA(cudaGetLastError());
     PGB_CUDA(cudaStreamSynchronize(s));
-    PGB_LAUNCHED(c, tot ? 4 : 2);
+    PGB_LAUNCHED(c, tot ? 5 : 2);
 }
 
 void build_corrections(pgb_ctx* c) {

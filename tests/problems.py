@@ -45,17 +45,5 @@ def oracle_system(bodies, eps_out=80.0, kappa=0.125, **params):
 
 
 def gpu_context(bodies, eps_out=80.0, kappa=0.125, **params):
-    import torch
-
-    import paper_1506_03745_gb300 as pgb
-    p = pgb.default_params(**params)
-    ctx = pgb.pgb_create(p, torch.cuda.current_stream())
-    for b in bodies:
-        kind = {"dielectric": pgb.PGB_DIELECTRIC, "sigma": pgb.PGB_SET_CHARGE, "phi": pgb.PGB_SET_POTENTIAL}[b["kind"]]
-        bid = pgb.pgb_mesh_load(ctx, kind, b["verts"], b["tris"], b["eps_in"], b["qxyz"] if len(b["q"]) else None,
-                                b["q"] if len(b["q"]) else None, b["bc"])
-        if b.get("R") is not None:
-            pgb.pgb_set_pose(ctx, bid, b["R"], b["t"])
-    pgb.pgb_set_solvent(ctx, eps_out, kappa)
-    pgb.pgb_tree_build(ctx)
-    return ctx
+    from paper_1506_03745_gb300.context import context
+    return context(bodies, eps_out, kappa, **params)

@@ -45,8 +45,8 @@ def test_argument_errors_need_no_device(libpgb):
     p = L.pgb_params()
     assert lib.pgb_default_params(ctypes.byref(p)) == 0
     assert (p.K, p.K_near, p.n_edge, p.P, p.theta, p.leaf_size) == (7, 19, 9, 6, 0.5, 32)
-    assert (p.p2p_item, p.m2p_item) == (64, 64)
-    for f, v in (("p2p_item", 5000), ("m2p_item", -1)):
+    assert (p.p2p_item, p.m2p_item, p.precond, p.graphs) == (64, 64, 0, 1)
+    for f, v in (("p2p_item", 5000), ("m2p_item", -1), ("precond", 2), ("graphs", 3)):
         q = L.pgb_params()
         lib.pgb_default_params(ctypes.byref(q))
         setattr(q, f, v)
