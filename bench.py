@@ -41,7 +41,7 @@ METRIC = "treecode matvecs/sec and GMRES solve ms at 1e-5 energy err, FP32+refin
 UNIT = "matvecs/s"
 WORKLOAD = "two spheres r=4 A, 2 x 20480 panels, sigma=0.05 C/m^2, R=12 A"
 PARAMS = dict(K=7, K_near=19, n_edge=9, P=6, theta=0.5, leaf_size=32, group_size=32, p2p_item=64, m2p_item=64,
-              precond=0)
+              precond=0, graphs=1, lanes=4)
 TOL = 1e-6
 RESTART = 100
 MAX_ITER = 2000
@@ -519,7 +519,7 @@ def run_poses(args):
     err = [abs(F[i, 3] - F64[i, 3]) / abs(F64[i, 3]) for i in range(2)]
     print(json.dumps({"workload": f"1 molecule ({pgb.pgb_tree_stats(ctx)['n_panels'] - 30420} panels, 900 "
                                   f"charges) x {args.poses} orientations x 4 gaps near a sphere r=40 A "
-                                  f"(30420 panels)", "poses": B, "ms": ms, "poses_per_s": B / (ms / 1e3),
+                                  f"(30420 panels)", "poses": B, "lanes": PARAMS["lanes"], "ms": ms, "poses_per_s": B / (ms / 1e3),
                       "mean_iterations": float(np.mean([s["iterations"] for s in st])),
                       "energy_rel_err_vs_fp64_first_2_poses": err, "status": code,
                       "stage_ms_per_pose": {k: v[0] / B for k, v in tim.items() if k != "kernel_launches" and v[0]},
@@ -608,10 +608,11 @@ def main():
     ap.add_argument("--m2p-item", type=int, default=None, help="override far nodes per M2P work item (sweeps)")
     ap.add_argument("--precond", type=int, default=None, help="1: block-diagonal GMRES preconditioner")
     ap.add_argument("--graphs", type=int, default=None, help="0: plain launches instead of the upward-pass graph")
+    ap.add_argument("--lanes", type=int, default=None, help="concurrent pose lanes of pgb_solve_batch")
     args = ap.parse_args()
     for k, v in (("leaf_size", args.leaf), ("P", args.P), ("theta", args.theta), ("p2p_item", args.p2p_item),
                  ("m2p_item", args.m2p_item), ("precond", args.precond),
-                 ("graphs", args.graphs)):
+                 ("graphs", args.graphs), ("lanes", args.lanes)):
         if v is not None:
             PARAMS[k] = v
     if args.impl == "reference":

@@ -1,14 +1,19 @@
 // C entry points of libpgb (declared in include/pgb.h).
 #include <math.h>
 
+#include <atomic>
 #include <cstring>
 #include <exception>
 #include <new>
+#include <thread>
 
 #include "common.cuh"
 #include "pgb_internal.cuh"
 
 namespace pgb {
+thread_local cudaStream_t g_alloc_stream = nullptr;
+thread_local bool g_alloc_scoped = false;
+int barrier_probe(int expected, int* timed_out);
 void cuda_check(cudaError_t e, const char* what) {
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
@@ -73,6 +78,7 @@ using namespace pgb;
 
 template <class F>
 static int guard(pgb_ctx* c, F f) {
+    AllocScope scope(c ? c->stream : nullptr);
     try {
         int r = f();
         if (c && r == PGB_OK) c->err.clear();
@@ -101,8 +107,154 @@ static int check_params(const pgb_params* p, std::string& why) {
     else if (p->m2p_item < 0 || p->m2p_item > 4096) why = "m2p_item must be in 1..4096 (0 = default)";
     else if (p->precond != 0 && p->precond != 1) why = "precond must be 0 or 1";
     else if (p->graphs != 0 && p->graphs != 1) why = "graphs must be 0 or 1";
+    else if (p->lanes < 0 || p->lanes > 16) why = "lanes must be in 1..16 (0 = default)";
     else return PGB_OK;
     return PGB_EINVAL;
+}
+
+// ---------------------------------------------------------------- pose lanes
+// One pose of a batch on context c: set the pose, rebuild what it changes,
+// solve and evaluate the energies into F4 (Coulomb, solvation, surface, total).
+static int solve_pose(pgb_ctx* c, int32_t body_id, int64_t index, const double* R, const double* t, int32_t mode,
+                      double tol, int32_t max_iter, int32_t restart, double* F4, pgb_solve_stats* stp) {
+    const int r = pgb_set_pose(c, body_id, R, t);
+    if (r != PGB_OK) fail(r, "pose " + std::to_string(index) + ": " + c->err);
+    {
+        StageTimer tm(c, PGB_STAGE_TREE);
+        if (!c->order_valid) {
+            upload_bodies(c);
+            build_order(c);
+            c->intra_valid = false;
+        }
+        build_geometry(c);
+        build_lists(c);
+        build_corrections(c);  // intra-body entries are reused across poses
+        c->tree_valid = true;
+    }
+    c->d_xbatch.resize(c->n_unk);
+    pgb_solve_stats st{};
+    const int rs = solve(c, mode, tol, max_iter, restart, c->d_xbatch, &st);
+    pgb_energies e{};
+    {
+        StageTimer tm(c, PGB_STAGE_ENERGY);
+        energies(c, c->d_xbatch, &e, nullptr);
+    }
+    F4[0] = e.coulomb;
+    F4[1] = e.solvation;
+    F4[2] = e.surface;
+    F4[3] = e.total;
+    if (stp) *stp = st;
+    return rs;
+}
+
+static void destroy_lanes(pgb_ctx* c) {
+    for (pgb_ctx* l : c->lane_ctx) pgb_destroy(l);
+    c->lane_ctx.clear();
+}
+
+static bool same_params(const pgb_params& a, const pgb_params& b) {
+    return a.K == b.K && a.K_near == b.K_near && a.n_edge == b.n_edge && a.P == b.P && a.theta == b.theta &&
+           a.leaf_size == b.leaf_size && a.group_size == b.group_size && a.p2p_item == b.p2p_item &&
+           a.m2p_item == b.m2p_item && a.precond == b.precond && a.graphs == b.graphs;
+}
+
+// Lane contexts: copies of c (bodies, solvent, parameters) with their own
+// non-blocking stream; kept while c's configuration is unchanged.  The other
+// bodies' poses follow c at every call.
+static void ensure_lanes(pgb_ctx* c, int L, int32_t body_id) {
+    bool ok = (int)c->lane_ctx.size() >= L && c->lane_gen == c->config_gen;
+    for (pgb_ctx* l : c->lane_ctx) ok = ok && same_params(l->p, c->p);
+    if (!ok) {
+        destroy_lanes(c);
+        for (int i = 0; i < L; ++i) {
+            pgb_ctx* l = new pgb_ctx;
+            l->p = c->p;
+            l->p.lanes = 1;
+            l->eps_out = c->eps_out;
+            l->kappa = c->kappa;
+            l->bodies = c->bodies;
+            if (cudaStreamCreateWithFlags(&l->stream, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaMallocHost(&l->h_pinned, 64) != cudaSuccess) {
+                (void)cudaGetLastError();
+                pgb_destroy(l);
+                fail(PGB_ECUDA, "lane context creation failed");
+            }
+            l->owns_stream = true;
+            c->lane_ctx.push_back(l);
+        }
+        c->lane_gen = c->config_gen;
+    }
+    for (pgb_ctx* l : c->lane_ctx) {
+        l->timing = c->timing;
+        for (size_t k = 0; k < c->bodies.size(); ++k) {
+            if ((int32_t)k == body_id) continue;
+            auto &a = l->bodies[k], &b = c->bodies[k];
+            if (memcmp(a.R, b.R, sizeof(a.R)) || memcmp(a.t, b.t, sizeof(a.t))) {
+                memcpy(a.R, b.R, sizeof(a.R));
+                memcpy(a.t, b.t, sizeof(a.t));
+                l->tree_valid = false;
+            }
+        }
+    }
+}
+
+// B poses over L lanes, each lane a host thread that takes the next pose
+// until none is left; the lanes' kernels overlap on the GPU.
+static int solve_lanes(pgb_ctx* c, int L, int32_t body_id, const double* R, const double* t, int64_t B, int32_t mode,
+                       double tol, int32_t max_iter, int32_t restart, double* F_out, pgb_solve_stats* stats) {
+    ensure_lanes(c, L, body_id);
+    int dev = 0;
+    PGB_CUDA(cudaGetDevice(&dev));
+    std::atomic<int64_t> next(0);
+    std::vector<int> rc(L, PGB_OK);
+    std::vector<std::string> msg(L);
+    std::vector<std::thread> th;
+    for (int l = 0; l < L; ++l)
+        th.emplace_back([&, l]() {
+            pgb_ctx* lc = c->lane_ctx[l];
+            AllocScope scope(lc->stream);
+            try {
+                cuda_check(cudaSetDevice(dev), "cudaSetDevice");
+                for (int64_t b; (b = next.fetch_add(1)) < B;) {
+                    const int r = solve_pose(lc, body_id, b, R + 9 * b, t + 3 * b, mode, tol, max_iter, restart,
+                                             F_out + 4 * b, stats ? stats + b : nullptr);
+                    if (r != PGB_OK && rc[l] == PGB_OK) rc[l] = r;
+                }
+                cuda_check(cudaStreamSynchronize(lc->stream), "lane sync");
+            } catch (const Error& e) {
+                rc[l] = e.code;
+                msg[l] = e.msg;
+            } catch (const std::exception& e) {
+                rc[l] = PGB_EINVAL;
+                msg[l] = e.what();
+            }
+        });
+    for (auto& x : th) x.join();
+    int out = PGB_OK;
+    for (int l = 0; l < L; ++l) {
+        pgb_ctx* lc = c->lane_ctx[l];
+        if (c->timing) {
+            collect_timing(lc);
+            for (int k = 0; k < PGB_N_STAGES; ++k) {
+                c->stage_ms[k] += lc->stage_ms[k];
+                c->stage_calls[k] += lc->stage_calls[k];
+                lc->stage_ms[k] = 0;
+                lc->stage_calls[k] = 0;
+            }
+        }
+        c->launches += lc->launches;
+        lc->launches = 0;
+    }
+    for (int l = 0; l < L; ++l)
+        if (rc[l] != PGB_OK && rc[l] != PGB_ENOCONV) {
+            const int code = rc[l];
+            const std::string m = msg[l];
+            destroy_lanes(c);
+            fail(code, "lane " + std::to_string(l) + ": " + m);
+        }
+    for (int l = 0; l < L; ++l)
+        if (rc[l] == PGB_ENOCONV) out = PGB_ENOCONV;
+    return out;
 }
 
 extern "C" {
@@ -120,6 +272,7 @@ int pgb_default_params(pgb_params* p) {
     p->m2p_item = 64;
     p->precond = 0;
     p->graphs = 1;
+    p->lanes = 4;
     return PGB_OK;
 }
 
@@ -136,9 +289,21 @@ int pgb_create(pgb_ctx** out, const pgb_params* p, void* stream) {
         (void)cudaGetLastError();
         return PGB_ECUDA;
     }
+    {
+        // temporaries are allocated in stream order from the device's default
+        // pool: let the pool keep freed memory for reuse (this process only)
+        int dev = 0;
+        cudaMemPool_t pool;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        (void)cudaGetLastError();
+    }
     pgb_ctx* c = new (std::nothrow) pgb_ctx;
     if (!c) return PGB_ENOMEM;
     if (q.p2p_item == 0) q.p2p_item = 64;
+    if (q.lanes == 0) q.lanes = 4;
     if (q.m2p_item == 0) q.m2p_item = 64;
     c->p = q;
     c->stream = (cudaStream_t)stream;
@@ -153,6 +318,7 @@ int pgb_create(pgb_ctx** out, const pgb_params* p, void* stream) {
 
 int pgb_destroy(pgb_ctx* c) {
     if (!c) return PGB_EINVAL;
+    destroy_lanes(c);
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto& p : c->ev_pending) {
         cudaEventDestroy(p.second.first);
@@ -163,7 +329,12 @@ int pgb_destroy(pgb_ctx* c) {
         if (gr.exec) cudaGraphExecDestroy(gr.exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
-    delete c;
+    cudaStream_t own = c->owns_stream ? c->stream : nullptr;
+    delete c;  // device buffers are freed in the order of their stream
+    if (own) {
+        cudaStreamSynchronize(own);
+        cudaStreamDestroy(own);
+    }
     return PGB_OK;
 }
 
@@ -215,6 +386,7 @@ int pgb_mesh_load(pgb_ctx* c, int32_t kind, const double* verts, int64_t nv, con
         if (kind == PGB_SET_CHARGE) b.bc = bc_value * 1e-20 / e;          // C/m^2 -> e/A^2
         if (kind == PGB_SET_POTENTIAL) b.bc = bc_value * eps0 * 1e-10 / e;  // V -> e/(eps0 A)
         c->bodies.push_back(std::move(b));
+        ++c->config_gen;
         c->tree_valid = false;
         c->order_valid = false;
         c->intra_valid = false;
@@ -233,6 +405,7 @@ int pgb_set_charges(pgb_ctx* c, int32_t id, const double* q, int64_t nq) {
         for (int64_t k = 0; k < nq; ++k)
             if (!isfinite(q[k])) fail(PGB_EINVAL, "non-finite charge");
         b.qval.assign(q, q + nq);
+        ++c->config_gen;
         if (c->order_valid && nq)  // device copy exists: update it in place
             PGB_CUDA(cudaMemcpyAsync(c->d_qval.p + b.q_off, q, 8 * nq, cudaMemcpyHostToDevice, c->stream));
         PGB_CUDA(cudaStreamSynchronize(c->stream));
@@ -249,6 +422,7 @@ int pgb_set_bc(pgb_ctx* c, int32_t id, double bc_value) {
         if (!isfinite(bc_value)) fail(PGB_EINVAL, "bc_value must be finite");
         const double e = 1.602176634e-19, eps0 = 8.8541878128e-12;
         b.bc = b.kind == PGB_SET_CHARGE ? bc_value * 1e-20 / e : bc_value * eps0 * 1e-10 / e;
+        ++c->config_gen;
         return PGB_OK;
     });
 }
@@ -260,6 +434,7 @@ int pgb_set_solvent(pgb_ctx* c, double eps_out, double kappa) {
         return PGB_EINVAL;
     }
     if (kappa != c->kappa) c->intra_valid = false;
+    ++c->config_gen;
     c->eps_out = eps_out;
     c->kappa = kappa;
     c->tree_valid = false;
@@ -402,37 +577,22 @@ int pgb_solve_batch(pgb_ctx* c, int32_t body_id, const double* R, const double* 
         if (body_id < 0 || body_id >= (int32_t)c->bodies.size()) fail(PGB_EINVAL, "bad body id");
         if (!(tol > 0 && tol < 1)) fail(PGB_EINVAL, "tol must be in (0, 1)");
         if (max_iter < 1 || restart < 1 || restart > 256) fail(PGB_EINVAL, "max_iter >= 1 and restart in 1..256");
+        if (B == 0) return PGB_OK;
+        const int L = (int)std::min<int64_t>(c->p.lanes, B);
         int first_err = PGB_OK;
-        for (int64_t b = 0; b < B; ++b) {
-            int r = pgb_set_pose(c, body_id, R + 9 * b, t + 3 * b);
-            if (r != PGB_OK) fail(r, "pose " + std::to_string(b) + ": " + c->err);
-            {
-                StageTimer tm(c, PGB_STAGE_TREE);
-                if (!c->order_valid) {
-                    upload_bodies(c);
-                    build_order(c);
-                    c->intra_valid = false;
-                }
-                build_geometry(c);
-                build_lists(c);
-                build_corrections(c);  // intra-body entries are reused across poses
-                c->tree_valid = true;
+        if (L <= 1) {
+            for (int64_t b = 0; b < B; ++b) {
+                const int rs = solve_pose(c, body_id, b, R + 9 * b, t + 3 * b, mode, tol, max_iter, restart,
+                                          F_out + 4 * b, stats ? stats + b : nullptr);
+                if (rs != PGB_OK && first_err == PGB_OK) first_err = rs;
             }
-            c->d_xbatch.resize(c->n_unk);
-            pgb_solve_stats st{};
-            int rs = solve(c, mode, tol, max_iter, restart, c->d_xbatch, &st);
-            if (rs != PGB_OK && first_err == PGB_OK) first_err = rs;
-            pgb_energies e{};
-            {
-                StageTimer tm(c, PGB_STAGE_ENERGY);
-                energies(c, c->d_xbatch, &e, nullptr);
-            }
-            F_out[4 * b] = e.coulomb;
-            F_out[4 * b + 1] = e.solvation;
-            F_out[4 * b + 2] = e.surface;
-            F_out[4 * b + 3] = e.total;
-            if (stats) stats[b] = st;
+        } else {
+            first_err = solve_lanes(c, L, body_id, R, t, B, mode, tol, max_iter, restart, F_out, stats);
         }
+        // the body keeps the last pose
+        memcpy(c->bodies[body_id].R, R + 9 * (B - 1), 9 * sizeof(double));
+        memcpy(c->bodies[body_id].t, t + 3 * (B - 1), 3 * sizeof(double));
+        if (L > 1) c->tree_valid = false;
         PGB_CUDA(cudaStreamSynchronize(c->stream));
         if (first_err == PGB_ENOCONV) c->err = "GMRES did not reach tol for at least one pose";
         return first_err;
@@ -611,6 +771,15 @@ int pgb_tree_export(pgb_ctx* c, int32_t* perm, int64_t* near_off, int32_t* near_
         PGB_CUDA(cudaStreamSynchronize(s));
         return PGB_OK;
     });
+}
+
+int pgb_barrier_check(int32_t expected_blocks, int32_t* timed_out) {
+    if (expected_blocks < 1 || expected_blocks > 2 || !timed_out) return PGB_EINVAL;
+    try {
+        return pgb::barrier_probe(expected_blocks, timed_out);
+    } catch (const pgb::Error& e) {
+        return e.code;
+    }
 }
 
 int pgb_math_check(const double* x, int64_t n, double* out) {

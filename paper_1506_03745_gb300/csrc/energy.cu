@@ -10,6 +10,45 @@
 
 namespace pgb {
 
+// Contribution of panel j (sorted index) of body b to phi_reac at xq
+// (without the 1/4pi): -K_L phi + V_L dphi with the 19-point rule when
+// |xq - c_j| < 2 L_j, else the K-point rule; 1/r by two Newton steps.
+__device__ __forceinline__ double phi_panel(const Geo& g, const BodyDev& bd, const Rules& r, const double* xq,
+                                            const double* x, int b, int64_t j) {
+    const int64_t s0 = bd.pan_off[b], N = bd.pan_off[b + 1] - s0, o = bd.unk_off[b];
+    const int64_t loc = g.perm[j] - s0;
+    const double phi = x[o + loc], dphi = x[o + N + loc];
+    const double* cj = g.c + 3 * j;
+    const double* nj = g.n + 3 * j;
+    double dx = xq[0] - cj[0], dy = xq[1] - cj[1], dz = xq[2] - cj[2];
+    double d2 = dx * dx + dy * dy + dz * dz;
+    double vl = 0, kl = 0;
+    if (d2 < 8.0 * g.A[j]) {
+        const double* v = g.v + 9 * j;
+        for (int m = 0; m < r.Kn; ++m) {
+            double y[3];
+            for (int a = 0; a < 3; ++a)
+                y[a] = cj[a] + ((r.mun[m][0] * (v[a] - cj[a]) + r.mun[m][1] * (v[3 + a] - cj[a])) +
+                                r.mun[m][2] * (v[6 + a] - cj[a]));
+            double ex = xq[0] - y[0], ey = xq[1] - y[1], ez = xq[2] - y[2];
+            double ri = rsqrt_nr<2>(ex * ex + ey * ey + ez * ez);
+            double w = r.wn[m] * g.A[j];
+            vl += w * ri;
+            kl += w * (nj[0] * ex + nj[1] * ey + nj[2] * ez) * ri * ri * ri;
+        }
+    } else {
+        for (int m = 0; m < g.K; ++m) {
+            const double* y = g.y + 3 * (j * g.K + m);
+            double ex = xq[0] - y[0], ey = xq[1] - y[1], ez = xq[2] - y[2];
+            double ri = rsqrt_nr<2>(ex * ex + ey * ey + ez * ez);
+            double w = g.w[j * g.K + m];
+            vl += w * ri;
+            kl += w * (nj[0] * ex + nj[1] * ey + nj[2] * ez) * ri * ri * ri;
+        }
+    }
+    return vl * dphi - kl * phi;
+}
+
 // phi_reac(r_k) = -K_L(phi) + V_L(dphi) at each charge of a dielectric body
 // (Eq. 13), three-tier rule with r_k as target: 19-point rule when
 // |r_k - c_j| < 2 L_j, the K-point rule otherwise.  One block per charge.
@@ -19,43 +58,53 @@ __global__ void k_phi_reac(Geo g, BodyDev bd, Rules r, const double* qxyz, const
     const int64_t k = blockIdx.x;
     const int b = qbody[k];
     const double xq[3] = {qxyz[3 * k], qxyz[3 * k + 1], qxyz[3 * k + 2]};
-    const int64_t s0 = bd.pan_off[b], s1 = bd.pan_off[b + 1], N = s1 - s0, o = bd.unk_off[b];
     double acc = 0;
-    for (int64_t j = s0 + threadIdx.x; j < s1; j += blockDim.x) {
-        const int64_t loc = g.perm[j] - s0;
-        const double phi = x[o + loc], dphi = x[o + N + loc];
-        const double* cj = g.c + 3 * j;
-        const double* nj = g.n + 3 * j;
-        double dx = xq[0] - cj[0], dy = xq[1] - cj[1], dz = xq[2] - cj[2];
-        double d2 = dx * dx + dy * dy + dz * dz;
-        double vl = 0, kl = 0;
-        if (d2 < 8.0 * g.A[j]) {
-            const double* v = g.v + 9 * j;
-            for (int m = 0; m < r.Kn; ++m) {
-                double y[3];
-                for (int a = 0; a < 3; ++a)
-                    y[a] = cj[a] + ((r.mun[m][0] * (v[a] - cj[a]) + r.mun[m][1] * (v[3 + a] - cj[a])) +
-                                    r.mun[m][2] * (v[6 + a] - cj[a]));
-                double ex = xq[0] - y[0], ey = xq[1] - y[1], ez = xq[2] - y[2];
-                double rr = sqrt(ex * ex + ey * ey + ez * ez), ri = 1.0 / rr;
-                double w = r.wn[m] * g.A[j];
-                vl += w * ri;
-                kl += w * (nj[0] * ex + nj[1] * ey + nj[2] * ez) * ri * ri * ri;
-            }
-        } else {
-            for (int m = 0; m < g.K; ++m) {
-                const double* y = g.y + 3 * (j * g.K + m);
-                double ex = xq[0] - y[0], ey = xq[1] - y[1], ez = xq[2] - y[2];
-                double rr = sqrt(ex * ex + ey * ey + ez * ez), ri = 1.0 / rr;
-                double w = g.w[j * g.K + m];
-                vl += w * ri;
-                kl += w * (nj[0] * ex + nj[1] * ey + nj[2] * ez) * ri * ri * ri;
-            }
-        }
-        acc += vl * dphi - kl * phi;
-    }
+    for (int64_t j = bd.pan_off[b] + threadIdx.x; j < bd.pan_off[b + 1]; j += blockDim.x)
+        acc += phi_panel(g, bd, r, xq, x, b, j);
     acc = block_sum(acc, sh);
     if (threadIdx.x == 0) out[k] = acc / PGB_FOUR_PI;
+}
+
+// The same sums split over blocks of PHI_CHUNK panels (grid: chunks x
+// charges) for few charges: part[k * nch + chunk], reduced in chunk order by
+// k_phi_reduce.
+#define PHI_CHUNK 256
+__global__ void __launch_bounds__(PHI_CHUNK) k_phi_reac_part(Geo g, BodyDev bd, Rules r, const double* qxyz,
+                                                            const int32_t* qbody, const double* x, int nch,
+                                                            double* part) {
+    __shared__ double sh[32];
+    const int64_t k = blockIdx.y;
+    const int b = qbody[k];
+    const double xq[3] = {qxyz[3 * k], qxyz[3 * k + 1], qxyz[3 * k + 2]};
+    const int64_t j = bd.pan_off[b] + (int64_t)blockIdx.x * PHI_CHUNK + threadIdx.x;
+    double acc = j < bd.pan_off[b + 1] ? phi_panel(g, bd, r, xq, x, b, j) : 0.0;
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[k * nch + blockIdx.x] = acc;
+}
+__global__ void k_phi_reduce(int64_t nq, int nch, const double* part, double* out) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= nq) return;
+    double acc = 0;
+    for (int i = 0; i < nch; ++i) acc += part[k * nch + i];
+    out[k] = acc / PGB_FOUR_PI;
+}
+
+// phi_reac at every charge into out (device, n_q): the chunked kernels when
+// the charges alone would not fill the GPU, else one block per charge.
+static void launch_phi_reac(pgb_ctx* c, const Rules& r, const double* x, double* out) {
+    int64_t nmax = 0;
+    for (auto& b : c->bodies) nmax = std::max<int64_t>(nmax, b.N);
+    const int nch = (int)std::max<int64_t>(1, (nmax + PHI_CHUNK - 1) / PHI_CHUNK);
+    if (c->n_q < 1024 && c->n_q * nch <= ((int64_t)1 << 22)) {
+        c->d_phi_part.resize((size_t)c->n_q * nch);
+        k_phi_reac_part<<<dim3((unsigned)nch, (unsigned)c->n_q), PHI_CHUNK, 0, c->stream>>>(
+            geo(c), body_dev(c), r, c->d_qxyz, c->d_q_body, x, nch, c->d_phi_part);
+        k_phi_reduce<<<(unsigned)((c->n_q + 127) / 128), 128, 0, c->stream>>>(c->n_q, nch, c->d_phi_part, out);
+        PGB_LAUNCHED(c, 1);
+    } else {
+        k_phi_reac<<<(unsigned)c->n_q, 128, 0, c->stream>>>(geo(c), body_dev(c), r, c->d_qxyz, c->d_q_body, x, out);
+    }
+    PGB_CUDA(cudaGetLastError());
 }
 
 // per-body sums: [0] sum q phi_reac, [2] sum_j u_j A_j (surfaces).  One
@@ -123,7 +172,7 @@ void energies(pgb_ctx* c, const double* x, pgb_energies* e, pgb_energies* per_bo
     qoff.resize(nb + 1);
     PGB_CUDA(cudaMemcpyAsync(qoff.p, qo.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
     Rules r = make_rules(c->p.K, c->p.K_near, c->p.n_edge);
-    if (c->n_q) k_phi_reac<<<(unsigned)c->n_q, 128, 0, s>>>(geo(c), body_dev(c), r, c->d_qxyz, c->d_q_body, x, phir);
+    if (c->n_q) launch_phi_reac(c, r, x, phir);
     k_body_sums<<<nb, 128, 0, s>>>(geo(c), body_dev(c), c->d_qxyz, c->d_qval, qoff, phir, x, sums);
     {
         DBuf<double> pair;
@@ -258,8 +307,7 @@ void energies_noalloc(pgb_ctx* c, const double* x, pgb_energies* e) {
 void phi_reac(pgb_ctx* c, const double* x, double* out) {
     if (!c->n_q) return;
     Rules r = make_rules(c->p.K, c->p.K_near, c->p.n_edge);
-    k_phi_reac<<<(unsigned)c->n_q, 128, 0, c->stream>>>(geo(c), body_dev(c), r, c->d_qxyz, c->d_q_body, x, out);
-    PGB_CUDA(cudaGetLastError());
+    launch_phi_reac(c, r, x, out);
     PGB_LAUNCHED(c, 1);
 }
 

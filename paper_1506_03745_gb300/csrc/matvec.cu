@@ -240,6 +240,8 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
         ev.src_active[b] = up.src_active[b] =
             known_only ? (known_mask ? known_mask[b] : (c->bodies[b].kind != PGB_DIELECTRIC)) : 1;
     }
+    ev.all_active = 1;
+    for (size_t b = 0; b < c->bodies.size(); ++b) ev.all_active &= ev.src_active[b];
     ev.near4 = c->d_near4;
     ev.far4 = c->d_far4;
     ev.tile_off = c->d_tile_off;

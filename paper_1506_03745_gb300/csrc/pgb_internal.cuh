@@ -29,24 +29,57 @@ void cuda_check(cudaError_t e, const char* what);
 #define PGB_CUDA(call) ::pgb::cuda_check((call), #call)
 void fail(int code, const std::string& msg);
 
+// Allocation stream of the calling thread (set by AllocScope for the
+// duration of a library call on a context).
+extern thread_local cudaStream_t g_alloc_stream;
+extern thread_local bool g_alloc_scoped;
+struct AllocScope {
+    cudaStream_t prev_stream;
+    bool prev_scoped;
+    explicit AllocScope(cudaStream_t s) : prev_stream(g_alloc_stream), prev_scoped(g_alloc_scoped) {
+        g_alloc_stream = s;
+        g_alloc_scoped = true;
+    }
+    ~AllocScope() {
+        g_alloc_stream = prev_stream;
+        g_alloc_scoped = prev_scoped;
+    }
+};
+
 template <typename T>
 struct DBuf {  // owning device buffer
     T* p = nullptr;
     size_t n = 0;
+    cudaStream_t st = nullptr;  // stream of a stream-ordered allocation
+    bool async = false;
     DBuf() = default;
     DBuf(const DBuf&) = delete;
     DBuf& operator=(const DBuf&) = delete;
     ~DBuf() { release(); }
     void release() {
-        if (p) cudaFree(p);
+        if (p) {
+            if (async) cudaFreeAsync(p, st);
+            else cudaFree(p);
+        }
         p = nullptr;
         n = 0;
+        async = false;
     }
+    // Inside a library call (AllocScope active) the buffer is allocated and
+    // freed in stream order on the context's stream, so temporaries cost no
+    // device-wide synchronisation; elsewhere plain cudaMalloc / cudaFree.
     void resize(size_t count) {  // contents undefined after growth
         if (count <= n && p) return;
         release();
         size_t c = count ? count : 1;
-        cudaError_t e = cudaMalloc(&p, c * sizeof(T));
+        cudaError_t e;
+        if (g_alloc_scoped) {
+            e = cudaMallocAsync((void**)&p, c * sizeof(T), g_alloc_stream);
+            async = e == cudaSuccess;
+            st = g_alloc_stream;
+        } else {
+            e = cudaMalloc(&p, c * sizeof(T));
+        }
         if (e != cudaSuccess) {
             p = nullptr;
             (void)cudaGetLastError();
@@ -106,6 +139,8 @@ struct BodyDev {  // per-body constants for kernels
 
 }  // namespace pgb
 
+#define PGB_CORR_CAP 48  // near-field candidates kept per target by the counting pass
+
 struct pgb_ctx {
     pgb_params p;
     cudaStream_t stream = nullptr;
@@ -153,6 +188,7 @@ struct pgb_ctx {
     pgb::DBuf<int64_t> d_near_off, d_far_off;
     pgb::DBuf<int32_t> d_near, d_far;
     pgb::DBuf<float4> d_near4, d_far4;   // FP32 entry offsets (node centre - group centre), node id
+    pgb::DBuf<int32_t> d_list_tmp;       // entries kept by the counting traversal (fixed rows per group)
     int64_t n_tiles = 0;                 // P2P tiles (<= 32 points of one near leaf) over all groups
     pgb::DBuf<int64_t> d_tile_off;
     pgb::DBuf<float4> d_tile_d;
@@ -173,6 +209,7 @@ struct pgb_ctx {
     pgb::DBuf<int32_t> d_corr_j, d_xcorr_j;
     pgb::DBuf<pgb::dbl4> d_corr_val, d_xcorr_val;  // dVL, dKL, dVY, dKY
     pgb::DBuf<double> d_yfine;             // 19-point nodes per panel (3 each), for the corrections
+    pgb::DBuf<int32_t> d_corr_tmp;         // candidates kept by the counting pass (PGB_CORR_CAP per panel)
     pgb::DBuf<double> d_xbatch;            // solution buffer of pgb_solve_batch
     // adjoint (transposed treecode): built on first use after each tree build
     bool adj_valid = false;
@@ -196,6 +233,7 @@ struct pgb_ctx {
     pgb::DBuf<double> d_dens;            // 3 per sorted panel: psiL, psiY, phi
     pgb::DBuf<float> d_mom32;            // 2*T per node
     pgb::DBuf<double> d_mom64;
+    pgb::DBuf<double> d_phi_part;        // chunk partial sums of phi_reac (few charges)
     pgb::DBuf<double> d_Up, d_Uf;        // P2P / M2P partial sums: 64 per work item (32 L, then 32 Y)
     pgb::DBuf<double> d_xtmp, d_ytmp;    // FP64 staging for FP32 matvec API
     // scratch
@@ -207,6 +245,8 @@ struct pgb_ctx {
     pgb::DBuf<pgb::dbl4> d_pc;           // block-diagonal preconditioner, per sorted panel
     pgb::DBuf<double> d_pz;              // its work vector
     bool pc_ready = false;
+    int coop_blocks = 0;                 // fused Arnoldi grid: 0 undecided, -1 unavailable
+    pgb::DBuf<unsigned> d_bar;           // its grid barrier state (count, generation, error)
     double* h_pinned = nullptr;
 
     // upward pass captured as a CUDA graph per precision, replayed on the
@@ -221,6 +261,10 @@ struct pgb_ctx {
     } up_graph[2];
     cudaStream_t cap_stream = nullptr;   // capture only (nothing runs on it)
     uint64_t tree_gen = 0;               // bumped whenever the octree structure is rebuilt
+    uint64_t config_gen = 0;             // bumped when bodies, charges, boundary values or solvent change
+    bool owns_stream = false;            // lane contexts create (and destroy) their stream
+    std::vector<pgb_ctx*> lane_ctx;      // pose lanes of pgb_solve_batch
+    uint64_t lane_gen = ~0ull;           // config_gen the lanes were copied at
 
     // statistics and stage timing
     bool timing = false;

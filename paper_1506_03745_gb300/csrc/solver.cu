@@ -183,6 +183,224 @@ __global__ void k_init_g(double* g, int m1, const double* beta) {
     if (i < m1) g[i] = (i == 0) ? *beta : 0.0;
 }
 
+// ---------------------------------------------------------------- fused Arnoldi step
+// One cooperative launch per GMRES iteration does the whole CGS2 step of
+// column j: two passes of (V_i . w for i <= j; w -= sum_i h_i V_i), the norm,
+// v_{j+1} = w / |w| and the Givens update, with a grid barrier between the
+// phases that exchange data between blocks.  Every thread keeps the same rows
+// in every phase, so w and v_{j+1} need no barrier; values written by other
+// blocks are read with ld.global.cg (L2, never a stale L1 line).
+struct GridBar {
+    unsigned count, gen;
+    int err, pad;
+};
+
+#define PGB_BARRIER_NS 1000000000ull  // 1 s
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier for a cooperative launch; the wait is bounded (1 s of
+// the global timer): on time-out the barrier records err and every block
+// falls through.
+__device__ __forceinline__ bool grid_sync(GridBar* b, unsigned nblocks) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = &b->gen;
+        volatile int* verr = &b->err;
+        const unsigned g0 = *vgen;
+        __threadfence();
+        if (atomicAdd(&b->count, 1u) == nblocks - 1) {
+            atomicExch(&b->count, 0u);
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+        } else {
+            // poll without sleeping (a barrier normally completes within
+            // microseconds); read the clock every 256 polls
+            const unsigned long long t0 = globaltimer_ns();
+            for (long long it = 1; *vgen == g0 && *verr == 0; ++it) {
+                if ((it & 255) == 0 && (globaltimer_ns() - t0 > PGB_BARRIER_NS || it > (1ll << 26))) {
+                    atomicExch(&b->err, 1);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *(volatile int*)&b->err == 0;
+}
+
+struct ArnoldiArgs {
+    double* V;      // basis, column i at V + i * ld
+    int64_t ld, n;
+    int j;          // the new column's index
+    double* w;      // A v_j on entry; destroyed
+    double* h;      // column j of H (m + 1 entries)
+    double* hc;     // second-pass coefficients (j + 1)
+    double* part;   // nb * (j + 1) block partial sums
+    double *cs, *sn, *g;
+    double* out;    // out[0] = |g_{j+1}|, out[1] = h_{j+1,j}, out[2] = 1 on a barrier time-out
+    GridBar* bar;
+};
+
+__global__ void __launch_bounds__(512) k_arnoldi(ArnoldiArgs a) {
+    extern __shared__ double shd[];  // max(32, m * warps) doubles
+    const int m = a.j + 1;
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned nb = gridDim.x;
+    const int64_t stride = (int64_t)nb * blockDim.x;
+    const int64_t r0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool ok = true;
+    for (int pass = 0; pass < 2 && ok; ++pass) {
+        double* coef = pass ? a.hc : a.h;
+        for (int i = 0; i < m; ++i) {  // block partials of V_i . w
+            const double* v = a.V + i * a.ld;
+            double t = 0;
+            for (int64_t r = r0; r < a.n; r += stride) t += v[r] * a.w[r];
+            t = warp_sum(t);
+            if (lane == 0) shd[i * nw + wi] = t;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            double t = 0;
+            for (int k = 0; k < nw; ++k) t += shd[i * nw + k];
+            a.part[(int64_t)i * nb + blockIdx.x] = t;
+        }
+        if (!(ok = grid_sync(a.bar, nb))) break;
+        for (int i = blockIdx.x; i < m; i += nb) {  // block i sums coefficient i
+            double t = 0;
+            for (unsigned b = threadIdx.x; b < nb; b += blockDim.x) t += __ldcg(a.part + (int64_t)i * nb + b);
+            t = block_sum(t, shd);
+            if (threadIdx.x == 0) coef[i] = t;
+        }
+        if (!(ok = grid_sync(a.bar, nb))) break;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) shd[i] = __ldcg(coef + i);
+        __syncthreads();
+        for (int64_t r = r0; r < a.n; r += stride) {
+            double t = 0;
+            for (int i = 0; i < m; ++i) t += shd[i] * a.V[i * a.ld + r];
+            a.w[r] -= t;
+        }
+        __syncthreads();
+    }
+    double nrm = 0;
+    if (ok) {
+        if (blockIdx.x == 0)  // H column: first pass + correction (read after the barrier)
+            for (int i = threadIdx.x; i < m; i += blockDim.x) a.h[i] = __ldcg(a.h + i) + __ldcg(a.hc + i);
+        double t = 0;
+        for (int64_t r = r0; r < a.n; r += stride) t += a.w[r] * a.w[r];
+        t = block_sum(t, shd);
+        if (threadIdx.x == 0) a.part[blockIdx.x] = t;
+        ok = grid_sync(a.bar, nb);
+    }
+    if (ok) {
+        double t = 0;  // every block forms the norm (nb values)
+        for (unsigned b = threadIdx.x; b < nb; b += blockDim.x) t += __ldcg(a.part + b);
+        t = block_sum(t, shd);
+        if (threadIdx.x == 0) shd[0] = sqrt(t);
+        __syncthreads();
+        nrm = shd[0];
+        double* vn = a.V + (int64_t)(a.j + 1) * a.ld;
+        for (int64_t r = r0; r < a.n; r += stride) vn[r] = nrm > 0 ? a.w[r] / nrm : 0.0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (ok) {  // Givens step on column j (as k_givens)
+            double* h = a.h;
+            h[a.j + 1] = nrm;
+            for (int i = 0; i < a.j; ++i) {
+                const double x = a.cs[i] * h[i] + a.sn[i] * h[i + 1];
+                const double y = -a.sn[i] * h[i] + a.cs[i] * h[i + 1];
+                h[i] = x;
+                h[i + 1] = y;
+            }
+            a.out[1] = h[a.j + 1];
+            const double p = h[a.j], q = h[a.j + 1];
+            const double r = hypot(p, q);
+            const double c = r > 0 ? p / r : 1.0, sv = r > 0 ? q / r : 0.0;
+            a.cs[a.j] = c;
+            a.sn[a.j] = sv;
+            h[a.j] = r;
+            h[a.j + 1] = 0;
+            a.g[a.j + 1] = -sv * a.g[a.j];
+            a.g[a.j] = c * a.g[a.j];
+            a.out[0] = fabs(a.g[a.j + 1]);
+        }
+        a.out[2] = ok ? 0.0 : 1.0;
+    }
+}
+
+// One block waits at a barrier sized for `expected` blocks: with expected > 1
+// nothing ever completes it, so the bounded wait must give up and say so.
+__global__ void k_barrier_probe(GridBar* b, unsigned expected, int* timed_out) {
+    const bool ok = grid_sync(b, expected);
+    if (threadIdx.x == 0) *timed_out = ok ? 0 : 1;
+}
+
+int barrier_probe(int expected, int* timed_out) {
+    DBuf<unsigned> bar;
+    DBuf<int> flag;
+    bar.resize(4);
+    flag.resize(1);
+    PGB_CUDA(cudaMemset(bar.p, 0, 16));
+    k_barrier_probe<<<1, 32>>>((GridBar*)bar.p, (unsigned)expected, flag.p);
+    PGB_CUDA(cudaGetLastError());
+    PGB_CUDA(cudaMemcpy(timed_out, flag.p, 4, cudaMemcpyDeviceToHost));
+    return PGB_OK;
+}
+
+// Launches the fused Arnoldi step (false: cooperative launch unavailable;
+// the caller takes the multi-kernel path).
+static bool arnoldi_fused(pgb_ctx* c, int j, double* w, double* h, double* hc, double* cs, double* sn, double* g,
+                          double* out) {
+    if (c->coop_blocks < 0) return false;
+    const int threads = 512, warps = threads / 32;  // one block per SM
+    if (c->coop_blocks == 0) {
+        int dev = 0, coop = 0, sms = 0, occ = 0;
+        PGB_CUDA(cudaGetDevice(&dev));
+        PGB_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        PGB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const size_t smem_max = 8 * (size_t)257 * warps;  // restart <= 256
+        PGB_CUDA(cudaFuncSetAttribute(k_arnoldi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+        PGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_arnoldi, threads, smem_max));
+        if (!coop || occ < 1) {
+            c->coop_blocks = -1;
+            return false;
+        }
+        c->coop_blocks = sms;
+        c->d_bar.resize(4);
+        PGB_CUDA(cudaMemsetAsync(c->d_bar.p, 0, 16, c->stream));
+    }
+    const int nb = c->coop_blocks;
+    c->d_red.resize(std::max<size_t>(c->d_red.n, (size_t)nb * (j + 2)));
+    ArnoldiArgs a;
+    a.V = c->d_V;
+    a.ld = c->n_unk;
+    a.n = c->n_unk;
+    a.j = j;
+    a.w = w;
+    a.h = h;
+    a.hc = hc;
+    a.part = c->d_red;
+    a.cs = cs;
+    a.sn = sn;
+    a.g = g;
+    a.out = out;
+    a.bar = (GridBar*)c->d_bar.p;
+    void* args[] = {&a};
+    const size_t smem = 8 * (size_t)std::max(32, (j + 1) * warps);
+    const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_arnoldi, nb, threads, args, smem, c->stream);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        c->coop_blocks = -1;
+        return false;
+    }
+    return true;
+}
+
 // Block-diagonal preconditioner from the self terms (no equation of the
 // paper: an addition to its GMRES).  The self entry of panel i holds
 // a = V_L,ii and V_Y,ii (K_ii = 0 on a flat panel), so its own unknowns enter
@@ -336,7 +554,13 @@ int gmres_op(pgb_ctx* c, int prec, bool transpose, const double* b, double* x, d
             apply_pc(vj, w);
             ++*matvecs;
             double* h = c->d_H.p + (size_t)j * (m + 1);
+            bool fused = false;
             {
+                StageTimer tm(c, PGB_STAGE_KRYLOV);
+                fused = arnoldi_fused(c, j, w, h, hcol, cs, sn, g, misc.p + 2);
+                if (fused) PGB_LAUNCHED(c, 1);
+            }
+            if (!fused) {
                 StageTimer tm(c, PGB_STAGE_KRYLOV);
                 for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
                     k_multi_dot<<<DOT_BLOCKS, DOT_THREADS, 8 * (DOT_THREADS / 32) * (j + 1), s>>>(c->d_V, n, j + 1, w, n,
@@ -351,8 +575,12 @@ int gmres_op(pgb_ctx* c, int prec, bool transpose, const double* b, double* x, d
                 PGB_CUDA(cudaGetLastError());
                 PGB_LAUNCHED(c, 12);
             }
-            PGB_CUDA(cudaMemcpyAsync(c->h_pinned, misc.p + 2, 16, cudaMemcpyDeviceToHost, s));
+            PGB_CUDA(cudaMemcpyAsync(c->h_pinned, misc.p + 2, fused ? 24 : 16, cudaMemcpyDeviceToHost, s));
             PGB_CUDA(cudaStreamSynchronize(s));
+            if (fused && c->h_pinned[2] != 0) {
+                PGB_CUDA(cudaMemsetAsync(c->d_bar.p, 0, 16, s));
+                fail(PGB_ETIMEOUT, "Arnoldi grid barrier timed out");
+            }
             est = c->h_pinned[0];
             double hnext = c->h_pinned[1];
             if (est <= abs_tol || !(hnext > 0)) {

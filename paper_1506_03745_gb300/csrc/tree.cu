@@ -79,12 +79,20 @@ __global__ void k_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* 
 }
 
 void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s, int64_t* total_host) {
-    static thread_local DBuf<int64_t> tot;
-    tot.resize(1);
+    // one total slot per host thread, outside any stream order, freed when the thread ends
+    struct Slot {
+        int64_t* p = nullptr;
+        ~Slot() {
+            if (p) cudaFree(p);
+        }
+    };
+    static thread_local Slot slot;
+    if (!slot.p) PGB_CUDA(cudaMalloc(&slot.p, sizeof(int64_t)));
+    int64_t* tot = slot.p;
     k_scan_i64<<<1, 1024, 0, s>>>(in, out, n, tot);
     PGB_CUDA(cudaGetLastError());
     if (total_host) {
-        PGB_CUDA(cudaMemcpyAsync(total_host, tot.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        PGB_CUDA(cudaMemcpyAsync(total_host, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         PGB_CUDA(cudaStreamSynchronize(s));
     }
 }
@@ -865,9 +873,15 @@ struct ListArgs {
 // one lane each, then pushed on the warp's stack in reverse order with their
 // class, so the entries come out in the sequential depth-first order.
 #define LIST_WARPS 4
+// The counting pass (fill == false) also keeps the first capn near and capf
+// far entries of each group in tmpn / tmpf (rows of capn / capf) and raises
+// *ovf when a group has more, so that the fill pass is needed only then.
+#define LIST_CAPN 256
+#define LIST_CAPF 512
 __global__ void __launch_bounds__(32 * LIST_WARPS) k_lists(ListArgs a, int64_t ng, bool fill, int64_t* ncnt,
                                                             int64_t* fcnt, const int64_t* noff, const int64_t* foff,
-                                                            int32_t* nearl, int32_t* farl, unsigned long long* stats) {
+                                                            int32_t* nearl, int32_t* farl, unsigned long long* stats,
+                                                            int32_t* tmpn, int32_t* tmpf, int* ovf) {
     __shared__ int32_t st_node[LIST_WARPS][PGB_LIST_STACK];
     __shared__ int8_t st_cls[LIST_WARPS][PGB_LIST_STACK];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -905,12 +919,14 @@ __global__ void __launch_bounds__(32 * LIST_WARPS) k_lists(ListArgs a, int64_t n
             __syncwarp();
             if (cls == 0) {
                 if (fill && lane == 0) farl[wf] = nd;
+                if (!fill && lane == 0 && nf < LIST_CAPF) tmpf[g * LIST_CAPF + nf] = nd;
                 ++wf;
                 ++nf;
                 m2p += gsize;
                 if (lap) m2pl += gsize;
             } else if (cls == 1) {
                 if (fill && lane == 0) nearl[wn] = nd;
+                if (!fill && lane == 0 && nn < LIST_CAPN) tmpn[g * LIST_CAPN + nn] = nd;
                 ++wn;
                 ++nn;
                 const unsigned long long pts = (unsigned long long)(a.nend[nd] - a.nstart[nd]) * a.K;
@@ -937,12 +953,23 @@ __global__ void __launch_bounds__(32 * LIST_WARPS) k_lists(ListArgs a, int64_t n
     if (!fill) {
         ncnt[g] = nn;
         fcnt[g] = nf;
-    } else {
+        if (nn > LIST_CAPN || nf > LIST_CAPF) atomicOr(ovf, 1);
         atomicAdd(&stats[0], p2p);
         atomicAdd(&stats[1], p2pl);
         atomicAdd(&stats[2], m2p);
         atomicAdd(&stats[3], m2pl);
     }
+}
+
+// Lists from the entries kept by the counting pass (no group overflowed);
+// one warp per group.
+__global__ void k_lists_compact(int64_t ng, const int64_t* noff, const int64_t* foff, const int32_t* tmpn,
+                                const int32_t* tmpf, int32_t* nearl, int32_t* farl) {
+    const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (g >= ng) return;
+    for (int64_t e = noff[g] + lane; e < noff[g + 1]; e += 32) nearl[e] = tmpn[g * LIST_CAPN + (e - noff[g])];
+    for (int64_t e = foff[g] + lane; e < foff[g + 1]; e += 32) farl[e] = tmpf[g * LIST_CAPF + (e - foff[g])];
 }
 
 // FP32 offset of every list entry: node centre - group centre (FP64
@@ -961,37 +988,59 @@ __global__ void k_list_offsets(int64_t ng, const int64_t* off, const int32_t* id
 // P2P tiles: every near leaf of a group cut into runs of at most 32
 // quadrature points; descriptor = (leaf centre - group centre in FP32, first
 // point) and (leaf, count, flags: 1 Laplace pair, 2 leaf holds group targets, body).
+// One warp per group; the lanes take its near entries 32 at a time.
 __global__ void k_tile_count(int64_t ng, const int64_t* noff, const int32_t* nearl, const int32_t* nstart,
                              const int32_t* nend, int K, int64_t* cnt) {
-    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (g >= ng) return;
     int64_t c = 0;
-    for (int64_t e = noff[g]; e < noff[g + 1]; ++e) {
-        int nd = nearl[e];
+    for (int64_t e = noff[g] + lane; e < noff[g + 1]; e += 32) {
+        const int nd = nearl[e];
         c += ((int64_t)(nend[nd] - nstart[nd]) * K + 31) / 32;
     }
-    cnt[g] = c;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) cnt[g] = c;
 }
+// Tiles in entry order: a warp scan of the lanes' tile counts places each
+// entry's run after those of the entries before it.
 __global__ void k_tile_fill(int64_t ng, const int64_t* noff, const int32_t* nearl, const float4* near4,
                             const int32_t* nstart, const int32_t* nend, const int32_t* nbody, const int32_t* gstart,
                             const int32_t* gend, const int32_t* gbody, BodyDev bd, int K, const int64_t* toff,
                             float4* td, int4* tm) {
-    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (g >= ng) return;
     int64_t w = toff[g];
     const int gb = gbody[g];
-    for (int64_t e = noff[g]; e < noff[g + 1]; ++e) {
-        const int nd = nearl[e];
-        const int nb = nbody[nd];
-        const int flags = ((nb == gb && bd.kind[gb] == PGB_DIELECTRIC) ? 1 : 0) |
-                          ((nstart[nd] < gend[g] && nend[nd] > gstart[g]) ? 2 : 0);
-        const int64_t s0 = (int64_t)nstart[nd] * K, s1 = (int64_t)nend[nd] * K;
-        for (int64_t q = s0; q < s1; q += 32) {
-            const float4 o = near4[e];
-            td[w] = make_float4(o.x, o.y, o.z, __int_as_float((int)q));
-            tm[w] = make_int4(nd, (int)min((int64_t)32, s1 - q), flags, nb);
-            ++w;
+    const int64_t e1 = noff[g + 1];
+    for (int64_t e0 = noff[g]; e0 < e1; e0 += 32) {
+        const int64_t e = e0 + lane;
+        int nd = 0;
+        int64_t s0 = 0, s1 = 0, nt = 0;
+        if (e < e1) {
+            nd = nearl[e];
+            s0 = (int64_t)nstart[nd] * K;
+            s1 = (int64_t)nend[nd] * K;
+            nt = (s1 - s0 + 31) / 32;
         }
+        int64_t incl = nt;  // inclusive scan over the lanes
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (e < e1) {
+            const int nb = nbody[nd];
+            const int flags = ((nb == gb && bd.kind[gb] == PGB_DIELECTRIC) ? 1 : 0) |
+                              ((nstart[nd] < gend[g] && nend[nd] > gstart[g]) ? 2 : 0);
+            const float4 o = near4[e];
+            int64_t t = w + incl - nt;
+            for (int64_t q = s0; q < s1; q += 32, ++t) {
+                td[t] = make_float4(o.x, o.y, o.z, __int_as_float((int)q));
+                tm[t] = make_int4(nd, (int)min((int64_t)32, s1 - q), flags, nb);
+            }
+        }
+        w += __shfl_sync(0xffffffffu, incl, 31);
     }
 }
 
@@ -1032,11 +1081,17 @@ void make_lists(pgb_ctx* c, const double* r2, const double* glo, const double* g
     noff.resize(ng + 1);
     foff.resize(ng + 1);
     DBuf<unsigned long long> st;
-    st.resize(5);
-    PGB_CUDA(cudaMemsetAsync(st.p, 0, 40, s));
+    st.resize(6);
+    PGB_CUDA(cudaMemsetAsync(st.p, 0, 48, s));
+    int* ovf = (int*)(st.p + 5);
+    c->d_list_tmp.resize((size_t)ng * (LIST_CAPN + LIST_CAPF));
+    int32_t* tmpn = c->d_list_tmp.p;
+    int32_t* tmpf = c->d_list_tmp.p + (size_t)ng * LIST_CAPN;
     k_lists<<<nblk(ng, LIST_WARPS), 32 * LIST_WARPS, 0, s>>>(a, ng, false, nc, fc, nullptr, nullptr, nullptr, nullptr,
-                                                              st);
+                                                              st, tmpn, tmpf, ovf);
     PGB_CUDA(cudaGetLastError());
+    unsigned long long h[6];
+    PGB_CUDA(cudaMemcpyAsync(h, st.p, 48, cudaMemcpyDeviceToHost, s));
     int64_t tn = 0, tf = 0;
     exclusive_scan_i64(nc, noff, ng, s, &tn);
     exclusive_scan_i64(fc, foff, ng, s, &tf);
@@ -1046,16 +1101,18 @@ void make_lists(pgb_ctx* c, const double* r2, const double* glo, const double* g
     n_far = tf;
     nearl.resize(tn);
     farl.resize(tf);
-    k_lists<<<nblk(ng, LIST_WARPS), 32 * LIST_WARPS, 0, s>>>(a, ng, true, nullptr, nullptr, noff, foff, nearl, farl,
-                                                              st);
+    // the scans synchronised the stream: h (counts' statistics, overflow) is valid
+    if (((int*)(h + 5))[0])
+        k_lists<<<nblk(ng, LIST_WARPS), 32 * LIST_WARPS, 0, s>>>(a, ng, true, nullptr, nullptr, noff, foff, nearl,
+                                                                  farl, st, nullptr, nullptr, nullptr);
+    else
+        k_lists_compact<<<nblk(32 * ng, 128), 128, 0, s>>>(ng, noff, foff, tmpn, tmpf, nearl, farl);
     PGB_CUDA(cudaGetLastError());
     near4.resize(tn);
     far4.resize(tf);
     k_list_offsets<<<(unsigned)ng, 64, 0, s>>>(ng, noff, nearl, c->d_node_center, c->d_group_center, near4);
     k_list_offsets<<<(unsigned)ng, 64, 0, s>>>(ng, foff, farl, c->d_node_center, c->d_group_center, far4);
     PGB_CUDA(cudaGetLastError());
-    unsigned long long h[5];
-    PGB_CUDA(cudaMemcpyAsync(h, st.p, 40, cudaMemcpyDeviceToHost, s));
     PGB_CUDA(cudaStreamSynchronize(s));
     if (h[4]) fail(PGB_EINVAL, "octree traversal stack overflow");
     if (stats4)
@@ -1077,7 +1134,7 @@ void build_lists(pgb_ctx* c) {
         DBuf<int64_t> tc;
         tc.resize(ng);
         c->d_tile_off.resize(ng + 1);
-        k_tile_count<<<nblk(ng, 128), 128, 0, s>>>(ng, c->d_near_off, c->d_near, c->d_node_start, c->d_node_end,
+        k_tile_count<<<nblk(32 * ng, 128), 128, 0, s>>>(ng, c->d_near_off, c->d_near, c->d_node_start, c->d_node_end,
                                                    c->p.K, tc);
         int64_t nt = 0;
         exclusive_scan_i64(tc, c->d_tile_off, ng, s, &nt);
@@ -1085,7 +1142,7 @@ void build_lists(pgb_ctx* c) {
         c->n_tiles = nt;
         c->d_tile_d.resize(nt);
         c->d_tile_m.resize(nt);
-        k_tile_fill<<<nblk(ng, 128), 128, 0, s>>>(ng, c->d_near_off, c->d_near, c->d_near4, c->d_node_start,
+        k_tile_fill<<<nblk(32 * ng, 128), 128, 0, s>>>(ng, c->d_near_off, c->d_near, c->d_near4, c->d_node_start,
                                                   c->d_node_end, c->d_node_body, c->d_group_start, c->d_group_end,
                                                   c->d_group_body, body_dev(c), c->p.K, c->d_tile_off, c->d_tile_d,
                                                   c->d_tile_m);
@@ -1126,8 +1183,11 @@ struct CorrArgs {
 
 // candidates j of target i: |c_i - c_j|^2 < 8 A_j (|x - c_j| < 2 L_j), or j == i;
 // cross == false: sources of the target's own body, true: of the other bodies
+// The counting pass also keeps the first `cap` candidates of each target in
+// tmp (row i at tmp + i * cap) and raises *overflow when a target has more,
+// so that the fill pass is needed only then.
 __global__ void k_corr_find(CorrArgs a, int64_t n, bool fill, bool cross, const int32_t* pbody, int64_t* cnt,
-                            const int64_t* off, int32_t* cj) {
+                            const int64_t* off, int32_t* cj, int32_t* tmp, int cap, int* overflow) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     double x[3] = {a.C[3 * i], a.C[3 * i + 1], a.C[3 * i + 2]};
@@ -1152,6 +1212,7 @@ __global__ void k_corr_find(CorrArgs a, int64_t n, bool fill, bool cross, const 
                     double dd = dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz));
                     if (j == i || dd < 8.0 * a.A[j]) {
                         if (fill) cj[w++] = (int32_t)j;
+                        else if (k < cap) tmp[i * cap + k] = (int32_t)j;
                         ++k;
                     }
                 }
@@ -1162,22 +1223,60 @@ __global__ void k_corr_find(CorrArgs a, int64_t n, bool fill, bool cross, const 
             }
         }
     }
-    if (!fill) cnt[i] = k;
+    if (!fill) {
+        cnt[i] = k;
+        if (k > cap) atomicOr(overflow, 1);
+    }
 }
 
+// CSR rows from the candidates kept by the counting pass (no row overflowed).
+__global__ void k_corr_compact(int64_t n, const int64_t* off, const int32_t* tmp, int cap, int32_t* cj) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t b = off[i], e = off[i + 1];
+    for (int64_t k = b; k < e; ++k) cj[k] = tmp[i * cap + (k - b)];
+}
+
+// Coefficients 1/k! of the Taylor series of e^z.
+template <int K>
+struct ExpCoef {
+    static constexpr double v = ExpCoef<K - 1>::v / K;
+};
+template <>
+struct ExpCoef<0> {
+    static constexpr double v = 1.0;
+};
+
 // Kernel values at a target x from a source point y with normal n (no 1/4pi);
-// 1/r by two Newton steps (FP64 rounding), e^{-kappa r} by exp2_taylor.
-// Without LAP only the Yukawa pair (vy, ky) is formed.
-template <bool LAP>
+// 1/r by one Newton step on the SFU estimate (relative error < 2e-13).
+// Without LAP only the Yukawa pair (vy, ky) is formed.  e^{-kappa r}: with
+// SHIFT, e0 * e^z, z = kappa (r0 - r), e0 = e^{-kappa r0} and |z| <= 0.05
+// (r0 = |x - c_j|, every node lies within rho_j of c_j and kappa rho_j <= 0.05),
+// the series to degree 7 (remainder < 1.1e-15 relative); else exp2_taylor.
+template <bool LAP, bool SHIFT>
 __device__ __forceinline__ void kern4(const double* x, const double* y, const double* n, double kappa, double w,
-                                      double& vl, double& kl, double& vy, double& ky) {
+                                      double kr0, double e0, double& vl, double& kl, double& vy, double& ky) {
     double dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
     double r2 = dx * dx + dy * dy + dz * dz;
     if (!(r2 > 0)) return;
-    double ri = rsqrt_nr<2>(r2);
+    double ri = rsqrt_nr<1>(r2);
     double r = r2 * ri;
     double nd = n[0] * dx + n[1] * dy + n[2] * dz;
-    double e = exp2_taylor(-kappa * 1.4426950408889634 * r);
+    double e;
+    if (SHIFT) {
+        const double z = fma(-kappa, r, kr0);
+        double p = ExpCoef<7>::v;
+        p = fma(p, z, ExpCoef<6>::v);
+        p = fma(p, z, ExpCoef<5>::v);
+        p = fma(p, z, ExpCoef<4>::v);
+        p = fma(p, z, ExpCoef<3>::v);
+        p = fma(p, z, ExpCoef<2>::v);
+        p = fma(p, z, 1.0);
+        p = fma(p, z, 1.0);
+        e = e0 * p;
+    } else {
+        e = exp2_taylor(-kappa * 1.4426950408889634 * r);
+    }
     double ri3 = ri * ri * ri;
     if (LAP) {
         vl += w * ri;
@@ -1200,14 +1299,14 @@ __global__ void k_fine_nodes(int64_t n, const double* V, const double* C, Rules 
                                   r.mun[m][2] * (v[6 + a] - cjp[a]));
 }
 
-template <bool LAP>
+template <bool LAP, bool SHIFT>
 __device__ __forceinline__ void corr_sums(const double* x, const double* nj, int64_t j, const double* YF,
                                           const double* Y, const double* W, double Aj, const Rules& r, double kappa,
-                                          double* tv, double* kv) {
+                                          double kr0, double e0, double* tv, double* kv) {
     for (int m = 0; m < r.Kn; ++m)
-        kern4<LAP>(x, YF + 3 * (j * r.Kn + m), nj, kappa, r.wn[m] * Aj, tv[0], tv[1], tv[2], tv[3]);
+        kern4<LAP, SHIFT>(x, YF + 3 * (j * r.Kn + m), nj, kappa, r.wn[m] * Aj, kr0, e0, tv[0], tv[1], tv[2], tv[3]);
     for (int m = 0; m < r.K; ++m)
-        kern4<LAP>(x, Y + 3 * (j * r.K + m), nj, kappa, W[j * r.K + m], kv[0], kv[1], kv[2], kv[3]);
+        kern4<LAP, SHIFT>(x, Y + 3 * (j * r.K + m), nj, kappa, W[j * r.K + m], kr0, e0, kv[0], kv[1], kv[2], kv[3]);
 }
 
 __device__ __forceinline__ int64_t owner_row(const int64_t* off, int64_t n, int64_t e) {
@@ -1224,8 +1323,8 @@ __device__ __forceinline__ int64_t owner_row(const int64_t* off, int64_t n, int6
 // for V_L, K_L, V_Y, K_Y (Section 3.1), FP64, one thread per entry; the
 // Laplace pair only where it enters a row (same dielectric body).
 __global__ void k_corr_values(int64_t n, int64_t tot, const int64_t* off, const int32_t* cj, const double* YF,
-                              const double* C, const double* Nn, const double* A, const double* Y, const double* W,
-                              const int32_t* pbody, BodyDev bd, Rules r, double kappa, dbl4* out) {
+                              const double* V, const double* C, const double* Nn, const double* A, const double* Y,
+                              const double* W, const int32_t* pbody, BodyDev bd, Rules r, double kappa, dbl4* out) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= tot) return;
     const int64_t i = owner_row(off, n, e);
@@ -1235,9 +1334,27 @@ __global__ void k_corr_values(int64_t n, int64_t tot, const int64_t* off, const 
     const double* nj = Nn + 3 * j;
     const int bi = pbody[i], bj = pbody[j];
     const bool lap = bi == bj && bd.kind[bi] == PGB_DIELECTRIC;
+    // r0 = |x - c_j| and the panel radius rho_j about its centroid
+    const double* cjp = C + 3 * j;
+    const double* vj = V + 9 * j;
+    double rho2 = 0;
+    for (int k = 0; k < 3; ++k) {
+        const double ax = vj[3 * k] - cjp[0], ay = vj[3 * k + 1] - cjp[1], az = vj[3 * k + 2] - cjp[2];
+        rho2 = fmax(rho2, ax * ax + ay * ay + az * az);
+    }
+    const double ox = x[0] - cjp[0], oy = x[1] - cjp[1], oz = x[2] - cjp[2];
+    const double r0 = sqrt(ox * ox + oy * oy + oz * oz);
+    const bool shift = kappa * sqrt(rho2) <= 0.05;
+    const double e0 = shift ? exp2_taylor(-kappa * 1.4426950408889634 * r0) : 0.0;
+    const double kr0 = kappa * r0;
     double tv[4] = {0, 0, 0, 0}, kv[4] = {0, 0, 0, 0};
-    if (lap) corr_sums<true>(x, nj, j, YF, Y, W, A[j], r, kappa, tv, kv);
-    else corr_sums<false>(x, nj, j, YF, Y, W, A[j], r, kappa, tv, kv);
+    if (lap) {
+        if (shift) corr_sums<true, true>(x, nj, j, YF, Y, W, A[j], r, kappa, kr0, e0, tv, kv);
+        else corr_sums<true, false>(x, nj, j, YF, Y, W, A[j], r, kappa, kr0, e0, tv, kv);
+    } else {
+        if (shift) corr_sums<false, true>(x, nj, j, YF, Y, W, A[j], r, kappa, kr0, e0, tv, kv);
+        else corr_sums<false, false>(x, nj, j, YF, Y, W, A[j], r, kappa, kr0, e0, tv, kv);
+    }
     double d[4];
     for (int q = 0; q < 4; ++q) d[q] = (tv[q] - kv[q]) / PGB_FOUR_PI;
     out[e] = dbl4{d[0], d[1], d[2], d[3]};
@@ -1309,20 +1426,30 @@ static void build_corr_part(pgb_ctx* c, bool cross, DBuf<int64_t>& off, DBuf<int
     DBuf<int64_t> cnt;
     cnt.resize(n);
     off.resize(n + 1);
-    k_corr_find<<<nblk(n, 64), 64, 0, s>>>(a, n, false, cross, c->d_pbody, cnt, nullptr, nullptr);
+    const int cap = PGB_CORR_CAP;
+    c->d_corr_tmp.resize((size_t)n * cap + 1);
+    int* ovf = (int*)(c->d_corr_tmp.p + (size_t)n * cap);
+    PGB_CUDA(cudaMemsetAsync(ovf, 0, 4, s));
+    k_corr_find<<<nblk(n, 64), 64, 0, s>>>(a, n, false, cross, c->d_pbody, cnt, nullptr, nullptr, c->d_corr_tmp, cap,
+                                           ovf);
     PGB_CUDA(cudaGetLastError());
+    int h_ovf = 0;
+    PGB_CUDA(cudaMemcpyAsync(&h_ovf, ovf, 4, cudaMemcpyDeviceToHost, s));
     int64_t tot = 0;
-    exclusive_scan_i64(cnt, off, n, s, &tot);
+    exclusive_scan_i64(cnt, off, n, s, &tot);  // synchronises: h_ovf is valid
     PGB_CUDA(cudaMemcpyAsync(off.p + n, &tot, 8, cudaMemcpyHostToDevice, s));
     count = tot;
     cj.resize(tot);
     val.resize(tot);
     if (tot) {
-        k_corr_find<<<nblk(n, 64), 64, 0, s>>>(a, n, true, cross, c->d_pbody, nullptr, off, cj);
+        if (h_ovf)
+            k_corr_find<<<nblk(n, 64), 64, 0, s>>>(a, n, true, cross, c->d_pbody, nullptr, off, cj, nullptr, 0, nullptr);
+        else
+            k_corr_compact<<<nblk(n, 128), 128, 0, s>>>(n, off, c->d_corr_tmp, cap, cj);
         Rules r = make_rules(c->p.K, c->p.K_near, c->p.n_edge);
         c->d_yfine.resize(3 * n * r.Kn);
         k_fine_nodes<<<nblk(n * r.Kn, 256), 256, 0, s>>>(n, c->d_v, c->d_c, r, c->d_yfine);
-        k_corr_values<<<nblk(tot, 128), 128, 0, s>>>(n, tot, off, cj, c->d_yfine, c->d_c, c->d_n, c->d_A, c->d_y,
+        k_corr_values<<<nblk(tot, 128), 128, 0, s>>>(n, tot, off, cj, c->d_yfine, c->d_v, c->d_c, c->d_n, c->d_A, c->d_y,
                                                      c->d_w, c->d_pbody, body_dev(c), r, c->kappa, val);
         if (!cross)
             k_corr_self<<<nblk(n, 128), 128, 0, s>>>(n, off, cj, c->d_v, c->d_c, c->d_pbody, body_dev(c), r,

@@ -139,6 +139,7 @@ struct EvalArgs {
     double kappa;
     int lap_body[PGB_MAX_BODIES];  // 1 when the body is dielectric
     int src_active[PGB_MAX_BODIES];  // 0: the body's densities are all zero (skip)
+    int all_active;                // every body active (the plain product): no per-node test
     const float4* near4;           // per near entry: leaf centre - group centre, node id bits
     const float4* far4;            // per far entry: node centre - group centre, node id bits
     const int64_t* tile_off;       // per group: its P2P tiles [tile_off[g], tile_off[g+1])
@@ -443,6 +444,7 @@ __global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a, const typename V4<r
     const int64_t fb = a.far_off[g] + (it - a.fitem_off[g]) * a.m2p_item;
     const int64_t f1 = min(a.far_off[g + 1], fb + a.m2p_item);
     auto seek = [&](int64_t ee) -> int64_t {  // next active entry of this warp
+        if (a.all_active) return ee;
         while (ee < f1) {
             int nn;
             real qx, qy, qz;
@@ -505,63 +507,96 @@ __device__ __constant__ const int kBinom[9][9] = {
     {1, 3, 3, 1, 0, 0, 0, 0, 0},      {1, 4, 6, 4, 1, 0, 0, 0, 0},      {1, 5, 10, 10, 5, 1, 0, 0, 0},
     {1, 6, 15, 20, 15, 6, 1, 0, 0},   {1, 7, 21, 35, 35, 21, 7, 1, 0}, {1, 8, 28, 56, 70, 56, 28, 8, 1}};
 
-// P2M: moments of every leaf about its centre, u = c - y (one block per leaf).
+// P2M: moments of every leaf about its centre, u = c - y (one block per leaf,
+// one thread per multi-index k).  The double-layer part is split off:
+//   M_k = sum_s q_s u^k + sum_a k_a D_a[k - e_a],  D_a[k'] = sum_s p_{s,a} u^{k'},
+// so each (point, k) costs one monomial (two products of cached powers) and
+// five multiply-adds; the D_a (|k'| <= P - 1) meet the Q sums in shared memory.
 template <typename real, int P>
 __global__ void __launch_bounds__(128) k_p2m_leaves(UpArgs a, const typename V4<real>::t* __restrict__ src,
                                                     real* __restrict__ mom) {
     using v4 = typename V4<real>::t;
     constexpr int T = MI<P>::T;
+    constexpr int TD = P * (P + 1) * (P + 2) / 6;  // terms of degree <= P - 1
+    static_assert(T <= 2 * 128, "two terms per thread at most");
     __shared__ real pw[128][3][P + 1];
     __shared__ real sq[128][5];
+    __shared__ real sd[3][TD > 0 ? TD : 1];
+    __shared__ short idx3[P + 1][P + 1][P + 1];
     const int tid = threadIdx.x;
     const int64_t leaf = blockIdx.x;
     if (leaf >= a.n_leaves) return;
     const int nd = a.leaf_node[leaf];
     if (!a.src_active[a.nbody[nd]]) return;
     const int64_t s0 = (int64_t)a.nstart[nd] * a.K, s1 = (int64_t)a.nend[nd] * a.K;
-    for (int k0 = 0; k0 < T; k0 += 128) {
-        const int k = k0 + tid;
-        int kx = 0, ky = 0, kz = 0;
-        if (k < T) decode_mi(k, kx, ky, kz);
-        real accL = 0, accY = 0;
-        for (int64_t t = s0; t < s1; t += 128) {
-            const int cnt = (int)min((int64_t)128, s1 - t);
-            __syncthreads();
-            if (tid < cnt) {
-                const v4 A = src[2 * (t + tid)], B = src[2 * (t + tid) + 1];
-                const real u[3] = {-A.x, -A.y, -A.z};
-                for (int q = 0; q < 3; ++q) {
-                    real v = 1;
-                    for (int m = 0; m <= P; ++m) {
-                        pw[tid][q][m] = v;
-                        v *= u[q];
-                    }
+    for (int k = tid; k < T; k += 128) {
+        int x, y, z;
+        decode_mi(k, x, y, z);
+        idx3[x][y][z] = (short)k;
+    }
+    // thread -> terms tid and tid + 128 (when T > 128)
+    int kx[2] = {0, 0}, ky[2] = {0, 0}, kz[2] = {0, 0};
+    bool on[2], low[2];
+    for (int h = 0; h < 2; ++h) {
+        const int k = tid + 128 * h;
+        on[h] = k < T;
+        if (on[h]) decode_mi(k, kx[h], ky[h], kz[h]);
+        low[h] = on[h] && kx[h] + ky[h] + kz[h] < P;  // also a D_a index (k < TD)
+    }
+    real qL[2] = {0, 0}, qY[2] = {0, 0}, dx[2] = {0, 0}, dy[2] = {0, 0}, dz[2] = {0, 0};
+    for (int64_t t = s0; t < s1; t += 128) {
+        const int cnt = (int)min((int64_t)128, s1 - t);
+        __syncthreads();
+        if (tid < cnt) {
+            const v4 A = src[2 * (t + tid)], B = src[2 * (t + tid) + 1];
+            const real u[3] = {-A.x, -A.y, -A.z};
+            for (int q = 0; q < 3; ++q) {
+                real v = 1;
+                for (int m = 0; m <= P; ++m) {
+                    pw[tid][q][m] = v;
+                    v *= u[q];
                 }
-                sq[tid][0] = A.w;  // qL
-                sq[tid][1] = B.w;  // qY
-                sq[tid][2] = B.x;  // p = w phi n
-                sq[tid][3] = B.y;
-                sq[tid][4] = B.z;
             }
-            __syncthreads();
-            if (k < T) {
-                for (int j = 0; j < cnt; ++j) {
-                    const real px = pw[j][0][kx], py = pw[j][1][ky], pz = pw[j][2][kz];
-                    const real mono = px * py * pz;
-                    // (q + p . grad_u) u^k
-                    real dl = 0;
-                    if (kx) dl += sq[j][2] * real(kx) * pw[j][0][kx - 1] * py * pz;
-                    if (ky) dl += sq[j][3] * real(ky) * px * pw[j][1][ky - 1] * pz;
-                    if (kz) dl += sq[j][4] * real(kz) * px * py * pw[j][2][kz - 1];
-                    accL += sq[j][0] * mono + dl;
-                    accY += sq[j][1] * mono + dl;
+            sq[tid][0] = A.w;  // qL
+            sq[tid][1] = B.w;  // qY
+            sq[tid][2] = B.x;  // p = w phi n
+            sq[tid][3] = B.y;
+            sq[tid][4] = B.z;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (!on[h]) continue;
+            for (int j = 0; j < cnt; ++j) {
+                const real mono = pw[j][0][kx[h]] * pw[j][1][ky[h]] * pw[j][2][kz[h]];
+                qL[h] += sq[j][0] * mono;
+                qY[h] += sq[j][1] * mono;
+                if (low[h]) {
+                    dx[h] += sq[j][2] * mono;
+                    dy[h] += sq[j][3] * mono;
+                    dz[h] += sq[j][4] * mono;
                 }
             }
         }
-        if (k < T) {
-            mom[(int64_t)nd * 2 * T + k] = accL;
-            mom[(int64_t)nd * 2 * T + T + k] = accY;
+    }
+    __syncthreads();
+    for (int h = 0; h < 2; ++h)
+        if (low[h]) {
+            const int k = tid + 128 * h;  // terms of degree < P come first in the graded order
+            sd[0][k] = dx[h];
+            sd[1][k] = dy[h];
+            sd[2][k] = dz[h];
         }
+    __syncthreads();
+    for (int h = 0; h < 2; ++h) {
+        if (!on[h]) continue;
+        const int k = tid + 128 * h;
+        real dl = 0;
+        if (kx[h]) dl += real(kx[h]) * sd[0][idx3[kx[h] - 1][ky[h]][kz[h]]];
+        if (ky[h]) dl += real(ky[h]) * sd[1][idx3[kx[h]][ky[h] - 1][kz[h]]];
+        if (kz[h]) dl += real(kz[h]) * sd[2][idx3[kx[h]][ky[h]][kz[h] - 1]];
+        mom[(int64_t)nd * 2 * T + k] = qL[h] + dl;
+        mom[(int64_t)nd * 2 * T + T + k] = qY[h] + dl;
     }
 }
 

@@ -130,3 +130,33 @@ def test_fp32_mode_energy_error_against_fp64():
             assert er[k] == pytest.approx(e64[k], rel=1e-5)
     finally:
         pgb.pgb_destroy(ctx)
+
+
+def test_lanes_match_the_serial_batch():
+    """Poses solved in concurrent lanes (own stream and host thread each)
+    give the serial batch's energies, across calls that reuse the lanes, a
+    change of charges and a move of the other body."""
+    bodies = _posed_pair()
+    bodies[1]["t"] = np.array([15.0, 0.0, 0.0])
+    bodies[1]["R"] = np.eye(3)
+    Rs = synth.random_rotations(31, 7)
+    ts = np.stack([np.array([0.3 * k, -0.2 * k, 0.1]) for k in range(7)])
+    c1 = gpu_context(bodies, theta=0.5, P=5, leaf_size=16, lanes=1)
+    cl = gpu_context(bodies, theta=0.5, P=5, leaf_size=16, lanes=3)
+    try:
+        for step in range(3):
+            if step == 1:  # new charges: the lanes are copied again
+                q = bodies[0]["q"] * 0.7
+                for c in (c1, cl):
+                    pgb.pgb_set_charges(c, 0, q)
+            if step == 2:  # the other body moves: the lanes follow
+                for c in (c1, cl):
+                    pgb.pgb_set_pose(c, 1, np.eye(3), [16.0, 1.0, 0.0])
+            code1, F1, st1 = pgb.pgb_solve_batch(c1, 0, Rs, ts, pgb.PGB_FP64, 1e-9, 2000, 100)
+            codel, Fl, stl = pgb.pgb_solve_batch(cl, 0, Rs, ts, pgb.PGB_FP64, 1e-9, 2000, 100)
+            assert code1 == 0 and codel == 0
+            np.testing.assert_allclose(Fl, F1, rtol=1e-12, atol=1e-14)
+            assert [s["iterations"] for s in stl] == [s["iterations"] for s in st1]
+    finally:
+        pgb.pgb_destroy(c1)
+        pgb.pgb_destroy(cl)
