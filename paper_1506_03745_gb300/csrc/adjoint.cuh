@@ -198,7 +198,7 @@ __device__ __forceinline__ void m2p_grad(real Rx, real Ry, real Rz, real nx, rea
 // M2P: one block per target group (K warps, as k_p2p_T); the block loads each
 // far node's moments once into shared memory; adds to out.
 template <typename real, int P>
-__global__ void __launch_bounds__(224) k_m2p_T(TArgs a, const typename V4<real>::t* __restrict__ ytg,
+__global__ void __launch_bounds__(224, sizeof(real) == 4 ? 2 : 1) k_m2p_T(TArgs a, const typename V4<real>::t* __restrict__ ytg,
                                                 const typename V4<real>::t* __restrict__ nrm,
                                                 const real* __restrict__ mom) {
     using v4 = typename V4<real>::t;

@@ -589,10 +589,21 @@ int pgb_solve_batch(pgb_ctx* c, int32_t body_id, const double* R, const double* 
         } else {
             first_err = solve_lanes(c, L, body_id, R, t, B, mode, tol, max_iter, restart, F_out, stats);
         }
-        // the body keeps the last pose
-        memcpy(c->bodies[body_id].R, R + 9 * (B - 1), 9 * sizeof(double));
-        memcpy(c->bodies[body_id].t, t + 3 * (B - 1), 3 * sizeof(double));
-        if (L > 1) c->tree_valid = false;
+        // the body keeps the last pose, with its tree built as after a serial batch
+        if (L > 1) {
+            memcpy(c->bodies[body_id].R, R + 9 * (B - 1), 9 * sizeof(double));
+            memcpy(c->bodies[body_id].t, t + 3 * (B - 1), 3 * sizeof(double));
+            c->tree_valid = false;
+            if (!c->order_valid) {
+                upload_bodies(c);
+                build_order(c);
+                c->intra_valid = false;
+            }
+            build_geometry(c);
+            build_lists(c);
+            build_corrections(c);
+            c->tree_valid = true;
+        }
         PGB_CUDA(cudaStreamSynchronize(c->stream));
         if (first_err == PGB_ENOCONV) c->err = "GMRES did not reach tol for at least one pose";
         return first_err;

@@ -246,7 +246,8 @@ struct pgb_ctx {
     pgb::DBuf<double> d_pz;              // its work vector
     bool pc_ready = false;
     int coop_blocks = 0;                 // fused Arnoldi grid: 0 undecided, -1 unavailable
-    pgb::DBuf<unsigned> d_bar;           // its grid barrier state (count, generation, error)
+    pgb::DBuf<unsigned> d_bar;           // its grid barrier state (arrivals, -, error)
+    unsigned bar_base = 0;               // arrivals before the next launch
     double* h_pinned = nullptr;
 
     // upward pass captured as a CUDA graph per precision, replayed on the

@@ -203,32 +203,34 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
-// Grid-wide barrier for a cooperative launch; the wait is bounded (1 s of
-// the global timer): on time-out the barrier records err and every block
-// falls through.
-__device__ __forceinline__ bool grid_sync(GridBar* b, unsigned nblocks) {
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier for a cooperative launch: the arrival counter only grows
+// (a release add per block), and barrier k of a launch waits (acquire loads)
+// until it reaches target = base + (k + 1) * blocks, so no reset and no extra
+// round trip are needed.  The wait is bounded (1 s of the global timer): on
+// time-out the barrier records err and every block falls through.
+__device__ __forceinline__ bool grid_sync(GridBar* b, unsigned target) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned* vgen = &b->gen;
+        red_release_add(&b->count, 1u);
         volatile int* verr = &b->err;
-        const unsigned g0 = *vgen;
-        __threadfence();
-        if (atomicAdd(&b->count, 1u) == nblocks - 1) {
-            atomicExch(&b->count, 0u);
-            __threadfence();
-            atomicAdd(&b->gen, 1u);
-        } else {
-            // poll without sleeping (a barrier normally completes within
-            // microseconds); read the clock every 256 polls
-            const unsigned long long t0 = globaltimer_ns();
-            for (long long it = 1; *vgen == g0 && *verr == 0; ++it) {
-                if ((it & 255) == 0 && (globaltimer_ns() - t0 > PGB_BARRIER_NS || it > (1ll << 26))) {
-                    atomicExch(&b->err, 1);
-                    break;
-                }
+        const unsigned long long t0 = globaltimer_ns();
+        for (long long it = 1;; ++it) {
+            if ((int)(ld_acquire(&b->count) - target) >= 0) break;
+            if (*verr) break;
+            if ((it & 255) == 0 && (globaltimer_ns() - t0 > PGB_BARRIER_NS || it > (1ll << 26))) {
+                atomicExch(&b->err, 1);
+                break;
             }
         }
-        __threadfence();
     }
     __syncthreads();
     return *(volatile int*)&b->err == 0;
@@ -245,6 +247,7 @@ struct ArnoldiArgs {
     double *cs, *sn, *g;
     double* out;    // out[0] = |g_{j+1}|, out[1] = h_{j+1,j}, out[2] = 1 on a barrier time-out
     GridBar* bar;
+    unsigned bar_base;  // arrival count before this launch (5 barriers per launch)
 };
 
 __global__ void __launch_bounds__(512) k_arnoldi(ArnoldiArgs a) {
@@ -257,12 +260,20 @@ __global__ void __launch_bounds__(512) k_arnoldi(ArnoldiArgs a) {
     bool ok = true;
     for (int pass = 0; pass < 2 && ok; ++pass) {
         double* coef = pass ? a.hc : a.h;
-        for (int i = 0; i < m; ++i) {  // block partials of V_i . w
-            const double* v = a.V + i * a.ld;
-            double t = 0;
-            for (int64_t r = r0; r < a.n; r += stride) t += v[r] * a.w[r];
-            t = warp_sum(t);
-            if (lane == 0) shd[i * nw + wi] = t;
+        for (int i0 = 0; i0 < m; i0 += 8) {  // block partials of V_i . w, eight vectors at a time
+            double t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int64_t r = r0; r < a.n; r += stride) {
+                const double wr = a.w[r];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (i0 + u < m) t[u] += a.V[(i0 + u) * a.ld + r] * wr;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) t[u] = warp_sum(t[u]);
+            if (lane == 0)
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (i0 + u < m) shd[(i0 + u) * nw + wi] = t[u];
         }
         __syncthreads();
         for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -270,20 +281,23 @@ __global__ void __launch_bounds__(512) k_arnoldi(ArnoldiArgs a) {
             for (int k = 0; k < nw; ++k) t += shd[i * nw + k];
             a.part[(int64_t)i * nb + blockIdx.x] = t;
         }
-        if (!(ok = grid_sync(a.bar, nb))) break;
+        if (!(ok = grid_sync(a.bar, a.bar_base + (2 * pass + 1) * nb))) break;
         for (int i = blockIdx.x; i < m; i += nb) {  // block i sums coefficient i
             double t = 0;
             for (unsigned b = threadIdx.x; b < nb; b += blockDim.x) t += __ldcg(a.part + (int64_t)i * nb + b);
             t = block_sum(t, shd);
             if (threadIdx.x == 0) coef[i] = t;
         }
-        if (!(ok = grid_sync(a.bar, nb))) break;
+        if (!(ok = grid_sync(a.bar, a.bar_base + (2 * pass + 2) * nb))) break;
         for (int i = threadIdx.x; i < m; i += blockDim.x) shd[i] = __ldcg(coef + i);
         __syncthreads();
         for (int64_t r = r0; r < a.n; r += stride) {
-            double t = 0;
-            for (int i = 0; i < m; ++i) t += shd[i] * a.V[i * a.ld + r];
-            a.w[r] -= t;
+            double t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int i0 = 0; i0 < m; i0 += 8)
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (i0 + u < m) t[u] += shd[i0 + u] * a.V[(i0 + u) * a.ld + r];
+            a.w[r] -= ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
         }
         __syncthreads();
     }
@@ -295,7 +309,7 @@ __global__ void __launch_bounds__(512) k_arnoldi(ArnoldiArgs a) {
         for (int64_t r = r0; r < a.n; r += stride) t += a.w[r] * a.w[r];
         t = block_sum(t, shd);
         if (threadIdx.x == 0) a.part[blockIdx.x] = t;
-        ok = grid_sync(a.bar, nb);
+        ok = grid_sync(a.bar, a.bar_base + 5 * nb);
     }
     if (ok) {
         double t = 0;  // every block forms the norm (nb values)
@@ -373,6 +387,7 @@ static bool arnoldi_fused(pgb_ctx* c, int j, double* w, double* h, double* hc, d
         c->coop_blocks = sms;
         c->d_bar.resize(4);
         PGB_CUDA(cudaMemsetAsync(c->d_bar.p, 0, 16, c->stream));
+        c->bar_base = 0;
     }
     const int nb = c->coop_blocks;
     c->d_red.resize(std::max<size_t>(c->d_red.n, (size_t)nb * (j + 2)));
@@ -390,6 +405,8 @@ static bool arnoldi_fused(pgb_ctx* c, int j, double* w, double* h, double* hc, d
     a.g = g;
     a.out = out;
     a.bar = (GridBar*)c->d_bar.p;
+    a.bar_base = c->bar_base;
+    c->bar_base += 5u * (unsigned)nb;
     void* args[] = {&a};
     const size_t smem = 8 * (size_t)std::max(32, (j + 1) * warps);
     const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_arnoldi, nb, threads, args, smem, c->stream);
@@ -579,6 +596,7 @@ int gmres_op(pgb_ctx* c, int prec, bool transpose, const double* b, double* x, d
             PGB_CUDA(cudaStreamSynchronize(s));
             if (fused && c->h_pinned[2] != 0) {
                 PGB_CUDA(cudaMemsetAsync(c->d_bar.p, 0, 16, s));
+                c->bar_base = 0;
                 fail(PGB_ETIMEOUT, "Arnoldi grid barrier timed out");
             }
             est = c->h_pinned[0];

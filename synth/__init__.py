@@ -21,7 +21,7 @@ import numpy as np
 __all__ = [
     "icosahedron", "icosphere", "geodesic_sphere", "star_radius", "star_surface",
     "star_coefficients", "interior_charges", "random_rotations", "translate",
-    "rotate", "mesh_area", "nu_for_density",
+    "rotate", "mesh_area", "nu_for_density", "brick",
 ]
 
 
@@ -245,3 +245,42 @@ def rotate(xyz, R):
 
 def translate(xyz, t):
     return np.asarray(xyz) + np.asarray(t, dtype=np.float64)
+
+
+def brick(lx: float, ly: float, lz: float, h: float, center=(0.0, 0.0, 0.0)):
+    """Closed surface of an axis-aligned box lx x ly x lz (Angstrom) centred at
+    `center`: each face cut into squares of side close to h (at least one per
+    edge), each square into two triangles; faces share their edge vertices
+    (watertight) and every triangle is counter-clockwise seen from outside."""
+    L = np.array([lx, ly, lz], dtype=float)
+    n = np.maximum(1, np.round(L / h).astype(int))
+    index = {}
+    verts = []
+
+    def vid(ijk):
+        key = tuple(int(c) for c in ijk)
+        if key not in index:
+            index[key] = len(verts)
+            verts.append([key[a] / n[a] * L[a] - 0.5 * L[a] for a in range(3)])
+        return index[key]
+
+    tris = []
+    for axis in range(3):
+        u, w = (axis + 1) % 3, (axis + 2) % 3          # (u, w, axis) is right-handed
+        for side in (0, 1):
+            for a in range(n[u]):
+                for b in range(n[w]):
+                    corner = []
+                    for du, dw in ((0, 0), (1, 0), (1, 1), (0, 1)):
+                        g = [0, 0, 0]
+                        g[axis] = side * n[axis]
+                        g[u] = a + du
+                        g[w] = b + dw
+                        corner.append(vid(g))
+                    q = [corner[0], corner[1], corner[2], corner[3]]
+                    if side == 0:                      # outward normal is -axis: reverse
+                        q = q[::-1]
+                    tris.append([q[0], q[1], q[2]])
+                    tris.append([q[0], q[2], q[3]])
+    v = np.asarray(verts, dtype=np.float64) + np.asarray(center, dtype=np.float64)
+    return v, np.asarray(tris, dtype=np.int32)

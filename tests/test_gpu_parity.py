@@ -276,3 +276,27 @@ def test_upward_graph_replay_matches_plain_launches():
     finally:
         pgb.pgb_destroy(cg)
         pgb.pgb_destroy(cp)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "refine"])
+def test_charged_brick_at_zero_ionic_strength(mode):
+    """Flat faces, edges and corners in the near field, and kappa = 0 (the
+    Yukawa kernels become Laplace's): a sphere molecule over a charged box."""
+    v, f = synth.brick(12.0, 12.0, 3.0, 1.5, center=(0.0, 0.0, -8.0))
+    bodies = spheres(level_mol=2, surface=False)
+    bodies.append(dict(kind="sigma", verts=v, tris=f, eps_in=1.0, qxyz=np.zeros((0, 3)), q=np.zeros(0), bc=0.02))
+    so = oracle_system(bodies, kappa=0.0, theta=0.0)
+    ctx = gpu_context(bodies, kappa=0.0, theta=0.0)
+    try:
+        n = pgb.pgb_num_unknowns(ctx)
+        x = torch.empty(n, dtype=torch.float64, device="cuda")
+        m = pgb.PGB_FP64 if mode == "fp64" else pgb.PGB_FP32_REFINE
+        code, st = pgb.pgb_solve(ctx, m, 1e-10, 2000, 100, x)
+        assert code == 0
+        xo = so.solve()
+        assert np.abs(x.cpu().numpy() - xo).max() / np.abs(xo).max() < 1e-8
+        e, eo = pgb.pgb_energy(ctx, x), energies(so, xo)
+        for k in ("solvation", "surface", "total"):
+            assert e[k] == pytest.approx(eo[k], rel=1e-8, abs=1e-12)
+    finally:
+        pgb.pgb_destroy(ctx)

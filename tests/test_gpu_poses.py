@@ -157,6 +157,12 @@ def test_lanes_match_the_serial_batch():
             assert code1 == 0 and codel == 0
             np.testing.assert_allclose(Fl, F1, rtol=1e-12, atol=1e-14)
             assert [s["iterations"] for s in stl] == [s["iterations"] for s in st1]
+            # both leave the body at the last pose with its tree built
+            assert pgb.pgb_tree_stats(cl)["n_panels"] == pgb.pgb_tree_stats(c1)["n_panels"]
+            _, e1 = _solve_energy(c1)
+            _, el = _solve_energy(cl)
+            assert el["total"] == pytest.approx(e1["total"], rel=1e-12)
+            assert el["total"] == pytest.approx(F1[-1, 3], rel=1e-8)
     finally:
         pgb.pgb_destroy(c1)
         pgb.pgb_destroy(cl)
