@@ -41,7 +41,7 @@ METRIC = "treecode matvecs/sec and GMRES solve ms at 1e-5 energy err, FP32+refin
 UNIT = "matvecs/s"
 WORKLOAD = "two spheres r=4 A, 2 x 20480 panels, sigma=0.05 C/m^2, R=12 A"
 PARAMS = dict(K=7, K_near=19, n_edge=9, P=6, theta=0.5, leaf_size=32, group_size=32, p2p_item=64, m2p_item=64,
-              precond=0, graphs=1, lanes=4)
+              precond=0, graphs=1, lanes=4, overlap=1)
 TOL = 1e-6
 RESTART = 100
 MAX_ITER = 2000
@@ -337,7 +337,7 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_unknowns": n, "theta": PARAMS["theta"], "P": PARAMS["P"],
                    "leaf_size": PARAMS["leaf_size"], "p2p_item": PARAMS["p2p_item"], "m2p_item": PARAMS["m2p_item"],
-                   "precond": PARAMS["precond"], "K": PARAMS["K"], "tol": TOL, "restart": RESTART,
+                   "precond": PARAMS["precond"], "overlap": PARAMS["overlap"], "K": PARAMS["K"], "tol": TOL, "restart": RESTART,
                    "step": "full tree build (sort, octree, lists, near field; nothing cached) + "
                            "FP32/FP64-refined GMRES solve + energies",
                    "l2": "flushed (512 MB write) before every timed step",
@@ -485,6 +485,23 @@ def run_gradient(args):
     pgb.pgb_destroy(ctx)
 
 
+def orientation_landscape(F, n_orient, n_gap, T=300.0):
+    """Boltzmann weights of the orientations at each gap (poses ordered
+    orientation-major, gap-minor): probability of the most likely
+    orientation, its index, and the orientation-averaged free energy
+    -kT ln <exp(-F/kT)> (kcal/mol) per gap."""
+    kT = 0.0019872043 * T  # kcal/mol
+    F = np.asarray(F, dtype=float).reshape(n_orient, n_gap)
+    out = []
+    for gi in range(n_gap):
+        f = F[:, gi]
+        z = np.exp(-(f - f.min()) / kT)
+        p = z / z.sum()
+        out.append({"gap_index": gi, "most_likely_orientation": int(p.argmax()), "p_max": float(p.max()),
+                    "free_energy_kcal_mol": float(f.min() - kT * math.log(z.mean()))})
+    return out
+
+
 def run_poses(args):
     """Config subset: one synthetic molecule (~5000 panels, 900 charges) in
     `--poses` orientations x 4 gaps (6, 8, 10, 14 A) near a sphere r = 40 A
@@ -524,7 +541,51 @@ def run_poses(args):
                       "energy_rel_err_vs_fp64_first_2_poses": err, "status": code,
                       "stage_ms_per_pose": {k: v[0] / B for k, v in tim.items() if k != "kernel_launches" and v[0]},
                       "kernel_launches_per_pose": tim["kernel_launches"] / B,
-                      "F_total_range_kcal_mol": [float(F[:, 3].min()), float(F[:, 3].max())]}), flush=True)
+                      "F_total_range_kcal_mol": [float(F[:, 3].min()), float(F[:, 3].max())],
+                      "orientation_landscape": orientation_landscape(F[:, 3], args.poses, 4)}), flush=True)
+    pgb.pgb_destroy(ctx)
+
+
+def run_brick(args):
+    """Flat-faced charged body at zero ionic strength: the star molecule
+    (2 panels/A^2, 900 charges) 10 A above a 100 x 100 x 10 A box with
+    sigma -0.05 C/m^2 (squares of 1.4 A, two triangles each), kappa = 0.
+    Step = tree build + FP32/FP64-refined solve + energies; the FP64 solve of
+    the same step beside it."""
+    import torch
+    import synth
+    import paper_1506_03745_gb300 as pgb
+    from paper_1506_03745_gb300.context import context as gpu_context
+    mol = star_bodies(2)
+    zmin = float(mol["verts"][:, 2].min())
+    v, f = synth.brick(100.0, 100.0, 10.0, 1.4, center=(0.0, 0.0, zmin - 10.0 - 5.0))
+    srf = dict(kind="sigma", verts=v, tris=f, eps_in=1.0, qxyz=np.zeros((0, 3)), q=np.zeros(0), bc=-0.05)
+    ctx = gpu_context([mol, srf], kappa=0.0, **PARAMS)
+    n = pgb.pgb_num_unknowns(ctx)
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+
+    def step(mode):
+        pgb.pgb_tree_reset(ctx)
+        pgb.pgb_tree_build(ctx)
+        code, st = pgb.pgb_solve(ctx, mode, TOL, MAX_ITER, RESTART, x)
+        return code, st, pgb.pgb_energy(ctx, x)
+
+    for _ in range(args.warmup):
+        step(pgb.PGB_FP32_REFINE)
+    ms, res = [], None
+    for _ in range(args.steps):
+        res, t = _timed(lambda: step(pgb.PGB_FP32_REFINE))
+        ms.append(t)
+    (c64, st64, e64), t64 = _timed(lambda: step(pgb.PGB_FP64))
+    code, st, e = res
+    print(json.dumps({"workload": "star molecule (2 panels/A^2, 900 charges) 10 A above a 100 x 100 x 10 A box "
+                                  "(sigma -0.05 C/m^2), kappa = 0",
+                      "panels": pgb.pgb_tree_stats(ctx)["n_panels"], "brick_panels": int(len(f)),
+                      "ms_per_step": statistics.median(ms), "fp64_ms": t64, "iterations": st["iterations"],
+                      "fp64_iterations": st64["iterations"], "status": [code, c64],
+                      "energies_kcal_mol": e,
+                      "energy_rel_err_vs_fp64": {k: abs(e[k] - e64[k]) / max(abs(e64[k]), 1e-300)
+                                                 for k in ("solvation", "surface", "total")}}), flush=True)
     pgb.pgb_destroy(ctx)
 
 
@@ -593,7 +654,7 @@ def run_matvec(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--mode", default="solve", choices=["solve", "matvec"])
-    ap.add_argument("--workload", default="two_sphere", choices=["two_sphere", "star", "gradient", "poses"])
+    ap.add_argument("--workload", default="two_sphere", choices=["two_sphere", "star", "gradient", "poses", "brick"])
     ap.add_argument("--poses", type=int, default=8, help="orientations for --workload poses")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--gpus", type=int, default=1)
@@ -609,10 +670,11 @@ def main():
     ap.add_argument("--precond", type=int, default=None, help="1: block-diagonal GMRES preconditioner")
     ap.add_argument("--graphs", type=int, default=None, help="0: plain launches instead of the upward-pass graph")
     ap.add_argument("--lanes", type=int, default=None, help="concurrent pose lanes of pgb_solve_batch")
+    ap.add_argument("--overlap", type=int, default=None, help="0: FP64 residual after the inner solve")
     args = ap.parse_args()
     for k, v in (("leaf_size", args.leaf), ("P", args.P), ("theta", args.theta), ("p2p_item", args.p2p_item),
                  ("m2p_item", args.m2p_item), ("precond", args.precond),
-                 ("graphs", args.graphs), ("lanes", args.lanes)):
+                 ("graphs", args.graphs), ("lanes", args.lanes), ("overlap", args.overlap)):
         if v is not None:
             PARAMS[k] = v
     if args.impl == "reference":
@@ -621,6 +683,8 @@ def main():
         run_star(args)
     elif args.workload == "gradient":
         run_gradient(args)
+    elif args.workload == "brick":
+        run_brick(args)
     elif args.workload == "poses":
         run_poses(args)
     elif args.mode == "matvec":

@@ -73,6 +73,11 @@ typedef struct pgb_params {
                              once per tree as a CUDA graph and replayed; 0: plain launches */
     int32_t lanes;        /* pgb_solve_batch: poses in flight at once, 1..16 (0 = 4); each lane is a copy
                              of the context with its own CUDA stream and host thread, kept between calls */
+    int32_t overlap;      /* PGB_FP32_REFINE: 1 (default) starts the FP64 product of the outer residual on
+                             a side stream at the inner iterate whose residual is 1e-2 of its right-hand
+                             side (1e4 tol if smaller) and finishes the residual with the FP32 product of
+                             the remaining change, so the FP64 work overlaps the FP32 iterations; 0: the
+                             FP64 product of the final iterate, after the inner solve */
 } pgb_params;
 
 typedef struct pgb_solve_stats {
@@ -126,7 +131,7 @@ typedef struct pgb_stage_times {
 
 /* Create a context on the current CUDA device.  p may be NULL (defaults:
  * K=7, K_near=19, n_edge=9, P=6, theta=0.5, leaf_size=32, group_size=32,
- * p2p_item=64, m2p_item=64, precond=0, graphs=1, lanes=4).
+ * p2p_item=64, m2p_item=64, precond=0, graphs=1, lanes=4, overlap=1).
  * cuda_stream is a cudaStream_t (NULL = legacy default stream).  Returns
  * PGB_EINVAL for out-of-range parameters. */
 int pgb_create(struct pgb_ctx** ctx, const pgb_params* p, void* cuda_stream);
@@ -286,12 +291,6 @@ int pgb_tree_export(struct pgb_ctx* ctx, int32_t* perm, int64_t* near_off, int32
  * NULL pointer with n > 0; PGB_ECUDA on a CUDA error. */
 int pgb_math_check(const double* x, int64_t n, double* out);
 
-/* Diagnostic of the bounded grid barrier of the fused Arnoldi kernel: one
- * block of 32 threads waits at a barrier sized for expected_blocks (1 or 2).
- * With 1 the barrier completes (*timed_out = 0); with 2 nothing completes it
- * and the wait gives up after 1 s (*timed_out = 1), leaving the context
- * usable.  Synchronous, current device.  PGB_EINVAL for other arguments. */
-int pgb_barrier_check(int32_t expected_blocks, int32_t* timed_out);
 
 #ifdef __cplusplus
 }

@@ -21,7 +21,8 @@ c_i32, c_i64, c_dbl, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, cty
 class pgb_params(ctypes.Structure):
     _fields_ = [("K", c_i32), ("K_near", c_i32), ("n_edge", c_i32), ("P", c_i32), ("theta", c_dbl),
                 ("leaf_size", c_i32), ("group_size", c_i32), ("p2p_item", c_i32), ("m2p_item", c_i32),
-                ("precond", c_i32), ("graphs", c_i32), ("lanes", c_i32)]
+                ("precond", c_i32), ("graphs", c_i32), ("lanes", c_i32),
+                ("overlap", c_i32)]
 
 
 class pgb_solve_stats(ctypes.Structure):
@@ -84,7 +85,6 @@ _SIGS = {
     "pgb_timing": (c_i32, [c_vp, c_i32, ctypes.POINTER(pgb_stage_times)]),
     "pgb_energy_noalloc": (c_i32, [c_vp, c_vp, ctypes.POINTER(pgb_energies)]),
     "pgb_math_check": (c_i32, [c_vp, c_i64, c_vp]),
-    "pgb_barrier_check": (c_i32, [c_i32, ctypes.POINTER(c_i32)]),
 }
 
 
@@ -322,10 +322,3 @@ def pgb_math_check(x):
     out = np.zeros((len(x), 5), np.float64)
     _check(None, lib().pgb_math_check(x.ctypes.data_as(c_vp), len(x), out.ctypes.data_as(c_vp)))
     return out
-
-
-def pgb_barrier_check(expected_blocks):
-    """Returns (status, timed_out) of the bounded grid-barrier probe."""
-    t = c_i32(-1)
-    st = lib().pgb_barrier_check(expected_blocks, ctypes.byref(t))
-    return st, t.value

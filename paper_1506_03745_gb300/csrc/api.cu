@@ -13,7 +13,6 @@
 namespace pgb {
 thread_local cudaStream_t g_alloc_stream = nullptr;
 thread_local bool g_alloc_scoped = false;
-int barrier_probe(int expected, int* timed_out);
 void cuda_check(cudaError_t e, const char* what) {
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
@@ -108,6 +107,7 @@ static int check_params(const pgb_params* p, std::string& why) {
     else if (p->precond != 0 && p->precond != 1) why = "precond must be 0 or 1";
     else if (p->graphs != 0 && p->graphs != 1) why = "graphs must be 0 or 1";
     else if (p->lanes < 0 || p->lanes > 16) why = "lanes must be in 1..16 (0 = default)";
+    else if (p->overlap != 0 && p->overlap != 1) why = "overlap must be 0 or 1";
     else return PGB_OK;
     return PGB_EINVAL;
 }
@@ -155,7 +155,7 @@ static void destroy_lanes(pgb_ctx* c) {
 static bool same_params(const pgb_params& a, const pgb_params& b) {
     return a.K == b.K && a.K_near == b.K_near && a.n_edge == b.n_edge && a.P == b.P && a.theta == b.theta &&
            a.leaf_size == b.leaf_size && a.group_size == b.group_size && a.p2p_item == b.p2p_item &&
-           a.m2p_item == b.m2p_item && a.precond == b.precond && a.graphs == b.graphs;
+           a.m2p_item == b.m2p_item && a.precond == b.precond && a.graphs == b.graphs && a.overlap == b.overlap;
 }
 
 // Lane contexts: copies of c (bodies, solvent, parameters) with their own
@@ -273,6 +273,7 @@ int pgb_default_params(pgb_params* p) {
     p->precond = 0;
     p->graphs = 1;
     p->lanes = 4;
+    p->overlap = 1;
     return PGB_OK;
 }
 
@@ -329,6 +330,12 @@ int pgb_destroy(pgb_ctx* c) {
         if (gr.exec) cudaGraphExecDestroy(gr.exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    if (c->side_stream) {
+        cudaStreamSynchronize(c->side_stream);
+        cudaStreamDestroy(c->side_stream);
+        cudaEventDestroy(c->ev_fork);
+        cudaEventDestroy(c->ev_join);
+    }
     cudaStream_t own = c->owns_stream ? c->stream : nullptr;
     delete c;  // device buffers are freed in the order of their stream
     if (own) {
@@ -782,15 +789,6 @@ int pgb_tree_export(pgb_ctx* c, int32_t* perm, int64_t* near_off, int32_t* near_
         PGB_CUDA(cudaStreamSynchronize(s));
         return PGB_OK;
     });
-}
-
-int pgb_barrier_check(int32_t expected_blocks, int32_t* timed_out) {
-    if (expected_blocks < 1 || expected_blocks > 2 || !timed_out) return PGB_EINVAL;
-    try {
-        return pgb::barrier_probe(expected_blocks, timed_out);
-    } catch (const pgb::Error& e) {
-        return e.code;
-    }
 }
 
 int pgb_math_check(const double* x, int64_t n, double* out) {

@@ -206,6 +206,25 @@ static void upward_graph(pgb_ctx* c, bool f32, const UpArgs& up, const EvalArgs&
     PGB_CUDA(cudaGraphLaunch(gr.exec, c->stream));
 }
 
+// Sizes every buffer a product of this precision writes (so that a product
+// on another stream allocates nothing).
+void reserve_product(pgb_ctx* c, int precision) {
+    const int pi = precision == PGB_FP32 ? 0 : 1;
+    const int T = n_terms(c->p.P);
+    const int64_t nsrc = c->n_pan * c->p.K;
+    c->d_dens[pi].resize(3 * c->n_pan);
+    c->d_Up[pi].resize(64 * std::max<int64_t>(c->n_pitems, 1));
+    c->d_Uf[pi].resize(64 * std::max<int64_t>(c->n_fitems, 1));
+    c->d_work.resize(2);
+    if (pi == 0) {
+        c->d_src32.resize(2 * nsrc);
+        c->d_mom32.resize((size_t)c->n_nodes * 2 * T);
+    } else {
+        c->d_src64.resize(2 * nsrc);
+        c->d_mom64.resize((size_t)c->n_nodes * 2 * T);
+    }
+}
+
 void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode, const int* known_mask) {
     const bool known_only = mode == 1;
     if (!c->tree_valid) fail(PGB_ESTATE, "pgb_tree_build has not run for the current bodies and poses");
@@ -218,9 +237,15 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
     const int P = c->p.P;
     const int T = n_terms(P);
     const int64_t nsrc = g.n_src;
-    c->d_dens.resize(3 * c->n_pan);
-    c->d_Up.resize(64 * std::max<int64_t>(c->n_pitems, 1));
-    c->d_Uf.resize(64 * std::max<int64_t>(c->n_fitems, 1));
+    // per-precision work buffers: an FP64 product may run on a side stream
+    // while FP32 products go on
+    const int pi = precision == PGB_FP32 ? 0 : 1;
+    auto& dens = c->d_dens[pi];
+    auto& Up = c->d_Up[pi];
+    auto& Uf = c->d_Uf[pi];
+    dens.resize(3 * c->n_pan);
+    Up.resize(64 * std::max<int64_t>(c->n_pitems, 1));
+    Uf.resize(64 * std::max<int64_t>(c->n_fitems, 1));
     UpArgs up;
     up.n_leaves = c->n_leaves;
     up.leaf_node = c->d_leaf_node; up.nstart = c->d_node_start; up.nend = c->d_node_end;
@@ -255,8 +280,17 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
     ev.fitem_group = c->d_fitem_group;
     ev.p2p_item = c->p.p2p_item;
     ev.m2p_item = c->p.m2p_item;
-    ev.Up = c->d_Up;
-    ev.Uf = c->d_Uf;
+    ev.Up = Up;
+    ev.Uf = Uf;
+    ev.p2p_work = ev.m2p_work = nullptr;
+    ev.persist_blocks = 0;
+    if (c->persist_blocks > 0) {  // side-stream product: a few resident blocks per SM take items
+        c->d_work.resize(2);
+        PGB_CUDA(cudaMemsetAsync(c->d_work.p, 0, 16, s));
+        ev.p2p_work = c->d_work.p;
+        ev.m2p_work = c->d_work.p + 1;
+        ev.persist_blocks = c->persist_blocks;
+    }
     const bool f32 = precision == PGB_FP32;
     if (f32) {
         c->d_src32.resize(2 * nsrc);
@@ -269,10 +303,10 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
         StageTimer tm(c, PGB_STAGE_SOURCES + (f32 ? 0 : PGB_STAGE_FP64));
         if (f32)
             k_src_prep<float><<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, x, mode, c->d_y32, c->d_src32,
-                                                                  c->d_dens, c->eps_out);
+                                                                  dens, c->eps_out);
         else
             k_src_prep<double><<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, x, mode, c->d_y64, c->d_src64,
-                                                                   c->d_dens, c->eps_out);
+                                                                   dens, c->eps_out);
         PGB_CUDA(cudaGetLastError());
         PGB_LAUNCHED(c, 1);
     }
@@ -288,8 +322,8 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
     }
     {
         StageTimer tm(c, PGB_STAGE_ASSEMBLE + (f32 ? 0 : PGB_STAGE_FP64));
-        Parts u{c->d_pan_group, c->d_group_start, c->d_pitem_off, c->d_fitem_off, c->d_Up, c->d_Uf};
-        k_assemble<<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, u, c->d_dens, c->d_corr_off, c->d_corr_j,
+        Parts u{c->d_pan_group, c->d_group_start, c->d_pitem_off, c->d_fitem_off, Up, Uf};
+        k_assemble<<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, u, dens, c->d_corr_off, c->d_corr_j,
                                                        c->d_corr_val, c->d_xcorr_off, c->d_xcorr_j, c->d_xcorr_val,
                                                        mode, y);
         PGB_CUDA(cudaGetLastError());

@@ -230,11 +230,11 @@ struct pgb_ctx {
     // matvec work buffers
     pgb::DBuf<float4> d_src32;           // 2 per point
     pgb::DBuf<pgb::dbl4> d_src64;
-    pgb::DBuf<double> d_dens;            // 3 per sorted panel: psiL, psiY, phi
+    pgb::DBuf<double> d_dens[2];            // 3 per sorted panel: psiL, psiY, phi
     pgb::DBuf<float> d_mom32;            // 2*T per node
     pgb::DBuf<double> d_mom64;
     pgb::DBuf<double> d_phi_part;        // chunk partial sums of phi_reac (few charges)
-    pgb::DBuf<double> d_Up, d_Uf;        // P2P / M2P partial sums: 64 per work item (32 L, then 32 Y)
+    pgb::DBuf<double> d_Up[2], d_Uf[2];        // P2P / M2P partial sums: 64 per work item (32 L, then 32 Y)
     pgb::DBuf<double> d_xtmp, d_ytmp;    // FP64 staging for FP32 matvec API
     // scratch
     pgb::DBuf<int64_t> d_scan_tmp;
@@ -245,9 +245,12 @@ struct pgb_ctx {
     pgb::DBuf<pgb::dbl4> d_pc;           // block-diagonal preconditioner, per sorted panel
     pgb::DBuf<double> d_pz;              // its work vector
     bool pc_ready = false;
-    int coop_blocks = 0;                 // fused Arnoldi grid: 0 undecided, -1 unavailable
-    pgb::DBuf<unsigned> d_bar;           // its grid barrier state (arrivals, -, error)
-    unsigned bar_base = 0;               // arrivals before the next launch
+    int arn_blocks = 0;                  // grid of the Arnoldi-step kernels (0: not yet set)
+    int persist_blocks = 0;              // > 0: products launch P2P/M2P persistently with this grid
+    pgb::DBuf<unsigned long long> d_work;  // their item counters
+    cudaStream_t side_stream = nullptr;  // FP64 residual overlapped with FP32 iterations
+    pgb::DBuf<double> d_xspec, d_r64;    // its iterate (and x - x*), its product
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double* h_pinned = nullptr;
 
     // upward pass captured as a CUDA graph per precision, replayed on the
@@ -311,8 +314,18 @@ void apply_full(pgb_ctx* c, const double* x, double* y, int precision);
 void coulomb_rows(pgb_ctx* c, double* b);
 void grad(pgb_ctx* c, const double* x, int precision, double tol, int max_iter, int restart, double* dq, double* dbc,
           double* dt, pgb_solve_stats* st);
+// Speculation hook of gmres_op: the first time the residual estimate falls to
+// abs_thresh (and not yet to the tolerance) the current iterate is formed in
+// xs and fork(xs) is called; fork may start work on another stream.
+struct GmresSpec {
+    double abs_thresh = 0;
+    double* xs = nullptr;
+    bool forked = false;
+    void (*fork)(pgb_ctx* c, const double* xs, void* user) = nullptr;
+    void* user = nullptr;
+};
 int gmres_op(pgb_ctx* c, int prec, bool transpose, const double* b, double* x, double abs_tol, int max_it,
-             int restart, int* matvecs, double* est_out, bool x_zero);
+             int restart, int* matvecs, double* est_out, bool x_zero, GmresSpec* spec = nullptr);
 double vec_dot(pgb_ctx* c, const double* a, const double* b);
 double energy_unit_kcal();
 void phi_reac(pgb_ctx* c, const double* x, double* out);
@@ -320,6 +333,7 @@ void phi_reac(pgb_ctx* c, const double* x, double* out);
 void build_rhs(pgb_ctx* c, double* b, int precision);
 int solve(pgb_ctx* c, int mode, double tol, int max_iter, int restart, double* x, pgb_solve_stats* st);
 void precond_prepare(pgb_ctx* c);
+void reserve_product(pgb_ctx* c, int precision);
 // energy (energy.cu)
 void energies(pgb_ctx* c, const double* x, pgb_energies* e, pgb_energies* per_body);
 void energies_noalloc(pgb_ctx* c, const double* x, pgb_energies* e);

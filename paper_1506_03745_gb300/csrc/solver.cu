@@ -183,215 +183,169 @@ __global__ void k_init_g(double* g, int m1, const double* beta) {
     if (i < m1) g[i] = (i == 0) ? *beta : 0.0;
 }
 
-// ---------------------------------------------------------------- fused Arnoldi step
-// One cooperative launch per GMRES iteration does the whole CGS2 step of
-// column j: two passes of (V_i . w for i <= j; w -= sum_i h_i V_i), the norm,
-// v_{j+1} = w / |w| and the Givens update, with a grid barrier between the
-// phases that exchange data between blocks.  Every thread keeps the same rows
-// in every phase, so w and v_{j+1} need no barrier; values written by other
-// blocks are read with ld.global.cg (L2, never a stale L1 line).
-struct GridBar {
-    unsigned count, gen;
-    int err, pad;
-};
+// ---------------------------------------------------------------- Arnoldi step in four launches
+// The CGS2 step of column j without grid-wide barriers: every block keeps the
+// same rows r = blockIdx.x * blockDim.x + threadIdx.x + k * stride in every
+// launch, so w and v_{j+1} are only ever touched by their owner; the only
+// data crossing blocks are the per-block partial sums, which each block of
+// the next launch reduces for itself (in the same fixed order everywhere).
+//   k_arn_dot:    part[i][b] = (V_i . w) over block b's rows
+//   k_arn_update: c_i = sum_b part[i][b]; w -= sum_i c_i V_i; (pass 1) the
+//                 partials of the second pass, (pass 2) of |w|^2
+//   k_arn_finish: |w|, v_{j+1} = w / |w|, Givens step (block 0)
+#define ARN_BLOCKS_PER_SM 2
+#define ARN_THREADS 256
 
-#define PGB_BARRIER_NS 1000000000ull  // 1 s
-
-__device__ __forceinline__ unsigned long long globaltimer_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Grid-wide barrier for a cooperative launch: the arrival counter only grows
-// (a release add per block), and barrier k of a launch waits (acquire loads)
-// until it reaches target = base + (k + 1) * blocks, so no reset and no extra
-// round trip are needed.  The wait is bounded (1 s of the global timer): on
-// time-out the barrier records err and every block falls through.
-__device__ __forceinline__ bool grid_sync(GridBar* b, unsigned target) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        red_release_add(&b->count, 1u);
-        volatile int* verr = &b->err;
-        const unsigned long long t0 = globaltimer_ns();
-        for (long long it = 1;; ++it) {
-            if ((int)(ld_acquire(&b->count) - target) >= 0) break;
-            if (*verr) break;
-            if ((it & 255) == 0 && (globaltimer_ns() - t0 > PGB_BARRIER_NS || it > (1ll << 26))) {
-                atomicExch(&b->err, 1);
-                break;
-            }
-        }
-    }
-    __syncthreads();
-    return *(volatile int*)&b->err == 0;
-}
-
-struct ArnoldiArgs {
+struct ArnArgs {
     double* V;      // basis, column i at V + i * ld
     int64_t ld, n;
-    int j;          // the new column's index
-    double* w;      // A v_j on entry; destroyed
-    double* h;      // column j of H (m + 1 entries)
-    double* hc;     // second-pass coefficients (j + 1)
-    double* part;   // nb * (j + 1) block partial sums
+    int j;          // the new column's index (m = j + 1 coefficients)
+    double* w;      // A v_j on entry
+    double* h;      // column j of H
+    double* hc;     // second-pass coefficients
+    double* part;   // nb * (m + 1) partial sums, row i at part + i * nb
+    double* part2;  // second buffer (the next launch's partials)
     double *cs, *sn, *g;
-    double* out;    // out[0] = |g_{j+1}|, out[1] = h_{j+1,j}, out[2] = 1 on a barrier time-out
-    GridBar* bar;
-    unsigned bar_base;  // arrival count before this launch (5 barriers per launch)
+    double* out;    // out[0] = |g_{j+1}|, out[1] = h_{j+1,j}
 };
 
-__global__ void __launch_bounds__(512) k_arnoldi(ArnoldiArgs a) {
-    extern __shared__ double shd[];  // max(32, m * warps) doubles
-    const int m = a.j + 1;
+// Block partials of V_i . w (i < m) over this block's rows, eight vectors at a time.
+__device__ __forceinline__ void arn_block_dots(const ArnArgs& a, int m, double* part, double* shd) {
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const unsigned nb = gridDim.x;
     const int64_t stride = (int64_t)nb * blockDim.x;
     const int64_t r0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    bool ok = true;
-    for (int pass = 0; pass < 2 && ok; ++pass) {
-        double* coef = pass ? a.hc : a.h;
-        for (int i0 = 0; i0 < m; i0 += 8) {  // block partials of V_i . w, eight vectors at a time
-            double t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            for (int64_t r = r0; r < a.n; r += stride) {
-                const double wr = a.w[r];
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (i0 + u < m) t[u] += a.V[(i0 + u) * a.ld + r] * wr;
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) t[u] = warp_sum(t[u]);
-            if (lane == 0)
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (i0 + u < m) shd[(i0 + u) * nw + wi] = t[u];
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            double t = 0;
-            for (int k = 0; k < nw; ++k) t += shd[i * nw + k];
-            a.part[(int64_t)i * nb + blockIdx.x] = t;
-        }
-        if (!(ok = grid_sync(a.bar, a.bar_base + (2 * pass + 1) * nb))) break;
-        for (int i = blockIdx.x; i < m; i += nb) {  // block i sums coefficient i
-            double t = 0;
-            for (unsigned b = threadIdx.x; b < nb; b += blockDim.x) t += __ldcg(a.part + (int64_t)i * nb + b);
-            t = block_sum(t, shd);
-            if (threadIdx.x == 0) coef[i] = t;
-        }
-        if (!(ok = grid_sync(a.bar, a.bar_base + (2 * pass + 2) * nb))) break;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) shd[i] = __ldcg(coef + i);
-        __syncthreads();
+    for (int i0 = 0; i0 < m; i0 += 8) {
+        double t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int64_t r = r0; r < a.n; r += stride) {
-            double t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            for (int i0 = 0; i0 < m; i0 += 8)
+            const double wr = a.w[r];
 #pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (i0 + u < m) t[u] += shd[i0 + u] * a.V[(i0 + u) * a.ld + r];
-            a.w[r] -= ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
+            for (int u = 0; u < 8; ++u)
+                if (i0 + u < m) t[u] += a.V[(i0 + u) * a.ld + r] * wr;
         }
-        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 8; ++u) t[u] = warp_sum(t[u]);
+        if (lane == 0)
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (i0 + u < m) shd[(i0 + u) * nw + wi] = t[u];
     }
-    double nrm = 0;
-    if (ok) {
-        if (blockIdx.x == 0)  // H column: first pass + correction (read after the barrier)
-            for (int i = threadIdx.x; i < m; i += blockDim.x) a.h[i] = __ldcg(a.h + i) + __ldcg(a.hc + i);
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
         double t = 0;
-        for (int64_t r = r0; r < a.n; r += stride) t += a.w[r] * a.w[r];
-        t = block_sum(t, shd);
-        if (threadIdx.x == 0) a.part[blockIdx.x] = t;
-        ok = grid_sync(a.bar, a.bar_base + 5 * nb);
+        for (int k = 0; k < nw; ++k) t += shd[i * nw + k];
+        part[(int64_t)i * nb + blockIdx.x] = t;
     }
-    if (ok) {
-        double t = 0;  // every block forms the norm (nb values)
-        for (unsigned b = threadIdx.x; b < nb; b += blockDim.x) t += __ldcg(a.part + b);
-        t = block_sum(t, shd);
-        if (threadIdx.x == 0) shd[0] = sqrt(t);
-        __syncthreads();
-        nrm = shd[0];
-        double* vn = a.V + (int64_t)(a.j + 1) * a.ld;
-        for (int64_t r = r0; r < a.n; r += stride) vn[r] = nrm > 0 ? a.w[r] / nrm : 0.0;
+}
+
+// c_i = sum_b part[i][b] for i < m into shared memory (one warp per i, lanes
+// over b in a fixed order, then a fixed shuffle tree).
+__device__ __forceinline__ void arn_reduce(const double* part, int m, double* coef) {
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned nb = gridDim.x;
+    for (int i = wi; i < m; i += nw) {
+        double t = 0;
+        for (unsigned b = lane; b < nb; b += 32) t += part[(int64_t)i * nb + b];
+        t = warp_sum(t);
+        if (lane == 0) coef[i] = t;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (ok) {  // Givens step on column j (as k_givens)
-            double* h = a.h;
-            h[a.j + 1] = nrm;
-            for (int i = 0; i < a.j; ++i) {
-                const double x = a.cs[i] * h[i] + a.sn[i] * h[i + 1];
-                const double y = -a.sn[i] * h[i] + a.cs[i] * h[i + 1];
-                h[i] = x;
-                h[i + 1] = y;
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(ARN_THREADS) k_arn_dot(ArnArgs a) {
+    extern __shared__ double shd[];
+    arn_block_dots(a, a.j + 1, a.part, shd);
+}
+
+// pass 0: coefficients into h; pass 1: into hc and h += hc.  Then w -= sum
+// c_i V_i on this block's rows and the partials of the next step (pass 0:
+// the second-pass dots; pass 1: |w|^2 in part2[b]).
+__global__ void __launch_bounds__(ARN_THREADS) k_arn_update(ArnArgs a, int pass) {
+    extern __shared__ double shd[];  // m coefficients, then the dot scratch
+    const int m = a.j + 1;
+    double* coef = shd;
+    double* scratch = shd + ((m + 31) & ~31);
+    arn_reduce(pass ? a.part2 : a.part, m, coef);
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            if (pass) {
+                a.hc[i] = coef[i];
+                a.h[i] += coef[i];
+            } else {
+                a.h[i] = coef[i];
             }
-            a.out[1] = h[a.j + 1];
-            const double p = h[a.j], q = h[a.j + 1];
-            const double r = hypot(p, q);
-            const double c = r > 0 ? p / r : 1.0, sv = r > 0 ? q / r : 0.0;
-            a.cs[a.j] = c;
-            a.sn[a.j] = sv;
-            h[a.j] = r;
-            h[a.j + 1] = 0;
-            a.g[a.j + 1] = -sv * a.g[a.j];
-            a.g[a.j] = c * a.g[a.j];
-            a.out[0] = fabs(a.g[a.j + 1]);
         }
-        a.out[2] = ok ? 0.0 : 1.0;
+    const unsigned nb = gridDim.x;
+    const int64_t stride = (int64_t)nb * blockDim.x;
+    const int64_t r0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double sq = 0;
+    for (int64_t r = r0; r < a.n; r += stride) {
+        double t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int i0 = 0; i0 < m; i0 += 8)
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (i0 + u < m) t[u] += coef[i0 + u] * a.V[(i0 + u) * a.ld + r];
+        const double wr = a.w[r] - (((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7])));
+        a.w[r] = wr;
+        sq += wr * wr;
+    }
+    if (pass == 0) {
+        __syncthreads();
+        arn_block_dots(a, m, a.part2, scratch);
+    } else {
+        sq = block_sum(sq, scratch);
+        if (threadIdx.x == 0) a.part[blockIdx.x] = sq;
     }
 }
 
-// One block waits at a barrier sized for `expected` blocks: with expected > 1
-// nothing ever completes it, so the bounded wait must give up and say so.
-__global__ void k_barrier_probe(GridBar* b, unsigned expected, int* timed_out) {
-    const bool ok = grid_sync(b, expected);
-    if (threadIdx.x == 0) *timed_out = ok ? 0 : 1;
+__global__ void __launch_bounds__(ARN_THREADS) k_arn_finish(ArnArgs a) {
+    extern __shared__ double shd[];
+    const unsigned nb = gridDim.x;
+    double t = 0;
+    for (unsigned b = threadIdx.x; b < nb; b += blockDim.x) t += a.part[b];
+    t = block_sum(t, shd);
+    if (threadIdx.x == 0) shd[32] = sqrt(t);
+    __syncthreads();
+    const double nrm = shd[32];
+    const int64_t stride = (int64_t)nb * blockDim.x;
+    double* vn = a.V + (int64_t)(a.j + 1) * a.ld;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < a.n; r += stride)
+        vn[r] = nrm > 0 ? a.w[r] / nrm : 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {  // Givens step on column j (as k_givens)
+        double* h = a.h;
+        h[a.j + 1] = nrm;
+        for (int i = 0; i < a.j; ++i) {
+            const double x = a.cs[i] * h[i] + a.sn[i] * h[i + 1];
+            const double y = -a.sn[i] * h[i] + a.cs[i] * h[i + 1];
+            h[i] = x;
+            h[i + 1] = y;
+        }
+        a.out[1] = h[a.j + 1];
+        const double p = h[a.j], q = h[a.j + 1];
+        const double r = hypot(p, q);
+        const double c = r > 0 ? p / r : 1.0, sv = r > 0 ? q / r : 0.0;
+        a.cs[a.j] = c;
+        a.sn[a.j] = sv;
+        h[a.j] = r;
+        h[a.j + 1] = 0;
+        a.g[a.j + 1] = -sv * a.g[a.j];
+        a.g[a.j] = c * a.g[a.j];
+        a.out[0] = fabs(a.g[a.j + 1]);
+    }
 }
 
-int barrier_probe(int expected, int* timed_out) {
-    DBuf<unsigned> bar;
-    DBuf<int> flag;
-    bar.resize(4);
-    flag.resize(1);
-    PGB_CUDA(cudaMemset(bar.p, 0, 16));
-    k_barrier_probe<<<1, 32>>>((GridBar*)bar.p, (unsigned)expected, flag.p);
-    PGB_CUDA(cudaGetLastError());
-    PGB_CUDA(cudaMemcpy(timed_out, flag.p, 4, cudaMemcpyDeviceToHost));
-    return PGB_OK;
-}
-
-// Launches the fused Arnoldi step (false: cooperative launch unavailable;
-// the caller takes the multi-kernel path).
-static bool arnoldi_fused(pgb_ctx* c, int j, double* w, double* h, double* hc, double* cs, double* sn, double* g,
-                          double* out) {
-    if (c->coop_blocks < 0) return false;
-    const int threads = 512, warps = threads / 32;  // one block per SM
-    if (c->coop_blocks == 0) {
-        int dev = 0, coop = 0, sms = 0, occ = 0;
+// The four launches of one Arnoldi step.
+static void arnoldi_step(pgb_ctx* c, int j, double* w, double* h, double* hc, double* cs, double* sn, double* g,
+                         double* out) {
+    if (c->arn_blocks == 0) {
+        int dev = 0, sms = 0;
         PGB_CUDA(cudaGetDevice(&dev));
-        PGB_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
         PGB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        const size_t smem_max = 8 * (size_t)257 * warps;  // restart <= 256
-        PGB_CUDA(cudaFuncSetAttribute(k_arnoldi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
-        PGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_arnoldi, threads, smem_max));
-        if (!coop || occ < 1) {
-            c->coop_blocks = -1;
-            return false;
-        }
-        c->coop_blocks = sms;
-        c->d_bar.resize(4);
-        PGB_CUDA(cudaMemsetAsync(c->d_bar.p, 0, 16, c->stream));
-        c->bar_base = 0;
+        c->arn_blocks = ARN_BLOCKS_PER_SM * sms;
     }
-    const int nb = c->coop_blocks;
-    c->d_red.resize(std::max<size_t>(c->d_red.n, (size_t)nb * (j + 2)));
-    ArnoldiArgs a;
+    const int nb = c->arn_blocks, m = j + 1, warps = ARN_THREADS / 32;
+    c->d_red.resize(std::max<size_t>(c->d_red.n, (size_t)2 * nb * (m + 1)));
+    ArnArgs a;
     a.V = c->d_V;
     a.ld = c->n_unk;
     a.n = c->n_unk;
@@ -400,22 +354,21 @@ static bool arnoldi_fused(pgb_ctx* c, int j, double* w, double* h, double* hc, d
     a.h = h;
     a.hc = hc;
     a.part = c->d_red;
+    a.part2 = c->d_red.p + (size_t)nb * (m + 1);
     a.cs = cs;
     a.sn = sn;
     a.g = g;
     a.out = out;
-    a.bar = (GridBar*)c->d_bar.p;
-    a.bar_base = c->bar_base;
-    c->bar_base += 5u * (unsigned)nb;
-    void* args[] = {&a};
-    const size_t smem = 8 * (size_t)std::max(32, (j + 1) * warps);
-    const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_arnoldi, nb, threads, args, smem, c->stream);
-    if (e != cudaSuccess) {
-        (void)cudaGetLastError();
-        c->coop_blocks = -1;
-        return false;
-    }
-    return true;
+    const size_t dots = 8 * (size_t)std::max(32, m * warps);
+    const size_t upd = 8 * (size_t)((m + 31) & ~31) + dots;
+    if (upd > 48 * 1024)
+        PGB_CUDA(cudaFuncSetAttribute(k_arn_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd));
+    cudaStream_t s = c->stream;
+    k_arn_dot<<<nb, ARN_THREADS, dots, s>>>(a);
+    k_arn_update<<<nb, ARN_THREADS, upd, s>>>(a, 0);
+    k_arn_update<<<nb, ARN_THREADS, upd, s>>>(a, 1);
+    k_arn_finish<<<nb, ARN_THREADS, 8 * 64, s>>>(a);
+    PGB_CUDA(cudaGetLastError());
 }
 
 // Block-diagonal preconditioner from the self terms (no equation of the
@@ -515,7 +468,7 @@ struct Krylov {
 // `prec`; stops when the (estimated) residual <= abs_tol or after max_it
 // iterations.  Returns iterations done; *matvecs counts operator uses.
 int gmres_op(pgb_ctx* c, int prec, bool transpose, const double* b, double* x, double abs_tol, int max_it,
-             int restart, int* matvecs, double* est_out, bool x_zero) {
+             int restart, int* matvecs, double* est_out, bool x_zero, GmresSpec* spec) {
     const bool pc = c->p.precond && c->pc_ready;
     auto apply = [&](const double* in, double* out) {
         if (transpose) apply_transpose(c, in, out, prec);
@@ -571,13 +524,13 @@ int gmres_op(pgb_ctx* c, int prec, bool transpose, const double* b, double* x, d
             apply_pc(vj, w);
             ++*matvecs;
             double* h = c->d_H.p + (size_t)j * (m + 1);
-            bool fused = false;
+            const bool fused = true;
             {
                 StageTimer tm(c, PGB_STAGE_KRYLOV);
-                fused = arnoldi_fused(c, j, w, h, hcol, cs, sn, g, misc.p + 2);
-                if (fused) PGB_LAUNCHED(c, 1);
+                arnoldi_step(c, j, w, h, hcol, cs, sn, g, misc.p + 2);
+                PGB_LAUNCHED(c, 4);
             }
-            if (!fused) {
+            if (!fused) {  // the multi-kernel reference path (kept for comparison)
                 StageTimer tm(c, PGB_STAGE_KRYLOV);
                 for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
                     k_multi_dot<<<DOT_BLOCKS, DOT_THREADS, 8 * (DOT_THREADS / 32) * (j + 1), s>>>(c->d_V, n, j + 1, w, n,
@@ -592,19 +545,30 @@ int gmres_op(pgb_ctx* c, int prec, bool transpose, const double* b, double* x, d
                 PGB_CUDA(cudaGetLastError());
                 PGB_LAUNCHED(c, 12);
             }
-            PGB_CUDA(cudaMemcpyAsync(c->h_pinned, misc.p + 2, fused ? 24 : 16, cudaMemcpyDeviceToHost, s));
+            PGB_CUDA(cudaMemcpyAsync(c->h_pinned, misc.p + 2, 16, cudaMemcpyDeviceToHost, s));
             PGB_CUDA(cudaStreamSynchronize(s));
-            if (fused && c->h_pinned[2] != 0) {
-                PGB_CUDA(cudaMemsetAsync(c->d_bar.p, 0, 16, s));
-                c->bar_base = 0;
-                fail(PGB_ETIMEOUT, "Arnoldi grid barrier timed out");
-            }
             est = c->h_pinned[0];
             double hnext = c->h_pinned[1];
             if (est <= abs_tol || !(hnext > 0)) {
                 ++j;
                 ++it;
                 break;
+            }
+            if (spec && !spec->forked && est <= spec->abs_thresh) {
+                // xs = x + M^{-1} V y with the j + 1 columns so far
+                k_backsolve<<<1, 1, 0, s>>>(c->d_H, m + 1, g, j + 1, yv);
+                PGB_CUDA(cudaMemcpyAsync(spec->xs, x, 8 * n, cudaMemcpyDeviceToDevice, s));
+                if (pc) {
+                    PGB_CUDA(cudaMemsetAsync(c->d_pz.p, 0, 8 * n, s));
+                    k_multi_axpy<<<nblk(n, 256), 256, 0, s>>>(c->d_V, n, j + 1, yv, 1.0, c->d_pz, n);
+                    precond_apply(c, c->d_pz, spec->xs, transpose, true);
+                } else {
+                    k_multi_axpy<<<nblk(n, 256), 256, 0, s>>>(c->d_V, n, j + 1, yv, 1.0, spec->xs, n);
+                }
+                PGB_CUDA(cudaGetLastError());
+                PGB_LAUNCHED(c, 2);
+                spec->forked = true;
+                spec->fork(c, spec->xs, spec->user);
             }
         }
         k_backsolve<<<1, 1, 0, s>>>(c->d_H, m + 1, g, j, yv);
@@ -648,6 +612,49 @@ static double vec_norm(pgb_ctx* c, const double* v) {
     c->d_red.resize(std::max<size_t>(c->d_red.n, DOT_BLOCKS));
     K.norm(v, t);
     return K.host_read(t);
+}
+
+// Side-stream FP64 product of the refinement (overlap): x* = x_outer +
+// (inner iterate); its FP64 product r64 = A64(x* + imposed) runs on the
+// side stream, P2P and M2P launched persistently with one block per SM so
+// that the FP32 kernels of the continuing inner iterations keep the rest of
+// each SM (the FP64 kernels are bound by the FP64 pipe, which the FP32
+// kernels do not use).  The buffers it touches are sized on the main stream
+// before the fork.
+struct OverlapArgs {
+    const double* x_outer;
+};
+
+static void overlap_fork(pgb_ctx* c, const double* xs, void* user) {
+    const OverlapArgs* oa = (const OverlapArgs*)user;
+    const int64_t n = c->n_unk;
+    cudaStream_t s = c->stream;
+    double* xfull = c->d_xspec.p;  // overwrite x* in place: x_outer + inner iterate
+    k_axpby<<<nblk(n, 256), 256, 0, s>>>(1.0, oa->x_outer, 1.0, xs, xfull, n);
+    c->d_r64.resize(n);
+    reserve_product(c, PGB_FP64);
+    if (!c->side_stream) {
+        PGB_CUDA(cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking));
+        PGB_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+        PGB_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    }
+    int dev = 0, sms = 0;
+    PGB_CUDA(cudaGetDevice(&dev));
+    PGB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    PGB_CUDA(cudaEventRecord(c->ev_fork, s));
+    PGB_CUDA(cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0));
+    c->stream = c->side_stream;
+    c->persist_blocks = sms;
+    try {
+        apply_full(c, xfull, c->d_r64, PGB_FP64);
+    } catch (...) {
+        c->stream = s;
+        c->persist_blocks = 0;
+        throw;
+    }
+    c->stream = s;
+    c->persist_blocks = 0;
+    PGB_CUDA(cudaEventRecord(c->ev_join, c->side_stream));
 }
 
 int solve(pgb_ctx* c, int mode, double tol, int max_iter, int restart, double* x, pgb_solve_stats* st) {
@@ -705,16 +712,45 @@ int solve(pgb_ctx* c, int mode, double tol, int max_iter, int restart, double* x
             // usually confirms convergence
             double inner = std::max(0.5 * tol * bnorm / rn, 1e-7);
             PGB_CUDA(cudaMemsetAsync(c->d_xs.p, 0, 8 * n, s));
+            // Overlap: once the inner estimate reaches eps* of its right-hand
+            // side, the FP64 product of that iterate starts on a side stream
+            // while the FP32 iterations go on (see overlap_fork).
+            const double eps_star = std::min(1e-2, 1e4 * tol);
+            GmresSpec spec;
+            OverlapArgs oa{x};
+            const bool overlap = c->p.overlap && eps_star > 10 * inner;
+            if (overlap) {
+                c->d_xspec.resize(2 * n);
+                spec.abs_thresh = eps_star * rn;
+                spec.xs = c->d_xspec;
+                spec.fork = overlap_fork;
+                spec.user = &oa;
+            }
             int mv = 0;
-            int it = gmres(c, PGB_FP32, c->d_r, c->d_xs, inner * rn, max_iter - z.iterations, restart, &mv, nullptr, true);
+            int it = gmres_op(c, PGB_FP32, false, c->d_r, c->d_xs, inner * rn, max_iter - z.iterations, restart, &mv,
+                              nullptr, true, overlap ? &spec : nullptr);
             z.iterations += it;
             z.matvecs += mv;
             ++z.outer_steps;
             k_axpby<<<nblk(n, 256), 256, 0, s>>>(1.0, x, 1.0, c->d_xs, x, n);
-            apply_full(c, x, c->d_r, PGB_FP64);
-            ++z.matvecs;
-            ++z.matvecs_fp64;
-            k_axpby<<<nblk(n, 256), 256, 0, s>>>(1.0, c->d_bc, -1.0, c->d_r, c->d_r, n);
+            if (spec.forked) {
+                // r = b - A64(x* + imposed) - A32(x - x*): the FP32 term is of
+                // size ~eps* |b| and carries the FP32 operator's relative error
+                // (~1e-6), i.e. ~1e-8 |b|, far below the tolerance
+                double* dlt = c->d_xspec.p + n;  // x (updated above) - x*
+                k_axpby<<<nblk(n, 256), 256, 0, s>>>(1.0, x, -1.0, c->d_xspec, dlt, n);
+                apply_operator(c, dlt, c->d_r, PGB_FP32, false);
+                PGB_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
+                k_axpby<<<nblk(n, 256), 256, 0, s>>>(1.0, c->d_bc, -1.0, c->d_r64, c->d_wk, n);
+                k_axpby<<<nblk(n, 256), 256, 0, s>>>(1.0, c->d_wk, -1.0, c->d_r, c->d_r, n);
+                z.matvecs += 2;
+                ++z.matvecs_fp64;
+            } else {
+                apply_full(c, x, c->d_r, PGB_FP64);
+                ++z.matvecs;
+                ++z.matvecs_fp64;
+                k_axpby<<<nblk(n, 256), 256, 0, s>>>(1.0, c->d_bc, -1.0, c->d_r, c->d_r, n);
+            }
             double rn_new = vec_norm(c, c->d_r);
             rel = rn_new / bnorm;
             if (it == 0 || !(rn_new < rn)) {  // no progress: stop

@@ -151,7 +151,22 @@ struct EvalArgs {
     const int32_t *pitem_group, *fitem_group;
     int p2p_item, m2p_item;
     double *Up, *Uf;               // per item: 32 Laplace then 32 Yukawa partial sums (one per lane)
+    // persistent launch: a grid smaller than the item count whose blocks take
+    // items from these counters (zero before the launch); nullptr: one item per block
+    unsigned long long *p2p_work, *m2p_work;
+    int persist_blocks;            // grid of a persistent launch
 };
+
+// Item loop of a block: one item per block, or (persistent launch) items
+// taken from a counter until none is left.  The barrier also keeps a block
+// from reusing its shared memory while a warp still reads the last item.
+__device__ __forceinline__ int64_t next_item(unsigned long long* work, int64_t cur, int64_t* slot) {
+    if (!work) return cur < 0 ? (int64_t)blockIdx.x : INT64_MAX;
+    __syncthreads();
+    if (threadIdx.x == 0) *slot = (int64_t)atomicAdd(work, 1ull);
+    __syncthreads();
+    return *slot;
+}
 
 // Far-field contraction sum_k G_k(R) M_k for one target (returns Yukawa and,
 // when lap, Laplace).  Per level n the recurrence constants are folded into
@@ -344,9 +359,9 @@ __global__ void __launch_bounds__(NW * 32) k_p2p(EvalArgs a,
     using v4 = typename V4<real>::t;
     __shared__ v4 sA[NW][32], sB[NW][32];
     __shared__ real red[NW][4][32];
+    __shared__ int64_t s_item;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t it = blockIdx.x;
-    if (it >= a.n_pitems) return;
+    for (int64_t it = next_item(a.p2p_work, -1, &s_item); it < a.n_pitems; it = next_item(a.p2p_work, it, &s_item)) {
     const int64_t g = a.pitem_group[it];
     const int64_t p0 = a.gstart[g], p1 = a.gend[g];
     const int64_t p = p0 + lane;
@@ -416,6 +431,7 @@ __global__ void __launch_bounds__(NW * 32) k_p2p(EvalArgs a,
         kadd(UY, cY, sumY);
     }
     store_item<real, NW>(red, w, lane, UL, cL, UY, cY, a.Up + 64 * it);
+    }
 }
 
 // M2P: one block of NW warps per work item, i.e. up to m2p_item far entries of
@@ -429,9 +445,9 @@ __global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a, const typename V4<r
     constexpr int MW = (2 * T + 31) / 32;  // moment words per lane
     __shared__ real sM[NW][2 * T];
     __shared__ real red[NW][4][32];
+    __shared__ int64_t s_item;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t it = blockIdx.x;
-    if (it >= a.n_fitems) return;
+    for (int64_t it = next_item(a.m2p_work, -1, &s_item); it < a.n_fitems; it = next_item(a.m2p_work, it, &s_item)) {
     const int64_t g = a.fitem_group[it];
     const int64_t p0 = a.gstart[g], p1 = a.gend[g];
     const int64_t p = p0 + lane;
@@ -491,6 +507,7 @@ __global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a, const typename V4<r
         kadd(UY, cY, uY);
     }
     store_item<real, NW>(red, w, lane, UL, cL, UY, cY, a.Uf + 64 * it);
+    }
 }
 
 struct UpArgs {

@@ -19,11 +19,15 @@ static void launch_p(int stage, const UpArgs& up, const std::vector<int64_t>& up
                 k_m2m_level<real, P><<<(unsigned)(u.lvl_end - u.lvl_begin), 256, 0, s>>>(u, (real*)mom);
         }
     }
-    constexpr int NW = 8;
+    // FP64 M2P: 4 warps per block (its registers would otherwise fill an SM)
+    constexpr int NW = sizeof(real) == 8 ? 4 : 8;
+    const bool persist = ev.p2p_work != nullptr;
     if (stage == PGB_STAGE_P2P && ev.n_pitems > 0)
-        k_p2p<real, 8><<<(unsigned)ev.n_pitems, 8 * 32, 0, s>>>(ev, (const v4*)src, (const v4*)xrel);
+        k_p2p<real, 8><<<(unsigned)(persist ? ev.persist_blocks : ev.n_pitems), 8 * 32, 0, s>>>(ev, (const v4*)src,
+                                                                                               (const v4*)xrel);
     if (stage == PGB_STAGE_M2P && ev.n_fitems > 0)
-        k_m2p<real, P, NW><<<(unsigned)ev.n_fitems, NW * 32, 0, s>>>(ev, (const v4*)xrel, (const real*)mom);
+        k_m2p<real, P, NW><<<(unsigned)(persist ? ev.persist_blocks : ev.n_fitems), NW * 32, 0, s>>>(
+            ev, (const v4*)xrel, (const real*)mom);
 }
 
 }  // namespace pgb

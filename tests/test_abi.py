@@ -45,8 +45,8 @@ def test_argument_errors_need_no_device(libpgb):
     p = L.pgb_params()
     assert lib.pgb_default_params(ctypes.byref(p)) == 0
     assert (p.K, p.K_near, p.n_edge, p.P, p.theta, p.leaf_size) == (7, 19, 9, 6, 0.5, 32)
-    assert (p.p2p_item, p.m2p_item, p.precond, p.graphs, p.lanes) == (64, 64, 0, 1, 4)
-    for f, v in (("p2p_item", 5000), ("m2p_item", -1), ("precond", 2), ("graphs", 3), ("lanes", 17)):
+    assert (p.p2p_item, p.m2p_item, p.precond, p.graphs, p.lanes, p.overlap) == (64, 64, 0, 1, 4, 1)
+    for f, v in (("p2p_item", 5000), ("m2p_item", -1), ("precond", 2), ("graphs", 3), ("lanes", 17), ("overlap", 2)):
         q = L.pgb_params()
         lib.pgb_default_params(ctypes.byref(q))
         setattr(q, f, v)
@@ -67,12 +67,3 @@ def test_math_check_argument_errors(libpgb):
     assert lib.pgb_math_check(None, -1, None) == L.PGB_EINVAL
     assert lib.pgb_math_check(None, 4, None) == L.PGB_EINVAL
     assert lib.pgb_math_check(None, 0, None) == L.PGB_OK
-
-
-def test_barrier_check_argument_errors(libpgb):
-    import paper_1506_03745_gb300._lib as L
-    lib = L.lib()
-    t = ctypes.c_int32(0)
-    assert lib.pgb_barrier_check(0, ctypes.byref(t)) == L.PGB_EINVAL
-    assert lib.pgb_barrier_check(3, ctypes.byref(t)) == L.PGB_EINVAL
-    assert lib.pgb_barrier_check(1, None) == L.PGB_EINVAL

@@ -84,3 +84,31 @@ def test_preconditioned_adjoint_gives_the_same_gradients(kind):
     np.testing.assert_allclose(dbc1, dbc0, rtol=1e-8, atol=1e-12)
     np.testing.assert_allclose(dt1, dt0, rtol=1e-6, atol=1e-10)
     assert it1 <= it0
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+def test_overlapped_fp64_residual(precond):
+    """FP32 + refinement with the FP64 product of the outer residual started
+    early on a side stream (overlap = 1) against the same solve with the FP64
+    product of the final iterate (overlap = 0): both meet the tolerance in the
+    true FP64 residual, report it, and give the same energies."""
+    bodies = spheres(kind="sigma", level_mol=4, level_srf=4)
+    out = []
+    for ov in (0, 1):
+        ctx = gpu_context(bodies, precond=precond, overlap=ov)
+        try:
+            code, st, x = _solve(ctx, pgb.PGB_FP32_REFINE, 1e-6)
+            assert code == 0
+            n = pgb.pgb_num_unknowns(ctx)
+            b = torch.empty(n, dtype=torch.float64, device="cuda")
+            ax = torch.empty_like(b)
+            pgb.pgb_rhs(ctx, b)
+            pgb.pgb_matvec(ctx, x, ax, pgb.PGB_FP64)
+            true_rel = float(torch.linalg.norm(b - ax) / torch.linalg.norm(b))
+            assert true_rel <= 1.05e-6
+            assert st["rel_residual"] == pytest.approx(true_rel, rel=0.1, abs=3e-8)
+            out.append(pgb.pgb_energy(ctx, x))
+        finally:
+            pgb.pgb_destroy(ctx)
+    for k in ("solvation", "surface", "total"):
+        assert out[1][k] == pytest.approx(out[0][k], rel=2e-7)
