@@ -330,18 +330,18 @@ int pgb_destroy(pgb_ctx* c) {
         if (gr.exec) cudaGraphExecDestroy(gr.exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
-    if (c->side_stream) {
-        cudaStreamSynchronize(c->side_stream);
-        cudaStreamDestroy(c->side_stream);
-        cudaEventDestroy(c->ev_fork);
-        cudaEventDestroy(c->ev_join);
-    }
+    if (c->side_stream) cudaStreamSynchronize(c->side_stream);
+    if (c->hp_stream) cudaStreamSynchronize(c->hp_stream);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     cudaStream_t own = c->owns_stream ? c->stream : nullptr;
-    delete c;  // device buffers are freed in the order of their stream
-    if (own) {
-        cudaStreamSynchronize(own);
-        cudaStreamDestroy(own);
-    }
+    cudaStream_t side = c->side_stream, hp = c->hp_stream;
+    delete c;  // device buffers are freed in the order of the stream they were allocated on
+    for (cudaStream_t x : {side, hp, own})
+        if (x) {
+            cudaStreamSynchronize(x);
+            cudaStreamDestroy(x);
+        }
     return PGB_OK;
 }
 

@@ -26,7 +26,7 @@ static inline int nblk(int64_t n, int t) { return (int)std::max<int64_t>(1, (n +
 template <typename real>
 __global__ void k_src_prep(Geo g, BodyDev bd, const double* __restrict__ x, int mode,
                            const typename V4<real>::t* __restrict__ yrel, typename V4<real>::t* __restrict__ src,
-                           double* __restrict__ dens, double eps_out) {
+                           real* __restrict__ dens, double eps_out) {
     const bool known = mode == 1;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= g.n_pan) return;
@@ -54,19 +54,23 @@ __global__ void k_src_prep(Geo g, BodyDev bd, const double* __restrict__ x, int 
         if (kind == PGB_SET_POTENTIAL) phi = bd.bc[b];
         else if (kind == PGB_SET_CHARGE) psiY = -bd.bc[b] / eps_out;
     }
-    dens[3 * i] = psiL;
-    dens[3 * i + 1] = psiY;
-    dens[3 * i + 2] = phi;
-    const double nx = g.n[3 * i], ny = g.n[3 * i + 1], nz = g.n[3 * i + 2];
+    // the FP32 product forms its source terms in FP32 (they are stored in
+    // FP32 anyway); the FP64 product in FP64
+    const real rL = (real)psiL, rY = (real)psiY, rp = (real)phi;
+    dens[3 * i] = rL;
+    dens[3 * i + 1] = rY;
+    dens[3 * i + 2] = rp;
+    const real nx = (real)g.n[3 * i], ny = (real)g.n[3 * i + 1], nz = (real)g.n[3 * i + 2];
     for (int m = 0; m < g.K; ++m) {
         const int64_t p = i * g.K + m;
-        const double w = g.w[p];
+        const real w = (real)g.w[p];
         typename V4<real>::t A = yrel[p], B;
-        A.w = (real)(w * psiL);
-        B.x = (real)(w * phi * nx);
-        B.y = (real)(w * phi * ny);
-        B.z = (real)(w * phi * nz);
-        B.w = (real)(w * psiY);
+        const real wp = w * rp;
+        A.w = w * rL;
+        B.x = wp * nx;
+        B.y = wp * ny;
+        B.z = wp * nz;
+        B.w = w * rY;
         src[2 * p] = A;
         src[2 * p + 1] = B;
     }
@@ -85,11 +89,15 @@ struct Parts {
     const double *Up, *Uf;
 };
 
-__global__ void k_assemble(Geo g, BodyDev bd, Parts u, const double* __restrict__ dens,
+// real: the arithmetic of the near-field corrections (FP32 product: FP32
+// copies of the FP64-computed corrections; FP64 product: FP64).
+template <typename real>
+__global__ void k_assemble(Geo g, BodyDev bd, Parts u, const real* __restrict__ dens,
                            const int64_t* __restrict__ coff, const int32_t* __restrict__ cj,
-                           const dbl4* __restrict__ cval, const int64_t* __restrict__ xoff,
-                           const int32_t* __restrict__ xj, const dbl4* __restrict__ xval, int mode,
-                           double* __restrict__ y) {
+                           const typename V4<real>::t* __restrict__ cval, const int64_t* __restrict__ xoff,
+                           const int32_t* __restrict__ xj, const typename V4<real>::t* __restrict__ xval, int mode,
+                           const double* __restrict__ x, double* __restrict__ y) {
+    using v4 = typename V4<real>::t;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= g.n_pan) return;
     const double inv4pi = 1.0 / PGB_FOUR_PI;
@@ -105,25 +113,37 @@ __global__ void k_assemble(Geo g, BodyDev bd, Parts u, const double* __restrict_
         sY += u.Uf[64 * it + 32 + lane];
     }
     double UL = sL * inv4pi, UY = sY * inv4pi;
+    // corrections: FP32 products with compensated sums in the FP32 product,
+    // plain FP64 in the FP64 one
+    real cL = 0, eL = 0, cY = 0, eY = 0;
     for (int64_t e = coff[i]; e < coff[i + 1]; ++e) {
         const int64_t j = cj[e];
-        const dbl4 d = cval[e];
-        const double psiL = dens[3 * j], psiY = dens[3 * j + 1], phi = dens[3 * j + 2];
-        UL += d.x * psiL - d.y * phi;
-        UY += d.z * psiY - d.w * phi;
+        const v4 d = cval[e];
+        const real psiL = dens[3 * j], psiY = dens[3 * j + 1], phi = dens[3 * j + 2];
+        if (sizeof(real) == 4) {
+            kadd(cL, eL, d.x * psiL - d.y * phi);
+            kadd(cY, eY, d.z * psiY - d.w * phi);
+        } else {
+            cL += d.x * psiL - d.y * phi;
+            cY += d.z * psiY - d.w * phi;
+        }
     }
     for (int64_t e = xoff[i]; e < xoff[i + 1]; ++e) {  // cross-body entries (Yukawa only)
         const int64_t j = xj[e];
-        const dbl4 d = xval[e];
-        UY += d.z * dens[3 * j + 1] - d.w * dens[3 * j + 2];
+        const v4 d = xval[e];
+        if (sizeof(real) == 4) kadd(cY, eY, d.z * dens[3 * j + 1] - d.w * dens[3 * j + 2]);
+        else cY += d.z * dens[3 * j + 1] - d.w * dens[3 * j + 2];
     }
+    UL += (double)cL + (double)eL;
+    UY += (double)cY + (double)eY;
     const int b = g.pbody[i];
     const int64_t loc = g.perm[i] - bd.pan_off[b];
     const int64_t N = bd.pan_off[b + 1] - bd.pan_off[b];
     const int64_t o = bd.unk_off[b];
     const int kind = bd.kind[b];
     if (mode == 0 || mode == 2) {
-        const double phi = dens[3 * i + 2];
+        // the jump terms from the unknowns themselves, in FP64
+        const double phi = kind == PGB_SET_POTENTIAL ? 0.0 : x[o + loc];
         if (kind == PGB_DIELECTRIC) {
             y[o + loc] = 0.5 * phi - UL;
             y[o + N + loc] = 0.5 * phi + UY;
@@ -303,10 +323,10 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
         StageTimer tm(c, PGB_STAGE_SOURCES + (f32 ? 0 : PGB_STAGE_FP64));
         if (f32)
             k_src_prep<float><<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, x, mode, c->d_y32, c->d_src32,
-                                                                  dens, c->eps_out);
+                                                                  (float*)dens.p, c->eps_out);
         else
             k_src_prep<double><<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, x, mode, c->d_y64, c->d_src64,
-                                                                   dens, c->eps_out);
+                                                                   dens.p, c->eps_out);
         PGB_CUDA(cudaGetLastError());
         PGB_LAUNCHED(c, 1);
     }
@@ -323,9 +343,14 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
     {
         StageTimer tm(c, PGB_STAGE_ASSEMBLE + (f32 ? 0 : PGB_STAGE_FP64));
         Parts u{c->d_pan_group, c->d_group_start, c->d_pitem_off, c->d_fitem_off, Up, Uf};
-        k_assemble<<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, u, dens, c->d_corr_off, c->d_corr_j,
-                                                       c->d_corr_val, c->d_xcorr_off, c->d_xcorr_j, c->d_xcorr_val,
-                                                       mode, y);
+        if (f32)
+            k_assemble<float><<<nblk(c->n_pan, 128), 128, 0, s>>>(
+                g, bd, u, (const float*)dens.p, c->d_corr_off, c->d_corr_j, c->d_corr_val32, c->d_xcorr_off,
+                c->d_xcorr_j, c->d_xcorr_val32, mode, x, y);
+        else
+            k_assemble<double><<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, u, dens.p, c->d_corr_off, c->d_corr_j,
+                                                                   c->d_corr_val, c->d_xcorr_off, c->d_xcorr_j,
+                                                                   c->d_xcorr_val, mode, x, y);
         PGB_CUDA(cudaGetLastError());
         PGB_LAUNCHED(c, 1);
     }

@@ -208,6 +208,7 @@ struct pgb_ctx {
     pgb::DBuf<int64_t> d_corr_off, d_xcorr_off;
     pgb::DBuf<int32_t> d_corr_j, d_xcorr_j;
     pgb::DBuf<pgb::dbl4> d_corr_val, d_xcorr_val;  // dVL, dKL, dVY, dKY
+    pgb::DBuf<float4> d_corr_val32, d_xcorr_val32;  // their FP32 copies (the FP32 product)
     pgb::DBuf<double> d_yfine;             // 19-point nodes per panel (3 each), for the corrections
     pgb::DBuf<int32_t> d_corr_tmp;         // candidates kept by the counting pass (PGB_CORR_CAP per panel)
     pgb::DBuf<double> d_xbatch;            // solution buffer of pgb_solve_batch
@@ -248,7 +249,8 @@ struct pgb_ctx {
     int arn_blocks = 0;                  // grid of the Arnoldi-step kernels (0: not yet set)
     int persist_blocks = 0;              // > 0: products launch P2P/M2P persistently with this grid
     pgb::DBuf<unsigned long long> d_work;  // their item counters
-    cudaStream_t side_stream = nullptr;  // FP64 residual overlapped with FP32 iterations
+    cudaStream_t side_stream = nullptr;  // FP64 residual overlapped with FP32 iterations (lowest priority)
+    cudaStream_t hp_stream = nullptr;    // the refinement's FP32 iterations (highest priority)
     pgb::DBuf<double> d_xspec, d_r64;    // its iterate (and x - x*), its product
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double* h_pinned = nullptr;

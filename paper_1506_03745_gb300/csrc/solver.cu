@@ -193,7 +193,7 @@ __global__ void k_init_g(double* g, int m1, const double* beta) {
 //   k_arn_update: c_i = sum_b part[i][b]; w -= sum_i c_i V_i; (pass 1) the
 //                 partials of the second pass, (pass 2) of |w|^2
 //   k_arn_finish: |w|, v_{j+1} = w / |w|, Givens step (block 0)
-#define ARN_BLOCKS_PER_SM 2
+#define ARN_BLOCKS_PER_SM 1
 #define ARN_THREADS 256
 
 struct ArnArgs {
@@ -209,6 +209,38 @@ struct ArnArgs {
     double* out;    // out[0] = |g_{j+1}|, out[1] = h_{j+1,j}
 };
 
+// Sums of eight values over the 32 lanes of a warp by a butterfly
+// reduce-scatter: each exchange halves the values a lane keeps, so a lane
+// does 9 additions instead of 40 (FP64 additions are scarce on this part).
+// Returns the full sum of value k = 4 b4 + 2 b3 + b2 (b_i: bit i of the lane)
+// in every lane; *k_out receives k.
+__device__ __forceinline__ double warp_sum8(const double (&t)[8], int* k_out) {
+    const int lane = threadIdx.x & 31;
+    double u[4], v[2], x;
+    const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double give = h4 ? t[k] : t[k + 4];
+        const double keep = h4 ? t[k + 4] : t[k];
+        u[k] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const double give = h3 ? u[k] : u[k + 2];
+        const double keep = h3 ? u[k + 2] : u[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
+    }
+    {
+        const double give = h2 ? v[0] : v[1];
+        const double keep = h2 ? v[1] : v[0];
+        x = keep + __shfl_xor_sync(0xffffffffu, give, 4);
+    }
+    x += __shfl_xor_sync(0xffffffffu, x, 2);
+    x += __shfl_xor_sync(0xffffffffu, x, 1);
+    *k_out = (h4 ? 4 : 0) + (h3 ? 2 : 0) + (h2 ? 1 : 0);
+    return x;
+}
+
 // Block partials of V_i . w (i < m) over this block's rows, eight vectors at a time.
 __device__ __forceinline__ void arn_block_dots(const ArnArgs& a, int m, double* part, double* shd) {
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -223,12 +255,9 @@ __device__ __forceinline__ void arn_block_dots(const ArnArgs& a, int m, double* 
             for (int u = 0; u < 8; ++u)
                 if (i0 + u < m) t[u] += a.V[(i0 + u) * a.ld + r] * wr;
         }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) t[u] = warp_sum(t[u]);
-        if (lane == 0)
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (i0 + u < m) shd[(i0 + u) * nw + wi] = t[u];
+        int k;
+        const double sum = warp_sum8(t, &k);
+        if ((lane & 3) == 0 && i0 + k < m) shd[(i0 + k) * nw + wi] = sum;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -614,6 +643,39 @@ static double vec_norm(pgb_ctx* c, const double* v) {
     return K.host_read(t);
 }
 
+// For the duration of a refinement with overlap: the context's work goes to
+// its highest-priority stream (ordered after the caller's stream at entry,
+// and the caller's stream after it at exit), and allocations follow.
+struct StreamSwap {
+    pgb_ctx* c;
+    cudaStream_t user = nullptr;
+    AllocScope* scope = nullptr;
+    StreamSwap(pgb_ctx* ctx, bool on) : c(ctx) {
+        if (!on) return;
+        if (!c->hp_stream) {
+            int least = 0, greatest = 0;
+            PGB_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+            PGB_CUDA(cudaStreamCreateWithPriority(&c->hp_stream, cudaStreamNonBlocking, greatest));
+            PGB_CUDA(cudaStreamCreateWithPriority(&c->side_stream, cudaStreamNonBlocking, least));
+            PGB_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+            PGB_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+        }
+        user = c->stream;
+        PGB_CUDA(cudaEventRecord(c->ev_fork, user));
+        PGB_CUDA(cudaStreamWaitEvent(c->hp_stream, c->ev_fork, 0));
+        c->stream = c->hp_stream;
+        scope = new AllocScope(c->hp_stream);
+    }
+    ~StreamSwap() {
+        if (!scope) return;
+        delete scope;
+        c->stream = user;
+        // the caller's stream continues after everything of the solve
+        cudaEventRecord(c->ev_join, c->hp_stream);
+        cudaStreamWaitEvent(user, c->ev_join, 0);
+    }
+};
+
 // Side-stream FP64 product of the refinement (overlap): x* = x_outer +
 // (inner iterate); its FP64 product r64 = A64(x* + imposed) runs on the
 // side stream, P2P and M2P launched persistently with one block per SM so
@@ -633,11 +695,6 @@ static void overlap_fork(pgb_ctx* c, const double* xs, void* user) {
     k_axpby<<<nblk(n, 256), 256, 0, s>>>(1.0, oa->x_outer, 1.0, xs, xfull, n);
     c->d_r64.resize(n);
     reserve_product(c, PGB_FP64);
-    if (!c->side_stream) {
-        PGB_CUDA(cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking));
-        PGB_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
-        PGB_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
-    }
     int dev = 0, sms = 0;
     PGB_CUDA(cudaGetDevice(&dev));
     PGB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -702,6 +759,11 @@ int solve(pgb_ctx* c, int mode, double tol, int max_iter, int restart, double* x
         // Inner FP32 solves take the right-hand side from the FP32 operator;
         // the outer residual is FP64 throughout: r = b_Coulomb - A64(x + imposed
         // densities), one FP64 product per outer step.
+        // With overlap the iterations run on a highest-priority stream and the
+        // FP64 product on a lowest-priority one, so that the block scheduler
+        // serves the FP32 chain first and the FP64 work fills the rest.
+        StreamSwap swap(c, c->p.overlap != 0);
+        s = c->stream;
         c->d_bc.resize(n);
         coulomb_rows(c, c->d_bc);
         PGB_CUDA(cudaMemcpyAsync(c->d_r.p, c->d_b.p, 8 * n, cudaMemcpyDeviceToDevice, s));

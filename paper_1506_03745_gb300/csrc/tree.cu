@@ -1415,8 +1415,16 @@ BodyDev body_dev(const pgb_ctx* c) {
     return b;
 }
 
+__global__ void k_dbl4_to_f4(const dbl4* a, float4* b, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) {
+        const dbl4 v = a[i];
+        b[i] = make_float4((float)v.x, (float)v.y, (float)v.z, (float)v.w);
+    }
+}
+
 static void build_corr_part(pgb_ctx* c, bool cross, DBuf<int64_t>& off, DBuf<int32_t>& cj, DBuf<dbl4>& val,
-                            int64_t& count) {
+                            DBuf<float4>& val32, int64_t& count) {
     cudaStream_t s = c->stream;
     int64_t n = c->n_pan;
     CorrArgs a;
@@ -1455,6 +1463,8 @@ static void build_corr_part(pgb_ctx* c, bool cross, DBuf<int64_t>& off, DBuf<int
             k_corr_self<<<nblk(n, 128), 128, 0, s>>>(n, off, cj, c->d_v, c->d_c, c->d_pbody, body_dev(c), r,
                                                      c->kappa, val);
     }
+    val32.resize(std::max<int64_t>(tot, 1));
+    if (tot) k_dbl4_to_f4<<<nblk(tot, 256), 256, 0, s>>>(val, val32, tot);
     PGB_CUDA(cudaGetLastError());
     PGB_CUDA(cudaStreamSynchronize(s));
     PGB_LAUNCHED(c, tot ? 5 : 2);
@@ -1462,10 +1472,10 @@ static void build_corr_part(pgb_ctx* c, bool cross, DBuf<int64_t>& off, DBuf<int
 
 void build_corrections(pgb_ctx* c) {
     if (!c->intra_valid) {
-        build_corr_part(c, false, c->d_corr_off, c->d_corr_j, c->d_corr_val, c->n_corr);
+        build_corr_part(c, false, c->d_corr_off, c->d_corr_j, c->d_corr_val, c->d_corr_val32, c->n_corr);
         c->intra_valid = true;
     }
-    build_corr_part(c, true, c->d_xcorr_off, c->d_xcorr_j, c->d_xcorr_val, c->n_xcorr);
+    build_corr_part(c, true, c->d_xcorr_off, c->d_xcorr_j, c->d_xcorr_val, c->d_xcorr_val32, c->n_xcorr);
 }
 
 Geo geo(const pgb_ctx* c) {
