@@ -41,11 +41,12 @@ METRIC = "treecode matvecs/sec and GMRES solve ms at 1e-5 energy err, FP32+refin
 UNIT = "matvecs/s"
 WORKLOAD = "two spheres r=4 A, 2 x 20480 panels, sigma=0.05 C/m^2, R=12 A"
 PARAMS = dict(K=7, K_near=19, n_edge=9, P=6, theta=0.5, leaf_size=32, group_size=32, p2p_item=64, m2p_item=64,
-              precond=0, graphs=1, lanes=4, overlap=1)
+              precond=0, graphs=1, lanes=4, overlap=0)
 TOL = 1e-6
 RESTART = 100
 MAX_ITER = 2000
 FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)"
+FP64_PEAK = 152 * 2 * 2 * 2.07e9 / 1e12  # TFLOP/s: 2 FP64 FMA lanes per SM per clock (measured pipe rate)
 
 
 def workload_bodies(level=5):
@@ -286,6 +287,7 @@ def run_gpu(args):
     step(pgb.PGB_FP32_REFINE)
     e_err = {k: abs(e32[k] - e64[k]) / max(abs(e64[k]), 1e-300) for k in ("solvation", "surface", "total")}
     pc = precond_solve(pgb, bodies, dev, stream, flush, e64) if not PARAMS.get("precond") else None
+    ov = variant_solve(pgb, bodies, dev, stream, flush, e64, overlap=1) if not PARAMS.get("overlap") else None
 
     info = pgb.pgb_tree_stats(ctx)
     peak_tflops = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -298,6 +300,16 @@ def run_gpu(args):
                            achieved=fl / (ms / calls / 1e3) / 1e12 if calls else None)
     dom = max(kern.values(), key=lambda k: k["total_ms"])
     traffic = recorded_traffic(dom["kernel"].split(" ")[0])
+    # the FP64 product of the refinement residual: same algorithmic counts,
+    # against the FP64 peak (152 SMs x 2 FP64 FMA lanes x 2 flop x 2.07 GHz);
+    # with overlap its kernels share the SMs with the FP32 iterations, so
+    # their durations include that sharing
+    for name, stage, fl in (("k_p2p<double> (P2P, FP64 residual)", "p2p_fp64", p2p_kernel_flops(info)),
+                            ("k_m2p<double,6> (M2P, FP64 residual)", "m2p_fp64", m2p_kernel_flops(info, PARAMS["P"]))):
+        ms, calls = timing[stage]
+        ach = fl / (ms / calls / 1e3) / 1e12 if calls else None
+        kern[stage] = dict(kernel=name, total_ms=ms, calls=calls, flops=fl, avg_ms=ms / calls if calls else None,
+                           achieved=ach, peak=FP64_PEAK, frac=(ach / FP64_PEAK) if ach else None)
 
     # ---- end to end through the public API with host inputs
     e2e_ms = []
@@ -348,7 +360,8 @@ def run_gpu(args):
                   "matvecs": st0["matvecs"], "matvecs_fp64": st0["matvecs_fp64"],
                   "fp64_iterations": st64["iterations"], "rel_residual": st0["rel_residual"],
                   "energy_rel_err_vs_fp64": e_err, "energies_kcal_mol": e32,
-                  "block_diagonal_precond": pc},
+                  "block_diagonal_precond": pc,
+                  "overlapped_fp64_residual": ov},
         "stage_ms_per_step": {k: v[0] / args.steps for k, v in timing.items() if k != "kernel_launches"},
         "gpu_launches": timing["kernel_launches"],
         "roofline": {"kernel": dom["kernel"], "bound": "alu", "achieved": dom["achieved"],
@@ -357,6 +370,9 @@ def run_gpu(args):
                      "traffic": traffic, "flops_per_launch": dom["flops"], "launches": dom["calls"],
                      "avg_launch_ms": dom["avg_ms"],
                      "peak_source": FP32_PEAK_NOTE + " (derived, not in MEASURED_PEAKS.json)",
+                     "note": "dominant kernel of the FP32 treecode product (30 of the 31 products of a step); "
+                             "the FP64 residual kernels, longer per launch, are in other_kernels against the "
+                             "FP64 peak",
                      "other_kernels": {k: {kk: vv for kk, vv in v.items() if kk != "kernel"} | {"kernel": v["kernel"]}
                                        for k, v in kern.items() if v is not dom}},
         "tree": info,
@@ -590,12 +606,19 @@ def run_brick(args):
 
 
 def precond_solve(pgb, bodies, dev, stream, flush, e64, steps=3):
-    """The same step with the block-diagonal right preconditioner (precond=1):
-    median device ms over `steps` steps after one warm-up, its iterations and
-    the energy difference to the unpreconditioned FP64 solve."""
+    """The same step with the block-diagonal right preconditioner (precond=1)."""
+    return variant_solve(pgb, bodies, dev, stream, flush, e64, steps, precond=1)
+
+
+def variant_solve(pgb, bodies, dev, stream, flush, e64, steps=3, **override):
+    """The same step with some parameters changed (e.g. precond=1, or
+    overlap=1: the FP64 product of the refinement residual started early on a
+    side stream): median device ms over `steps` steps after one warm-up, its
+    iterations, products, products per second, and the energy difference to
+    the FP64 solve."""
     import torch
     from paper_1506_03745_gb300.context import context as gpu_context
-    ctx = gpu_context(bodies, **dict(PARAMS, precond=1))
+    ctx = gpu_context(bodies, **dict(PARAMS, **override))
     n = pgb.pgb_num_unknowns(ctx)
     x = torch.empty(n, dtype=torch.float64, device=dev)
     ms, st, e = [], None, None
@@ -610,11 +633,13 @@ def precond_solve(pgb, bodies, dev, stream, flush, e64, steps=3):
         b.record(stream)
         b.synchronize()
         if code != 0:
-            raise RuntimeError(f"preconditioned solve did not converge: {st}")
+            raise RuntimeError(f"solve with {override} did not converge: {st}")
         if i:
             ms.append(a.elapsed_time(b))
     pgb.pgb_destroy(ctx)
-    return {"ms_per_step": statistics.median(ms), "iterations": st["iterations"], "matvecs": st["matvecs"],
+    return {"params": override, "ms_per_step": statistics.median(ms), "iterations": st["iterations"],
+            "matvecs": st["matvecs"], "matvecs_per_s": st["matvecs"] / (statistics.median(ms) / 1e3),
+            "rel_residual": st["rel_residual"],
             "energy_rel_err_vs_fp64": {k: abs(e[k] - e64[k]) / max(abs(e64[k]), 1e-300)
                                        for k in ("solvation", "surface", "total")}}
 

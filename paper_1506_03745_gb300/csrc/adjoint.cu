@@ -310,6 +310,7 @@ void apply_transpose(pgb_ctx* c, const double* lam, double* y, int precision) {
     up.leaf_node = c->d_leaf_node; up.nstart = c->d_node_start; up.nend = c->d_node_end;
     up.child = c->d_node_child; up.nchild = c->d_node_nchild; up.nbody = c->d_node_body;
     up.ncenter = c->d_node_center; up.K = 1;
+    up.p2m_grid = 0;
     for (int b = 0; b < PGB_MAX_BODIES; ++b) up.src_active[b] = 1;
     up.lvl_begin = up.lvl_end = 0;
     c->d_sT.resize(2 * n);

@@ -272,6 +272,13 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
     up.child = c->d_node_child; up.nchild = c->d_node_nchild;
     up.ncenter = c->d_node_center; up.K = c->p.K; up.nbody = c->d_node_body;
     up.lvl_begin = up.lvl_end = 0;
+    up.p2m_grid = 0;
+    if (precision != PGB_FP32) {  // FP64 P2M: two blocks per SM, leaves strided
+        int dev = 0, sms = 0;
+        PGB_CUDA(cudaGetDevice(&dev));
+        PGB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        up.p2m_grid = 2 * sms;
+    }
     EvalArgs ev;
     ev.n_groups = c->n_groups;
     ev.gstart = c->d_group_start; ev.gend = c->d_group_end; ev.gbody = c->d_group_body;

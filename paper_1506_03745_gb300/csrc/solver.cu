@@ -136,7 +136,8 @@ __global__ void k_multi_axpy(const double* __restrict__ V, int64_t ld, int m, co
 __global__ void k_scale_by(const double* w, const double* nrm, double* v, int64_t n) {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double a = *nrm;
-    if (r < n) v[r] = a > 0 ? w[r] / a : 0.0;
+    const double inv = a > 0 ? 1.0 / a : 0.0;
+    if (r < n) v[r] = w[r] * inv;
 }
 
 __global__ void k_axpby(double a, const double* x, double b, const double* y, double* out, int64_t n) {
@@ -336,10 +337,10 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arn_finish(ArnArgs a) {
     if (threadIdx.x == 0) shd[32] = sqrt(t);
     __syncthreads();
     const double nrm = shd[32];
+    const double inv = nrm > 0 ? 1.0 / nrm : 0.0;  // one division per block, not per row
     const int64_t stride = (int64_t)nb * blockDim.x;
     double* vn = a.V + (int64_t)(a.j + 1) * a.ld;
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < a.n; r += stride)
-        vn[r] = nrm > 0 ? a.w[r] / nrm : 0.0;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < a.n; r += stride) vn[r] = a.w[r] * inv;
     if (blockIdx.x == 0 && threadIdx.x == 0) {  // Givens step on column j (as k_givens)
         double* h = a.h;
         h[a.j + 1] = nrm;

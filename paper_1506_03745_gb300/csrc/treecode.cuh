@@ -517,6 +517,7 @@ struct UpArgs {
     const double* ncenter;
     int K;
     int64_t lvl_begin, lvl_end;  // node ids of the level for k_m2m_level
+    int p2m_grid;                // > 0: P2M over at most this many blocks (leaves strided)
 };
 
 __device__ __constant__ const int kBinom[9][9] = {
@@ -541,16 +542,17 @@ __global__ void __launch_bounds__(128) k_p2m_leaves(UpArgs a, const typename V4<
     __shared__ real sd[3][TD > 0 ? TD : 1];
     __shared__ short idx3[P + 1][P + 1][P + 1];
     const int tid = threadIdx.x;
-    const int64_t leaf = blockIdx.x;
-    if (leaf >= a.n_leaves) return;
-    const int nd = a.leaf_node[leaf];
-    if (!a.src_active[a.nbody[nd]]) return;
-    const int64_t s0 = (int64_t)a.nstart[nd] * a.K, s1 = (int64_t)a.nend[nd] * a.K;
     for (int k = tid; k < T; k += 128) {
         int x, y, z;
         decode_mi(k, x, y, z);
         idx3[x][y][z] = (short)k;
     }
+    // leaves blockIdx.x, blockIdx.x + gridDim.x, ... (one leaf per block when
+    // the grid covers them; a smaller grid holds fewer SM resources)
+    for (int64_t leaf = blockIdx.x; leaf < a.n_leaves; leaf += gridDim.x) {
+    const int nd = a.leaf_node[leaf];
+    if (!a.src_active[a.nbody[nd]]) continue;
+    const int64_t s0 = (int64_t)a.nstart[nd] * a.K, s1 = (int64_t)a.nend[nd] * a.K;
     // thread -> terms tid and tid + 128 (when T > 128)
     int kx[2] = {0, 0}, ky[2] = {0, 0}, kz[2] = {0, 0};
     bool on[2], low[2];
@@ -614,6 +616,8 @@ __global__ void __launch_bounds__(128) k_p2m_leaves(UpArgs a, const typename V4<
         if (kz[h]) dl += real(kz[h]) * sd[2][idx3[kx[h]][ky[h]][kz[h] - 1]];
         mom[(int64_t)nd * 2 * T + k] = qL[h] + dl;
         mom[(int64_t)nd * 2 * T + T + k] = qY[h] + dl;
+    }
+    __syncthreads();  // sd and pw are reused by the next leaf
     }
 }
 
