@@ -187,7 +187,8 @@ void apply_full(pgb_ctx* c, const double* x, double* y, int precision) { apply_m
 // used, then one cudaGraphLaunch on the context stream per product.
 static void upward_graph(pgb_ctx* c, bool f32, const UpArgs& up, const EvalArgs& ev, const void* src, void* mom) {
     auto& gr = c->up_graph[f32 ? 0 : 1];
-    bool ok = gr.exec && gr.tree_gen == c->tree_gen && gr.src == src && gr.mom == mom && gr.ncenter == up.ncenter;
+    bool ok = gr.exec && gr.tree_gen == c->tree_gen && gr.src == src && gr.mom == mom && gr.ncenter == up.ncenter &&
+              gr.p2m_grid == up.p2m_grid;
     for (int b = 0; ok && b < PGB_MAX_BODIES; ++b) ok = gr.src_active[b] == up.src_active[b];
     if (!ok) {
         if (gr.exec) {
@@ -221,6 +222,7 @@ static void upward_graph(pgb_ctx* c, bool f32, const UpArgs& up, const EvalArgs&
         gr.src = src;
         gr.mom = mom;
         gr.ncenter = up.ncenter;
+        gr.p2m_grid = up.p2m_grid;
         for (int b = 0; b < PGB_MAX_BODIES; ++b) gr.src_active[b] = up.src_active[b];
     }
     PGB_CUDA(cudaGraphLaunch(gr.exec, c->stream));
@@ -273,12 +275,8 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
     up.ncenter = c->d_node_center; up.K = c->p.K; up.nbody = c->d_node_body;
     up.lvl_begin = up.lvl_end = 0;
     up.p2m_grid = 0;
-    if (precision != PGB_FP32) {  // FP64 P2M: two blocks per SM, leaves strided
-        int dev = 0, sms = 0;
-        PGB_CUDA(cudaGetDevice(&dev));
-        PGB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        up.p2m_grid = 2 * sms;
-    }
+    if (precision != PGB_FP32 && c->persist_blocks > 0)  // side product: P2M on two blocks per SM
+        up.p2m_grid = 2 * c->persist_blocks;
     EvalArgs ev;
     ev.n_groups = c->n_groups;
     ev.gstart = c->d_group_start; ev.gend = c->d_group_end; ev.gbody = c->d_group_body;

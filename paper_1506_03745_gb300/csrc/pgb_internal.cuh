@@ -263,6 +263,7 @@ struct pgb_ctx {
         const void* src = nullptr;
         void* mom = nullptr;
         const double* ncenter = nullptr;
+        int p2m_grid = 0;
         int src_active[PGB_MAX_BODIES] = {0};
     } up_graph[2];
     cudaStream_t cap_stream = nullptr;   // capture only (nothing runs on it)
