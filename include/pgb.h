@@ -209,8 +209,8 @@ int pgb_solve(struct pgb_ctx* ctx, int32_t mode, double tol, int32_t max_iter, i
  *                   surfaces, 0 for molecules;
  *   dF_dt[3 n_bodies] dF/dt for a rigid translation of each body (kcal/mol/A).
  * x: the solution of pgb_solve (device doubles).  Host output pointers may be
- * NULL.  Needs P <= 7 and the bodies farther apart than 2L (no cross-body
- * near-field entries), else PGB_EINVAL.  adj (may be NULL) receives the
+ * NULL.  Needs the bodies farther apart than 2L (no cross-body near-field
+ * entries), else PGB_EINVAL.  adj (may be NULL) receives the
  * adjoint iterations and the relative residual of A^T lam = dF/dx. */
 int pgb_grad(struct pgb_ctx* ctx, const double* x, int32_t precision, double tol, int32_t max_iter, int32_t restart,
              double* dF_dq, double* dF_dbc, double* dF_dt, pgb_solve_stats* adj);

@@ -14,50 +14,7 @@ namespace pgb {
 static inline int nblk(int64_t n, int t) { return (int)std::max<int64_t>(1, (n + t - 1) / t); }
 
 // ---------------------------------------------------------------- set-up
-// Quadrature nodes relative to their group centre, unit normals, centroids
-// relative to their leaf centre, per-group node boxes.
-__global__ void k_adj_geom(const int32_t* gstart, const int32_t* gend, int64_t ng, const double* gcen,
-                           const double* Y, const double* W, int K, float4* y32, dbl4* y64, double* glo,
-                           double* ghi) {
-    const int64_t g = blockIdx.x;
-    if (g >= ng) return;
-    __shared__ double sh[6][32];
-    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int64_t q = gstart[g] * (int64_t)K + threadIdx.x; q < gend[g] * (int64_t)K; q += blockDim.x) {
-        double d[3];
-        for (int a = 0; a < 3; ++a) {
-            d[a] = Y[3 * q + a] - gcen[3 * g + a];
-            lo[a] = fmin(lo[a], Y[3 * q + a]);
-            hi[a] = fmax(hi[a], Y[3 * q + a]);
-        }
-        y32[q] = make_float4((float)d[0], (float)d[1], (float)d[2], (float)W[q]);
-        y64[q] = dbl4{d[0], d[1], d[2], W[q]};
-    }
-    for (int o = 16; o > 0; o >>= 1)
-        for (int a = 0; a < 3; ++a) {
-            lo[a] = fmin(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
-            hi[a] = fmax(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
-        }
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0)
-        for (int a = 0; a < 3; ++a) {
-            sh[a][w] = lo[a];
-            sh[3 + a][w] = hi[a];
-        }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int k = 1; k < (int)(blockDim.x >> 5); ++k)
-            for (int a = 0; a < 3; ++a) {
-                sh[a][0] = fmin(sh[a][0], sh[a][k]);
-                sh[3 + a][0] = fmax(sh[3 + a][0], sh[3 + a][k]);
-            }
-        for (int a = 0; a < 3; ++a) {
-            glo[3 * g + a] = sh[a][0];
-            ghi[3 * g + a] = sh[3 + a][0];
-        }
-    }
-}
-
+// Unit normals and centroids relative to their leaf centre.
 __global__ void k_adj_panels(int64_t n, const double* C, const double* Nn, const int32_t* pan_leaf,
                              const int32_t* leaf_node, const double* ncen, float4* n32, dbl4* n64, float4* c32,
                              dbl4* c64) {
@@ -70,25 +27,6 @@ __global__ void k_adj_panels(int64_t n, const double* C, const double* Nn, const
     n64[i] = dbl4{Nn[3 * i], Nn[3 * i + 1], Nn[3 * i + 2], 0.0};
     c32[i] = make_float4((float)d[0], (float)d[1], (float)d[2], 0.f);
     c64[i] = dbl4{d[0], d[1], d[2], 0.0};
-}
-
-// radius^2 of each node's centroids about its centre (one block per node)
-__global__ void k_node_rT2(const int32_t* nstart, const int32_t* nend, const double* ncen, const double* C,
-                           double* rT2) {
-    __shared__ double sh[32];
-    const int nd = blockIdx.x;
-    double m = 0;
-    for (int64_t i = nstart[nd] + threadIdx.x; i < nend[nd]; i += blockDim.x) {
-        double dx = C[3 * i] - ncen[3 * nd], dy = C[3 * i + 1] - ncen[3 * nd + 1], dz = C[3 * i + 2] - ncen[3 * nd + 2];
-        m = fmax(m, dx * dx + dy * dy + dz * dz);
-    }
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, sh[k]);
-        rT2[nd] = m;
-    }
 }
 
 // Transposed near-field corrections: CSR by source panel j, entries sorted by i.
@@ -129,23 +67,70 @@ __global__ void k_i64_from_u64(const unsigned long long* a, int64_t* b, int64_t 
     if (i < n) b[i] = (int64_t)a[i];
 }
 
+// group of every forward near entry
+__global__ void k_entry_group(int64_t ng, const int64_t* noff, int32_t* eg) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    for (int64_t e = noff[g]; e < noff[g + 1]; ++e) eg[e] = (int32_t)g;
+}
+__global__ void k_tn_count(int64_t ne, const int32_t* nearl, unsigned long long* cnt) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < ne) atomicAdd(cnt + nearl[e], 1ull);
+}
+__global__ void k_tn_fill(int64_t ne, const int32_t* nearl, const int64_t* toff, unsigned long long* cur,
+                          int64_t* te) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    const int nd = nearl[e];
+    te[toff[nd] + (int64_t)atomicAdd(cur + nd, 1ull)] = e;
+}
+__global__ void k_tn_sort(int64_t nn, const int64_t* toff, int64_t* te) {  // insertion sort per node
+    const int64_t nd = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (nd >= nn) return;
+    for (int64_t a = toff[nd] + 1; a < toff[nd + 1]; ++a) {
+        const int64_t v = te[a];
+        int64_t b = a - 1;
+        while (b >= toff[nd] && te[b] > v) {
+            te[b + 1] = te[b];
+            --b;
+        }
+        te[b + 1] = v;
+    }
+}
+
 static void build_adjoint(pgb_ctx* c) {
     if (c->adj_valid) return;
     cudaStream_t s = c->stream;
     const int64_t n = c->n_pan, ng = c->n_groups, K = c->p.K;
-    c->d_yT32.resize(n * K); c->d_yT64.resize(n * K);
-    c->d_gTlo.resize(3 * ng); c->d_gThi.resize(3 * ng);
-    k_adj_geom<<<(unsigned)ng, 128, 0, s>>>(c->d_group_start, c->d_group_end, ng, c->d_group_center, c->d_y, c->d_w,
-                                            (int)K, c->d_yT32, c->d_yT64, c->d_gTlo, c->d_gThi);
     c->d_n32.resize(n); c->d_n64.resize(n); c->d_cT32.resize(n); c->d_cT64.resize(n);
     k_adj_panels<<<nblk(n, 128), 128, 0, s>>>(n, c->d_c, c->d_n, c->d_pan_leaf, c->d_leaf_node, c->d_node_center,
                                              c->d_n32, c->d_n64, c->d_cT32, c->d_cT64);
-    c->d_rT2.resize(c->n_nodes);
-    k_node_rT2<<<(unsigned)c->n_nodes, 128, 0, s>>>(c->d_node_start, c->d_node_end, c->d_node_center, c->d_c,
-                                                    c->d_rT2);
     PGB_CUDA(cudaGetLastError());
-    make_lists(c, c->d_rT2, c->d_gTlo, c->d_gThi, c->d_Tnear_off, c->d_Tnear, c->d_Tfar_off, c->d_Tfar,
-               c->d_Tnear4, c->d_Tfar4, c->n_Tnear, c->n_Tfar, nullptr);
+    // the forward near lists by source leaf: for every leaf node, the forward
+    // near entries (group, leaf) that hold it, in entry (= group) order
+    {
+        const int64_t nn = c->n_nodes, ne = c->n_near;
+        c->d_near_group.resize(std::max<int64_t>(ne, 1));
+        k_entry_group<<<nblk(ng, 128), 128, 0, s>>>(ng, c->d_near_off, c->d_near_group);
+        DBuf<unsigned long long> tcnt, tcur;
+        tcnt.resize(nn);
+        tcur.resize(nn);
+        PGB_CUDA(cudaMemsetAsync(tcnt.p, 0, 8 * nn, s));
+        PGB_CUDA(cudaMemsetAsync(tcur.p, 0, 8 * nn, s));
+        k_tn_count<<<nblk(ne, 256), 256, 0, s>>>(ne, c->d_near, tcnt);
+        DBuf<int64_t> t64;
+        t64.resize(nn);
+        k_i64_from_u64<<<nblk(nn, 256), 256, 0, s>>>(tcnt, t64, nn);
+        c->d_tn_off.resize(nn + 1);
+        int64_t tot_tn = 0;
+        exclusive_scan_i64(t64, c->d_tn_off, nn, s, &tot_tn);
+        PGB_CUDA(cudaMemcpyAsync(c->d_tn_off.p + nn, &tot_tn, 8, cudaMemcpyHostToDevice, s));
+        if (tot_tn != ne) fail(PGB_EINVAL, "transposed near-list count mismatch");
+        c->d_tn_e.resize(std::max<int64_t>(ne, 1));
+        k_tn_fill<<<nblk(ne, 256), 256, 0, s>>>(ne, c->d_near, c->d_tn_off, tcur, c->d_tn_e);
+        k_tn_sort<<<nblk(nn, 128), 128, 0, s>>>(nn, c->d_tn_off, c->d_tn_e);
+        PGB_CUDA(cudaGetLastError());
+    }
     // transpose the near-field corrections (intra + cross)
     const int64_t tot = c->n_corr + c->n_xcorr;
     DBuf<unsigned long long> cnt, cur;
@@ -179,33 +164,6 @@ static void build_adjoint(pgb_ctx* c) {
 }
 
 // ---------------------------------------------------------------- A^T lam
-// Source strengths at the centroids: s_L = lam of the interior (Laplace) row
-// of a molecule panel, s_Y = lam of its exterior row or of a surface row.
-template <typename real>
-__global__ void k_srcT_prep(Geo g, BodyDev bd, const double* __restrict__ lam,
-                            const typename V4<real>::t* __restrict__ crel, typename V4<real>::t* __restrict__ srcT,
-                            double* __restrict__ sT) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= g.n_pan) return;
-    const int b = g.pbody[i];
-    const int64_t loc = g.perm[i] - bd.pan_off[b], N = bd.pan_off[b + 1] - bd.pan_off[b], o = bd.unk_off[b];
-    double sL = 0, sY;
-    if (bd.kind[b] == PGB_DIELECTRIC) {
-        sL = lam[o + loc];
-        sY = lam[o + N + loc];
-    } else {
-        sY = lam[o + loc];
-    }
-    typename V4<real>::t A = crel[i], B;
-    A.w = (real)sL;
-    B.x = (real)sY;
-    B.y = B.z = B.w = real(0);
-    srcT[2 * i] = A;
-    srcT[2 * i + 1] = B;
-    sT[2 * i] = sL;
-    sT[2 * i + 1] = sY;
-}
-
 // Per panel j: the K nodes' potentials and normal derivatives weighted by w_s
 // (the transposed V and K products), the transposed near-field corrections,
 // then the columns of A^T lam in the caller's layout.
@@ -250,38 +208,64 @@ __global__ void k_assemble_T(Geo g, BodyDev bd, const double* __restrict__ out4,
 }
 
 template <typename real, int P>
-static void launch_T(pgb_ctx* c, const TArgs& ta, const UpArgs& up, const void* srcT, const void* ytg,
-                     const void* nrm, void* mom) {
+static void launch_T(pgb_ctx* c, const TArgs& ta0, const void* xrel, const void* yrel, const void* nrm, void* L) {
     using v4 = typename V4<real>::t;
+    constexpr int T = MI<P>::T;
+    constexpr int NW = 4;
     cudaStream_t s = c->stream;
-    k_p2m_T<real, P><<<(unsigned)up.n_leaves, 128, 0, s>>>(up, (const v4*)srcT, (real*)mom);
-    for (int l = (int)c->level_begin.size() - 3; l >= 0; --l) {
-        UpArgs u = up;
-        u.lvl_begin = c->level_begin[l];
-        u.lvl_end = c->level_begin[l + 1];
-        if (u.lvl_end > u.lvl_begin)
-            k_m2m_level<real, P><<<(unsigned)(u.lvl_end - u.lvl_begin), 256, 0, s>>>(u, (real*)mom);
+    TArgs ta = ta0;
+    PGB_CUDA(cudaMemsetAsync(L, 0, sizeof(real) * (size_t)c->n_nodes * 2 * T, s));
+    k_p2p_T<real><<<(unsigned)std::max<int64_t>(ta.n_leaves, 1), 256, 0, s>>>(ta, (const v4*)xrel, c->d_sT,
+                                                                                (const v4*)yrel, (const v4*)nrm);
+    if (ta.n_fitems > 0)
+        k_m2p_T<real, P, NW><<<(unsigned)ta.n_fitems, NW * 32, 0, s>>>(ta, (const v4*)xrel, c->d_sT, (real*)L);
+    int launches = 3;
+    for (size_t l = 0; l + 2 < c->level_begin.size(); ++l) {  // parents at level l push to level l + 1
+        ta.lvl_begin = c->level_begin[l];
+        ta.lvl_end = c->level_begin[l + 1];
+        if (ta.lvl_end > ta.lvl_begin) {
+            k_l2l_level<real, P><<<(unsigned)(ta.lvl_end - ta.lvl_begin), 256, 0, s>>>(ta, (real*)L);
+            ++launches;
+        }
     }
-    k_p2p_T<real><<<(unsigned)ta.n_groups, 224, 0, s>>>(ta, (const v4*)ytg, (const v4*)nrm, (const v4*)srcT);
-    k_m2p_T<real, P><<<(unsigned)ta.n_groups, 224, 0, s>>>(ta, (const v4*)ytg, (const v4*)nrm, (const real*)mom);
+    k_l2p<real, P><<<(unsigned)std::max<int64_t>(ta.n_leaves, 1), 128, 0, s>>>(ta, (const v4*)yrel, (const v4*)nrm,
+                                                                               (const real*)L);
     PGB_CUDA(cudaGetLastError());
-    PGB_LAUNCHED(c, (int64_t)c->level_begin.size() + 1);
+    PGB_LAUNCHED(c, launches);
 }
 
 template <typename real>
-static void dispatch_T(pgb_ctx* c, const TArgs& ta, const UpArgs& up, const void* srcT, const void* ytg,
-                       const void* nrm, void* mom) {
+static void dispatch_T(pgb_ctx* c, const TArgs& ta, const void* xrel, const void* yrel, const void* nrm, void* L) {
     switch (c->p.P) {
-        case 0: launch_T<real, 0>(c, ta, up, srcT, ytg, nrm, mom); break;
-        case 1: launch_T<real, 1>(c, ta, up, srcT, ytg, nrm, mom); break;
-        case 2: launch_T<real, 2>(c, ta, up, srcT, ytg, nrm, mom); break;
-        case 3: launch_T<real, 3>(c, ta, up, srcT, ytg, nrm, mom); break;
-        case 4: launch_T<real, 4>(c, ta, up, srcT, ytg, nrm, mom); break;
-        case 5: launch_T<real, 5>(c, ta, up, srcT, ytg, nrm, mom); break;
-        case 6: launch_T<real, 6>(c, ta, up, srcT, ytg, nrm, mom); break;
-        case 7: launch_T<real, 7>(c, ta, up, srcT, ytg, nrm, mom); break;
-        default: fail(PGB_EINVAL, "the adjoint supports P <= 7");
+        case 0: launch_T<real, 0>(c, ta, xrel, yrel, nrm, L); break;
+        case 1: launch_T<real, 1>(c, ta, xrel, yrel, nrm, L); break;
+        case 2: launch_T<real, 2>(c, ta, xrel, yrel, nrm, L); break;
+        case 3: launch_T<real, 3>(c, ta, xrel, yrel, nrm, L); break;
+        case 4: launch_T<real, 4>(c, ta, xrel, yrel, nrm, L); break;
+        case 5: launch_T<real, 5>(c, ta, xrel, yrel, nrm, L); break;
+        case 6: launch_T<real, 6>(c, ta, xrel, yrel, nrm, L); break;
+        case 7: launch_T<real, 7>(c, ta, xrel, yrel, nrm, L); break;
+        case 8: launch_T<real, 8>(c, ta, xrel, yrel, nrm, L); break;
+        default: fail(PGB_EINVAL, "P out of range");
     }
+}
+
+// Row weights of the transposed product: s_L = lam of the interior (Laplace)
+// row of a molecule panel, s_Y = lam of its exterior row or of a surface row.
+__global__ void k_sT(Geo g, BodyDev bd, const double* __restrict__ lam, double* __restrict__ sT) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= g.n_pan) return;
+    const int b = g.pbody[i];
+    const int64_t loc = g.perm[i] - bd.pan_off[b], N = bd.pan_off[b + 1] - bd.pan_off[b], o = bd.unk_off[b];
+    double sL = 0, sY;
+    if (bd.kind[b] == PGB_DIELECTRIC) {
+        sL = lam[o + loc];
+        sY = lam[o + N + loc];
+    } else {
+        sY = lam[o + loc];
+    }
+    sT[2 * i] = sL;
+    sT[2 * i + 1] = sY;
 }
 
 void apply_transpose(pgb_ctx* c, const double* lam, double* y, int precision) {
@@ -295,35 +279,32 @@ void apply_transpose(pgb_ctx* c, const double* lam, double* y, int precision) {
     TArgs ta;
     ta.n_groups = c->n_groups;
     ta.gstart = c->d_group_start; ta.gend = c->d_group_end; ta.gbody = c->d_group_body;
-    ta.near_off = c->d_Tnear_off; ta.far_off = c->d_Tfar_off; ta.near4 = c->d_Tnear4; ta.far4 = c->d_Tfar4;
-    ta.near_l = c->d_Tnear; ta.far_l = c->d_Tfar;
+    ta.gcenter = c->d_group_center; ta.ncenter = c->d_node_center;
     ta.nstart = c->d_node_start; ta.nend = c->d_node_end; ta.nbody = c->d_node_body;
-    ta.ncenter = c->d_node_center; ta.gcenter = c->d_group_center;
+    ta.nchild = c->d_node_nchild; ta.child = c->d_node_child;
     ta.K = (int)K;
     ta.kappa = c->kappa;
     for (int b = 0; b < PGB_MAX_BODIES; ++b) ta.lap_body[b] = 0;
     for (size_t b = 0; b < c->bodies.size(); ++b) ta.lap_body[b] = c->bodies[b].kind == PGB_DIELECTRIC;
+    ta.n_fitems = c->n_fitems;
+    ta.far_off = c->d_far_off; ta.fitem_off = c->d_fitem_off; ta.far_l = c->d_far; ta.fitem_group = c->d_fitem_group;
+    ta.far4 = c->d_far4;
+    ta.m2p_item = c->p.m2p_item;
+    ta.tn_off = c->d_tn_off; ta.tn_e = c->d_tn_e; ta.near_group = c->d_near_group; ta.near4 = c->d_near4;
+    ta.near_l = c->d_near;
+    ta.n_leaves = c->n_leaves;
+    ta.leaf_node = c->d_leaf_node;
+    ta.lvl_begin = ta.lvl_end = 0;
     c->d_Tout.resize(4 * n * K);
     ta.out = c->d_Tout;
-    UpArgs up;
-    up.n_leaves = c->n_leaves;
-    up.leaf_node = c->d_leaf_node; up.nstart = c->d_node_start; up.nend = c->d_node_end;
-    up.child = c->d_node_child; up.nchild = c->d_node_nchild; up.nbody = c->d_node_body;
-    up.ncenter = c->d_node_center; up.K = 1;
-    up.p2m_grid = 0;
-    for (int b = 0; b < PGB_MAX_BODIES; ++b) up.src_active[b] = 1;
-    up.lvl_begin = up.lvl_end = 0;
     c->d_sT.resize(2 * n);
+    k_sT<<<nblk(n, 128), 128, 0, s>>>(g, bd, lam, c->d_sT);
     if (precision == PGB_FP32) {
-        c->d_srcT32.resize(2 * n);
         c->d_momT32.resize((size_t)c->n_nodes * 2 * T);
-        k_srcT_prep<float><<<nblk(n, 128), 128, 0, s>>>(g, bd, lam, c->d_cT32, c->d_srcT32, c->d_sT);
-        dispatch_T<float>(c, ta, up, c->d_srcT32, c->d_yT32, c->d_n32, c->d_momT32);
+        dispatch_T<float>(c, ta, c->d_x32, c->d_y32, c->d_n32, c->d_momT32);
     } else {
-        c->d_srcT64.resize(2 * n);
         c->d_momT64.resize((size_t)c->n_nodes * 2 * T);
-        k_srcT_prep<double><<<nblk(n, 128), 128, 0, s>>>(g, bd, lam, c->d_cT64, c->d_srcT64, c->d_sT);
-        dispatch_T<double>(c, ta, up, c->d_srcT64, c->d_yT64, c->d_n64, c->d_momT64);
+        dispatch_T<double>(c, ta, c->d_x64, c->d_y64, c->d_n64, c->d_momT64);
     }
     k_assemble_T<<<nblk(n, 128), 128, 0, s>>>(g, bd, c->d_Tout, c->d_sT, c->d_ct_off, c->d_ct_i, c->d_ct_val, lam, y);
     PGB_CUDA(cudaGetLastError());
@@ -516,7 +497,6 @@ void grad(pgb_ctx* c, const double* x, int precision, double tol, int max_iter, 
           double* dt, pgb_solve_stats* st) {
     if (!c->tree_valid) fail(PGB_ESTATE, "pgb_tree_build has not run");
     if (c->n_xcorr) fail(PGB_EINVAL, "gradients need the bodies farther apart than 2L (cross-body near entries exist)");
-    if (c->p.P > 7) fail(PGB_EINVAL, "the adjoint supports P <= 7");
     if (precision != PGB_FP32 && precision != PGB_FP64) fail(PGB_EINVAL, "precision must be PGB_FP32 or PGB_FP64");
     cudaStream_t s = c->stream;
     const int64_t n = c->n_unk, np = c->n_pan;

@@ -640,7 +640,6 @@ int pgb_matvec_transpose(pgb_ctx* c, const double* lam, double* y, int32_t preci
     return guard(c, [&]() -> int {
         if (!lam || !y) fail(PGB_EINVAL, "null vector");
         if (precision != PGB_FP32 && precision != PGB_FP64) fail(PGB_EINVAL, "precision must be PGB_FP32 or PGB_FP64");
-        if (c->p.P > 7) fail(PGB_EINVAL, "the adjoint supports P <= 7");
         apply_transpose(c, lam, y, precision);
         PGB_CUDA(cudaGetLastError());
         return PGB_OK;

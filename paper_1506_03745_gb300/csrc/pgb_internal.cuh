@@ -223,6 +223,8 @@ struct pgb_ctx {
     pgb::DBuf<int32_t> d_Tnear, d_Tfar, d_ct_i;
     pgb::DBuf<float4> d_Tnear4, d_Tfar4;
     pgb::DBuf<pgb::dbl4> d_ct_val;
+    pgb::DBuf<int32_t> d_near_group;     // group of each forward near entry
+    pgb::DBuf<int64_t> d_tn_off, d_tn_e;   // forward near entries by source leaf (CSR over nodes)
     pgb::DBuf<float4> d_srcT32;
     pgb::DBuf<pgb::dbl4> d_srcT64;
     pgb::DBuf<float> d_momT32;

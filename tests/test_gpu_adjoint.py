@@ -87,6 +87,32 @@ def test_dot_product_identity_direct_sum():
         pgb.pgb_destroy(ctx)
 
 
+@pytest.mark.parametrize("kind,theta,P", [("phi", 0.5, 6), ("sigma", 0.6, 3), ("sigma", 0.4, 8)])
+def test_transpose_is_exact_for_the_treecode(kind, theta, P):
+    """The transposed treecode is the exact transpose of the forward treecode
+    product (same near/far split, expansion and corrections):
+    <A x, lam> = <x, A^T lam> to rounding for any theta and P."""
+    bodies = _bodies(kind, nu=6, level=3)
+    ctx = gpu_context(bodies, theta=theta, P=P, leaf_size=8)
+    try:
+        assert pgb.pgb_tree_stats(ctx)["n_far"] > 0
+        n = pgb.pgb_num_unknowns(ctx)
+        rng = np.random.default_rng(8)
+        x, lam = rng.normal(size=n), rng.normal(size=n)
+        xt = torch.tensor(x, device="cuda")
+        yt = torch.empty_like(xt)
+        pgb.pgb_matvec(ctx, xt, yt, pgb.PGB_FP64)
+        lhs = lam @ yt.cpu().numpy()
+        rhs = _tmv(ctx, lam, pgb.PGB_FP64) @ x
+        assert rhs == pytest.approx(lhs, rel=1e-11)
+        x32 = torch.tensor(x, dtype=torch.float32, device="cuda")
+        y32 = torch.empty_like(x32)
+        pgb.pgb_matvec(ctx, x32, y32, pgb.PGB_FP32)
+        assert _tmv(ctx, lam, pgb.PGB_FP32) @ x == pytest.approx(lam @ y32.double().cpu().numpy(), rel=1e-5)
+    finally:
+        pgb.pgb_destroy(ctx)
+
+
 def _solve(ctx, tol=1e-11):
     n = pgb.pgb_num_unknowns(ctx)
     x = torch.empty(n, dtype=torch.float64, device="cuda")
