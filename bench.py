@@ -562,6 +562,48 @@ def run_poses(args):
     pgb.pgb_destroy(ctx)
 
 
+def run_scaling(args):
+    """The two-sphere configuration at icosphere levels 4..7 (2 x 5120 ... 2 x
+    327680 panels): the step (tree + FP32/FP64-refined solve + energies) and
+    the FP32 product alone, to show the growth with N."""
+    import torch
+    import paper_1506_03745_gb300 as pgb
+    from paper_1506_03745_gb300.context import context as gpu_context
+    out = []
+    for level in (4, 5, 6, 7):
+        bodies = workload_bodies(level)
+        ctx = gpu_context(bodies, **PARAMS)
+        n = pgb.pgb_num_unknowns(ctx)
+        x = torch.empty(n, dtype=torch.float64, device="cuda")
+
+        def step():
+            pgb.pgb_tree_reset(ctx)
+            pgb.pgb_tree_build(ctx)
+            code, st = pgb.pgb_solve(ctx, pgb.PGB_FP32_REFINE, TOL, MAX_ITER, RESTART, x)
+            return code, st, pgb.pgb_energy(ctx, x)
+
+        step()
+        ms, res = [], None
+        for _ in range(max(1, args.steps)):
+            res, t = _timed(step)
+            ms.append(t)
+        x32 = torch.randn(n, dtype=torch.float32, device="cuda")
+        y32 = torch.empty_like(x32)
+        pgb.pgb_matvec(ctx, x32, y32, pgb.PGB_FP32)
+        _, tmv = _timed(lambda: [pgb.pgb_matvec(ctx, x32, y32, pgb.PGB_FP32) for _ in range(10)])
+        code, st, e = res
+        info = pgb.pgb_tree_stats(ctx)
+        out.append({"panels": info["n_panels"], "unknowns": n, "ms_per_step": statistics.median(ms),
+                    "iterations": st["iterations"], "status": code, "fp32_matvec_ms": tmv / 10,
+                    "near_pairs": info["p2p_pairs"], "far_evaluations": info["m2p_pairs"],
+                    "solvation_kcal_mol": e["solvation"]})
+        pgb.pgb_destroy(ctx)
+        del x, x32, y32
+        torch.cuda.empty_cache()
+    print(json.dumps({"workload": "two spheres r=4 A, sigma 0.05 C/m^2, R=12 A, icosphere levels 4-7",
+                      "results": out}), flush=True)
+
+
 def run_brick(args):
     """Flat-faced charged body at zero ionic strength: the star molecule
     (2 panels/A^2, 900 charges) 10 A above a 100 x 100 x 10 A box with
@@ -679,7 +721,7 @@ def run_matvec(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--mode", default="solve", choices=["solve", "matvec"])
-    ap.add_argument("--workload", default="two_sphere", choices=["two_sphere", "star", "gradient", "poses", "brick"])
+    ap.add_argument("--workload", default="two_sphere", choices=["two_sphere", "star", "gradient", "poses", "brick", "scaling"])
     ap.add_argument("--poses", type=int, default=8, help="orientations for --workload poses")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--gpus", type=int, default=1)
@@ -710,6 +752,8 @@ def main():
         run_gradient(args)
     elif args.workload == "brick":
         run_brick(args)
+    elif args.workload == "scaling":
+        run_scaling(args)
     elif args.workload == "poses":
         run_poses(args)
     elif args.mode == "matvec":

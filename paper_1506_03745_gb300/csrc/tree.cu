@@ -1475,7 +1475,38 @@ void build_corrections(pgb_ctx* c) {
         build_corr_part(c, false, c->d_corr_off, c->d_corr_j, c->d_corr_val, c->d_corr_val32, c->n_corr);
         c->intra_valid = true;
     }
-    build_corr_part(c, true, c->d_xcorr_off, c->d_xcorr_j, c->d_xcorr_val, c->d_xcorr_val32, c->n_xcorr);
+    // cross-body entries: none when every pair of bodies is farther apart
+    // (centroid boxes of the roots) than the larger 2L reach (a8) of the two
+    const int nb = (int)c->bodies.size();
+    bool reach = false;
+    if (nb > 1) {
+        std::vector<double> lo(3 * nb), hi(3 * nb), a8(nb);
+        cudaStream_t s = c->stream;
+        PGB_CUDA(cudaMemcpyAsync(lo.data(), c->d_node_clo.p, 24 * nb, cudaMemcpyDeviceToHost, s));
+        PGB_CUDA(cudaMemcpyAsync(hi.data(), c->d_node_chi.p, 24 * nb, cudaMemcpyDeviceToHost, s));
+        PGB_CUDA(cudaMemcpyAsync(a8.data(), c->d_node_a8.p, 8 * nb, cudaMemcpyDeviceToHost, s));
+        PGB_CUDA(cudaStreamSynchronize(s));
+        for (int a = 0; a < nb && !reach; ++a)
+            for (int b = a + 1; b < nb && !reach; ++b) {
+                double d2 = 0;
+                for (int q = 0; q < 3; ++q) {
+                    const double u = std::max(std::max(lo[3 * a + q] - hi[3 * b + q], lo[3 * b + q] - hi[3 * a + q]), 0.0);
+                    d2 += u * u;
+                }
+                // the traversal's test is d2 < a8 with d2 >= this box distance
+                reach = !(d2 >= std::max(a8[a], a8[b]) * 1.000001);
+            }
+    }
+    if (reach) {
+        build_corr_part(c, true, c->d_xcorr_off, c->d_xcorr_j, c->d_xcorr_val, c->d_xcorr_val32, c->n_xcorr);
+    } else {
+        c->d_xcorr_off.resize(c->n_pan + 1);
+        PGB_CUDA(cudaMemsetAsync(c->d_xcorr_off.p, 0, 8 * (c->n_pan + 1), c->stream));
+        c->d_xcorr_j.resize(1);
+        c->d_xcorr_val.resize(1);
+        c->d_xcorr_val32.resize(1);
+        c->n_xcorr = 0;
+    }
 }
 
 Geo geo(const pgb_ctx* c) {
