@@ -41,7 +41,7 @@ METRIC = "treecode matvecs/sec and GMRES solve ms at 1e-5 energy err, FP32+refin
 UNIT = "matvecs/s"
 WORKLOAD = "two spheres r=4 A, 2 x 20480 panels, sigma=0.05 C/m^2, R=12 A"
 PARAMS = dict(K=7, K_near=19, n_edge=9, P=6, theta=0.5, leaf_size=32, group_size=32, p2p_item=64, m2p_item=64,
-              precond=0, graphs=1, lanes=4, overlap=0)
+              precond=0, graphs=1, lanes=4, overlap=0, batch=1)
 TOL = 1e-6
 RESTART = 100
 MAX_ITER = 2000
@@ -552,7 +552,8 @@ def run_poses(args):
     err = [abs(F[i, 3] - F64[i, 3]) / abs(F64[i, 3]) for i in range(2)]
     print(json.dumps({"workload": f"1 molecule ({pgb.pgb_tree_stats(ctx)['n_panels'] - 30420} panels, 900 "
                                   f"charges) x {args.poses} orientations x 4 gaps near a sphere r=40 A "
-                                  f"(30420 panels)", "poses": B, "lanes": PARAMS["lanes"], "ms": ms, "poses_per_s": B / (ms / 1e3),
+                                  f"(30420 panels)", "poses": B, "lanes": PARAMS["lanes"],
+                      "batch": PARAMS["batch"], "ms": ms, "poses_per_s": B / (ms / 1e3),
                       "mean_iterations": float(np.mean([s["iterations"] for s in st])),
                       "energy_rel_err_vs_fp64_first_2_poses": err, "status": code,
                       "stage_ms_per_pose": {k: v[0] / B for k, v in tim.items() if k != "kernel_launches" and v[0]},
@@ -560,6 +561,88 @@ def run_poses(args):
                       "F_total_range_kcal_mol": [float(F[:, 3].min()), float(F[:, 3].max())],
                       "orientation_landscape": orientation_landscape(F[:, 3], args.poses, 4)}), flush=True)
     pgb.pgb_destroy(ctx)
+
+
+def run_poses_uneven(args):
+    """Pose sweep over 8 distinct synthetic molecules of uneven size (star
+    surfaces r0 = 15 A from the molecule generator, about 5000 ... 40000
+    panels in geometric steps, 900 charges each) near a sphere r = 40 A
+    (30420 panels, sigma -0.05 C/m^2): `--poses` orientations x 4 gaps (6, 8,
+    10, 14 A) per molecule in pure FP32 (tol 1e-5).  Batched: pgb_solve_poses
+    with chunks of `batch` poses (default 8, one pose of every molecule per
+    chunk: one launch per stage over eight molecules of different sizes);
+    beside it the same poses molecule by molecule through pgb_solve_batch
+    with 4 lanes.  The energy error against FP64 is taken on the first
+    chunk."""
+    import torch
+    import synth
+    import paper_1506_03745_gb300 as pgb
+    from paper_1506_03745_gb300.context import context as gpu_context
+    batch = PARAMS["batch"] if PARAMS["batch"] > 1 else 8
+    sizes = np.geomspace(5000, 40000, 8)
+    srf = sphere_body()
+    ctxs, verts, npan, mols = [], [], [], []
+    for k, N in enumerate(sizes):
+        nu = int(round(math.sqrt(N / 20)))
+        seed = 300 + k
+        v, f = synth.star_surface(seed, nu)
+        coeffs = synth.star_coefficients(seed)
+        xyz, q = synth.interior_charges(seed, 900, v, f,
+                                        radius_fn=lambda d, c=coeffs: synth.star_radius(d, c, 15.0))
+        mol = dict(kind="dielectric", verts=v, tris=f, eps_in=4.0, qxyz=xyz, q=q, bc=0.0)
+        prm = dict(PARAMS, batch=batch) if k == 0 else dict(PARAMS, batch=1)
+        ctxs.append(gpu_context([mol, srf], **prm))
+        mols.append(mol)
+        verts.append(v)
+        npan.append(len(f))
+    Rs = synth.random_rotations(17, args.poses)
+    R, t, pc = [], [], []
+    for Ro in Rs:
+        for gap in (6.0, 8.0, 10.0, 14.0):
+            for k in range(8):
+                R.append(Ro)
+                t.append([place_for_gap(verts[k], Ro, 40.0, gap), 0.0, 0.0])
+                pc.append(k)
+    R, t, pc = np.array(R), np.array(t), np.array(pc, dtype=np.int32)
+    B = len(R)
+    tol = 1e-5
+    pgb.pgb_solve_poses(ctxs, pc[:batch], 0, R[:batch], t[:batch], pgb.PGB_FP32, tol, MAX_ITER, RESTART)  # warm-up
+    pgb.pgb_timing(ctxs[0], True, read=True)
+    (code, F, st), ms = _timed(lambda: pgb.pgb_solve_poses(ctxs, pc, 0, R, t, pgb.PGB_FP32, tol, MAX_ITER,
+                                                            RESTART))
+    tim = pgb.pgb_timing(ctxs[0], False, read=True)
+    # the same poses molecule by molecule with concurrent lanes (molecule 0
+    # needs a context of its own without the batch parameter)
+    c0 = gpu_context([mols[0], srf], **dict(PARAMS, batch=1))
+    F_l = np.zeros_like(F)
+    ms_l = 0.0
+    for k in range(8):
+        sel = np.nonzero(pc == k)[0]
+        ck = c0 if k == 0 else ctxs[k]
+        pgb.pgb_solve_batch(ck, 0, R[sel[:2]], t[sel[:2]], pgb.PGB_FP32, tol, MAX_ITER, RESTART)  # warm-up
+        (_, Fk, _), msk = _timed(lambda: pgb.pgb_solve_batch(ck, 0, R[sel], t[sel], pgb.PGB_FP32, tol, MAX_ITER,
+                                                             RESTART))
+        F_l[sel] = Fk
+        ms_l += msk
+    pgb.pgb_destroy(c0)
+    # FP64 reference for the first chunk
+    code64, F64, _ = pgb.pgb_solve_poses(ctxs, pc[:batch], 0, R[:batch], t[:batch], pgb.PGB_FP64, 1e-9, MAX_ITER,
+                                         RESTART)
+    err = np.abs(F[:batch, 3] - F64[:, 3]) / np.abs(F64[:, 3])
+    its = np.array([s["iterations"] for s in st])
+    print(json.dumps({"workload": f"8 molecules ({min(npan)}-{max(npan)} panels, 900 charges each) x {args.poses} "
+                                  f"orientations x 4 gaps near a sphere r=40 A (30420 panels)",
+                      "poses": B, "batch": batch, "ms": ms, "poses_per_s": B / (ms / 1e3),
+                      "lanes_4_per_molecule": {"ms": ms_l, "poses_per_s": B / (ms_l / 1e3),
+                                               "max_rel_diff_total_energy": float(np.max(np.abs(F_l[:, 3] - F[:, 3]) /
+                                                                                         np.abs(F[:, 3])))},
+                      "molecule_panels": npan, "mean_iterations": float(its.mean()),
+                      "iterations_range": [int(its.min()), int(its.max())], "status": code,
+                      "energy_rel_err_vs_fp64_first_chunk_max": float(err.max()),
+                      "stage_ms_per_pose": {k: v[0] / B for k, v in tim.items() if k != "kernel_launches" and v[0]},
+                      "kernel_launches_per_pose": tim["kernel_launches"] / B}), flush=True)
+    for c in ctxs:
+        pgb.pgb_destroy(c)
 
 
 def run_scaling(args):
@@ -721,7 +804,8 @@ def run_matvec(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--mode", default="solve", choices=["solve", "matvec"])
-    ap.add_argument("--workload", default="two_sphere", choices=["two_sphere", "star", "gradient", "poses", "brick", "scaling"])
+    ap.add_argument("--workload", default="two_sphere", choices=["two_sphere", "star", "gradient", "poses", "poses_uneven", "brick",
+                                                            "scaling"])
     ap.add_argument("--poses", type=int, default=8, help="orientations for --workload poses")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--gpus", type=int, default=1)
@@ -738,10 +822,11 @@ def main():
     ap.add_argument("--graphs", type=int, default=None, help="0: plain launches instead of the upward-pass graph")
     ap.add_argument("--lanes", type=int, default=None, help="concurrent pose lanes of pgb_solve_batch")
     ap.add_argument("--overlap", type=int, default=None, help="0: FP64 residual after the inner solve")
+    ap.add_argument("--batch", type=int, default=None, help="poses per block-diagonal union solve (pose workloads)")
     args = ap.parse_args()
     for k, v in (("leaf_size", args.leaf), ("P", args.P), ("theta", args.theta), ("p2p_item", args.p2p_item),
                  ("m2p_item", args.m2p_item), ("precond", args.precond),
-                 ("graphs", args.graphs), ("lanes", args.lanes), ("overlap", args.overlap)):
+                 ("graphs", args.graphs), ("lanes", args.lanes), ("overlap", args.overlap), ("batch", args.batch)):
         if v is not None:
             PARAMS[k] = v
     if args.impl == "reference":
@@ -756,6 +841,8 @@ def main():
         run_scaling(args)
     elif args.workload == "poses":
         run_poses(args)
+    elif args.workload == "poses_uneven":
+        run_poses_uneven(args)
     elif args.mode == "matvec":
         run_matvec(args)
     else:

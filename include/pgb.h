@@ -78,6 +78,11 @@ typedef struct pgb_params {
                              side (1e4 tol if smaller) and finishes the residual with the FP32 product of
                              the remaining change, so the FP64 work overlaps the FP32 iterations; 0: the
                              FP64 product of the final iterate, after the inner solve */
+    int32_t batch;        /* pgb_solve_batch / pgb_solve_poses: poses solved together as one
+                             block-diagonal system, 1..64 (0 = 1); > 1 replaces the lanes: every stage
+                             is one launch over the batch and GMRES runs in lockstep with per-pose
+                             coefficients and stopping tests.  The batch's bodies (poses x bodies of
+                             a pose) must not exceed 64. */
 } pgb_params;
 
 typedef struct pgb_solve_stats {
@@ -226,8 +231,30 @@ int pgb_matvec_transpose(struct pgb_ctx* ctx, const double* lam, double* y, int3
  * F_out[4b..4b+3] = Coulomb, solvation, surface, total (kcal/mol); stats may be
  * NULL or hold B entries.  The body keeps the last pose.  Returns PGB_ENOCONV
  * if any pose missed tol (all poses are still written). */
+/* With pgb_params.batch > 1 the poses go in chunks of `batch` to a union
+ * context (kept on ctx between calls) that holds every pose's bodies side by
+ * side, as independent problems of one block-diagonal system: the tree,
+ * lists and near-field entries never couple two poses, each treecode stage
+ * is one launch over the chunk, and GMRES advances all poses together, each
+ * with its own Krylov coefficients and stopping test (the residual each pose
+ * reaches is its own).  A last partial chunk is padded with repeats of its
+ * last pose, whose results are dropped. */
 int pgb_solve_batch(struct pgb_ctx* ctx, int32_t body_id, const double* R, const double* t, int64_t B, int32_t mode,
                     double tol, int32_t max_iter, int32_t restart, double* F_out, pgb_solve_stats* stats);
+
+/* Poses of several molecules (contexts of possibly different mesh sizes,
+ * each with the same solvent and the same body layout) solved in batches as
+ * above: pose b is body body_id of ctxs[pose_ctx[b]] at (R + 9 b, t + 3 b);
+ * the other bodies keep their poses in their own contexts.  ctxs[0] holds
+ * the union context and its parameters (batch, K, P, theta, ...) apply; a
+ * chunk is the next ctxs[0]->p.batch poses in order, so listing the poses
+ * with a repeating sequence of contexts lets every chunk reuse one union
+ * (its trees and near-field entries).  F_out and stats as pgb_solve_batch;
+ * the contexts' own trees are left as they were.  ctxs[k] must stay alive
+ * and unchanged while the call runs. */
+int pgb_solve_poses(struct pgb_ctx* const* ctxs, int32_t n_ctx, const int32_t* pose_ctx, int32_t body_id,
+                    const double* R, const double* t, int64_t B, int32_t mode, double tol, int32_t max_iter,
+                    int32_t restart, double* F_out, pgb_solve_stats* stats);
 
 /* Energies (Section 3.3, Eq. 11-16) of a solution x (device doubles):
  * Coulomb, solvation (phi_reac of Eq. 13 at the charges with the three-tier
@@ -262,8 +289,10 @@ int pgb_energy_noalloc(struct pgb_ctx* ctx, const double* x, pgb_energies* e);
  * energy.  The reference is the candidate with the smallest theta, largest P
  * and first leaf size; among the candidates whose total energy is within
  * target_rel_err of the reference, the one with the shortest solve time
- * (tree build + solve) is chosen.  The context keeps the chosen parameters and
- * a built tree; *chosen receives them.  report (may be NULL) receives, per
+ * (tree build + solve) is chosen.  With it, the work-item sizes p2p_item and
+ * m2p_item (one after the other, from {16, 32, 64, 128}) are then chosen by
+ * the time of `reps` FP32 matvecs; the product does not depend on them.  The
+ * context keeps the chosen parameters and a built tree; *chosen receives them.  report (may be NULL) receives, per
  * candidate in loop order theta-major, then P, then leaf: matvec ms, solve ms,
  * relative energy difference to the reference. */
 int pgb_autotune(struct pgb_ctx* ctx, const double* thetas, int32_t n_theta, const int32_t* Ps, int32_t n_P,

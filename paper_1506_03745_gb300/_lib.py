@@ -22,7 +22,7 @@ class pgb_params(ctypes.Structure):
     _fields_ = [("K", c_i32), ("K_near", c_i32), ("n_edge", c_i32), ("P", c_i32), ("theta", c_dbl),
                 ("leaf_size", c_i32), ("group_size", c_i32), ("p2p_item", c_i32), ("m2p_item", c_i32),
                 ("precond", c_i32), ("graphs", c_i32), ("lanes", c_i32),
-                ("overlap", c_i32)]
+                ("overlap", c_i32), ("batch", c_i32)]
 
 
 class pgb_solve_stats(ctypes.Structure):
@@ -79,6 +79,8 @@ _SIGS = {
     "pgb_solve": (c_i32, [c_vp, c_i32, c_dbl, c_i32, c_i32, c_vp, ctypes.POINTER(pgb_solve_stats)]),
     "pgb_energy": (c_i32, [c_vp, c_vp, ctypes.POINTER(pgb_energies), c_vp]),
     "pgb_solve_batch": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_i64, c_i32, c_dbl, c_i32, c_i32, c_vp, c_vp]),
+    "pgb_solve_poses": (c_i32, [c_vp, c_i32, c_vp, c_i32, c_vp, c_vp, c_i64, c_i32, c_dbl, c_i32, c_i32, c_vp,
+                                c_vp]),
     "pgb_grad": (c_i32, [c_vp, c_vp, c_i32, c_dbl, c_i32, c_i32, c_vp, c_vp, c_vp, ctypes.POINTER(pgb_solve_stats)]),
     "pgb_matvec_transpose": (c_i32, [c_vp, c_vp, c_vp, c_i32]),
     "pgb_tree_export": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
@@ -249,6 +251,24 @@ def pgb_solve_batch(ctx, body_id, R, t, mode, tol, max_iter, restart):
     st = (pgb_solve_stats * max(1, B))()
     code = _check(ctx, lib().pgb_solve_batch(ctx, body_id, Rp, tp, B, mode, tol, max_iter, restart,
                                              F.ctypes.data_as(c_vp), st), allow=(PGB_ENOCONV,))
+    return code, F, [{n: getattr(s, n) for n, _ in pgb_solve_stats._fields_} for s in st[:B]]
+
+
+def pgb_solve_poses(ctxs, pose_ctx, body_id, R, t, mode, tol, max_iter, restart):
+    """Poses of several contexts in batches of ctxs[0]'s `batch` parameter:
+    pose b is body body_id of ctxs[pose_ctx[b]] at (R[b], t[b]).  Returns
+    (status, F (B,4), list of stats dicts) as pgb_solve_batch."""
+    R_, Rp = _hptr(np.asarray(R).reshape(-1, 9), np.float64)
+    t_, tp = _hptr(np.asarray(t).reshape(-1, 3), np.float64)
+    pc_, pcp = _hptr(np.asarray(pose_ctx).reshape(-1), np.int32)
+    B = R_.shape[0]
+    if t_.shape[0] != B or pc_.shape[0] != B:
+        raise ValueError("R, t and pose_ctx batch sizes differ")
+    arr = (c_vp * len(ctxs))(*[c.value if isinstance(c, c_vp) else c for c in ctxs])
+    F = np.zeros((B, 4))
+    st = (pgb_solve_stats * max(1, B))()
+    code = _check(ctxs[0], lib().pgb_solve_poses(arr, len(ctxs), pcp, body_id, Rp, tp, B, mode, tol, max_iter,
+                                                 restart, F.ctypes.data_as(c_vp), st), allow=(PGB_ENOCONV,))
     return code, F, [{n: getattr(s, n) for n, _ in pgb_solve_stats._fields_} for s in st[:B]]
 
 

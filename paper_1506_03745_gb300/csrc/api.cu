@@ -108,8 +108,73 @@ static int check_params(const pgb_params* p, std::string& why) {
     else if (p->graphs != 0 && p->graphs != 1) why = "graphs must be 0 or 1";
     else if (p->lanes < 0 || p->lanes > 16) why = "lanes must be in 1..16 (0 = default)";
     else if (p->overlap != 0 && p->overlap != 1) why = "overlap must be 0 or 1";
+    else if (p->batch < 0 || p->batch > PGB_MAX_BODIES) why = "batch must be in 1..64 (0 = 1)";
     else return PGB_OK;
     return PGB_EINVAL;
+}
+
+// Why (R, t) is not a rigid pose (R orthonormal with det > 0, t finite), or
+// nullptr.
+static const char* pose_error(const double* R, const double* t) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0;
+            for (int k = 0; k < 3; ++k) s += R[3 * i + k] * R[3 * j + k];
+            if (!(fabs(s - (i == j ? 1.0 : 0.0)) < 1e-9)) return "R is not orthonormal";
+        }
+    double det = R[0] * (R[4] * R[8] - R[5] * R[7]) - R[1] * (R[3] * R[8] - R[5] * R[6]) + R[2] * (R[3] * R[7] - R[4] * R[6]);
+    if (!(det > 0) || !isfinite(t[0]) || !isfinite(t[1]) || !isfinite(t[2]))
+        return "R must be a proper rotation and t finite";
+    return nullptr;
+}
+
+// Poses b = 0 .. B-1 (body body_id of ctxs[pose_ctx[b]], or of ctxs[0] when
+// pose_ctx is null) through c's union context in chunks of c->p.batch.  A
+// last partial chunk is padded: with the union's own sources at their
+// current poses when its sequence of sources starts like the chunk (the
+// union is then reused), else with repeats of the chunk's last pose.
+static int solve_chunks(pgb_ctx* c, pgb_ctx* const* ctxs, const int32_t* pose_ctx, int32_t body_id,
+                        const double* R, const double* t, int64_t B, int32_t mode, double tol, int32_t max_iter,
+                        int32_t restart, double* F_out, pgb_solve_stats* stats) {
+    for (int64_t b = 0; b < B; ++b) {
+        const char* why = pose_error(R + 9 * b, t + 3 * b);
+        if (why) fail(PGB_EINVAL, "pose " + std::to_string(b) + ": " + why);
+    }
+    const int Bc = (int)std::min<int64_t>(c->p.batch, B);
+    auto src_of = [&](int64_t b) { return ctxs[pose_ctx ? pose_ctx[b] : 0]; };
+    std::vector<pgb_ctx*> src(Bc);
+    std::vector<double> Rc(9 * Bc), tc(3 * Bc), Fc(4 * Bc);
+    std::vector<pgb_solve_stats> sc(Bc);
+    int out = PGB_OK;
+    for (int64_t k0 = 0; k0 < B; k0 += Bc) {
+        const int nk = (int)std::min<int64_t>(Bc, B - k0);
+        bool prefix = c->union_ctx && (int)c->union_src.size() == Bc;
+        for (int q = 0; q < nk && prefix; ++q) prefix = c->union_src[q] == src_of(k0 + q);
+        for (int q = 0; q < Bc; ++q) {
+            const double *Rq, *tq;
+            if (q < nk || !prefix) {
+                const int64_t b = k0 + std::min(q, nk - 1);
+                src[q] = src_of(b);
+                Rq = R + 9 * b;
+                tq = t + 3 * b;
+            } else {
+                src[q] = c->union_src[q];
+                Rq = src[q]->bodies[body_id].R;
+                tq = src[q]->bodies[body_id].t;
+            }
+            memcpy(&Rc[9 * q], Rq, 9 * sizeof(double));
+            memcpy(&tc[3 * q], tq, 3 * sizeof(double));
+        }
+        const int r = solve_union(c, src, body_id, Rc.data(), tc.data(), mode, tol, max_iter, restart, Fc.data(),
+                                  sc.data());
+        if (r != PGB_OK && r != PGB_ENOCONV) return r;
+        for (int q = 0; q < nk; ++q) {
+            memcpy(F_out + 4 * (k0 + q), &Fc[4 * q], 4 * sizeof(double));
+            if (stats) stats[k0 + q] = sc[q];
+            if (!(sc[q].rel_residual <= tol)) out = PGB_ENOCONV;
+        }
+    }
+    return out;
 }
 
 // ---------------------------------------------------------------- pose lanes
@@ -274,6 +339,7 @@ int pgb_default_params(pgb_params* p) {
     p->graphs = 1;
     p->lanes = 4;
     p->overlap = 1;
+    p->batch = 1;
     return PGB_OK;
 }
 
@@ -306,6 +372,7 @@ int pgb_create(pgb_ctx** out, const pgb_params* p, void* stream) {
     if (q.p2p_item == 0) q.p2p_item = 64;
     if (q.lanes == 0) q.lanes = 4;
     if (q.m2p_item == 0) q.m2p_item = 64;
+    if (q.batch == 0) q.batch = 1;
     c->p = q;
     c->stream = (cudaStream_t)stream;
     if (cudaMallocHost(&c->h_pinned, 64) != cudaSuccess) {
@@ -320,6 +387,7 @@ int pgb_create(pgb_ctx** out, const pgb_params* p, void* stream) {
 int pgb_destroy(pgb_ctx* c) {
     if (!c) return PGB_EINVAL;
     destroy_lanes(c);
+    destroy_union(c);
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto& p : c->ev_pending) {
         cudaEventDestroy(p.second.first);
@@ -454,18 +522,9 @@ int pgb_set_pose(pgb_ctx* c, int32_t id, const double R[9], const double t[3]) {
         c->err = "bad body id or pose";
         return PGB_EINVAL;
     }
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            double s = 0;
-            for (int k = 0; k < 3; ++k) s += R[3 * i + k] * R[3 * j + k];
-            if (!(fabs(s - (i == j ? 1.0 : 0.0)) < 1e-9)) {
-                c->err = "R is not orthonormal";
-                return PGB_EINVAL;
-            }
-        }
-    double det = R[0] * (R[4] * R[8] - R[5] * R[7]) - R[1] * (R[3] * R[8] - R[5] * R[6]) + R[2] * (R[3] * R[7] - R[4] * R[6]);
-    if (!(det > 0) || !isfinite(t[0]) || !isfinite(t[1]) || !isfinite(t[2])) {
-        c->err = "R must be a proper rotation and t finite";
+    const char* why = pose_error(R, t);
+    if (why) {
+        c->err = why;
         return PGB_EINVAL;
     }
     auto& b = c->bodies[id];
@@ -585,9 +644,12 @@ int pgb_solve_batch(pgb_ctx* c, int32_t body_id, const double* R, const double* 
         if (!(tol > 0 && tol < 1)) fail(PGB_EINVAL, "tol must be in (0, 1)");
         if (max_iter < 1 || restart < 1 || restart > 256) fail(PGB_EINVAL, "max_iter >= 1 and restart in 1..256");
         if (B == 0) return PGB_OK;
-        const int L = (int)std::min<int64_t>(c->p.lanes, B);
+        const int L = c->p.batch > 1 ? 0 : (int)std::min<int64_t>(c->p.lanes, B);
         int first_err = PGB_OK;
-        if (L <= 1) {
+        if (c->p.batch > 1) {
+            pgb_ctx* self = c;
+            first_err = solve_chunks(c, &self, nullptr, body_id, R, t, B, mode, tol, max_iter, restart, F_out, stats);
+        } else if (L <= 1) {
             for (int64_t b = 0; b < B; ++b) {
                 const int rs = solve_pose(c, body_id, b, R + 9 * b, t + 3 * b, mode, tol, max_iter, restart,
                                           F_out + 4 * b, stats ? stats + b : nullptr);
@@ -597,7 +659,7 @@ int pgb_solve_batch(pgb_ctx* c, int32_t body_id, const double* R, const double* 
             first_err = solve_lanes(c, L, body_id, R, t, B, mode, tol, max_iter, restart, F_out, stats);
         }
         // the body keeps the last pose, with its tree built as after a serial batch
-        if (L > 1) {
+        if (L > 1 || c->p.batch > 1) {
             memcpy(c->bodies[body_id].R, R + 9 * (B - 1), 9 * sizeof(double));
             memcpy(c->bodies[body_id].t, t + 3 * (B - 1), 3 * sizeof(double));
             c->tree_valid = false;
@@ -614,6 +676,29 @@ int pgb_solve_batch(pgb_ctx* c, int32_t body_id, const double* R, const double* 
         PGB_CUDA(cudaStreamSynchronize(c->stream));
         if (first_err == PGB_ENOCONV) c->err = "GMRES did not reach tol for at least one pose";
         return first_err;
+    });
+}
+
+int pgb_solve_poses(pgb_ctx* const* ctxs, int32_t n_ctx, const int32_t* pose_ctx, int32_t body_id, const double* R,
+                    const double* t, int64_t B, int32_t mode, double tol, int32_t max_iter, int32_t restart,
+                    double* F_out, pgb_solve_stats* stats) {
+    if (!ctxs || n_ctx < 1 || !ctxs[0]) return PGB_EINVAL;
+    pgb_ctx* c = ctxs[0];
+    return guard(c, [&]() -> int {
+        if (!R || !t || !F_out || !pose_ctx || B < 0) fail(PGB_EINVAL, "null argument or negative batch");
+        for (int32_t k = 0; k < n_ctx; ++k) {
+            if (!ctxs[k]) fail(PGB_EINVAL, "null context " + std::to_string(k));
+            if (body_id < 0 || body_id >= (int32_t)ctxs[k]->bodies.size())
+                fail(PGB_EINVAL, "bad body id for context " + std::to_string(k));
+        }
+        for (int64_t b = 0; b < B; ++b)
+            if (pose_ctx[b] < 0 || pose_ctx[b] >= n_ctx) fail(PGB_EINVAL, "pose_ctx out of range at " + std::to_string(b));
+        if (!(tol > 0 && tol < 1)) fail(PGB_EINVAL, "tol must be in (0, 1)");
+        if (max_iter < 1 || restart < 1 || restart > 256) fail(PGB_EINVAL, "max_iter >= 1 and restart in 1..256");
+        if (B == 0) return PGB_OK;
+        const int r = solve_chunks(c, ctxs, pose_ctx, body_id, R, t, B, mode, tol, max_iter, restart, F_out, stats);
+        if (r == PGB_ENOCONV) c->err = "GMRES did not reach tol for at least one pose";
+        return r;
     });
 }
 
@@ -749,6 +834,39 @@ int pgb_autotune(pgb_ctx* c, const double* thetas, int32_t n_theta, const int32_
         if (tree_changes) c->order_valid = false;
         c->tree_valid = false;
         int r = pgb_tree_build(c);
+        if (r != PGB_OK) fail(r, c->err);
+        // then the work-item sizes (the product does not depend on them): each
+        // of p2p_item and m2p_item in turn from {16, 32, 64, 128}, by the FP32
+        // product time with the chosen parameters
+        PGB_CUDA(cudaEventCreate(&e0));
+        PGB_CUDA(cudaEventCreate(&e1));
+        for (int which = 0; which < 2; ++which) {
+            const int32_t keep = which ? c->p.m2p_item : c->p.p2p_item;
+            int32_t best_item = keep;
+            float best_ms = INFINITY;
+            for (int32_t item : {16, 32, 64, 128}) {
+                (which ? c->p.m2p_item : c->p.p2p_item) = item;
+                c->tree_valid = false;
+                r = pgb_tree_build(c);
+                if (r != PGB_OK) fail(r, c->err);
+                apply_operator(c, x, y, PGB_FP32, false);  // warm
+                PGB_CUDA(cudaEventRecord(e0, c->stream));
+                for (int k = 0; k < reps; ++k) apply_operator(c, x, y, PGB_FP32, false);
+                PGB_CUDA(cudaEventRecord(e1, c->stream));
+                PGB_CUDA(cudaEventSynchronize(e1));
+                float ms = 0;
+                PGB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best_item = item;
+                }
+            }
+            (which ? c->p.m2p_item : c->p.p2p_item) = best_item;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        c->tree_valid = false;
+        r = pgb_tree_build(c);
         if (r != PGB_OK) fail(r, c->err);
         if (chosen) *chosen = c->p;
         return PGB_OK;

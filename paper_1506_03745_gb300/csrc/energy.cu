@@ -2,6 +2,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -10,19 +11,17 @@
 
 namespace pgb {
 
-// Contribution of panel j (sorted index) of body b to phi_reac at xq
-// (without the 1/4pi): -K_L phi + V_L dphi with the 19-point rule when
-// |xq - c_j| < 2 L_j, else the K-point rule; 1/r by two Newton steps.
-__device__ __forceinline__ double phi_panel(const Geo& g, const BodyDev& bd, const Rules& r, const double* xq,
-                                            const double* x, int b, int64_t j) {
-    const int64_t s0 = bd.pan_off[b], N = bd.pan_off[b + 1] - s0, o = bd.unk_off[b];
-    const int64_t loc = g.perm[j] - s0;
-    const double phi = x[o + loc], dphi = x[o + N + loc];
+// V_L and K_L (without the 1/4pi) of panel j (sorted index) at the point xq:
+// the 19-point rule when |xq - c_j| < 2 L_j, else the K-point rule; 1/r by
+// two Newton steps.
+__device__ __forceinline__ void panel_vk(const Geo& g, const Rules& r, const double* xq, int64_t j, double& vl,
+                                         double& kl) {
     const double* cj = g.c + 3 * j;
     const double* nj = g.n + 3 * j;
     double dx = xq[0] - cj[0], dy = xq[1] - cj[1], dz = xq[2] - cj[2];
     double d2 = dx * dx + dy * dy + dz * dz;
-    double vl = 0, kl = 0;
+    vl = 0;
+    kl = 0;
     if (d2 < 8.0 * g.A[j]) {
         const double* v = g.v + 9 * j;
         for (int m = 0; m < r.Kn; ++m) {
@@ -46,7 +45,44 @@ __device__ __forceinline__ double phi_panel(const Geo& g, const BodyDev& bd, con
             kl += w * (nj[0] * ex + nj[1] * ey + nj[2] * ez) * ri * ri * ri;
         }
     }
+}
+
+// Contribution of panel j (sorted index) of body b to phi_reac at xq
+// (without the 1/4pi): -K_L phi + V_L dphi.
+__device__ __forceinline__ double phi_panel(const Geo& g, const BodyDev& bd, const Rules& r, const double* xq,
+                                            const double* x, int b, int64_t j) {
+    const int64_t s0 = bd.pan_off[b], N = bd.pan_off[b + 1] - s0, o = bd.unk_off[b];
+    const int64_t loc = g.perm[j] - s0;
+    const double phi = x[o + loc], dphi = x[o + N + loc];
+    double vl, kl;
+    panel_vk(g, r, xq, j, vl, kl);
     return vl * dphi - kl * phi;
+}
+
+// Charge weights of every panel j of a dielectric body b (Eq. 13 summed over
+// the charges first): sum_k q_k phi_reac(r_k) = sum_j (wV_j dphi_j - wK_j
+// phi_j) with wV_j = sum_k q_k V_L(r_k, j), wK_j = sum_k q_k K_L(r_k, j)
+// (without the 1/4pi), each pair with the rule of phi_panel.  The weights
+// depend on the body's own mesh and charges only, so they hold for every
+// rigid pose.  One warp per panel, lanes over the charges.
+__global__ void k_charge_weights(Geo g, BodyDev bd, Rules r, const double* qxyz, const double* qv,
+                                 const int64_t* qoff, double2* w) {
+    const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= g.n_pan) return;
+    const int b = g.pbody[j];
+    double sv = 0, sk = 0;
+    if (bd.kind[b] == PGB_DIELECTRIC)
+        for (int64_t k = qoff[b] + lane; k < qoff[b + 1]; k += 32) {
+            const double xq[3] = {qxyz[3 * k], qxyz[3 * k + 1], qxyz[3 * k + 2]};
+            double vl, kl;
+            panel_vk(g, r, xq, j, vl, kl);
+            sv += qv[k] * vl;
+            sk += qv[k] * kl;
+        }
+    sv = warp_sum(sv);
+    sk = warp_sum(sk);
+    if (lane == 0) w[j] = make_double2(sv, sk);
 }
 
 // phi_reac(r_k) = -K_L(phi) + V_L(dphi) at each charge of a dielectric body
@@ -107,19 +143,26 @@ static void launch_phi_reac(pgb_ctx* c, const Rules& r, const double* x, double*
     PGB_CUDA(cudaGetLastError());
 }
 
-// per-body sums: [0] sum q phi_reac, [2] sum_j u_j A_j (surfaces).  One
-// block per body.  The Coulomb pair sum is k_coulomb_pairs.
+// per-body sums: [0] sum q phi_reac (from phir at the charges, or, when w
+// is given, from the charge weights of the body's panels), [2] sum_j u_j A_j
+// (surfaces).  One block per body.  The Coulomb pair sum is k_coulomb_pairs.
 __global__ void k_body_sums(Geo g, BodyDev bd, const double* qxyz, const double* qv, const int64_t* qoff,
-                            const double* phir, const double* x, double* out) {
+                            const double* phir, const double2* w, const double* x, double* out) {
     __shared__ double sh[32];
     const int b = blockIdx.x;
     double s0 = 0, s2 = 0;
-    for (int64_t k = qoff[b] + threadIdx.x; k < qoff[b + 1]; k += blockDim.x) s0 += qv[k] * phir[k];
-    if (bd.kind[b] != PGB_DIELECTRIC) {
-        const int64_t p0 = bd.pan_off[b], p1 = bd.pan_off[b + 1];
-        for (int64_t j = p0 + threadIdx.x; j < p1; j += blockDim.x)
-            s2 += x[bd.unk_off[b] + (g.perm[j] - p0)] * g.A[j];
+    const int64_t p0 = bd.pan_off[b], p1 = bd.pan_off[b + 1], N = p1 - p0, o = bd.unk_off[b];
+    if (!w) {
+        for (int64_t k = qoff[b] + threadIdx.x; k < qoff[b + 1]; k += blockDim.x) s0 += qv[k] * phir[k];
+    } else if (bd.kind[b] == PGB_DIELECTRIC) {
+        for (int64_t j = p0 + threadIdx.x; j < p1; j += blockDim.x) {
+            const int64_t loc = g.perm[j] - p0;
+            s0 += w[j].x * x[o + N + loc] - w[j].y * x[o + loc];
+        }
+        s0 *= 1.0 / PGB_FOUR_PI;
     }
+    if (bd.kind[b] != PGB_DIELECTRIC)
+        for (int64_t j = p0 + threadIdx.x; j < p1; j += blockDim.x) s2 += x[o + (g.perm[j] - p0)] * g.A[j];
     s0 = block_sum(s0, sh);
     s2 = block_sum(s2, sh);
     if (threadIdx.x == 0) {
@@ -162,9 +205,8 @@ void energies(pgb_ctx* c, const double* x, pgb_energies* e, pgb_energies* per_bo
     if (!c->tree_valid) fail(PGB_ESTATE, "pgb_tree_build has not run");
     cudaStream_t s = c->stream;
     const int nb = (int)c->bodies.size();
-    DBuf<double> phir, sums;
+    DBuf<double> sums;
     DBuf<int64_t> qoff;
-    phir.resize(std::max<int64_t>(1, c->n_q));
     sums.resize(3 * nb);
     std::vector<int64_t> qo(nb + 1);
     for (int b = 0; b < nb; ++b) qo[b] = c->bodies[b].q_off;
@@ -172,8 +214,21 @@ void energies(pgb_ctx* c, const double* x, pgb_energies* e, pgb_energies* per_bo
     qoff.resize(nb + 1);
     PGB_CUDA(cudaMemcpyAsync(qoff.p, qo.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
     Rules r = make_rules(c->p.K, c->p.K_near, c->p.n_edge);
-    if (c->n_q) launch_phi_reac(c, r, x, phir);
-    k_body_sums<<<nb, 128, 0, s>>>(geo(c), body_dev(c), c->d_qxyz, c->d_qval, qoff, phir, x, sums);
+    // charge weights of the panels: computed once per tree, charges and rule,
+    // then every solution costs one pass over the panels
+    if (c->n_q) {
+        const uint64_t key[4] = {c->tree_gen, c->config_gen, (uint64_t)c->p.K, (uint64_t)c->p.K_near};
+        if (memcmp(key, c->qw_key, sizeof(key))) {
+            c->d_qw.resize(c->n_pan);
+            k_charge_weights<<<(unsigned)((c->n_pan * 32 + 127) / 128), 128, 0, s>>>(
+                geo(c), body_dev(c), r, c->d_qxyz, c->d_qval, qoff, c->d_qw);
+            PGB_CUDA(cudaGetLastError());
+            PGB_LAUNCHED(c, 1);
+            memcpy(c->qw_key, key, sizeof(key));
+        }
+    }
+    k_body_sums<<<nb, 128, 0, s>>>(geo(c), body_dev(c), c->d_qxyz, c->d_qval, qoff, nullptr,
+                                   c->n_q ? (const double2*)c->d_qw.p : nullptr, x, sums);
     {
         DBuf<double> pair;
         pair.resize(std::max<int64_t>(1, c->n_q));
@@ -185,7 +240,7 @@ void energies(pgb_ctx* c, const double* x, pgb_energies* e, pgb_energies* per_bo
         PGB_CUDA(cudaGetLastError());
         PGB_CUDA(cudaStreamSynchronize(s));
     }
-    PGB_LAUNCHED(c, c->n_q ? 4 : 2);
+    PGB_LAUNCHED(c, c->n_q ? 3 : 2);
     std::vector<double> h(3 * nb);
     PGB_CUDA(cudaMemcpyAsync(h.data(), sums.p, 8 * 3 * nb, cudaMemcpyDeviceToHost, s));
     PGB_CUDA(cudaStreamSynchronize(s));
@@ -267,7 +322,7 @@ void energies_noalloc(pgb_ctx* c, const double* x, pgb_energies* e) {
     PGB_CUDA(cudaMemcpyAsync(qoff, qo, 8 * (nb + 1), cudaMemcpyHostToDevice, s));
     Rules r = make_rules(c->p.K, c->p.K_near, c->p.n_edge);
     if (c->n_q) k_phi_reac<<<(unsigned)c->n_q, 128, 0, s>>>(geo(c), body_dev(c), r, c->d_qxyz, c->d_q_body, x, phir);
-    k_body_sums<<<nb, 128, 0, s>>>(geo(c), body_dev(c), c->d_qxyz, c->d_qval, qoff, phir, x, sums);
+    k_body_sums<<<nb, 128, 0, s>>>(geo(c), body_dev(c), c->d_qxyz, c->d_qval, qoff, phir, nullptr, x, sums);
     PGB_CUDA(cudaGetLastError());
     // Coulomb pair sums, one block per charge, accumulated into the scratch
     // after the per-body sums (pair sums reuse the reaction-potential slots

@@ -288,7 +288,7 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
         ev.lap_body[b] = c->bodies[b].kind == PGB_DIELECTRIC;
         // imposed-boundary terms: molecules carry no known density
         ev.src_active[b] = up.src_active[b] =
-            known_only ? (known_mask ? known_mask[b] : (c->bodies[b].kind != PGB_DIELECTRIC)) : 1;
+            !c->body_off[b] && (known_only ? (known_mask ? known_mask[b] : (c->bodies[b].kind != PGB_DIELECTRIC)) : 1);
     }
     ev.all_active = 1;
     for (size_t b = 0; b < c->bodies.size(); ++b) ev.all_active &= ev.src_active[b];

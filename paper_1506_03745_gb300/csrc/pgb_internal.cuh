@@ -109,6 +109,9 @@ struct Body {
     // tree frame
     double lo[3] = {0, 0, 0}, ext = 1.0;
     int32_t root = 0;
+    // independent problem the body belongs to: bodies of different problems
+    // do not interact (a batch of poses solved as one block-diagonal system)
+    int prob = 0;
 };
 
 // Device-side view of the problem passed by value to kernels.
@@ -237,6 +240,8 @@ struct pgb_ctx {
     pgb::DBuf<float> d_mom32;            // 2*T per node
     pgb::DBuf<double> d_mom64;
     pgb::DBuf<double> d_phi_part;        // chunk partial sums of phi_reac (few charges)
+    pgb::DBuf<double2> d_qw;             // charge weights (wV, wK) per sorted panel (energies)
+    uint64_t qw_key[4] = {~0ull, ~0ull, 0, 0};  // tree_gen, config_gen, K, K_near they were made for
     pgb::DBuf<double> d_Up[2], d_Uf[2];        // P2P / M2P partial sums: 64 per work item (32 L, then 32 Y)
     pgb::DBuf<double> d_xtmp, d_ytmp;    // FP64 staging for FP32 matvec API
     // scratch
@@ -274,6 +279,22 @@ struct pgb_ctx {
     bool owns_stream = false;            // lane contexts create (and destroy) their stream
     std::vector<pgb_ctx*> lane_ctx;      // pose lanes of pgb_solve_batch
     uint64_t lane_gen = ~0ull;           // config_gen the lanes were copied at
+    // block-diagonal pose batches: this context as the union of n_prob
+    // independent problems (bodies prob_first[p] .. prob_first[p + 1]; rows
+    // d_poff[p] .. d_poff[p + 1]), and, on the caller's context, the union
+    // it keeps with the sources it was copied from
+    int n_prob = 1;
+    std::vector<int> prob_first;
+    pgb::DBuf<int64_t> d_poff;
+    int seg_nbp = 0;                     // blocks per problem of the segmented kernels
+    pgb::DBuf<double> d_seg, d_seg_red;  // per-problem Krylov vectors; segmented partial sums
+    pgb::DBuf<int> d_segi;               // per-problem activity and column counts
+    // bodies left out of the products (1: its sources and rows are not
+    // computed; the problems that no longer iterate in a lockstep solve)
+    char body_off[PGB_MAX_BODIES] = {0};
+    pgb_ctx* union_ctx = nullptr;
+    std::vector<pgb_ctx*> union_src;
+    std::vector<uint64_t> union_gen;
 
     // statistics and stage timing
     bool timing = false;
@@ -332,12 +353,30 @@ struct GmresSpec {
 int gmres_op(pgb_ctx* c, int prec, bool transpose, const double* b, double* x, double abs_tol, int max_it,
              int restart, int* matvecs, double* est_out, bool x_zero, GmresSpec* spec = nullptr);
 double vec_dot(pgb_ctx* c, const double* a, const double* b);
+// Problems of a block-diagonal system for arnoldi_step: B problems, rows
+// poff[p] .. poff[p + 1] (device), act[p] (device) = 0 to skip problem p,
+// nbp blocks per problem; per-problem strides of H (sH) and of the
+// rotation / coefficient vectors (sV).
+struct ArnSeg {
+    int B, nbp;
+    const int64_t* poff;
+    const int* act;
+    int64_t sH, sV;
+};
+void arnoldi_step(pgb_ctx* c, int j, double* w, double* h, double* hc, double* cs, double* sn, double* g,
+                  double* out, const ArnSeg* sg);
 double energy_unit_kcal();
 void phi_reac(pgb_ctx* c, const double* x, double* out);
 // solver (solver.cu)
 void build_rhs(pgb_ctx* c, double* b, int precision);
 int solve(pgb_ctx* c, int mode, double tol, int max_iter, int restart, double* x, pgb_solve_stats* st);
 void precond_prepare(pgb_ctx* c);
+void precond_apply(pgb_ctx* c, const double* v, double* z, bool transpose, bool add);
+// batched poses (batch.cu)
+int solve_seg(pgb_ctx* c, int mode, double tol, int max_iter, int restart, double* x, pgb_solve_stats* st);
+int solve_union(pgb_ctx* c, const std::vector<pgb_ctx*>& src, int32_t body_id, const double* R, const double* t,
+                int32_t mode, double tol, int32_t max_iter, int32_t restart, double* F, pgb_solve_stats* st);
+void destroy_union(pgb_ctx* c);
 void reserve_product(pgb_ctx* c, int precision);
 // energy (energy.cu)
 void energies(pgb_ctx* c, const double* x, pgb_energies* e, pgb_energies* per_body);

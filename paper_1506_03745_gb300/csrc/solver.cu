@@ -208,7 +208,36 @@ struct ArnArgs {
     double* part2;  // second buffer (the next launch's partials)
     double *cs, *sn, *g;
     double* out;    // out[0] = |g_{j+1}|, out[1] = h_{j+1,j}
+    // Independent problems of a block-diagonal system, one per blockIdx.y:
+    // problem p owns rows poff[p] .. poff[p + 1] (poff == nullptr: one
+    // problem, rows 0 .. n) and its own H, rotations and partial sums at
+    // p * sH (h), p * sV (hc, cs, sn, g), p * sP (part, part2) and 2 p (out);
+    // act[p] == 0 leaves problem p untouched (act == nullptr: all active).
+    const int64_t* poff;
+    const int* act;
+    int64_t sH, sV, sP;
 };
+
+// The slice of ArnArgs that block (., p) works on; false when p is inactive.
+struct ArnView {
+    double *h, *hc, *part, *part2, *cs, *sn, *g, *out;
+    int64_t lo, hi;
+};
+__device__ __forceinline__ bool arn_view(const ArnArgs& a, ArnView& v) {
+    const int p = blockIdx.y;
+    if (a.act && !a.act[p]) return false;
+    v.lo = a.poff ? a.poff[p] : 0;
+    v.hi = a.poff ? a.poff[p + 1] : a.n;
+    v.h = a.h + p * a.sH;
+    v.hc = a.hc + p * a.sV;
+    v.cs = a.cs + p * a.sV;
+    v.sn = a.sn + p * a.sV;
+    v.g = a.g + p * a.sV;
+    v.part = a.part + p * a.sP;
+    v.part2 = a.part2 + p * a.sP;
+    v.out = a.out + 2 * p;
+    return true;
+}
 
 // Sums of eight values over the 32 lanes of a warp by a butterfly
 // reduce-scatter: each exchange halves the values a lane keeps, so a lane
@@ -242,15 +271,16 @@ __device__ __forceinline__ double warp_sum8(const double (&t)[8], int* k_out) {
     return x;
 }
 
-// Block partials of V_i . w (i < m) over this block's rows, eight vectors at a time.
-__device__ __forceinline__ void arn_block_dots(const ArnArgs& a, int m, double* part, double* shd) {
+// Block partials of V_i . w (i < m) over this block's rows of its problem,
+// eight vectors at a time.
+__device__ __forceinline__ void arn_block_dots(const ArnArgs& a, const ArnView& v, int m, double* part, double* shd) {
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const unsigned nb = gridDim.x;
     const int64_t stride = (int64_t)nb * blockDim.x;
-    const int64_t r0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t r0 = v.lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     for (int i0 = 0; i0 < m; i0 += 8) {
         double t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int64_t r = r0; r < a.n; r += stride) {
+        for (int64_t r = r0; r < v.hi; r += stride) {
             const double wr = a.w[r];
 #pragma unroll
             for (int u = 0; u < 8; ++u)
@@ -284,7 +314,9 @@ __device__ __forceinline__ void arn_reduce(const double* part, int m, double* co
 
 __global__ void __launch_bounds__(ARN_THREADS) k_arn_dot(ArnArgs a) {
     extern __shared__ double shd[];
-    arn_block_dots(a, a.j + 1, a.part, shd);
+    ArnView v;
+    if (!arn_view(a, v)) return;
+    arn_block_dots(a, v, a.j + 1, v.part, shd);
 }
 
 // pass 0: coefficients into h; pass 1: into hc and h += hc.  Then w -= sum
@@ -292,24 +324,26 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arn_dot(ArnArgs a) {
 // the second-pass dots; pass 1: |w|^2 in part2[b]).
 __global__ void __launch_bounds__(ARN_THREADS) k_arn_update(ArnArgs a, int pass) {
     extern __shared__ double shd[];  // m coefficients, then the dot scratch
+    ArnView v;
+    if (!arn_view(a, v)) return;
     const int m = a.j + 1;
     double* coef = shd;
     double* scratch = shd + ((m + 31) & ~31);
-    arn_reduce(pass ? a.part2 : a.part, m, coef);
+    arn_reduce(pass ? v.part2 : v.part, m, coef);
     if (blockIdx.x == 0)
         for (int i = threadIdx.x; i < m; i += blockDim.x) {
             if (pass) {
-                a.hc[i] = coef[i];
-                a.h[i] += coef[i];
+                v.hc[i] = coef[i];
+                v.h[i] += coef[i];
             } else {
-                a.h[i] = coef[i];
+                v.h[i] = coef[i];
             }
         }
     const unsigned nb = gridDim.x;
     const int64_t stride = (int64_t)nb * blockDim.x;
-    const int64_t r0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t r0 = v.lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double sq = 0;
-    for (int64_t r = r0; r < a.n; r += stride) {
+    for (int64_t r = r0; r < v.hi; r += stride) {
         double t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int i0 = 0; i0 < m; i0 += 8)
 #pragma unroll
@@ -321,18 +355,20 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arn_update(ArnArgs a, int pass)
     }
     if (pass == 0) {
         __syncthreads();
-        arn_block_dots(a, m, a.part2, scratch);
+        arn_block_dots(a, v, m, v.part2, scratch);
     } else {
         sq = block_sum(sq, scratch);
-        if (threadIdx.x == 0) a.part[blockIdx.x] = sq;
+        if (threadIdx.x == 0) v.part[blockIdx.x] = sq;
     }
 }
 
 __global__ void __launch_bounds__(ARN_THREADS) k_arn_finish(ArnArgs a) {
     extern __shared__ double shd[];
+    ArnView v;
+    if (!arn_view(a, v)) return;
     const unsigned nb = gridDim.x;
     double t = 0;
-    for (unsigned b = threadIdx.x; b < nb; b += blockDim.x) t += a.part[b];
+    for (unsigned b = threadIdx.x; b < nb; b += blockDim.x) t += v.part[b];
     t = block_sum(t, shd);
     if (threadIdx.x == 0) shd[32] = sqrt(t);
     __syncthreads();
@@ -340,41 +376,44 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arn_finish(ArnArgs a) {
     const double inv = nrm > 0 ? 1.0 / nrm : 0.0;  // one division per block, not per row
     const int64_t stride = (int64_t)nb * blockDim.x;
     double* vn = a.V + (int64_t)(a.j + 1) * a.ld;
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < a.n; r += stride) vn[r] = a.w[r] * inv;
+    for (int64_t r = v.lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < v.hi; r += stride)
+        vn[r] = a.w[r] * inv;
     if (blockIdx.x == 0 && threadIdx.x == 0) {  // Givens step on column j (as k_givens)
-        double* h = a.h;
+        double* h = v.h;
         h[a.j + 1] = nrm;
         for (int i = 0; i < a.j; ++i) {
-            const double x = a.cs[i] * h[i] + a.sn[i] * h[i + 1];
-            const double y = -a.sn[i] * h[i] + a.cs[i] * h[i + 1];
+            const double x = v.cs[i] * h[i] + v.sn[i] * h[i + 1];
+            const double y = -v.sn[i] * h[i] + v.cs[i] * h[i + 1];
             h[i] = x;
             h[i + 1] = y;
         }
-        a.out[1] = h[a.j + 1];
+        v.out[1] = h[a.j + 1];
         const double p = h[a.j], q = h[a.j + 1];
         const double r = hypot(p, q);
         const double c = r > 0 ? p / r : 1.0, sv = r > 0 ? q / r : 0.0;
-        a.cs[a.j] = c;
-        a.sn[a.j] = sv;
+        v.cs[a.j] = c;
+        v.sn[a.j] = sv;
         h[a.j] = r;
         h[a.j + 1] = 0;
-        a.g[a.j + 1] = -sv * a.g[a.j];
-        a.g[a.j] = c * a.g[a.j];
-        a.out[0] = fabs(a.g[a.j + 1]);
+        v.g[a.j + 1] = -sv * v.g[a.j];
+        v.g[a.j] = c * v.g[a.j];
+        v.out[0] = fabs(v.g[a.j + 1]);
     }
 }
 
-// The four launches of one Arnoldi step.
-static void arnoldi_step(pgb_ctx* c, int j, double* w, double* h, double* hc, double* cs, double* sn, double* g,
-                         double* out) {
+// The four launches of one Arnoldi step; with sg, for the problems of a
+// block-diagonal system (sg->nbp blocks per problem).
+void arnoldi_step(pgb_ctx* c, int j, double* w, double* h, double* hc, double* cs, double* sn, double* g,
+                  double* out, const ArnSeg* sg) {
     if (c->arn_blocks == 0) {
         int dev = 0, sms = 0;
         PGB_CUDA(cudaGetDevice(&dev));
         PGB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         c->arn_blocks = ARN_BLOCKS_PER_SM * sms;
     }
-    const int nb = c->arn_blocks, m = j + 1, warps = ARN_THREADS / 32;
-    c->d_red.resize(std::max<size_t>(c->d_red.n, (size_t)2 * nb * (m + 1)));
+    const int B = sg ? sg->B : 1;
+    const int nb = sg ? sg->nbp : c->arn_blocks, m = j + 1, warps = ARN_THREADS / 32;
+    c->d_red.resize(std::max<size_t>(c->d_red.n, (size_t)2 * nb * (m + 1) * B));
     ArnArgs a;
     a.V = c->d_V;
     a.ld = c->n_unk;
@@ -384,20 +423,26 @@ static void arnoldi_step(pgb_ctx* c, int j, double* w, double* h, double* hc, do
     a.h = h;
     a.hc = hc;
     a.part = c->d_red;
-    a.part2 = c->d_red.p + (size_t)nb * (m + 1);
+    a.part2 = c->d_red.p + (size_t)nb * (m + 1) * B;
     a.cs = cs;
     a.sn = sn;
     a.g = g;
     a.out = out;
+    a.poff = sg ? sg->poff : nullptr;
+    a.act = sg ? sg->act : nullptr;
+    a.sH = sg ? sg->sH : 0;
+    a.sV = sg ? sg->sV : 0;
+    a.sP = (int64_t)nb * (m + 1);
     const size_t dots = 8 * (size_t)std::max(32, m * warps);
     const size_t upd = 8 * (size_t)((m + 31) & ~31) + dots;
     if (upd > 48 * 1024)
         PGB_CUDA(cudaFuncSetAttribute(k_arn_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd));
     cudaStream_t s = c->stream;
-    k_arn_dot<<<nb, ARN_THREADS, dots, s>>>(a);
-    k_arn_update<<<nb, ARN_THREADS, upd, s>>>(a, 0);
-    k_arn_update<<<nb, ARN_THREADS, upd, s>>>(a, 1);
-    k_arn_finish<<<nb, ARN_THREADS, 8 * 64, s>>>(a);
+    const dim3 grid(nb, B);
+    k_arn_dot<<<grid, ARN_THREADS, dots, s>>>(a);
+    k_arn_update<<<grid, ARN_THREADS, upd, s>>>(a, 0);
+    k_arn_update<<<grid, ARN_THREADS, upd, s>>>(a, 1);
+    k_arn_finish<<<grid, ARN_THREADS, 8 * 64, s>>>(a);
     PGB_CUDA(cudaGetLastError());
 }
 
@@ -470,7 +515,7 @@ void precond_prepare(pgb_ctx* c) {
     c->pc_ready = true;
 }
 
-static void precond_apply(pgb_ctx* c, const double* v, double* z, bool transpose, bool add) {
+void precond_apply(pgb_ctx* c, const double* v, double* z, bool transpose, bool add) {
     k_precond_apply<<<nblk(c->n_pan, 128), 128, 0, c->stream>>>(geo(c), body_dev(c), c->d_pc, v, z,
                                                                 transpose ? 1 : 0, add ? 1 : 0);
     PGB_CUDA(cudaGetLastError());
@@ -557,7 +602,7 @@ int gmres_op(pgb_ctx* c, int prec, bool transpose, const double* b, double* x, d
             const bool fused = true;
             {
                 StageTimer tm(c, PGB_STAGE_KRYLOV);
-                arnoldi_step(c, j, w, h, hcol, cs, sn, g, misc.p + 2);
+                arnoldi_step(c, j, w, h, hcol, cs, sn, g, misc.p + 2, nullptr);
                 PGB_LAUNCHED(c, 4);
             }
             if (!fused) {  // the multi-kernel reference path (kept for comparison)

@@ -863,6 +863,7 @@ struct ListArgs {
     const double *center, *r2, *glo, *ghi;
     int n_bodies;
     int kind[PGB_MAX_BODIES];
+    int prob[PGB_MAX_BODIES];  // problem of each body (no lists across problems)
     double theta, theta2;
     int K;
 };
@@ -904,6 +905,7 @@ __global__ void __launch_bounds__(32 * LIST_WARPS) k_lists(ListArgs a, int64_t n
         return a.nchild[nd] == 0 ? 1 : 2;
     };
     for (int b = 0; b < a.n_bodies; ++b) {
+        if (a.prob[b] != a.prob[gb]) continue;
         const bool lap = (b == gb) && a.kind[b] == PGB_DIELECTRIC;
         int sp = 0;
         if (lane == 0) {
@@ -1072,7 +1074,10 @@ void make_lists(pgb_ctx* c, const double* r2, const double* glo, const double* g
     a.nbody = c->d_node_body; a.gstart = c->d_group_start; a.gend = c->d_group_end; a.gbody = c->d_group_body;
     a.center = c->d_node_center; a.r2 = r2; a.glo = glo; a.ghi = ghi;
     a.n_bodies = (int)c->bodies.size();
-    for (int b = 0; b < a.n_bodies; ++b) a.kind[b] = c->bodies[b].kind;
+    for (int b = 0; b < a.n_bodies; ++b) {
+        a.kind[b] = c->bodies[b].kind;
+        a.prob[b] = c->bodies[b].prob;
+    }
     a.theta = c->p.theta;
     a.theta2 = c->p.theta * c->p.theta;
     a.K = c->p.K;
@@ -1179,6 +1184,7 @@ struct CorrArgs {
     const int32_t *nchild, *child, *nstart, *nend;
     const double *clo, *chi, *a8, *C, *A;
     int n_bodies;
+    int prob[PGB_MAX_BODIES];  // problem of each body (no entries across problems)
 };
 
 // candidates j of target i: |c_i - c_j|^2 < 8 A_j (|x - c_j| < 2 L_j), or j == i;
@@ -1195,7 +1201,7 @@ __global__ void k_corr_find(CorrArgs a, int64_t n, bool fill, bool cross, const 
     int64_t k = 0, w = fill ? off[i] : 0;
     const int ib = pbody[i];
     for (int b = 0; b < a.n_bodies; ++b) {
-        if ((b != ib) != cross) continue;
+        if ((b != ib) != cross || a.prob[b] != a.prob[ib]) continue;
         int sp = 0;
         stack[sp++] = b;
         while (sp > 0) {
@@ -1431,6 +1437,7 @@ static void build_corr_part(pgb_ctx* c, bool cross, DBuf<int64_t>& off, DBuf<int
     a.nchild = c->d_node_nchild; a.child = c->d_node_child; a.nstart = c->d_node_start; a.nend = c->d_node_end;
     a.clo = c->d_node_clo; a.chi = c->d_node_chi; a.a8 = c->d_node_a8; a.C = c->d_c; a.A = c->d_A;
     a.n_bodies = (int)c->bodies.size();
+    for (int b = 0; b < a.n_bodies; ++b) a.prob[b] = c->bodies[b].prob;
     DBuf<int64_t> cnt;
     cnt.resize(n);
     off.resize(n + 1);
@@ -1475,8 +1482,9 @@ void build_corrections(pgb_ctx* c) {
         build_corr_part(c, false, c->d_corr_off, c->d_corr_j, c->d_corr_val, c->d_corr_val32, c->n_corr);
         c->intra_valid = true;
     }
-    // cross-body entries: none when every pair of bodies is farther apart
-    // (centroid boxes of the roots) than the larger 2L reach (a8) of the two
+    // cross-body entries: none when every pair of bodies of one problem is
+    // farther apart (centroid boxes of the roots) than the larger 2L reach
+    // (a8) of the two
     const int nb = (int)c->bodies.size();
     bool reach = false;
     if (nb > 1) {
@@ -1488,6 +1496,7 @@ void build_corrections(pgb_ctx* c) {
         PGB_CUDA(cudaStreamSynchronize(s));
         for (int a = 0; a < nb && !reach; ++a)
             for (int b = a + 1; b < nb && !reach; ++b) {
+                if (c->bodies[a].prob != c->bodies[b].prob) continue;
                 double d2 = 0;
                 for (int q = 0; q < 3; ++q) {
                     const double u = std::max(std::max(lo[3 * a + q] - hi[3 * b + q], lo[3 * b + q] - hi[3 * a + q]), 0.0);

@@ -26,6 +26,8 @@ def test_autotune_picks_fastest_accurate_candidate():
             (chosen["theta"], chosen["P"], chosen["leaf_size"]))
         assert ok[k] and rep[k, 1] == rep[ok, 1].min()
         assert rep[0, 2] == 0.0 or min(rep[:, 2]) == 0.0   # the reference itself
+        # the work-item sizes come from their own candidate set
+        assert chosen["p2p_item"] in (16, 32, 64, 128) and chosen["m2p_item"] in (16, 32, 64, 128)
         # the context is usable with the chosen parameters
         n = pgb.pgb_num_unknowns(ctx)
         x = torch.empty(n, dtype=torch.float64, device="cuda")
