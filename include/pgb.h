@@ -51,6 +51,10 @@ extern "C" {
 #define PGB_FP64 1          /* every treecode kernel in FP64 */
 #define PGB_FP32_REFINE 2   /* solve: FP32 inner GMRES, FP64 outer residual b - A x (one FP64
                                product with the imposed densities folded in per outer step) */
+#define PGB_FP64_DS 3       /* matvec: the FP64 product with P2P and M2P evaluated in double-single
+                               arithmetic (pairs of FP32, about 48 significant bits, relative
+                               error near 1e-13) on the FP32 pipe; upward pass, near-field
+                               corrections and assembly in FP64 (pgb_params.residual) */
 
 /* Numerical parameters: the seven columns of the paper's parameter tables
  * (Tables 1, 2, 4: Gauss points in-element per edge, close-by, far-away;
@@ -83,6 +87,8 @@ typedef struct pgb_params {
                              is one launch over the batch and GMRES runs in lockstep with per-pose
                              coefficients and stopping tests.  The batch's bodies (poses x bodies of
                              a pose) must not exceed 64. */
+    int32_t residual;     /* PGB_FP32_REFINE: precision of the outer residual's product: 1 (default)
+                             PGB_FP64_DS (GB300 issues FP64 at 1/64 of its FP32 rate), 0 native FP64 */
 } pgb_params;
 
 typedef struct pgb_solve_stats {
@@ -313,10 +319,12 @@ int pgb_tree_export(struct pgb_ctx* ctx, int32_t* perm, int64_t* near_off, int32
 
 /* Diagnostic: evaluate the device's FP64 elementary functions of the
  * near-field sums at n host points x (no context; the current device, its
- * default stream, synchronous).  out (host, n x 5, row-major) receives per
+ * default stream, synchronous).  out (host, n x 7, row-major) receives per
  * point: the one-step and two-step Newton reciprocal square roots (valid for
- * 1e-30 < x < 1e30), the Taylor 2^x (valid for -2^30 < x <= 1020), and the CUDA
- * library's rsqrt(x) and exp2(x) for comparison.  PGB_EINVAL for n < 0 or a
+ * 1e-30 < x < 1e30), the Taylor 2^x (valid for -2^30 < x <= 1020), the CUDA
+ * library's rsqrt(x) and exp2(x) for comparison, and the double-single
+ * reciprocal square root (1e-30 < x < 1e30) and 2^x (-100 < x < 127) of the
+ * PGB_FP64_DS product, each converted back to a double.  PGB_EINVAL for n < 0 or a
  * NULL pointer with n > 0; PGB_ECUDA on a CUDA error. */
 int pgb_math_check(const double* x, int64_t n, double* out);
 

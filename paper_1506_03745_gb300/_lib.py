@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libpgb.so")
 
 PGB_OK, PGB_EINVAL, PGB_ENOMEM, PGB_ECUDA, PGB_ENOCONV, PGB_ETIMEOUT, PGB_ESTATE = 0, -1, -2, -3, -4, -5, -6
 PGB_DIELECTRIC, PGB_SET_CHARGE, PGB_SET_POTENTIAL = 0, 1, 2
-PGB_FP32, PGB_FP64, PGB_FP32_REFINE = 0, 1, 2
+PGB_FP32, PGB_FP64, PGB_FP32_REFINE, PGB_FP64_DS = 0, 1, 2, 3
 
 c_i32, c_i64, c_dbl, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
 
@@ -22,7 +22,7 @@ class pgb_params(ctypes.Structure):
     _fields_ = [("K", c_i32), ("K_near", c_i32), ("n_edge", c_i32), ("P", c_i32), ("theta", c_dbl),
                 ("leaf_size", c_i32), ("group_size", c_i32), ("p2p_item", c_i32), ("m2p_item", c_i32),
                 ("precond", c_i32), ("graphs", c_i32), ("lanes", c_i32),
-                ("overlap", c_i32), ("batch", c_i32)]
+                ("overlap", c_i32), ("batch", c_i32), ("residual", c_i32)]
 
 
 class pgb_solve_stats(ctypes.Structure):
@@ -337,8 +337,9 @@ def pgb_tree_export(ctx):
 
 def pgb_math_check(x):
     """Device FP64 functions at the points x (host array): columns one-step
-    and two-step Newton rsqrt, Taylor exp2, library rsqrt, library exp2."""
+    and two-step Newton rsqrt, Taylor exp2, library rsqrt, library exp2,
+    double-single rsqrt, double-single exp2."""
     x = np.ascontiguousarray(x, dtype=np.float64)
-    out = np.zeros((len(x), 5), np.float64)
+    out = np.zeros((len(x), 7), np.float64)
     _check(None, lib().pgb_math_check(x.ctypes.data_as(c_vp), len(x), out.ctypes.data_as(c_vp)))
     return out

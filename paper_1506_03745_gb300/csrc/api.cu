@@ -8,6 +8,7 @@
 #include <thread>
 
 #include "common.cuh"
+#include "ds.cuh"
 #include "pgb_internal.cuh"
 
 namespace pgb {
@@ -25,11 +26,13 @@ __global__ void k_math_check(int64_t n, const double* x, double* y) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double v = x[i];
-    y[5 * i] = rsqrt_nr<1>(v);
-    y[5 * i + 1] = rsqrt_nr<2>(v);
-    y[5 * i + 2] = exp2_taylor(v);
-    y[5 * i + 3] = rsqrt(v);
-    y[5 * i + 4] = exp2(v);
+    y[7 * i] = rsqrt_nr<1>(v);
+    y[7 * i + 1] = rsqrt_nr<2>(v);
+    y[7 * i + 2] = exp2_taylor(v);
+    y[7 * i + 3] = rsqrt(v);
+    y[7 * i + 4] = exp2(v);
+    y[7 * i + 5] = ds_to_double(ds_rsqrt(ds_from_double(v)));
+    y[7 * i + 6] = ds_to_double(ds_exp2(ds_from_double(v)));
 }
 
 static cudaEvent_t get_event(pgb_ctx* c) {
@@ -109,6 +112,7 @@ static int check_params(const pgb_params* p, std::string& why) {
     else if (p->lanes < 0 || p->lanes > 16) why = "lanes must be in 1..16 (0 = default)";
     else if (p->overlap != 0 && p->overlap != 1) why = "overlap must be 0 or 1";
     else if (p->batch < 0 || p->batch > PGB_MAX_BODIES) why = "batch must be in 1..64 (0 = 1)";
+    else if (p->residual != 0 && p->residual != 1) why = "residual must be 0 or 1";
     else return PGB_OK;
     return PGB_EINVAL;
 }
@@ -340,6 +344,7 @@ int pgb_default_params(pgb_params* p) {
     p->lanes = 4;
     p->overlap = 1;
     p->batch = 1;
+    p->residual = 1;
     return PGB_OK;
 }
 
@@ -594,10 +599,11 @@ int pgb_matvec(pgb_ctx* c, const void* x, void* y, int32_t precision) {
     if (!c) return PGB_EINVAL;
     return guard(c, [&]() -> int {
         if (!x || !y) fail(PGB_EINVAL, "null vector");
-        if (precision != PGB_FP32 && precision != PGB_FP64) fail(PGB_EINVAL, "precision must be PGB_FP32 or PGB_FP64");
+        if (precision != PGB_FP32 && precision != PGB_FP64 && precision != PGB_FP64_DS)
+            fail(PGB_EINVAL, "precision must be PGB_FP32, PGB_FP64 or PGB_FP64_DS");
         if (!c->tree_valid) fail(PGB_ESTATE, "pgb_tree_build has not run for the current bodies and poses");
-        if (precision == PGB_FP64) {
-            apply_operator(c, (const double*)x, (double*)y, PGB_FP64, false);
+        if (precision != PGB_FP32) {
+            apply_operator(c, (const double*)x, (double*)y, precision, false);
         } else {
             c->d_xtmp.resize(c->n_unk);
             c->d_ytmp.resize(c->n_unk);
@@ -913,11 +919,11 @@ int pgb_math_check(const double* x, int64_t n, double* out) {
     if (n == 0) return PGB_OK;
     double *dx = nullptr, *dy = nullptr;
     int rc = PGB_OK;
-    if (cudaMalloc(&dx, 8 * n) != cudaSuccess || cudaMalloc(&dy, 40 * n) != cudaSuccess) rc = PGB_ECUDA;
+    if (cudaMalloc(&dx, 8 * n) != cudaSuccess || cudaMalloc(&dy, 56 * n) != cudaSuccess) rc = PGB_ECUDA;
     if (rc == PGB_OK && cudaMemcpy(dx, x, 8 * n, cudaMemcpyHostToDevice) != cudaSuccess) rc = PGB_ECUDA;
     if (rc == PGB_OK) {
         pgb::k_math_check<<<(unsigned)((n + 255) / 256), 256>>>(n, dx, dy);
-        if (cudaGetLastError() != cudaSuccess || cudaMemcpy(out, dy, 40 * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+        if (cudaGetLastError() != cudaSuccess || cudaMemcpy(out, dy, 56 * n, cudaMemcpyDeviceToHost) != cudaSuccess)
             rc = PGB_ECUDA;
     }
     if (rc != PGB_OK) (void)cudaGetLastError();

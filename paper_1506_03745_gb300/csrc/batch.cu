@@ -324,7 +324,7 @@ int solve_seg(pgb_ctx* c, int mode, double tol, int max_iter, int restart, doubl
             std::vector<int> on(B);
             for (int p = 0; p < B; ++p) on[p] = !done[p];
             set_products(c, on);
-            apply_full(c, x, c->d_r, PGB_FP64);
+            apply_full(c, x, c->d_r, c->p.residual ? PGB_FP64_DS : PGB_FP64);
             all_products(c);
             k_seg_axpby<<<nblk(n, 256), 256, 0, s>>>(1.0, c->d_bc, -1.0, c->d_r, c->d_r, n);
             PGB_LAUNCHED(c, 2);

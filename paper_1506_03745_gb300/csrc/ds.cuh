@@ -1,0 +1,125 @@
+// Double-single arithmetic: a number is the unevaluated sum hi + lo of two
+// FP32 values with |lo| <= ulp(hi) / 2, about 48 significant bits in the
+// FP32 exponent range (magnitudes from about 1e-38 to 1e38; lo loses bits
+// below about 1e-31).  Built on the error-free transformations of Knuth
+// (two-sum, TAOCP vol. 2, 4.2.2) and Dekker (product error, here by one fused
+// multiply-add; Numer. Math. 18, 1971).  The treecode's FP64-class product
+// (the outer residual of the refinement) runs in it on the FP32 pipe, which
+// GB300 issues 64 times as fast as FP64.  Every operation is written with
+// the _rn intrinsics so that the compiler neither fuses nor reorders them.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace pgb {
+
+struct ds {
+    float hi, lo;
+    ds() = default;
+    __host__ __device__ constexpr ds(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ constexpr ds(int i) : hi((float)i), lo(0.f) {}  // exact for |i| < 2^24
+};
+
+// Split of a double constant (folded at compile time for literals).
+__host__ __device__ constexpr ds ds_const(double d) {
+    return ds((float)d, (float)(d - (double)(float)d));
+}
+
+__device__ __forceinline__ ds ds_from_double(double d) {
+    const float h = __double2float_rn(d);
+    return ds(h, __double2float_rn(d - (double)h));
+}
+__device__ __forceinline__ double ds_to_double(ds a) { return (double)a.hi + (double)a.lo; }
+
+// s + e = a + b exactly (Knuth)
+__device__ __forceinline__ ds two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return ds(s, e);
+}
+// the same when |a| >= |b| (or a == 0)
+__device__ __forceinline__ ds fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return ds(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+// a + b with error below about 2^-47 (|a| + |b|)
+__device__ __forceinline__ ds operator+(ds a, ds b) {
+    const ds s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ds operator-(ds a) { return ds(-a.hi, -a.lo); }
+__device__ __forceinline__ ds operator-(ds a, ds b) { return a + (-b); }
+__device__ __forceinline__ ds& operator+=(ds& a, ds b) {
+    a = a + b;
+    return a;
+}
+// a b: the exact product of the high parts by one fused multiply-add, the
+// cross terms added to its error (relative error below about 2^-46)
+__device__ __forceinline__ ds operator*(ds a, ds b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ds mul_f(ds a, float b) {
+    const float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ bool operator>(ds a, ds b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+
+// 1/sqrt(x), x > 0 (x = 0 gives a non-finite value; callers mask it): the
+// SFU estimate y of 1/sqrt(x.hi) (relative error below 2^-22) and one Newton
+// step y + (y/2)(1 - x y^2) with the residual 1 - x y^2 formed in
+// double-single; the step leaves a relative error of about 1.5 d^2 < 3e-14.
+__device__ __forceinline__ ds ds_rsqrt(ds x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x.hi));
+    const ds e = ds(1) - mul_f(mul_f(x, y), y);
+    return two_sum(y, __fmul_rn(__fmul_rn(0.5f, y), e.hi));
+}
+
+// 2^t for t < 127 (results below 2^-126 are returned as 0): t = n + f with
+// n = rint(t.hi) and f = t - n, |f| <= 1/2 (t.hi - n is exact); 2^f from its
+// Taylor series sum_k (ln 2)^k f^k / k!: the terms k = 7..12 in FP32 (they
+// are below 1.3e-7 in all, so FP32 leaves them an error below 1e-14), k = 0..6
+// by Horner steps in double-single; the truncation after k = 12 is below
+// 0.347^13 / 13! < 2e-16.  Then 2^n is applied to both parts (exact).
+template <int K>
+struct DsCoef {
+    static constexpr ds v = ds_const(Exp2Coef<K>::v);
+};
+__device__ __forceinline__ ds ds_exp2(ds t) {
+    const float n = rintf(t.hi);
+    const ds f = two_sum(__fsub_rn(t.hi, n), t.lo);
+    // tail k = 7..12 in FP32 (Horner), as the coefficient of f^7
+    float q = (float)Exp2Coef<12>::v;
+    q = __fmaf_rn(q, f.hi, (float)Exp2Coef<11>::v);
+    q = __fmaf_rn(q, f.hi, (float)Exp2Coef<10>::v);
+    q = __fmaf_rn(q, f.hi, (float)Exp2Coef<9>::v);
+    q = __fmaf_rn(q, f.hi, (float)Exp2Coef<8>::v);
+    q = __fmaf_rn(q, f.hi, (float)Exp2Coef<7>::v);
+    ds p = DsCoef<6>::v + mul_f(f, q);
+    p = p * f + DsCoef<5>::v;
+    p = p * f + DsCoef<4>::v;
+    p = p * f + DsCoef<3>::v;
+    p = p * f + DsCoef<2>::v;
+    p = p * f + DsCoef<1>::v;
+    p = p * f + ds(1);
+    if (n < -126.f) return ds(0);
+    const float sc = __int_as_float((127 + (int)n) << 23);
+    return ds(__fmul_rn(p.hi, sc), __fmul_rn(p.lo, sc));
+}
+
+// e^x = 2^(x log2 e)
+__device__ __forceinline__ ds ds_exp(ds x) {
+    constexpr ds log2e = ds_const(1.44269504088896340735992468100189);
+    return ds_exp2(x * log2e);
+}
+
+}  // namespace pgb

@@ -10,6 +10,8 @@ void treecode_launch_f32(int stage, int P, const UpArgs& up, const std::vector<i
                          const void* src, const void* xrel, void* mom, cudaStream_t s);
 void treecode_launch_f64(int stage, int P, const UpArgs& up, const std::vector<int64_t>& lv, const EvalArgs& ev,
                          const void* src, const void* xrel, void* mom, cudaStream_t s);
+void treecode_launch_ds(int stage, int P, const EvalArgs& ev, const void* src, const void* xrel, const void* mom,
+                        cudaStream_t s);
 
 static inline int nblk(int64_t n, int t) { return (int)std::max<int64_t>(1, (n + t - 1) / t); }
 
@@ -341,6 +343,8 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
             upward_graph(c, f32, up, ev, f32 ? (const void*)c->d_src32.p : (const void*)c->d_src64.p,
                          f32 ? (void*)c->d_mom32.p : (void*)c->d_mom64.p);
         else if (f32) treecode_launch_f32(stage, P, up, c->level_begin, ev, c->d_src32, c->d_x32, c->d_mom32, s);
+        else if (precision == PGB_FP64_DS && stage != PGB_STAGE_UPWARD)
+            treecode_launch_ds(stage, P, ev, c->d_src64, c->d_x64, c->d_mom64, s);
         else treecode_launch_f64(stage, P, up, c->level_begin, ev, c->d_src64, c->d_x64, c->d_mom64, s);
         PGB_CUDA(cudaGetLastError());
         PGB_LAUNCHED(c, stage == PGB_STAGE_UPWARD ? (int64_t)c->level_begin.size() - 2 : 1);

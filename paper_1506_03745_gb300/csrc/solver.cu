@@ -749,7 +749,7 @@ static void overlap_fork(pgb_ctx* c, const double* xs, void* user) {
     c->stream = c->side_stream;
     c->persist_blocks = sms;
     try {
-        apply_full(c, xfull, c->d_r64, PGB_FP64);
+        apply_full(c, xfull, c->d_r64, c->p.residual ? PGB_FP64_DS : PGB_FP64);
     } catch (...) {
         c->stream = s;
         c->persist_blocks = 0;
@@ -854,7 +854,7 @@ int solve(pgb_ctx* c, int mode, double tol, int max_iter, int restart, double* x
                 z.matvecs += 2;
                 ++z.matvecs_fp64;
             } else {
-                apply_full(c, x, c->d_r, PGB_FP64);
+                apply_full(c, x, c->d_r, c->p.residual ? PGB_FP64_DS : PGB_FP64);
                 ++z.matvecs;
                 ++z.matvecs_fp64;
                 k_axpby<<<nblk(n, 256), 256, 0, s>>>(1.0, c->d_bc, -1.0, c->d_r, c->d_r, n);

@@ -19,9 +19,14 @@
 // Moment shift (upward pass): M_k(c') = sum_{j<=k} C(k,j) (c'-c)^{k-j} M_j(c).
 #pragma once
 #include "common.cuh"
+#include "ds.cuh"
 #include "pgb_internal.cuh"
 
 namespace pgb {
+
+struct ds4 {
+    ds x, y, z, w;
+};
 
 template <typename T>
 struct V4;
@@ -33,6 +38,59 @@ template <>
 struct V4<double> {
     using t = dbl4;
 };
+template <>
+struct V4<ds> {
+    using t = ds4;
+};
+
+// Storage type of the kernels' inputs per arithmetic type: the
+// double-single kernels read the FP64 product's data (source terms, target
+// offsets, moments) and convert as they stage it.
+template <typename C>
+struct Store {
+    using S = C;
+};
+template <>
+struct Store<ds> {
+    using S = double;
+};
+template <typename C>
+__device__ __forceinline__ C to_c(typename Store<C>::S v) {
+    return v;
+}
+template <>
+__device__ __forceinline__ ds to_c<ds>(double v) {
+    return ds_from_double(v);
+}
+template <typename C>
+__device__ __forceinline__ typename V4<C>::t cvt4(const typename V4<typename Store<C>::S>::t& v) {
+    return v;
+}
+template <>
+__device__ __forceinline__ ds4 cvt4<ds>(const dbl4& v) {
+    return ds4{ds_from_double(v.x), ds_from_double(v.y), ds_from_double(v.z), ds_from_double(v.w)};
+}
+__device__ __forceinline__ double to_dbl(float v) { return (double)v; }
+__device__ __forceinline__ double to_dbl(double v) { return v; }
+__device__ __forceinline__ double to_dbl(ds v) { return ds_to_double(v); }
+// a double literal in the arithmetic type (split at compile time for ds)
+template <typename C>
+__device__ __forceinline__ C lit(double d) {
+    return (C)d;
+}
+template <>
+__device__ __forceinline__ ds lit<ds>(double d) {
+    return ds_const(d);
+}
+// 1/n in the arithmetic type (n a compile-time constant after unrolling)
+template <typename C>
+__device__ __forceinline__ C inv_int(int n) {
+    return C(1) / C(n);
+}
+template <>
+__device__ __forceinline__ ds inv_int<ds>(int n) {
+    return ds_const(1.0 / n);
+}
 
 __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
@@ -56,6 +114,10 @@ __device__ __forceinline__ float rsqrt_fast(float x) {
     return y;
 }
 __device__ __forceinline__ double rsqrt_fast(double x) { return rsqrt_nr<1>(x); }
+__device__ __forceinline__ ds rsqrt_(ds x) { return ds_rsqrt(x); }
+__device__ __forceinline__ ds rsqrt_fast(ds x) { return ds_rsqrt(x); }
+__device__ __forceinline__ ds exp_(ds x) { return ds_exp(x); }
+__device__ __forceinline__ ds exp2_(ds x) { return ds_exp2(x); }
 
 // Neumaier-compensated accumulation s + c += v.
 template <typename T>
@@ -64,6 +126,8 @@ __device__ __forceinline__ void kadd(T& s, T& c, T v) {
     c += (fabs(s) >= fabs(v)) ? ((s - t) + v) : ((v - t) + s);
     s = t;
 }
+// double-single sums carry their own error term (c stays 0)
+__device__ __forceinline__ void kadd(ds& s, ds&, ds v) { s = s + v; }
 
 // Multi-indices of total degree <= P: graded, and within a degree kx
 // descending then ky descending.
@@ -185,7 +249,7 @@ __device__ __forceinline__ void m2p_eval(real Rx, real Ry, real Rz, real kappa, 
     real an[P + 1], bn[P + 1], en[P + 1], hn[P + 1];
 #pragma unroll
     for (int n = 1; n <= P; ++n) {
-        const real inv_n = real(1) / real(n);
+        const real inv_n = inv_int<real>(n);
         an[n] = -(real(2 * n - 1) * inv_n) * i2;
         bn[n] = -(real(n - 1) * inv_n) * i2;
         hn[n] = -kappa * inv_n;
@@ -272,7 +336,7 @@ __device__ __forceinline__ void p2p_tile(const typename V4<real>::t* sA, const t
                                          int64_t t, int64_t own_lo, int64_t own_hi, real r0x, real r0y, real r0z,
                                          real kappa, real& sumL, real& sumY) {
     using v4 = typename V4<real>::t;
-    const real nkl = -kappa * real(1.4426950408889634);  // -kappa log2(e)
+    const real nkl = -kappa * lit<real>(1.4426950408889634);  // -kappa log2(e)
     real sL2 = 0, sY2 = 0;  // second accumulator pair: two independent chains
 #pragma unroll 4
     for (int j = 0; j < cnt; ++j) {
@@ -343,8 +407,8 @@ __device__ __forceinline__ void store_item(real (*red)[4][32], int w, int lane, 
             kadd(sY, eY, red[k][2][lane]);
             kadd(sY, eY, red[k][3][lane]);
         }
-        out[lane] = (double)sL + (double)eL;
-        out[32 + lane] = (double)sY + (double)eY;
+        out[lane] = to_dbl(sL) + to_dbl(eL);
+        out[32 + lane] = to_dbl(sY) + to_dbl(eY);
     }
 }
 
@@ -354,9 +418,11 @@ __device__ __forceinline__ void store_item(real (*red)[4][32], int w, int lane, 
 // next tile prefetched into registers.  The item's partial sums go to Up.
 template <typename real, int NW>
 __global__ void __launch_bounds__(NW * 32) k_p2p(EvalArgs a,
-                                                                    const typename V4<real>::t* __restrict__ src,
-                                                                    const typename V4<real>::t* __restrict__ xrel) {
+                                                 const typename V4<typename Store<real>::S>::t* __restrict__ src,
+                                                 const typename V4<typename Store<real>::S>::t* __restrict__ xrel) {
+    using S = typename Store<real>::S;  // storage type of the inputs
     using v4 = typename V4<real>::t;
+    using s4 = typename V4<S>::t;
     __shared__ v4 sA[NW][32], sB[NW][32];
     __shared__ real red[NW][4][32];
     __shared__ int64_t s_item;
@@ -366,15 +432,15 @@ __global__ void __launch_bounds__(NW * 32) k_p2p(EvalArgs a,
     const int64_t p0 = a.gstart[g], p1 = a.gend[g];
     const int64_t p = p0 + lane;
     const bool active = p < p1;
-    const v4 xr = active ? xrel[p] : xrel[p0];
+    const s4 xr = active ? xrel[p] : xrel[p0];
     const double gc0 = a.gcenter[3 * g], gc1 = a.gcenter[3 * g + 1], gc2 = a.gcenter[3 * g + 2];
-    const real kappa = (real)a.kappa;
+    const real kappa = to_c<real>((S)a.kappa);
     const int64_t own_lo = p * a.K, own_hi = own_lo + a.K;
     real UL = 0, cL = 0, UY = 0, cY = 0;
     const int64_t tb = a.tile_off[g] + (it - a.pitem_off[g]) * a.p2p_item;
     const int64_t t1 = min(a.tile_off[g + 1], tb + a.p2p_item);
     int64_t t = tb + w;
-    v4 pa = v4(), pb = v4();
+    s4 pa = s4(), pb = s4();
     int4 m = make_int4(0, 0, 0, 0);
     float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
     if (t < t1) {
@@ -389,21 +455,26 @@ __global__ void __launch_bounds__(NW * 32) k_p2p(EvalArgs a,
     while (t < t1) {
         const int cnt = m.y, flags = m.z | (a.src_active[m.w] ? 0 : 4);
         const int64_t first = (int64_t)__float_as_int(d.w);
-        real ox, oy, oz;
-        if (sizeof(real) == sizeof(float)) {
-            ox = (real)d.x;
-            oy = (real)d.y;
-            oz = (real)d.z;
+        // target relative to the leaf centre: FP32 from the tile's offset,
+        // else formed in FP64 (and split for double-single)
+        real r0x, r0y, r0z;
+        if constexpr (sizeof(real) == sizeof(float)) {
+            r0x = xr.x - (real)d.x;
+            r0y = xr.y - (real)d.y;
+            r0z = xr.z - (real)d.z;
         } else {
             const int nd = m.x;
-            ox = (real)(a.ncenter[3 * nd] - gc0);
-            oy = (real)(a.ncenter[3 * nd + 1] - gc1);
-            oz = (real)(a.ncenter[3 * nd + 2] - gc2);
+            const S ox = (S)(a.ncenter[3 * nd] - gc0);
+            const S oy = (S)(a.ncenter[3 * nd + 1] - gc1);
+            const S oz = (S)(a.ncenter[3 * nd + 2] - gc2);
+            r0x = to_c<real>(xr.x - ox);
+            r0y = to_c<real>(xr.y - oy);
+            r0z = to_c<real>(xr.z - oz);
         }
         __syncwarp();
         if (lane < cnt) {
-            sA[w][lane] = pa;
-            sB[w][lane] = pb;
+            sA[w][lane] = cvt4<real>(pa);
+            sB[w][lane] = cvt4<real>(pb);
         }
         __syncwarp();
         t += NW;
@@ -416,7 +487,6 @@ __global__ void __launch_bounds__(NW * 32) k_p2p(EvalArgs a,
                 pb = src[2 * q + 1];
             }
         }
-        const real r0x = xr.x - ox, r0y = xr.y - oy, r0z = xr.z - oz;
         real sumL = 0, sumY = 0;
         if (flags & 4) {
             // source body without density in this product (imposed-boundary terms)
@@ -438,9 +508,11 @@ __global__ void __launch_bounds__(NW * 32) k_p2p(EvalArgs a,
 // one target group; the nodes go round robin to the warps with the next
 // node's moments prefetched.  The item's partial sums go to Uf.
 template <typename real, int P, int NW>
-__global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a, const typename V4<real>::t* __restrict__ xrel,
-                                                  const real* __restrict__ mom) {
-    using v4 = typename V4<real>::t;
+__global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a,
+                                                 const typename V4<typename Store<real>::S>::t* __restrict__ xrel,
+                                                 const typename Store<real>::S* __restrict__ mom) {
+    using S = typename Store<real>::S;  // storage type of the inputs
+    using s4 = typename V4<S>::t;
     constexpr int T = MI<P>::T;
     constexpr int MW = (2 * T + 31) / 32;  // moment words per lane
     __shared__ real sM[NW][2 * T];
@@ -452,10 +524,10 @@ __global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a, const typename V4<r
     const int64_t p0 = a.gstart[g], p1 = a.gend[g];
     const int64_t p = p0 + lane;
     const bool active = p < p1;
-    const v4 xr = active ? xrel[p] : xrel[p0];
+    const s4 xr = active ? xrel[p] : xrel[p0];
     const double gc0 = a.gcenter[3 * g], gc1 = a.gcenter[3 * g + 1], gc2 = a.gcenter[3 * g + 2];
     const int gb = a.gbody[g];
-    const real kappa = (real)a.kappa;
+    const real kappa = to_c<real>((S)a.kappa);
     real UL = 0, cL = 0, UY = 0, cY = 0;
     const int64_t fb = a.far_off[g] + (it - a.fitem_off[g]) * a.m2p_item;
     const int64_t f1 = min(a.far_off[g + 1], fb + a.m2p_item);
@@ -463,23 +535,23 @@ __global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a, const typename V4<r
         if (a.all_active) return ee;
         while (ee < f1) {
             int nn;
-            real qx, qy, qz;
-            entry_offset<real>(a, ee, true, gc0, gc1, gc2, nn, qx, qy, qz);
+            S qx, qy, qz;
+            entry_offset<S>(a, ee, true, gc0, gc1, gc2, nn, qx, qy, qz);
             if (a.src_active[a.nbody[nn]]) return ee;
             ee += NW;
         }
         return ee;
     };
-    real pm[MW];
+    S pm[MW];
     int nd = -1;
-    real ox = 0, oy = 0, oz = 0;
+    S ox = 0, oy = 0, oz = 0;
     int64_t e = seek(fb + w);
     if (e < f1) {
-        entry_offset<real>(a, e, true, gc0, gc1, gc2, nd, ox, oy, oz);
+        entry_offset<S>(a, e, true, gc0, gc1, gc2, nd, ox, oy, oz);
 #pragma unroll
         for (int q = 0; q < MW; ++q) {
             const int k = lane + 32 * q;
-            pm[q] = k < 2 * T ? mom[(int64_t)nd * 2 * T + k] : real(0);
+            pm[q] = k < 2 * T ? mom[(int64_t)nd * 2 * T + k] : S(0);
         }
     }
     while (e < f1) {
@@ -487,18 +559,18 @@ __global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a, const typename V4<r
 #pragma unroll
         for (int q = 0; q < MW; ++q) {
             const int k = lane + 32 * q;
-            if (k < 2 * T) sM[w][k] = pm[q];
+            if (k < 2 * T) sM[w][k] = to_c<real>(pm[q]);
         }
         __syncwarp();
         const bool lap = (a.nbody[nd] == gb) && a.lap_body[gb];
-        const real Rx = xr.x - ox, Ry = xr.y - oy, Rz = xr.z - oz;
+        const real Rx = to_c<real>(xr.x - ox), Ry = to_c<real>(xr.y - oy), Rz = to_c<real>(xr.z - oz);
         e = seek(e + NW);
         if (e < f1) {  // prefetch the next node
-            entry_offset<real>(a, e, true, gc0, gc1, gc2, nd, ox, oy, oz);
+            entry_offset<S>(a, e, true, gc0, gc1, gc2, nd, ox, oy, oz);
 #pragma unroll
             for (int q = 0; q < MW; ++q) {
                 const int k = lane + 32 * q;
-                pm[q] = k < 2 * T ? mom[(int64_t)nd * 2 * T + k] : real(0);
+                pm[q] = k < 2 * T ? mom[(int64_t)nd * 2 * T + k] : S(0);
             }
         }
         real uL, uY;

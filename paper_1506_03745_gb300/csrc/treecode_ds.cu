@@ -1,0 +1,38 @@
+// Double-single evaluation kernels (P2P, M2P) of the FP64-class product: they
+// read the FP64 product's source terms, target offsets and moments (its
+// upward pass runs in FP64) and compute in double-single on the FP32 pipe.
+#include "treecode.cuh"
+
+namespace pgb {
+
+template <int P>
+static void launch_ds(int stage, const EvalArgs& ev, const void* src, const void* xrel, const void* mom,
+                      cudaStream_t s) {
+    constexpr int NW = 4;   // M2P warps per block (registers, as the FP64 kernel)
+    constexpr int NWP = 8;  // P2P warps per block
+    const bool persist = ev.p2p_work != nullptr;
+    if (stage == PGB_STAGE_P2P && ev.n_pitems > 0)
+        k_p2p<ds, NWP><<<(unsigned)(persist ? ev.persist_blocks : ev.n_pitems), NWP * 32, 0, s>>>(
+            ev, (const dbl4*)src, (const dbl4*)xrel);
+    if (stage == PGB_STAGE_M2P && ev.n_fitems > 0)
+        k_m2p<ds, P, NW><<<(unsigned)(persist ? ev.persist_blocks : ev.n_fitems), NW * 32, 0, s>>>(
+            ev, (const dbl4*)xrel, (const double*)mom);
+}
+
+void treecode_launch_ds(int stage, int P, const EvalArgs& ev, const void* src, const void* xrel, const void* mom,
+                        cudaStream_t s) {
+    switch (P) {
+        case 0: launch_ds<0>(stage, ev, src, xrel, mom, s); break;
+        case 1: launch_ds<1>(stage, ev, src, xrel, mom, s); break;
+        case 2: launch_ds<2>(stage, ev, src, xrel, mom, s); break;
+        case 3: launch_ds<3>(stage, ev, src, xrel, mom, s); break;
+        case 4: launch_ds<4>(stage, ev, src, xrel, mom, s); break;
+        case 5: launch_ds<5>(stage, ev, src, xrel, mom, s); break;
+        case 6: launch_ds<6>(stage, ev, src, xrel, mom, s); break;
+        case 7: launch_ds<7>(stage, ev, src, xrel, mom, s); break;
+        case 8: launch_ds<8>(stage, ev, src, xrel, mom, s); break;
+        default: fail(PGB_EINVAL, "P out of range");
+    }
+}
+
+}  // namespace pgb
