@@ -787,8 +787,8 @@ def run_matvec(args):
     dev = torch.device("cuda", 0)
     ctx = gpu_context(workload_bodies(), **PARAMS)
     n = pgb.pgb_num_unknowns(ctx)
-    prec = pgb.PGB_FP64 if args.precision == "fp64" else pgb.PGB_FP32
-    dt = torch.float64 if prec == pgb.PGB_FP64 else torch.float32
+    prec = {"fp32": pgb.PGB_FP32, "fp64": pgb.PGB_FP64, "fp64_ds": pgb.PGB_FP64_DS}[args.precision]
+    dt = torch.float32 if prec == pgb.PGB_FP32 else torch.float64
     x = torch.randn(n, dtype=dt, device=dev)
     y = torch.empty_like(x)
     for _ in range(args.warmup):
@@ -816,7 +816,7 @@ def main():
     ap.add_argument("--workload", default="two_sphere", choices=["two_sphere", "star", "gradient", "poses", "poses_uneven", "brick",
                                                             "scaling"])
     ap.add_argument("--poses", type=int, default=8, help="orientations for --workload poses")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp64_ds"])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)

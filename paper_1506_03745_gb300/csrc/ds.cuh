@@ -65,6 +65,16 @@ __device__ __forceinline__ ds operator*(ds a, ds b) {
     e = __fmaf_rn(a.lo, b.hi, e);
     return fast_two_sum(p, e);
 }
+// a b + c in one pass: the product's error term joins the sum (error below
+// about 2^-46 (|a b| + |c|)); 15 FP32 operations instead of 18
+__device__ __forceinline__ ds ds_fma(ds a, ds b, ds c) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const ds s = two_sum(p, c.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo)));
+}
 __device__ __forceinline__ ds mul_f(ds a, float b) {
     const float p = __fmul_rn(a.hi, b);
     float e = __fmaf_rn(a.hi, b, -p);
@@ -105,12 +115,12 @@ __device__ __forceinline__ ds ds_exp2(ds t) {
     q = __fmaf_rn(q, f.hi, (float)Exp2Coef<8>::v);
     q = __fmaf_rn(q, f.hi, (float)Exp2Coef<7>::v);
     ds p = DsCoef<6>::v + mul_f(f, q);
-    p = p * f + DsCoef<5>::v;
-    p = p * f + DsCoef<4>::v;
-    p = p * f + DsCoef<3>::v;
-    p = p * f + DsCoef<2>::v;
-    p = p * f + DsCoef<1>::v;
-    p = p * f + ds(1);
+    p = ds_fma(p, f, DsCoef<5>::v);
+    p = ds_fma(p, f, DsCoef<4>::v);
+    p = ds_fma(p, f, DsCoef<3>::v);
+    p = ds_fma(p, f, DsCoef<2>::v);
+    p = ds_fma(p, f, DsCoef<1>::v);
+    p = ds_fma(p, f, ds(1));
     if (n < -126.f) return ds(0);
     const float sc = __int_as_float((127 + (int)n) << 23);
     return ds(__fmul_rn(p.hi, sc), __fmul_rn(p.lo, sc));

@@ -129,6 +129,18 @@ __device__ __forceinline__ void kadd(T& s, T& c, T v) {
 // double-single sums carry their own error term (c stays 0)
 __device__ __forceinline__ void kadd(ds& s, ds&, ds v) { s = s + v; }
 
+// c + a b: as written for FP32 / FP64 (the compiler contracts it), one fused
+// double-single operation for ds
+template <typename T>
+__device__ __forceinline__ T madd(T a, T b, T c) {
+    return c + a * b;
+}
+__device__ __forceinline__ ds madd(ds a, ds b, ds c) { return ds_fma(a, b, c); }
+template <typename T>
+constexpr bool is_ds = false;
+template <>
+constexpr bool is_ds<ds> = true;
+
 // Multi-indices of total degree <= P: graded, and within a degree kx
 // descending then ky descending.
 template <int P>
@@ -270,8 +282,8 @@ __device__ __forceinline__ void m2p_eval(real Rx, real Ry, real Rz, real kappa, 
         for (int a = 0; a < 3; ++a) {
             if (mi.m1[k][a] >= 0) {
                 if (h1) {
-                    S1 += R[a] * G[mi.m1[k][a]];
-                    T1 += R[a] * H[mi.m1[k][a]];
+                    S1 = madd(R[a], G[mi.m1[k][a]], S1);
+                    T1 = madd(R[a], H[mi.m1[k][a]], T1);
                 } else {
                     S1 = R[a] * G[mi.m1[k][a]];
                     T1 = R[a] * H[mi.m1[k][a]];
@@ -291,12 +303,14 @@ __device__ __forceinline__ void m2p_eval(real Rx, real Ry, real Rz, real kappa, 
         }
         if (h2) {
             if (n < P) H[k] = hn[n] * (S1 + S2);
-            G[k] = an[n] * S1 + bn[n] * S2 + en[n] * (T1 + T2);
+            if constexpr (is_ds<real>) G[k] = madd(an[n], S1, madd(bn[n], S2, en[n] * (T1 + T2)));
+            else G[k] = an[n] * S1 + bn[n] * S2 + en[n] * (T1 + T2);
         } else {
             if (n < P) H[k] = hn[n] * S1;
-            G[k] = an[n] * S1 + en[n] * T1;
+            if constexpr (is_ds<real>) G[k] = madd(an[n], S1, en[n] * T1);
+            else G[k] = an[n] * S1 + en[n] * T1;
         }
-        accY += G[k] * MY[k];
+        accY = madd(G[k], MY[k], accY);
     }
     uY = accY;
     if (lap) {
@@ -311,7 +325,7 @@ __device__ __forceinline__ void m2p_eval(real Rx, real Ry, real Rz, real kappa, 
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 if (mi.m1[k][a] >= 0) {
-                    S1 = h1 ? S1 + R[a] * L[mi.m1[k][a]] : R[a] * L[mi.m1[k][a]];
+                    S1 = h1 ? madd(R[a], L[mi.m1[k][a]], S1) : R[a] * L[mi.m1[k][a]];
                     h1 = true;
                 }
                 if (mi.m2[k][a] >= 0) {
@@ -319,8 +333,9 @@ __device__ __forceinline__ void m2p_eval(real Rx, real Ry, real Rz, real kappa, 
                     h2 = true;
                 }
             }
-            L[k] = h2 ? an[n] * S1 + bn[n] * S2 : an[n] * S1;
-            accL += L[k] * ML[k];
+            if constexpr (is_ds<real>) L[k] = h2 ? madd(an[n], S1, bn[n] * S2) : an[n] * S1;
+            else L[k] = h2 ? an[n] * S1 + bn[n] * S2 : an[n] * S1;
+            accL = madd(L[k], ML[k], accL);
         }
         uL = accL;
     } else {
@@ -342,23 +357,38 @@ __device__ __forceinline__ void p2p_tile(const typename V4<real>::t* sA, const t
     for (int j = 0; j < cnt; ++j) {
         const v4 A = sA[j], B = sB[j];
         const real dx = r0x - A.x, dy = r0y - A.y, dz = r0z - A.z;
-        const real r2 = dx * dx + dy * dy + dz * dz;
+        real r2;
+        if constexpr (is_ds<real>) r2 = madd(dx, dx, madd(dy, dy, dz * dz));
+        else r2 = dx * dx + dy * dy + dz * dz;
         // a quadrature node of another panel never coincides with a target
         // centroid on a valid (non-overlapping) mesh; only the target's own
         // panel, in the leaf that holds the group, needs the exclusion
         real ri = rsqrt_fast(r2);
         if (OWN) ri = (r2 > real(0) && !(t + j >= own_lo && t + j < own_hi)) ? ri : real(0);
-        const real pd = B.x * dx + B.y * dy + B.z * dz;
+        real pd;
+        if constexpr (is_ds<real>) pd = madd(B.x, dx, madd(B.y, dy, B.z * dz));
+        else pd = B.x * dx + B.y * dy + B.z * dz;
         const real tt = pd * (ri * ri);
         const real r = r2 * ri;
         const real ex = exp2_(nkl * r);
-        const real gg = kappa * r + real(1);
-        if (j & 1) {
-            if (LAP) sL2 += ri * (A.w - tt);
-            sY2 += (ex * ri) * (B.w - gg * tt);
+        if constexpr (is_ds<real>) {
+            const ds yw = madd(-madd(kappa, r, ds(1)), tt, B.w);  // B.w - (kappa r + 1) tt
+            if (j & 1) {
+                if (LAP) sL2 = madd(ri, A.w - tt, sL2);
+                sY2 = madd(ex * ri, yw, sY2);
+            } else {
+                if (LAP) sumL = madd(ri, A.w - tt, sumL);
+                sumY = madd(ex * ri, yw, sumY);
+            }
         } else {
-            if (LAP) sumL += ri * (A.w - tt);
-            sumY += (ex * ri) * (B.w - gg * tt);
+            const real gg = kappa * r + real(1);
+            if (j & 1) {
+                if (LAP) sL2 += ri * (A.w - tt);
+                sY2 += (ex * ri) * (B.w - gg * tt);
+            } else {
+                if (LAP) sumL += ri * (A.w - tt);
+                sumY += (ex * ri) * (B.w - gg * tt);
+            }
         }
     }
     sumL += sL2;
