@@ -473,6 +473,51 @@ def run_star(args):
                       "results": rows}), flush=True)
 
 
+def run_stern(args):
+    """Nested interfaces: the star molecule (2 panels/A^2, 900 charges) inside
+    a Stern layer -- the same star surface at r0 = 17 A (about 2 A further
+    out, ion-free, eps 80) -- 10 A from a sphere r = 40 A (30420 panels,
+    sigma -0.05 C/m^2): FP32 + refinement (tol 1e-6) with one treecode pass
+    per region, against FP64 and against the same system without the layer."""
+    import torch
+    import synth
+    import paper_1506_03745_gb300 as pgb
+    from paper_1506_03745_gb300.context import context as gpu_context
+    mol = star_bodies(2)
+    nu = synth.nu_for_density(3, 2)
+    vs, fs = synth.star_surface(3, nu, 17.0)
+    stern = dict(kind="dielectric", verts=vs, tris=fs, eps_in=80.0, qxyz=np.zeros((0, 3)), q=np.zeros(0), bc=0.0)
+    srf = sphere_body()
+    D = place_for_gap(vs, np.eye(3), 40.0, 10.0)
+    for b in (mol, stern):
+        b["R"], b["t"] = np.eye(3), np.array([D, 0.0, 0.0])
+    out = {}
+    for name, bodies in (("stern", [dict(mol, parent=1), stern, srf]), ("plain", [mol, srf])):
+        ctx = gpu_context(bodies, **PARAMS)
+        n = pgb.pgb_num_unknowns(ctx)
+        x = torch.empty(n, dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup):
+            pgb.pgb_solve(ctx, pgb.PGB_FP32_REFINE, TOL, MAX_ITER, RESTART, x)
+        ms = []
+        for _ in range(args.steps):
+            (code, st), t = _timed(lambda: (pgb.pgb_tree_build(ctx),
+                                            pgb.pgb_solve(ctx, pgb.PGB_FP32_REFINE, TOL, MAX_ITER, RESTART, x))[1])
+            e32, te = _timed(lambda: pgb.pgb_energy(ctx, x))
+            ms.append(t + te)
+        (c64, st64), t64 = _timed(lambda: pgb.pgb_solve(ctx, pgb.PGB_FP64, TOL, MAX_ITER, RESTART, x))
+        e64 = pgb.pgb_energy(ctx, x)
+        out[name] = {"panels": pgb.pgb_tree_stats(ctx)["n_panels"], "unknowns": n,
+                     "ms_per_step": statistics.median(ms), "fp64_solve_ms": t64, "iterations": st["iterations"],
+                     "status": code, "energies_kcal_mol": e32,
+                     "energy_rel_err_vs_fp64": {k: abs(e32[k] - e64[k]) / max(abs(e64[k]), 1e-300)
+                                                for k in ("solvation", "surface", "total")}}
+        pgb.pgb_destroy(ctx)
+    print(json.dumps({"workload": "star molecule (2 panels/A^2, 900 charges) in a 2 A Stern layer, 10 A from a "
+                                  "sphere r=40 A (30420 panels, sigma -0.05 C/m^2)",
+                      "step": "tree build + FP32/FP64-refined solve (tol 1e-6) + energies", "results": out}),
+          flush=True)
+
+
 def run_gradient(args):
     """Config: star molecule (2 panels/A^2, 900 charges) 10 A from a sphere
     r = 40 A (30420 panels, sigma -0.05 C/m^2): adjoint gradient time."""
@@ -814,7 +859,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--mode", default="solve", choices=["solve", "matvec"])
     ap.add_argument("--workload", default="two_sphere", choices=["two_sphere", "star", "gradient", "poses", "poses_uneven", "brick",
-                                                            "scaling"])
+                                                            "scaling", "stern"])
     ap.add_argument("--poses", type=int, default=8, help="orientations for --workload poses")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp64_ds"])
     ap.add_argument("--gpus", type=int, default=1)
@@ -850,6 +895,8 @@ def main():
         run_brick(args)
     elif args.workload == "scaling":
         run_scaling(args)
+    elif args.workload == "stern":
+        run_stern(args)
     elif args.workload == "poses":
         run_poses(args)
     elif args.workload == "poses_uneven":

@@ -288,6 +288,27 @@ int pgb_energy(struct pgb_ctx* ctx, const double* x, pgb_energies* e, pgb_energi
 #define PGB_NOALLOC_MAX_CHARGES 65536
 int pgb_energy_noalloc(struct pgb_ctx* ctx, const double* x, pgb_energies* e);
 
+/* Nested interfaces (Section 2 after Eq. 7: Stern layers and solvent-filled
+ * cavities add surfaces, hence block rows).  Places body `id` in the interior
+ * region of the dielectric body `parent` (-1: in the solvent, the default)
+ * and gives its own interior the screening kappa_in (A^-1, default 0; only
+ * dielectric bodies without charges may have one).  Every region -- the
+ * solvent and each dielectric body's interior -- then has its permittivity
+ * (eps_out, or the body's eps_in) and screening, and each row is Green's
+ * representation in the region it belongs to: a dielectric body's interior
+ * row in its interior, its exterior row in the region around it, with the
+ * bodies bounding that region as sources (from inside: dphi; from outside:
+ * (eps_in / eps_region) dphi, the flux condition).  A Stern layer around a
+ * molecule M is a dielectric body S with eps_in = eps_out and kappa_in = 0
+ * that is M's parent; a cavity in M is a dielectric body with parent M.  The
+ * solvation energy of M includes its cavities' share of the reaction
+ * potential.  Surfaces with imposed values stay in the solvent; gradients,
+ * pgb_matvec_transpose, pgb_energy_noalloc and pose batches (batch > 1) are
+ * not available with nesting (PGB_EINVAL).  Products run one treecode pass
+ * per region.  PGB_EINVAL for a bad id, a non-dielectric parent, a cycle, a
+ * negative kappa_in, or a screened interior holding charges. */
+int pgb_set_region(struct pgb_ctx* ctx, int32_t id, int32_t parent, double kappa_in);
+
 /* Treecode parameter autotuner (a library feature; the paper fixes its
  * parameters by hand, Tables 1, 2, 4).  For every candidate (theta, P,
  * leaf_size) of the given lists it builds the tree, times `reps` FP32

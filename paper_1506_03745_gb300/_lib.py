@@ -70,6 +70,7 @@ _SIGS = {
     "pgb_autotune": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_i32, c_vp, c_i32, c_i32, c_dbl, c_dbl,
                              ctypes.POINTER(pgb_params), c_vp]),
     "pgb_set_pose": (c_i32, [c_vp, c_i32, c_vp, c_vp]),
+    "pgb_set_region": (c_i32, [c_vp, c_i32, c_i32, c_dbl]),
     "pgb_tree_build": (c_i32, [c_vp]),
     "pgb_tree_reset": (c_i32, [c_vp]),
     "pgb_tree_stats": (c_i32, [c_vp, ctypes.POINTER(pgb_tree_info)]),
@@ -193,6 +194,10 @@ def pgb_autotune(ctx, thetas, Ps, leaves, reps=5, tol=1e-6, target_rel_err=1e-5)
     _check(ctx, lib().pgb_autotune(ctx, thp, len(th), ppp, len(pp), lvp, len(lv), reps, tol, target_rel_err,
                                    ctypes.byref(ch), rep.ctypes.data_as(c_vp)))
     return {n: getattr(ch, n) for n, _ in pgb_params._fields_}, rep
+
+
+def pgb_set_region(ctx, body_id, parent, kappa_in=0.0):
+    return _check(ctx, lib().pgb_set_region(ctx, body_id, parent, float(kappa_in)))
 
 
 def pgb_set_pose(ctx, body_id, R, t):

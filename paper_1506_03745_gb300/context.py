@@ -23,6 +23,9 @@ def context(bodies, eps_out=80.0, kappa=0.125, stream=None, build=True, **params
                                   b["qxyz"] if has_q else None, b["q"] if has_q else None, b["bc"])
             if b.get("R") is not None:
                 L.pgb_set_pose(ctx, bid, b["R"], b["t"])
+        for bid, b in enumerate(bodies):
+            if b.get("parent", -1) != -1 or b.get("kappa_in", 0.0) != 0.0:
+                L.pgb_set_region(ctx, bid, b.get("parent", -1), b.get("kappa_in", 0.0))
         L.pgb_set_solvent(ctx, eps_out, kappa)
         if build:
             L.pgb_tree_build(ctx)

@@ -521,6 +521,28 @@ int pgb_set_solvent(pgb_ctx* c, double eps_out, double kappa) {
     return PGB_OK;
 }
 
+int pgb_set_region(pgb_ctx* c, int32_t id, int32_t parent, double kappa_in) {
+    if (!c) return PGB_EINVAL;
+    return guard(c, [&]() -> int {
+        const int nb = (int)c->bodies.size();
+        if (id < 0 || id >= nb) fail(PGB_EINVAL, "bad body id");
+        if (parent < -1 || parent >= nb || parent == id) fail(PGB_EINVAL, "bad parent id");
+        if (!(kappa_in >= 0 && isfinite(kappa_in))) fail(PGB_EINVAL, "kappa_in must be >= 0");
+        auto& b = c->bodies[id];
+        if (b.kind != PGB_DIELECTRIC && (parent >= 0 || kappa_in != 0))
+            fail(PGB_EINVAL, "surfaces with an imposed value lie in the solvent");
+        if (parent >= 0 && c->bodies[parent].kind != PGB_DIELECTRIC) fail(PGB_EINVAL, "a parent must be a dielectric body");
+        if (kappa_in != 0 && b.nq > 0) fail(PGB_EINVAL, "a body with charges has an unscreened interior");
+        for (int p = parent, steps = 0; p >= 0; p = c->bodies[p].parent)
+            if (p == id || ++steps > nb) fail(PGB_EINVAL, "nesting would form a cycle");
+        b.parent = parent;
+        b.kappa_in = kappa_in;
+        ++c->config_gen;
+        c->tree_valid = false;
+        return PGB_OK;
+    });
+}
+
 int pgb_set_pose(pgb_ctx* c, int32_t id, const double R[9], const double t[3]) {
     if (!c) return PGB_EINVAL;
     if (id < 0 || id >= (int32_t)c->bodies.size() || !R || !t) {
@@ -715,6 +737,7 @@ int pgb_grad(pgb_ctx* c, const double* x, int32_t precision, double tol, int32_t
         if (!x) fail(PGB_EINVAL, "null x");
         if (!(tol > 0 && tol < 1)) fail(PGB_EINVAL, "tol must be in (0, 1)");
         if (max_iter < 1 || restart < 1 || restart > 256) fail(PGB_EINVAL, "max_iter >= 1 and restart in 1..256");
+        if (nested(c)) fail(PGB_EINVAL, "gradients are not available with nested interfaces");
         pgb_solve_stats st{};
         grad(c, x, precision, tol, max_iter, restart, dq, dbc, dt, &st);
         if (adj) *adj = st;
@@ -731,6 +754,7 @@ int pgb_matvec_transpose(pgb_ctx* c, const double* lam, double* y, int32_t preci
     return guard(c, [&]() -> int {
         if (!lam || !y) fail(PGB_EINVAL, "null vector");
         if (precision != PGB_FP32 && precision != PGB_FP64) fail(PGB_EINVAL, "precision must be PGB_FP32 or PGB_FP64");
+        if (nested(c)) fail(PGB_EINVAL, "the transposed operator is not available with nested interfaces");
         apply_transpose(c, lam, y, precision);
         PGB_CUDA(cudaGetLastError());
         return PGB_OK;
@@ -753,6 +777,7 @@ int pgb_energy_noalloc(pgb_ctx* c, const double* x, pgb_energies* e) {
     if (!c) return PGB_EINVAL;
     return guard(c, [&]() -> int {
         if (!x || !e) fail(PGB_EINVAL, "null argument");
+        if (nested(c)) fail(PGB_EINVAL, "pgb_energy_noalloc does not take nested interfaces (use pgb_energy)");
         energies_noalloc(c, x, e);
         return PGB_OK;
     });

@@ -380,6 +380,7 @@ static pgb_ctx* ensure_union(pgb_ctx* c, const std::vector<pgb_ctx*>& src) {
         if (q->eps_out != c->eps_out || q->kappa != c->kappa)
             fail(PGB_EINVAL, "every context of a pose batch needs the solvent (eps_out, kappa) of the first");
         if (q->bodies.empty()) fail(PGB_ESTATE, "a context of the pose batch has no bodies");
+        if (nested(q)) fail(PGB_EINVAL, "pose batches do not take nested interfaces (use lanes)");
         nbod += q->bodies.size();
     }
     if (nbod > PGB_MAX_BODIES)

@@ -64,25 +64,33 @@ __device__ __forceinline__ double phi_panel(const Geo& g, const BodyDev& bd, con
 // phi_j) with wV_j = sum_k q_k V_L(r_k, j), wK_j = sum_k q_k K_L(r_k, j)
 // (without the 1/4pi), each pair with the rule of phi_panel.  The weights
 // depend on the body's own mesh and charges only, so they hold for every
-// rigid pose.  One warp per panel, lanes over the charges.
+// rigid pose.  With nested interfaces a panel also bounds the interior of the
+// body enclosing it (a cavity's panels bound the molecule's interior): its
+// second pair of weights takes that body's charges.  One warp per panel,
+// lanes over the charges.  w[j] = {wV own, wK own, wV enclosing, wK enclosing}.
 __global__ void k_charge_weights(Geo g, BodyDev bd, Rules r, const double* qxyz, const double* qv,
-                                 const int64_t* qoff, double2* w) {
+                                 const int64_t* qoff, dbl4* w) {
     const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (j >= g.n_pan) return;
     const int b = g.pbody[j];
-    double sv = 0, sk = 0;
-    if (bd.kind[b] == PGB_DIELECTRIC)
-        for (int64_t k = qoff[b] + lane; k < qoff[b + 1]; k += 32) {
+    double sv[2] = {0, 0}, sk[2] = {0, 0};
+    for (int side = 0; side < 2; ++side) {
+        const int src = side == 0 ? (bd.kind[b] == PGB_DIELECTRIC ? b : -1) : bd.parent[b];
+        if (src < 0) continue;
+        for (int64_t k = qoff[src] + lane; k < qoff[src + 1]; k += 32) {
             const double xq[3] = {qxyz[3 * k], qxyz[3 * k + 1], qxyz[3 * k + 2]};
             double vl, kl;
             panel_vk(g, r, xq, j, vl, kl);
-            sv += qv[k] * vl;
-            sk += qv[k] * kl;
+            sv[side] += qv[k] * vl;
+            sk[side] += qv[k] * kl;
         }
-    sv = warp_sum(sv);
-    sk = warp_sum(sk);
-    if (lane == 0) w[j] = make_double2(sv, sk);
+    }
+    for (int side = 0; side < 2; ++side) {
+        sv[side] = warp_sum(sv[side]);
+        sk[side] = warp_sum(sk[side]);
+    }
+    if (lane == 0) w[j] = dbl4{sv[0], sk[0], sv[1], sk[1]};
 }
 
 // phi_reac(r_k) = -K_L(phi) + V_L(dphi) at each charge of a dielectric body
@@ -143,30 +151,43 @@ static void launch_phi_reac(pgb_ctx* c, const Rules& r, const double* x, double*
     PGB_CUDA(cudaGetLastError());
 }
 
-// per-body sums: [0] sum q phi_reac (from phir at the charges, or, when w
-// is given, from the charge weights of the body's panels), [2] sum_j u_j A_j
-// (surfaces).  One block per body.  The Coulomb pair sum is k_coulomb_pairs.
+// per-body sums: [0] sum q phi_reac over the body's own charges (from phir
+// at the charges, or, when w is given, from the charge weights of the
+// body's panels), [1] the part of the enclosing body's sum that this body's
+// panels carry (nested interfaces; added to the enclosing body on the host),
+// [2] sum_j u_j A_j (surfaces).  One block per body.  The Coulomb pair sum is
+// k_coulomb_pairs (which overwrites [1] afterwards; energies() keeps [1]
+// first).
 __global__ void k_body_sums(Geo g, BodyDev bd, const double* qxyz, const double* qv, const int64_t* qoff,
-                            const double* phir, const double2* w, const double* x, double* out) {
+                            const double* phir, const dbl4* w, const double* x, double* out) {
     __shared__ double sh[32];
     const int b = blockIdx.x;
-    double s0 = 0, s2 = 0;
+    double s0 = 0, s1 = 0, s2 = 0;
     const int64_t p0 = bd.pan_off[b], p1 = bd.pan_off[b + 1], N = p1 - p0, o = bd.unk_off[b];
     if (!w) {
         for (int64_t k = qoff[b] + threadIdx.x; k < qoff[b + 1]; k += blockDim.x) s0 += qv[k] * phir[k];
     } else if (bd.kind[b] == PGB_DIELECTRIC) {
+        // the enclosing body's interior sees this body from outside: sign -1
+        // and the flux-scaled density (eps_in(b) / eps_in(parent)) dphi
+        const int pb = bd.parent[b];
+        const double f = pb >= 0 ? bd.eps_ratio[b] / bd.eps_ratio[pb] : 0.0;
         for (int64_t j = p0 + threadIdx.x; j < p1; j += blockDim.x) {
             const int64_t loc = g.perm[j] - p0;
-            s0 += w[j].x * x[o + N + loc] - w[j].y * x[o + loc];
+            const double phi = x[o + loc], dphi = x[o + N + loc];
+            s0 += w[j].x * dphi - w[j].y * phi;
+            if (pb >= 0) s1 -= w[j].z * f * dphi - w[j].w * phi;
         }
         s0 *= 1.0 / PGB_FOUR_PI;
+        s1 *= 1.0 / PGB_FOUR_PI;
     }
     if (bd.kind[b] != PGB_DIELECTRIC)
         for (int64_t j = p0 + threadIdx.x; j < p1; j += blockDim.x) s2 += x[o + (g.perm[j] - p0)] * g.A[j];
     s0 = block_sum(s0, sh);
+    s1 = block_sum(s1, sh);
     s2 = block_sum(s2, sh);
     if (threadIdx.x == 0) {
         out[3 * b] = s0;
+        out[3 * b + 1] = s1;
         out[3 * b + 2] = s2;
     }
 }
@@ -228,7 +249,12 @@ void energies(pgb_ctx* c, const double* x, pgb_energies* e, pgb_energies* per_bo
         }
     }
     k_body_sums<<<nb, 128, 0, s>>>(geo(c), body_dev(c), c->d_qxyz, c->d_qval, qoff, nullptr,
-                                   c->n_q ? (const double2*)c->d_qw.p : nullptr, x, sums);
+                                   c->n_q ? c->d_qw.p : nullptr, x, sums);
+    // the cavities' share of each body's reaction potential, before the
+    // Coulomb reduction reuses slot [1]
+    DBuf<double> inner;
+    inner.resize(nb);
+    PGB_CUDA(cudaMemcpy2DAsync(inner.p, 8, sums.p + 1, 24, 8, nb, cudaMemcpyDeviceToDevice, s));
     {
         DBuf<double> pair;
         pair.resize(std::max<int64_t>(1, c->n_q));
@@ -241,9 +267,13 @@ void energies(pgb_ctx* c, const double* x, pgb_energies* e, pgb_energies* per_bo
         PGB_CUDA(cudaStreamSynchronize(s));
     }
     PGB_LAUNCHED(c, c->n_q ? 3 : 2);
-    std::vector<double> h(3 * nb);
+    std::vector<double> h(3 * nb), hin(nb);
     PGB_CUDA(cudaMemcpyAsync(h.data(), sums.p, 8 * 3 * nb, cudaMemcpyDeviceToHost, s));
+    PGB_CUDA(cudaMemcpyAsync(hin.data(), inner.p, 8 * nb, cudaMemcpyDeviceToHost, s));
     PGB_CUDA(cudaStreamSynchronize(s));
+    // each body's reaction-potential sum includes what its cavities carry
+    for (int b = 0; b < nb; ++b)
+        if (c->bodies[b].parent >= 0) h[3 * c->bodies[b].parent] += hin[b];
     const double U = energy_unit_kcal();
     pgb_energies tot{0, 0, 0, 0};
     for (int b = 0; b < nb; ++b) {

@@ -161,6 +161,130 @@ __global__ void k_assemble(Geo g, BodyDev bd, Parts u, const real* __restrict__ 
     }
 }
 
+// ---------------------------------------------------------------- nested interfaces
+// With nested interfaces every row is its body's jump term minus the
+// representation sum of the region the row belongs to (the interior row of a
+// dielectric body: its interior; the exterior row, or a surface's row: the
+// region around it), and each region's sum runs as its own treecode pass.
+// Rows start from the jump terms (modes 0 and 2; mode 1: minus the imposed
+// jump).
+__global__ void k_rows_init(Geo g, BodyDev bd, const double* x, int mode, double* y) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= g.n_pan) return;
+    const int b = g.pbody[i];
+    const int64_t loc = g.perm[i] - bd.pan_off[b];
+    const int64_t N = bd.pan_off[b + 1] - bd.pan_off[b];
+    const int64_t o = bd.unk_off[b];
+    const int kind = bd.kind[b];
+    if (kind == PGB_DIELECTRIC) {
+        const double v = mode == 1 ? 0.0 : 0.5 * x[o + loc];
+        y[o + loc] = v;
+        y[o + N + loc] = v;
+    } else if (kind == PGB_SET_CHARGE) {
+        y[o + loc] = mode == 1 ? 0.0 : 0.5 * x[o + loc];
+    } else {
+        y[o + loc] = mode == 0 ? 0.0 : (mode == 2 ? 0.5 * bd.bc[b] : -0.5 * bd.bc[b]);
+    }
+}
+
+// Source terms of one region's pass: every body on the region's boundary
+// with the densities of its side of the interface and the side's sign folded
+// in, so that the pass sums s [V psi - K phi] (the Yukawa slots, at the
+// region's screening; kappa = 0 is Laplace); all other bodies are zero.
+//   dielectric: phi, psi = fac dphi (fac = 1 inside, eps_in / eps_R outside)
+//   imposed potential: psi = u, phi = phi0 (known); imposed charge: phi = u,
+//   psi = -sigma0 / eps_R (known).   mode as k_src_prep (x unused for 1).
+template <typename real>
+__global__ void k_src_region(Geo g, BodyDev bd, RegionDev rd, const double* __restrict__ x, int mode,
+                             const typename V4<real>::t* __restrict__ yrel, typename V4<real>::t* __restrict__ src,
+                             real* __restrict__ dens) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= g.n_pan) return;
+    const int b = g.pbody[i];
+    const int sg = rd.sign[b];
+    double psi = 0, phi = 0;
+    if (sg != 0) {
+        const int64_t loc = g.perm[i] - bd.pan_off[b];
+        const int64_t N = bd.pan_off[b + 1] - bd.pan_off[b];
+        const int64_t o = bd.unk_off[b];
+        const int kind = bd.kind[b];
+        if (kind == PGB_DIELECTRIC) {
+            if (mode != 1) {
+                phi = x[o + loc];
+                psi = rd.fac[b] * x[o + N + loc];
+            }
+        } else if (kind == PGB_SET_POTENTIAL) {
+            if (mode != 1) psi = x[o + loc];
+            if (mode != 0) phi = bd.bc[b];
+        } else {
+            if (mode != 1) phi = x[o + loc];
+            if (mode != 0) psi = rd.psi_known[b];
+        }
+        psi *= sg;
+        phi *= sg;
+    }
+    const real rY = (real)psi, rp = (real)phi;
+    dens[3 * i] = 0;
+    dens[3 * i + 1] = rY;
+    dens[3 * i + 2] = rp;
+    const real nx = (real)g.n[3 * i], ny = (real)g.n[3 * i + 1], nz = (real)g.n[3 * i + 2];
+    for (int m = 0; m < g.K; ++m) {
+        const int64_t p = i * g.K + m;
+        const real w = (real)g.w[p];
+        typename V4<real>::t A = yrel[p], B;
+        const real wp = w * rp;
+        A.w = 0;
+        B.x = wp * nx;
+        B.y = wp * ny;
+        B.z = wp * nz;
+        B.w = w * rY;
+        src[2 * p] = A;
+        src[2 * p + 1] = B;
+    }
+}
+
+// One region's sums into its rows: the pass's item partials (Yukawa slots)
+// plus the region's near-field corrections, subtracted from the row of the
+// target's side (added for mode 1, the right-hand side of imposed terms).
+template <typename real>
+__global__ void k_assemble_region(Geo g, BodyDev bd, RegionDev rd, Parts u, const real* __restrict__ dens,
+                                  const int64_t* __restrict__ coff, const int32_t* __restrict__ cj,
+                                  const typename V4<real>::t* __restrict__ cval, const int64_t* __restrict__ xoff,
+                                  const int32_t* __restrict__ xj, const typename V4<real>::t* __restrict__ xval,
+                                  int mode, double* __restrict__ y) {
+    using v4 = typename V4<real>::t;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= g.n_pan) return;
+    const int b = g.pbody[i];
+    const int sg = rd.sign[b];
+    if (sg == 0) return;
+    const int gi = u.pan_group[i];
+    const int lane = (int)(i - u.gstart[gi]);
+    double sY = 0;
+    for (int64_t it = u.pitem_off[gi]; it < u.pitem_off[gi + 1]; ++it) sY += u.Up[64 * it + 32 + lane];
+    for (int64_t it = u.fitem_off[gi]; it < u.fitem_off[gi + 1]; ++it) sY += u.Uf[64 * it + 32 + lane];
+    double U = sY * (1.0 / PGB_FOUR_PI);
+    real cY = 0, eY = 0;
+    for (int64_t e = coff[i]; e < coff[i + 1]; ++e) {
+        const int64_t j = cj[e];
+        const v4 d = cval[e];
+        if (sizeof(real) == 4) kadd(cY, eY, d.z * dens[3 * j + 1] - d.w * dens[3 * j + 2]);
+        else cY += d.z * dens[3 * j + 1] - d.w * dens[3 * j + 2];
+    }
+    for (int64_t e = xoff[i]; e < xoff[i + 1]; ++e) {
+        const int64_t j = xj[e];
+        const v4 d = xval[e];
+        if (sizeof(real) == 4) kadd(cY, eY, d.z * dens[3 * j + 1] - d.w * dens[3 * j + 2]);
+        else cY += d.z * dens[3 * j + 1] - d.w * dens[3 * j + 2];
+    }
+    U += (double)cY + (double)eY;
+    const int64_t loc = g.perm[i] - bd.pan_off[b];
+    const int64_t N = bd.pan_off[b + 1] - bd.pan_off[b];
+    const int64_t o = bd.unk_off[b];
+    const int64_t r = (bd.kind[b] == PGB_DIELECTRIC && sg < 0) ? o + N + loc : o + loc;
+    y[r] += mode == 1 ? U : -U;
+}
+
 __global__ void k_f32_to_f64(const float* a, double* b, int64_t n) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) b[i] = a[i];
@@ -325,6 +449,60 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
     } else {
         c->d_src64.resize(2 * nsrc);
         c->d_mom64.resize((size_t)c->n_nodes * 2 * T);
+    }
+    if (nested(c)) {
+        // one treecode pass per region: rows from the jump terms, then each
+        // region's sum subtracted from the rows on its boundary
+        if (known_mask) fail(PGB_EINVAL, "imposed-term selection is not available with nested interfaces");
+        k_rows_init<<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, x, mode, y);
+        PGB_LAUNCHED(c, 1);
+        for (int b = 0; b < PGB_MAX_BODIES; ++b) ev.lap_body[b] = 0;
+        for (const auto& reg : c->regions) {
+            const RegionDev& rd = reg->dev;
+            ev.kappa = rd.kappa;
+            if (ev.p2p_work)  // persistent launches take items from counters: fresh ones per pass
+                PGB_CUDA(cudaMemsetAsync(c->d_work.p, 0, 16, s));
+            ev.all_active = 1;
+            for (size_t b = 0; b < c->bodies.size(); ++b) {
+                ev.src_active[b] = up.src_active[b] = rd.sign[b] != 0 && !c->body_off[b];
+                ev.all_active &= ev.src_active[b];
+            }
+            {
+                StageTimer tm(c, PGB_STAGE_SOURCES + (f32 ? 0 : PGB_STAGE_FP64));
+                if (f32)
+                    k_src_region<float><<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, rd, x, mode, c->d_y32, c->d_src32,
+                                                                             (float*)dens.p);
+                else
+                    k_src_region<double><<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, rd, x, mode, c->d_y64,
+                                                                              c->d_src64, dens.p);
+                PGB_CUDA(cudaGetLastError());
+                PGB_LAUNCHED(c, 1);
+            }
+            for (int stage : {PGB_STAGE_UPWARD, PGB_STAGE_P2P, PGB_STAGE_M2P}) {
+                StageTimer tm(c, stage + (f32 ? 0 : PGB_STAGE_FP64));
+                if (f32) treecode_launch_f32(stage, P, up, c->level_begin, ev, c->d_src32, c->d_x32, c->d_mom32, s);
+                else if (precision == PGB_FP64_DS && stage != PGB_STAGE_UPWARD)
+                    treecode_launch_ds(stage, P, ev, c->d_src64, c->d_x64, c->d_mom64, s);
+                else treecode_launch_f64(stage, P, up, c->level_begin, ev, c->d_src64, c->d_x64, c->d_mom64, s);
+                PGB_CUDA(cudaGetLastError());
+                PGB_LAUNCHED(c, stage == PGB_STAGE_UPWARD ? (int64_t)c->level_begin.size() - 2 : 1);
+            }
+            {
+                StageTimer tm(c, PGB_STAGE_ASSEMBLE + (f32 ? 0 : PGB_STAGE_FP64));
+                Parts u{c->d_pan_group, c->d_group_start, c->d_pitem_off, c->d_fitem_off, Up, Uf};
+                if (f32)
+                    k_assemble_region<float><<<nblk(c->n_pan, 128), 128, 0, s>>>(
+                        g, bd, rd, u, (const float*)dens.p, reg->corr_off, reg->corr_j, reg->corr_val32,
+                        reg->xcorr_off, reg->xcorr_j, reg->xcorr_val32, mode, y);
+                else
+                    k_assemble_region<double><<<nblk(c->n_pan, 128), 128, 0, s>>>(
+                        g, bd, rd, u, dens.p, reg->corr_off, reg->corr_j, reg->corr_val, reg->xcorr_off, reg->xcorr_j,
+                        reg->xcorr_val, mode, y);
+                PGB_CUDA(cudaGetLastError());
+                PGB_LAUNCHED(c, 1);
+            }
+        }
+        return;
     }
     {
         StageTimer tm(c, PGB_STAGE_SOURCES + (f32 ? 0 : PGB_STAGE_FP64));

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -112,6 +113,10 @@ struct Body {
     // independent problem the body belongs to: bodies of different problems
     // do not interact (a batch of poses solved as one block-diagonal system)
     int prob = 0;
+    // nesting: the body lies in the interior region of body `parent` (-1: in
+    // the solvent); kappa_in screens its own interior (dielectric bodies)
+    int parent = -1;
+    double kappa_in = 0.0;
 };
 
 // Device-side view of the problem passed by value to kernels.
@@ -137,7 +142,20 @@ struct BodyDev {  // per-body constants for kernels
     double bc[PGB_MAX_BODIES];
     int64_t pan_off[PGB_MAX_BODIES + 1];
     int64_t unk_off[PGB_MAX_BODIES];
+    int parent[PGB_MAX_BODIES];        // enclosing body, -1: the solvent
     int n_bodies;
+};
+
+// One region of a nested system for a treecode pass: the bodies bounding it
+// (sign +1: the region is the body's interior, -1: its exterior, 0: not on
+// the boundary), the factor of each body's dphi on the region's side
+// (eps_in(b) / eps_R from outside, 1 from inside), the imposed normal
+// derivative -sigma0 / eps_R of charged surfaces, and its screening.
+struct RegionDev {
+    int sign[PGB_MAX_BODIES];
+    double fac[PGB_MAX_BODIES];
+    double psi_known[PGB_MAX_BODIES];
+    double kappa;
 };
 
 }  // namespace pgb
@@ -240,7 +258,8 @@ struct pgb_ctx {
     pgb::DBuf<float> d_mom32;            // 2*T per node
     pgb::DBuf<double> d_mom64;
     pgb::DBuf<double> d_phi_part;        // chunk partial sums of phi_reac (few charges)
-    pgb::DBuf<double2> d_qw;             // charge weights (wV, wK) per sorted panel (energies)
+    pgb::DBuf<pgb::dbl4> d_qw;           // charge weights per sorted panel (energies): own charges
+                                         // (wV, wK), then the enclosing body's (wV, wK)
     uint64_t qw_key[4] = {~0ull, ~0ull, 0, 0};  // tree_gen, config_gen, K, K_near they were made for
     pgb::DBuf<double> d_Up[2], d_Uf[2];        // P2P / M2P partial sums: 64 per work item (32 L, then 32 Y)
     pgb::DBuf<double> d_xtmp, d_ytmp;    // FP64 staging for FP32 matvec API
@@ -292,6 +311,17 @@ struct pgb_ctx {
     // bodies left out of the products (1: its sources and rows are not
     // computed; the problems that no longer iterate in a lockstep solve)
     char body_off[PGB_MAX_BODIES] = {0};
+    // nested interfaces (pgb_set_region): regions and their near-field
+    // corrections, one treecode pass per region in every product
+    struct Region {
+        pgb::RegionDev dev;
+        int64_t n_corr = 0, n_xcorr = 0;
+        pgb::DBuf<int64_t> corr_off, xcorr_off;
+        pgb::DBuf<int32_t> corr_j, xcorr_j;
+        pgb::DBuf<pgb::dbl4> corr_val, xcorr_val;
+        pgb::DBuf<float4> corr_val32, xcorr_val32;
+    };
+    std::vector<std::unique_ptr<Region>> regions;
     pgb_ctx* union_ctx = nullptr;
     std::vector<pgb_ctx*> union_src;
     std::vector<uint64_t> union_gen;
@@ -308,6 +338,13 @@ struct pgb_ctx {
 };
 
 namespace pgb {
+// Whether the context holds nested interfaces (a body inside another, or a
+// screened interior): products then run one treecode pass per region.
+inline bool nested(const pgb_ctx* c) {
+    for (const auto& b : c->bodies)
+        if (b.parent >= 0 || b.kappa_in != 0.0) return true;
+    return false;
+}
 // CUDA-event interval on the context stream around one stage (no-op when
 // timing is off).
 struct StageTimer {

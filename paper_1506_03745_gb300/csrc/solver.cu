@@ -16,6 +16,9 @@ static inline int nblk(int64_t n, int t) { return (int)std::max<int64_t>(1, (n +
 
 // Coulomb rows (first line of Eq. 5, with its 1/eps_in kept -- reading of
 // Eq. 6/7): (1/eps_in) sum_k q_k / (4 pi |c_i - r_k|) over the body's charges.
+// With nested interfaces the outer row of a body inside another (a cavity in
+// a molecule) takes the enclosing body's charges the same way (added to the
+// row, which may hold imposed terms already).
 __global__ void k_coulomb_rows(Geo g, BodyDev bd, const double* qxyz, const double* qv, const int64_t* qoff,
                                const double* eps_in, double* b) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -23,13 +26,19 @@ __global__ void k_coulomb_rows(Geo g, BodyDev bd, const double* qxyz, const doub
     const int bi = g.pbody[i];
     if (bd.kind[bi] != PGB_DIELECTRIC) return;
     const double x = g.c[3 * i], y = g.c[3 * i + 1], z = g.c[3 * i + 2];
-    double s = 0;
-    for (int64_t k = qoff[bi]; k < qoff[bi + 1]; ++k) {
-        double dx = x - qxyz[3 * k], dy = y - qxyz[3 * k + 1], dz = z - qxyz[3 * k + 2];
-        s += qv[k] / sqrt(dx * dx + dy * dy + dz * dz);
-    }
     const int64_t loc = g.perm[i] - bd.pan_off[bi];
-    b[bd.unk_off[bi] + loc] = s / (PGB_FOUR_PI * eps_in[bi]);
+    const int64_t N = bd.pan_off[bi + 1] - bd.pan_off[bi];
+    for (int side = 0; side < 2; ++side) {
+        const int src = side == 0 ? bi : bd.parent[bi];
+        if (src < 0) continue;
+        double s = 0;
+        for (int64_t k = qoff[src]; k < qoff[src + 1]; ++k) {
+            double dx = x - qxyz[3 * k], dy = y - qxyz[3 * k + 1], dz = z - qxyz[3 * k + 2];
+            s += qv[k] / sqrt(dx * dx + dy * dy + dz * dz);
+        }
+        if (side == 0) b[bd.unk_off[bi] + loc] = s / (PGB_FOUR_PI * eps_in[bi]);
+        else b[bd.unk_off[bi] + N + loc] += s / (PGB_FOUR_PI * eps_in[src]);
+    }
 }
 
 // b = 0 except the Coulomb rows of the molecules.

@@ -1184,7 +1184,8 @@ struct CorrArgs {
     const int32_t *nchild, *child, *nstart, *nend;
     const double *clo, *chi, *a8, *C, *A;
     int n_bodies;
-    int prob[PGB_MAX_BODIES];  // problem of each body (no entries across problems)
+    int prob[PGB_MAX_BODIES];    // problem of each body (no entries across problems)
+    int in_set[PGB_MAX_BODIES];  // bodies taking part (targets and sources; a region's boundary)
 };
 
 // candidates j of target i: |c_i - c_j|^2 < 8 A_j (|x - c_j| < 2 L_j), or j == i;
@@ -1200,8 +1201,8 @@ __global__ void k_corr_find(CorrArgs a, int64_t n, bool fill, bool cross, const 
     int32_t stack[PGB_LIST_STACK];
     int64_t k = 0, w = fill ? off[i] : 0;
     const int ib = pbody[i];
-    for (int b = 0; b < a.n_bodies; ++b) {
-        if ((b != ib) != cross || a.prob[b] != a.prob[ib]) continue;
+    for (int b = 0; b < a.n_bodies && a.in_set[ib]; ++b) {
+        if ((b != ib) != cross || a.prob[b] != a.prob[ib] || !a.in_set[b]) continue;
         int sp = 0;
         stack[sp++] = b;
         while (sp > 0) {
@@ -1416,6 +1417,7 @@ BodyDev body_dev(const pgb_ctx* c) {
         b.bc[i] = bb.bc;
         b.pan_off[i] = bb.pan_off;
         b.unk_off[i] = bb.unk_off;
+        b.parent[i] = bb.parent;
     }
     b.pan_off[b.n_bodies] = c->n_pan;
     return b;
@@ -1429,15 +1431,20 @@ __global__ void k_dbl4_to_f4(const dbl4* a, float4* b, int64_t n) {
     }
 }
 
+// in_set (host, per body; nullptr: all bodies) restricts targets and sources
+// to a region's boundary; kappa is the screening of the Yukawa values.
 static void build_corr_part(pgb_ctx* c, bool cross, DBuf<int64_t>& off, DBuf<int32_t>& cj, DBuf<dbl4>& val,
-                            DBuf<float4>& val32, int64_t& count) {
+                            DBuf<float4>& val32, int64_t& count, const int* in_set, double kappa) {
     cudaStream_t s = c->stream;
     int64_t n = c->n_pan;
     CorrArgs a;
     a.nchild = c->d_node_nchild; a.child = c->d_node_child; a.nstart = c->d_node_start; a.nend = c->d_node_end;
     a.clo = c->d_node_clo; a.chi = c->d_node_chi; a.a8 = c->d_node_a8; a.C = c->d_c; a.A = c->d_A;
     a.n_bodies = (int)c->bodies.size();
-    for (int b = 0; b < a.n_bodies; ++b) a.prob[b] = c->bodies[b].prob;
+    for (int b = 0; b < a.n_bodies; ++b) {
+        a.prob[b] = c->bodies[b].prob;
+        a.in_set[b] = in_set ? in_set[b] : 1;
+    }
     DBuf<int64_t> cnt;
     cnt.resize(n);
     off.resize(n + 1);
@@ -1465,10 +1472,10 @@ static void build_corr_part(pgb_ctx* c, bool cross, DBuf<int64_t>& off, DBuf<int
         c->d_yfine.resize(3 * n * r.Kn);
         k_fine_nodes<<<nblk(n * r.Kn, 256), 256, 0, s>>>(n, c->d_v, c->d_c, r, c->d_yfine);
         k_corr_values<<<nblk(tot, 128), 128, 0, s>>>(n, tot, off, cj, c->d_yfine, c->d_v, c->d_c, c->d_n, c->d_A, c->d_y,
-                                                     c->d_w, c->d_pbody, body_dev(c), r, c->kappa, val);
+                                                     c->d_w, c->d_pbody, body_dev(c), r, kappa, val);
         if (!cross)
             k_corr_self<<<nblk(n, 128), 128, 0, s>>>(n, off, cj, c->d_v, c->d_c, c->d_pbody, body_dev(c), r,
-                                                     c->kappa, val);
+                                                     kappa, val);
     }
     val32.resize(std::max<int64_t>(tot, 1));
     if (tot) k_dbl4_to_f4<<<nblk(tot, 256), 256, 0, s>>>(val, val32, tot);
@@ -1477,9 +1484,48 @@ static void build_corr_part(pgb_ctx* c, bool cross, DBuf<int64_t>& off, DBuf<int
     PGB_LAUNCHED(c, tot ? 5 : 2);
 }
 
+// Regions of a nested system (the solvent, then the interior of every
+// dielectric body) with the bodies bounding each, and each region's
+// near-field corrections at its own screening, among its boundary bodies.
+static void build_regions(pgb_ctx* c) {
+    const int nb = (int)c->bodies.size();
+    c->regions.clear();
+    for (int R = 0; R <= nb; ++R) {
+        if (R > 0 && c->bodies[R - 1].kind != PGB_DIELECTRIC) continue;
+        auto reg = std::make_unique<pgb_ctx::Region>();
+        RegionDev& d = reg->dev;
+        memset(&d, 0, sizeof(d));
+        const double epsR = R == 0 ? c->eps_out : c->bodies[R - 1].eps_in;
+        d.kappa = R == 0 ? c->kappa : c->bodies[R - 1].kappa_in;
+        int in_set[PGB_MAX_BODIES] = {0};
+        bool any = false;
+        for (int b = 0; b < nb; ++b) {
+            const auto& bb = c->bodies[b];
+            const int outer = bb.parent < 0 ? 0 : bb.parent + 1;
+            const int inner = bb.kind == PGB_DIELECTRIC ? b + 1 : -1;
+            const int sg = inner == R ? 1 : (outer == R ? -1 : 0);
+            d.sign[b] = sg;
+            if (!sg) continue;
+            any = true;
+            in_set[b] = 1;
+            d.fac[b] = sg > 0 ? 1.0 : (bb.kind == PGB_DIELECTRIC ? bb.eps_in / epsR : 1.0);
+            d.psi_known[b] = bb.kind == PGB_SET_CHARGE ? -bb.bc / epsR : 0.0;
+        }
+        if (!any) continue;
+        build_corr_part(c, false, reg->corr_off, reg->corr_j, reg->corr_val, reg->corr_val32, reg->n_corr, in_set,
+                        d.kappa);
+        build_corr_part(c, true, reg->xcorr_off, reg->xcorr_j, reg->xcorr_val, reg->xcorr_val32, reg->n_xcorr, in_set,
+                        d.kappa);
+        c->regions.push_back(std::move(reg));
+    }
+}
+
 void build_corrections(pgb_ctx* c) {
+    if (nested(c)) build_regions(c);
+    else c->regions.clear();
     if (!c->intra_valid) {
-        build_corr_part(c, false, c->d_corr_off, c->d_corr_j, c->d_corr_val, c->d_corr_val32, c->n_corr);
+        build_corr_part(c, false, c->d_corr_off, c->d_corr_j, c->d_corr_val, c->d_corr_val32, c->n_corr, nullptr,
+                        c->kappa);
         c->intra_valid = true;
     }
     // cross-body entries: none when every pair of bodies of one problem is
@@ -1507,7 +1553,8 @@ void build_corrections(pgb_ctx* c) {
             }
     }
     if (reach) {
-        build_corr_part(c, true, c->d_xcorr_off, c->d_xcorr_j, c->d_xcorr_val, c->d_xcorr_val32, c->n_xcorr);
+        build_corr_part(c, true, c->d_xcorr_off, c->d_xcorr_j, c->d_xcorr_val, c->d_xcorr_val32, c->n_xcorr, nullptr,
+                        c->kappa);
     } else {
         c->d_xcorr_off.resize(c->n_pan + 1);
         PGB_CUDA(cudaMemsetAsync(c->d_xcorr_off.p, 0, 8 * (c->n_pan + 1), c->stream));
