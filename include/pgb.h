@@ -119,6 +119,8 @@ typedef struct pgb_tree_info {
     int64_t m2p_pairs;         /* target x node M2P evaluations per matvec */
     int64_t m2p_laplace_pairs;
     int64_t n_corrections;     /* near-field correction entries */
+    int64_t n_p2p_items;       /* P2P work items (one block each) per matvec */
+    int64_t n_m2p_items;       /* M2P work items */
 } pgb_tree_info;
 
 /* Device time per stage of the hot path, accumulated with CUDA events on

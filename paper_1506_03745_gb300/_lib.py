@@ -37,7 +37,7 @@ class pgb_energies(ctypes.Structure):
 class pgb_tree_info(ctypes.Structure):
     _fields_ = [(n, c_i64) for n in ("n_panels", "n_unknowns", "n_nodes", "n_leaves", "n_groups", "n_near",
                                      "n_far", "p2p_pairs", "p2p_laplace_pairs", "m2p_pairs", "m2p_laplace_pairs",
-                                     "n_corrections")]
+                                     "n_corrections", "n_p2p_items", "n_m2p_items")]
 
 
 N_STAGES = 14

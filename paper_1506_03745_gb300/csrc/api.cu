@@ -606,6 +606,8 @@ int pgb_tree_stats(pgb_ctx* c, pgb_tree_info* info) {
     info->m2p_pairs = c->m2p_pairs;
     info->m2p_laplace_pairs = c->m2p_lap;
     info->n_corrections = c->n_corr + c->n_xcorr;
+    info->n_p2p_items = c->n_pitems;
+    info->n_m2p_items = c->n_fitems;
     return PGB_OK;
 }
 
