@@ -77,11 +77,12 @@ typedef struct pgb_params {
                              once per tree as a CUDA graph and replayed; 0: plain launches */
     int32_t lanes;        /* pgb_solve_batch: poses in flight at once, 1..16 (0 = 4); each lane is a copy
                              of the context with its own CUDA stream and host thread, kept between calls */
-    int32_t overlap;      /* PGB_FP32_REFINE: 1 (default) starts the FP64 product of the outer residual on
-                             a side stream at the inner iterate whose residual is 1e-2 of its right-hand
-                             side (1e4 tol if smaller) and finishes the residual with the FP32 product of
-                             the remaining change, so the FP64 work overlaps the FP32 iterations; 0: the
-                             FP64 product of the final iterate, after the inner solve */
+    int32_t overlap;      /* PGB_FP32_REFINE: 1 starts the FP64 product of the outer residual on a side
+                             stream at the inner iterate whose residual is 1e-2 of its right-hand side
+                             (1e4 tol if smaller) and finishes the residual with the FP32 product of the
+                             remaining change, so the FP64 work overlaps the FP32 iterations (it pays
+                             with residual = 0, whose kernels use the FP64 pipe); 0 (default): the
+                             residual's product of the final iterate, after the inner solve */
     int32_t batch;        /* pgb_solve_batch / pgb_solve_poses: poses solved together as one
                              block-diagonal system, 1..64 (0 = 1); > 1 replaces the lanes: every stage
                              is one launch over the batch and GMRES runs in lockstep with per-pose

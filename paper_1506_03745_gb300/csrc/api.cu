@@ -342,7 +342,7 @@ int pgb_default_params(pgb_params* p) {
     p->precond = 0;
     p->graphs = 1;
     p->lanes = 4;
-    p->overlap = 1;
+    p->overlap = 0;
     p->batch = 1;
     p->residual = 1;
     return PGB_OK;
