@@ -653,7 +653,7 @@ def run_poses_uneven(args):
     batch = PARAMS["batch"] if PARAMS["batch"] > 1 else 8
     sizes = np.geomspace(5000, 40000, 8)
     srf = sphere_body()
-    ctxs, verts, npan, mols = [], [], [], []
+    verts, npan, mols = [], [], []
     for k, N in enumerate(sizes):
         nu = int(round(math.sqrt(N / 20)))
         seed = 300 + k
@@ -661,12 +661,30 @@ def run_poses_uneven(args):
         coeffs = synth.star_coefficients(seed)
         xyz, q = synth.interior_charges(seed, 900, v, f,
                                         radius_fn=lambda d, c=coeffs: synth.star_radius(d, c, 15.0))
-        mol = dict(kind="dielectric", verts=v, tris=f, eps_in=4.0, qxyz=xyz, q=q, bc=0.0)
-        prm = dict(PARAMS, batch=batch) if k == 0 else dict(PARAMS, batch=1)
-        ctxs.append(gpu_context([mol, srf], **prm))
-        mols.append(mol)
+        mols.append(dict(kind="dielectric", verts=v, tris=f, eps_in=4.0, qxyz=xyz, q=q, bc=0.0))
         verts.append(v)
         npan.append(len(f))
+    # treecode parameters and work-item sizes by the autotuner, on the first
+    # molecule 8 A from the sphere: the fastest FP32 solve whose total energy
+    # is within 1e-4 of the most accurate candidate's (theta 0.5, P 7)
+    prm = dict(PARAMS)
+    tune = None
+    if not args.no_autotune:
+        m0 = dict(mols[0], R=np.eye(3), t=np.array([place_for_gap(verts[0], np.eye(3), 40.0, 8.0), 0.0, 0.0]))
+        ct = gpu_context([m0, srf], **PARAMS)
+        thetas, Ps, leaves = [0.5, 0.6, 0.7], [5, 6, 7], [32, 64]
+        (chosen, rep), t_ms = _timed(lambda: pgb.pgb_autotune(ct, thetas, Ps, leaves, reps=3, tol=1e-5,
+                                                              target_rel_err=1e-4))
+        pgb.pgb_destroy(ct)
+        for k in ("theta", "P", "leaf_size", "p2p_item", "m2p_item"):
+            prm[k] = chosen[k]
+        tune = {"chosen": {k: prm[k] for k in ("theta", "P", "leaf_size", "p2p_item", "m2p_item")},
+                "candidates": [{"theta": t_, "P": p_, "leaf": l_, "matvec_ms": rep[i, 0], "solve_ms": rep[i, 1],
+                                "energy_rel_diff": rep[i, 2]}
+                               for i, (t_, p_, l_) in enumerate((t_, p_, l_) for t_ in thetas for p_ in Ps
+                                                                 for l_ in leaves)],
+                "ms": t_ms}
+    ctxs = [gpu_context([mols[k], srf], **dict(prm, batch=batch if k == 0 else 1)) for k in range(8)]
     Rs = synth.random_rotations(17, args.poses)
     R, t, pc = [], [], []
     for Ro in Rs:
@@ -685,7 +703,7 @@ def run_poses_uneven(args):
     tim = pgb.pgb_timing(ctxs[0], False, read=True)
     # the same poses molecule by molecule with concurrent lanes (molecule 0
     # needs a context of its own without the batch parameter)
-    c0 = gpu_context([mols[0], srf], **dict(PARAMS, batch=1))
+    c0 = gpu_context([mols[0], srf], **dict(prm, batch=1))
     F_l = np.zeros_like(F)
     ms_l = 0.0
     for k in range(8):
@@ -708,7 +726,7 @@ def run_poses_uneven(args):
                       "lanes_4_per_molecule": {"ms": ms_l, "poses_per_s": B / (ms_l / 1e3),
                                                "max_rel_diff_total_energy": float(np.max(np.abs(F_l[:, 3] - F[:, 3]) /
                                                                                          np.abs(F[:, 3])))},
-                      "molecule_panels": npan, "mean_iterations": float(its.mean()),
+                      "molecule_panels": npan, "mean_iterations": float(its.mean()), "autotune": tune,
                       "iterations_range": [int(its.min()), int(its.max())], "status": code,
                       "energy_rel_err_vs_fp64_first_chunk_max": float(err.max()),
                       "stage_ms_per_pose": {k: v[0] / B for k, v in tim.items() if k != "kernel_launches" and v[0]},
@@ -896,6 +914,7 @@ def main():
     ap.add_argument("--overlap", type=int, default=None, help="0: FP64 residual after the inner solve")
     ap.add_argument("--batch", type=int, default=None, help="poses per block-diagonal union solve (pose workloads)")
     ap.add_argument("--residual", type=int, default=None, help="0: native FP64 outer residual, 1: double-single")
+    ap.add_argument("--no-autotune", action="store_true", help="pose sweep over 8 molecules: library parameters")
     args = ap.parse_args()
     for k, v in (("leaf_size", args.leaf), ("P", args.P), ("theta", args.theta), ("p2p_item", args.p2p_item),
                  ("m2p_item", args.m2p_item), ("precond", args.precond),
