@@ -418,6 +418,11 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
     }
     ev.all_active = 1;
     for (size_t b = 0; b < c->bodies.size(); ++b) ev.all_active &= ev.src_active[b];
+    // rows of bodies left out of the product (a lockstep batch's finished
+    // problems) are not computed
+    ev.tgt_mask = ~0ull;
+    for (size_t b = 0; b < c->bodies.size(); ++b)
+        if (c->body_off[b]) ev.tgt_mask &= ~(1ull << b);
     ev.near4 = c->d_near4;
     ev.far4 = c->d_far4;
     ev.tile_off = c->d_tile_off;
@@ -463,9 +468,11 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
             if (ev.p2p_work)  // persistent launches take items from counters: fresh ones per pass
                 PGB_CUDA(cudaMemsetAsync(c->d_work.p, 0, 16, s));
             ev.all_active = 1;
+            ev.tgt_mask = 0;
             for (size_t b = 0; b < c->bodies.size(); ++b) {
                 ev.src_active[b] = up.src_active[b] = rd.sign[b] != 0 && !c->body_off[b];
                 ev.all_active &= ev.src_active[b];
+                if (ev.src_active[b]) ev.tgt_mask |= 1ull << b;  // only the region's own rows
             }
             {
                 StageTimer tm(c, PGB_STAGE_SOURCES + (f32 ? 0 : PGB_STAGE_FP64));
