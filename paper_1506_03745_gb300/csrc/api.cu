@@ -224,7 +224,8 @@ static void destroy_lanes(pgb_ctx* c) {
 static bool same_params(const pgb_params& a, const pgb_params& b) {
     return a.K == b.K && a.K_near == b.K_near && a.n_edge == b.n_edge && a.P == b.P && a.theta == b.theta &&
            a.leaf_size == b.leaf_size && a.group_size == b.group_size && a.p2p_item == b.p2p_item &&
-           a.m2p_item == b.m2p_item && a.precond == b.precond && a.graphs == b.graphs && a.overlap == b.overlap;
+           a.m2p_item == b.m2p_item && a.precond == b.precond && a.graphs == b.graphs && a.overlap == b.overlap &&
+           a.residual == b.residual;
 }
 
 // Lane contexts: copies of c (bodies, solvent, parameters) with their own

@@ -370,7 +370,8 @@ static pgb_ctx* ensure_union(pgb_ctx* c, const std::vector<pgb_ctx*>& src) {
         const pgb_params &a = c->union_ctx->p, &b = c->p;
         ok = ok && a.K == b.K && a.K_near == b.K_near && a.n_edge == b.n_edge && a.P == b.P && a.theta == b.theta &&
              a.leaf_size == b.leaf_size && a.p2p_item == b.p2p_item && a.m2p_item == b.m2p_item &&
-             a.precond == b.precond && a.graphs == b.graphs && c->union_ctx->eps_out == c->eps_out &&
+             a.precond == b.precond && a.graphs == b.graphs && a.residual == b.residual &&
+             c->union_ctx->eps_out == c->eps_out &&
              c->union_ctx->kappa == c->kappa;
     }
     if (ok) return c->union_ctx;
