@@ -640,7 +640,8 @@ def run_poses_uneven(args):
     surfaces r0 = 15 A from the molecule generator, about 5000 ... 40000
     panels in geometric steps, 900 charges each) near a sphere r = 40 A
     (30420 panels, sigma -0.05 C/m^2): `--poses` orientations x 4 gaps (6, 8,
-    10, 14 A) per molecule in pure FP32 (tol 1e-5).  Batched: pgb_solve_poses
+    10, 14 A) per molecule, FP32 + refinement with the double-single
+    residual (tol 1e-5).  Batched: pgb_solve_poses
     with chunks of `batch` poses (default 8, one pose of every molecule per
     chunk: one launch per stage over eight molecules of different sizes);
     beside it the same poses molecule by molecule through pgb_solve_batch
@@ -666,7 +667,7 @@ def run_poses_uneven(args):
         npan.append(len(f))
     # treecode parameters and work-item sizes by the autotuner, on the first
     # molecule 8 A from the sphere: the fastest FP32 solve whose total energy
-    # is within 1e-4 of the most accurate candidate's (theta 0.5, P 7)
+    # is within 1e-5 of the most accurate candidate's (theta 0.5, P 7)
     prm = dict(PARAMS)
     tune = None
     if not args.no_autotune:
@@ -674,7 +675,7 @@ def run_poses_uneven(args):
         ct = gpu_context([m0, srf], **PARAMS)
         thetas, Ps, leaves = [0.5, 0.6, 0.7], [5, 6, 7], [32, 64]
         (chosen, rep), t_ms = _timed(lambda: pgb.pgb_autotune(ct, thetas, Ps, leaves, reps=3, tol=1e-5,
-                                                              target_rel_err=1e-4))
+                                                              target_rel_err=1e-5))
         pgb.pgb_destroy(ct)
         for k in ("theta", "P", "leaf_size", "p2p_item", "m2p_item"):
             prm[k] = chosen[k]
@@ -696,25 +697,29 @@ def run_poses_uneven(args):
     R, t, pc = np.array(R), np.array(t), np.array(pc, dtype=np.int32)
     B = len(R)
     tol = 1e-5
-    pgb.pgb_solve_poses(ctxs, pc[:batch], 0, R[:batch], t[:batch], pgb.PGB_FP32, tol, MAX_ITER, RESTART)  # warm-up
+    mode = pgb.PGB_FP32_REFINE
+    pgb.pgb_solve_poses(ctxs, pc[:batch], 0, R[:batch], t[:batch], mode, tol, MAX_ITER, RESTART)  # warm-up
     pgb.pgb_timing(ctxs[0], True, read=True)
-    (code, F, st), ms = _timed(lambda: pgb.pgb_solve_poses(ctxs, pc, 0, R, t, pgb.PGB_FP32, tol, MAX_ITER,
-                                                            RESTART))
+    (code, F, st), ms = _timed(lambda: pgb.pgb_solve_poses(ctxs, pc, 0, R, t, mode, tol, MAX_ITER, RESTART))
     tim = pgb.pgb_timing(ctxs[0], False, read=True)
     # the same poses molecule by molecule with concurrent lanes (molecule 0
     # needs a context of its own without the batch parameter)
-    c0 = gpu_context([mols[0], srf], **dict(prm, batch=1))
-    F_l = np.zeros_like(F)
-    ms_l = 0.0
-    for k in range(8):
-        sel = np.nonzero(pc == k)[0]
-        ck = c0 if k == 0 else ctxs[k]
-        pgb.pgb_solve_batch(ck, 0, R[sel[:2]], t[sel[:2]], pgb.PGB_FP32, tol, MAX_ITER, RESTART)  # warm-up
-        (_, Fk, _), msk = _timed(lambda: pgb.pgb_solve_batch(ck, 0, R[sel], t[sel], pgb.PGB_FP32, tol, MAX_ITER,
-                                                             RESTART))
-        F_l[sel] = Fk
-        ms_l += msk
-    pgb.pgb_destroy(c0)
+    lanes = None
+    if not args.no_lanes:
+        c0 = gpu_context([mols[0], srf], **dict(prm, batch=1))
+        F_l = np.zeros_like(F)
+        ms_l = 0.0
+        for k in range(8):
+            sel = np.nonzero(pc == k)[0]
+            ck = c0 if k == 0 else ctxs[k]
+            pgb.pgb_solve_batch(ck, 0, R[sel[:2]], t[sel[:2]], mode, tol, MAX_ITER, RESTART)  # warm-up
+            (_, Fk, _), msk = _timed(lambda: pgb.pgb_solve_batch(ck, 0, R[sel], t[sel], mode, tol, MAX_ITER,
+                                                                 RESTART))
+            F_l[sel] = Fk
+            ms_l += msk
+        pgb.pgb_destroy(c0)
+        lanes = {"ms": ms_l, "poses_per_s": B / (ms_l / 1e3),
+                 "max_rel_diff_total_energy": float(np.max(np.abs(F_l[:, 3] - F[:, 3]) / np.abs(F[:, 3])))}
     # FP64 reference for the first chunk
     code64, F64, _ = pgb.pgb_solve_poses(ctxs, pc[:batch], 0, R[:batch], t[:batch], pgb.PGB_FP64, 1e-9, MAX_ITER,
                                          RESTART)
@@ -723,14 +728,17 @@ def run_poses_uneven(args):
     print(json.dumps({"workload": f"8 molecules ({min(npan)}-{max(npan)} panels, 900 charges each) x {args.poses} "
                                   f"orientations x 4 gaps near a sphere r=40 A (30420 panels)",
                       "poses": B, "batch": batch, "ms": ms, "poses_per_s": B / (ms / 1e3),
-                      "lanes_4_per_molecule": {"ms": ms_l, "poses_per_s": B / (ms_l / 1e3),
-                                               "max_rel_diff_total_energy": float(np.max(np.abs(F_l[:, 3] - F[:, 3]) /
-                                                                                         np.abs(F[:, 3])))},
+                      "lanes_4_per_molecule": lanes, "mode": "FP32 + refinement (double-single residual)",
+                      "max_rel_residual": float(max(s_["rel_residual"] for s_ in st)),
                       "molecule_panels": npan, "mean_iterations": float(its.mean()), "autotune": tune,
                       "iterations_range": [int(its.min()), int(its.max())], "status": code,
                       "energy_rel_err_vs_fp64_first_chunk_max": float(err.max()),
                       "stage_ms_per_pose": {k: v[0] / B for k, v in tim.items() if k != "kernel_launches" and v[0]},
-                      "kernel_launches_per_pose": tim["kernel_launches"] / B}), flush=True)
+                      "kernel_launches_per_pose": tim["kernel_launches"] / B,
+                      # per molecule, per gap: Boltzmann weights over the orientations (poses are
+                      # ordered orientation, gap, molecule)
+                      "orientation_landscape": {f"molecule_{k}": orientation_landscape(F[k::8, 3], args.poses, 4)
+                                                for k in range(8)}}), flush=True)
     for c in ctxs:
         pgb.pgb_destroy(c)
 
@@ -915,6 +923,7 @@ def main():
     ap.add_argument("--batch", type=int, default=None, help="poses per block-diagonal union solve (pose workloads)")
     ap.add_argument("--residual", type=int, default=None, help="0: native FP64 outer residual, 1: double-single")
     ap.add_argument("--no-autotune", action="store_true", help="pose sweep over 8 molecules: library parameters")
+    ap.add_argument("--no-lanes", action="store_true", help="pose sweep over 8 molecules: skip the lanes comparison")
     args = ap.parse_args()
     for k, v in (("leaf_size", args.leaf), ("P", args.P), ("theta", args.theta), ("p2p_item", args.p2p_item),
                  ("m2p_item", args.m2p_item), ("precond", args.precond),
