@@ -154,30 +154,6 @@ __global__ void k_axpby(double a, const double* x, double b, const double* y, do
     if (r < n) out[r] = a * x[r] + b * y[r];
 }
 
-// Givens step on column j of H (column-major, ld = m+1): apply the previous
-// rotations, form the new one, rotate g; out[0] = |g_{j+1}|, out[1] = h_{j+1,j}.
-__global__ void k_givens(double* H, int ld, double* cs, double* sn, double* g, int j, double* out) {
-    if (threadIdx.x || blockIdx.x) return;
-    double* h = H + (int64_t)j * ld;
-    for (int i = 0; i < j; ++i) {
-        double a = cs[i] * h[i] + sn[i] * h[i + 1];
-        double b = -sn[i] * h[i] + cs[i] * h[i + 1];
-        h[i] = a;
-        h[i + 1] = b;
-    }
-    out[1] = h[j + 1];
-    double a = h[j], b = h[j + 1];
-    double r = hypot(a, b);
-    double c = r > 0 ? a / r : 1.0, s = r > 0 ? b / r : 0.0;
-    cs[j] = c;
-    sn[j] = s;
-    h[j] = r;
-    h[j + 1] = 0;
-    g[j + 1] = -s * g[j];
-    g[j] = c * g[j];
-    out[0] = fabs(g[j + 1]);
-}
-
 // y = H(0:k,0:k)^{-1} g(0:k) (upper triangular)
 __global__ void k_backsolve(const double* H, int ld, const double* g, int k, double* y) {
     if (threadIdx.x || blockIdx.x) return;
@@ -387,7 +363,9 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arn_finish(ArnArgs a) {
     double* vn = a.V + (int64_t)(a.j + 1) * a.ld;
     for (int64_t r = v.lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < v.hi; r += stride)
         vn[r] = a.w[r] * inv;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {  // Givens step on column j (as k_givens)
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // Givens step on column j of H (column-major, ld = m + 1): the previous
+        // rotations, then the new one, applied to g; out[0] = |g_{j+1}|, out[1] = h_{j+1,j}
         double* h = v.h;
         h[a.j + 1] = nrm;
         for (int i = 0; i < a.j; ++i) {
@@ -608,26 +586,10 @@ int gmres_op(pgb_ctx* c, int prec, bool transpose, const double* b, double* x, d
             apply_pc(vj, w);
             ++*matvecs;
             double* h = c->d_H.p + (size_t)j * (m + 1);
-            const bool fused = true;
             {
                 StageTimer tm(c, PGB_STAGE_KRYLOV);
                 arnoldi_step(c, j, w, h, hcol, cs, sn, g, misc.p + 2, nullptr);
                 PGB_LAUNCHED(c, 4);
-            }
-            if (!fused) {  // the multi-kernel reference path (kept for comparison)
-                StageTimer tm(c, PGB_STAGE_KRYLOV);
-                for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
-                    k_multi_dot<<<DOT_BLOCKS, DOT_THREADS, 8 * (DOT_THREADS / 32) * (j + 1), s>>>(c->d_V, n, j + 1, w, n,
-                                                                                            c->d_red);
-                    k_reduce_partials<<<j + 1, 256, 0, s>>>(c->d_red, DOT_BLOCKS, pass ? hcol : h, 0, 0);
-                    k_multi_axpy<<<nblk(n, 256), 256, 0, s>>>(c->d_V, n, j + 1, pass ? hcol : h, -1.0, w, n);
-                    if (pass) k_axpby<<<1, 256, 0, s>>>(1.0, h, 1.0, hcol, h, j + 1);
-                }
-                K.norm(w, h + j + 1);
-                k_scale_by<<<nblk(n, 256), 256, 0, s>>>(w, h + j + 1, c->d_V.p + (size_t)(j + 1) * n, n);
-                k_givens<<<1, 1, 0, s>>>(c->d_H, m + 1, cs, sn, g, j, misc.p + 2);
-                PGB_CUDA(cudaGetLastError());
-                PGB_LAUNCHED(c, 12);
             }
             PGB_CUDA(cudaMemcpyAsync(c->h_pinned, misc.p + 2, 16, cudaMemcpyDeviceToHost, s));
             PGB_CUDA(cudaStreamSynchronize(s));
