@@ -26,7 +26,7 @@ import math
 import numpy as np
 import scipy.linalg
 
-from .bem import DIELECTRIC, SET_CHARGE, SET_POTENTIAL, System
+from .bem import DIELECTRIC, SET_CHARGE, System
 from .energy import energies
 from .integrals import panel_operator_blocks
 from .units import ENERGY_KCAL, phi_from_volt, sigma_from_c_m2

@@ -4,8 +4,6 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import units
-from oracle.bem import SET_CHARGE
 from oracle.gradient import gradients
 from problems import gpu_context, oracle_system
 

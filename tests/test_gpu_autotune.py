@@ -1,6 +1,5 @@
 """pgb_autotune: the chosen parameters come from the candidate set, meet the
 accuracy target against the reference candidate and are the fastest such."""
-import numpy as np
 import pytest
 
 from problems import gpu_context, spheres

@@ -10,8 +10,7 @@ from scipy.special import eval_legendre, spherical_in, spherical_kn
 import synth
 from oracle import units
 from oracle.analytical import (B_matrix, interaction, isolated_molecule_solvation,
-                               isolated_surface_charge, isolated_surface_potential,
-                               two_sphere_energies)
+                               isolated_surface_charge, isolated_surface_potential)
 from oracle.bem import DIELECTRIC, SET_CHARGE, SET_POTENTIAL, Body, System
 from oracle.energy import energies, interaction_energy
 
