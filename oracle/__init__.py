@@ -24,8 +24,8 @@ Modules (each function cites the passage of the paper it restates):
                  Taylor expansion evaluated by univariate power series
                  (Section 3.2).
   regions     -- more interfaces (Stern layers, solvent-filled cavities: the
-                 extension stated after Eq. 7) as per-region rows, and the
-                 closed forms that pin them.
+                 extension stated after Eq. 7) as per-region rows, their
+                 treecode product, and the closed forms that pin them.
 
 Parity status: every function is pinned by a test in tests/test_oracle_*.py
 except where its docstring says "parity unpinned".

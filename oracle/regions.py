@@ -253,3 +253,124 @@ def concentric_cavity_solvation(q, c, a, b, eps_cav, eps_mol, eps_out, kappa, lm
         A_, B_, C_, D_ = np.linalg.solve(M, rhs)
         phi += B_ * c ** l + C_ * c ** (-(l + 1))
     return 0.5 * q * phi * ENERGY_KCAL
+
+
+class RegionTreecode:
+    """Treecode product of a RegionSystem (the per-region rows above): per
+    region R, the truncated expansion and near sums of oracle.treecode with
+    R's screening, over the bodies bounding R with their signed side
+    densities, plus R's tiered corrections; then row = jump - U_R.  Trees,
+    target groups and interaction lists are those of oracle.treecode
+    (Section 3.2 readings there); only the kernel and the densities depend on
+    the region."""
+
+    def __init__(self, rs, theta=None, P=None):
+        from .treecode import BodyTree, interaction_lists
+        self.rs = rs
+        p = rs.p
+        self.theta = p.theta if theta is None else theta
+        self.P = p.P if P is None else P
+        self.trees = [BodyTree(b, pn, p.K, p.leaf_size) for b, pn in zip(rs.bodies, rs.panels)]
+        self.y, self.w = zip(*[pn.points(p.K) for pn in rs.panels])
+        self.groups = []
+        for a, (tr, pn) in enumerate(zip(self.trees, rs.panels)):
+            for g0 in range(0, pn.N, p.group_size):
+                idx = tr.perm[g0:g0 + p.group_size]
+                x = pn.c[idx]
+                self.groups.append((a, idx, x.min(0), x.max(0)))
+        self.lists = {(gi, b): interaction_lists(tr, lo, hi, self.theta)
+                      for gi, (a, idx, lo, hi) in enumerate(self.groups) for b, tr in enumerate(self.trees)}
+        self.regions = sorted({R for b in range(len(rs.bodies)) for R in (rs.inner(b), rs.outer(b)) if R is not None})
+
+    def _side(self, x, b, s, R):
+        """(psi, phi) of body b seen from region R with the sign s folded in
+        (unknowns only: the imposed values belong to the right-hand side)."""
+        rs = self.rs
+        bb = rs.bodies[b]
+        N = rs.panels[b].N
+        if bb.kind == DIELECTRIC:
+            phi, dphi = rs.blocks(x, b)
+            psi = dphi if s > 0 else (bb.eps_in / rs.region_eps(R)) * dphi
+        elif bb.kind == SET_POTENTIAL:
+            (psi,) = rs.blocks(x, b)
+            phi = np.zeros(N)
+        else:
+            (phi,) = rs.blocks(x, b)
+            psi = np.zeros(N)
+        return s * psi, s * phi
+
+    def _region_sum(self, x, R):
+        from .integrals import kernel_terms
+        from .treecode import _Sub, truncated_kernel
+        rs = self.rs
+        p = rs.p
+        kap = rs.region_kappa(R)
+        lap = kap == 0
+        bnd = dict(rs.boundary(R))
+        U = {a: np.zeros(rs.panels[a].N) for a in bnd}
+        side = {b: self._side(x, b, s, R) for b, s in bnd.items()}
+        pick = (lambda t: (t[0], t[1])) if lap else (lambda t: (t[2], t[3]))
+        for gi, (a, idx, lo, hi) in enumerate(self.groups):
+            if a not in bnd:
+                continue
+            xt = rs.panels[a].c[idx]
+            for b in bnd:
+                psi, phi = side[b]
+                tr = self.trees[b]
+                near, far = self.lists[(gi, b)]
+                K = p.K
+                q = self.w[b] * psi[:, None]
+                pv = (self.w[b] * phi[:, None])[..., None] * rs.panels[b].n[:, None, :]
+                for nid in near:
+                    nd = tr.nodes[nid]
+                    pj = tr.perm[nd["start"]:nd["end"]]
+                    y = self.y[b][pj].reshape(-1, 3)
+                    nrm = np.repeat(rs.panels[b].n[pj], K, axis=0)
+                    g, k = pick(kernel_terms(xt[:, None, :], y[None], nrm[None], kap))
+                    wphi = (pv[pj].reshape(-1, 3) * nrm).sum(-1)
+                    U[a][idx] += g @ q[pj].reshape(-1) - k @ wphi
+                for nid in far:
+                    nd = tr.nodes[nid]
+                    pj = tr.perm[nd["start"]:nd["end"]]
+                    c = nd["center"]
+                    y = self.y[b][pj].reshape(-1, 3)
+                    Rv = (xt - c)[:, None, :] * np.ones((1, len(y), 1))
+                    dvec = np.broadcast_to((y - c)[None], Rv.shape)
+                    pp = np.broadcast_to(pv[pj].reshape(-1, 3)[None], Rv.shape)
+                    F, dF = truncated_kernel(Rv, dvec, pp, kap, self.P, lap)
+                    U[a][idx] += F @ q[pj].reshape(-1) - dF.sum(1)
+        # tiered corrections among the region's bodies
+        for a in bnd:
+            pa = rs.panels[a]
+            for b in bnd:
+                pb = rs.panels[b]
+                psi, phi = side[b]
+                dc = pa.c[:, None, :] - pb.c[None, :, :]
+                near = np.einsum("ijk,ijk->ij", dc, dc) < 8.0 * pb.A[None, :]
+                if a == b:
+                    near[np.arange(pa.N), np.arange(pa.N)] = True
+                for i, j in zip(*np.nonzero(near)):
+                    tier = pick(panel_operator_blocks(pa.c[i:i + 1], _Sub(pb, j), kap, p.K, p.K_near, p.n_edge,
+                                                      np.array([0 if (a == b and i == j) else -1])))
+                    kp = pick(kernel_terms(pa.c[i][None, :], self.y[b][j], pb.n[j][None, :], kap))
+                    dV = tier[0][0, 0] - float((kp[0] * self.w[b][j]).sum())
+                    dK = tier[1][0, 0] - float((kp[1] * self.w[b][j]).sum())
+                    U[a][i] += dV * psi[j] - dK * phi[j]
+        return U
+
+    def apply(self, x):
+        """A x of the per-region rows (same as RegionSystem.assemble()[0] @ x
+        up to the treecode truncation)."""
+        rs = self.rs
+        out = np.zeros(rs.n)
+        for a, ba in enumerate(rs.bodies):
+            Na = rs.panels[a].N
+            for r0, R in rs.rows(a):
+                if ba.kind == DIELECTRIC or ba.kind == SET_CHARGE:
+                    out[r0:r0 + Na] = 0.5 * x[rs.offsets[a]:rs.offsets[a] + Na]
+        for R in self.regions:
+            for a, Ua in self._region_sum(x, R).items():
+                for r0, Ra in self.rs.rows(a):
+                    if Ra == R:
+                        out[r0:r0 + rs.panels[a].N] -= Ua
+        return out

@@ -102,3 +102,50 @@ def test_series_limits():
     # kappa = 0: Born's formula
     born0 = 0.5 * (1.0 / 80.0 - 1.0 / 4.0) / 4.0 * units.COULOMB_KCAL
     assert stern_sphere_solvation(1.0, 4.0, 6.0, 4.0, 80.0, 0.0) == pytest.approx(born0, rel=1e-12)
+
+
+def _stern_bodies():
+    v1, f1 = synth.icosphere(1, 4.0)
+    v2, f2 = synth.icosphere(1, 6.0)
+    return [Body(DIELECTRIC, v1, f1, eps_in=4.0, charge_xyz=np.array([[0.5, 0.0, 0.0]]), charge_q=np.array([1.0])),
+            Body(DIELECTRIC, v2, f2, eps_in=80.0)]
+
+
+def test_region_treecode_at_theta_zero_is_the_dense_rows():
+    """theta = 0: every node is opened, so the per-region treecode is the
+    direct sum of the dense rows (to rounding)."""
+    from oracle.regions import RegionTreecode
+    rs = RegionSystem(_stern_bodies(), 80.0, 0.125, parent=[1, -1], params=Params(theta=0.0, leaf_size=8))
+    x = np.random.default_rng(1).normal(size=rs.n)
+    ref = rs.assemble()[0] @ x
+    y = RegionTreecode(rs).apply(x)
+    assert np.abs(y - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_region_treecode_converges_with_P():
+    from oracle.regions import RegionTreecode
+    bodies = _stern_bodies()
+    A = RegionSystem(bodies, 80.0, 0.125, parent=[1, -1]).assemble()[0]
+    x = np.random.default_rng(1).normal(size=A.shape[0])
+    ref = A @ x
+    errs = []
+    for P in (2, 4, 6):
+        rs = RegionSystem(bodies, 80.0, 0.125, parent=[1, -1], params=Params(theta=0.5, P=P, leaf_size=8))
+        errs.append(np.abs(RegionTreecode(rs).apply(x) - ref).max() / np.abs(ref).max())
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 2e-4
+
+
+def test_region_treecode_without_nesting_is_the_plain_treecode():
+    """No nesting: the per-region passes (molecule interior, solvent) give
+    exactly the fused treecode of oracle.treecode."""
+    from oracle.regions import RegionTreecode
+    from oracle.treecode import TreecodeOperator
+    v1, f1 = synth.icosphere(1, 4.0)
+    v2, f2 = synth.icosphere(0, 3.0)
+    bodies = [Body(DIELECTRIC, v1, f1, eps_in=4.0, charge_xyz=np.array([[0.3, 0.0, 0.0]]), charge_q=np.array([1.0])),
+              Body(SET_CHARGE, v2 + [9.0, 0, 0], f2, bc_value=units.sigma_from_c_m2(0.05))]
+    prm = Params(theta=0.5, P=4, leaf_size=8)
+    x = np.random.default_rng(2).normal(size=RegionSystem(bodies, 80.0, 0.125).n)
+    ya = RegionTreecode(RegionSystem(bodies, 80.0, 0.125, params=prm)).apply(x)
+    yb = TreecodeOperator(System(bodies, 80.0, 0.125, prm)).apply(x)
+    assert np.abs(ya - yb).max() <= 1e-13 * np.abs(yb).max()
