@@ -149,3 +149,26 @@ def test_region_treecode_without_nesting_is_the_plain_treecode():
     ya = RegionTreecode(RegionSystem(bodies, 80.0, 0.125, params=prm)).apply(x)
     yb = TreecodeOperator(System(bodies, 80.0, 0.125, prm)).apply(x)
     assert np.abs(ya - yb).max() <= 1e-13 * np.abs(yb).max()
+
+
+def test_charged_surface_behind_an_interface_between_equal_media():
+    """An imposed-charge sphere and a molecule, both inside a shell whose
+    interior is the solvent itself (same eps and kappa): surface and
+    solvation energies equal those without the shell, so the rows of a
+    surface in a region other than the solvent (its imposed density
+    -sigma0 / eps_R) and the surface energy there are consistent."""
+    kap = 0.125
+    vm, fm = synth.icosphere(2, 3.0)
+    vs, fs = synth.icosphere(1, 2.0)
+    vb, fb = synth.icosphere(2, 12.0)
+    mol = Body(DIELECTRIC, vm + [-4.0, 0, 0], fm, eps_in=4.0, charge_xyz=np.array([[-4.0, 0.2, 0.0]]),
+               charge_q=np.array([1.0]))
+    srf = Body(SET_CHARGE, vs + [4.0, 0, 0], fs, bc_value=units.sigma_from_c_m2(0.05))
+    shell = Body(DIELECTRIC, vb, fb, eps_in=80.0)
+    e_in = _energy([mol, srf, shell], kap, parent=[2, 2, -1], kappa_in=[0.0, 0.0, kap])
+    e_plain = _energy([mol, srf], kap)
+    for k in ("solvation", "surface", "total"):
+        assert e_in[k] == pytest.approx(e_plain[k], rel=2e-3)
+    # and the test sees the medium: an unscreened interior moves the surface energy by 30 %
+    e_bad = _energy([mol, srf, shell], kap, parent=[2, 2, -1], kappa_in=[0.0, 0.0, 0.0])
+    assert abs(e_bad["surface"] - e_plain["surface"]) > 0.1 * abs(e_plain["surface"])
