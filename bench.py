@@ -407,6 +407,12 @@ def run_gpu(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h,
                 "ms_per_step": statistics.mean(e2e_ms)},
         "cpu_baseline": cpu,
+        # the paper's only stated timing, as context (another workload and machine)
+        "paper_context": {"timing": "less than one minute per run",
+                          "hardware": "Intel Xeon X5650 CPUs + 1 NVIDIA Tesla C2075 (Fermi)",
+                          "workload": "protein G B1 D4' (4 elem/A^2) near a charged block (2 elem/A^2), "
+                                      "N_crit 300, P 4, theta 0.5, GMRES tol 1e-5 (structure and meshes not "
+                                      "available here)"},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
