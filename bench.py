@@ -29,9 +29,6 @@ import sys
 import tempfile
 import time
 
-for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
-    os.environ.setdefault(_v, "1")
-
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -45,8 +42,19 @@ PARAMS = dict(K=7, K_near=19, n_edge=9, P=6, theta=0.5, leaf_size=32, group_size
 TOL = 1e-6
 RESTART = 100
 MAX_ITER = 2000
-FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)"
-FP64_PEAK = 152 * 2 * 2 * 2.07e9 / 1e12  # TFLOP/s: 2 FP64 FMA lanes per SM per clock (measured pipe rate)
+
+
+def device_peaks(dev):
+    """FP32 ALU peak of the device from its SM count (cudaDevAttrMultiProcessorCount
+    through torch) and the maximum SM clock (sm_max_mhz of MEASURED_PEAKS.json,
+    else 2070 MHz): SMs x 128 FP32 lanes x 2 flop (FMA) x clock."""
+    import torch
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = float(load_peaks().get("sm_max_mhz", 2070.0))
+    tf = n_sm * 128 * 2 * mhz * 1e6 / 1e12
+    note = (f"{n_sm} SMs (device attribute) x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz (sm_max_mhz of "
+            f"MEASURED_PEAKS.json): derived, the file holds no FP32 figure")
+    return {"fp32_tflops": tf, "sm_count": n_sm, "sm_max_mhz": mhz, "note": note}
 
 
 def workload_bodies(level=5):
@@ -156,6 +164,30 @@ def recorded_traffic(kernel):
     return float(kv["dram_bytes_per_launch_full"])
 
 
+def recorded_counters(fname):
+    """key = value lines of a committed ncu summary (profiles/fname) when its
+    recorded source hash matches the current kernels (else empty)."""
+    path = os.path.join(ROOT, "profiles", fname)
+    src = os.path.join(ROOT, "paper_1506_03745_gb300", "csrc", "treecode.cuh")
+    if not os.path.exists(path):
+        return {}
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    kv = {}
+    for line in open(path):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.split("=", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("treecode_cuh_sha256_16") != h:
+        return {}
+    out = {}
+    for k, v in kv.items():
+        try:
+            out[k] = float(v)
+        except ValueError:
+            pass
+    return out
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -164,42 +196,169 @@ def load_peaks():
 
 
 # ------------------------------------------------------------------ reference (oracle)
-def oracle_rate(bodies, n_targets, seed=0):
-    """Direct-sum FP64 oracle rows for n_targets molecule panels: returns
-    (seconds, matvec fraction)."""
+def cpu_info():
+    """Host cores the oracle runs on (os.cpu_count) and the CPU model."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return os.cpu_count() or 1, model or "unknown"
+
+
+def _oracle_rows_task(task):
+    """Worker: direct-sum FP64 oracle rows of the two-sphere workload for the
+    molecule targets [t0, t1) (both rows of each); returns seconds."""
+    t0, t1, seed = task
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     from problems import oracle_system
-    so = oracle_system(bodies, theta=0.0)
+    so = oracle_system(workload_bodies(), theta=0.0)
     x = np.random.default_rng(seed).normal(size=so.n)
-    rows = np.arange(n_targets)
-    t0 = time.perf_counter()
-    so.apply_rows(x, 0, rows)
-    dt = time.perf_counter() - t0
-    n_pan = sum(p.N for p in so.panels)
-    return dt, n_targets / n_pan
+    c0 = time.perf_counter()
+    so.apply_rows(x, 0, np.arange(t0, t1))
+    return time.perf_counter() - c0
+
+
+def _dense_rows_task(task):
+    """Worker: rows of the dense oracle system (oracle.bem.System.assemble_rows)
+    for a chunk of target panels of one body of a small workload."""
+    name, body, rows = task
+    so = _dense_system(name)
+    per = [np.zeros(0, dtype=np.int64) for _ in so.bodies]
+    per[body] = np.asarray(rows)
+    return so.assemble_rows(per)
+
+
+def _dense_system(name):
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from problems import oracle_system, spheres
+    if name == "kirkwood":   # config 1: one sphere, 1280 panels, central charge
+        return oracle_system(spheres(level_mol=3, surface=False), theta=0.0)
+    return oracle_system(spheres(level_mol=3, level_srf=3, kind="sigma"), theta=0.0)   # 2 x 1280 panels
+
+
+def _pool(n):
+    """Spawned worker processes (the parent holds a CUDA context), one BLAS
+    thread each."""
+    import multiprocessing as mp
+    old = {v: os.environ.get(v) for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
+    for v in old:
+        os.environ[v] = "1"
+    try:
+        return mp.get_context("spawn").Pool(n)
+    finally:
+        for v, val in old.items():
+            if val is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = val
+
+
+def oracle_matvec_rate(pool, cores, rows_per_task=6, rounds=1, seed=0):
+    """Direct-sum oracle rows sampled over all host cores: tasks of
+    rows_per_task molecule targets, `cores` tasks per round.  Returns
+    (matvecs per second of wall time, targets sampled, wall seconds)."""
+    tasks = [(k * rows_per_task, (k + 1) * rows_per_task, seed) for k in range(cores * rounds)]
+    c0 = time.perf_counter()
+    pool.map(_oracle_rows_task, tasks, chunksize=1)
+    wall = time.perf_counter() - c0
+    n_t = rows_per_task * len(tasks)
+    return (n_t / 40960) / wall, n_t, wall
+
+
+def oracle_dense_solves(pool, cores):
+    """Dense FP64 assembly (rows split over the host cores) and LAPACK LU
+    solve (threaded BLAS of the parent) of two small workloads: ms each."""
+    import scipy.linalg
+    out = []
+    for name, label in (("kirkwood", "Kirkwood sphere, 1280 panels (2560 unknowns)"),
+                        ("two_spheres_l3", "two spheres r=4 A, 2 x 1280 panels (3840 unknowns)")):
+        so = _dense_system(name)
+        tasks = []
+        for b, pn in enumerate(so.panels):
+            for ch in np.array_split(np.arange(pn.N), max(1, cores)):
+                if len(ch):
+                    tasks.append((name, b, ch))
+        c0 = time.perf_counter()
+        parts = pool.map(_dense_rows_task, tasks, chunksize=1)
+        A = np.zeros((so.n, so.n))
+        rhs = np.zeros(so.n)
+        for idx, Ar, br in parts:
+            A[idx] = Ar
+            rhs[idx] = br
+        c1 = time.perf_counter()
+        lu = scipy.linalg.lu_factor(A)
+        scipy.linalg.lu_solve(lu, rhs)
+        c2 = time.perf_counter()
+        out.append({"workload": label, "unknowns": int(so.n), "assembly_ms": 1e3 * (c1 - c0),
+                    "lu_solve_ms": 1e3 * (c2 - c1), "solve_ms": 1e3 * (c2 - c0)})
+    return out
+
+
+def cpu_baseline_record(target_s=10.0):
+    """The oracle on the host cores: the direct-sum matvec rate of the
+    two-sphere workload (sampled rows, about target_s of wall time on all
+    cores) and the dense assembly + LU solve times of two small workloads."""
+    cores, model = cpu_info()
+    pool = _pool(cores)
+    try:
+        oracle_matvec_rate(pool, cores, rows_per_task=1)       # start the workers
+        n_t, wall, seed = 0, 0.0, 1
+        while wall < target_s:
+            _, n, w = oracle_matvec_rate(pool, cores, rows_per_task=16, seed=seed)
+            n_t += n
+            wall += w
+            seed += 1
+        rate = (n_t / 40960) / wall
+        dense = oracle_dense_solves(pool, cores)
+    finally:
+        pool.close()
+        pool.join()
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": model,
+            "sample": f"{n_t} of 40960 target panels (both rows each) in {wall:.1f} s on {cores} worker processes, "
+                      f"direct-sum FP64 oracle rows (dense O(N^2) operator, not a treecode), extrapolated to whole "
+                      f"matvecs",
+            "dense_lu": dense}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    bodies = workload_bodies()
-    per_step = 24
-    for _ in range(args.warmup):
-        oracle_rate(bodies, 4)
-    tot, frac = 0.0, 0.0
-    for _ in range(args.steps):
-        dt, f = oracle_rate(bodies, per_step)
-        tot += dt
-        frac += f
-    value = frac / tot
-    sample = (f"{per_step} of 40960 target panels per step (both rows of each), direct-sum FP64 oracle "
-              f"over all 286720 source points, extrapolated to whole matvecs")
+    cores, model = cpu_info()
+    pool = _pool(cores)
+    try:
+        for _ in range(args.warmup):
+            oracle_matvec_rate(pool, cores, rows_per_task=1)
+        tot, n_tot = 0.0, 0
+        for _ in range(args.steps):
+            _, n_t, wall = oracle_matvec_rate(pool, cores, rows_per_task=2)
+            tot += wall
+            n_tot += n_t
+    finally:
+        pool.close()
+        pool.join()
+    value = (n_tot / 40960) / tot
+    sample = (f"{n_tot // args.steps} of 40960 target panels per step (both rows of each) on {cores} worker "
+              f"processes, direct-sum FP64 oracle over all 286720 source points, extrapolated to whole matvecs")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": model},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -291,7 +450,8 @@ def run_gpu(args):
     native = variant_solve(pgb, bodies, dev, stream, flush, e64, residual=0) if PARAMS.get("residual") else None
 
     info = pgb.pgb_tree_stats(ctx)
-    peak_tflops = 152 * 128 * 2 * 2.07e9 / 1e12
+    peaks = device_peaks(dev)
+    peak_tflops = peaks["fp32_tflops"]
     kern = {}
     for name, stage, fl in (("k_p2p<float> (P2P, near leaves)", "p2p", p2p_kernel_flops(info)),
                             ("k_m2p<float,6> (M2P, far nodes)", "m2p", m2p_kernel_flops(info, PARAMS["P"]))):
@@ -301,21 +461,33 @@ def run_gpu(args):
                            achieved=fl / (ms / calls / 1e3) / 1e12 if calls else None)
     dom = max(kern.values(), key=lambda k: k["total_ms"])
     traffic = recorded_traffic(dom["kernel"].split(" ")[0])
-    # the FP64 product of the refinement residual: same algorithmic counts,
-    # against the FP64 peak (152 SMs x 2 FP64 FMA lanes x 2 flop x 2.07 GHz);
-    # with overlap its kernels share the SMs with the FP32 iterations, so
-    # their durations include that sharing
-    # (residual = 1: the double-single kernels on the FP32 pipe; their
-    # FP64-class flop rate is still set against the native FP64 peak, so a
-    # frac above 1 is the gain of the emulation over FP64 hardware)
+    # the FP64-class product of the refinement residual: same algorithmic
+    # counts.  residual = 1: double-single kernels on the FP32 pipe, set
+    # against the FP32 peak with the FP32 operations they issue per FP64-class
+    # operation (ncu, profiles/ds_residual_two_sphere.txt); residual = 0:
+    # native FP64 kernels against the FP64 pipe (2 FMA lanes per SM per clock)
+    fp64_peak = peaks["sm_count"] * 2 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
     tag = "ds" if PARAMS["residual"] else "double"
+    ds_prof = recorded_counters("ds_residual_two_sphere.txt")
     for name, stage, fl in ((f"k_p2p<{tag}> (P2P, FP64-class residual)", "p2p_fp64", p2p_kernel_flops(info)),
                             (f"k_m2p<{tag},6> (M2P, FP64-class residual)", "m2p_fp64",
                              m2p_kernel_flops(info, PARAMS["P"]))):
         ms, calls = timing[stage]
         ach = fl / (ms / calls / 1e3) / 1e12 if calls else None
-        kern[stage] = dict(kernel=name, total_ms=ms, calls=calls, flops=fl, avg_ms=ms / calls if calls else None,
-                           achieved=ach, peak=FP64_PEAK, frac=(ach / FP64_PEAK) if ach else None)
+        rec = dict(kernel=name, total_ms=ms, calls=calls, flops=fl, avg_ms=ms / calls if calls else None,
+                   achieved_fp64_class=ach, unit="TFLOP/s")
+        if PARAMS["residual"]:
+            key = stage.split("_")[0]
+            rec.update(bound="alu (FP32 pipe, double-single)", fp32_peak=peak_tflops,
+                       fp32_ops_per_fp64_class_op=ds_prof.get(f"{key}_fp32_ops_per_op"),
+                       ncu_fma_pipe=ds_prof.get(f"{key}_fma_pipe"), ncu_issue_active=ds_prof.get(f"{key}_issue"),
+                       note="FP64-class operations counted as the FP32 kernels' flops; ncu figures from the "
+                            "committed capture when it was taken on the current source, else null")
+            if ach and rec["fp32_ops_per_fp64_class_op"]:
+                rec["fp32_pipe_frac"] = ach * rec["fp32_ops_per_fp64_class_op"] / peak_tflops
+        else:
+            rec.update(bound="alu (FP64 pipe)", peak=fp64_peak, frac=(ach / fp64_peak) if ach else None)
+        kern[stage] = rec
 
     # the assembly of the FP32 product (item partial sums, near-field
     # correction SpMV, rows): the memory-bound kernel, against the measured
@@ -357,14 +529,7 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, frac = 0.0, 0.0
-        while dt < 10.0:
-            d, f = oracle_rate(bodies, 32)
-            dt += d
-            frac += f
-        cpu = {"value": frac / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{int(round(frac * 40960))} of 40960 target panels, direct-sum FP64 oracle rows "
-                         f"(dense O(N^2) operator, not a treecode), extrapolated to whole matvecs"}
+        cpu = cpu_baseline_record()
 
     st0 = stats[0]
     line = {
@@ -396,10 +561,10 @@ def run_gpu(args):
                      "frac": (dom["achieved"] / peak_tflops) if dom["achieved"] else None,
                      "traffic": traffic, "flops_per_launch": dom["flops"], "launches": dom["calls"],
                      "avg_launch_ms": dom["avg_ms"],
-                     "peak_source": FP32_PEAK_NOTE + " (derived, not in MEASURED_PEAKS.json)",
-                     "note": "dominant kernel of the FP32 treecode product (30 of the 31 products of a step); "
-                             "the FP64-class residual kernels are in other_kernels, their FP64-class flop rate "
-                             "against the native FP64 peak",
+                     "peak_source": peaks["note"], "sm_count": peaks["sm_count"],
+                     "sm_max_mhz": peaks["sm_max_mhz"],
+                     "note": "dominant kernel of the FP32 treecode product (the inner products of a step); "
+                             "the FP64-class residual kernels are in other_kernels, against the FP32 pipe",
                      "other_kernels": {k: {kk: vv for kk, vv in v.items() if kk != "kernel"} | {"kernel": v["kernel"]}
                                        for k, v in kern.items() if v is not dom}},
         "tree": info,
@@ -413,6 +578,11 @@ def run_gpu(args):
                           "workload": "protein G B1 D4' (4 elem/A^2) near a charged block (2 elem/A^2), "
                                       "N_crit 300, P 4, theta 0.5, GMRES tol 1e-5 (structure and meshes not "
                                       "available here)"},
+        # the FP32 + refinement solve against the plain FP64 solve on the same
+        # GPU, last so that a tail of the line keeps it
+        "solve_vs_fp64": {"fp32_refine_ms": t_max / args.steps, "fp64_ms": fp64_ms,
+                          "speedup_vs_fp64": fp64_ms / (t_max / args.steps),
+                          "energy_rel_err_vs_fp64": e_err},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -145,7 +145,8 @@ typedef struct pgb_stage_times {
 
 /* Create a context on the current CUDA device.  p may be NULL (defaults:
  * K=7, K_near=19, n_edge=9, P=6, theta=0.5, leaf_size=32, group_size=32,
- * p2p_item=64, m2p_item=64, precond=0, graphs=1, lanes=4, overlap=1).
+ * p2p_item=64, m2p_item=64, precond=0, graphs=1, lanes=4, overlap=0,
+ * batch=1, residual=1).
  * cuda_stream is a cudaStream_t (NULL = legacy default stream).  Returns
  * PGB_EINVAL for out-of-range parameters. */
 int pgb_create(struct pgb_ctx** ctx, const pgb_params* p, void* cuda_stream);
@@ -186,6 +187,18 @@ int pgb_set_pose(struct pgb_ctx* ctx, int32_t body_id, const double R[9], const 
  * current bodies and poses (Section 3.1 tiers, Section 3.2 treecode). */
 int pgb_tree_build(struct pgb_ctx* ctx);
 int pgb_tree_stats(struct pgb_ctx* ctx, pgb_tree_info* info);
+
+/* Recompute what the current poses change -- world geometry, node and group
+ * centres, the offsets of the list entries and P2P tiles, cross-body
+ * near-field entries -- while keeping the near/far interaction lists (and the
+ * work items) of the last pgb_tree_build.  The product is then the treecode
+ * with those lists at the new poses: a small pose change (finite differences
+ * of an energy in a translation, as for the adjoint gradient of pgb_grad)
+ * moves no node across the acceptance criterion, so the difference carries no
+ * jump from a changed list.  The caller keeps the poses close to the ones the
+ * lists were built for (the criterion is not re-tested).  PGB_ESTATE without
+ * such a tree (nothing built, or bodies loaded since). */
+int pgb_tree_refresh(struct pgb_ctx* ctx);
 
 /* Drop every cached geometric structure (Morton order, octree, each body's
  * own near-field entries), so that the next pgb_tree_build recomputes all of
@@ -351,6 +364,12 @@ int pgb_tree_export(struct pgb_ctx* ctx, int32_t* perm, int64_t* near_off, int32
  * PGB_FP64_DS product, each converted back to a double.  PGB_EINVAL for n < 0 or a
  * NULL pointer with n > 0; PGB_ECUDA on a CUDA error. */
 int pgb_math_check(const double* x, int64_t n, double* out);
+
+/* Diagnostic: *n receives the number of memory allocations libpgb has made
+ * in this process so far (device buffers, stream-ordered or not, and pinned
+ * host buffers).  No context and no device call; PGB_EINVAL for n = NULL.
+ * Two reads around a call show whether that call allocated. */
+int pgb_alloc_count(int64_t* n);
 
 
 #ifdef __cplusplus

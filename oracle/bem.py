@@ -97,36 +97,66 @@ class System:
     # ---- dense assembly (Eq. 6 / Eq. 7) ---------------------------------
     def assemble(self):
         """Dense matrix A (n x n) and right-hand side b of the block system."""
-        A = np.zeros((self.n, self.n))
-        rhs = np.zeros(self.n)
+        idx, A, rhs = self.assemble_rows([np.arange(pn.N) for pn in self.panels])
+        Af = np.zeros((self.n, self.n))
+        bf = np.zeros(self.n)
+        Af[idx] = A
+        bf[idx] = rhs
+        return Af, bf
+
+    def assemble_rows(self, rows):
+        """The rows of the dense system that belong to the target panels
+        rows[a] (indices into body a's panels) of every body a: returns the
+        global row indices, those rows of A and of the right-hand side.  The
+        entries are those of assemble(); splitting the targets into chunks
+        splits the assembly (the oracle's CPU timing runs chunks in parallel)."""
+        idx, blocks, rhs_parts = [], [], []
         for a, ba in enumerate(self.bodies):
-            Na = self.panels[a].N
+            ra = np.asarray(rows[a], dtype=np.int64)
+            if len(ra) == 0:
+                continue
+            nr = len(ra)
             oa = self.offsets[a]
+            Na = self.panels[a].N
             ext = oa + Na if ba.kind == DIELECTRIC else oa   # exterior/surface row start
+            n_blk = 2 if ba.kind == DIELECTRIC else 1
+            A = np.zeros((n_blk * nr, self.n))
+            rhs = np.zeros(n_blk * nr)
+            e0 = nr if ba.kind == DIELECTRIC else 0          # exterior/surface rows within A
             for b, bb in enumerate(self.bodies):
                 Nb = self.panels[b].N
                 ob = self.offsets[b]
-                VL, KL, VY, KY = self.operator_blocks(a, b, laplace=(a == b))
-                I = np.eye(Na) if a == b else None
+                si = ra if a == b else None
+                VL, KL, VY, KY = panel_operator_blocks(self.panels[a].c[ra], self.panels[b], self.kappa,
+                                                       self.p.K, self.p.K_near, self.p.n_edge, si, a == b)
+                if a == b:
+                    I = np.zeros((nr, Nb))
+                    I[np.arange(nr), ra] = 1.0
+                else:
+                    I = None
                 if bb.kind == DIELECTRIC:
                     if a == b:   # interior row (Laplace), Eq. 5 line 1
-                        A[oa:oa + Na, ob:ob + Nb] = 0.5 * I + KL
-                        A[oa:oa + Na, ob + Nb:ob + 2 * Nb] = -VL
+                        A[0:nr, ob:ob + Nb] = 0.5 * I + KL
+                        A[0:nr, ob + Nb:ob + 2 * Nb] = -VL
                     blk = -KY + (0.5 * I if a == b else 0.0)
-                    A[ext:ext + Na, ob:ob + Nb] = blk
-                    A[ext:ext + Na, ob + Nb:ob + 2 * Nb] = (bb.eps_in / self.eps_out) * VY
+                    A[e0:e0 + nr, ob:ob + Nb] = blk
+                    A[e0:e0 + nr, ob + Nb:ob + 2 * Nb] = (bb.eps_in / self.eps_out) * VY
                 elif bb.kind == SET_POTENTIAL:
                     phi0 = bb.bc_value
-                    A[ext:ext + Na, ob:ob + Nb] = VY
+                    A[e0:e0 + nr, ob:ob + Nb] = VY
                     known = (-KY + (0.5 * I if a == b else 0.0)) @ np.full(Nb, phi0)
-                    rhs[ext:ext + Na] -= known
+                    rhs[e0:e0 + nr] -= known
                 else:            # SET_CHARGE
                     dphi = -bb.bc_value / self.eps_out
-                    A[ext:ext + Na, ob:ob + Nb] = -KY + (0.5 * I if a == b else 0.0)
-                    rhs[ext:ext + Na] -= VY @ np.full(Nb, dphi)
+                    A[e0:e0 + nr, ob:ob + Nb] = -KY + (0.5 * I if a == b else 0.0)
+                    rhs[e0:e0 + nr] -= VY @ np.full(Nb, dphi)
             if ba.kind == DIELECTRIC:
-                rhs[oa:oa + Na] = self.coulomb_rhs(a)
-        return A, rhs
+                rhs[0:nr] = self.coulomb_rhs(a)[ra]
+                idx.append(oa + ra)
+            idx.append(ext + ra)
+            blocks.append(A)
+            rhs_parts.append(rhs)
+        return np.concatenate(idx), np.concatenate(blocks), np.concatenate(rhs_parts)
 
     def coulomb_rhs(self, a):
         """(1/eps_a) sum_k q_k / (4 pi |c_i - r_k|) at the centroids of body a (Eq. 5, G2)."""

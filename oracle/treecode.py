@@ -44,7 +44,7 @@ import math
 import numpy as np
 
 from .bem import DIELECTRIC, SET_CHARGE, System
-from .geometry import rigid_transform
+from .geometry import Panels, rigid_transform
 from .integrals import kernel_terms, panel_operator_blocks
 
 FOUR_PI = 4.0 * math.pi
@@ -194,9 +194,14 @@ def truncated_kernel(R, d, p, kappa, P, laplace):
 
 
 class TreecodeOperator:
-    """Treecode matvec of a System (same rows as System.apply)."""
+    """Treecode matvec of a System (same rows as System.apply).
 
-    def __init__(self, sys: System, theta=None, P=None):
+    groups: optional indices of target groups (numbered over the bodies in
+    order, group_size targets each in Morton order) to which the product is
+    restricted; apply() then returns NaN in the rows of every other target.
+    The lists, corrections and sums of the kept targets are unchanged."""
+
+    def __init__(self, sys: System, theta=None, P=None, groups=None):
         self.sys = sys
         p = sys.p
         self.theta = p.theta if theta is None else theta
@@ -209,6 +214,12 @@ class TreecodeOperator:
                 idx = tr.perm[g0:g0 + p.group_size]
                 x = pn.c[idx]
                 self.groups.append((a, idx, x.min(0), x.max(0)))
+        self.rows = None
+        if groups is not None:
+            self.groups = [self.groups[g] for g in groups]
+            self.rows = [np.zeros(pn.N, dtype=bool) for pn in sys.panels]
+            for a, idx, _, _ in self.groups:
+                self.rows[a][idx] = True
         self.lists = {}
         for gi, (a, idx, lo, hi) in enumerate(self.groups):
             for b, tr in enumerate(self.trees):
@@ -221,13 +232,15 @@ class TreecodeOperator:
         p = sys.p
         self.corr = {}
         for a, pa in enumerate(sys.panels):
+            rows = np.arange(pa.N) if self.rows is None else np.nonzero(self.rows[a])[0]
             for b, pb in enumerate(sys.panels):
-                dc = pa.c[:, None, :] - pb.c[None, :, :]
+                dc = pa.c[rows][:, None, :] - pb.c[None, :, :]
                 d2 = np.einsum("ijk,ijk->ij", dc, dc)
                 near = d2 < 8.0 * pb.A[None, :]
                 if a == b:
-                    near[np.arange(pa.N), np.arange(pa.N)] = True
+                    near[np.arange(len(rows)), rows] = True
                 ii, jj = np.nonzero(near)
+                ii = rows[ii]
                 vals = np.zeros((len(ii), 4))
                 for t, (i, j) in enumerate(zip(ii, jj)):
                     tier = panel_operator_blocks(pa.c[i:i + 1], _Sub(pb, j), sys.kappa, p.K, p.K_near,
@@ -305,6 +318,11 @@ class TreecodeOperator:
             else:
                 (u,) = sys.blocks(x, a)
                 out[o:o + N] = UY[a] + (0.5 * u if ba.kind == SET_CHARGE else 0.0)
+        if self.rows is not None:
+            for a, ba in enumerate(sys.bodies):
+                o, N = sys.offsets[a], sys.panels[a].N
+                for k in range(2 if ba.kind == DIELECTRIC else 1):
+                    out[o + k * N:o + (k + 1) * N][~self.rows[a]] = np.nan
         return out
 
 
@@ -321,5 +339,5 @@ class _Sub:
         self._pn, self._j = pn, j
 
     def points(self, K):
-        y, w = self._pn.points(K)
-        return y[self._j:self._j + 1], w[self._j:self._j + 1]
+        # the rule of Panels.points applied to this one panel
+        return Panels.points(self, K)

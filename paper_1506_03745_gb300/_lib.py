@@ -73,6 +73,7 @@ _SIGS = {
     "pgb_set_region": (c_i32, [c_vp, c_i32, c_i32, c_dbl]),
     "pgb_tree_build": (c_i32, [c_vp]),
     "pgb_tree_reset": (c_i32, [c_vp]),
+    "pgb_tree_refresh": (c_i32, [c_vp]),
     "pgb_tree_stats": (c_i32, [c_vp, ctypes.POINTER(pgb_tree_info)]),
     "pgb_num_unknowns": (c_i32, [c_vp, ctypes.POINTER(c_i64)]),
     "pgb_matvec": (c_i32, [c_vp, c_vp, c_vp, c_i32]),
@@ -88,6 +89,7 @@ _SIGS = {
     "pgb_timing": (c_i32, [c_vp, c_i32, ctypes.POINTER(pgb_stage_times)]),
     "pgb_energy_noalloc": (c_i32, [c_vp, c_vp, ctypes.POINTER(pgb_energies)]),
     "pgb_math_check": (c_i32, [c_vp, c_i64, c_vp]),
+    "pgb_alloc_count": (c_i32, [ctypes.POINTER(c_i64)]),
 }
 
 
@@ -212,6 +214,10 @@ def pgb_tree_build(ctx):
 
 def pgb_tree_reset(ctx):
     return _check(ctx, lib().pgb_tree_reset(ctx))
+
+
+def pgb_tree_refresh(ctx):
+    return _check(ctx, lib().pgb_tree_refresh(ctx))
 
 
 def pgb_tree_stats(ctx):
@@ -348,3 +354,11 @@ def pgb_math_check(x):
     out = np.zeros((len(x), 7), np.float64)
     _check(None, lib().pgb_math_check(x.ctypes.data_as(c_vp), len(x), out.ctypes.data_as(c_vp)))
     return out
+
+
+def pgb_alloc_count():
+    """Allocations libpgb has made in this process so far (device buffers and
+    pinned host buffers); two reads around a call show whether it allocated."""
+    n = c_i64()
+    _check(None, lib().pgb_alloc_count(ctypes.byref(n)))
+    return int(n.value)

@@ -39,10 +39,13 @@ class FreeEnergy:
     """Differentiable total free energy of a loaded context.
 
     kinds: list of body kinds (L.PGB_DIELECTRIC, ...), n_charges: list of the
-    charge counts per body, R: optional list of per-body rotations."""
+    charge counts per body, R: optional list of per-body rotations.
+    frozen_lists: after the first forward, later forwards keep its
+    interaction lists (pgb_tree_refresh instead of pgb_tree_build), so that
+    finite differences in t see no change of the near/far split."""
 
     def __init__(self, ctx, kinds, n_charges, R=None, mode=L.PGB_FP32_REFINE, tol=1e-6,
-                 grad_precision=L.PGB_FP32, grad_tol=1e-6, max_iter=2000, restart=100):
+                 grad_precision=L.PGB_FP32, grad_tol=1e-6, max_iter=2000, restart=100, frozen_lists=False):
         self.ctx = ctx
         self.kinds = list(kinds)
         self.nq = list(n_charges)
@@ -50,6 +53,7 @@ class FreeEnergy:
         self.mode, self.tol = mode, tol
         self.gp, self.gtol = grad_precision, grad_tol
         self.max_iter, self.restart = max_iter, restart
+        self.frozen, self._built = frozen_lists, False
 
     def __call__(self, q, bc, t):
         return _FreeEnergy.apply(self, q, bc, t)
@@ -63,7 +67,11 @@ class FreeEnergy:
             elif kind != L.PGB_DIELECTRIC:
                 L.pgb_set_bc(self.ctx, b, bc[b])
             L.pgb_set_pose(self.ctx, b, self.R[b], t[b])
-        L.pgb_tree_build(self.ctx)
+        if self.frozen and self._built:
+            L.pgb_tree_refresh(self.ctx)
+        else:
+            L.pgb_tree_build(self.ctx)
+            self._built = True
         x = torch.empty(L.pgb_num_unknowns(self.ctx), dtype=torch.float64, device="cuda")
         code, st = L.pgb_solve(self.ctx, self.mode, self.tol, self.max_iter, self.restart, x)
         if code != L.PGB_OK:

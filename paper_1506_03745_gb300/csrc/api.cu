@@ -14,6 +14,8 @@
 namespace pgb {
 thread_local cudaStream_t g_alloc_stream = nullptr;
 thread_local bool g_alloc_scoped = false;
+static std::atomic<int64_t> g_alloc_count{0};
+void note_alloc() { g_alloc_count.fetch_add(1, std::memory_order_relaxed); }
 void cuda_check(cudaError_t e, const char* what) {
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
@@ -243,6 +245,7 @@ static void ensure_lanes(pgb_ctx* c, int L, int32_t body_id) {
             l->eps_out = c->eps_out;
             l->kappa = c->kappa;
             l->bodies = c->bodies;
+            note_alloc();
             if (cudaStreamCreateWithFlags(&l->stream, cudaStreamNonBlocking) != cudaSuccess ||
                 cudaMallocHost(&l->h_pinned, 64) != cudaSuccess) {
                 (void)cudaGetLastError();
@@ -381,6 +384,7 @@ int pgb_create(pgb_ctx** out, const pgb_params* p, void* stream) {
     if (q.batch == 0) q.batch = 1;
     c->p = q;
     c->stream = (cudaStream_t)stream;
+    note_alloc();
     if (cudaMallocHost(&c->h_pinned, 64) != cudaSuccess) {
         (void)cudaGetLastError();
         delete c;
@@ -470,6 +474,7 @@ int pgb_mesh_load(pgb_ctx* c, int32_t kind, const double* verts, int64_t nv, con
         ++c->config_gen;
         c->tree_valid = false;
         c->order_valid = false;
+        c->lists_valid = false;
         c->intra_valid = false;
         if (body_id_out) *body_id_out = (int32_t)c->bodies.size() - 1;
         return PGB_OK;
@@ -580,9 +585,24 @@ int pgb_tree_build(pgb_ctx* c) {
     });
 }
 
+int pgb_tree_refresh(pgb_ctx* c) {
+    if (!c) return PGB_EINVAL;
+    return guard(c, [&]() -> int {
+        if (!c->order_valid || !c->lists_valid)
+            fail(PGB_ESTATE, "pgb_tree_refresh needs a tree built by pgb_tree_build for the loaded bodies");
+        StageTimer tm(c, PGB_STAGE_TREE);
+        build_geometry(c);
+        refresh_lists(c);
+        build_corrections(c);
+        c->tree_valid = true;
+        return PGB_OK;
+    });
+}
+
 int pgb_tree_reset(pgb_ctx* c) {
     if (!c) return PGB_EINVAL;
     c->order_valid = false;
+    c->lists_valid = false;
     c->intra_valid = false;
     c->tree_valid = false;
     c->adj_valid = false;
@@ -825,6 +845,7 @@ int pgb_autotune(pgb_ctx* c, const double* thetas, int32_t n_theta, const int32_
             const bool tree_changes = cd.p.leaf_size != c->p.leaf_size;
             c->p = cd.p;
             if (tree_changes) c->order_valid = false;
+            if (tree_changes) c->lists_valid = false;
             c->tree_valid = false;
             PGB_CUDA(cudaEventRecord(e0, c->stream));
             int r = pgb_tree_build(c);
@@ -866,6 +887,7 @@ int pgb_autotune(pgb_ctx* c, const double* thetas, int32_t n_theta, const int32_
         const bool tree_changes = cands[best].p.leaf_size != c->p.leaf_size;
         c->p = cands[best].p;
         if (tree_changes) c->order_valid = false;
+        if (tree_changes) c->lists_valid = false;
         c->tree_valid = false;
         int r = pgb_tree_build(c);
         if (r != PGB_OK) fail(r, c->err);
@@ -947,6 +969,8 @@ int pgb_math_check(const double* x, int64_t n, double* out) {
     if (n == 0) return PGB_OK;
     double *dx = nullptr, *dy = nullptr;
     int rc = PGB_OK;
+    pgb::note_alloc();
+    pgb::note_alloc();
     if (cudaMalloc(&dx, 8 * n) != cudaSuccess || cudaMalloc(&dy, 56 * n) != cudaSuccess) rc = PGB_ECUDA;
     if (rc == PGB_OK && cudaMemcpy(dx, x, 8 * n, cudaMemcpyHostToDevice) != cudaSuccess) rc = PGB_ECUDA;
     if (rc == PGB_OK) {
@@ -958,6 +982,12 @@ int pgb_math_check(const double* x, int64_t n, double* out) {
     cudaFree(dx);
     cudaFree(dy);
     return rc;
+}
+
+int pgb_alloc_count(int64_t* n) {
+    if (!n) return PGB_EINVAL;
+    *n = pgb::g_alloc_count.load(std::memory_order_relaxed);
+    return PGB_OK;
 }
 
 }  // extern "C"

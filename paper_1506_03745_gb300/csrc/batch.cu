@@ -402,6 +402,7 @@ static pgb_ctx* ensure_union(pgb_ctx* c, const std::vector<pgb_ctx*>& src) {
     }
     u->prob_first.push_back((int)u->bodies.size());
     u->n_prob = (int)src.size();
+    note_alloc();
     if (cudaStreamCreateWithFlags(&u->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMallocHost(&u->h_pinned, 64) != cudaSuccess) {
         (void)cudaGetLastError();

@@ -330,8 +330,11 @@ static double* energy_scratch() {
     return g_scratch_ptr[dev];
 }
 
-// Same kernels and arithmetic as energies(); every buffer is either the
-// context's or the static scratch, and the host side uses only stack arrays.
+// The solvation energy is summed per charge here (phi_reac at every charge,
+// k_phi_reac, then the per-body sums), whereas energies() sums over the
+// per-panel charge weights it caches; the two orders agree to rounding.
+// Every buffer is either the context's or the static scratch, and the host
+// side uses only stack arrays.
 void energies_noalloc(pgb_ctx* c, const double* x, pgb_energies* e) {
     if (!c->tree_valid) fail(PGB_ESTATE, "pgb_tree_build has not run");
     if (c->n_q > PGB_NOALLOC_MAX_CHARGES)

@@ -34,6 +34,9 @@ void fail(int code, const std::string& msg);
 // duration of a library call on a context).
 extern thread_local cudaStream_t g_alloc_stream;
 extern thread_local bool g_alloc_scoped;
+// Allocations the library has made in this process (device buffers and
+// pinned host buffers), reported by pgb_alloc_count.
+void note_alloc();
 struct AllocScope {
     cudaStream_t prev_stream;
     bool prev_scoped;
@@ -86,6 +89,7 @@ struct DBuf {  // owning device buffer
             (void)cudaGetLastError();
             fail(PGB_ENOMEM, "cudaMalloc of " + std::to_string(c * sizeof(T)) + " bytes failed");
         }
+        note_alloc();
         n = c;
     }
     operator T*() const { return p; }
@@ -170,6 +174,7 @@ struct pgb_ctx {
     std::vector<pgb::Body> bodies;
     bool tree_valid = false;
     bool order_valid = false;  // Morton order / octree structure (body frame)
+    bool lists_valid = false;  // interaction lists of the current order (pgb_tree_refresh keeps them)
     int64_t n_pan = 0, n_unk = 0, n_q = 0, n_verts = 0;
 
     // inputs on the device
@@ -361,6 +366,7 @@ void upload_bodies(pgb_ctx* c);
 void build_order(pgb_ctx* c);
 void build_geometry(pgb_ctx* c);
 void build_lists(pgb_ctx* c);
+void refresh_lists(pgb_ctx* c);
 void make_lists(pgb_ctx* c, const double* r2, const double* glo, const double* ghi, DBuf<int64_t>& noff,
                 DBuf<int32_t>& nearl, DBuf<int64_t>& foff, DBuf<int32_t>& farl, DBuf<float4>& near4,
                 DBuf<float4>& far4, int64_t& n_near, int64_t& n_far, unsigned long long* stats4);

@@ -87,7 +87,10 @@ void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t
         }
     };
     static thread_local Slot slot;
-    if (!slot.p) PGB_CUDA(cudaMalloc(&slot.p, sizeof(int64_t)));
+    if (!slot.p) {
+        note_alloc();
+        PGB_CUDA(cudaMalloc(&slot.p, sizeof(int64_t)));
+    }
     int64_t* tot = slot.p;
     k_scan_i64<<<1, 1024, 0, s>>>(in, out, n, tot);
     PGB_CUDA(cudaGetLastError());
@@ -1177,6 +1180,26 @@ void build_lists(pgb_ctx* c) {
         PGB_CUDA(cudaStreamSynchronize(s));
     }
     PGB_LAUNCHED(c, 4);
+    c->lists_valid = true;
+}
+
+// Offsets of the kept list entries and P2P tiles after the node and group
+// centres moved (pgb_tree_refresh): entries, tiles and work items stay.
+void refresh_lists(pgb_ctx* c) {
+    cudaStream_t s = c->stream;
+    const int64_t ng = c->n_groups;
+    if (ng == 0) return;
+    k_list_offsets<<<(unsigned)ng, 64, 0, s>>>(ng, c->d_near_off, c->d_near, c->d_node_center, c->d_group_center,
+                                               c->d_near4);
+    k_list_offsets<<<(unsigned)ng, 64, 0, s>>>(ng, c->d_far_off, c->d_far, c->d_node_center, c->d_group_center,
+                                               c->d_far4);
+    k_tile_fill<<<nblk(32 * ng, 128), 128, 0, s>>>(ng, c->d_near_off, c->d_near, c->d_near4, c->d_node_start,
+                                                   c->d_node_end, c->d_node_body, c->d_group_start, c->d_group_end,
+                                                   c->d_group_body, body_dev(c), c->p.K, c->d_tile_off, c->d_tile_d,
+                                                   c->d_tile_m);
+    PGB_CUDA(cudaGetLastError());
+    PGB_CUDA(cudaStreamSynchronize(s));
+    PGB_LAUNCHED(c, 3);
 }
 
 // ---------------------------------------------------------------- corrections

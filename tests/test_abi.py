@@ -69,3 +69,10 @@ def test_math_check_argument_errors(libpgb):
     assert lib.pgb_math_check(None, -1, None) == L.PGB_EINVAL
     assert lib.pgb_math_check(None, 4, None) == L.PGB_EINVAL
     assert lib.pgb_math_check(None, 0, None) == L.PGB_OK
+
+
+def test_alloc_count_needs_no_device(libpgb):
+    import paper_1506_03745_gb300._lib as L
+    lib = L.lib()
+    assert lib.pgb_alloc_count(None) == L.PGB_EINVAL
+    assert L.pgb_alloc_count() >= 0

@@ -141,24 +141,73 @@ def test_gradients_match_dense_adjoint(kind):
         pgb.pgb_destroy(ctx)
 
 
-def test_translation_gradient_matches_finite_differences_treecode():
+def _fd_translation(ctx, bodies, h, frozen):
+    """Central differences of the total energy in the surface's translation;
+    frozen: the interaction lists of the base pose are kept (reading G20)."""
+    t0 = np.asarray(bodies[1]["t"])
+    fd = np.zeros(3)
+    for ax in range(3):
+        f = []
+        for sgn in (1, -1):
+            tt = t0.copy()
+            tt[ax] += sgn * h
+            pgb.pgb_set_pose(ctx, 1, np.eye(3), tt)
+            if frozen:
+                pgb.pgb_tree_refresh(ctx)
+            else:
+                pgb.pgb_tree_build(ctx)
+            f.append(pgb.pgb_energy(ctx, _solve(ctx))["total"])
+        fd[ax] = (f[0] - f[1]) / (2 * h)
+    pgb.pgb_set_pose(ctx, 1, np.eye(3), t0)
+    return fd
+
+
+@pytest.mark.parametrize("theta,P", [(0.0, 6), (0.5, 8)])
+def test_translation_gradient_matches_finite_differences(theta, P):
+    """dF/dt of the adjoint (FP64) against central differences with h = 1e-3 A,
+    within 1e-4 of the gradient's norm: the direct sum, and the treecode with
+    the lists of the base pose held for the displaced solves."""
     bodies = _bodies("sigma", nu=6, level=3)
-    ctx = gpu_context(bodies, theta=0.5, P=6, leaf_size=16)
+    ctx = gpu_context(bodies, theta=theta, P=P, leaf_size=16)
     try:
+        if theta > 0:
+            assert pgb.pgb_tree_stats(ctx)["n_far"] > 0
         x = _solve(ctx)
+        code, dq, dbc, dt, st = pgb.pgb_grad(ctx, x, 6, 2, pgb.PGB_FP64, 1e-11, 2000, 100)
+        assert code == 0
+        fd = _fd_translation(ctx, bodies, 1e-3, frozen=theta > 0)
+        assert np.abs(dt[1] - fd).max() <= 1e-4 * np.linalg.norm(fd)
+        # the refreshed tree at the base pose gives the base solution back
+        pgb.pgb_tree_refresh(ctx)
+        assert pgb.pgb_energy(ctx, _solve(ctx))["total"] == pytest.approx(pgb.pgb_energy(ctx, x)["total"], rel=1e-10)
+    finally:
+        pgb.pgb_destroy(ctx)
+
+
+def test_translation_gradient_fp32_adjoint():
+    """The FP32 adjoint of the FP32 + refinement solve, the same differences
+    (treecode, lists held) within 1e-4 of the gradient's norm."""
+    bodies = _bodies("sigma", nu=6, level=3)
+    ctx = gpu_context(bodies, theta=0.5, P=8, leaf_size=16)
+    try:
+        n = pgb.pgb_num_unknowns(ctx)
+        x = torch.empty(n, dtype=torch.float64, device="cuda")
+        code, _ = pgb.pgb_solve(ctx, pgb.PGB_FP32_REFINE, 1e-9, 3000, 100, x)
+        assert code == 0
         code, dq, dbc, dt, st = pgb.pgb_grad(ctx, x, 6, 2, pgb.PGB_FP32, 1e-6, 2000, 100)
         assert code == 0
-        h = 1e-3
-        t0 = np.asarray(bodies[1]["t"])
-        for ax in range(3):
-            f = []
-            for sgn in (1, -1):
-                tt = t0.copy()
-                tt[ax] += sgn * h
-                pgb.pgb_set_pose(ctx, 1, np.eye(3), tt)
-                pgb.pgb_tree_build(ctx)
-                f.append(pgb.pgb_energy(ctx, _solve(ctx))["total"])
-            fd = (f[0] - f[1]) / (2 * h)
-            assert dt[1, ax] == pytest.approx(fd, rel=1e-3, abs=2e-5)
+        fd = _fd_translation(ctx, bodies, 1e-3, frozen=True)
+        assert np.abs(dt[1] - fd).max() <= 1e-4 * np.linalg.norm(fd)
+    finally:
+        pgb.pgb_destroy(ctx)
+
+
+def test_refresh_needs_a_built_tree():
+    bodies = _bodies("sigma")
+    ctx = gpu_context(bodies, theta=0.5, build=False)
+    try:
+        with pytest.raises(pgb.PgbError) as ei:
+            pgb.pgb_tree_refresh(ctx)
+        assert ei.value.code == pgb.PGB_ESTATE
     finally:
         pgb.pgb_destroy(ctx)

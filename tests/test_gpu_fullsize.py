@@ -1,13 +1,16 @@
 """The benchmark workload at full size (two spheres, 2 x 20480 panels,
 theta 0.5, P 6, leaf 32, K 7) in the launch configuration bench.py times:
-sampled rows against the oracle's direct sum, FP32 against FP64, and the
-solve's energies against the dense/analytical expectations."""
+sampled rows against the oracle's direct sum, eight sampled target groups
+against the oracle's treecode row by row (FP32 and FP64), FP32 against FP64,
+and the solve's energies against the dense/analytical expectations."""
+import os
+
 import numpy as np
 import pytest
 
 from oracle.analytical import interaction
 from oracle import units
-from problems import gpu_context, oracle_system
+from problems import fullsize_vectors, gpu_context, oracle_system
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -49,6 +52,55 @@ def test_sampled_rows_match_direct_sum(full):
         blocks = [y[pgb.PGB_FP64][off + k * N + rows] for k in range(len(ref))]
         for got, want in zip(blocks, ref):
             assert np.abs(got - want).max() / np.abs(want).max() < 5e-4
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fullsize_rows.txt")
+
+
+def _golden_rows():
+    out = {}
+    for line in open(GOLDEN):
+        if line.startswith("#"):
+            continue
+        name, i, v = line.split()
+        out.setdefault(name, ([], []))
+        out[name][0].append(int(i))
+        out[name][1].append(float(v))
+    return {k: (np.array(a), np.array(b)) for k, (a, b) in out.items()}
+
+
+# bounds on |GPU - oracle treecode| per sampled row: the FP64 product carries
+# only rounding (1e-11); the FP32 one the FP32 kernels' rounding (SFU
+# rsqrt/ex2 to about 2^-22, FP32 moments and recurrences) on every term
+ROW_TOL = {"fp64": 1e-11, "fp32": 2e-6}
+
+
+def test_sampled_groups_match_oracle_treecode_row_by_row(full):
+    """Eight target groups (256 targets; tests/golden/fullsize_rows.txt from
+    make_fullsize_rows.py, oracle/ only).  Positive densities: every row is a
+    sum of terms of one sign (up to the near-field corrections), so each row
+    is held to a relative bound of its own.  Normal densities: rows with
+    cancellation, held relative to the largest sampled row of their block."""
+    bodies, ctx = full
+    n = pgb.pgb_num_unknowns(ctx)
+    N = 20480
+    ref = _golden_rows()
+    vecs = fullsize_vectors(n)
+    for name, (idx, want) in ref.items():
+        assert len(idx) == 8 * 32 * 3 // 2          # 4 molecule groups x 2 rows + 4 surface groups
+        for prec, dt, key in ((pgb.PGB_FP32, torch.float32, "fp32"), (pgb.PGB_FP64, torch.float64, "fp64")):
+            xt = torch.tensor(vecs[name], dtype=dt, device="cuda")
+            yt = torch.empty_like(xt)
+            pgb.pgb_matvec(ctx, xt, yt, prec)
+            torch.cuda.synchronize()
+            got = yt.double().cpu().numpy()[idx]
+            err = np.abs(got - want)
+            if name == "positive":
+                assert np.all(err <= ROW_TOL[key] * np.abs(want)), (key, (err / np.abs(want)).max())
+            else:
+                for lo, hi in ((0, N), (N, 2 * N), (2 * N, 3 * N)):
+                    blk = (idx >= lo) & (idx < hi)
+                    assert np.all(err[blk] <= ROW_TOL[key] * np.abs(want[blk]).max()), (key, lo)
 
 
 def test_full_size_solve_energy_is_close_to_analytical(full):

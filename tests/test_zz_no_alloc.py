@@ -49,6 +49,25 @@ def test_noalloc_energy_matches_pgb_energy_twice(which):
         pgb.pgb_destroy(ctx)
 
 
+def test_noalloc_energy_makes_no_allocation():
+    """The library's allocation counter does not move across calls of the
+    no-alloc entry point (after its first call on the device, which only looks
+    up the static array's address), while a tree rebuild does move it."""
+    ctx, x = _solved(spheres(kind="sigma", level_mol=2, level_srf=2))
+    try:
+        pgb.pgb_energy_noalloc(ctx, x)
+        n0 = pgb.pgb_alloc_count()
+        for _ in range(3):
+            pgb.pgb_energy_noalloc(ctx, x)
+        torch.cuda.synchronize()
+        assert pgb.pgb_alloc_count() == n0
+        pgb.pgb_tree_reset(ctx)
+        pgb.pgb_tree_build(ctx)
+        assert pgb.pgb_alloc_count() > n0
+    finally:
+        pgb.pgb_destroy(ctx)
+
+
 def test_noalloc_rejects_too_many_charges():
     import synth
     v, f = synth.icosphere(1, 20.0)
