@@ -75,19 +75,16 @@ def p2p_flops(laplace):
 
 
 def m2p_flops(P, laplace):
-    """Operations per (target, far node) of the Taylor recurrences and the
-    contraction with the moments, counted term by term."""
-    terms = [(x, y, n - x - y) for n in range(P + 1) for x in range(n, -1, -1) for y in range(n - x, -1, -1)]
-    yuk = 3 + 5 + 1 + 1 + 1 + 2 + 1 + 1   # R, r^2, rsqrt, 1/r^2, rho, exp, G0, G0*M0
-    lap = 1
-    for k in terms[1:]:
-        a1 = sum(1 for c in k if c >= 1)
-        a2 = sum(1 for c in k if c >= 2)
-        s1 = 2 * a1 - 1
-        s2 = max(a2 - 1, 0)
-        yuk += 2 * s1 + 2 * s2 + (1 if a2 else 0) + 1 + 1 + (2 if a2 else 0) + (1 if a2 else 0) + 2 + 1 + 2
-        lap += s1 + s2 + 1 + (2 if a2 else 0) + 1 + 2
-    return yuk + (lap if laplace else 0)
+    """Operations per (target, far node) of the far-field evaluation as the
+    kernel runs it (far_eval: monomials of S = R/r^2 in nested order, one
+    product each, summed per degree against the node's coefficients), counted
+    term by term: setup 22 (R 3, r^2 5, rsqrt 1, 1/r^2 1, S 3, r 1, x 1, x^2 1,
+    g_1 1, exp 1, prefactor 2, final product 2), T - 1 monomial products,
+    2 per Yukawa multiply-add, the radial factors g_p (3 each for p >= 2) and
+    their multiply-adds (2 each for p >= 1); Laplace adds 2 per term and 1."""
+    T = (P + 1) * (P + 2) * (P + 3) // 6
+    yuk = 22 + (T - 1) + 2 * T + 2 * min(P, 1) + 5 * max(P - 1, 0)
+    return yuk + ((2 * T + 1) if laplace else 0)
 
 
 def p2p_kernel_flops(info):

@@ -365,6 +365,22 @@ int pgb_tree_export(struct pgb_ctx* ctx, int32_t* perm, int64_t* near_off, int32
  * NULL pointer with n > 0; PGB_ECUDA on a CUDA error. */
 int pgb_math_check(const double* x, int64_t n, double* out);
 
+/* Diagnostic: the host-computed table that turns a node's Taylor moments
+ * (Section 3.2) into the coefficients its far field is evaluated from, for
+ * order P (0..8) and screening kappa >= 0.  With T = (P+1)(P+2)(P+3)/6, out
+ * (host, n = 2 T^2 doubles) receives the Yukawa table then the Laplace
+ * table, each T x T row-major: row = coefficient of S^(a,b,c), S = R/|R|^2,
+ * in the order a = 0..P, b = 0..P-a, c = 0..P-a-b; column = moment M_k with
+ * k in the graded order (total degree, then k_x and k_y descending).  The
+ * far field at R from the node centre is
+ *   U_Y = e^{-kappa r}/r sum_p g_p(kappa r) sum_{a+b+c=p} Y[.][k] M_k S^(a,b,c),
+ *   U_L = 1/r sum L[.][k] M_k S^(a,b,c),
+ * g_0 = 1, g_1 = -(1+x), g_p = x^2 g_{p-2} - (2p-1) g_{p-1} (the sum over
+ * k of G_k(R) M_k with G_k the Taylor coefficients of e^{-kappa r}/r or 1/r,
+ * without the 1/(4 pi)).  No device call; PGB_EINVAL for a bad P, kappa,
+ * pointer or n. */
+int pgb_far_table(int32_t P, double kappa, double* out, int64_t n);
+
 /* Diagnostic: *n receives the number of memory allocations libpgb has made
  * in this process so far (device buffers, stream-ordered or not, and pinned
  * host buffers).  No context and no device call; PGB_EINVAL for n = NULL.

@@ -90,6 +90,7 @@ _SIGS = {
     "pgb_energy_noalloc": (c_i32, [c_vp, c_vp, ctypes.POINTER(pgb_energies)]),
     "pgb_math_check": (c_i32, [c_vp, c_i64, c_vp]),
     "pgb_alloc_count": (c_i32, [ctypes.POINTER(c_i64)]),
+    "pgb_far_table": (c_i32, [c_i32, c_dbl, c_vp, c_i64]),
 }
 
 
@@ -362,3 +363,11 @@ def pgb_alloc_count():
     n = c_i64()
     _check(None, lib().pgb_alloc_count(ctypes.byref(n)))
     return int(n.value)
+
+
+def pgb_far_table(P, kappa):
+    """(Yukawa, Laplace) far-field tables (T x T each) for order P and kappa."""
+    T = (P + 1) * (P + 2) * (P + 3) // 6
+    out = np.zeros(2 * T * T)
+    _check(None, lib().pgb_far_table(P, float(kappa), out.ctypes.data_as(c_vp), len(out)))
+    return out[:T * T].reshape(T, T), out[T * T:].reshape(T, T)

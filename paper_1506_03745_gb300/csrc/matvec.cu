@@ -7,10 +7,10 @@
 namespace pgb {
 
 void treecode_launch_f32(int stage, int P, const UpArgs& up, const std::vector<int64_t>& lv, const EvalArgs& ev,
-                         const void* src, const void* xrel, void* mom, cudaStream_t s);
+                         const void* src, const void* xrel, void* mom, void* far, cudaStream_t s);
 void treecode_launch_f64(int stage, int P, const UpArgs& up, const std::vector<int64_t>& lv, const EvalArgs& ev,
-                         const void* src, const void* xrel, void* mom, cudaStream_t s);
-void treecode_launch_ds(int stage, int P, const EvalArgs& ev, const void* src, const void* xrel, const void* mom,
+                         const void* src, const void* xrel, void* mom, void* far, cudaStream_t s);
+void treecode_launch_ds(int stage, int P, const EvalArgs& ev, const void* src, const void* xrel, const void* far,
                         cudaStream_t s);
 
 static inline int nblk(int64_t n, int t) { return (int)std::max<int64_t>(1, (n + t - 1) / t); }
@@ -314,7 +314,7 @@ void apply_full(pgb_ctx* c, const double* x, double* y, int precision) { apply_m
 static void upward_graph(pgb_ctx* c, bool f32, const UpArgs& up, const EvalArgs& ev, const void* src, void* mom) {
     auto& gr = c->up_graph[f32 ? 0 : 1];
     bool ok = gr.exec && gr.tree_gen == c->tree_gen && gr.src == src && gr.mom == mom && gr.ncenter == up.ncenter &&
-              gr.p2m_grid == up.p2m_grid;
+              gr.p2m_grid == up.p2m_grid && gr.far == up.far && gr.far_tab == up.far_tab;
     for (int b = 0; ok && b < PGB_MAX_BODIES; ++b) ok = gr.src_active[b] == up.src_active[b];
     if (!ok) {
         if (gr.exec) {
@@ -325,8 +325,12 @@ static void upward_graph(pgb_ctx* c, bool f32, const UpArgs& up, const EvalArgs&
         PGB_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
         std::string why;
         try {
-            if (f32) treecode_launch_f32(PGB_STAGE_UPWARD, c->p.P, up, c->level_begin, ev, src, nullptr, mom, c->cap_stream);
-            else treecode_launch_f64(PGB_STAGE_UPWARD, c->p.P, up, c->level_begin, ev, src, nullptr, mom, c->cap_stream);
+            if (f32)
+                treecode_launch_f32(PGB_STAGE_UPWARD, c->p.P, up, c->level_begin, ev, src, nullptr, mom, up.far,
+                                    c->cap_stream);
+            else
+                treecode_launch_f64(PGB_STAGE_UPWARD, c->p.P, up, c->level_begin, ev, src, nullptr, mom, up.far,
+                                    c->cap_stream);
         } catch (const Error& e) {
             why = e.msg;
         }
@@ -347,6 +351,8 @@ static void upward_graph(pgb_ctx* c, bool f32, const UpArgs& up, const EvalArgs&
         gr.tree_gen = c->tree_gen;
         gr.src = src;
         gr.mom = mom;
+        gr.far = up.far;
+        gr.far_tab = up.far_tab;
         gr.ncenter = up.ncenter;
         gr.p2m_grid = up.p2m_grid;
         for (int b = 0; b < PGB_MAX_BODIES; ++b) gr.src_active[b] = up.src_active[b];
@@ -364,13 +370,18 @@ void reserve_product(pgb_ctx* c, int precision) {
     c->d_Up[pi].resize(64 * std::max<int64_t>(c->n_pitems, 1));
     c->d_Uf[pi].resize(64 * std::max<int64_t>(c->n_fitems, 1));
     c->d_work.resize(2);
+    const int TP = n_terms_pad(c->p.P);
     if (pi == 0) {
         c->d_src32.resize(2 * nsrc);
         c->d_mom32.resize((size_t)c->n_nodes * 2 * T);
+        c->d_far32.resize((size_t)c->n_nodes * 2 * TP);
     } else {
         c->d_src64.resize(2 * nsrc);
         c->d_mom64.resize((size_t)c->n_nodes * 2 * T);
+        c->d_far64.resize((size_t)c->n_nodes * 2 * TP);
     }
+    (void)far_table(c, c->kappa);
+    for (const auto& reg : c->regions) (void)far_table(c, reg->dev.kappa);
 }
 
 void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode, const int* known_mask) {
@@ -401,6 +412,7 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
     up.ncenter = c->d_node_center; up.K = c->p.K; up.nbody = c->d_node_body;
     up.lvl_begin = up.lvl_end = 0;
     up.p2m_grid = 0;
+    up.n_nodes = c->n_nodes;
     if (precision != PGB_FP32 && c->persist_blocks > 0)  // side product: P2M on two blocks per SM
         up.p2m_grid = 2 * c->persist_blocks;
     EvalArgs ev;
@@ -448,13 +460,23 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
         ev.persist_blocks = c->persist_blocks;
     }
     const bool f32 = precision == PGB_FP32;
+    const int TP = n_terms_pad(P);
     if (f32) {
         c->d_src32.resize(2 * nsrc);
         c->d_mom32.resize((size_t)c->n_nodes * 2 * T);
+        c->d_far32.resize((size_t)c->n_nodes * 2 * TP);
+        up.far = c->d_far32.p;
     } else {
         c->d_src64.resize(2 * nsrc);
         c->d_mom64.resize((size_t)c->n_nodes * 2 * T);
+        c->d_far64.resize((size_t)c->n_nodes * 2 * TP);
+        up.far = c->d_far64.p;
     }
+    auto tab_for = [&](double kappa) -> const void* {
+        const FarTab& t = far_table(c, kappa);
+        return f32 ? (const void*)t.t32.p : (const void*)t.t64.p;
+    };
+    up.far_tab = tab_for(c->kappa);
     if (nested(c)) {
         // one treecode pass per region: rows from the jump terms, then each
         // region's sum subtracted from the rows on its boundary
@@ -465,6 +487,7 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
         for (const auto& reg : c->regions) {
             const RegionDev& rd = reg->dev;
             ev.kappa = rd.kappa;
+            up.far_tab = tab_for(rd.kappa);
             if (ev.p2p_work)  // persistent launches take items from counters: fresh ones per pass
                 PGB_CUDA(cudaMemsetAsync(c->d_work.p, 0, 16, s));
             ev.all_active = 1;
@@ -487,12 +510,16 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
             }
             for (int stage : {PGB_STAGE_UPWARD, PGB_STAGE_P2P, PGB_STAGE_M2P}) {
                 StageTimer tm(c, stage + (f32 ? 0 : PGB_STAGE_FP64));
-                if (f32) treecode_launch_f32(stage, P, up, c->level_begin, ev, c->d_src32, c->d_x32, c->d_mom32, s);
+                if (f32)
+                    treecode_launch_f32(stage, P, up, c->level_begin, ev, c->d_src32, c->d_x32, c->d_mom32,
+                                        c->d_far32, s);
                 else if (precision == PGB_FP64_DS && stage != PGB_STAGE_UPWARD)
-                    treecode_launch_ds(stage, P, ev, c->d_src64, c->d_x64, c->d_mom64, s);
-                else treecode_launch_f64(stage, P, up, c->level_begin, ev, c->d_src64, c->d_x64, c->d_mom64, s);
+                    treecode_launch_ds(stage, P, ev, c->d_src64, c->d_x64, c->d_far64, s);
+                else
+                    treecode_launch_f64(stage, P, up, c->level_begin, ev, c->d_src64, c->d_x64, c->d_mom64,
+                                        c->d_far64, s);
                 PGB_CUDA(cudaGetLastError());
-                PGB_LAUNCHED(c, stage == PGB_STAGE_UPWARD ? (int64_t)c->level_begin.size() - 2 : 1);
+                PGB_LAUNCHED(c, stage == PGB_STAGE_UPWARD ? (int64_t)c->level_begin.size() : 1);
             }
             {
                 StageTimer tm(c, PGB_STAGE_ASSEMBLE + (f32 ? 0 : PGB_STAGE_FP64));
@@ -527,12 +554,14 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
         if (stage == PGB_STAGE_UPWARD && c->p.graphs)
             upward_graph(c, f32, up, ev, f32 ? (const void*)c->d_src32.p : (const void*)c->d_src64.p,
                          f32 ? (void*)c->d_mom32.p : (void*)c->d_mom64.p);
-        else if (f32) treecode_launch_f32(stage, P, up, c->level_begin, ev, c->d_src32, c->d_x32, c->d_mom32, s);
+        else if (f32)
+            treecode_launch_f32(stage, P, up, c->level_begin, ev, c->d_src32, c->d_x32, c->d_mom32, c->d_far32, s);
         else if (precision == PGB_FP64_DS && stage != PGB_STAGE_UPWARD)
-            treecode_launch_ds(stage, P, ev, c->d_src64, c->d_x64, c->d_mom64, s);
-        else treecode_launch_f64(stage, P, up, c->level_begin, ev, c->d_src64, c->d_x64, c->d_mom64, s);
+            treecode_launch_ds(stage, P, ev, c->d_src64, c->d_x64, c->d_far64, s);
+        else
+            treecode_launch_f64(stage, P, up, c->level_begin, ev, c->d_src64, c->d_x64, c->d_mom64, c->d_far64, s);
         PGB_CUDA(cudaGetLastError());
-        PGB_LAUNCHED(c, stage == PGB_STAGE_UPWARD ? (int64_t)c->level_begin.size() - 2 : 1);
+        PGB_LAUNCHED(c, stage == PGB_STAGE_UPWARD ? (int64_t)c->level_begin.size() : 1);
     }
     {
         StageTimer tm(c, PGB_STAGE_ASSEMBLE + (f32 ? 0 : PGB_STAGE_FP64));

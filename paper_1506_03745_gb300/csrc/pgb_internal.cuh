@@ -96,7 +96,19 @@ struct DBuf {  // owning device buffer
 };
 
 // Taylor term count of total degree <= P in three variables.
-constexpr int n_terms(int P) { return (P + 1) * (P + 2) * (P + 3) / 6; }
+__host__ __device__ constexpr int n_terms(int P) { return (P + 1) * (P + 2) * (P + 3) / 6; }
+
+// Far-field coefficient tables (farfield.cu) of one Taylor order and
+// screening: moments -> the coefficients the M2P kernels evaluate.
+struct FarTab {
+    int P = -1;
+    double kappa = 0.0;
+    DBuf<double> t64;
+    DBuf<float> t32;
+};
+// padded coefficient count per kernel: rows of 16 bytes for vector loads
+__host__ __device__ constexpr int n_terms_pad(int P) { return (n_terms(P) + 3) & ~3; }
+void far_tables(int P, double kappa, std::vector<double>& tab);
 
 struct Body {
     int kind = PGB_DIELECTRIC;
@@ -262,6 +274,9 @@ struct pgb_ctx {
     pgb::DBuf<double> d_dens[2];            // 3 per sorted panel: psiL, psiY, phi
     pgb::DBuf<float> d_mom32;            // 2*T per node
     pgb::DBuf<double> d_mom64;
+    pgb::DBuf<float> d_far32;            // far-field coefficients: 2 * n_terms_pad(P) per node
+    pgb::DBuf<double> d_far64;
+    std::vector<std::unique_ptr<pgb::FarTab>> far_tabs;  // per (P, kappa)
     pgb::DBuf<double> d_phi_part;        // chunk partial sums of phi_reac (few charges)
     pgb::DBuf<pgb::dbl4> d_qw;           // charge weights per sorted panel (energies): own charges
                                          // (wV, wK), then the enclosing body's (wV, wK)
@@ -293,6 +308,8 @@ struct pgb_ctx {
         uint64_t tree_gen = 0;
         const void* src = nullptr;
         void* mom = nullptr;
+        void* far = nullptr;
+        const void* far_tab = nullptr;
         const double* ncenter = nullptr;
         int p2m_grid = 0;
         int src_active[PGB_MAX_BODIES] = {0};
@@ -366,6 +383,7 @@ void upload_bodies(pgb_ctx* c);
 void build_order(pgb_ctx* c);
 void build_geometry(pgb_ctx* c);
 void build_lists(pgb_ctx* c);
+const FarTab& far_table(pgb_ctx* c, double kappa);
 void refresh_lists(pgb_ctx* c);
 void make_lists(pgb_ctx* c, const double* r2, const double* glo, const double* ghi, DBuf<int64_t>& noff,
                 DBuf<int32_t>& nearl, DBuf<int64_t>& foff, DBuf<int32_t>& farl, DBuf<float4>& near4,

@@ -245,103 +245,76 @@ __device__ __forceinline__ int64_t next_item(unsigned long long* work, int64_t c
     return *slot;
 }
 
-// Far-field contraction sum_k G_k(R) M_k for one target (returns Yukawa and,
-// when lap, Laplace).  Per level n the recurrence constants are folded into
-// a_n = -(2n-1)/(n rho^2), b_n = -(n-1)/(n rho^2), e_n = -kappa/(n rho^2) and
-// h_n = -kappa/n; H is not formed at the last level.
-template <typename real, int P>
-__device__ __forceinline__ void m2p_eval(real Rx, real Ry, real Rz, real kappa, const real* ML, const real* MY,
-                                         bool lap, real& uL, real& uY) {
-    constexpr MI<P> mi{};
-    constexpr int T = MI<P>::T;
-    const real R[3] = {Rx, Ry, Rz};
-    const real r2 = Rx * Rx + Ry * Ry + Rz * Rz;
+// 16-byte vector of the arithmetic type (4 floats, 2 doubles, 2 double-singles),
+// for loads of consecutive coefficients from shared memory.
+template <typename real>
+struct Vec16 {
+    static constexpr int N = 16 / sizeof(real);
+    real v[N];
+};
+
+// Far field of one node at R = target - node centre from its coefficients in
+// the evaluation order (a = 0..P, b = 0..P-a, c = 0..P-a-b for S^(a,b,c)),
+// S = R / r^2 and x = kappa r (the tables of farfield.cu):
+//   U_Y = (e^{-x} / r) sum_p g_p(x) sum_{a+b+c=p} cY_abc S^(a,b,c),
+//   U_L = (1 / r) sum_abc cL_abc S^(a,b,c),
+// g_0 = 1, g_1 = -(1 + x), g_p = x^2 g_{p-2} - (2p - 1) g_{p-1}.  The monomials
+// are formed in nested order, one product each, and summed per degree, so
+// that a term costs one product and one multiply-add per kernel.
+template <typename real, int P, bool LAP>
+__device__ __forceinline__ void far_eval(real Rx, real Ry, real Rz, real kappa, const real* __restrict__ cL,
+                                         const real* __restrict__ cY, real& uL, real& uY) {
+    using V = Vec16<real>;
+    constexpr int VN = V::N;
+    real r2;
+    if constexpr (is_ds<real>) r2 = madd(Rx, Rx, madd(Ry, Ry, Rz * Rz));
+    else r2 = Rx * Rx + Ry * Ry + Rz * Rz;
     const real ri = rsqrt_(r2);
     const real i2 = ri * ri;
-    const real rho = r2 * ri;
-    real an[P + 1], bn[P + 1], en[P + 1], hn[P + 1];
+    const real sx = Rx * i2, sy = Ry * i2, sz = Rz * i2;
+    real acc[P + 1];
 #pragma unroll
-    for (int n = 1; n <= P; ++n) {
-        const real inv_n = inv_int<real>(n);
-        an[n] = -(real(2 * n - 1) * inv_n) * i2;
-        bn[n] = -(real(n - 1) * inv_n) * i2;
-        hn[n] = -kappa * inv_n;
-        en[n] = hn[n] * i2;
-    }
-    real G[T], H[T];
-    H[0] = exp_(-kappa * rho);
-    G[0] = H[0] * ri;
-    real accY = G[0] * MY[0];
+    for (int p = 0; p <= P; ++p) acc[p] = real(0);
+    real aL = real(0);
+    V qy, ql;
+    int idx = 0;
+    real xa = real(1);
 #pragma unroll
-    for (int k = 1; k < T; ++k) {
-        const int n = mi.lvl[k];
-        // S1 = sum_a R_a G_{k-e_a}, S2 = sum_a G_{k-2e_a} (T1, T2 with H); the
-        // parent sets are compile-time, so the sums start at their first term
-        real S1 = 0, S2 = 0, T1 = 0, T2 = 0;
-        bool h1 = false, h2 = false;
+    for (int a = 0; a <= P; ++a) {
+        real xy = xa;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            if (mi.m1[k][a] >= 0) {
-                if (h1) {
-                    S1 = madd(R[a], G[mi.m1[k][a]], S1);
-                    T1 = madd(R[a], H[mi.m1[k][a]], T1);
-                } else {
-                    S1 = R[a] * G[mi.m1[k][a]];
-                    T1 = R[a] * H[mi.m1[k][a]];
-                    h1 = true;
+        for (int b = 0; b <= P - a; ++b) {
+            real t = xy;
+#pragma unroll
+            for (int c = 0; c <= P - a - b; ++c) {
+                if (idx % VN == 0) {
+                    qy = *reinterpret_cast<const V*>(cY + idx);
+                    if (LAP) ql = *reinterpret_cast<const V*>(cL + idx);
                 }
+                acc[a + b + c] = madd(qy.v[idx % VN], t, acc[a + b + c]);
+                if (LAP) aL = madd(ql.v[idx % VN], t, aL);
+                ++idx;
+                if (c < P - a - b) t = t * sz;
             }
-            if (mi.m2[k][a] >= 0) {
-                if (h2) {
-                    S2 += G[mi.m2[k][a]];
-                    T2 += H[mi.m2[k][a]];
-                } else {
-                    S2 = G[mi.m2[k][a]];
-                    T2 = H[mi.m2[k][a]];
-                    h2 = true;
-                }
-            }
+            if (b < P - a) xy = xy * sy;
         }
-        if (h2) {
-            if (n < P) H[k] = hn[n] * (S1 + S2);
-            if constexpr (is_ds<real>) G[k] = madd(an[n], S1, madd(bn[n], S2, en[n] * (T1 + T2)));
-            else G[k] = an[n] * S1 + bn[n] * S2 + en[n] * (T1 + T2);
-        } else {
-            if (n < P) H[k] = hn[n] * S1;
-            if constexpr (is_ds<real>) G[k] = madd(an[n], S1, en[n] * T1);
-            else G[k] = an[n] * S1 + en[n] * T1;
-        }
-        accY = madd(G[k], MY[k], accY);
+        if (a < P) xa = xa * sx;
     }
-    uY = accY;
-    if (lap) {
-        real L[T];
-        L[0] = ri;
-        real accL = L[0] * ML[0];
+    const real r = r2 * ri;
+    const real x = kappa * r;
+    const real x2 = x * x;
+    real u = acc[0];
+    real gm2 = real(1), gm1 = -(x + real(1));
+    if (P >= 1) u = madd(gm1, acc[P >= 1 ? 1 : 0], u);
 #pragma unroll
-        for (int k = 1; k < T; ++k) {
-            const int n = mi.lvl[k];
-            real S1 = 0, S2 = 0;
-            bool h1 = false, h2 = false;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                if (mi.m1[k][a] >= 0) {
-                    S1 = h1 ? madd(R[a], L[mi.m1[k][a]], S1) : R[a] * L[mi.m1[k][a]];
-                    h1 = true;
-                }
-                if (mi.m2[k][a] >= 0) {
-                    S2 = h2 ? S2 + L[mi.m2[k][a]] : L[mi.m2[k][a]];
-                    h2 = true;
-                }
-            }
-            if constexpr (is_ds<real>) L[k] = h2 ? madd(an[n], S1, bn[n] * S2) : an[n] * S1;
-            else L[k] = h2 ? an[n] * S1 + bn[n] * S2 : an[n] * S1;
-            accL = madd(L[k], ML[k], accL);
-        }
-        uL = accL;
-    } else {
-        uL = 0;
+    for (int p = 2; p <= P; ++p) {
+        const real g = madd(x2, gm2, -(real(2 * p - 1) * gm1));
+        u = madd(g, acc[p], u);
+        gm2 = gm1;
+        gm1 = g;
     }
+    uY = (exp_(-x) * ri) * u;
+    uL = LAP ? aL * ri : real(0);
 }
 
 // K-point sums of one tile of source points for one target (relative position
@@ -538,16 +511,17 @@ __global__ void __launch_bounds__(NW * 32) k_p2p(EvalArgs a,
 
 // M2P: one block of NW warps per work item, i.e. up to m2p_item far entries of
 // one target group; the nodes go round robin to the warps with the next
-// node's moments prefetched.  The item's partial sums go to Uf.
+// node's far-field coefficients (k_far_coef) prefetched.  The item's partial
+// sums go to Uf.
 template <typename real, int P, int NW>
 __global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a,
                                                  const typename V4<typename Store<real>::S>::t* __restrict__ xrel,
-                                                 const typename Store<real>::S* __restrict__ mom) {
+                                                 const typename Store<real>::S* __restrict__ far) {
     using S = typename Store<real>::S;  // storage type of the inputs
     using s4 = typename V4<S>::t;
-    constexpr int T = MI<P>::T;
-    constexpr int MW = (2 * T + 31) / 32;  // moment words per lane
-    __shared__ real sM[NW][2 * T];
+    constexpr int TP = n_terms_pad(P);
+    constexpr int MW = (2 * TP + 31) / 32;  // coefficient words per lane
+    __shared__ __align__(16) real sM[NW][2 * TP];
     __shared__ real red[NW][4][32];
     __shared__ int64_t s_item;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -584,7 +558,7 @@ __global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a,
 #pragma unroll
         for (int q = 0; q < MW; ++q) {
             const int k = lane + 32 * q;
-            pm[q] = k < 2 * T ? mom[(int64_t)nd * 2 * T + k] : S(0);
+            pm[q] = k < 2 * TP ? far[(int64_t)nd * 2 * TP + k] : S(0);
         }
     }
     while (e < f1) {
@@ -592,7 +566,7 @@ __global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a,
 #pragma unroll
         for (int q = 0; q < MW; ++q) {
             const int k = lane + 32 * q;
-            if (k < 2 * T) sM[w][k] = to_c<real>(pm[q]);
+            if (k < 2 * TP) sM[w][k] = to_c<real>(pm[q]);
         }
         __syncwarp();
         const bool lap = (a.nbody[nd] == gb) && a.lap_body[gb];
@@ -603,11 +577,12 @@ __global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a,
 #pragma unroll
             for (int q = 0; q < MW; ++q) {
                 const int k = lane + 32 * q;
-                pm[q] = k < 2 * T ? mom[(int64_t)nd * 2 * T + k] : S(0);
+                pm[q] = k < 2 * TP ? far[(int64_t)nd * 2 * TP + k] : S(0);
             }
         }
         real uL, uY;
-        m2p_eval<real, P>(Rx, Ry, Rz, kappa, sM[w], sM[w] + T, lap, uL, uY);
+        if (lap) far_eval<real, P, true>(Rx, Ry, Rz, kappa, sM[w], sM[w] + TP, uL, uY);
+        else far_eval<real, P, false>(Rx, Ry, Rz, kappa, sM[w], sM[w] + TP, uL, uY);
         kadd(UL, cL, uL);
         kadd(UY, cY, uY);
     }
@@ -623,6 +598,9 @@ struct UpArgs {
     int K;
     int64_t lvl_begin, lvl_end;  // node ids of the level for k_m2m_level
     int p2m_grid;                // > 0: P2M over at most this many blocks (leaves strided)
+    int64_t n_nodes;             // k_far_coef: every node
+    const void* far_tab;         // its table (farfield.cu) in the arithmetic type
+    void* far;                   // its output: 2 * n_terms_pad(P) coefficients per node
 };
 
 __device__ __constant__ const int kBinom[9][9] = {
@@ -797,6 +775,63 @@ __global__ void __launch_bounds__(256) k_m2m_level(UpArgs a, real* __restrict__ 
         real acc = 0;
         for (int ci = 0; ci < nc; ++ci) acc += bufB[ci][k];
         mom[nd * 2 * T + k] = acc;
+    }
+}
+
+// Degree a + b + c of the evaluation-order index j (a, then b, then c).
+__device__ __forceinline__ int eval_degree(int j, int P) {
+    int a = 0;
+    for (;; ++a) {
+        const int n = (P - a + 1) * (P - a + 2) / 2;
+        if (j < n) break;
+        j -= n;
+    }
+    int b = 0;
+    for (;; ++b) {
+        const int n = P - a - b + 1;
+        if (j < n) break;
+        j -= n;
+    }
+    return a + b + j;
+}
+
+// Far-field coefficients of every node of an active body from its moments
+// (farfield.cu): out_Y[j] = sum_k tabY[j][k] M_Y[k] over the moments of the
+// degrees p, p + 2, ... (p the degree of j), out_L[j] = sum_k tabL[j][k] M_L[k]
+// over degree p.  Output per node: Laplace then Yukawa, each padded to
+// n_terms_pad(P) with zeros.  One block per node.
+template <typename real, int P>
+__global__ void __launch_bounds__(128) k_far_coef(UpArgs a, const real* __restrict__ mom) {
+    constexpr int T = MI<P>::T;
+    constexpr int TP = n_terms_pad(P);
+    const real* __restrict__ tab = (const real*)a.far_tab;
+    real* __restrict__ far = (real*)a.far;
+    __shared__ real sm[2 * T];
+    for (int64_t nd = blockIdx.x; nd < a.n_nodes; nd += gridDim.x) {
+        if (!a.src_active[a.nbody[nd]]) continue;  // block-uniform
+        __syncthreads();
+        for (int k = threadIdx.x; k < 2 * T; k += blockDim.x) sm[k] = mom[nd * 2 * T + k];
+        __syncthreads();
+        for (int o = threadIdx.x; o < 2 * TP; o += blockDim.x) {
+            const bool yuk = o >= TP;
+            const int j = yuk ? o - TP : o;
+            real acc = 0;
+            if (j < T) {
+                const int p = eval_degree(j, P);
+                if (yuk) {
+                    const real* row = tab + (int64_t)j * T;
+                    for (int n = p; n <= P; n += 2) {
+                        const int k0 = n * (n + 1) * (n + 2) / 6, k1 = k0 + (n + 1) * (n + 2) / 2;
+                        for (int k = k0; k < k1; ++k) acc += row[k] * sm[T + k];
+                    }
+                } else {
+                    const real* row = tab + (int64_t)T * T + (int64_t)j * T;
+                    const int k0 = p * (p + 1) * (p + 2) / 6, k1 = k0 + (p + 1) * (p + 2) / 2;
+                    for (int k = k0; k < k1; ++k) acc += row[k] * sm[k];
+                }
+            }
+            far[nd * 2 * TP + o] = acc;
+        }
     }
 }
 

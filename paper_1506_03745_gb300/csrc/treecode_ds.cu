@@ -6,7 +6,7 @@
 namespace pgb {
 
 template <int P>
-static void launch_ds(int stage, const EvalArgs& ev, const void* src, const void* xrel, const void* mom,
+static void launch_ds(int stage, const EvalArgs& ev, const void* src, const void* xrel, const void* far,
                       cudaStream_t s) {
     constexpr int NW = 4;   // M2P warps per block (registers, as the FP64 kernel)
     constexpr int NWP = 8;  // P2P warps per block
@@ -16,21 +16,21 @@ static void launch_ds(int stage, const EvalArgs& ev, const void* src, const void
             ev, (const dbl4*)src, (const dbl4*)xrel);
     if (stage == PGB_STAGE_M2P && ev.n_fitems > 0)
         k_m2p<ds, P, NW><<<(unsigned)(persist ? ev.persist_blocks : ev.n_fitems), NW * 32, 0, s>>>(
-            ev, (const dbl4*)xrel, (const double*)mom);
+            ev, (const dbl4*)xrel, (const double*)far);
 }
 
-void treecode_launch_ds(int stage, int P, const EvalArgs& ev, const void* src, const void* xrel, const void* mom,
+void treecode_launch_ds(int stage, int P, const EvalArgs& ev, const void* src, const void* xrel, const void* far,
                         cudaStream_t s) {
     switch (P) {
-        case 0: launch_ds<0>(stage, ev, src, xrel, mom, s); break;
-        case 1: launch_ds<1>(stage, ev, src, xrel, mom, s); break;
-        case 2: launch_ds<2>(stage, ev, src, xrel, mom, s); break;
-        case 3: launch_ds<3>(stage, ev, src, xrel, mom, s); break;
-        case 4: launch_ds<4>(stage, ev, src, xrel, mom, s); break;
-        case 5: launch_ds<5>(stage, ev, src, xrel, mom, s); break;
-        case 6: launch_ds<6>(stage, ev, src, xrel, mom, s); break;
-        case 7: launch_ds<7>(stage, ev, src, xrel, mom, s); break;
-        case 8: launch_ds<8>(stage, ev, src, xrel, mom, s); break;
+        case 0: launch_ds<0>(stage, ev, src, xrel, far, s); break;
+        case 1: launch_ds<1>(stage, ev, src, xrel, far, s); break;
+        case 2: launch_ds<2>(stage, ev, src, xrel, far, s); break;
+        case 3: launch_ds<3>(stage, ev, src, xrel, far, s); break;
+        case 4: launch_ds<4>(stage, ev, src, xrel, far, s); break;
+        case 5: launch_ds<5>(stage, ev, src, xrel, far, s); break;
+        case 6: launch_ds<6>(stage, ev, src, xrel, far, s); break;
+        case 7: launch_ds<7>(stage, ev, src, xrel, far, s); break;
+        case 8: launch_ds<8>(stage, ev, src, xrel, far, s); break;
         default: fail(PGB_EINVAL, "P out of range");
     }
 }
