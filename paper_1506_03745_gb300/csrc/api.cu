@@ -48,16 +48,16 @@ static cudaEvent_t get_event(pgb_ctx* c) {
     return e;
 }
 
-StageTimer::StageTimer(pgb_ctx* ctx, int st) : c(ctx), stage(st) {
+StageTimer::StageTimer(pgb_ctx* ctx, int st, cudaStream_t s) : c(ctx), stage(st), on(s) {
     if (!c->timing) return;
     e0 = get_event(c);
     e1 = get_event(c);
-    cudaEventRecord(e0, c->stream);
+    cudaEventRecord(e0, on ? on : c->stream);
 }
 
 StageTimer::~StageTimer() {
     if (!e0) return;
-    cudaEventRecord(e1, c->stream);
+    cudaEventRecord(e1, on ? on : c->stream);
     c->ev_pending.push_back({stage, {e0, e1}});
 }
 
@@ -407,6 +407,14 @@ int pgb_destroy(pgb_ctx* c) {
     for (auto& gr : c->up_graph)
         if (gr.exec) cudaGraphExecDestroy(gr.exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (int q = 0; q < 2; ++q) {
+        if (c->up_stream[q]) {
+            cudaStreamSynchronize(c->up_stream[q]);
+            cudaStreamDestroy(c->up_stream[q]);
+        }
+        if (c->up_fork[q]) cudaEventDestroy(c->up_fork[q]);
+        if (c->up_join[q]) cudaEventDestroy(c->up_join[q]);
+    }
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->side_stream) cudaStreamSynchronize(c->side_stream);
     if (c->hp_stream) cudaStreamSynchronize(c->hp_stream);

@@ -144,8 +144,16 @@ void far_tables(int P, double kappa, std::vector<double>& tab) {
 const FarTab& far_table(pgb_ctx* c, double kappa) {
     for (const auto& t : c->far_tabs)
         if (t->P == c->p.P && t->kappa == kappa) return *t;
-    std::vector<double> h;
-    far_tables(c->p.P, kappa, h);
+    std::vector<double> rowmajor;
+    far_tables(c->p.P, kappa, rowmajor);
+    // device layout: each table transposed, tab[k][j] with rows of T rounded
+    // up to a multiple of 128 (k_far_coef reads 16 bytes per lane, whole warps of j)
+    const int T = n_terms(c->p.P), TR = (T + 127) & ~127;
+    std::vector<double> h(2 * (size_t)T * TR, 0.0);
+    for (int q = 0; q < 2; ++q)
+        for (int j = 0; j < T; ++j)
+            for (int k = 0; k < T; ++k)
+                h[(size_t)q * T * TR + (size_t)k * TR + j] = rowmajor[(size_t)q * T * T + (size_t)j * T + k];
     std::vector<float> hf(h.begin(), h.end());
     auto t = std::make_unique<FarTab>();
     t->P = c->p.P;

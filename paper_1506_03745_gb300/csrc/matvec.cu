@@ -12,6 +12,7 @@ void treecode_launch_f64(int stage, int P, const UpArgs& up, const std::vector<i
                          const void* src, const void* xrel, void* mom, void* far, cudaStream_t s);
 void treecode_launch_ds(int stage, int P, const EvalArgs& ev, const void* src, const void* xrel, const void* far,
                         cudaStream_t s);
+void convert_src_ds(const void* src64, void* src_ds, int64_t n, cudaStream_t s);
 
 static inline int nblk(int64_t n, int t) { return (int)std::max<int64_t>(1, (n + t - 1) / t); }
 
@@ -311,7 +312,8 @@ void apply_full(pgb_ctx* c, const double* x, double* y, int precision) { apply_m
 // Upward pass as a CUDA graph: captured (on a private stream; nothing runs
 // there) the first time a tree / buffer / source-activity combination is
 // used, then one cudaGraphLaunch on the context stream per product.
-static void upward_graph(pgb_ctx* c, bool f32, const UpArgs& up, const EvalArgs& ev, const void* src, void* mom) {
+static void upward_graph(pgb_ctx* c, bool f32, const UpArgs& up, const EvalArgs& ev, const void* src, void* mom,
+                         cudaStream_t on) {
     auto& gr = c->up_graph[f32 ? 0 : 1];
     bool ok = gr.exec && gr.tree_gen == c->tree_gen && gr.src == src && gr.mom == mom && gr.ncenter == up.ncenter &&
               gr.p2m_grid == up.p2m_grid && gr.far == up.far && gr.far_tab == up.far_tab;
@@ -357,7 +359,19 @@ static void upward_graph(pgb_ctx* c, bool f32, const UpArgs& up, const EvalArgs&
         gr.p2m_grid = up.p2m_grid;
         for (int b = 0; b < PGB_MAX_BODIES; ++b) gr.src_active[b] = up.src_active[b];
     }
-    PGB_CUDA(cudaGraphLaunch(gr.exec, c->stream));
+    PGB_CUDA(cudaGraphLaunch(gr.exec, on));
+}
+
+// The upward-pass stream of a precision (created on first use).
+static cudaStream_t upward_stream(pgb_ctx* c, int pi) {
+    if (!c->up_stream[pi]) {
+        int least = 0, greatest = 0;
+        PGB_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        PGB_CUDA(cudaStreamCreateWithPriority(&c->up_stream[pi], cudaStreamNonBlocking, greatest));
+        PGB_CUDA(cudaEventCreateWithFlags(&c->up_fork[pi], cudaEventDisableTiming));
+        PGB_CUDA(cudaEventCreateWithFlags(&c->up_join[pi], cudaEventDisableTiming));
+    }
+    return c->up_stream[pi];
 }
 
 // Sizes every buffer a product of this precision writes (so that a product
@@ -377,11 +391,17 @@ void reserve_product(pgb_ctx* c, int precision) {
         c->d_far32.resize((size_t)c->n_nodes * 2 * TP);
     } else {
         c->d_src64.resize(2 * nsrc);
+        c->d_src_ds.resize(2 * nsrc);
         c->d_mom64.resize((size_t)c->n_nodes * 2 * T);
         c->d_far64.resize((size_t)c->n_nodes * 2 * TP);
     }
     (void)far_table(c, c->kappa);
     for (const auto& reg : c->regions) (void)far_table(c, reg->dev.kappa);
+    if (c->arrive_gen[pi] != c->tree_gen || c->d_arrive[pi].n < (size_t)c->n_nodes) {
+        c->d_arrive[pi].resize(std::max<int64_t>(c->n_nodes, 1));
+        PGB_CUDA(cudaMemsetAsync(c->d_arrive[pi].p, 0, sizeof(int) * c->d_arrive[pi].n, c->stream));
+        c->arrive_gen[pi] = c->tree_gen;
+    }
 }
 
 void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode, const int* known_mask) {
@@ -413,6 +433,17 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
     up.lvl_begin = up.lvl_end = 0;
     up.p2m_grid = 0;
     up.n_nodes = c->n_nodes;
+    up.parent = c->d_node_parent;
+    {
+        const int pi_up = precision == PGB_FP32 ? 0 : 1;
+        auto& cnt = c->d_arrive[pi_up];
+        if (c->arrive_gen[pi_up] != c->tree_gen || cnt.n < (size_t)c->n_nodes) {
+            cnt.resize(std::max<int64_t>(c->n_nodes, 1));
+            PGB_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int) * cnt.n, s));
+            c->arrive_gen[pi_up] = c->tree_gen;
+        }
+        up.arrive = cnt.p;
+    }
     if (precision != PGB_FP32 && c->persist_blocks > 0)  // side product: P2M on two blocks per SM
         up.p2m_grid = 2 * c->persist_blocks;
     EvalArgs ev;
@@ -471,6 +502,7 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
         c->d_mom64.resize((size_t)c->n_nodes * 2 * T);
         c->d_far64.resize((size_t)c->n_nodes * 2 * TP);
         up.far = c->d_far64.p;
+        if (precision == PGB_FP64_DS) c->d_src_ds.resize(2 * nsrc);
     }
     auto tab_for = [&](double kappa) -> const void* {
         const FarTab& t = far_table(c, kappa);
@@ -505,8 +537,9 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
                 else
                     k_src_region<double><<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, rd, x, mode, c->d_y64,
                                                                               c->d_src64, dens.p);
+                if (precision == PGB_FP64_DS) convert_src_ds(c->d_src64, c->d_src_ds, 2 * nsrc, s);
                 PGB_CUDA(cudaGetLastError());
-                PGB_LAUNCHED(c, 1);
+                PGB_LAUNCHED(c, precision == PGB_FP64_DS ? 2 : 1);
             }
             for (int stage : {PGB_STAGE_UPWARD, PGB_STAGE_P2P, PGB_STAGE_M2P}) {
                 StageTimer tm(c, stage + (f32 ? 0 : PGB_STAGE_FP64));
@@ -514,12 +547,12 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
                     treecode_launch_f32(stage, P, up, c->level_begin, ev, c->d_src32, c->d_x32, c->d_mom32,
                                         c->d_far32, s);
                 else if (precision == PGB_FP64_DS && stage != PGB_STAGE_UPWARD)
-                    treecode_launch_ds(stage, P, ev, c->d_src64, c->d_x64, c->d_far64, s);
+                    treecode_launch_ds(stage, P, ev, c->d_src_ds, c->d_x64, c->d_far64, s);
                 else
                     treecode_launch_f64(stage, P, up, c->level_begin, ev, c->d_src64, c->d_x64, c->d_mom64,
                                         c->d_far64, s);
                 PGB_CUDA(cudaGetLastError());
-                PGB_LAUNCHED(c, stage == PGB_STAGE_UPWARD ? (int64_t)c->level_begin.size() : 1);
+                PGB_LAUNCHED(c, 1);
             }
             {
                 StageTimer tm(c, PGB_STAGE_ASSEMBLE + (f32 ? 0 : PGB_STAGE_FP64));
@@ -546,22 +579,41 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
         else
             k_src_prep<double><<<nblk(c->n_pan, 128), 128, 0, s>>>(g, bd, x, mode, c->d_y64, c->d_src64,
                                                                    dens.p, c->eps_out);
+        if (precision == PGB_FP64_DS) convert_src_ds(c->d_src64, c->d_src_ds, 2 * nsrc, s);
         PGB_CUDA(cudaGetLastError());
-        PGB_LAUNCHED(c, 1);
+        PGB_LAUNCHED(c, precision == PGB_FP64_DS ? 2 : 1);
     }
-    for (int stage : {PGB_STAGE_UPWARD, PGB_STAGE_P2P, PGB_STAGE_M2P}) {
-        StageTimer tm(c, stage + (f32 ? 0 : PGB_STAGE_FP64));
-        if (stage == PGB_STAGE_UPWARD && c->p.graphs)
+    // the upward pass on its own stream, beside P2P (which does not read the
+    // moments); M2P waits for it
+    cudaStream_t us = upward_stream(c, pi);
+    PGB_CUDA(cudaEventRecord(c->up_fork[pi], s));
+    PGB_CUDA(cudaStreamWaitEvent(us, c->up_fork[pi], 0));
+    {
+        StageTimer tm(c, PGB_STAGE_UPWARD + (f32 ? 0 : PGB_STAGE_FP64), us);
+        if (c->p.graphs)
             upward_graph(c, f32, up, ev, f32 ? (const void*)c->d_src32.p : (const void*)c->d_src64.p,
-                         f32 ? (void*)c->d_mom32.p : (void*)c->d_mom64.p);
+                         f32 ? (void*)c->d_mom32.p : (void*)c->d_mom64.p, us);
         else if (f32)
+            treecode_launch_f32(PGB_STAGE_UPWARD, P, up, c->level_begin, ev, c->d_src32, c->d_x32, c->d_mom32,
+                                c->d_far32, us);
+        else
+            treecode_launch_f64(PGB_STAGE_UPWARD, P, up, c->level_begin, ev, c->d_src64, c->d_x64, c->d_mom64,
+                                c->d_far64, us);
+        PGB_CUDA(cudaGetLastError());
+        PGB_LAUNCHED(c, 2);
+    }
+    PGB_CUDA(cudaEventRecord(c->up_join[pi], us));
+    for (int stage : {PGB_STAGE_P2P, PGB_STAGE_M2P}) {
+        if (stage == PGB_STAGE_M2P) PGB_CUDA(cudaStreamWaitEvent(s, c->up_join[pi], 0));
+        StageTimer tm(c, stage + (f32 ? 0 : PGB_STAGE_FP64));
+        if (f32)
             treecode_launch_f32(stage, P, up, c->level_begin, ev, c->d_src32, c->d_x32, c->d_mom32, c->d_far32, s);
         else if (precision == PGB_FP64_DS && stage != PGB_STAGE_UPWARD)
-            treecode_launch_ds(stage, P, ev, c->d_src64, c->d_x64, c->d_far64, s);
+            treecode_launch_ds(stage, P, ev, c->d_src_ds, c->d_x64, c->d_far64, s);
         else
             treecode_launch_f64(stage, P, up, c->level_begin, ev, c->d_src64, c->d_x64, c->d_mom64, c->d_far64, s);
         PGB_CUDA(cudaGetLastError());
-        PGB_LAUNCHED(c, stage == PGB_STAGE_UPWARD ? (int64_t)c->level_begin.size() : 1);
+        PGB_LAUNCHED(c, 1);
     }
     {
         StageTimer tm(c, PGB_STAGE_ASSEMBLE + (f32 ? 0 : PGB_STAGE_FP64));

@@ -271,9 +271,12 @@ struct pgb_ctx {
     // matvec work buffers
     pgb::DBuf<float4> d_src32;           // 2 per point
     pgb::DBuf<pgb::dbl4> d_src64;
+    pgb::DBuf<pgb::dbl4> d_src_ds;       // the same split into double-single (32 bytes each)
     pgb::DBuf<double> d_dens[2];            // 3 per sorted panel: psiL, psiY, phi
     pgb::DBuf<float> d_mom32;            // 2*T per node
     pgb::DBuf<double> d_mom64;
+    pgb::DBuf<int> d_arrive[2];          // upward pass: children finished per node, per precision
+    uint64_t arrive_gen[2] = {~0ull, ~0ull};  // tree_gen the counters were zeroed for
     pgb::DBuf<float> d_far32;            // far-field coefficients: 2 * n_terms_pad(P) per node
     pgb::DBuf<double> d_far64;
     std::vector<std::unique_ptr<pgb::FarTab>> far_tabs;  // per (P, kappa)
@@ -315,6 +318,10 @@ struct pgb_ctx {
         int src_active[PGB_MAX_BODIES] = {0};
     } up_graph[2];
     cudaStream_t cap_stream = nullptr;   // capture only (nothing runs on it)
+    // the upward pass of a product runs on its own (highest-priority) stream
+    // beside the P2P kernel, which does not need the moments; per precision
+    cudaStream_t up_stream[2] = {nullptr, nullptr};
+    cudaEvent_t up_fork[2] = {nullptr, nullptr}, up_join[2] = {nullptr, nullptr};
     uint64_t tree_gen = 0;               // bumped whenever the octree structure is rebuilt
     uint64_t config_gen = 0;             // bumped when bodies, charges, boundary values or solvent change
     bool owns_stream = false;            // lane contexts create (and destroy) their stream
@@ -373,7 +380,8 @@ struct StageTimer {
     pgb_ctx* c;
     int stage;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    StageTimer(pgb_ctx* ctx, int st);
+    cudaStream_t on = nullptr;
+    StageTimer(pgb_ctx* ctx, int st, cudaStream_t on = nullptr);  // on: a stream other than the context's
     ~StageTimer();
 };
 void collect_timing(pgb_ctx* c);

@@ -420,9 +420,10 @@ __device__ __forceinline__ void store_item(real (*red)[4][32], int w, int lane, 
 // (up to 32 quadrature points of one near leaf each) of one target group (32
 // targets, one per lane); the tiles are dealt round robin to the warps, the
 // next tile prefetched into registers.  The item's partial sums go to Up.
+// The source terms come in the arithmetic type (for double-single, split
+// once per product by k_src_to_ds); the targets in the storage type.
 template <typename real, int NW>
-__global__ void __launch_bounds__(NW * 32) k_p2p(EvalArgs a,
-                                                 const typename V4<typename Store<real>::S>::t* __restrict__ src,
+__global__ void __launch_bounds__(NW * 32) k_p2p(EvalArgs a, const typename V4<real>::t* __restrict__ src,
                                                  const typename V4<typename Store<real>::S>::t* __restrict__ xrel) {
     using S = typename Store<real>::S;  // storage type of the inputs
     using v4 = typename V4<real>::t;
@@ -445,7 +446,7 @@ __global__ void __launch_bounds__(NW * 32) k_p2p(EvalArgs a,
     const int64_t tb = a.tile_off[g] + (it - a.pitem_off[g]) * a.p2p_item;
     const int64_t t1 = min(a.tile_off[g + 1], tb + a.p2p_item);
     int64_t t = tb + w;
-    s4 pa = s4(), pb = s4();
+    v4 pa = v4(), pb = v4();
     int4 m = make_int4(0, 0, 0, 0);
     float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
     if (t < t1) {
@@ -478,8 +479,8 @@ __global__ void __launch_bounds__(NW * 32) k_p2p(EvalArgs a,
         }
         __syncwarp();
         if (lane < cnt) {
-            sA[w][lane] = cvt4<real>(pa);
-            sB[w][lane] = cvt4<real>(pb);
+            sA[w][lane] = pa;
+            sB[w][lane] = pb;
         }
         __syncwarp();
         t += NW;
@@ -601,6 +602,8 @@ struct UpArgs {
     int64_t n_nodes;             // k_far_coef: every node
     const void* far_tab;         // its table (farfield.cu) in the arithmetic type
     void* far;                   // its output: 2 * n_terms_pad(P) coefficients per node
+    const int32_t* parent;       // k_upward: parent of every node (-1 at a body's root)
+    int* arrive;                 // k_upward: per node, children finished (zero between launches)
 };
 
 __device__ __constant__ const int kBinom[9][9] = {
@@ -796,41 +799,266 @@ __device__ __forceinline__ int eval_degree(int j, int P) {
 }
 
 // Far-field coefficients of every node of an active body from its moments
-// (farfield.cu): out_Y[j] = sum_k tabY[j][k] M_Y[k] over the moments of the
-// degrees p, p + 2, ... (p the degree of j), out_L[j] = sum_k tabL[j][k] M_L[k]
-// over degree p.  Output per node: Laplace then Yukawa, each padded to
-// n_terms_pad(P) with zeros.  One block per node.
+// (farfield.cu): E_Y[j] = sum_k tabY[j][k] M_Y[k], E_L[j] = sum_k tabL[j][k] M_L[k].
+// The tables come transposed (tab[k][j], rows of T rounded up to 128) so
+// that a lane reads the 16 bytes of its VN consecutive outputs and the warp
+// a whole row segment; a Yukawa output of degree p takes the moments of
+// degrees p, p + 2, ..., a Laplace one those of degree p (the other entries
+// are zero), and the loop over k starts at the smallest degree among the
+// warp's outputs.  One warp per node; output per node: Laplace then Yukawa,
+// each padded with zeros.
 template <typename real, int P>
 __global__ void __launch_bounds__(128) k_far_coef(UpArgs a, const real* __restrict__ mom) {
+    using V = Vec16<real>;
+    constexpr int VN = V::N;
     constexpr int T = MI<P>::T;
     constexpr int TP = n_terms_pad(P);
-    const real* __restrict__ tab = (const real*)a.far_tab;
+    constexpr int TR = (T + 127) & ~127;  // table row: every lane of a round in bounds
+    const real* __restrict__ tabY = (const real*)a.far_tab;
+    const real* __restrict__ tabL = tabY + (int64_t)T * TR;
     real* __restrict__ far = (real*)a.far;
-    __shared__ real sm[2 * T];
-    for (int64_t nd = blockIdx.x; nd < a.n_nodes; nd += gridDim.x) {
-        if (!a.src_active[a.nbody[nd]]) continue;  // block-uniform
-        __syncthreads();
-        for (int k = threadIdx.x; k < 2 * T; k += blockDim.x) sm[k] = mom[nd * 2 * T + k];
-        __syncthreads();
-        for (int o = threadIdx.x; o < 2 * TP; o += blockDim.x) {
-            const bool yuk = o >= TP;
-            const int j = yuk ? o - TP : o;
-            real acc = 0;
-            if (j < T) {
-                const int p = eval_degree(j, P);
-                if (yuk) {
-                    const real* row = tab + (int64_t)j * T;
-                    for (int n = p; n <= P; n += 2) {
-                        const int k0 = n * (n + 1) * (n + 2) / 6, k1 = k0 + (n + 1) * (n + 2) / 2;
-                        for (int k = k0; k < k1; ++k) acc += row[k] * sm[T + k];
-                    }
-                } else {
-                    const real* row = tab + (int64_t)T * T + (int64_t)j * T;
-                    const int k0 = p * (p + 1) * (p + 2) / 6, k1 = k0 + (p + 1) * (p + 2) / 2;
-                    for (int k = k0; k < k1; ++k) acc += row[k] * sm[k];
+    __shared__ real sm[4][2 * T];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t nd = (int64_t)blockIdx.x * 4 + w; nd < a.n_nodes; nd += (int64_t)gridDim.x * 4) {
+        if (!a.src_active[a.nbody[nd]]) continue;  // warp-uniform
+        __syncwarp();
+        for (int k = lane; k < 2 * T; k += 32) sm[w][k] = mom[nd * 2 * T + k];
+        __syncwarp();
+        for (int j0 = 0; j0 < TP; j0 += 32 * VN) {
+            const int jb = j0 + VN * lane;  // this lane's first output
+            int pmin = P;
+            for (int q = 0; q < VN; ++q)
+                if (jb + q < T) pmin = min(pmin, eval_degree(jb + q, P));
+            for (int o = 16; o > 0; o >>= 1) pmin = min(pmin, __shfl_xor_sync(0xffffffffu, pmin, o));
+            real aY[VN], aL[VN];
+#pragma unroll
+            for (int q = 0; q < VN; ++q) aY[q] = aL[q] = real(0);
+#pragma unroll 4
+            for (int k = pmin * (pmin + 1) * (pmin + 2) / 6; k < T; ++k) {
+                const V ty = *reinterpret_cast<const V*>(tabY + (int64_t)k * TR + jb);
+                const V tl = *reinterpret_cast<const V*>(tabL + (int64_t)k * TR + jb);
+                const real m = sm[w][T + k], l = sm[w][k];
+#pragma unroll
+                for (int q = 0; q < VN; ++q) {
+                    aY[q] += ty.v[q] * m;
+                    aL[q] += tl.v[q] * l;
                 }
             }
-            far[nd * 2 * TP + o] = acc;
+#pragma unroll
+            for (int q = 0; q < VN; ++q)
+                if (jb + q < TP) {
+                    far[nd * 2 * TP + jb + q] = aL[q];
+                    far[nd * 2 * TP + TP + jb + q] = aY[q];
+                }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- fused upward pass
+// The upward pass in one launch: each block takes leaves (P2M), and a node's
+// moment shift runs in the block whose child finished last (a counter per
+// node; the last of nchild increments goes on up, the others stop), so the
+// tree is climbed without a launch or a barrier per level and no block waits
+// for another.  Writers fence before their increment; the climbing block
+// fences after it and reads the children's moments from L2 (ld.global.cg).
+// The far-field coefficients follow in k_far_coef.
+template <typename real, int P>
+struct UpShared {
+    static constexpr int T = MI<P>::T;
+    static constexpr int TD = P * (P + 1) * (P + 2) / 6 > 0 ? P * (P + 1) * (P + 2) / 6 : 1;
+    struct P2M {
+        real pw[128][3][P + 1];
+        real sq[128][5];
+        real sd[3][TD];
+    };
+    struct M2M {
+        real bufA[8][2 * T], bufB[8][2 * T];
+        real cd[8][3][P + 1];
+    };
+    union {
+        P2M p;
+        M2M m;
+    } u;
+    real binom[P + 1][P + 1];
+    short idx3[P + 1][P + 1][P + 1];
+    signed char kk[T][3];
+    int next;
+};
+
+template <typename real>
+__device__ __forceinline__ real ld_cg(const real* p) {
+    return __ldcg(p);
+}
+
+// P2M of node nd (a leaf) into mom[nd]: see k_p2m_leaves.
+template <typename real, int P>
+__device__ __forceinline__ void up_p2m(const UpArgs& a, int nd, const typename V4<real>::t* __restrict__ src,
+                                       real* __restrict__ mom, UpShared<real, P>& sh) {
+    using v4 = typename V4<real>::t;
+    constexpr int T = MI<P>::T;
+    const int tid = threadIdx.x;
+    const int64_t s0 = (int64_t)a.nstart[nd] * a.K, s1 = (int64_t)a.nend[nd] * a.K;
+    int kx[2] = {0, 0}, ky[2] = {0, 0}, kz[2] = {0, 0};
+    bool on[2], low[2];
+    for (int h = 0; h < 2; ++h) {
+        const int k = tid + 128 * h;
+        on[h] = k < T;
+        if (on[h]) {
+            kx[h] = sh.kk[k][0];
+            ky[h] = sh.kk[k][1];
+            kz[h] = sh.kk[k][2];
+        }
+        low[h] = on[h] && kx[h] + ky[h] + kz[h] < P;
+    }
+    real qL[2] = {0, 0}, qY[2] = {0, 0}, dx[2] = {0, 0}, dy[2] = {0, 0}, dz[2] = {0, 0};
+    for (int64_t t = s0; t < s1; t += 128) {
+        const int cnt = (int)min((int64_t)128, s1 - t);
+        __syncthreads();
+        if (tid < cnt) {
+            const v4 A = src[2 * (t + tid)], B = src[2 * (t + tid) + 1];
+            const real u[3] = {-A.x, -A.y, -A.z};
+            for (int q = 0; q < 3; ++q) {
+                real v = 1;
+                for (int m = 0; m <= P; ++m) {
+                    sh.u.p.pw[tid][q][m] = v;
+                    v *= u[q];
+                }
+            }
+            sh.u.p.sq[tid][0] = A.w;
+            sh.u.p.sq[tid][1] = B.w;
+            sh.u.p.sq[tid][2] = B.x;
+            sh.u.p.sq[tid][3] = B.y;
+            sh.u.p.sq[tid][4] = B.z;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (!on[h]) continue;
+            for (int j = 0; j < cnt; ++j) {
+                const real mono = sh.u.p.pw[j][0][kx[h]] * sh.u.p.pw[j][1][ky[h]] * sh.u.p.pw[j][2][kz[h]];
+                qL[h] += sh.u.p.sq[j][0] * mono;
+                qY[h] += sh.u.p.sq[j][1] * mono;
+                if (low[h]) {
+                    dx[h] += sh.u.p.sq[j][2] * mono;
+                    dy[h] += sh.u.p.sq[j][3] * mono;
+                    dz[h] += sh.u.p.sq[j][4] * mono;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int h = 0; h < 2; ++h)
+        if (low[h]) {
+            const int k = tid + 128 * h;
+            sh.u.p.sd[0][k] = dx[h];
+            sh.u.p.sd[1][k] = dy[h];
+            sh.u.p.sd[2][k] = dz[h];
+        }
+    __syncthreads();
+    for (int h = 0; h < 2; ++h) {
+        if (!on[h]) continue;
+        const int k = tid + 128 * h;
+        real dl = 0;
+        if (kx[h]) dl += real(kx[h]) * sh.u.p.sd[0][sh.idx3[kx[h] - 1][ky[h]][kz[h]]];
+        if (ky[h]) dl += real(ky[h]) * sh.u.p.sd[1][sh.idx3[kx[h]][ky[h] - 1][kz[h]]];
+        if (kz[h]) dl += real(kz[h]) * sh.u.p.sd[2][sh.idx3[kx[h]][ky[h]][kz[h] - 1]];
+        mom[(int64_t)nd * 2 * T + k] = qL[h] + dl;
+        mom[(int64_t)nd * 2 * T + T + k] = qY[h] + dl;
+    }
+}
+
+// Moment shift of node nd from its children (see k_m2m_level); the
+// children's moments are read from L2.
+template <typename real, int P>
+__device__ __forceinline__ void up_m2m(const UpArgs& a, int nd, real* __restrict__ mom, UpShared<real, P>& sh) {
+    constexpr int T = MI<P>::T;
+    const int tid = threadIdx.x;
+    const int nc = a.nchild[nd];
+    const int fc = a.child[nd];
+    __syncthreads();
+    for (int q = tid; q < nc * 2 * T; q += blockDim.x) {
+        const int ci = q / (2 * T), k = q - ci * 2 * T;
+        sh.u.m.bufA[ci][k] = ld_cg(mom + (int64_t)(fc + ci) * 2 * T + k);
+    }
+    if (tid < 3 * nc) {
+        const int ci = tid / 3, ax = tid - 3 * ci;
+        const real d = (real)(a.ncenter[3 * nd + ax] - a.ncenter[3 * (fc + ci) + ax]);
+        real v = 1;
+        for (int m = 0; m <= P; ++m) {
+            sh.u.m.cd[ci][ax][m] = v;
+            v *= d;
+        }
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int ax = 0; ax < 3; ++ax) {
+        real(*srcb)[2 * T] = (ax == 1) ? sh.u.m.bufB : sh.u.m.bufA;
+        real(*dstb)[2 * T] = (ax == 1) ? sh.u.m.bufA : sh.u.m.bufB;
+        for (int it = tid; it < nc * T; it += blockDim.x) {
+            const int ci = it / T, k = it - ci * T;
+            const int k0 = sh.kk[k][0], k1 = sh.kk[k][1], k2 = sh.kk[k][2];
+            const int ka = sh.kk[k][ax];
+            real sL = 0, sY = 0;
+            for (int j = 0; j <= ka; ++j) {
+                const int jx = ax == 0 ? j : k0, jy = ax == 1 ? j : k1, jz = ax == 2 ? j : k2;
+                const int jj = sh.idx3[jx][jy][jz];
+                const real coef = sh.binom[ka][j] * sh.u.m.cd[ci][ax][ka - j];
+                sL += coef * srcb[ci][jj];
+                sY += coef * srcb[ci][T + jj];
+            }
+            dstb[ci][k] = sL;
+            dstb[ci][T + k] = sY;
+        }
+        __syncthreads();
+    }
+    for (int k = tid; k < 2 * T; k += blockDim.x) {
+        real acc = 0;
+        for (int ci = 0; ci < nc; ++ci) acc += sh.u.m.bufB[ci][k];
+        mom[(int64_t)nd * 2 * T + k] = acc;
+    }
+}
+
+template <typename real, int P>
+__global__ void __launch_bounds__(128) k_upward(UpArgs a, const typename V4<real>::t* __restrict__ src,
+                                                real* __restrict__ mom) {
+    constexpr int T = MI<P>::T;
+    static_assert(T <= 2 * 128, "two terms per thread at most");
+    __shared__ UpShared<real, P> sh;
+    const int tid = threadIdx.x;
+    for (int k = tid; k < T; k += blockDim.x) {
+        int x, y, z;
+        decode_mi(k, x, y, z);
+        sh.idx3[x][y][z] = (short)k;
+        sh.kk[k][0] = (signed char)x;
+        sh.kk[k][1] = (signed char)y;
+        sh.kk[k][2] = (signed char)z;
+    }
+    for (int q = tid; q < (P + 1) * (P + 1); q += blockDim.x) {
+        const int n = q / (P + 1), m = q - n * (P + 1);
+        sh.binom[n][m] = (real)kBinom[n][m];
+    }
+    __syncthreads();
+    for (int64_t leaf = blockIdx.x; leaf < a.n_leaves; leaf += gridDim.x) {
+        int nd = a.leaf_node[leaf];
+        if (!a.src_active[a.nbody[nd]]) continue;  // block-uniform
+        up_p2m<real, P>(a, nd, src, mom, sh);
+        for (;;) {
+            // publish nd's moments, then count it at its parent
+            __syncthreads();
+            __threadfence();
+            if (tid == 0) {
+                const int par = a.parent[nd];
+                int go = -1;
+                if (par >= 0 && atomicAdd(a.arrive + par, 1) == a.nchild[par] - 1) go = par;
+                sh.next = go;
+            }
+            __syncthreads();
+            const int par = sh.next;
+            if (par < 0) break;
+            __threadfence();
+            up_m2m<real, P>(a, par, mom, sh);
+            if (tid == 0) a.arrive[par] = 0;  // every child has arrived: ready for the next launch
+            nd = par;
         }
     }
 }

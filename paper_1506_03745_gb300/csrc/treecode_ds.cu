@@ -13,10 +13,23 @@ static void launch_ds(int stage, const EvalArgs& ev, const void* src, const void
     const bool persist = ev.p2p_work != nullptr;
     if (stage == PGB_STAGE_P2P && ev.n_pitems > 0)
         k_p2p<ds, NWP><<<(unsigned)(persist ? ev.persist_blocks : ev.n_pitems), NWP * 32, 0, s>>>(
-            ev, (const dbl4*)src, (const dbl4*)xrel);
+            ev, (const ds4*)src, (const dbl4*)xrel);
     if (stage == PGB_STAGE_M2P && ev.n_fitems > 0)
         k_m2p<ds, P, NW><<<(unsigned)(persist ? ev.persist_blocks : ev.n_fitems), NW * 32, 0, s>>>(
             ev, (const dbl4*)xrel, (const double*)far);
+}
+
+// FP64 source terms split into double-single once per product, so that the
+// P2P tiles stage them without conversion.
+__global__ void k_src_to_ds(const dbl4* __restrict__ in, ds4* __restrict__ out, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = cvt4<ds>(in[i]);
+}
+
+// src_ds (2 n_src entries of 32 bytes) = the FP64 source terms src64 split
+// into double-single.
+void convert_src_ds(const void* src64, void* src_ds, int64_t n, cudaStream_t s) {
+    if (n > 0) k_src_to_ds<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const dbl4*)src64, (ds4*)src_ds, n);
 }
 
 void treecode_launch_ds(int stage, int P, const EvalArgs& ev, const void* src, const void* xrel, const void* far,

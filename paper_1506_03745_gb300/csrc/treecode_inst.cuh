@@ -11,21 +11,13 @@ static void launch_p(int stage, const UpArgs& up, const std::vector<int64_t>& up
                      const void* src, const void* xrel, void* mom, void* far, cudaStream_t s) {
     using v4 = typename V4<real>::t;
     if (stage == PGB_STAGE_UPWARD && up.n_leaves > 0) {
+        // P2M, moment shifts and far-field coefficients in one launch
         const int64_t grid = up.p2m_grid > 0 ? std::min<int64_t>(up.n_leaves, up.p2m_grid) : up.n_leaves;
-        k_p2m_leaves<real, P><<<(unsigned)grid, 128, 0, s>>>(up, (const v4*)src, (real*)mom);
-        // inner nodes level by level, deepest first
-        for (int l = (int)up_levels.size() - 3; l >= 0; --l) {  // the deepest level holds only leaves
-            UpArgs u = up;
-            u.lvl_begin = up_levels[l];
-            u.lvl_end = up_levels[l + 1];
-            if (u.lvl_end > u.lvl_begin)
-                k_m2m_level<real, P><<<(unsigned)(u.lvl_end - u.lvl_begin), 256, 0, s>>>(u, (real*)mom);
-        }
-        // moments -> far-field coefficients of every node
-        if (up.n_nodes > 0) {
-            const int64_t g = up.p2m_grid > 0 ? std::min<int64_t>(up.n_nodes, up.p2m_grid) : up.n_nodes;
-            k_far_coef<real, P><<<(unsigned)g, 128, 0, s>>>(up, (const real*)mom);
-        }
+        k_upward<real, P><<<(unsigned)grid, 128, 0, s>>>(up, (const v4*)src, (real*)mom);
+        (void)up_levels;
+        const int64_t gf = (up.n_nodes + 3) / 4;   // four nodes (warps) per block
+        const int64_t gfc = up.p2m_grid > 0 ? std::min<int64_t>(gf, up.p2m_grid) : gf;
+        k_far_coef<real, P><<<(unsigned)std::max<int64_t>(gfc, 1), 128, 0, s>>>(up, (const real*)mom);
     }
     // FP64 M2P: 4 warps per block (its registers would otherwise fill an SM)
     constexpr int NW = sizeof(real) == 8 ? 4 : 8;
