@@ -14,7 +14,7 @@
 
 namespace pgb {
 
-struct ds {
+struct __align__(8) ds {
     float hi, lo;
     ds() = default;
     __host__ __device__ constexpr ds(float h, float l) : hi(h), lo(l) {}

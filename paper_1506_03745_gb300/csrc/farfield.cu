@@ -146,15 +146,36 @@ const FarTab& far_table(pgb_ctx* c, double kappa) {
         if (t->P == c->p.P && t->kappa == kappa) return *t;
     std::vector<double> rowmajor;
     far_tables(c->p.P, kappa, rowmajor);
-    // device layout: each table transposed, tab[k][j] with rows of T rounded
-    // up to a multiple of 128 (k_far_coef reads 16 bytes per lane, whole warps of j)
-    const int T = n_terms(c->p.P), TR = (T + 127) & ~127;
-    std::vector<double> h(2 * (size_t)T * TR, 0.0);
+    // device layout: packed rows in the graded order of the moments, per row
+    // the Yukawa entries over the moment degrees p, p + 2, ..., P then the
+    // Laplace entries over degree p (k_far_coef)
+    const int P = c->p.P, T = n_terms(P);
+    std::vector<int> ev((P + 1) * (P + 1) * (P + 1), -1);
+    {
+        int e = 0;
+        for (int a = 0; a <= P; ++a)
+            for (int b = 0; b <= P - a; ++b)
+                for (int cc = 0; cc <= P - a - b; ++cc) ev[(a * (P + 1) + b) * (P + 1) + cc] = e++;
+    }
+    std::vector<double> h;
+    for (int n = 0; n <= P; ++n)
+        for (int a = n; a >= 0; --a)
+            for (int b = n - a; b >= 0; --b) {
+                const int row = ev[(a * (P + 1) + b) * (P + 1) + (n - a - b)];
+                for (int q = n; q <= P; q += 2)
+                    for (int k = (q > 0 ? n_terms(q - 1) : 0); k < n_terms(q); ++k)
+                        h.push_back(rowmajor[(size_t)row * T + k]);
+                for (int k = (n > 0 ? n_terms(n - 1) : 0); k < n_terms(n); ++k)
+                    h.push_back(rowmajor[(size_t)T * T + (size_t)row * T + k]);
+            }
+    // FP32 layout: each table transposed, tab[k][j] with rows of far_tr(P)
+    // columns (k_far_f32), Yukawa then Laplace
+    const int TR = (((T + 3) & ~3) + 31) & ~31;
+    std::vector<float> hf(2 * (size_t)T * TR, 0.f);
     for (int q = 0; q < 2; ++q)
         for (int j = 0; j < T; ++j)
             for (int k = 0; k < T; ++k)
-                h[(size_t)q * T * TR + (size_t)k * TR + j] = rowmajor[(size_t)q * T * T + (size_t)j * T + k];
-    std::vector<float> hf(h.begin(), h.end());
+                hf[(size_t)q * T * TR + (size_t)k * TR + j] = (float)rowmajor[(size_t)q * T * T + (size_t)j * T + k];
     auto t = std::make_unique<FarTab>();
     t->P = c->p.P;
     t->kappa = kappa;

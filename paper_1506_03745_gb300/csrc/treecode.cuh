@@ -24,7 +24,7 @@
 
 namespace pgb {
 
-struct ds4 {
+struct __align__(16) ds4 {
     ds x, y, z, w;
 };
 
@@ -248,7 +248,7 @@ __device__ __forceinline__ int64_t next_item(unsigned long long* work, int64_t c
 // 16-byte vector of the arithmetic type (4 floats, 2 doubles, 2 double-singles),
 // for loads of consecutive coefficients from shared memory.
 template <typename real>
-struct Vec16 {
+struct alignas(16) Vec16 {
     static constexpr int N = 16 / sizeof(real);
     real v[N];
 };
@@ -798,60 +798,109 @@ __device__ __forceinline__ int eval_degree(int j, int P) {
     return a + b + j;
 }
 
+// Nonzero entries of one output row of the far-field tables: a Yukawa
+// output of degree p takes the moments of degrees p, p + 2, ..., P, a Laplace
+// output those of degree p.
+__host__ __device__ constexpr int far_row_nnz(int p, int P) {
+    int n = (p + 1) * (p + 2) / 2;  // Laplace
+    for (int q = p; q <= P; q += 2) n += (q + 1) * (q + 2) / 2;
+    return n;
+}
+// Packed table size, and the offset of the first row of degree p (rows in
+// the graded order of the moments).
+__host__ __device__ constexpr int far_pack_offset(int p, int P) {
+    int o = 0;
+    for (int q = 0; q < p; ++q) o += (q + 1) * (q + 2) / 2 * far_row_nnz(q, P);
+    return o;
+}
+
 // Far-field coefficients of every node of an active body from its moments
-// (farfield.cu): E_Y[j] = sum_k tabY[j][k] M_Y[k], E_L[j] = sum_k tabL[j][k] M_L[k].
-// The tables come transposed (tab[k][j], rows of T rounded up to 128) so
-// that a lane reads the 16 bytes of its VN consecutive outputs and the warp
-// a whole row segment; a Yukawa output of degree p takes the moments of
-// degrees p, p + 2, ..., a Laplace one those of degree p (the other entries
-// are zero), and the loop over k starts at the smallest degree among the
-// warp's outputs.  One warp per node; output per node: Laplace then Yukawa,
-// each padded with zeros.
+// (farfield.cu).  The table comes packed: per output row in the graded order,
+// its Yukawa entries over the moments of degrees p, p + 2, ... then its
+// Laplace entries over degree p (far_pack_offset, far_row_nnz); it is staged
+// in shared memory once per block.  The block then takes nodes in turn: the
+// node's moments go to shared memory, each thread forms outputs (its row of
+// the packed table against the moments) and writes them in the evaluation
+// order of far_eval.  Output per node: Laplace then Yukawa, each padded with
+// zeros.
 template <typename real, int P>
 __global__ void __launch_bounds__(128) k_far_coef(UpArgs a, const real* __restrict__ mom) {
-    using V = Vec16<real>;
-    constexpr int VN = V::N;
     constexpr int T = MI<P>::T;
     constexpr int TP = n_terms_pad(P);
-    constexpr int TR = (T + 127) & ~127;  // table row: every lane of a round in bounds
-    const real* __restrict__ tabY = (const real*)a.far_tab;
-    const real* __restrict__ tabL = tabY + (int64_t)T * TR;
+    constexpr int NNZ = far_pack_offset(P + 1, P);
+    extern __shared__ __align__(16) unsigned char far_smem[];
+    real* tab = reinterpret_cast<real*>(far_smem);
+    real* sm = tab + ((NNZ + 3) & ~3);
+    const real* __restrict__ gtab = (const real*)a.far_tab;
+    for (int k = threadIdx.x; k < NNZ; k += blockDim.x) tab[k] = gtab[k];
     real* __restrict__ far = (real*)a.far;
-    __shared__ real sm[4][2 * T];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int64_t nd = (int64_t)blockIdx.x * 4 + w; nd < a.n_nodes; nd += (int64_t)gridDim.x * 4) {
-        if (!a.src_active[a.nbody[nd]]) continue;  // warp-uniform
-        __syncwarp();
-        for (int k = lane; k < 2 * T; k += 32) sm[w][k] = mom[nd * 2 * T + k];
-        __syncwarp();
-        for (int j0 = 0; j0 < TP; j0 += 32 * VN) {
-            const int jb = j0 + VN * lane;  // this lane's first output
-            int pmin = P;
-            for (int q = 0; q < VN; ++q)
-                if (jb + q < T) pmin = min(pmin, eval_degree(jb + q, P));
-            for (int o = 16; o > 0; o >>= 1) pmin = min(pmin, __shfl_xor_sync(0xffffffffu, pmin, o));
-            real aY[VN], aL[VN];
-#pragma unroll
-            for (int q = 0; q < VN; ++q) aY[q] = aL[q] = real(0);
-#pragma unroll 4
-            for (int k = pmin * (pmin + 1) * (pmin + 2) / 6; k < T; ++k) {
-                const V ty = *reinterpret_cast<const V*>(tabY + (int64_t)k * TR + jb);
-                const V tl = *reinterpret_cast<const V*>(tabL + (int64_t)k * TR + jb);
-                const real m = sm[w][T + k], l = sm[w][k];
-#pragma unroll
-                for (int q = 0; q < VN; ++q) {
-                    aY[q] += ty.v[q] * m;
-                    aL[q] += tl.v[q] * l;
-                }
+    for (int64_t nd = blockIdx.x; nd < a.n_nodes; nd += gridDim.x) {
+        if (!a.src_active[a.nbody[nd]]) continue;  // block-uniform
+        __syncthreads();
+        for (int k = threadIdx.x; k < 2 * T; k += blockDim.x) sm[k] = mom[nd * 2 * T + k];
+        for (int k = T + threadIdx.x; k < TP; k += blockDim.x) {  // padding
+            far[nd * 2 * TP + k] = real(0);
+            far[nd * 2 * TP + TP + k] = real(0);
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < T; j += blockDim.x) {
+            int x, y, z;
+            decode_mi(j, x, y, z);
+            const int p = x + y + z;
+            const int g0 = p * (p + 1) * (p + 2) / 6;  // first graded index of degree p
+            const real* row = tab + far_pack_offset(p, P) + (j - g0) * far_row_nnz(p, P);
+            real aY = 0, aL = 0;
+            int e = 0;
+            for (int q = p; q <= P; q += 2) {
+                const int k0 = q * (q + 1) * (q + 2) / 6, k1 = k0 + (q + 1) * (q + 2) / 2;
+                for (int k = k0; k < k1; ++k) aY += row[e++] * sm[T + k];
             }
-#pragma unroll
-            for (int q = 0; q < VN; ++q)
-                if (jb + q < TP) {
-                    far[nd * 2 * TP + jb + q] = aL[q];
-                    far[nd * 2 * TP + TP + jb + q] = aY[q];
-                }
+            for (int k = g0; k < g0 + (p + 1) * (p + 2) / 2; ++k) aL += row[e++] * sm[k];
+            // evaluation-order index of (x, y, z): a = x, b = y, c = z
+            int ev = 0;
+            for (int aa = 0; aa < x; ++aa) ev += (P - aa + 1) * (P - aa + 2) / 2;
+            ev += y * (P - x + 1) - y * (y - 1) / 2 + z;
+            far[nd * 2 * TP + ev] = aL;
+            far[nd * 2 * TP + TP + ev] = aY;
         }
     }
+}
+
+template <typename real, int P>
+constexpr size_t far_coef_smem() {
+    return sizeof(real) * (((far_pack_offset(P + 1, P) + 3) & ~3) + 2 * MI<P>::T);
+}
+
+// FP32 far-field coefficients: one block per (node, table), one thread per
+// output j of the evaluation order (blockDim = n_terms_pad(P) rounded up to
+// 32), E[j] = sum_k M[k] tab[k][j] over the table transposed and padded
+// (tab[k][j], rows of far_tr(P) columns, Yukawa then Laplace, zeros off the
+// degree pattern): the warp's 32 threads read consecutive entries of a row
+// (L1-resident after first use) against the node's moments broadcast from
+// shared memory.  The problem is small (nodes x 2 T outputs), so the work is
+// spread over as many warps as it has outputs to hide the load latency.
+__host__ __device__ constexpr int far_tr(int P) { return (n_terms_pad(P) + 31) & ~31; }
+template <int P>
+__global__ void __launch_bounds__(256) k_far_f32(UpArgs a, const float* __restrict__ mom) {
+    constexpr int T = MI<P>::T;
+    constexpr int TP = n_terms_pad(P);
+    constexpr int TR = far_tr(P);
+    __shared__ float m[T];
+    const int64_t nd = blockIdx.x;
+    const int t = blockIdx.y;  // 0: Yukawa (moments T .. 2T-1), 1: Laplace
+    if (!a.src_active[a.nbody[nd]]) return;  // block-uniform
+    for (int k = threadIdx.x; k < T; k += blockDim.x) m[k] = mom[nd * 2 * T + (t == 0 ? T : 0) + k];
+    __syncthreads();
+    const int j = threadIdx.x;
+    const float* __restrict__ tab = (const float*)a.far_tab + (size_t)t * T * TR + j;
+    float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll 8
+    for (int k = 0; k + 1 < T; k += 2) {
+        acc0 += m[k] * __ldg(tab + (size_t)k * TR);
+        acc1 += m[k + 1] * __ldg(tab + (size_t)(k + 1) * TR);
+    }
+    if (T & 1) acc0 += m[T - 1] * __ldg(tab + (size_t)(T - 1) * TR);
+    if (j < TP) ((float*)a.far)[nd * 2 * TP + (t == 0 ? TP : 0) + j] = acc0 + acc1;
 }
 
 // ---------------------------------------------------------------- fused upward pass

@@ -15,9 +15,27 @@ static void launch_p(int stage, const UpArgs& up, const std::vector<int64_t>& up
         const int64_t grid = up.p2m_grid > 0 ? std::min<int64_t>(up.n_leaves, up.p2m_grid) : up.n_leaves;
         k_upward<real, P><<<(unsigned)grid, 128, 0, s>>>(up, (const v4*)src, (real*)mom);
         (void)up_levels;
-        const int64_t gf = (up.n_nodes + 3) / 4;   // four nodes (warps) per block
-        const int64_t gfc = up.p2m_grid > 0 ? std::min<int64_t>(gf, up.p2m_grid) : gf;
-        k_far_coef<real, P><<<(unsigned)std::max<int64_t>(gfc, 1), 128, 0, s>>>(up, (const real*)mom);
+        if constexpr (sizeof(real) == sizeof(float)) {
+            // FP32: a block per (node, table), a thread per output
+            if (up.n_nodes > 0)
+                k_far_f32<P><<<dim3((unsigned)up.n_nodes, 2), far_tr(P), 0, s>>>(up, (const float*)mom);
+            return;
+        }
+        // FP64: a few blocks per SM, each with the packed table in shared
+        // memory, taking the nodes in turn
+        constexpr size_t smem = far_coef_smem<real, P>();
+        static bool attr_set = false;  // per instantiation
+        if (!attr_set) {
+            PGB_CUDA(cudaFuncSetAttribute(k_far_coef<real, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+            attr_set = true;
+        }
+        int dev = 0, n_sm = 0;
+        PGB_CUDA(cudaGetDevice(&dev));
+        PGB_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+        int64_t gf = std::min<int64_t>(up.n_nodes, 4 * (int64_t)n_sm);
+        if (up.p2m_grid > 0) gf = std::min<int64_t>(gf, up.p2m_grid);
+        k_far_coef<real, P><<<(unsigned)std::max<int64_t>(gf, 1), 128, smem, s>>>(up, (const real*)mom);
     }
     // FP64 M2P: 4 warps per block (its registers would otherwise fill an SM)
     constexpr int NW = sizeof(real) == 8 ? 4 : 8;
