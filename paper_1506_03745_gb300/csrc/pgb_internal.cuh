@@ -248,6 +248,8 @@ struct pgb_ctx {
     pgb::DBuf<pgb::dbl4> d_corr_val, d_xcorr_val;  // dVL, dKL, dVY, dKY
     pgb::DBuf<float4> d_corr_val32, d_xcorr_val32;  // their FP32 copies (the FP32 product)
     pgb::DBuf<double> d_yfine;             // 19-point nodes per panel (3 each), for the corrections
+    pgb::DBuf<double> d_yfine_ds, d_y_ds;  // the 19- and K-point nodes as double-single pairs (8 bytes each)
+    pgb::DBuf<float4> d_corr_pf4, d_corr_nlo4, d_corr_nhi4;  // FP32 prefilter of the near-field search
     pgb::DBuf<int32_t> d_corr_tmp;         // candidates kept by the counting pass (PGB_CORR_CAP per panel)
     pgb::DBuf<double> d_xbatch;            // solution buffer of pgb_solve_batch
     // adjoint (transposed treecode): built on first use after each tree build

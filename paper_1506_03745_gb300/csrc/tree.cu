@@ -6,6 +6,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "ds.cuh"
 #include "pgb_internal.cuh"
 
 namespace pgb {
@@ -1206,6 +1207,11 @@ void refresh_lists(pgb_ctx* c) {
 struct CorrArgs {
     const int32_t *nchild, *child, *nstart, *nend;
     const double *clo, *chi, *a8, *C, *A;
+    // FP32 copies for the prefilters: per panel (centroid, sqrt(8 A)), per
+    // node (box low corner, sqrt(a8)) and (box high corner, 0); delta bounds
+    // the error of a difference of two FP32-rounded coordinates
+    const float4 *pf4, *nlo4, *nhi4;
+    float delta;
     int n_bodies;
     int prob[PGB_MAX_BODIES];    // problem of each body (no entries across problems)
     int in_set[PGB_MAX_BODIES];  // bodies taking part (targets and sources; a region's boundary)
@@ -1216,46 +1222,109 @@ struct CorrArgs {
 // The counting pass also keeps the first `cap` candidates of each target in
 // tmp (row i at tmp + i * cap) and raises *overflow when a target has more,
 // so that the fill pass is needed only then.
-__global__ void k_corr_find(CorrArgs a, int64_t n, bool fill, bool cross, const int32_t* pbody, int64_t* cnt,
-                            const int64_t* off, int32_t* cj, int32_t* tmp, int cap, int* overflow) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double x[3] = {a.C[3 * i], a.C[3 * i + 1], a.C[3 * i + 2]};
-    int32_t stack[PGB_LIST_STACK];
-    int64_t k = 0, w = fill ? off[i] : 0;
-    const int ib = pbody[i];
-    for (int b = 0; b < a.n_bodies && a.in_set[ib]; ++b) {
-        if ((b != ib) != cross || a.prob[b] != a.prob[ib] || !a.in_set[b]) continue;
+// One warp per 32 consecutive targets (sorted order, so they lie close
+// together): the warp walks the union of the nodes its targets need (a node
+// is opened when any lane's target is within its reach, the FP64 test of the
+// per-target walk), and at a leaf every lane tests its own target against
+// the leaf's panels.  The panel test is prefiltered in FP32 on the FP64
+// differences (a panel is skipped only when its squared distance exceeds
+// 8 A_j by more than 1e-5 relative, far above the FP32 rounding of the
+// squares) and decided in FP64 as the oracle does, so each row holds the
+// per-target walk's entries in the same depth-first order.
+#define CORR_WARPS 4
+__global__ void __launch_bounds__(32 * CORR_WARPS) k_corr_find(CorrArgs a, int64_t n, bool fill, bool cross,
+                                                               const int32_t* pbody, int64_t* cnt,
+                                                               const int64_t* off, int32_t* cj, int32_t* tmp,
+                                                               int cap, int* overflow) {
+    __shared__ int32_t stack[CORR_WARPS][PGB_LIST_STACK];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i0 = ((int64_t)blockIdx.x * CORR_WARPS + w) * 32;
+    if (i0 >= n) return;  // warp-uniform
+    const int64_t i = i0 + lane;
+    const bool valid = i < n;
+    const int64_t ii = valid ? i : i0;
+    const double x[3] = {a.C[3 * ii], a.C[3 * ii + 1], a.C[3 * ii + 2]};
+    const float xf[3] = {(float)x[0], (float)x[1], (float)x[2]};
+    int64_t k = 0, wr = fill && valid ? off[i] : 0;
+    const int ib = pbody[ii];
+    for (int b = 0; b < a.n_bodies; ++b) {
+        const bool mine = valid && a.in_set[ib] && ((b != ib) == cross) && a.prob[b] == a.prob[ib] && a.in_set[b];
+        if (!__any_sync(0xffffffffu, mine)) continue;
         int sp = 0;
-        stack[sp++] = b;
+        if (lane == 0) stack[w][0] = b;
+        sp = 1;
+        __syncwarp();
         while (sp > 0) {
-            int nd = stack[--sp];
-            double d2 = 0;
-            for (int q = 0; q < 3; ++q) {
-                double u = fmax(fmax(a.clo[3 * nd + q] - x[q], x[q] - a.chi[3 * nd + q]), 0.0);
-                d2 += u * u;
+            const int nd = stack[w][--sp];
+            __syncwarp();
+            bool need = false;
+            if (mine) {
+                // conservative FP32 form of the FP64 test d2 < a8 (or d2 = 0):
+                // a node it passes may still hold no candidate (the panel test
+                // below decides), a node it fails holds none
+                const float4 lo = a.nlo4[nd], hi = a.nhi4[nd];
+                const float ux = fmaxf(fmaxf(lo.x - xf[0], xf[0] - hi.x), 0.f);
+                const float uy = fmaxf(fmaxf(lo.y - xf[1], xf[1] - hi.y), 0.f);
+                const float uz = fmaxf(fmaxf(lo.z - xf[2], xf[2] - hi.z), 0.f);
+                const float d2 = ux * ux + uy * uy + uz * uz;
+                const float reach = lo.w + a.delta;
+                need = d2 < reach * reach * 1.000004f || d2 == 0.f;
             }
-            if (!(d2 < a.a8[nd]) && !(d2 == 0.0)) continue;
+            if (!__any_sync(0xffffffffu, need)) continue;
             if (a.nchild[nd] == 0) {
-                for (int64_t j = a.nstart[nd]; j < a.nend[nd]; ++j) {
-                    double dx = x[0] - a.C[3 * j], dy = x[1] - a.C[3 * j + 1], dz = x[2] - a.C[3 * j + 2];
-                    double dd = dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz));
-                    if (j == i || dd < 8.0 * a.A[j]) {
-                        if (fill) cj[w++] = (int32_t)j;
-                        else if (k < cap) tmp[i * cap + k] = (int32_t)j;
-                        ++k;
+                if (need) {
+                    for (int64_t j = a.nstart[nd]; j < a.nend[nd]; ++j) {
+                        // FP32 distance of the rounded centroids, off by at most
+                        // delta: clearly outside or inside 2L is decided here,
+                        // the band between goes to the FP64 test of the oracle
+                        const float4 pj = a.pf4[j];
+                        const float fx = xf[0] - pj.x, fy = xf[1] - pj.y, fz = xf[2] - pj.z;
+                        const float fd = __fmaf_rn(fx, fx, __fmaf_rn(fy, fy, fz * fz));
+                        const float up = pj.w + a.delta, dn = pj.w - a.delta;
+                        bool near = j == ii;
+                        if (!near) {
+                            if (fd > up * up * 1.000004f) continue;
+                            if (dn > 0.5f * pj.w && fd < dn * dn * 0.999996f) {
+                                near = true;
+                            } else {
+                                const double dx = x[0] - a.C[3 * j], dy = x[1] - a.C[3 * j + 1],
+                                             dz = x[2] - a.C[3 * j + 2];
+                                const double dd = dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz));
+                                near = dd < 8.0 * a.A[j];
+                            }
+                        }
+                        if (near) {
+                            if (fill) cj[wr++] = (int32_t)j;
+                            else if (k < cap) tmp[ii * cap + k] = (int32_t)j;
+                            ++k;
+                        }
                     }
                 }
             } else {
-                int fc = a.child[nd], m = a.nchild[nd];
+                const int fc = a.child[nd], m = a.nchild[nd];
                 if (sp + m > PGB_LIST_STACK) continue;
-                for (int q = m - 1; q >= 0; --q) stack[sp++] = fc + q;
+                if (lane == 0)
+                    for (int q = m - 1; q >= 0; --q) stack[w][sp + (m - 1 - q)] = fc + q;
+                sp += m;
+                __syncwarp();
             }
         }
     }
-    if (!fill) {
+    if (!fill && valid) {
         cnt[i] = k;
         if (k > cap) atomicOr(overflow, 1);
+    }
+}
+
+// FP32 prefilter data of the near-field search (CorrArgs).
+__global__ void k_corr_prefilter(int64_t n, int64_t nn, const double* C, const double* A, const double* clo,
+                                 const double* chi, const double* a8, float4* pf4, float4* nlo4, float4* nhi4) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n)
+        pf4[t] = make_float4((float)C[3 * t], (float)C[3 * t + 1], (float)C[3 * t + 2], sqrtf((float)(8.0 * A[t])));
+    if (t < nn) {
+        nlo4[t] = make_float4((float)clo[3 * t], (float)clo[3 * t + 1], (float)clo[3 * t + 2], sqrtf((float)a8[t]));
+        nhi4[t] = make_float4((float)chi[3 * t], (float)chi[3 * t + 1], (float)chi[3 * t + 2], 0.f);
     }
 }
 
@@ -1265,55 +1334,6 @@ __global__ void k_corr_compact(int64_t n, const int64_t* off, const int32_t* tmp
     if (i >= n) return;
     const int64_t b = off[i], e = off[i + 1];
     for (int64_t k = b; k < e; ++k) cj[k] = tmp[i * cap + (k - b)];
-}
-
-// Coefficients 1/k! of the Taylor series of e^z.
-template <int K>
-struct ExpCoef {
-    static constexpr double v = ExpCoef<K - 1>::v / K;
-};
-template <>
-struct ExpCoef<0> {
-    static constexpr double v = 1.0;
-};
-
-// Kernel values at a target x from a source point y with normal n (no 1/4pi);
-// 1/r by one Newton step on the SFU estimate (relative error < 2e-13).
-// Without LAP only the Yukawa pair (vy, ky) is formed.  e^{-kappa r}: with
-// SHIFT, e0 * e^z, z = kappa (r0 - r), e0 = e^{-kappa r0} and |z| <= 0.05
-// (r0 = |x - c_j|, every node lies within rho_j of c_j and kappa rho_j <= 0.05),
-// the series to degree 7 (remainder < 1.1e-15 relative); else exp2_taylor.
-template <bool LAP, bool SHIFT>
-__device__ __forceinline__ void kern4(const double* x, const double* y, const double* n, double kappa, double w,
-                                      double kr0, double e0, double& vl, double& kl, double& vy, double& ky) {
-    double dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
-    double r2 = dx * dx + dy * dy + dz * dz;
-    if (!(r2 > 0)) return;
-    double ri = rsqrt_nr<1>(r2);
-    double r = r2 * ri;
-    double nd = n[0] * dx + n[1] * dy + n[2] * dz;
-    double e;
-    if (SHIFT) {
-        const double z = fma(-kappa, r, kr0);
-        double p = ExpCoef<7>::v;
-        p = fma(p, z, ExpCoef<6>::v);
-        p = fma(p, z, ExpCoef<5>::v);
-        p = fma(p, z, ExpCoef<4>::v);
-        p = fma(p, z, ExpCoef<3>::v);
-        p = fma(p, z, ExpCoef<2>::v);
-        p = fma(p, z, 1.0);
-        p = fma(p, z, 1.0);
-        e = e0 * p;
-    } else {
-        e = exp2_taylor(-kappa * 1.4426950408889634 * r);
-    }
-    double ri3 = ri * ri * ri;
-    if (LAP) {
-        vl += w * ri;
-        kl += w * nd * ri3;
-    }
-    vy += w * e * ri;
-    ky += w * nd * (1.0 + kappa * r) * e * ri3;
 }
 
 // Fine-rule (19-point) nodes of every panel, mapped like the K-point nodes.
@@ -1329,14 +1349,45 @@ __global__ void k_fine_nodes(int64_t n, const double* V, const double* C, Rules 
                                   r.mun[m][2] * (v[6 + a] - cjp[a]));
 }
 
-template <bool LAP, bool SHIFT>
-__device__ __forceinline__ void corr_sums(const double* x, const double* nj, int64_t j, const double* YF,
-                                          const double* Y, const double* W, double Aj, const Rules& r, double kappa,
-                                          double kr0, double e0, double* tv, double* kv) {
+// Quadrature nodes (3 doubles each) split into double-single once per build.
+__global__ void k_nodes_to_ds(const double* __restrict__ in, ds* __restrict__ out, int64_t n) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n) out[t] = ds_from_double(in[t]);
+}
+
+// Kernel values at a target x from a source point y with normal n (no 1/4pi)
+// in double-single arithmetic (about 48 significant bits, on the FP32 pipe):
+// V_L, K_L (with LAP), V_Y, K_Y weighted by w.
+template <bool LAP>
+__device__ __forceinline__ void kern4_ds(const ds* x, const ds* y, const ds* n, ds kappa, ds w, ds& vl, ds& kl,
+                                         ds& vy, ds& ky) {
+    const ds dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
+    const ds r2 = ds_fma(dx, dx, ds_fma(dy, dy, dz * dz));
+    if (!(r2.hi > 0.f)) return;
+    const ds ri = ds_rsqrt(r2);
+    const ds r = r2 * ri;
+    const ds nd = ds_fma(n[0], dx, ds_fma(n[1], dy, n[2] * dz));
+    const ds kr = kappa * r;
+    const ds e = ds_exp(-kr);
+    const ds ri3 = (ri * ri) * ri;
+    const ds wn = w * nd;
+    if (LAP) {
+        vl = ds_fma(w, ri, vl);
+        kl = ds_fma(wn, ri3, kl);
+    }
+    vy = ds_fma(w * e, ri, vy);
+    ky = ds_fma((wn * (kr + ds(1))) * e, ri3, ky);
+}
+
+template <bool LAP>
+__device__ __forceinline__ void corr_sums_ds(const ds* x, const ds* nj, int64_t j, const ds* YF, const ds* Y,
+                                             const double* W, double Aj, const Rules& r, ds kappa, ds* tv, ds* kv) {
     for (int m = 0; m < r.Kn; ++m)
-        kern4<LAP, SHIFT>(x, YF + 3 * (j * r.Kn + m), nj, kappa, r.wn[m] * Aj, kr0, e0, tv[0], tv[1], tv[2], tv[3]);
+        kern4_ds<LAP>(x, YF + 3 * (j * r.Kn + m), nj, kappa, ds_from_double(r.wn[m] * Aj), tv[0], tv[1], tv[2],
+                      tv[3]);
     for (int m = 0; m < r.K; ++m)
-        kern4<LAP, SHIFT>(x, Y + 3 * (j * r.K + m), nj, kappa, W[j * r.K + m], kr0, e0, kv[0], kv[1], kv[2], kv[3]);
+        kern4_ds<LAP>(x, Y + 3 * (j * r.K + m), nj, kappa, ds_from_double(W[j * r.K + m]), kv[0], kv[1], kv[2],
+                      kv[3]);
 }
 
 __device__ __forceinline__ int64_t owner_row(const int64_t* off, int64_t n, int64_t e) {
@@ -1350,43 +1401,28 @@ __device__ __forceinline__ int64_t owner_row(const int64_t* off, int64_t n, int6
 }
 
 // Correction entries (i, j), j != i: 19-point rule minus the K-point sum,
-// for V_L, K_L, V_Y, K_Y (Section 3.1), FP64, one thread per entry; the
-// Laplace pair only where it enters a row (same dielectric body).
-__global__ void k_corr_values(int64_t n, int64_t tot, const int64_t* off, const int32_t* cj, const double* YF,
-                              const double* V, const double* C, const double* Nn, const double* A, const double* Y,
-                              const double* W, const int32_t* pbody, BodyDev bd, Rules r, double kappa, dbl4* out) {
+// for V_L, K_L, V_Y, K_Y (Section 3.1), one thread per entry, in
+// double-single arithmetic from the nodes split once per build (YF, Y); the
+// Laplace pair only where it enters a row (same dielectric body).  The
+// semi-analytical self entries stay FP64 (k_corr_self).
+__global__ void k_corr_values(int64_t n, int64_t tot, const int64_t* off, const int32_t* cj, const ds* YF,
+                              const double* C, const double* Nn, const double* A, const ds* Y, const double* W,
+                              const int32_t* pbody, BodyDev bd, Rules r, double kappa, dbl4* out) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= tot) return;
     const int64_t i = owner_row(off, n, e);
     const int64_t j = cj[e];
     if (j == i) return;  // self entries: k_corr_self
-    const double* x = C + 3 * i;
-    const double* nj = Nn + 3 * j;
+    const ds x[3] = {ds_from_double(C[3 * i]), ds_from_double(C[3 * i + 1]), ds_from_double(C[3 * i + 2])};
+    const ds nj[3] = {ds_from_double(Nn[3 * j]), ds_from_double(Nn[3 * j + 1]), ds_from_double(Nn[3 * j + 2])};
     const int bi = pbody[i], bj = pbody[j];
     const bool lap = bi == bj && bd.kind[bi] == PGB_DIELECTRIC;
-    // r0 = |x - c_j| and the panel radius rho_j about its centroid
-    const double* cjp = C + 3 * j;
-    const double* vj = V + 9 * j;
-    double rho2 = 0;
-    for (int k = 0; k < 3; ++k) {
-        const double ax = vj[3 * k] - cjp[0], ay = vj[3 * k + 1] - cjp[1], az = vj[3 * k + 2] - cjp[2];
-        rho2 = fmax(rho2, ax * ax + ay * ay + az * az);
-    }
-    const double ox = x[0] - cjp[0], oy = x[1] - cjp[1], oz = x[2] - cjp[2];
-    const double r0 = sqrt(ox * ox + oy * oy + oz * oz);
-    const bool shift = kappa * sqrt(rho2) <= 0.05;
-    const double e0 = shift ? exp2_taylor(-kappa * 1.4426950408889634 * r0) : 0.0;
-    const double kr0 = kappa * r0;
-    double tv[4] = {0, 0, 0, 0}, kv[4] = {0, 0, 0, 0};
-    if (lap) {
-        if (shift) corr_sums<true, true>(x, nj, j, YF, Y, W, A[j], r, kappa, kr0, e0, tv, kv);
-        else corr_sums<true, false>(x, nj, j, YF, Y, W, A[j], r, kappa, kr0, e0, tv, kv);
-    } else {
-        if (shift) corr_sums<false, true>(x, nj, j, YF, Y, W, A[j], r, kappa, kr0, e0, tv, kv);
-        else corr_sums<false, false>(x, nj, j, YF, Y, W, A[j], r, kappa, kr0, e0, tv, kv);
-    }
+    const ds kp = ds_from_double(kappa);
+    ds tv[4] = {ds(0), ds(0), ds(0), ds(0)}, kv[4] = {ds(0), ds(0), ds(0), ds(0)};
+    if (lap) corr_sums_ds<true>(x, nj, j, YF, Y, W, A[j], r, kp, tv, kv);
+    else corr_sums_ds<false>(x, nj, j, YF, Y, W, A[j], r, kp, tv, kv);
     double d[4];
-    for (int q = 0; q < 4; ++q) d[q] = (tv[q] - kv[q]) / PGB_FOUR_PI;
+    for (int q = 0; q < 4; ++q) d[q] = ds_to_double(tv[q] - kv[q]) / PGB_FOUR_PI;
     out[e] = dbl4{d[0], d[1], d[2], d[3]};
 }
 
@@ -1468,6 +1504,30 @@ static void build_corr_part(pgb_ctx* c, bool cross, DBuf<int64_t>& off, DBuf<int
         a.prob[b] = c->bodies[b].prob;
         a.in_set[b] = in_set ? in_set[b] : 1;
     }
+    {
+        // prefilter copies, and delta from the largest coordinate of the body
+        // boxes (a difference of two FP32-rounded coordinates of size <= m
+        // is off by at most 2^-23 m per axis; sqrt(3) for the distance, with
+        // a factor 2 of room)
+        const int64_t nn = c->n_nodes;
+        c->d_corr_pf4.resize(n);
+        c->d_corr_nlo4.resize(nn);
+        c->d_corr_nhi4.resize(nn);
+        k_corr_prefilter<<<nblk(std::max(n, nn), 256), 256, 0, s>>>(n, nn, c->d_c, c->d_A, c->d_node_clo,
+                                                                    c->d_node_chi, c->d_node_a8, c->d_corr_pf4,
+                                                                    c->d_corr_nlo4, c->d_corr_nhi4);
+        const int nb = (int)c->bodies.size();
+        std::vector<double> lo(3 * nb), hi(3 * nb);
+        PGB_CUDA(cudaMemcpyAsync(lo.data(), c->d_node_clo.p, 24 * nb, cudaMemcpyDeviceToHost, s));
+        PGB_CUDA(cudaMemcpyAsync(hi.data(), c->d_node_chi.p, 24 * nb, cudaMemcpyDeviceToHost, s));
+        PGB_CUDA(cudaStreamSynchronize(s));
+        double m = 0;
+        for (int q = 0; q < 3 * nb; ++q) m = std::max(m, std::max(fabs(lo[q]), fabs(hi[q])));
+        a.delta = (float)(2.0 * 1.7320508075688772 * ldexp(m, -23)) + 1e-30f;
+        a.pf4 = c->d_corr_pf4;
+        a.nlo4 = c->d_corr_nlo4;
+        a.nhi4 = c->d_corr_nhi4;
+    }
     DBuf<int64_t> cnt;
     cnt.resize(n);
     off.resize(n + 1);
@@ -1475,7 +1535,8 @@ static void build_corr_part(pgb_ctx* c, bool cross, DBuf<int64_t>& off, DBuf<int
     c->d_corr_tmp.resize((size_t)n * cap + 1);
     int* ovf = (int*)(c->d_corr_tmp.p + (size_t)n * cap);
     PGB_CUDA(cudaMemsetAsync(ovf, 0, 4, s));
-    k_corr_find<<<nblk(n, 64), 64, 0, s>>>(a, n, false, cross, c->d_pbody, cnt, nullptr, nullptr, c->d_corr_tmp, cap,
+    k_corr_find<<<nblk(n, 32 * CORR_WARPS), 32 * CORR_WARPS, 0, s>>>(a, n, false, cross, c->d_pbody, cnt, nullptr,
+                                                                     nullptr, c->d_corr_tmp, cap,
                                            ovf);
     PGB_CUDA(cudaGetLastError());
     int h_ovf = 0;
@@ -1488,14 +1549,21 @@ static void build_corr_part(pgb_ctx* c, bool cross, DBuf<int64_t>& off, DBuf<int
     val.resize(tot);
     if (tot) {
         if (h_ovf)
-            k_corr_find<<<nblk(n, 64), 64, 0, s>>>(a, n, true, cross, c->d_pbody, nullptr, off, cj, nullptr, 0, nullptr);
+            k_corr_find<<<nblk(n, 32 * CORR_WARPS), 32 * CORR_WARPS, 0, s>>>(a, n, true, cross, c->d_pbody, nullptr,
+                                                                             off, cj, nullptr, 0, nullptr);
         else
             k_corr_compact<<<nblk(n, 128), 128, 0, s>>>(n, off, c->d_corr_tmp, cap, cj);
         Rules r = make_rules(c->p.K, c->p.K_near, c->p.n_edge);
         c->d_yfine.resize(3 * n * r.Kn);
         k_fine_nodes<<<nblk(n * r.Kn, 256), 256, 0, s>>>(n, c->d_v, c->d_c, r, c->d_yfine);
-        k_corr_values<<<nblk(tot, 128), 128, 0, s>>>(n, tot, off, cj, c->d_yfine, c->d_v, c->d_c, c->d_n, c->d_A, c->d_y,
-                                                     c->d_w, c->d_pbody, body_dev(c), r, kappa, val);
+        // both node sets split into double-single (8 bytes a value, as doubles)
+        c->d_yfine_ds.resize(3 * n * r.Kn);
+        c->d_y_ds.resize(3 * n * r.K);
+        k_nodes_to_ds<<<nblk(3 * n * r.Kn, 256), 256, 0, s>>>(c->d_yfine, (ds*)c->d_yfine_ds.p, 3 * n * r.Kn);
+        k_nodes_to_ds<<<nblk(3 * n * r.K, 256), 256, 0, s>>>(c->d_y, (ds*)c->d_y_ds.p, 3 * n * r.K);
+        k_corr_values<<<nblk(tot, 128), 128, 0, s>>>(n, tot, off, cj, (const ds*)c->d_yfine_ds.p, c->d_c, c->d_n,
+                                                     c->d_A, (const ds*)c->d_y_ds.p, c->d_w, c->d_pbody, body_dev(c),
+                                                     r, kappa, val);
         if (!cross)
             k_corr_self<<<nblk(n, 128), 128, 0, s>>>(n, off, cj, c->d_v, c->d_c, c->d_pbody, body_dev(c), r,
                                                      kappa, val);
@@ -1504,7 +1572,7 @@ static void build_corr_part(pgb_ctx* c, bool cross, DBuf<int64_t>& off, DBuf<int
     if (tot) k_dbl4_to_f4<<<nblk(tot, 256), 256, 0, s>>>(val, val32, tot);
     PGB_CUDA(cudaGetLastError());
     PGB_CUDA(cudaStreamSynchronize(s));
-    PGB_LAUNCHED(c, tot ? 5 : 2);
+    PGB_LAUNCHED(c, tot ? 7 : 2);
 }
 
 // Regions of a nested system (the solvent, then the interior of every
