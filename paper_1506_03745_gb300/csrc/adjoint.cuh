@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(NW * 32) k_m2p_T(TArgs a, const typename V4<re
 
 // Downward shift for every node of one level that has children:
 // L_j(child) += sum_{k >= j} C(k, j) (c - c_child)^{k - j} L_k(c), applied as
-// three one-axis passes (the transpose of the moment shift of k_m2m_level).
+// three one-axis passes (the transpose of the moment shift of the upward pass, up_m2m).
 template <typename real, int P>
 __global__ void __launch_bounds__(256) k_l2l_level(TArgs a, real* __restrict__ Lmom) {
     constexpr int T = MI<P>::T;

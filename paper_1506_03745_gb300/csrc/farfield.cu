@@ -179,10 +179,19 @@ const FarTab& far_table(pgb_ctx* c, double kappa) {
     auto t = std::make_unique<FarTab>();
     t->P = c->p.P;
     t->kappa = kappa;
+    // double-single: hi = the FP32 rounding, lo = the FP32 rounding of the rest
+    std::vector<float> hds(2 * h.size());
+    for (size_t q = 0; q < h.size(); ++q) {
+        const float hi = (float)h[q];
+        hds[2 * q] = hi;
+        hds[2 * q + 1] = (float)(h[q] - (double)hi);
+    }
     t->t64.resize(h.size());
     t->t32.resize(hf.size());
+    t->tds.resize(h.size());
     PGB_CUDA(cudaMemcpyAsync(t->t64.p, h.data(), 8 * h.size(), cudaMemcpyHostToDevice, c->stream));
     PGB_CUDA(cudaMemcpyAsync(t->t32.p, hf.data(), 4 * hf.size(), cudaMemcpyHostToDevice, c->stream));
+    PGB_CUDA(cudaMemcpyAsync(t->tds.p, hds.data(), 4 * hds.size(), cudaMemcpyHostToDevice, c->stream));
     PGB_CUDA(cudaStreamSynchronize(c->stream));
     c->far_tabs.push_back(std::move(t));
     return *c->far_tabs.back();

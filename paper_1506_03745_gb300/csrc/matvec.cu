@@ -10,8 +10,8 @@ void treecode_launch_f32(int stage, int P, const UpArgs& up, const std::vector<i
                          const void* src, const void* xrel, void* mom, void* far, cudaStream_t s);
 void treecode_launch_f64(int stage, int P, const UpArgs& up, const std::vector<int64_t>& lv, const EvalArgs& ev,
                          const void* src, const void* xrel, void* mom, void* far, cudaStream_t s);
-void treecode_launch_ds(int stage, int P, const EvalArgs& ev, const void* src, const void* xrel, const void* far,
-                        cudaStream_t s);
+void treecode_launch_ds(int stage, int P, const UpArgs& up, const EvalArgs& ev, const void* src, const void* xrel,
+                        void* mom, const void* far, cudaStream_t s);
 void convert_src_ds(const void* src64, void* src_ds, int64_t n, cudaStream_t s);
 
 static inline int nblk(int64_t n, int t) { return (int)std::max<int64_t>(1, (n + t - 1) / t); }
@@ -312,9 +312,9 @@ void apply_full(pgb_ctx* c, const double* x, double* y, int precision) { apply_m
 // Upward pass as a CUDA graph: captured (on a private stream; nothing runs
 // there) the first time a tree / buffer / source-activity combination is
 // used, then one cudaGraphLaunch on the context stream per product.
-static void upward_graph(pgb_ctx* c, bool f32, const UpArgs& up, const EvalArgs& ev, const void* src, void* mom,
-                         cudaStream_t on) {
-    auto& gr = c->up_graph[f32 ? 0 : 1];
+static void upward_graph(pgb_ctx* c, int kind, const UpArgs& up, const EvalArgs& ev, const void* src, void* mom,
+                         cudaStream_t on) {  // kind: 0 FP32, 1 FP64, 2 double-single
+    auto& gr = c->up_graph[kind];
     bool ok = gr.exec && gr.tree_gen == c->tree_gen && gr.src == src && gr.mom == mom && gr.ncenter == up.ncenter &&
               gr.p2m_grid == up.p2m_grid && gr.far == up.far && gr.far_tab == up.far_tab;
     for (int b = 0; ok && b < PGB_MAX_BODIES; ++b) ok = gr.src_active[b] == up.src_active[b];
@@ -327,12 +327,14 @@ static void upward_graph(pgb_ctx* c, bool f32, const UpArgs& up, const EvalArgs&
         PGB_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
         std::string why;
         try {
-            if (f32)
+            if (kind == 0)
                 treecode_launch_f32(PGB_STAGE_UPWARD, c->p.P, up, c->level_begin, ev, src, nullptr, mom, up.far,
                                     c->cap_stream);
-            else
+            else if (kind == 1)
                 treecode_launch_f64(PGB_STAGE_UPWARD, c->p.P, up, c->level_begin, ev, src, nullptr, mom, up.far,
                                     c->cap_stream);
+            else
+                treecode_launch_ds(PGB_STAGE_UPWARD, c->p.P, up, ev, src, nullptr, mom, up.far, c->cap_stream);
         } catch (const Error& e) {
             why = e.msg;
         }
@@ -394,6 +396,8 @@ void reserve_product(pgb_ctx* c, int precision) {
         c->d_src_ds.resize(2 * nsrc);
         c->d_mom64.resize((size_t)c->n_nodes * 2 * T);
         c->d_far64.resize((size_t)c->n_nodes * 2 * TP);
+        c->d_mom_ds.resize((size_t)c->n_nodes * 2 * T);
+        c->d_far_ds.resize((size_t)c->n_nodes * 2 * TP);
     }
     (void)far_table(c, c->kappa);
     for (const auto& reg : c->regions) (void)far_table(c, reg->dev.kappa);
@@ -502,11 +506,17 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
         c->d_mom64.resize((size_t)c->n_nodes * 2 * T);
         c->d_far64.resize((size_t)c->n_nodes * 2 * TP);
         up.far = c->d_far64.p;
-        if (precision == PGB_FP64_DS) c->d_src_ds.resize(2 * nsrc);
+        if (precision == PGB_FP64_DS) {
+            c->d_src_ds.resize(2 * nsrc);
+            c->d_mom_ds.resize((size_t)c->n_nodes * 2 * T);
+            c->d_far_ds.resize((size_t)c->n_nodes * 2 * TP);
+            up.far = c->d_far_ds.p;
+        }
     }
+    const bool dsp = precision == PGB_FP64_DS;
     auto tab_for = [&](double kappa) -> const void* {
         const FarTab& t = far_table(c, kappa);
-        return f32 ? (const void*)t.t32.p : (const void*)t.t64.p;
+        return f32 ? (const void*)t.t32.p : dsp ? (const void*)t.tds.p : (const void*)t.t64.p;
     };
     up.far_tab = tab_for(c->kappa);
     if (nested(c)) {
@@ -546,8 +556,8 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
                 if (f32)
                     treecode_launch_f32(stage, P, up, c->level_begin, ev, c->d_src32, c->d_x32, c->d_mom32,
                                         c->d_far32, s);
-                else if (precision == PGB_FP64_DS && stage != PGB_STAGE_UPWARD)
-                    treecode_launch_ds(stage, P, ev, c->d_src_ds, c->d_x64, c->d_far64, s);
+                else if (dsp)
+                    treecode_launch_ds(stage, P, up, ev, c->d_src_ds, c->d_x64, c->d_mom_ds, c->d_far_ds, s);
                 else
                     treecode_launch_f64(stage, P, up, c->level_begin, ev, c->d_src64, c->d_x64, c->d_mom64,
                                         c->d_far64, s);
@@ -590,12 +600,15 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
     PGB_CUDA(cudaStreamWaitEvent(us, c->up_fork[pi], 0));
     {
         StageTimer tm(c, PGB_STAGE_UPWARD + (f32 ? 0 : PGB_STAGE_FP64), us);
+        const void* usrc = f32 ? (const void*)c->d_src32.p : dsp ? (const void*)c->d_src_ds.p : (const void*)c->d_src64.p;
+        void* umom = f32 ? (void*)c->d_mom32.p : dsp ? (void*)c->d_mom_ds.p : (void*)c->d_mom64.p;
         if (c->p.graphs)
-            upward_graph(c, f32, up, ev, f32 ? (const void*)c->d_src32.p : (const void*)c->d_src64.p,
-                         f32 ? (void*)c->d_mom32.p : (void*)c->d_mom64.p, us);
+            upward_graph(c, f32 ? 0 : dsp ? 2 : 1, up, ev, usrc, umom, us);
         else if (f32)
             treecode_launch_f32(PGB_STAGE_UPWARD, P, up, c->level_begin, ev, c->d_src32, c->d_x32, c->d_mom32,
                                 c->d_far32, us);
+        else if (dsp)
+            treecode_launch_ds(PGB_STAGE_UPWARD, P, up, ev, c->d_src_ds, c->d_x64, c->d_mom_ds, c->d_far_ds, us);
         else
             treecode_launch_f64(PGB_STAGE_UPWARD, P, up, c->level_begin, ev, c->d_src64, c->d_x64, c->d_mom64,
                                 c->d_far64, us);
@@ -608,8 +621,8 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
         StageTimer tm(c, stage + (f32 ? 0 : PGB_STAGE_FP64));
         if (f32)
             treecode_launch_f32(stage, P, up, c->level_begin, ev, c->d_src32, c->d_x32, c->d_mom32, c->d_far32, s);
-        else if (precision == PGB_FP64_DS && stage != PGB_STAGE_UPWARD)
-            treecode_launch_ds(stage, P, ev, c->d_src_ds, c->d_x64, c->d_far64, s);
+        else if (dsp)
+            treecode_launch_ds(stage, P, up, ev, c->d_src_ds, c->d_x64, c->d_mom_ds, c->d_far_ds, s);
         else
             treecode_launch_f64(stage, P, up, c->level_begin, ev, c->d_src64, c->d_x64, c->d_mom64, c->d_far64, s);
         PGB_CUDA(cudaGetLastError());

@@ -105,6 +105,7 @@ struct FarTab {
     double kappa = 0.0;
     DBuf<double> t64;
     DBuf<float> t32;
+    DBuf<double> tds;  // the FP64 table split into double-single pairs (8 bytes each)
 };
 // padded coefficient count per kernel: rows of 16 bytes for vector loads
 __host__ __device__ constexpr int n_terms_pad(int P) { return (n_terms(P) + 3) & ~3; }
@@ -281,6 +282,7 @@ struct pgb_ctx {
     uint64_t arrive_gen[2] = {~0ull, ~0ull};  // tree_gen the counters were zeroed for
     pgb::DBuf<float> d_far32;            // far-field coefficients: 2 * n_terms_pad(P) per node
     pgb::DBuf<double> d_far64;
+    pgb::DBuf<double> d_mom_ds, d_far_ds;  // moments and coefficients of the double-single product (8 bytes each)
     std::vector<std::unique_ptr<pgb::FarTab>> far_tabs;  // per (P, kappa)
     pgb::DBuf<double> d_phi_part;        // chunk partial sums of phi_reac (few charges)
     pgb::DBuf<pgb::dbl4> d_qw;           // charge weights per sorted panel (energies): own charges
@@ -318,7 +320,7 @@ struct pgb_ctx {
         const double* ncenter = nullptr;
         int p2m_grid = 0;
         int src_active[PGB_MAX_BODIES] = {0};
-    } up_graph[2];
+    } up_graph[3];  // FP32, FP64, double-single
     cudaStream_t cap_stream = nullptr;   // capture only (nothing runs on it)
     // the upward pass of a product runs on its own (highest-priority) stream
     // beside the P2P kernel, which does not need the moments; per precision

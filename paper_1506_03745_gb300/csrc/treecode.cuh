@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(NW * 32) k_p2p(EvalArgs a, const typename V4<r
 template <typename real, int P, int NW>
 __global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a,
                                                  const typename V4<typename Store<real>::S>::t* __restrict__ xrel,
-                                                 const typename Store<real>::S* __restrict__ far) {
+                                                 const real* __restrict__ far) {
     using S = typename Store<real>::S;  // storage type of the inputs
     using s4 = typename V4<S>::t;
     constexpr int TP = n_terms_pad(P);
@@ -550,7 +550,7 @@ __global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a,
         }
         return ee;
     };
-    S pm[MW];
+    real pm[MW];
     int nd = -1;
     S ox = 0, oy = 0, oz = 0;
     int64_t e = seek(fb + w);
@@ -559,7 +559,7 @@ __global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a,
 #pragma unroll
         for (int q = 0; q < MW; ++q) {
             const int k = lane + 32 * q;
-            pm[q] = k < 2 * TP ? far[(int64_t)nd * 2 * TP + k] : S(0);
+            pm[q] = k < 2 * TP ? far[(int64_t)nd * 2 * TP + k] : real(0);
         }
     }
     while (e < f1) {
@@ -567,7 +567,7 @@ __global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a,
 #pragma unroll
         for (int q = 0; q < MW; ++q) {
             const int k = lane + 32 * q;
-            if (k < 2 * TP) sM[w][k] = to_c<real>(pm[q]);
+            if (k < 2 * TP) sM[w][k] = pm[q];
         }
         __syncwarp();
         const bool lap = (a.nbody[nd] == gb) && a.lap_body[gb];
@@ -578,7 +578,7 @@ __global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a,
 #pragma unroll
             for (int q = 0; q < MW; ++q) {
                 const int k = lane + 32 * q;
-                pm[q] = k < 2 * TP ? far[(int64_t)nd * 2 * TP + k] : S(0);
+                pm[q] = k < 2 * TP ? far[(int64_t)nd * 2 * TP + k] : real(0);
             }
         }
         real uL, uY;
@@ -597,7 +597,7 @@ struct UpArgs {
     int src_active[PGB_MAX_BODIES];
     const double* ncenter;
     int K;
-    int64_t lvl_begin, lvl_end;  // node ids of the level for k_m2m_level
+    int64_t lvl_begin, lvl_end;  // node ids of one level (unused by k_upward)
     int p2m_grid;                // > 0: P2M over at most this many blocks (leaves strided)
     int64_t n_nodes;             // k_far_coef: every node
     const void* far_tab;         // its table (farfield.cu) in the arithmetic type
@@ -610,176 +610,6 @@ __device__ __constant__ const int kBinom[9][9] = {
     {1, 0, 0, 0, 0, 0, 0, 0, 0},      {1, 1, 0, 0, 0, 0, 0, 0, 0},      {1, 2, 1, 0, 0, 0, 0, 0, 0},
     {1, 3, 3, 1, 0, 0, 0, 0, 0},      {1, 4, 6, 4, 1, 0, 0, 0, 0},      {1, 5, 10, 10, 5, 1, 0, 0, 0},
     {1, 6, 15, 20, 15, 6, 1, 0, 0},   {1, 7, 21, 35, 35, 21, 7, 1, 0}, {1, 8, 28, 56, 70, 56, 28, 8, 1}};
-
-// P2M: moments of every leaf about its centre, u = c - y (one block per leaf,
-// one thread per multi-index k).  The double-layer part is split off:
-//   M_k = sum_s q_s u^k + sum_a k_a D_a[k - e_a],  D_a[k'] = sum_s p_{s,a} u^{k'},
-// so each (point, k) costs one monomial (two products of cached powers) and
-// five multiply-adds; the D_a (|k'| <= P - 1) meet the Q sums in shared memory.
-template <typename real, int P>
-__global__ void __launch_bounds__(128) k_p2m_leaves(UpArgs a, const typename V4<real>::t* __restrict__ src,
-                                                    real* __restrict__ mom) {
-    using v4 = typename V4<real>::t;
-    constexpr int T = MI<P>::T;
-    constexpr int TD = P * (P + 1) * (P + 2) / 6;  // terms of degree <= P - 1
-    static_assert(T <= 2 * 128, "two terms per thread at most");
-    __shared__ real pw[128][3][P + 1];
-    __shared__ real sq[128][5];
-    __shared__ real sd[3][TD > 0 ? TD : 1];
-    __shared__ short idx3[P + 1][P + 1][P + 1];
-    const int tid = threadIdx.x;
-    for (int k = tid; k < T; k += 128) {
-        int x, y, z;
-        decode_mi(k, x, y, z);
-        idx3[x][y][z] = (short)k;
-    }
-    // leaves blockIdx.x, blockIdx.x + gridDim.x, ... (one leaf per block when
-    // the grid covers them; a smaller grid holds fewer SM resources)
-    for (int64_t leaf = blockIdx.x; leaf < a.n_leaves; leaf += gridDim.x) {
-    const int nd = a.leaf_node[leaf];
-    if (!a.src_active[a.nbody[nd]]) continue;
-    const int64_t s0 = (int64_t)a.nstart[nd] * a.K, s1 = (int64_t)a.nend[nd] * a.K;
-    // thread -> terms tid and tid + 128 (when T > 128)
-    int kx[2] = {0, 0}, ky[2] = {0, 0}, kz[2] = {0, 0};
-    bool on[2], low[2];
-    for (int h = 0; h < 2; ++h) {
-        const int k = tid + 128 * h;
-        on[h] = k < T;
-        if (on[h]) decode_mi(k, kx[h], ky[h], kz[h]);
-        low[h] = on[h] && kx[h] + ky[h] + kz[h] < P;  // also a D_a index (k < TD)
-    }
-    real qL[2] = {0, 0}, qY[2] = {0, 0}, dx[2] = {0, 0}, dy[2] = {0, 0}, dz[2] = {0, 0};
-    for (int64_t t = s0; t < s1; t += 128) {
-        const int cnt = (int)min((int64_t)128, s1 - t);
-        __syncthreads();
-        if (tid < cnt) {
-            const v4 A = src[2 * (t + tid)], B = src[2 * (t + tid) + 1];
-            const real u[3] = {-A.x, -A.y, -A.z};
-            for (int q = 0; q < 3; ++q) {
-                real v = 1;
-                for (int m = 0; m <= P; ++m) {
-                    pw[tid][q][m] = v;
-                    v *= u[q];
-                }
-            }
-            sq[tid][0] = A.w;  // qL
-            sq[tid][1] = B.w;  // qY
-            sq[tid][2] = B.x;  // p = w phi n
-            sq[tid][3] = B.y;
-            sq[tid][4] = B.z;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            if (!on[h]) continue;
-            for (int j = 0; j < cnt; ++j) {
-                const real mono = pw[j][0][kx[h]] * pw[j][1][ky[h]] * pw[j][2][kz[h]];
-                qL[h] += sq[j][0] * mono;
-                qY[h] += sq[j][1] * mono;
-                if (low[h]) {
-                    dx[h] += sq[j][2] * mono;
-                    dy[h] += sq[j][3] * mono;
-                    dz[h] += sq[j][4] * mono;
-                }
-            }
-        }
-    }
-    __syncthreads();
-    for (int h = 0; h < 2; ++h)
-        if (low[h]) {
-            const int k = tid + 128 * h;  // terms of degree < P come first in the graded order
-            sd[0][k] = dx[h];
-            sd[1][k] = dy[h];
-            sd[2][k] = dz[h];
-        }
-    __syncthreads();
-    for (int h = 0; h < 2; ++h) {
-        if (!on[h]) continue;
-        const int k = tid + 128 * h;
-        real dl = 0;
-        if (kx[h]) dl += real(kx[h]) * sd[0][idx3[kx[h] - 1][ky[h]][kz[h]]];
-        if (ky[h]) dl += real(ky[h]) * sd[1][idx3[kx[h]][ky[h] - 1][kz[h]]];
-        if (kz[h]) dl += real(kz[h]) * sd[2][idx3[kx[h]][ky[h]][kz[h] - 1]];
-        mom[(int64_t)nd * 2 * T + k] = qL[h] + dl;
-        mom[(int64_t)nd * 2 * T + T + k] = qY[h] + dl;
-    }
-    __syncthreads();  // sd and pw are reused by the next leaf
-    }
-}
-
-// Moment shift for every inner node of one level from its (at most eight)
-// children: M_k(c) = sum_{j<=k} C(k,j) (c - c_child)^{k-j} M_j(c_child).  The
-// shift is separable, so it is applied as three one-axis passes
-// A -> B (x) -> C (y) -> D (z), each output summing at most P+1 terms; all
-// children are shifted at once, then summed in child order.
-template <typename real, int P>
-__global__ void __launch_bounds__(256) k_m2m_level(UpArgs a, real* __restrict__ mom) {
-    constexpr int T = MI<P>::T;
-    __shared__ real bufA[8][2 * T], bufB[8][2 * T];
-    __shared__ real cd[8][3][P + 1];
-    __shared__ real binom[P + 1][P + 1];
-    __shared__ short idx3[P + 1][P + 1][P + 1];
-    __shared__ signed char kk[T][3];
-    const int tid = threadIdx.x;
-    const int64_t nd = a.lvl_begin + blockIdx.x;
-    if (nd >= a.lvl_end) return;
-    const int nc = a.nchild[nd];
-    if (nc == 0 || !a.src_active[a.nbody[nd]]) return;
-    const int fc = a.child[nd];
-    for (int k = tid; k < T; k += blockDim.x) {
-        int x, y, z;
-        decode_mi(k, x, y, z);
-        idx3[x][y][z] = (short)k;
-        kk[k][0] = (signed char)x;
-        kk[k][1] = (signed char)y;
-        kk[k][2] = (signed char)z;
-    }
-    for (int q = tid; q < (P + 1) * (P + 1); q += blockDim.x) {
-        const int n = q / (P + 1), m = q - n * (P + 1);
-        binom[n][m] = (real)kBinom[n][m];
-    }
-    for (int q = tid; q < nc * 2 * T; q += blockDim.x) {
-        const int ci = q / (2 * T), k = q - ci * 2 * T;
-        bufA[ci][k] = mom[(int64_t)(fc + ci) * 2 * T + k];
-    }
-    if (tid < 3 * nc) {
-        const int ci = tid / 3, ax = tid - 3 * ci;
-        const real d = (real)(a.ncenter[3 * nd + ax] - a.ncenter[3 * (fc + ci) + ax]);
-        real v = 1;
-        for (int m = 0; m <= P; ++m) {
-            cd[ci][ax][m] = v;
-            v *= d;
-        }
-    }
-    __syncthreads();
-    // three passes, alternating the two buffers: x (A->B), y (B->A), z (A->B)
-#pragma unroll 1
-    for (int ax = 0; ax < 3; ++ax) {
-        real(*src)[2 * T] = (ax == 1) ? bufB : bufA;
-        real(*dst)[2 * T] = (ax == 1) ? bufA : bufB;
-        for (int it = tid; it < nc * T; it += blockDim.x) {
-            const int ci = it / T, k = it - ci * T;
-            const int k0 = kk[k][0], k1 = kk[k][1], k2 = kk[k][2];
-            const int ka = kk[k][ax];
-            real sL = 0, sY = 0;
-            for (int j = 0; j <= ka; ++j) {
-                const int jx = ax == 0 ? j : k0, jy = ax == 1 ? j : k1, jz = ax == 2 ? j : k2;
-                const int jj = idx3[jx][jy][jz];
-                const real coef = binom[ka][j] * cd[ci][ax][ka - j];
-                sL += coef * src[ci][jj];
-                sY += coef * src[ci][T + jj];
-            }
-            dst[ci][k] = sL;
-            dst[ci][T + k] = sY;
-        }
-        __syncthreads();
-    }
-    for (int k = tid; k < 2 * T; k += blockDim.x) {
-        real acc = 0;
-        for (int ci = 0; ci < nc; ++ci) acc += bufB[ci][k];
-        mom[nd * 2 * T + k] = acc;
-    }
-}
 
 // Degree a + b + c of the evaluation-order index j (a, then b, then c).
 __device__ __forceinline__ int eval_degree(int j, int P) {
@@ -938,8 +768,26 @@ template <typename real>
 __device__ __forceinline__ real ld_cg(const real* p) {
     return __ldcg(p);
 }
+__device__ __forceinline__ ds ld_cg(const ds* p) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    return ds(v.x, v.y);
+}
+// a double in the arithmetic type
+template <typename real>
+__device__ __forceinline__ real from_dbl(double v) {
+    return (real)v;
+}
+template <>
+__device__ __forceinline__ ds from_dbl<ds>(double v) {
+    return ds_from_double(v);
+}
 
-// P2M of node nd (a leaf) into mom[nd]: see k_p2m_leaves.
+// P2M of node nd (a leaf) into mom[nd]: the moments about its centre,
+// u = c - y, one thread per multi-index k (two when T > 128).  The
+// double-layer part is split off:
+//   M_k = sum_s q_s u^k + sum_a k_a D_a[k - e_a],  D_a[k'] = sum_s p_{s,a} u^{k'},
+// so each (point, k) costs one monomial (two products of cached powers) and
+// five multiply-adds; the D_a (|k'| <= P - 1) meet the q sums in shared memory.
 template <typename real, int P>
 __device__ __forceinline__ void up_p2m(const UpArgs& a, int nd, const typename V4<real>::t* __restrict__ src,
                                        real* __restrict__ mom, UpShared<real, P>& sh) {
@@ -970,7 +818,7 @@ __device__ __forceinline__ void up_p2m(const UpArgs& a, int nd, const typename V
                 real v = 1;
                 for (int m = 0; m <= P; ++m) {
                     sh.u.p.pw[tid][q][m] = v;
-                    v *= u[q];
+                    v = v * u[q];
                 }
             }
             sh.u.p.sq[tid][0] = A.w;
@@ -1016,8 +864,11 @@ __device__ __forceinline__ void up_p2m(const UpArgs& a, int nd, const typename V
     }
 }
 
-// Moment shift of node nd from its children (see k_m2m_level); the
-// children's moments are read from L2.
+// Moment shift of node nd from its (at most eight) children,
+// M_k(c) = sum_{j<=k} C(k,j) (c - c_child)^{k-j} M_j(c_child): the shift is
+// separable, so it is applied as three one-axis passes x, y, z, each output
+// summing at most P+1 terms; all children are shifted at once, then summed
+// in child order.  The children's moments are read from L2.
 template <typename real, int P>
 __device__ __forceinline__ void up_m2m(const UpArgs& a, int nd, real* __restrict__ mom, UpShared<real, P>& sh) {
     constexpr int T = MI<P>::T;
@@ -1031,11 +882,11 @@ __device__ __forceinline__ void up_m2m(const UpArgs& a, int nd, real* __restrict
     }
     if (tid < 3 * nc) {
         const int ci = tid / 3, ax = tid - 3 * ci;
-        const real d = (real)(a.ncenter[3 * nd + ax] - a.ncenter[3 * (fc + ci) + ax]);
+        const real d = from_dbl<real>(a.ncenter[3 * nd + ax] - a.ncenter[3 * (fc + ci) + ax]);
         real v = 1;
         for (int m = 0; m <= P; ++m) {
             sh.u.m.cd[ci][ax][m] = v;
-            v *= d;
+            v = v * d;
         }
     }
     __syncthreads();

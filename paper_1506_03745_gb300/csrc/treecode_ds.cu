@@ -1,22 +1,43 @@
-// Double-single evaluation kernels (P2P, M2P) of the FP64-class product: they
-// read the FP64 product's source terms, target offsets and moments (its
-// upward pass runs in FP64) and compute in double-single on the FP32 pipe.
+// Double-single kernels of the FP64-class product (upward pass, far-field
+// coefficients, P2P, M2P): they read the FP64 source terms split into
+// double-single once per product and the FP64 target offsets, and compute
+// in double-single on the FP32 pipe.
+#include <algorithm>
+
 #include "treecode.cuh"
 
 namespace pgb {
 
 template <int P>
-static void launch_ds(int stage, const EvalArgs& ev, const void* src, const void* xrel, const void* far,
-                      cudaStream_t s) {
+static void launch_ds(int stage, const UpArgs& up, const EvalArgs& ev, const void* src, const void* xrel, void* mom,
+                      const void* far, cudaStream_t s) {
     constexpr int NW = 4;   // M2P warps per block (registers, as the FP64 kernel)
     constexpr int NWP = 8;  // P2P warps per block
     const bool persist = ev.p2p_work != nullptr;
+    if (stage == PGB_STAGE_UPWARD && up.n_leaves > 0) {
+        // P2M and the moment shifts, then the far-field coefficients, all in
+        // double-single on the FP32 pipe
+        const int64_t grid = up.p2m_grid > 0 ? std::min<int64_t>(up.n_leaves, up.p2m_grid) : up.n_leaves;
+        k_upward<ds, P><<<(unsigned)grid, 128, 0, s>>>(up, (const ds4*)src, (ds*)mom);
+        constexpr size_t smem = far_coef_smem<ds, P>();
+        static bool attr_set = false;
+        if (!attr_set) {
+            PGB_CUDA(cudaFuncSetAttribute(k_far_coef<ds, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr_set = true;
+        }
+        int dev = 0, n_sm = 0;
+        PGB_CUDA(cudaGetDevice(&dev));
+        PGB_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+        int64_t gf = std::min<int64_t>(up.n_nodes, 4 * (int64_t)n_sm);
+        if (up.p2m_grid > 0) gf = std::min<int64_t>(gf, up.p2m_grid);
+        k_far_coef<ds, P><<<(unsigned)std::max<int64_t>(gf, 1), 128, smem, s>>>(up, (const ds*)mom);
+    }
     if (stage == PGB_STAGE_P2P && ev.n_pitems > 0)
         k_p2p<ds, NWP><<<(unsigned)(persist ? ev.persist_blocks : ev.n_pitems), NWP * 32, 0, s>>>(
             ev, (const ds4*)src, (const dbl4*)xrel);
     if (stage == PGB_STAGE_M2P && ev.n_fitems > 0)
         k_m2p<ds, P, NW><<<(unsigned)(persist ? ev.persist_blocks : ev.n_fitems), NW * 32, 0, s>>>(
-            ev, (const dbl4*)xrel, (const double*)far);
+            ev, (const dbl4*)xrel, (const ds*)far);
 }
 
 // FP64 source terms split into double-single once per product, so that the
@@ -32,18 +53,18 @@ void convert_src_ds(const void* src64, void* src_ds, int64_t n, cudaStream_t s) 
     if (n > 0) k_src_to_ds<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const dbl4*)src64, (ds4*)src_ds, n);
 }
 
-void treecode_launch_ds(int stage, int P, const EvalArgs& ev, const void* src, const void* xrel, const void* far,
-                        cudaStream_t s) {
+void treecode_launch_ds(int stage, int P, const UpArgs& up, const EvalArgs& ev, const void* src, const void* xrel,
+                        void* mom, const void* far, cudaStream_t s) {
     switch (P) {
-        case 0: launch_ds<0>(stage, ev, src, xrel, far, s); break;
-        case 1: launch_ds<1>(stage, ev, src, xrel, far, s); break;
-        case 2: launch_ds<2>(stage, ev, src, xrel, far, s); break;
-        case 3: launch_ds<3>(stage, ev, src, xrel, far, s); break;
-        case 4: launch_ds<4>(stage, ev, src, xrel, far, s); break;
-        case 5: launch_ds<5>(stage, ev, src, xrel, far, s); break;
-        case 6: launch_ds<6>(stage, ev, src, xrel, far, s); break;
-        case 7: launch_ds<7>(stage, ev, src, xrel, far, s); break;
-        case 8: launch_ds<8>(stage, ev, src, xrel, far, s); break;
+        case 0: launch_ds<0>(stage, up, ev, src, xrel, mom, far, s); break;
+        case 1: launch_ds<1>(stage, up, ev, src, xrel, mom, far, s); break;
+        case 2: launch_ds<2>(stage, up, ev, src, xrel, mom, far, s); break;
+        case 3: launch_ds<3>(stage, up, ev, src, xrel, mom, far, s); break;
+        case 4: launch_ds<4>(stage, up, ev, src, xrel, mom, far, s); break;
+        case 5: launch_ds<5>(stage, up, ev, src, xrel, mom, far, s); break;
+        case 6: launch_ds<6>(stage, up, ev, src, xrel, mom, far, s); break;
+        case 7: launch_ds<7>(stage, up, ev, src, xrel, mom, far, s); break;
+        case 8: launch_ds<8>(stage, up, ev, src, xrel, mom, far, s); break;
         default: fail(PGB_EINVAL, "P out of range");
     }
 }
