@@ -38,7 +38,7 @@ METRIC = "treecode matvecs/sec and GMRES solve ms at 1e-5 energy err, FP32+refin
 UNIT = "matvecs/s"
 WORKLOAD = "two spheres r=4 A, 2 x 20480 panels, sigma=0.05 C/m^2, R=12 A"
 PARAMS = dict(K=7, K_near=19, n_edge=9, P=6, theta=0.5, leaf_size=32, group_size=32, p2p_item=64, m2p_item=64,
-              precond=0, graphs=1, lanes=4, overlap=0, batch=1, residual=1)
+              precond=0, graphs=2, lanes=4, overlap=0, batch=1, residual=1)
 TOL = 1e-6
 RESTART = 100
 MAX_ITER = 2000
@@ -748,19 +748,10 @@ def run_gradient(args):
 
 def orientation_landscape(F, n_orient, n_gap, T=300.0):
     """Boltzmann weights of the orientations at each gap (poses ordered
-    orientation-major, gap-minor): probability of the most likely
-    orientation, its index, and the orientation-averaged free energy
-    -kT ln <exp(-F/kT)> (kcal/mol) per gap."""
-    kT = 0.0019872043 * T  # kcal/mol
-    F = np.asarray(F, dtype=float).reshape(n_orient, n_gap)
-    out = []
-    for gi in range(n_gap):
-        f = F[:, gi]
-        z = np.exp(-(f - f.min()) / kT)
-        p = z / z.sum()
-        out.append({"gap_index": gi, "most_likely_orientation": int(p.argmax()), "p_max": float(p.max()),
-                    "free_energy_kcal_mol": float(f.min() - kT * math.log(z.mean()))})
-    return out
+    orientation-major, gap-minor), computed by the library
+    (pgb_orientation_landscape)."""
+    import paper_1506_03745_gb300 as pgb
+    return pgb.pgb_orientation_landscape(F, n_orient, n_gap, T)
 
 
 def run_poses(args):

@@ -73,8 +73,12 @@ typedef struct pgb_params {
     int32_t precond;      /* GMRES preconditioner: 0 none (the paper's solver), 1 block-diagonal: per
                              panel, the inverse of the 2x2 (molecule) or 1x1 (surface) block of its own
                              self terms, applied on the right so the residual test is unchanged */
-    int32_t graphs;       /* 1 (default): the upward pass (P2M + one launch per tree level) is captured
-                             once per tree as a CUDA graph and replayed; 0: plain launches */
+    int32_t graphs;       /* 2 (default): the GMRES iterations after the first column of each restart
+                             cycle are replayed from one CUDA graph whose device-side loop stops on
+                             the residual estimate (no host round trip per iteration), and the
+                             upward pass of every other product (P2M, moment shifts, far-field
+                             coefficients) is captured once per tree and replayed; 1: the upward
+                             pass only; 0: plain launches */
     int32_t lanes;        /* pgb_solve_batch: poses in flight at once, 1..16 (0 = 4); each lane is a copy
                              of the context with its own CUDA stream and host thread, kept between calls */
     int32_t overlap;      /* PGB_FP32_REFINE: 1 starts the FP64 product of the outer residual on a side
@@ -145,7 +149,7 @@ typedef struct pgb_stage_times {
 
 /* Create a context on the current CUDA device.  p may be NULL (defaults:
  * K=7, K_near=19, n_edge=9, P=6, theta=0.5, leaf_size=32, group_size=32,
- * p2p_item=64, m2p_item=64, precond=0, graphs=1, lanes=4, overlap=0,
+ * p2p_item=64, m2p_item=64, precond=0, graphs=2, lanes=4, overlap=0,
  * batch=1, residual=1).
  * cuda_stream is a cudaStream_t (NULL = legacy default stream).  Returns
  * PGB_EINVAL for out-of-range parameters. */
@@ -364,6 +368,21 @@ int pgb_tree_export(struct pgb_ctx* ctx, int32_t* perm, int64_t* near_off, int32
  * PGB_FP64_DS product, each converted back to a double.  PGB_EINVAL for n < 0 or a
  * NULL pointer with n > 0; PGB_ECUDA on a CUDA error. */
 int pgb_math_check(const double* x, int64_t n, double* out);
+
+/* Orientation free-energy landscape of a pose sweep (the application the
+ * paper motivates, Section 1: how a protein orients near a charged surface):
+ * F holds total free energies (kcal/mol) of n_orient orientations x n_gap
+ * separations, orientation-major (F[o * n_gap + g], the order of
+ * pgb_solve_batch poses listed orientation by orientation).  For each
+ * separation g, with Boltzmann weights p_o = e^{-F_o/kT} / sum e^{-F/kT} at
+ * the given temperature (K; k = 0.0019872043 kcal/(mol K)):
+ *   out[3g]     the most likely orientation (its index, as a double),
+ *   out[3g + 1] its probability,
+ *   out[3g + 2] the orientation-averaged free energy -kT ln <e^{-F/kT}>
+ *               (the mean over the n_orient orientations), kcal/mol.
+ * Host arrays; no device call.  PGB_EINVAL for bad sizes, a non-positive
+ * temperature or a non-finite energy. */
+int pgb_orientation_landscape(const double* F, int32_t n_orient, int32_t n_gap, double temperature, double* out);
 
 /* Diagnostic: the host-computed table that turns a node's Taylor moments
  * (Section 3.2) into the coefficients its far field is evaluated from, for

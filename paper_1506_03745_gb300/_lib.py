@@ -91,6 +91,7 @@ _SIGS = {
     "pgb_math_check": (c_i32, [c_vp, c_i64, c_vp]),
     "pgb_alloc_count": (c_i32, [ctypes.POINTER(c_i64)]),
     "pgb_far_table": (c_i32, [c_i32, c_dbl, c_vp, c_i64]),
+    "pgb_orientation_landscape": (c_i32, [c_vp, c_i32, c_i32, c_dbl, c_vp]),
 }
 
 
@@ -371,3 +372,16 @@ def pgb_far_table(P, kappa):
     out = np.zeros(2 * T * T)
     _check(None, lib().pgb_far_table(P, float(kappa), out.ctypes.data_as(c_vp), len(out)))
     return out[:T * T].reshape(T, T), out[T * T:].reshape(T, T)
+
+
+def pgb_orientation_landscape(F, n_orient, n_gap, temperature=300.0):
+    """Per separation: dict(most_likely_orientation, p_max, free_energy_kcal_mol)
+    from F (n_orient x n_gap energies, orientation-major)."""
+    F_, Fp = _hptr(np.asarray(F, dtype=np.float64).reshape(-1), np.float64)
+    if F_.shape[0] != n_orient * n_gap:
+        raise ValueError("F must hold n_orient * n_gap energies")
+    out = np.zeros(3 * n_gap)
+    _check(None, lib().pgb_orientation_landscape(Fp, n_orient, n_gap, float(temperature),
+                                                 out.ctypes.data_as(c_vp)))
+    return [{"gap_index": g, "most_likely_orientation": int(out[3 * g]), "p_max": float(out[3 * g + 1]),
+             "free_energy_kcal_mol": float(out[3 * g + 2])} for g in range(n_gap)]

@@ -110,7 +110,7 @@ static int check_params(const pgb_params* p, std::string& why) {
     else if (p->p2p_item < 0 || p->p2p_item > 4096) why = "p2p_item must be in 1..4096 (0 = default)";
     else if (p->m2p_item < 0 || p->m2p_item > 4096) why = "m2p_item must be in 1..4096 (0 = default)";
     else if (p->precond != 0 && p->precond != 1) why = "precond must be 0 or 1";
-    else if (p->graphs != 0 && p->graphs != 1) why = "graphs must be 0 or 1";
+    else if (p->graphs < 0 || p->graphs > 2) why = "graphs must be 0, 1 or 2";
     else if (p->lanes < 0 || p->lanes > 16) why = "lanes must be in 1..16 (0 = default)";
     else if (p->overlap != 0 && p->overlap != 1) why = "overlap must be 0 or 1";
     else if (p->batch < 0 || p->batch > PGB_MAX_BODIES) why = "batch must be in 1..64 (0 = 1)";
@@ -344,7 +344,7 @@ int pgb_default_params(pgb_params* p) {
     p->p2p_item = 64;
     p->m2p_item = 64;
     p->precond = 0;
-    p->graphs = 1;
+    p->graphs = 2;
     p->lanes = 4;
     p->overlap = 0;
     p->batch = 1;
@@ -406,6 +406,11 @@ int pgb_destroy(pgb_ctx* c) {
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     for (auto& gr : c->up_graph)
         if (gr.exec) cudaGraphExecDestroy(gr.exec);
+    if (c->gm_graph.exec) cudaGraphExecDestroy(c->gm_graph.exec);
+    if (c->gm_stream) {
+        cudaStreamSynchronize(c->gm_stream);
+        cudaStreamDestroy(c->gm_stream);
+    }
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (int q = 0; q < 2; ++q) {
         if (c->up_stream[q]) {
@@ -990,6 +995,31 @@ int pgb_math_check(const double* x, int64_t n, double* out) {
     cudaFree(dx);
     cudaFree(dy);
     return rc;
+}
+
+int pgb_orientation_landscape(const double* F, int32_t n_orient, int32_t n_gap, double temperature, double* out) {
+    if (!F || !out || n_orient < 1 || n_gap < 1 || !(temperature > 0) || !isfinite(temperature)) return PGB_EINVAL;
+    for (int64_t k = 0; k < (int64_t)n_orient * n_gap; ++k)
+        if (!isfinite(F[k])) return PGB_EINVAL;
+    const double kT = 0.0019872043 * temperature;  // Boltzmann constant in kcal/(mol K)
+    for (int gi = 0; gi < n_gap; ++gi) {
+        double fmin = INFINITY;
+        int best = 0;
+        for (int o = 0; o < n_orient; ++o) {
+            const double f = F[(int64_t)o * n_gap + gi];
+            if (f < fmin) {
+                fmin = f;
+                best = o;
+            }
+        }
+        // weights relative to the lowest energy (no overflow), summed in orientation order
+        double z = 0;
+        for (int o = 0; o < n_orient; ++o) z += exp(-(F[(int64_t)o * n_gap + gi] - fmin) / kT);
+        out[3 * gi] = best;
+        out[3 * gi + 1] = 1.0 / z;
+        out[3 * gi + 2] = fmin - kT * log(z / n_orient);
+    }
+    return PGB_OK;
 }
 
 int pgb_alloc_count(int64_t* n) {

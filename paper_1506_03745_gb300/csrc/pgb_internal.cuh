@@ -322,6 +322,24 @@ struct pgb_ctx {
         int src_active[PGB_MAX_BODIES] = {0};
     } up_graph[3];  // FP32, FP64, double-single
     cudaStream_t cap_stream = nullptr;   // capture only (nothing runs on it)
+    // GMRES iterations replayed from a graph with a device-side loop
+    // (pgb_params.graphs = 2): one graph per operator setup, rebuilt when a
+    // pointer or size it holds changes
+    struct GmGraph {
+        cudaGraphExec_t exec = nullptr;
+        uint64_t tree_gen = 0;
+        int prec = -1, m = 0, pc = -1;
+        const void *V = nullptr, *w = nullptr, *H = nullptr, *g = nullptr;
+        int64_t n = 0;
+        int P = -1;
+        double theta = -1;
+        int64_t body_launches = 0;
+    } gm_graph;
+    cudaStream_t gm_stream = nullptr;    // stream of its capture
+    bool capturing = false;              // products enqueue plain launches (no nested graph launch)
+    pgb::DBuf<int> d_gmi;                // device column index of the replayed iterations
+    pgb::DBuf<double> d_gmd;             // tolerance, column limit, last estimate
+    pgb::DBuf<double> d_xsel;            // the column the replayed product reads
     // the upward pass of a product runs on its own (highest-priority) stream
     // beside the P2P kernel, which does not need the moments; per precision
     cudaStream_t up_stream[2] = {nullptr, nullptr};
@@ -436,8 +454,11 @@ struct ArnSeg {
     const int* act;
     int64_t sH, sV;
 };
+// jdev != nullptr: the step of the column index held at jdev on the device
+// (h is then the base of H, column j at h + j (mcap + 1)); buffers sized for
+// columns up to mcap
 void arnoldi_step(pgb_ctx* c, int j, double* w, double* h, double* hc, double* cs, double* sn, double* g,
-                  double* out, const ArnSeg* sg);
+                  double* out, const ArnSeg* sg, const int* jdev = nullptr, int mcap = 0);
 double energy_unit_kcal();
 void phi_reac(pgb_ctx* c, const double* x, double* out);
 // solver (solver.cu)

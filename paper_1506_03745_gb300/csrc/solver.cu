@@ -201,19 +201,26 @@ struct ArnArgs {
     const int64_t* poff;
     const int* act;
     int64_t sH, sV, sP;
+    // jdev != nullptr: the column index is read from device memory (an
+    // Arnoldi step replayed from a graph), j above is ignored and column j
+    // of H is at Hb + j * ldH
+    const int* jdev;
+    double* Hb;
+    int64_t ldH;
 };
+__device__ __forceinline__ int arn_j(const ArnArgs& a) { return a.jdev ? *a.jdev : a.j; }
 
 // The slice of ArnArgs that block (., p) works on; false when p is inactive.
 struct ArnView {
     double *h, *hc, *part, *part2, *cs, *sn, *g, *out;
     int64_t lo, hi;
 };
-__device__ __forceinline__ bool arn_view(const ArnArgs& a, ArnView& v) {
+__device__ __forceinline__ bool arn_view(const ArnArgs& a, int j, ArnView& v) {
     const int p = blockIdx.y;
     if (a.act && !a.act[p]) return false;
     v.lo = a.poff ? a.poff[p] : 0;
     v.hi = a.poff ? a.poff[p + 1] : a.n;
-    v.h = a.h + p * a.sH;
+    v.h = (a.jdev ? a.Hb + (int64_t)j * a.ldH : a.h) + p * a.sH;
     v.hc = a.hc + p * a.sV;
     v.cs = a.cs + p * a.sV;
     v.sn = a.sn + p * a.sV;
@@ -299,9 +306,10 @@ __device__ __forceinline__ void arn_reduce(const double* part, int m, double* co
 
 __global__ void __launch_bounds__(ARN_THREADS) k_arn_dot(ArnArgs a) {
     extern __shared__ double shd[];
+    const int j = arn_j(a);
     ArnView v;
-    if (!arn_view(a, v)) return;
-    arn_block_dots(a, v, a.j + 1, v.part, shd);
+    if (!arn_view(a, j, v)) return;
+    arn_block_dots(a, v, j + 1, v.part, shd);
 }
 
 // pass 0: coefficients into h; pass 1: into hc and h += hc.  Then w -= sum
@@ -309,9 +317,10 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arn_dot(ArnArgs a) {
 // the second-pass dots; pass 1: |w|^2 in part2[b]).
 __global__ void __launch_bounds__(ARN_THREADS) k_arn_update(ArnArgs a, int pass) {
     extern __shared__ double shd[];  // m coefficients, then the dot scratch
+    const int j = arn_j(a);
     ArnView v;
-    if (!arn_view(a, v)) return;
-    const int m = a.j + 1;
+    if (!arn_view(a, j, v)) return;
+    const int m = j + 1;
     double* coef = shd;
     double* scratch = shd + ((m + 31) & ~31);
     arn_reduce(pass ? v.part2 : v.part, m, coef);
@@ -349,8 +358,9 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arn_update(ArnArgs a, int pass)
 
 __global__ void __launch_bounds__(ARN_THREADS) k_arn_finish(ArnArgs a) {
     extern __shared__ double shd[];
+    const int j = arn_j(a);
     ArnView v;
-    if (!arn_view(a, v)) return;
+    if (!arn_view(a, j, v)) return;
     const unsigned nb = gridDim.x;
     double t = 0;
     for (unsigned b = threadIdx.x; b < nb; b += blockDim.x) t += v.part[b];
@@ -360,38 +370,38 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arn_finish(ArnArgs a) {
     const double nrm = shd[32];
     const double inv = nrm > 0 ? 1.0 / nrm : 0.0;  // one division per block, not per row
     const int64_t stride = (int64_t)nb * blockDim.x;
-    double* vn = a.V + (int64_t)(a.j + 1) * a.ld;
+    double* vn = a.V + (int64_t)(j + 1) * a.ld;
     for (int64_t r = v.lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < v.hi; r += stride)
         vn[r] = a.w[r] * inv;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         // Givens step on column j of H (column-major, ld = m + 1): the previous
         // rotations, then the new one, applied to g; out[0] = |g_{j+1}|, out[1] = h_{j+1,j}
         double* h = v.h;
-        h[a.j + 1] = nrm;
-        for (int i = 0; i < a.j; ++i) {
+        h[j + 1] = nrm;
+        for (int i = 0; i < j; ++i) {
             const double x = v.cs[i] * h[i] + v.sn[i] * h[i + 1];
             const double y = -v.sn[i] * h[i] + v.cs[i] * h[i + 1];
             h[i] = x;
             h[i + 1] = y;
         }
-        v.out[1] = h[a.j + 1];
-        const double p = h[a.j], q = h[a.j + 1];
+        v.out[1] = h[j + 1];
+        const double p = h[j], q = h[j + 1];
         const double r = hypot(p, q);
         const double c = r > 0 ? p / r : 1.0, sv = r > 0 ? q / r : 0.0;
-        v.cs[a.j] = c;
-        v.sn[a.j] = sv;
-        h[a.j] = r;
-        h[a.j + 1] = 0;
-        v.g[a.j + 1] = -sv * v.g[a.j];
-        v.g[a.j] = c * v.g[a.j];
-        v.out[0] = fabs(v.g[a.j + 1]);
+        v.cs[j] = c;
+        v.sn[j] = sv;
+        h[j] = r;
+        h[j + 1] = 0;
+        v.g[j + 1] = -sv * v.g[j];
+        v.g[j] = c * v.g[j];
+        v.out[0] = fabs(v.g[j + 1]);
     }
 }
 
 // The four launches of one Arnoldi step; with sg, for the problems of a
 // block-diagonal system (sg->nbp blocks per problem).
 void arnoldi_step(pgb_ctx* c, int j, double* w, double* h, double* hc, double* cs, double* sn, double* g,
-                  double* out, const ArnSeg* sg) {
+                  double* out, const ArnSeg* sg, const int* jdev, int mcap) {
     if (c->arn_blocks == 0) {
         int dev = 0, sms = 0;
         PGB_CUDA(cudaGetDevice(&dev));
@@ -399,7 +409,8 @@ void arnoldi_step(pgb_ctx* c, int j, double* w, double* h, double* hc, double* c
         c->arn_blocks = ARN_BLOCKS_PER_SM * sms;
     }
     const int B = sg ? sg->B : 1;
-    const int nb = sg ? sg->nbp : c->arn_blocks, m = j + 1, warps = ARN_THREADS / 32;
+    // with jdev the column is only known on the device: sizes for the largest (mcap)
+    const int nb = sg ? sg->nbp : c->arn_blocks, m = jdev ? mcap : j + 1, warps = ARN_THREADS / 32;
     c->d_red.resize(std::max<size_t>(c->d_red.n, (size_t)2 * nb * (m + 1) * B));
     ArnArgs a;
     a.V = c->d_V;
@@ -420,6 +431,9 @@ void arnoldi_step(pgb_ctx* c, int j, double* w, double* h, double* hc, double* c
     a.sH = sg ? sg->sH : 0;
     a.sV = sg ? sg->sV : 0;
     a.sP = (int64_t)nb * (m + 1);
+    a.jdev = jdev;
+    a.Hb = h;
+    a.ldH = (int64_t)mcap + 1;
     const size_t dots = 8 * (size_t)std::max(32, m * warps);
     const size_t upd = 8 * (size_t)((m + 31) & ~31) + dots;
     if (upd > 48 * 1024)
@@ -526,9 +540,110 @@ struct Krylov {
     }
 };
 
+// ---------------------------------------------------------------- replayed iterations
+// The column the next replayed product reads: dst = V_j, j from the device.
+__global__ void k_gm_select(const double* __restrict__ V, int64_t n, const int* __restrict__ jdev,
+                            double* __restrict__ dst) {
+    const int64_t j = *jdev;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        dst[r] = V[j * n + r];
+}
+// After the Arnoldi step of column j: keep the estimate, advance j and set the
+// graph's loop condition (go on while the estimate is above the tolerance,
+// no breakdown and columns remain): ctl = {tol, column limit, estimate}.
+__global__ void k_gm_check(const double* __restrict__ out, int* jdev, double* ctl, cudaGraphConditionalHandle h) {
+    const int j = *jdev;
+    const double est = out[0], hnext = out[1];
+    *jdev = j + 1;
+    ctl[2] = est;
+    const bool more = est > ctl[0] && hnext > 0 && (double)(j + 1) < ctl[1];
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
 // Restarted GMRES on A x = b from the given x; precision of the operator
 // `prec`; stops when the (estimated) residual <= abs_tol or after max_it
 // iterations.  Returns iterations done; *matvecs counts operator uses.
+// Graph of the GMRES iterations after the first column of a cycle: a
+// device-side while loop whose body takes column j (k_gm_select), applies the
+// (preconditioned) operator, makes the Arnoldi step of column j and tests the
+// estimate (k_gm_check).  Captured from the launches the host loop makes,
+// with the context's work sent to its own capture stream; rebuilt when the
+// tree, a parameter or a buffer it holds changes (gmres_op also drops it at
+// the start of every call).
+template <class ApplyPc>
+static void gm_graph_ready(pgb_ctx* c, int prec, bool pc, int m, double* w, double* hcol, double* cs, double* sn,
+                           double* g, double* out2, ApplyPc apply_pc) {
+    auto& gg = c->gm_graph;
+    const int64_t n = c->n_unk;
+    if (gg.exec && gg.tree_gen == c->tree_gen && gg.prec == prec && gg.m == m && gg.pc == (int)pc &&
+        gg.V == c->d_V.p && gg.w == w && gg.H == c->d_H.p && gg.g == g && gg.n == n && gg.P == c->p.P &&
+        gg.theta == c->p.theta)
+        return;
+    if (gg.exec) {
+        PGB_CUDA(cudaGraphExecDestroy(gg.exec));
+        gg.exec = nullptr;
+    }
+    if (!c->gm_stream) PGB_CUDA(cudaStreamCreateWithFlags(&c->gm_stream, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    PGB_CUDA(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle h;
+    PGB_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    PGB_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t saved = c->stream;
+    const bool saved_timing = c->timing;
+    const int64_t l0 = c->launches;
+    c->stream = c->gm_stream;
+    c->timing = false;
+    c->capturing = true;
+    std::string why;
+    PGB_CUDA(cudaStreamBeginCaptureToGraph(c->gm_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    try {
+        k_gm_select<<<nblk(n, 256), 256, 0, c->gm_stream>>>(c->d_V, n, c->d_gmi, c->d_xsel);
+        apply_pc(c->d_xsel.p, w);
+        arnoldi_step(c, 0, w, c->d_H, hcol, cs, sn, g, out2, nullptr, c->d_gmi, m);
+        k_gm_check<<<1, 1, 0, c->gm_stream>>>(out2, c->d_gmi, c->d_gmd, h);
+        PGB_LAUNCHED(c, 6);
+    } catch (const Error& e) {
+        why = e.msg;
+    }
+    const cudaError_t le = cudaGetLastError();
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(c->gm_stream, &captured);
+    c->stream = saved;
+    c->timing = saved_timing;
+    c->capturing = false;
+    gg.body_launches = c->launches - l0;
+    c->launches = l0;
+    if (!why.empty() || le != cudaSuccess || ce != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        (void)cudaGetLastError();
+        fail(PGB_ECUDA, "GMRES iteration graph capture: " +
+                            (why.empty() ? std::string(cudaGetErrorString(le != cudaSuccess ? le : ce)) : why));
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&gg.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) gg.exec = nullptr;
+    PGB_CUDA(ie);
+    gg.tree_gen = c->tree_gen;
+    gg.prec = prec;
+    gg.m = m;
+    gg.pc = (int)pc;
+    gg.V = c->d_V.p;
+    gg.w = w;
+    gg.H = c->d_H.p;
+    gg.g = g;
+    gg.n = n;
+    gg.P = c->p.P;
+    gg.theta = c->p.theta;
+}
+
 int gmres_op(pgb_ctx* c, int prec, bool transpose, const double* b, double* x, double abs_tol, int max_it,
              int restart, int* matvecs, double* est_out, bool x_zero, GmresSpec* spec) {
     const bool pc = c->p.precond && c->pc_ready;
@@ -560,6 +675,32 @@ int gmres_op(pgb_ctx* c, int prec, bool transpose, const double* b, double* x, d
     double* yv = hcol + (m + 1);       // m+1
     DBuf<double> misc;
     misc.resize(8);
+    // iterations replayed from a graph (not with the overlap's fork, which
+    // the host decides, nor for the transposed operator)
+    const bool graph = c->p.graphs >= 2 && !spec && !transpose && m >= 2;
+    if (graph) {
+        // The graph holds the launches of this call's operator (kernel
+        // arguments, buffer addresses, grid sizes), which other calls may
+        // change (parameters, trees, buffers): it is captured afresh for
+        // each call, on its first replay, and kept for its restart cycles.
+        if (c->gm_graph.exec) {
+            PGB_CUDA(cudaGraphExecDestroy(c->gm_graph.exec));
+            c->gm_graph.exec = nullptr;
+        }
+        // everything the replayed body touches is sized here, outside the capture
+        c->d_gmi.resize(1);
+        c->d_gmd.resize(3);
+        c->d_xsel.resize(n);
+        if (pc) c->d_pz.resize(n);
+        reserve_product(c, prec);
+        if (c->arn_blocks == 0) {
+            int dev = 0, sms = 0;
+            PGB_CUDA(cudaGetDevice(&dev));
+            PGB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            c->arn_blocks = ARN_BLOCKS_PER_SM * sms;
+        }
+        c->d_red.resize(std::max<size_t>(c->d_red.n, (size_t)2 * c->arn_blocks * (m + 1)));
+    }
     int it = 0;
     double est = INFINITY;
     while (it < max_it) {
@@ -598,6 +739,29 @@ int gmres_op(pgb_ctx* c, int prec, bool transpose, const double* b, double* x, d
             if (est <= abs_tol || !(hnext > 0)) {
                 ++j;
                 ++it;
+                break;
+            }
+            if (graph && j == 0 && j + 1 < m && it + 1 < max_it) {
+                // columns 1 .. from the graph: the first column sized every
+                // buffer the body touches
+                const int jmax = (int)std::min<int64_t>(m, (int64_t)j + 1 + (max_it - it - 1));
+                gm_graph_ready(c, prec, pc, m, w, hcol, cs, sn, g, misc.p + 2, apply_pc);
+                c->h_pinned[4] = abs_tol;
+                c->h_pinned[5] = (double)jmax;
+                int* hj = reinterpret_cast<int*>(c->h_pinned + 6);
+                hj[0] = 1;
+                PGB_CUDA(cudaMemcpyAsync(c->d_gmi.p, hj, sizeof(int), cudaMemcpyHostToDevice, s));
+                PGB_CUDA(cudaMemcpyAsync(c->d_gmd.p, c->h_pinned + 4, 16, cudaMemcpyHostToDevice, s));
+                PGB_CUDA(cudaGraphLaunch(c->gm_graph.exec, s));
+                PGB_CUDA(cudaMemcpyAsync(hj, c->d_gmi.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+                PGB_CUDA(cudaMemcpyAsync(c->h_pinned + 5, c->d_gmd.p + 2, 8, cudaMemcpyDeviceToHost, s));
+                PGB_CUDA(cudaStreamSynchronize(s));
+                const int done = hj[0] - 1;  // columns the graph made
+                est = c->h_pinned[5];
+                c->launches += done * c->gm_graph.body_launches;
+                *matvecs += done;
+                it += 1 + done;
+                j += 1 + done;
                 break;
             }
             if (spec && !spec->forked && est <= spec->abs_thresh) {

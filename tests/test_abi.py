@@ -45,7 +45,7 @@ def test_argument_errors_need_no_device(libpgb):
     p = L.pgb_params()
     assert lib.pgb_default_params(ctypes.byref(p)) == 0
     assert (p.K, p.K_near, p.n_edge, p.P, p.theta, p.leaf_size) == (7, 19, 9, 6, 0.5, 32)
-    assert (p.p2p_item, p.m2p_item, p.precond, p.graphs, p.lanes, p.overlap) == (64, 64, 0, 1, 4, 0)
+    assert (p.p2p_item, p.m2p_item, p.precond, p.graphs, p.lanes, p.overlap) == (64, 64, 0, 2, 4, 0)
     assert (p.batch, p.residual) == (1, 1)
     for f, v in (("p2p_item", 5000), ("m2p_item", -1), ("precond", 2), ("graphs", 3), ("lanes", 17), ("overlap", 2),
                  ("batch", 65), ("batch", -1), ("residual", 2)):

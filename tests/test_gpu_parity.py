@@ -300,3 +300,36 @@ def test_charged_brick_at_zero_ionic_strength(mode):
             assert e[k] == pytest.approx(eo[k], rel=1e-8, abs=1e-12)
     finally:
         pgb.pgb_destroy(ctx)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp32", "refine"])
+@pytest.mark.parametrize("precond", [0, 1])
+def test_iteration_graph_matches_host_loop(mode, precond):
+    """GMRES iterations replayed from the graph with the device-side loop
+    (graphs = 2) make the same iterations and the bit-identical solution as
+    the host-driven loop (graphs = 0), over restart cycles (restart 8), a
+    rebuilt tree (graph recaptured) and a second solve (graph reused)."""
+    m = {"fp64": pgb.PGB_FP64, "fp32": pgb.PGB_FP32, "refine": pgb.PGB_FP32_REFINE}[mode]
+    tol = 1e-6 if mode == "fp32" else 1e-9
+    bodies = spheres(**CASES["sigma_pair"])
+    cg = gpu_context(bodies, theta=0.5, P=5, leaf_size=8, graphs=2, precond=precond)
+    cp = gpu_context(bodies, theta=0.5, P=5, leaf_size=8, graphs=0, precond=precond)
+    try:
+        n = pgb.pgb_num_unknowns(cg)
+        for step in range(3):
+            if step == 1:
+                for c in (cg, cp):
+                    pgb.pgb_tree_reset(c)
+                    pgb.pgb_tree_build(c)
+            out = []
+            for c in (cg, cp):
+                x = torch.empty(n, dtype=torch.float64, device="cuda")
+                code, st = pgb.pgb_solve(c, m, tol, 1000, 8, x)
+                assert code == 0
+                out.append((x.cpu().numpy(), st))
+            assert out[0][1]["iterations"] == out[1][1]["iterations"] > 8
+            assert out[0][1]["matvecs"] == out[1][1]["matvecs"]
+            assert np.array_equal(out[0][0], out[1][0])
+    finally:
+        pgb.pgb_destroy(cg)
+        pgb.pgb_destroy(cp)
