@@ -38,6 +38,7 @@ extern "C" {
 #define PGB_ENOCONV (-4)    /* GMRES did not reach tol; solution and stats still written */
 #define PGB_ETIMEOUT (-5)   /* a bounded device-side wait gave up */
 #define PGB_ESTATE (-6)     /* call out of order (e.g. matvec before pgb_tree_build) */
+#define PGB_ECOLL (-7)      /* a collective callback of a sharded solve reported failure */
 
 /* body kinds (Eq. 1): molecule interface Gamma_1, or surface Gamma_2 */
 #define PGB_DIELECTRIC 0
@@ -383,6 +384,60 @@ int pgb_math_check(const double* x, int64_t n, double* out);
  * Host arrays; no device call.  PGB_EINVAL for bad sizes, a non-positive
  * temperature or a non-finite energy. */
 int pgb_orientation_landscape(const double* F, int32_t n_orient, int32_t n_gap, double temperature, double* out);
+
+/* ---- one solve sharded over ranks (one process per GPU) ----
+ * The GMRES solve of Section 3.2 split by target rows: every rank holds the
+ * whole geometry, tree and near field and computes the upward pass itself;
+ * rank r computes the rows of a contiguous range of target groups (Morton
+ * order, balanced by their P2P and M2P work) from the full density vector,
+ * assembled by one allgather per product, and the Arnoldi dot products are
+ * summed by allreduce.  The unknowns are taken in the sharded order: sorted
+ * panel by sorted panel, each panel's rows together (phi, dphi/dn for a
+ * molecule; u for a surface), so that each rank's rows are contiguous.
+ * Nested interfaces are not sharded (PGB_EINVAL). */
+
+/* Balanced contiguous split of n_groups groups of the given (host) work over
+ * world ranks: bounds[r] .. bounds[r+1] (world + 1 entries) are rank r's
+ * groups.  Host only, no device call. */
+int pgb_shard_partition(const double* work, int64_t n_groups, int32_t world, int64_t* bounds);
+
+/* The ranks' rows in the sharded order: row_begin[r] .. row_begin[r+1]
+ * (world + 1 host entries) for the context's built tree. */
+int pgb_shard_rows(struct pgb_ctx* ctx, int32_t world, int64_t* row_begin);
+
+/* x (caller order) -> xs (sharded order), or back with inverse != 0; device
+ * doubles, n_unknowns each. */
+int pgb_to_sharded(struct pgb_ctx* ctx, const double* x, double* xs, int32_t inverse);
+
+/* Rank `rank`'s rows of y = A x: xs the whole vector in the sharded order,
+ * ys its rows (row_begin[rank+1] - row_begin[rank] device doubles; the
+ * product's precision as pgb_matvec, in and out FP64).  The rows are those of
+ * the whole product (same arithmetic). */
+int pgb_matvec_shard(struct pgb_ctx* ctx, int32_t rank, int32_t world, const double* xs, double* ys,
+                     int32_t precision);
+
+/* Collectives of a sharded solve, done by the caller (torch.distributed over
+ * NCCL or gloo, MPI, ...).  op PGB_COLL_ALLGATHER: the exchange buffer xs
+ * (n_unknowns device doubles, sharded order) holds this rank's rows;
+ * fill every other rank's rows from the other ranks (count = n_unknowns).
+ * op PGB_COLL_ALLREDUCE: replace the first count doubles of the reduce buffer
+ * by their sum over the ranks.  The library has synchronised its stream
+ * before the call; the callback returns 0 once the exchange is complete in
+ * device memory, non-zero on failure (the solve then returns PGB_ECOLL). */
+#define PGB_COLL_ALLGATHER 0
+#define PGB_COLL_ALLREDUCE 1
+typedef int (*pgb_collective_fn)(void* user, int32_t op, int64_t count);
+
+/* Sharded solve of Eq. 6 / Eq. 7: mode PGB_FP64 or PGB_FP32_REFINE (FP32
+ * inner GMRES, FP64-class outer residual), tol, max_iter and restart as
+ * pgb_solve.  xs: exchange buffer (n_unknowns device doubles), red: reduce
+ * buffer (restart + 2 device doubles), both the caller's and used by coll.
+ * Every rank must make the call with the same arguments but its rank; on
+ * return x_out (device doubles, caller order) holds the whole solution on
+ * every rank and stats (may be NULL) the iterations. */
+int pgb_solve_shard(struct pgb_ctx* ctx, int32_t rank, int32_t world, double* xs, double* red,
+                    pgb_collective_fn coll, void* user, int32_t mode, double tol, int32_t max_iter,
+                    int32_t restart, double* x_out, pgb_solve_stats* stats);
 
 /* Diagnostic: the host-computed table that turns a node's Taylor moments
  * (Section 3.2) into the coefficients its far field is evaluated from, for

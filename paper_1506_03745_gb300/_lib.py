@@ -12,6 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libpgb.so")
 
 PGB_OK, PGB_EINVAL, PGB_ENOMEM, PGB_ECUDA, PGB_ENOCONV, PGB_ETIMEOUT, PGB_ESTATE = 0, -1, -2, -3, -4, -5, -6
+PGB_ECOLL = -7
 PGB_DIELECTRIC, PGB_SET_CHARGE, PGB_SET_POTENTIAL = 0, 1, 2
 PGB_FP32, PGB_FP64, PGB_FP32_REFINE, PGB_FP64_DS = 0, 1, 2, 3
 
@@ -92,6 +93,12 @@ _SIGS = {
     "pgb_alloc_count": (c_i32, [ctypes.POINTER(c_i64)]),
     "pgb_far_table": (c_i32, [c_i32, c_dbl, c_vp, c_i64]),
     "pgb_orientation_landscape": (c_i32, [c_vp, c_i32, c_i32, c_dbl, c_vp]),
+    "pgb_shard_partition": (c_i32, [c_vp, c_i64, c_i32, c_vp]),
+    "pgb_shard_rows": (c_i32, [c_vp, c_i32, c_vp]),
+    "pgb_to_sharded": (c_i32, [c_vp, c_vp, c_vp, c_i32]),
+    "pgb_matvec_shard": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_vp, c_i32]),
+    "pgb_solve_shard": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_i32, c_dbl, c_i32, c_i32, c_vp,
+                                ctypes.POINTER(pgb_solve_stats)]),
 }
 
 
@@ -385,3 +392,42 @@ def pgb_orientation_landscape(F, n_orient, n_gap, temperature=300.0):
                                                  out.ctypes.data_as(c_vp)))
     return [{"gap_index": g, "most_likely_orientation": int(out[3 * g]), "p_max": float(out[3 * g + 1]),
              "free_energy_kcal_mol": float(out[3 * g + 2])} for g in range(n_gap)]
+
+
+PGB_COLL_ALLGATHER = 0
+PGB_COLL_ALLREDUCE = 1
+
+
+def pgb_shard_partition(work, world):
+    """Group bounds (world + 1) of a balanced contiguous split of the work."""
+    w, wp = _hptr(np.asarray(work, dtype=np.float64).reshape(-1), np.float64)
+    b = np.zeros(world + 1, np.int64)
+    _check(None, lib().pgb_shard_partition(wp, w.shape[0], world, b.ctypes.data_as(c_vp)))
+    return b
+
+
+def pgb_shard_rows(ctx, world):
+    rb = np.zeros(world + 1, np.int64)
+    _check(ctx, lib().pgb_shard_rows(ctx, world, rb.ctypes.data_as(c_vp)))
+    return rb
+
+
+def pgb_to_sharded(ctx, x, xs, inverse=False):
+    n = pgb_num_unknowns(ctx)
+    return _check(ctx, lib().pgb_to_sharded(ctx, _dptr(x, "float64", n), _dptr(xs, "float64", n), int(inverse)))
+
+
+def pgb_matvec_shard(ctx, rank, world, xs, ys, precision):
+    return _check(ctx, lib().pgb_matvec_shard(ctx, rank, world, _dptr(xs, "float64", pgb_num_unknowns(ctx)),
+                                              _dptr(ys, "float64"), precision))
+
+
+def pgb_solve_shard(ctx, rank, world, xs, red, callback, mode, tol, max_iter, restart, x_out):
+    """callback: a ctypes CFUNCTYPE(int, void*, int32, int64) object doing the
+    collectives.  Returns (status, stats dict)."""
+    n = pgb_num_unknowns(ctx)
+    st = pgb_solve_stats()
+    code = _check(ctx, lib().pgb_solve_shard(ctx, rank, world, _dptr(xs, "float64", n), _dptr(red, "float64"),
+                                             ctypes.cast(callback, c_vp), None, mode, tol, max_iter, restart,
+                                             _dptr(x_out, "float64", n), ctypes.byref(st)), allow=(PGB_ENOCONV,))
+    return code, {k: getattr(st, k) for k, _ in pgb_solve_stats._fields_}

@@ -90,6 +90,7 @@ struct Parts {
     const int32_t *pan_group, *gstart;
     const int64_t *pitem_off, *fitem_off;
     const double *Up, *Uf;
+    int64_t g_lo, g_hi;  // rows of the groups g_lo <= g < g_hi only (a rank's rows of a sharded product)
 };
 
 // real: the arithmetic of the near-field corrections (FP32 product: FP32
@@ -105,6 +106,7 @@ __global__ void k_assemble(Geo g, BodyDev bd, Parts u, const real* __restrict__ 
     if (i >= g.n_pan) return;
     const double inv4pi = 1.0 / PGB_FOUR_PI;
     const int gi = u.pan_group[i];
+    if (gi < u.g_lo || gi >= u.g_hi) return;
     const int lane = (int)(i - u.gstart[gi]);
     double sL = 0, sY = 0;
     for (int64_t it = u.pitem_off[gi]; it < u.pitem_off[gi + 1]; ++it) {
@@ -260,6 +262,7 @@ __global__ void k_assemble_region(Geo g, BodyDev bd, RegionDev rd, Parts u, cons
     const int sg = rd.sign[b];
     if (sg == 0) return;
     const int gi = u.pan_group[i];
+    if (gi < u.g_lo || gi >= u.g_hi) return;
     const int lane = (int)(i - u.gstart[gi]);
     double sY = 0;
     for (int64_t it = u.pitem_off[gi]; it < u.pitem_off[gi + 1]; ++it) sY += u.Up[64 * it + 32 + lane];
@@ -470,6 +473,8 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
     ev.tgt_mask = ~0ull;
     for (size_t b = 0; b < c->bodies.size(); ++b)
         if (c->body_off[b]) ev.tgt_mask &= ~(1ull << b);
+    ev.g_lo = c->shard_g[0] >= 0 ? c->shard_g[0] : 0;
+    ev.g_hi = c->shard_g[0] >= 0 ? c->shard_g[1] : c->n_groups;
     ev.near4 = c->d_near4;
     ev.far4 = c->d_far4;
     ev.tile_off = c->d_tile_off;
@@ -566,7 +571,7 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
             }
             {
                 StageTimer tm(c, PGB_STAGE_ASSEMBLE + (f32 ? 0 : PGB_STAGE_FP64));
-                Parts u{c->d_pan_group, c->d_group_start, c->d_pitem_off, c->d_fitem_off, Up, Uf};
+                Parts u{c->d_pan_group, c->d_group_start, c->d_pitem_off, c->d_fitem_off, Up, Uf, ev.g_lo, ev.g_hi};
                 if (f32)
                     k_assemble_region<float><<<nblk(c->n_pan, 128), 128, 0, s>>>(
                         g, bd, rd, u, (const float*)dens.p, reg->corr_off, reg->corr_j, reg->corr_val32,
@@ -630,7 +635,7 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
     }
     {
         StageTimer tm(c, PGB_STAGE_ASSEMBLE + (f32 ? 0 : PGB_STAGE_FP64));
-        Parts u{c->d_pan_group, c->d_group_start, c->d_pitem_off, c->d_fitem_off, Up, Uf};
+        Parts u{c->d_pan_group, c->d_group_start, c->d_pitem_off, c->d_fitem_off, Up, Uf, ev.g_lo, ev.g_hi};
         if (f32)
             k_assemble<float><<<nblk(c->n_pan, 128), 128, 0, s>>>(
                 g, bd, u, (const float*)dens.p, c->d_corr_off, c->d_corr_j, c->d_corr_val32, c->d_xcorr_off,

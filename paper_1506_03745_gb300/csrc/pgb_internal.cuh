@@ -337,6 +337,11 @@ struct pgb_ctx {
     } gm_graph;
     cudaStream_t gm_stream = nullptr;    // stream of its capture
     bool capturing = false;              // products enqueue plain launches (no nested graph launch)
+    // sharded products: the target groups [shard_g[0], shard_g[1]) of this
+    // rank (shard_g[0] < 0: every group)
+    int64_t shard_g[2] = {-1, -1};
+    pgb::DBuf<double> d_shard_tmp, d_shard_part, d_shard_V, d_shard_w, d_shard_h;  // sharded solve (shard.cu)
+    pgb::DBuf<double> d_shard_b, d_shard_bc, d_shard_x, d_shard_r, d_shard_d;
     pgb::DBuf<int> d_gmi;                // device column index of the replayed iterations
     pgb::DBuf<double> d_gmd;             // tolerance, column limit, last estimate
     pgb::DBuf<double> d_xsel;            // the column the replayed product reads
@@ -427,6 +432,9 @@ void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t
 void apply_operator(pgb_ctx* c, const double* x, double* y, int precision, bool known_only,
                     const int* known_mask = nullptr);
 void apply_transpose(pgb_ctx* c, const double* lam, double* y, int precision);
+// mode 0: A x; 1: the imposed-boundary terms only; 2: A (x + imposed); known_mask
+// selects the surfaces of mode 1 (nullptr: all)
+void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode, const int* known_mask);
 void apply_full(pgb_ctx* c, const double* x, double* y, int precision);
 void coulomb_rows(pgb_ctx* c, double* b);
 void grad(pgb_ctx* c, const double* x, int precision, double tol, int max_iter, int restart, double* dq, double* dbc,

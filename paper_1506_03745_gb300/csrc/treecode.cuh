@@ -217,6 +217,7 @@ struct EvalArgs {
     int src_active[PGB_MAX_BODIES];  // 0: the body's densities are all zero (skip)
     int all_active;                // every body active (the plain product): no per-node test
     unsigned long long tgt_mask;   // bit b: the rows of body b are used (other groups' items are skipped)
+    int64_t g_lo, g_hi;            // only the groups g_lo <= g < g_hi (a rank's rows of a sharded product)
     const float4* near4;           // per near entry: leaf centre - group centre, node id bits
     const float4* far4;            // per far entry: node centre - group centre, node id bits
     const int64_t* tile_off;       // per group: its P2P tiles [tile_off[g], tile_off[g+1])
@@ -434,7 +435,7 @@ __global__ void __launch_bounds__(NW * 32) k_p2p(EvalArgs a, const typename V4<r
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int64_t it = next_item(a.p2p_work, -1, &s_item); it < a.n_pitems; it = next_item(a.p2p_work, it, &s_item)) {
     const int64_t g = a.pitem_group[it];
-    if (!((a.tgt_mask >> a.gbody[g]) & 1ull)) continue;  // rows not used by this product (block-uniform)
+    if (!((a.tgt_mask >> a.gbody[g]) & 1ull) || g < a.g_lo || g >= a.g_hi) continue;  // rows not used (block-uniform)
     const int64_t p0 = a.gstart[g], p1 = a.gend[g];
     const int64_t p = p0 + lane;
     const bool active = p < p1;
@@ -528,7 +529,7 @@ __global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a,
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int64_t it = next_item(a.m2p_work, -1, &s_item); it < a.n_fitems; it = next_item(a.m2p_work, it, &s_item)) {
     const int64_t g = a.fitem_group[it];
-    if (!((a.tgt_mask >> a.gbody[g]) & 1ull)) continue;  // rows not used by this product (block-uniform)
+    if (!((a.tgt_mask >> a.gbody[g]) & 1ull) || g < a.g_lo || g >= a.g_hi) continue;  // rows not used (block-uniform)
     const int64_t p0 = a.gstart[g], p1 = a.gend[g];
     const int64_t p = p0 + lane;
     const bool active = p < p1;
