@@ -551,8 +551,9 @@ def run_gpu(args):
                   "block_diagonal_precond": pc,
                   "overlapped_fp64_residual": ov,
                   "native_fp64_residual": native},
-        "stage_ms_per_step": {k: v[0] / args.steps for k, v in timing.items() if k != "kernel_launches"},
+        "stage_ms_per_step": {k: v[0] / args.steps for k, v in timing.items() if k not in ("kernel_launches", "host_launches")},
         "gpu_launches": timing["kernel_launches"],
+        "host_launch_calls": timing["host_launches"],
         "roofline": {"kernel": dom["kernel"], "bound": "alu", "achieved": dom["achieved"],
                      "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": (dom["achieved"] / peak_tflops) if dom["achieved"] else None,
@@ -792,8 +793,9 @@ def run_poses(args):
                       "batch": PARAMS["batch"], "ms": ms, "poses_per_s": B / (ms / 1e3),
                       "mean_iterations": float(np.mean([s["iterations"] for s in st])),
                       "energy_rel_err_vs_fp64_first_2_poses": err, "status": code,
-                      "stage_ms_per_pose": {k: v[0] / B for k, v in tim.items() if k != "kernel_launches" and v[0]},
+                      "stage_ms_per_pose": {k: v[0] / B for k, v in tim.items() if k not in ("kernel_launches", "host_launches") and v[0]},
                       "kernel_launches_per_pose": tim["kernel_launches"] / B,
+                      "host_launch_calls_per_pose": tim["host_launches"] / B,
                       "F_total_range_kcal_mol": [float(F[:, 3].min()), float(F[:, 3].max())],
                       "orientation_landscape": orientation_landscape(F[:, 3], args.poses, 4)}), flush=True)
     pgb.pgb_destroy(ctx)
@@ -809,8 +811,9 @@ def run_poses_uneven(args):
     with chunks of `batch` poses (default 8, one pose of every molecule per
     chunk: one launch per stage over eight molecules of different sizes);
     beside it the same poses molecule by molecule through pgb_solve_batch
-    with 4 lanes.  The energy error against FP64 is taken on the first
-    chunk."""
+    with 4 lanes.  The batched FP64 solve (tol 1e-9) is timed beside the
+    batched FP32 + refinement solve on the leading 8 chunks: speedup and
+    per-pose energy error."""
     import torch
     import synth
     import paper_1506_03745_gb300 as pgb
@@ -884,10 +887,18 @@ def run_poses_uneven(args):
         pgb.pgb_destroy(c0)
         lanes = {"ms": ms_l, "poses_per_s": B / (ms_l / 1e3),
                  "max_rel_diff_total_energy": float(np.max(np.abs(F_l[:, 3] - F[:, 3]) / np.abs(F[:, 3])))}
-    # FP64 reference for the first chunk
-    code64, F64, _ = pgb.pgb_solve_poses(ctxs, pc[:batch], 0, R[:batch], t[:batch], pgb.PGB_FP64, 1e-9, MAX_ITER,
-                                         RESTART)
-    err = np.abs(F[:batch, 3] - F64[:, 3]) / np.abs(F64[:, 3])
+    # the batched FP64 solve (tol 1e-9) beside the batched FP32 + refinement
+    # solve on the same leading poses (up to 8 chunks): time and per-pose
+    # energy error
+    n64 = min(B, 8 * batch)
+    (_, F32s, _), ms32 = _timed(lambda: pgb.pgb_solve_poses(ctxs, pc[:n64], 0, R[:n64], t[:n64], mode, tol,
+                                                            MAX_ITER, RESTART))
+    (code64, F64, st64), ms64 = _timed(lambda: pgb.pgb_solve_poses(ctxs, pc[:n64], 0, R[:n64], t[:n64],
+                                                                   pgb.PGB_FP64, 1e-9, MAX_ITER, RESTART))
+    err = np.abs(F[:n64, 3] - F64[:, 3]) / np.abs(F64[:, 3])
+    vs64 = {"poses": n64, "fp32_refine_ms": ms32, "fp64_ms": ms64, "speedup": ms64 / ms32, "fp64_status": code64,
+            "fp64_mean_iterations": float(np.mean([s_["iterations"] for s_ in st64])),
+            "energy_rel_err_max": float(err.max()), "energy_rel_err_median": float(np.median(err))}
     its = np.array([s["iterations"] for s in st])
     print(json.dumps({"workload": f"8 molecules ({min(npan)}-{max(npan)} panels, 900 charges each) x {args.poses} "
                                   f"orientations x 4 gaps near a sphere r=40 A (30420 panels)",
@@ -896,9 +907,10 @@ def run_poses_uneven(args):
                       "max_rel_residual": float(max(s_["rel_residual"] for s_ in st)),
                       "molecule_panels": npan, "mean_iterations": float(its.mean()), "autotune": tune,
                       "iterations_range": [int(its.min()), int(its.max())], "status": code,
-                      "energy_rel_err_vs_fp64_first_chunk_max": float(err.max()),
-                      "stage_ms_per_pose": {k: v[0] / B for k, v in tim.items() if k != "kernel_launches" and v[0]},
+                      "batched_vs_fp64": vs64,
+                      "stage_ms_per_pose": {k: v[0] / B for k, v in tim.items() if k not in ("kernel_launches", "host_launches") and v[0]},
                       "kernel_launches_per_pose": tim["kernel_launches"] / B,
+                      "host_launch_calls_per_pose": tim["host_launches"] / B,
                       # per molecule, per gap: Boltzmann weights over the orientations (poses are
                       # ordered orientation, gap, molecule)
                       "orientation_landscape": {f"molecule_{k}": orientation_landscape(F[k::8, 3], args.poses, 4)
@@ -1058,7 +1070,7 @@ def run_matvec(args):
     ms = e0.elapsed_time(e1) / args.steps
     print(json.dumps({"mode": "matvec", "precision": args.precision, "ms_per_matvec": ms,
                       "matvecs_per_s": 1e3 / ms,
-                      "stage_ms_per_matvec": {k: v[0] / args.steps for k, v in t.items() if k != "kernel_launches"},
+                      "stage_ms_per_matvec": {k: v[0] / args.steps for k, v in t.items() if k not in ("kernel_launches", "host_launches")},
                       "tree": pgb.pgb_tree_stats(ctx)}), flush=True)
     pgb.pgb_destroy(ctx)
 

@@ -145,7 +145,10 @@ typedef struct pgb_tree_info {
 typedef struct pgb_stage_times {
     double ms[PGB_N_STAGES];        /* summed device milliseconds */
     int64_t calls[PGB_N_STAGES];    /* timed intervals */
-    int64_t kernel_launches;        /* kernels the library launched (all stages) */
+    int64_t kernel_launches;        /* kernels the library ran (all stages; a replayed
+                                       graph counts the kernels it ran) */
+    int64_t host_launches;          /* launch calls the host made: kernels launched
+                                       directly plus graph launches */
 } pgb_stage_times;
 
 /* Create a context on the current CUDA device.  p may be NULL (defaults:

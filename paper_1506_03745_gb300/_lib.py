@@ -47,7 +47,8 @@ STAGES = ("sources", "upward", "p2p", "m2p", "assemble", "krylov", "tree", "ener
 
 
 class pgb_stage_times(ctypes.Structure):
-    _fields_ = [("ms", c_dbl * N_STAGES), ("calls", c_i64 * N_STAGES), ("kernel_launches", c_i64)]
+    _fields_ = [("ms", c_dbl * N_STAGES), ("calls", c_i64 * N_STAGES), ("kernel_launches", c_i64),
+                ("host_launches", c_i64)]
 
 
 class PgbError(RuntimeError):
@@ -333,13 +334,15 @@ def pgb_energy_noalloc(ctx, x):
 
 def pgb_timing(ctx, enable, read=True):
     """Enable/disable stage timing; when read, return and reset the
-    accumulated {stage: (ms, calls)} and the kernel launch count."""
+    accumulated {stage: (ms, calls)}, the kernels run and the host's launch
+    calls (direct kernel launches plus graph launches)."""
     t = pgb_stage_times()
     _check(ctx, lib().pgb_timing(ctx, 1 if enable else 0, ctypes.byref(t) if read else None))
     if not read:
         return None
     d = {STAGES[i]: (t.ms[i], t.calls[i]) for i in range(N_STAGES)}
     d["kernel_launches"] = t.kernel_launches
+    d["host_launches"] = t.host_launches
     return d
 
 

@@ -316,7 +316,9 @@ static int solve_lanes(pgb_ctx* c, int L, int32_t body_id, const double* R, cons
             }
         }
         c->launches += lc->launches;
-        lc->launches = 0;
+        c->graph_kernels += lc->graph_kernels;
+        c->graph_launches += lc->graph_launches;
+        lc->launches = lc->graph_kernels = lc->graph_launches = 0;
     }
     for (int l = 0; l < L; ++l)
         if (rc[l] != PGB_OK && rc[l] != PGB_ENOCONV) {
@@ -407,6 +409,7 @@ int pgb_destroy(pgb_ctx* c) {
     for (auto& gr : c->up_graph)
         if (gr.exec) cudaGraphExecDestroy(gr.exec);
     if (c->gm_graph.exec) cudaGraphExecDestroy(c->gm_graph.exec);
+    if (c->seg_exec) cudaGraphExecDestroy(c->seg_exec);
     if (c->gm_stream) {
         cudaStreamSynchronize(c->gm_stream);
         cudaStreamDestroy(c->gm_stream);
@@ -954,7 +957,8 @@ int pgb_timing(pgb_ctx* c, int32_t enable, pgb_stage_times* out) {
                 c->stage_calls[i] = 0;
             }
             out->kernel_launches = c->launches;
-            c->launches = 0;
+            out->host_launches = c->launches - c->graph_kernels + c->graph_launches;
+            c->launches = c->graph_kernels = c->graph_launches = 0;
         }
         c->timing = enable != 0;
         return PGB_OK;

@@ -98,6 +98,54 @@ __global__ void k_seg_axpby(double a, const double* x, double b, const double* y
     if (r < n) out[r] = a * x[r] + b * y[r];
 }
 
+// ---------------------------------------------------------------- replayed lockstep iterations
+// The column the next replayed product reads: dst = V_j, j from the device.
+__global__ void k_seg_select(const double* __restrict__ V, int64_t n, const int* __restrict__ jdev,
+                             double* __restrict__ dst) {
+    const int64_t j = *jdev;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        dst[r] = V[j * n + r];
+}
+
+// After the segmented Arnoldi step of column j, one thread per problem (at
+// most 64): an active problem counts the column, keeps its estimate and
+// leaves when it meets its tolerance or breaks down; the body mask of the
+// next product keeps the problems still active; j advances and the loop goes
+// on while a problem is active and columns remain (j + 1 < *jmax).
+// ctl: {j, jmax}.
+__global__ void __launch_bounds__(64) k_seg_check(const double* __restrict__ out, int B, int* act, int* kcol, int* itc,
+                                                  double* estd, const double* __restrict__ told,
+                                                  const unsigned long long* __restrict__ pmask,
+                                                  unsigned long long* bmask, int* ctl, cudaGraphConditionalHandle h) {
+    __shared__ unsigned long long keep;
+    __shared__ int any;
+    if (threadIdx.x == 0) {
+        keep = 0;
+        any = 0;
+    }
+    __syncthreads();
+    const int j = ctl[0];
+    const int p = threadIdx.x;
+    if (p < B && act[p]) {
+        kcol[p] = j + 1;
+        ++itc[p];
+        const double est = out[2 * p], hnext = out[2 * p + 1];
+        estd[p] = est;
+        if (est <= told[p] || !(hnext > 0)) {
+            act[p] = 0;
+        } else {
+            atomicOr(&keep, pmask[p]);
+            any = 1;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctl[0] = j + 1;
+        *bmask = keep;
+        cudaGraphSetConditional(h, (any && j + 1 < ctl[1]) ? 1u : 0u);
+    }
+}
+
 // Leave the problems with on[p] == 0 out of the following products (their
 // rows come out without the treecode sums and are not used).
 static void set_products(pgb_ctx* c, const std::vector<int>& on) {
@@ -125,6 +173,76 @@ static std::vector<double> seg_norms(pgb_ctx* c, const double* v) {
     return h;
 }
 
+// Graph of the lockstep iterations after the first column of a cycle: a
+// device-side while loop whose body takes column j (k_seg_select), applies
+// the (preconditioned) operator to the problems the run-time body mask keeps,
+// makes the segmented Arnoldi step of column j and updates every problem's
+// state (k_seg_check).  Captured on the context's capture stream from the
+// launches the host loop makes; the caller sizes every buffer first.
+template <class ApplyPc>
+static void seg_graph_capture(pgb_ctx* c, const ArnSeg& sg, int m, double* hc, double* cs, double* sn, double* g,
+                              double* out, int* act, int* kcol, int* itc, double* estd, const double* told, int* ctl,
+                              ApplyPc apply_pc) {
+    const int64_t n = c->n_unk;
+    const int B = c->n_prob;
+    if (c->seg_exec) {
+        PGB_CUDA(cudaGraphExecDestroy(c->seg_exec));
+        c->seg_exec = nullptr;
+    }
+    if (!c->gm_stream) PGB_CUDA(cudaStreamCreateWithFlags(&c->gm_stream, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    PGB_CUDA(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle h;
+    PGB_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    PGB_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t saved = c->stream;
+    const bool saved_timing = c->timing;
+    const int64_t l0 = c->launches;
+    c->stream = c->gm_stream;
+    c->timing = false;
+    c->capturing = true;
+    c->dev_bmask = c->d_segm.p;
+    all_products(c);
+    std::string why;
+    PGB_CUDA(cudaStreamBeginCaptureToGraph(c->gm_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    try {
+        k_seg_select<<<nblk(n, 256), 256, 0, c->gm_stream>>>(c->d_V, n, ctl, c->d_xsel);
+        apply_pc(c->d_xsel.p, c->d_wk.p);
+        arnoldi_step(c, 0, c->d_wk, c->d_H, hc, cs, sn, g, out, &sg, ctl, m);
+        k_seg_check<<<1, 64, 0, c->gm_stream>>>(out, B, act, kcol, itc, estd, told, c->d_segm.p + 1, c->d_segm.p,
+                                                 ctl, h);
+        PGB_LAUNCHED(c, 6);
+    } catch (const Error& e) {
+        why = e.msg;
+    }
+    const cudaError_t le = cudaGetLastError();
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(c->gm_stream, &captured);
+    c->stream = saved;
+    c->timing = saved_timing;
+    c->capturing = false;
+    c->dev_bmask = nullptr;
+    c->seg_body_launches = c->launches - l0;
+    c->launches = l0;
+    if (!why.empty() || le != cudaSuccess || ce != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        (void)cudaGetLastError();
+        fail(PGB_ECUDA, "lockstep iteration graph capture: " +
+                            (why.empty() ? std::string(cudaGetErrorString(le != cudaSuccess ? le : ce)) : why));
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&c->seg_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) c->seg_exec = nullptr;
+    PGB_CUDA(ie);
+}
+
 // Lockstep restarted GMRES on the c->n_prob problems of a block-diagonal
 // system: each iteration is one product of the whole system and one
 // segmented Arnoldi step; problem p stops on its own test (estimated
@@ -146,8 +264,8 @@ static int gmres_seg(pgb_ctx* c, int prec, const double* b, double* x, const dou
     c->d_V.resize((size_t)(m + 1) * n);
     c->d_H.resize((size_t)B * sH);
     c->d_wk.resize(n);
-    c->d_seg.resize((size_t)5 * B * sV + 3 * B);
-    c->d_segi.resize(2 * (size_t)B);
+    c->d_seg.resize((size_t)5 * B * sV + 5 * B);
+    c->d_segi.resize(3 * (size_t)B + 2);
     if (pc) c->d_pz.resize(n);
     double* cs = c->d_seg.p;
     double* sn = cs + B * sV;
@@ -156,8 +274,12 @@ static int gmres_seg(pgb_ctx* c, int prec, const double* b, double* x, const dou
     double* yv = hc + B * sV;
     double* out = yv + B * sV;  // 2 per problem
     double* nrm = out + 2 * B;  // 1 per problem
+    double* estd = nrm + B;     // replayed iterations: each problem's last estimate
+    double* told = estd + B;    // and its tolerance
     int* act = c->d_segi.p;
     int* kcol = act + B;
+    int* itc = kcol + B;        // replayed iterations: columns each problem made
+    int* ctl = itc + B;         // {column j, column limit}
     const ArnSeg sg{B, nbp, c->d_poff, act, sH, sV};
     std::vector<char> done(B, 0);
     std::vector<int> act_h(B, 0), kcol_h(B, 0);
@@ -165,6 +287,26 @@ static int gmres_seg(pgb_ctx* c, int prec, const double* b, double* x, const dou
     for (int p = 0; p < B; ++p) {
         iters[p] = 0;
         est[p] = INFINITY;
+    }
+    // the iterations after a cycle's first column replayed from a graph
+    // (captured afresh in each call, on its first use)
+    const bool graph = c->p.graphs >= 2 && m >= 2 && B <= 64;
+    std::vector<unsigned long long> pm(B + 1, 0);
+    std::vector<int> ib(3 * B + 2);
+    if (c->seg_exec) {
+        PGB_CUDA(cudaGraphExecDestroy(c->seg_exec));
+        c->seg_exec = nullptr;
+    }
+    if (graph) {
+        // everything the replayed body touches is sized here, outside the capture
+        c->d_segm.resize(B + 1);
+        c->d_xsel.resize(n);
+        reserve_product(c, prec);
+        c->d_red.resize(std::max<size_t>(c->d_red.n, (size_t)2 * nbp * (m + 1) * B));
+        for (int p = 0; p < B; ++p)
+            for (int k = c->prob_first[p]; k < c->prob_first[p + 1]; ++k) pm[1 + p] |= 1ull << k;
+        PGB_CUDA(cudaMemcpyAsync(c->d_segm.p + 1, pm.data() + 1, 8 * B, cudaMemcpyHostToDevice, s));
+        PGB_CUDA(cudaMemcpyAsync(told, abs_tol, 8 * B, cudaMemcpyHostToDevice, s));
     }
     int it = 0;
     while (it < max_it) {
@@ -226,6 +368,49 @@ static int gmres_seg(pgb_ctx* c, int prec, const double* b, double* x, const dou
             }
             if (!left) break;
             if (changed) PGB_CUDA(cudaMemcpyAsync(act, act_h.data(), 4 * B, cudaMemcpyHostToDevice, s));
+            if (graph && j == 0 && j + 1 < m && it < max_it) {
+                // columns 1 .. from the graph: the first column sized every
+                // buffer the body touches
+                if (!c->seg_exec)
+                    seg_graph_capture(c, sg, m, hc, cs, sn, g, out, act, kcol, itc, estd, told, ctl, apply_pc);
+                const int jmax = (int)std::min<int64_t>(m, (int64_t)j + 1 + (max_it - it));
+                unsigned long long keep = 0;
+                for (int p = 0; p < B; ++p) {
+                    ib[p] = act_h[p];
+                    ib[B + p] = kcol_h[p];
+                    ib[2 * B + p] = 0;
+                    if (act_h[p]) keep |= pm[1 + p];
+                }
+                ib[3 * B] = 1;
+                ib[3 * B + 1] = jmax;
+                pm[0] = keep;
+                PGB_CUDA(cudaMemcpyAsync(act, ib.data(), 4 * (3 * B + 2), cudaMemcpyHostToDevice, s));
+                PGB_CUDA(cudaMemcpyAsync(c->d_segm.p, pm.data(), 8, cudaMemcpyHostToDevice, s));
+                PGB_CUDA(cudaGraphLaunch(c->seg_exec, s));
+                std::vector<double> eh(B);
+                PGB_CUDA(cudaMemcpyAsync(ib.data(), act, 4 * (3 * B + 2), cudaMemcpyDeviceToHost, s));
+                PGB_CUDA(cudaMemcpyAsync(eh.data(), estd, 8 * B, cudaMemcpyDeviceToHost, s));
+                PGB_CUDA(cudaStreamSynchronize(s));
+                const int cols = ib[3 * B] - 1;  // columns the graph made
+                for (int p = 0; p < B; ++p) {
+                    if (!act_h[p]) continue;
+                    iters[p] += ib[2 * B + p];
+                    if (ib[2 * B + p] > 0) {
+                        est[p] = eh[p];
+                        kcol_h[p] = ib[B + p];
+                    }
+                    if (!ib[p]) {
+                        act_h[p] = 0;
+                        if (est[p] <= abs_tol[p]) done[p] = 1;
+                    }
+                }
+                it += cols;
+                *matvecs += cols;
+                c->launches += cols * c->seg_body_launches;
+                c->graph_kernels += cols * c->seg_body_launches;
+                ++c->graph_launches;
+                break;
+            }
         }
         // x += M^{-1} V y, problem by problem with its own column count
         PGB_CUDA(cudaMemcpyAsync(kcol, kcol_h.data(), 4 * B, cudaMemcpyHostToDevice, s));
@@ -496,7 +681,9 @@ int solve_union(pgb_ctx* c, const std::vector<pgb_ctx*>& src, int32_t body_id, c
         }
     }
     c->launches += u->launches;
-    u->launches = 0;
+    c->graph_kernels += u->graph_kernels;
+    c->graph_launches += u->graph_launches;
+    u->launches = u->graph_kernels = u->graph_launches = 0;
     return rs;
 }
 

@@ -468,6 +468,9 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
     }
     ev.all_active = 1;
     for (size_t b = 0; b < c->bodies.size(); ++b) ev.all_active &= ev.src_active[b];
+    // a replayed lockstep iteration: which problems take part is known on the device only
+    ev.bmask = up.bmask = c->dev_bmask;
+    if (c->dev_bmask) ev.all_active = 0;
     // rows of bodies left out of the product (a lockstep batch's finished
     // problems) are not computed
     ev.tgt_mask = ~0ull;
@@ -607,8 +610,11 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
         StageTimer tm(c, PGB_STAGE_UPWARD + (f32 ? 0 : PGB_STAGE_FP64), us);
         const void* usrc = f32 ? (const void*)c->d_src32.p : dsp ? (const void*)c->d_src_ds.p : (const void*)c->d_src64.p;
         void* umom = f32 ? (void*)c->d_mom32.p : dsp ? (void*)c->d_mom_ds.p : (void*)c->d_mom64.p;
-        if (c->p.graphs && !c->capturing)
+        if (c->p.graphs && !c->capturing) {
             upward_graph(c, f32 ? 0 : dsp ? 2 : 1, up, ev, usrc, umom, us);
+            c->graph_kernels += 2;
+            ++c->graph_launches;
+        }
         else if (f32)
             treecode_launch_f32(PGB_STAGE_UPWARD, P, up, c->level_begin, ev, c->d_src32, c->d_x32, c->d_mom32,
                                 c->d_far32, us);

@@ -337,6 +337,11 @@ struct pgb_ctx {
     } gm_graph;
     cudaStream_t gm_stream = nullptr;    // stream of its capture
     bool capturing = false;              // products enqueue plain launches (no nested graph launch)
+    // a lockstep batch's replayed iterations (batch.cu), captured per solve call
+    cudaGraphExec_t seg_exec = nullptr;
+    int64_t seg_body_launches = 0;
+    // device body mask the products of a capture read (nullptr: none)
+    const unsigned long long* dev_bmask = nullptr;
     // sharded products: the target groups [shard_g[0], shard_g[1]) of this
     // rank (shard_g[0] < 0: every group)
     int64_t shard_g[2] = {-1, -1};
@@ -364,6 +369,7 @@ struct pgb_ctx {
     int seg_nbp = 0;                     // blocks per problem of the segmented kernels
     pgb::DBuf<double> d_seg, d_seg_red;  // per-problem Krylov vectors; segmented partial sums
     pgb::DBuf<int> d_segi;               // per-problem activity and column counts
+    pgb::DBuf<unsigned long long> d_segm;  // run-time body mask, then each problem's bodies
     // bodies left out of the products (1: its sources and rows are not
     // computed; the problems that no longer iterate in a lockstep solve)
     char body_off[PGB_MAX_BODIES] = {0};
@@ -389,6 +395,8 @@ struct pgb_ctx {
     double stage_ms[PGB_N_STAGES] = {0};
     int64_t stage_calls[PGB_N_STAGES] = {0};
     int64_t launches = 0;
+    // of those, kernels run inside replayed graphs, and the graph launches
+    int64_t graph_kernels = 0, graph_launches = 0;
     pgb_tree_info info{};
     int64_t p2p_pairs = 0, p2p_lap = 0, m2p_pairs = 0, m2p_lap = 0;
 };

@@ -759,6 +759,8 @@ int gmres_op(pgb_ctx* c, int prec, bool transpose, const double* b, double* x, d
                 const int done = hj[0] - 1;  // columns the graph made
                 est = c->h_pinned[5];
                 c->launches += done * c->gm_graph.body_launches;
+                c->graph_kernels += done * c->gm_graph.body_launches;
+                ++c->graph_launches;
                 *matvecs += done;
                 it += 1 + done;
                 j += 1 + done;

@@ -203,6 +203,9 @@ __device__ __forceinline__ void decode_mi(int t, int& x, int& y, int& z) {
     z = n - x - y;
 }
 
+// the run-time body mask of a product (all bodies without one)
+__device__ __forceinline__ unsigned long long body_mask(const unsigned long long* m) { return m ? *m : ~0ull; }
+
 struct EvalArgs {
     int64_t n_groups;
     const int32_t *gstart, *gend, *gbody;
@@ -218,6 +221,10 @@ struct EvalArgs {
     int all_active;                // every body active (the plain product): no per-node test
     unsigned long long tgt_mask;   // bit b: the rows of body b are used (other groups' items are skipped)
     int64_t g_lo, g_hi;            // only the groups g_lo <= g < g_hi (a rank's rows of a sharded product)
+    // device copy of a further body mask, read at run time (a replayed
+    // lockstep iteration: bit b clear = body b's rows and sources left out);
+    // nullptr: none.  With it all_active is 0.
+    const unsigned long long* bmask = nullptr;
     const float4* near4;           // per near entry: leaf centre - group centre, node id bits
     const float4* far4;            // per far entry: node centre - group centre, node id bits
     const int64_t* tile_off;       // per group: its P2P tiles [tile_off[g], tile_off[g+1])
@@ -433,9 +440,10 @@ __global__ void __launch_bounds__(NW * 32) k_p2p(EvalArgs a, const typename V4<r
     __shared__ real red[NW][4][32];
     __shared__ int64_t s_item;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned long long dm = body_mask(a.bmask);
     for (int64_t it = next_item(a.p2p_work, -1, &s_item); it < a.n_pitems; it = next_item(a.p2p_work, it, &s_item)) {
     const int64_t g = a.pitem_group[it];
-    if (!((a.tgt_mask >> a.gbody[g]) & 1ull) || g < a.g_lo || g >= a.g_hi) continue;  // rows not used (block-uniform)
+    if (!(((a.tgt_mask & dm) >> a.gbody[g]) & 1ull) || g < a.g_lo || g >= a.g_hi) continue;  // rows not used (block-uniform)
     const int64_t p0 = a.gstart[g], p1 = a.gend[g];
     const int64_t p = p0 + lane;
     const bool active = p < p1;
@@ -460,7 +468,7 @@ __global__ void __launch_bounds__(NW * 32) k_p2p(EvalArgs a, const typename V4<r
         }
     }
     while (t < t1) {
-        const int cnt = m.y, flags = m.z | (a.src_active[m.w] ? 0 : 4);
+        const int cnt = m.y, flags = m.z | (a.src_active[m.w] && ((dm >> m.w) & 1ull) ? 0 : 4);
         const int64_t first = (int64_t)__float_as_int(d.w);
         // target relative to the leaf centre: FP32 from the tile's offset,
         // else formed in FP64 (and split for double-single)
@@ -527,9 +535,10 @@ __global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a,
     __shared__ real red[NW][4][32];
     __shared__ int64_t s_item;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned long long dm = body_mask(a.bmask);
     for (int64_t it = next_item(a.m2p_work, -1, &s_item); it < a.n_fitems; it = next_item(a.m2p_work, it, &s_item)) {
     const int64_t g = a.fitem_group[it];
-    if (!((a.tgt_mask >> a.gbody[g]) & 1ull) || g < a.g_lo || g >= a.g_hi) continue;  // rows not used (block-uniform)
+    if (!(((a.tgt_mask & dm) >> a.gbody[g]) & 1ull) || g < a.g_lo || g >= a.g_hi) continue;  // rows not used (block-uniform)
     const int64_t p0 = a.gstart[g], p1 = a.gend[g];
     const int64_t p = p0 + lane;
     const bool active = p < p1;
@@ -546,7 +555,7 @@ __global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a,
             int nn;
             S qx, qy, qz;
             entry_offset<S>(a, ee, true, gc0, gc1, gc2, nn, qx, qy, qz);
-            if (a.src_active[a.nbody[nn]]) return ee;
+            if (a.src_active[a.nbody[nn]] && ((dm >> a.nbody[nn]) & 1ull)) return ee;
             ee += NW;
         }
         return ee;
@@ -596,6 +605,7 @@ struct UpArgs {
     int64_t n_leaves;
     const int32_t *leaf_node, *nstart, *nend, *child, *nchild, *nbody;
     int src_active[PGB_MAX_BODIES];
+    const unsigned long long* bmask = nullptr;  // as EvalArgs::bmask
     const double* ncenter;
     int K;
     int64_t lvl_begin, lvl_end;  // node ids of one level (unused by k_upward)
@@ -606,6 +616,12 @@ struct UpArgs {
     const int32_t* parent;       // k_upward: parent of every node (-1 at a body's root)
     int* arrive;                 // k_upward: per node, children finished (zero between launches)
 };
+// a source body of the upward pass is used (its densities are not all zero
+// and the run-time mask keeps it)
+__device__ __forceinline__ bool body_on(const UpArgs& a, int b) {
+    return a.src_active[b] && (!a.bmask || ((*a.bmask >> b) & 1ull));
+}
+
 
 __device__ __constant__ const int kBinom[9][9] = {
     {1, 0, 0, 0, 0, 0, 0, 0, 0},      {1, 1, 0, 0, 0, 0, 0, 0, 0},      {1, 2, 1, 0, 0, 0, 0, 0, 0},
@@ -666,7 +682,7 @@ __global__ void __launch_bounds__(128) k_far_coef(UpArgs a, const real* __restri
     for (int k = threadIdx.x; k < NNZ; k += blockDim.x) tab[k] = gtab[k];
     real* __restrict__ far = (real*)a.far;
     for (int64_t nd = blockIdx.x; nd < a.n_nodes; nd += gridDim.x) {
-        if (!a.src_active[a.nbody[nd]]) continue;  // block-uniform
+        if (!body_on(a, a.nbody[nd])) continue;  // block-uniform
         __syncthreads();
         for (int k = threadIdx.x; k < 2 * T; k += blockDim.x) sm[k] = mom[nd * 2 * T + k];
         for (int k = T + threadIdx.x; k < TP; k += blockDim.x) {  // padding
@@ -719,7 +735,7 @@ __global__ void __launch_bounds__(256) k_far_f32(UpArgs a, const float* __restri
     __shared__ float m[T];
     const int64_t nd = blockIdx.x;
     const int t = blockIdx.y;  // 0: Yukawa (moments T .. 2T-1), 1: Laplace
-    if (!a.src_active[a.nbody[nd]]) return;  // block-uniform
+    if (!body_on(a, a.nbody[nd])) return;  // block-uniform
     for (int k = threadIdx.x; k < T; k += blockDim.x) m[k] = mom[nd * 2 * T + (t == 0 ? T : 0) + k];
     __syncthreads();
     const int j = threadIdx.x;
@@ -941,7 +957,7 @@ __global__ void __launch_bounds__(128) k_upward(UpArgs a, const typename V4<real
     __syncthreads();
     for (int64_t leaf = blockIdx.x; leaf < a.n_leaves; leaf += gridDim.x) {
         int nd = a.leaf_node[leaf];
-        if (!a.src_active[a.nbody[nd]]) continue;  // block-uniform
+        if (!body_on(a, a.nbody[nd])) continue;  // block-uniform
         up_p2m<real, P>(a, nd, src, mom, sh);
         for (;;) {
             // publish nd's moments, then count it at its parent

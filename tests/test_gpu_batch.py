@@ -141,3 +141,54 @@ def test_pose_batch_argument_checks():
             pgb.pgb_destroy(c2)
     finally:
         pgb.pgb_destroy(c)
+
+
+@pytest.mark.parametrize("mode", sorted(MODES))
+@pytest.mark.parametrize("precond", [0, 1])
+def test_replayed_lockstep_iterations_match_host_loop(mode, precond):
+    """The lockstep iterations replayed from a graph (graphs = 2: a device
+    while loop, per-problem convergence and the body mask of the products on
+    the device) reproduce the host-driven loop (graphs = 1) bit for bit, with
+    the same iteration counts, through restarts (restart 8) and problems that
+    finish at different iterations; the host makes far fewer launch calls."""
+    m, tol, _ = MODES[mode]
+    Rs, ts = _poses(47, 5)
+    ch = gpu_context(_pair(), batch=5, graphs=1, precond=precond, **TC)
+    cg = gpu_context(_pair(), batch=5, graphs=2, precond=precond, **TC)
+    try:
+        pgb.pgb_timing(ch, True, read=False)
+        pgb.pgb_timing(cg, True, read=False)
+        codeh, Fh, sth = pgb.pgb_solve_batch(ch, 0, Rs, ts, m, tol, 2000, 8)
+        codeg, Fg, stg = pgb.pgb_solve_batch(cg, 0, Rs, ts, m, tol, 2000, 8)
+        th = pgb.pgb_timing(ch, False, read=True)
+        tg = pgb.pgb_timing(cg, False, read=True)
+        assert codeh == 0 and codeg == 0
+        assert np.array_equal(Fg, Fh)
+        assert [s["iterations"] for s in stg] == [s["iterations"] for s in sth]
+        assert [s["rel_residual"] for s in stg] == [s["rel_residual"] for s in sth]
+        assert tg["host_launches"] < 0.5 * th["host_launches"]
+    finally:
+        pgb.pgb_destroy(ch)
+        pgb.pgb_destroy(cg)
+
+
+@pytest.mark.parametrize("mode", ["fp32", "refine"])
+def test_replayed_iterations_molecules_of_two_sizes(mode):
+    """Chunks of two molecules of different sizes (their problems finish at
+    different iterations, so the device body mask drops finished ones from
+    the products mid-cycle): graphs = 2 equals the host loop bit for bit."""
+    m, tol, _ = MODES[mode]
+    Rs, ts = _poses(53, 6)
+    pose_ctx = np.array([0, 1, 0, 1, 0, 1])
+    out = {}
+    for gr in (1, 2):
+        ctxs = [gpu_context(_pair(nu=5), batch=3, graphs=gr, **TC), gpu_context(_pair(seed=9, nu=7), graphs=gr, **TC)]
+        try:
+            out[gr] = pgb.pgb_solve_poses(ctxs, pose_ctx, 0, Rs, ts, m, tol, 2000, 100)
+        finally:
+            for c in ctxs:
+                pgb.pgb_destroy(c)
+    (c1, F1, s1), (c2, F2, s2) = out[1], out[2]
+    assert c1 == 0 and c2 == 0
+    assert np.array_equal(F2, F1)
+    assert [s["iterations"] for s in s2] == [s["iterations"] for s in s1]
