@@ -65,7 +65,8 @@ typedef struct pgb_params {
     int32_t K;            /* far-field points per panel: 1, 3, 4 or 7 (Section 3.1) */
     int32_t K_near;       /* fine rule inside 2L: 19 (Section 3.1) */
     int32_t n_edge;       /* Gauss points per edge for the self panel: 3, 6, 9 or 12 */
-    int32_t P;            /* Taylor order, 0..8 (Section 3.2) */
+    int32_t P;            /* Taylor order: 0..8, 10, 12 or 15 (Section 3.2; Tables 1
+                             and 2 use 15); pgb_grad takes 0..8 */
     double theta;         /* multipole acceptance criterion; 0 = direct sum */
     int32_t leaf_size;    /* N_crit: max panels per octree leaf, 1..1024 */
     int32_t group_size;   /* targets per interaction list: 32 (one warp) */
@@ -444,7 +445,7 @@ int pgb_solve_shard(struct pgb_ctx* ctx, int32_t rank, int32_t world, double* xs
 
 /* Diagnostic: the host-computed table that turns a node's Taylor moments
  * (Section 3.2) into the coefficients its far field is evaluated from, for
- * order P (0..8) and screening kappa >= 0.  With T = (P+1)(P+2)(P+3)/6, out
+ * order P (0..15) and screening kappa >= 0.  With T = (P+1)(P+2)(P+3)/6, out
  * (host, n = 2 T^2 doubles) receives the Yukawa table then the Laplace
  * table, each T x T row-major: row = coefficient of S^(a,b,c), S = R/|R|^2,
  * in the order a = 0..P, b = 0..P-a, c = 0..P-a-b; column = moment M_k with

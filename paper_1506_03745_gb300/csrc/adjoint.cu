@@ -246,7 +246,7 @@ static void dispatch_T(pgb_ctx* c, const TArgs& ta, const void* xrel, const void
         case 6: launch_T<real, 6>(c, ta, xrel, yrel, nrm, L); break;
         case 7: launch_T<real, 7>(c, ta, xrel, yrel, nrm, L); break;
         case 8: launch_T<real, 8>(c, ta, xrel, yrel, nrm, L); break;
-        default: fail(PGB_EINVAL, "P out of range");
+        default: fail(PGB_EINVAL, "the transposed treecode takes P in 0..8");
     }
 }
 

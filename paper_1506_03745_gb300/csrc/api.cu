@@ -103,7 +103,7 @@ static int check_params(const pgb_params* p, std::string& why) {
     if (!(p->K == 1 || p->K == 3 || p->K == 4 || p->K == 7)) why = "K must be 1, 3, 4 or 7";
     else if (p->K_near != 19) why = "K_near must be 19";
     else if (!(p->n_edge == 3 || p->n_edge == 6 || p->n_edge == 9 || p->n_edge == 12)) why = "n_edge must be 3, 6, 9 or 12";
-    else if (p->P < 0 || p->P > PGB_MAX_P) why = "P must be in 0..8";
+    else if (!p_supported(p->P)) why = "P must be in 0..8, or 10, 12 or 15";
     else if (!(p->theta >= 0 && p->theta < 1)) why = "theta must be in [0, 1)";
     else if (p->leaf_size < 1 || p->leaf_size > 1024) why = "leaf_size must be in 1..1024";
     else if (p->group_size != 32) why = "group_size must be 32";
@@ -777,6 +777,7 @@ int pgb_grad(pgb_ctx* c, const double* x, int32_t precision, double tol, int32_t
         if (!(tol > 0 && tol < 1)) fail(PGB_EINVAL, "tol must be in (0, 1)");
         if (max_iter < 1 || restart < 1 || restart > 256) fail(PGB_EINVAL, "max_iter >= 1 and restart in 1..256");
         if (nested(c)) fail(PGB_EINVAL, "gradients are not available with nested interfaces");
+        if (c->p.P > 8) fail(PGB_EINVAL, "adjoint gradients take P in 0..8");
         pgb_solve_stats st{};
         grad(c, x, precision, tol, max_iter, restart, dq, dbc, dt, &st);
         if (adj) *adj = st;

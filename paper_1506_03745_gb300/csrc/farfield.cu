@@ -139,8 +139,8 @@ void far_tables(int P, double kappa, std::vector<double>& tab) {
 }
 
 // Device copy of the tables for the context's P and the screening kappa
-// (one per kappa: the solvent, and each region of a nested system), in FP64
-// and FP32.
+// (one per kappa: the solvent, and each region of a nested system), in FP64,
+// double-single and FP32 (transposed dense, and packed for orders above 8).
 const FarTab& far_table(pgb_ctx* c, double kappa) {
     for (const auto& t : c->far_tabs)
         if (t->P == c->p.P && t->kappa == kappa) return *t;
@@ -186,12 +186,16 @@ const FarTab& far_table(pgb_ctx* c, double kappa) {
         hds[2 * q] = hi;
         hds[2 * q + 1] = (float)(h[q] - (double)hi);
     }
+    std::vector<float> hp(h.size());
+    for (size_t q = 0; q < h.size(); ++q) hp[q] = (float)h[q];
     t->t64.resize(h.size());
     t->t32.resize(hf.size());
     t->tds.resize(h.size());
+    t->t32p.resize(hp.size());
     PGB_CUDA(cudaMemcpyAsync(t->t64.p, h.data(), 8 * h.size(), cudaMemcpyHostToDevice, c->stream));
     PGB_CUDA(cudaMemcpyAsync(t->t32.p, hf.data(), 4 * hf.size(), cudaMemcpyHostToDevice, c->stream));
     PGB_CUDA(cudaMemcpyAsync(t->tds.p, hds.data(), 4 * hds.size(), cudaMemcpyHostToDevice, c->stream));
+    PGB_CUDA(cudaMemcpyAsync(t->t32p.p, hp.data(), 4 * hp.size(), cudaMemcpyHostToDevice, c->stream));
     PGB_CUDA(cudaStreamSynchronize(c->stream));
     c->far_tabs.push_back(std::move(t));
     return *c->far_tabs.back();
@@ -200,7 +204,7 @@ const FarTab& far_table(pgb_ctx* c, double kappa) {
 }  // namespace pgb
 
 extern "C" int pgb_far_table(int32_t P, double kappa, double* out, int64_t n) {
-    if (P < 0 || P > PGB_MAX_P || kappa < 0 || !out) return PGB_EINVAL;
+    if (P < 0 || P > PGB_MAX_P || !(kappa >= 0) || !out) return PGB_EINVAL;
     const int T = pgb::n_terms(P);
     if (n != 2 * (int64_t)T * T) return PGB_EINVAL;
     std::vector<double> tab;

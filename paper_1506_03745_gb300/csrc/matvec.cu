@@ -524,7 +524,8 @@ void apply_mode(pgb_ctx* c, const double* x, double* y, int precision, int mode,
     const bool dsp = precision == PGB_FP64_DS;
     auto tab_for = [&](double kappa) -> const void* {
         const FarTab& t = far_table(c, kappa);
-        return f32 ? (const void*)t.t32.p : dsp ? (const void*)t.tds.p : (const void*)t.t64.p;
+        if (f32) return P > 8 ? (const void*)t.t32p.p : (const void*)t.t32.p;
+        return dsp ? (const void*)t.tds.p : (const void*)t.t64.p;
     };
     up.far_tab = tab_for(c->kappa);
     if (nested(c)) {

@@ -9,7 +9,9 @@
 
 #include "../../include/pgb.h"
 
-#define PGB_MAX_P 8
+#define PGB_MAX_P 15
+// Taylor orders with compiled kernels: 0..8, 10, 12 and 15 (the adjoint: 0..8)
+inline bool p_supported(int P) { return (P >= 0 && P <= 8) || P == 10 || P == 12 || P == 15; }
 #define PGB_MAX_BODIES 64
 #define PGB_LIST_STACK 96
 
@@ -106,6 +108,7 @@ struct FarTab {
     DBuf<double> t64;
     DBuf<float> t32;
     DBuf<double> tds;  // the FP64 table split into double-single pairs (8 bytes each)
+    DBuf<float> t32p;  // the packed layout of t64 rounded to FP32 (orders above 8)
 };
 // padded coefficient count per kernel: rows of 16 bytes for vector loads
 __host__ __device__ constexpr int n_terms_pad(int P) { return (n_terms(P) + 3) & ~3; }

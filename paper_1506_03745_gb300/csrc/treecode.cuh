@@ -18,6 +18,8 @@
 // Laplace is the same with kappa = 0 (H_0 = 1, H_k = 0).
 // Moment shift (upward pass): M_k(c') = sum_{j<=k} C(k,j) (c'-c)^{k-j} M_j(c).
 #pragma once
+#include <algorithm>
+
 #include "common.cuh"
 #include "ds.cuh"
 #include "pgb_internal.cuh"
@@ -530,7 +532,11 @@ __global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a,
     using S = typename Store<real>::S;  // storage type of the inputs
     using s4 = typename V4<S>::t;
     constexpr int TP = n_terms_pad(P);
-    constexpr int MW = (2 * TP + 31) / 32;  // coefficient words per lane
+    // orders up to 8: the next node's coefficients are prefetched into
+    // registers (MW words per lane) while the current one is evaluated;
+    // above, they are loaded into shared memory when needed
+    constexpr bool BIG = P > 8;
+    constexpr int MW = BIG ? 1 : (2 * TP + 31) / 32;
     __shared__ __align__(16) real sM[NW][2 * TP];
     __shared__ real red[NW][4][32];
     __shared__ int64_t s_item;
@@ -566,29 +572,37 @@ __global__ void __launch_bounds__(NW * 32) k_m2p(EvalArgs a,
     int64_t e = seek(fb + w);
     if (e < f1) {
         entry_offset<S>(a, e, true, gc0, gc1, gc2, nd, ox, oy, oz);
+        if constexpr (!BIG) {
 #pragma unroll
-        for (int q = 0; q < MW; ++q) {
-            const int k = lane + 32 * q;
-            pm[q] = k < 2 * TP ? far[(int64_t)nd * 2 * TP + k] : real(0);
+            for (int q = 0; q < MW; ++q) {
+                const int k = lane + 32 * q;
+                pm[q] = k < 2 * TP ? far[(int64_t)nd * 2 * TP + k] : real(0);
+            }
         }
     }
     while (e < f1) {
         __syncwarp();
+        if constexpr (BIG) {
+            for (int k = lane; k < 2 * TP; k += 32) sM[w][k] = far[(int64_t)nd * 2 * TP + k];
+        } else {
 #pragma unroll
-        for (int q = 0; q < MW; ++q) {
-            const int k = lane + 32 * q;
-            if (k < 2 * TP) sM[w][k] = pm[q];
+            for (int q = 0; q < MW; ++q) {
+                const int k = lane + 32 * q;
+                if (k < 2 * TP) sM[w][k] = pm[q];
+            }
         }
         __syncwarp();
         const bool lap = (a.nbody[nd] == gb) && a.lap_body[gb];
         const real Rx = to_c<real>(xr.x - ox), Ry = to_c<real>(xr.y - oy), Rz = to_c<real>(xr.z - oz);
         e = seek(e + NW);
-        if (e < f1) {  // prefetch the next node
+        if (e < f1) {  // the next node (its coefficients prefetched up to order 8)
             entry_offset<S>(a, e, true, gc0, gc1, gc2, nd, ox, oy, oz);
+            if constexpr (!BIG) {
 #pragma unroll
-            for (int q = 0; q < MW; ++q) {
-                const int k = lane + 32 * q;
-                pm[q] = k < 2 * TP ? far[(int64_t)nd * 2 * TP + k] : real(0);
+                for (int q = 0; q < MW; ++q) {
+                    const int k = lane + 32 * q;
+                    pm[q] = k < 2 * TP ? far[(int64_t)nd * 2 * TP + k] : real(0);
+                }
             }
         }
         real uL, uY;
@@ -622,6 +636,14 @@ __device__ __forceinline__ bool body_on(const UpArgs& a, int b) {
     return a.src_active[b] && (!a.bmask || ((*a.bmask >> b) & 1ull));
 }
 
+
+// C(n, m) (0 for m > n), exact in double for the orders used here
+__device__ __forceinline__ double binom_exact(int n, int m) {
+    if (m > n) return 0.0;
+    double b = 1.0;
+    for (int i = 1; i <= m; ++i) b = b * (n - m + i) / i;
+    return b;
+}
 
 __device__ __constant__ const int kBinom[9][9] = {
     {1, 0, 0, 0, 0, 0, 0, 0, 0},      {1, 1, 0, 0, 0, 0, 0, 0, 0},      {1, 2, 1, 0, 0, 0, 0, 0, 0},
@@ -718,6 +740,73 @@ constexpr size_t far_coef_smem() {
     return sizeof(real) * (((far_pack_offset(P + 1, P) + 3) & ~3) + 2 * MI<P>::T);
 }
 
+// Orders above 8, where the packed table no longer fits shared memory: the
+// table is read from global memory (L2-resident) and each of its entries
+// serves NB nodes, whose moments the block stages in shared memory; a
+// thread forms output rows j (sums in the order of k_far_coef) for all NB
+// nodes.  Inactive nodes in a block get no output.
+template <typename real, int P, int NB>
+__global__ void __launch_bounds__(128) k_far_big(UpArgs a, const real* __restrict__ mom) {
+    constexpr int T = MI<P>::T;
+    constexpr int TP = n_terms_pad(P);
+    extern __shared__ __align__(16) unsigned char far_smem[];
+    real(*sm)[2 * T] = reinterpret_cast<real(*)[2 * T]>(far_smem);
+    const real* __restrict__ tab = (const real*)a.far_tab;
+    real* __restrict__ far = (real*)a.far;
+    for (int64_t n0 = (int64_t)blockIdx.x * NB; n0 < a.n_nodes; n0 += (int64_t)gridDim.x * NB) {
+        const int nn = (int)min((int64_t)NB, a.n_nodes - n0);
+        bool act[NB];
+#pragma unroll
+        for (int i = 0; i < NB; ++i) act[i] = i < nn && body_on(a, a.nbody[n0 + i]);
+        __syncthreads();
+        for (int q = threadIdx.x; q < NB * 2 * T; q += blockDim.x) {
+            const int i = q / (2 * T), k = q - i * 2 * T;
+            sm[i][k] = act[i] ? mom[(n0 + i) * 2 * T + k] : real(0);
+        }
+        for (int q = threadIdx.x; q < NB * (TP - T); q += blockDim.x) {  // padding
+            const int i = q / (TP - T), k = T + q - i * (TP - T);
+            if (act[i]) {
+                far[(n0 + i) * 2 * TP + k] = real(0);
+                far[(n0 + i) * 2 * TP + TP + k] = real(0);
+            }
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < T; j += blockDim.x) {
+            int x, y, z;
+            decode_mi(j, x, y, z);
+            const int p = x + y + z;
+            const int g0 = p * (p + 1) * (p + 2) / 6;
+            const real* row = tab + far_pack_offset(p, P) + (int64_t)(j - g0) * far_row_nnz(p, P);
+            real aY[NB], aL[NB];
+#pragma unroll
+            for (int i = 0; i < NB; ++i) aY[i] = aL[i] = real(0);
+            int e = 0;
+            for (int q = p; q <= P; q += 2) {
+                const int k0 = q * (q + 1) * (q + 2) / 6, k1 = k0 + (q + 1) * (q + 2) / 2;
+                for (int k = k0; k < k1; ++k) {
+                    const real t = row[e++];
+#pragma unroll
+                    for (int i = 0; i < NB; ++i) aY[i] += t * sm[i][T + k];
+                }
+            }
+            for (int k = g0; k < g0 + (p + 1) * (p + 2) / 2; ++k) {
+                const real t = row[e++];
+#pragma unroll
+                for (int i = 0; i < NB; ++i) aL[i] += t * sm[i][k];
+            }
+            int ev = 0;
+            for (int aa = 0; aa < x; ++aa) ev += (P - aa + 1) * (P - aa + 2) / 2;
+            ev += y * (P - x + 1) - y * (y - 1) / 2 + z;
+#pragma unroll
+            for (int i = 0; i < NB; ++i)
+                if (act[i]) {
+                    far[(n0 + i) * 2 * TP + ev] = aL[i];
+                    far[(n0 + i) * 2 * TP + TP + ev] = aY[i];
+                }
+        }
+    }
+}
+
 // FP32 far-field coefficients: one block per (node, table), one thread per
 // output j of the evaluation order (blockDim = n_terms_pad(P) rounded up to
 // 32), E[j] = sum_k M[k] tab[k][j] over the table transposed and padded
@@ -758,18 +847,26 @@ __global__ void __launch_bounds__(256) k_far_f32(UpArgs a, const float* __restri
 // for another.  Writers fence before their increment; the climbing block
 // fences after it and reads the children's moments from L2 (ld.global.cg).
 // The far-field coefficients follow in k_far_coef.
+// children shifted at once by the moment shift: all eight while their two
+// buffers take at most 64 KB, else half as many per halving
+__host__ __device__ constexpr int up_child_batch(int bytes, int T) {
+    int cb = 8;
+    while (cb > 1 && 2 * cb * 2 * T * bytes > 64 * 1024) cb /= 2;
+    return cb;
+}
 template <typename real, int P>
 struct UpShared {
     static constexpr int T = MI<P>::T;
     static constexpr int TD = P * (P + 1) * (P + 2) / 6 > 0 ? P * (P + 1) * (P + 2) / 6 : 1;
+    static constexpr int CB = up_child_batch((int)sizeof(real), T);
     struct P2M {
         real pw[128][3][P + 1];
         real sq[128][5];
         real sd[3][TD];
     };
     struct M2M {
-        real bufA[8][2 * T], bufB[8][2 * T];
-        real cd[8][3][P + 1];
+        real bufA[CB][2 * T], bufB[CB][2 * T];
+        real cd[CB][3][P + 1];
     };
     union {
         P2M p;
@@ -810,21 +907,25 @@ __device__ __forceinline__ void up_p2m(const UpArgs& a, int nd, const typename V
                                        real* __restrict__ mom, UpShared<real, P>& sh) {
     using v4 = typename V4<real>::t;
     constexpr int T = MI<P>::T;
+    constexpr int H = (T + 127) / 128;  // multi-indices per thread
     const int tid = threadIdx.x;
     const int64_t s0 = (int64_t)a.nstart[nd] * a.K, s1 = (int64_t)a.nend[nd] * a.K;
-    int kx[2] = {0, 0}, ky[2] = {0, 0}, kz[2] = {0, 0};
-    bool on[2], low[2];
-    for (int h = 0; h < 2; ++h) {
+    int kx[H], ky[H], kz[H];
+    bool on[H], low[H];
+    real qL[H], qY[H], dx[H], dy[H], dz[H];
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
         const int k = tid + 128 * h;
         on[h] = k < T;
+        kx[h] = ky[h] = kz[h] = 0;
         if (on[h]) {
             kx[h] = sh.kk[k][0];
             ky[h] = sh.kk[k][1];
             kz[h] = sh.kk[k][2];
         }
         low[h] = on[h] && kx[h] + ky[h] + kz[h] < P;
+        qL[h] = qY[h] = dx[h] = dy[h] = dz[h] = real(0);
     }
-    real qL[2] = {0, 0}, qY[2] = {0, 0}, dx[2] = {0, 0}, dy[2] = {0, 0}, dz[2] = {0, 0};
     for (int64_t t = s0; t < s1; t += 128) {
         const int cnt = (int)min((int64_t)128, s1 - t);
         __syncthreads();
@@ -846,7 +947,7 @@ __device__ __forceinline__ void up_p2m(const UpArgs& a, int nd, const typename V
         }
         __syncthreads();
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < H; ++h) {
             if (!on[h]) continue;
             for (int j = 0; j < cnt; ++j) {
                 const real mono = sh.u.p.pw[j][0][kx[h]] * sh.u.p.pw[j][1][ky[h]] * sh.u.p.pw[j][2][kz[h]];
@@ -861,7 +962,8 @@ __device__ __forceinline__ void up_p2m(const UpArgs& a, int nd, const typename V
         }
     }
     __syncthreads();
-    for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int h = 0; h < H; ++h)
         if (low[h]) {
             const int k = tid + 128 * h;
             sh.u.p.sd[0][k] = dx[h];
@@ -869,7 +971,8 @@ __device__ __forceinline__ void up_p2m(const UpArgs& a, int nd, const typename V
             sh.u.p.sd[2][k] = dz[h];
         }
     __syncthreads();
-    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
         if (!on[h]) continue;
         const int k = tid + 128 * h;
         real dl = 0;
@@ -884,54 +987,68 @@ __device__ __forceinline__ void up_p2m(const UpArgs& a, int nd, const typename V
 // Moment shift of node nd from its (at most eight) children,
 // M_k(c) = sum_{j<=k} C(k,j) (c - c_child)^{k-j} M_j(c_child): the shift is
 // separable, so it is applied as three one-axis passes x, y, z, each output
-// summing at most P+1 terms; all children are shifted at once, then summed
-// in child order.  The children's moments are read from L2.
+// summing at most P+1 terms; CB children are shifted at once, and the results
+// summed in child order.  The children's moments are read from L2.
 template <typename real, int P>
 __device__ __forceinline__ void up_m2m(const UpArgs& a, int nd, real* __restrict__ mom, UpShared<real, P>& sh) {
     constexpr int T = MI<P>::T;
+    constexpr int CB = UpShared<real, P>::CB;
+    constexpr int HO = (2 * T + 127) / 128;  // outputs per thread
     const int tid = threadIdx.x;
     const int nc = a.nchild[nd];
     const int fc = a.child[nd];
-    __syncthreads();
-    for (int q = tid; q < nc * 2 * T; q += blockDim.x) {
-        const int ci = q / (2 * T), k = q - ci * 2 * T;
-        sh.u.m.bufA[ci][k] = ld_cg(mom + (int64_t)(fc + ci) * 2 * T + k);
-    }
-    if (tid < 3 * nc) {
-        const int ci = tid / 3, ax = tid - 3 * ci;
-        const real d = from_dbl<real>(a.ncenter[3 * nd + ax] - a.ncenter[3 * (fc + ci) + ax]);
-        real v = 1;
-        for (int m = 0; m <= P; ++m) {
-            sh.u.m.cd[ci][ax][m] = v;
-            v = v * d;
+    real acc[HO];
+#pragma unroll
+    for (int h = 0; h < HO; ++h) acc[h] = real(0);
+    for (int c0 = 0; c0 < nc; c0 += CB) {
+        const int nb = min(CB, nc - c0);
+        __syncthreads();
+        for (int q = tid; q < nb * 2 * T; q += blockDim.x) {
+            const int ci = q / (2 * T), k = q - ci * 2 * T;
+            sh.u.m.bufA[ci][k] = ld_cg(mom + (int64_t)(fc + c0 + ci) * 2 * T + k);
         }
-    }
-    __syncthreads();
-#pragma unroll 1
-    for (int ax = 0; ax < 3; ++ax) {
-        real(*srcb)[2 * T] = (ax == 1) ? sh.u.m.bufB : sh.u.m.bufA;
-        real(*dstb)[2 * T] = (ax == 1) ? sh.u.m.bufA : sh.u.m.bufB;
-        for (int it = tid; it < nc * T; it += blockDim.x) {
-            const int ci = it / T, k = it - ci * T;
-            const int k0 = sh.kk[k][0], k1 = sh.kk[k][1], k2 = sh.kk[k][2];
-            const int ka = sh.kk[k][ax];
-            real sL = 0, sY = 0;
-            for (int j = 0; j <= ka; ++j) {
-                const int jx = ax == 0 ? j : k0, jy = ax == 1 ? j : k1, jz = ax == 2 ? j : k2;
-                const int jj = sh.idx3[jx][jy][jz];
-                const real coef = sh.binom[ka][j] * sh.u.m.cd[ci][ax][ka - j];
-                sL += coef * srcb[ci][jj];
-                sY += coef * srcb[ci][T + jj];
+        if (tid < 3 * nb) {
+            const int ci = tid / 3, ax = tid - 3 * ci;
+            const real d = from_dbl<real>(a.ncenter[3 * nd + ax] - a.ncenter[3 * (fc + c0 + ci) + ax]);
+            real v = 1;
+            for (int m = 0; m <= P; ++m) {
+                sh.u.m.cd[ci][ax][m] = v;
+                v = v * d;
             }
-            dstb[ci][k] = sL;
-            dstb[ci][T + k] = sY;
         }
         __syncthreads();
+#pragma unroll 1
+        for (int ax = 0; ax < 3; ++ax) {
+            real(*srcb)[2 * T] = (ax == 1) ? sh.u.m.bufB : sh.u.m.bufA;
+            real(*dstb)[2 * T] = (ax == 1) ? sh.u.m.bufA : sh.u.m.bufB;
+            for (int it = tid; it < nb * T; it += blockDim.x) {
+                const int ci = it / T, k = it - ci * T;
+                const int k0 = sh.kk[k][0], k1 = sh.kk[k][1], k2 = sh.kk[k][2];
+                const int ka = sh.kk[k][ax];
+                real sL = 0, sY = 0;
+                for (int j = 0; j <= ka; ++j) {
+                    const int jx = ax == 0 ? j : k0, jy = ax == 1 ? j : k1, jz = ax == 2 ? j : k2;
+                    const int jj = sh.idx3[jx][jy][jz];
+                    const real coef = sh.binom[ka][j] * sh.u.m.cd[ci][ax][ka - j];
+                    sL += coef * srcb[ci][jj];
+                    sY += coef * srcb[ci][T + jj];
+                }
+                dstb[ci][k] = sL;
+                dstb[ci][T + k] = sY;
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int h = 0; h < HO; ++h) {
+            const int k = tid + 128 * h;
+            if (k < 2 * T)
+                for (int ci = 0; ci < nb; ++ci) acc[h] += sh.u.m.bufB[ci][k];
+        }
     }
-    for (int k = tid; k < 2 * T; k += blockDim.x) {
-        real acc = 0;
-        for (int ci = 0; ci < nc; ++ci) acc += sh.u.m.bufB[ci][k];
-        mom[(int64_t)nd * 2 * T + k] = acc;
+#pragma unroll
+    for (int h = 0; h < HO; ++h) {
+        const int k = tid + 128 * h;
+        if (k < 2 * T) mom[(int64_t)nd * 2 * T + k] = acc[h];
     }
 }
 
@@ -939,8 +1056,8 @@ template <typename real, int P>
 __global__ void __launch_bounds__(128) k_upward(UpArgs a, const typename V4<real>::t* __restrict__ src,
                                                 real* __restrict__ mom) {
     constexpr int T = MI<P>::T;
-    static_assert(T <= 2 * 128, "two terms per thread at most");
-    __shared__ UpShared<real, P> sh;
+    extern __shared__ __align__(16) unsigned char up_smem[];
+    UpShared<real, P>& sh = *reinterpret_cast<UpShared<real, P>*>(up_smem);
     const int tid = threadIdx.x;
     for (int k = tid; k < T; k += blockDim.x) {
         int x, y, z;
@@ -952,7 +1069,7 @@ __global__ void __launch_bounds__(128) k_upward(UpArgs a, const typename V4<real
     }
     for (int q = tid; q < (P + 1) * (P + 1); q += blockDim.x) {
         const int n = q / (P + 1), m = q - n * (P + 1);
-        sh.binom[n][m] = (real)kBinom[n][m];
+        sh.binom[n][m] = from_dbl<real>(binom_exact(n, m));
     }
     __syncthreads();
     for (int64_t leaf = blockIdx.x; leaf < a.n_leaves; leaf += gridDim.x) {
@@ -977,6 +1094,68 @@ __global__ void __launch_bounds__(128) k_upward(UpArgs a, const typename V4<real
             if (tid == 0) a.arrive[par] = 0;  // every child has arrived: ready for the next launch
             nd = par;
         }
+    }
+}
+
+// M2P warps per block: 8 (FP32) or 4 (8-byte types, for their registers),
+// halved while the per-warp coefficient slices exceed 40 KB of shared memory
+template <typename real, int P>
+constexpr int m2p_warps() {
+    int nw = sizeof(real) == 8 ? 4 : 8;
+    while (nw > 1 && (size_t)nw * 2 * n_terms_pad(P) * sizeof(real) > 40 * 1024) nw /= 2;
+    return nw;
+}
+
+// Nodes per block of k_far_big.
+constexpr int FAR_BIG_NB = 4;
+
+// The upward pass of one product: P2M and the moment shifts in one launch
+// (k_upward), then the far-field coefficients (orders up to 8: k_far_f32 in
+// FP32, k_far_coef with the packed table in shared memory otherwise; above:
+// k_far_big for every type).
+template <typename real, int P>
+void launch_upward(const UpArgs& up, const void* src, void* mom, cudaStream_t s) {
+    using v4 = typename V4<real>::t;
+    if (up.n_leaves <= 0) return;
+    constexpr size_t up_smem = sizeof(UpShared<real, P>);
+    static bool up_attr = false;  // per instantiation
+    if (!up_attr) {
+        PGB_CUDA(cudaFuncSetAttribute(k_upward<real, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)up_smem));
+        up_attr = true;
+    }
+    const int64_t grid = up.p2m_grid > 0 ? std::min<int64_t>(up.n_leaves, up.p2m_grid) : up.n_leaves;
+    k_upward<real, P><<<(unsigned)grid, 128, up_smem, s>>>(up, (const v4*)src, (real*)mom);
+    if (up.n_nodes <= 0) return;
+    int dev = 0, n_sm = 0;
+    PGB_CUDA(cudaGetDevice(&dev));
+    PGB_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    if constexpr (P > 8) {
+        constexpr size_t smem = sizeof(real) * FAR_BIG_NB * 2 * MI<P>::T;
+        static bool attr = false;
+        if (!attr) {
+            PGB_CUDA(cudaFuncSetAttribute(k_far_big<real, P, FAR_BIG_NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+            attr = true;
+        }
+        int64_t gf = (up.n_nodes + FAR_BIG_NB - 1) / FAR_BIG_NB;
+        if (up.p2m_grid > 0) gf = std::min<int64_t>(gf, up.p2m_grid);
+        k_far_big<real, P, FAR_BIG_NB><<<(unsigned)std::max<int64_t>(gf, 1), 128, smem, s>>>(up, (const real*)mom);
+    } else if constexpr (sizeof(real) == sizeof(float)) {
+        // FP32: a block per (node, table), a thread per output
+        k_far_f32<P><<<dim3((unsigned)up.n_nodes, 2), far_tr(P), 0, s>>>(up, (const float*)mom);
+    } else {
+        // a few blocks per SM, each with the packed table in shared memory,
+        // taking the nodes in turn
+        constexpr size_t smem = far_coef_smem<real, P>();
+        static bool attr = false;
+        if (!attr) {
+            PGB_CUDA(cudaFuncSetAttribute(k_far_coef<real, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+            attr = true;
+        }
+        int64_t gf = std::min<int64_t>(up.n_nodes, 4 * (int64_t)n_sm);
+        if (up.p2m_grid > 0) gf = std::min<int64_t>(gf, up.p2m_grid);
+        k_far_coef<real, P><<<(unsigned)std::max<int64_t>(gf, 1), 128, smem, s>>>(up, (const real*)mom);
     }
 }
 

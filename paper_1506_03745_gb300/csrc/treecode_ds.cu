@@ -11,27 +11,12 @@ namespace pgb {
 template <int P>
 static void launch_ds(int stage, const UpArgs& up, const EvalArgs& ev, const void* src, const void* xrel, void* mom,
                       const void* far, cudaStream_t s) {
-    constexpr int NW = 4;   // M2P warps per block (registers, as the FP64 kernel)
-    constexpr int NWP = 8;  // P2P warps per block
+    constexpr int NW = m2p_warps<ds, P>();  // M2P warps per block (registers, as the FP64 kernel)
+    constexpr int NWP = 8;                   // P2P warps per block
     const bool persist = ev.p2p_work != nullptr;
-    if (stage == PGB_STAGE_UPWARD && up.n_leaves > 0) {
-        // P2M and the moment shifts, then the far-field coefficients, all in
-        // double-single on the FP32 pipe
-        const int64_t grid = up.p2m_grid > 0 ? std::min<int64_t>(up.n_leaves, up.p2m_grid) : up.n_leaves;
-        k_upward<ds, P><<<(unsigned)grid, 128, 0, s>>>(up, (const ds4*)src, (ds*)mom);
-        constexpr size_t smem = far_coef_smem<ds, P>();
-        static bool attr_set = false;
-        if (!attr_set) {
-            PGB_CUDA(cudaFuncSetAttribute(k_far_coef<ds, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr_set = true;
-        }
-        int dev = 0, n_sm = 0;
-        PGB_CUDA(cudaGetDevice(&dev));
-        PGB_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-        int64_t gf = std::min<int64_t>(up.n_nodes, 4 * (int64_t)n_sm);
-        if (up.p2m_grid > 0) gf = std::min<int64_t>(gf, up.p2m_grid);
-        k_far_coef<ds, P><<<(unsigned)std::max<int64_t>(gf, 1), 128, smem, s>>>(up, (const ds*)mom);
-    }
+    // P2M and the moment shifts, then the far-field coefficients, all in
+    // double-single on the FP32 pipe
+    if (stage == PGB_STAGE_UPWARD) launch_upward<ds, P>(up, src, mom, s);
     if (stage == PGB_STAGE_P2P && ev.n_pitems > 0)
         k_p2p<ds, NWP><<<(unsigned)(persist ? ev.persist_blocks : ev.n_pitems), NWP * 32, 0, s>>>(
             ev, (const ds4*)src, (const dbl4*)xrel);
@@ -65,6 +50,9 @@ void treecode_launch_ds(int stage, int P, const UpArgs& up, const EvalArgs& ev, 
         case 6: launch_ds<6>(stage, up, ev, src, xrel, mom, far, s); break;
         case 7: launch_ds<7>(stage, up, ev, src, xrel, mom, far, s); break;
         case 8: launch_ds<8>(stage, up, ev, src, xrel, mom, far, s); break;
+        case 10: launch_ds<10>(stage, up, ev, src, xrel, mom, far, s); break;
+        case 12: launch_ds<12>(stage, up, ev, src, xrel, mom, far, s); break;
+        case 15: launch_ds<15>(stage, up, ev, src, xrel, mom, far, s); break;
         default: fail(PGB_EINVAL, "P out of range");
     }
 }

@@ -14,6 +14,9 @@ void treecode_launch_f32(int stage, int P, const UpArgs& up, const std::vector<i
         case 6: launch_p<float, 6>(stage, up, lv, ev, src, xrel, mom, far, s); break;
         case 7: launch_p<float, 7>(stage, up, lv, ev, src, xrel, mom, far, s); break;
         case 8: launch_p<float, 8>(stage, up, lv, ev, src, xrel, mom, far, s); break;
+        case 10: launch_p<float, 10>(stage, up, lv, ev, src, xrel, mom, far, s); break;
+        case 12: launch_p<float, 12>(stage, up, lv, ev, src, xrel, mom, far, s); break;
+        case 15: launch_p<float, 15>(stage, up, lv, ev, src, xrel, mom, far, s); break;
         default: fail(PGB_EINVAL, "P out of range");
     }
 }

@@ -14,6 +14,9 @@ void treecode_launch_f64(int stage, int P, const UpArgs& up, const std::vector<i
         case 6: launch_p<double, 6>(stage, up, lv, ev, src, xrel, mom, far, s); break;
         case 7: launch_p<double, 7>(stage, up, lv, ev, src, xrel, mom, far, s); break;
         case 8: launch_p<double, 8>(stage, up, lv, ev, src, xrel, mom, far, s); break;
+        case 10: launch_p<double, 10>(stage, up, lv, ev, src, xrel, mom, far, s); break;
+        case 12: launch_p<double, 12>(stage, up, lv, ev, src, xrel, mom, far, s); break;
+        case 15: launch_p<double, 15>(stage, up, lv, ev, src, xrel, mom, far, s); break;
         default: fail(PGB_EINVAL, "P out of range");
     }
 }

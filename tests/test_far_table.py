@@ -2,7 +2,7 @@
 far field they give, sum_p D^p G(r) E_p(R) with E = table . moments, equals
 the oracle's truncated Taylor expansion of order P (Section 3.2) summed over
 point sources with single- and double-layer strengths, for Laplace and
-Yukawa kernels and P = 0..8."""
+Yukawa kernels and P = 0..8, 10, 12 and 15 (the paper's Tables 1 and 2)."""
 import math
 
 import numpy as np
@@ -51,7 +51,7 @@ def _far(P, kappa, tab, M, R, laplace):
     return math.exp(-x) / r * float((E * mono * np.array(g)[deg]).sum())
 
 
-@pytest.mark.parametrize("P", [0, 1, 2, 4, 6, 8])
+@pytest.mark.parametrize("P", [0, 1, 2, 4, 6, 8, 10, 12, 15])
 @pytest.mark.parametrize("kappa", [0.0, 0.125, 0.9])
 def test_far_table_reproduces_truncated_expansion(P, kappa):
     import paper_1506_03745_gb300._lib as L
@@ -78,6 +78,7 @@ def test_far_table_argument_errors():
     import paper_1506_03745_gb300._lib as L
     lib = L.lib()
     buf = (ctypes.c_double * 8)()
+    assert lib.pgb_far_table(16, 0.1, buf, 8) == L.PGB_EINVAL
     assert lib.pgb_far_table(9, 0.1, buf, 8) == L.PGB_EINVAL
     assert lib.pgb_far_table(0, -1.0, buf, 2) == L.PGB_EINVAL
     assert lib.pgb_far_table(0, 0.1, buf, 3) == L.PGB_EINVAL

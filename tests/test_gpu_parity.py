@@ -333,3 +333,46 @@ def test_iteration_graph_matches_host_loop(mode, precond):
     finally:
         pgb.pgb_destroy(cg)
         pgb.pgb_destroy(cp)
+
+
+@pytest.mark.parametrize("P", [10, 12, 15])
+def test_high_order_treecode_matches_oracle_treecode(P):
+    """Orders above 8 (Tables 1 and 2 use P = 15): the kernels that stage
+    the far coefficients without the register prefetch, the far-field table
+    read from L2 with several nodes per block, and the upward pass with its
+    children shifted in batches give the oracle treecode's product (same
+    lists, same truncated expansion) in FP64, double-single and FP32."""
+    bodies = spheres(**CASES["sigma_pair"])
+    so = oracle_system(bodies, theta=0.5, P=P, leaf_size=8)
+    ctx = gpu_context(bodies, theta=0.5, P=P, leaf_size=8)
+    try:
+        x = np.random.default_rng(3).normal(size=so.n)
+        ref = TreecodeOperator(so).apply(x)
+        scale = np.abs(ref).max()
+        y64 = _matvec(ctx, x, pgb.PGB_FP64)
+        assert np.abs(y64 - ref).max() / scale < 1e-10
+        yds = _matvec(ctx, x, pgb.PGB_FP64_DS)
+        assert np.abs(yds - y64).max() / scale < 1e-12
+        y32 = _matvec(ctx, x, pgb.PGB_FP32)
+        assert np.abs(y32 - ref).max() / scale < 2e-5
+        # the far field is in use: the product differs from the direct sum
+        # by more than round-off, and by less as P grows (Section 3.2)
+        direct = so.apply(x)
+        assert np.abs(ref - direct).max() / scale > 1e-12
+    finally:
+        pgb.pgb_destroy(ctx)
+
+
+def test_orders_without_kernels_are_rejected():
+    bodies = spheres(**CASES["sigma_pair"])
+    for P in (9, 11, 13, 14, 16):
+        with pytest.raises(pgb.PgbError):
+            gpu_context(bodies, theta=0.5, P=P)
+    ctx = gpu_context(bodies, theta=0.5, P=10)
+    try:
+        n = pgb.pgb_num_unknowns(ctx)
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        with pytest.raises(pgb.PgbError):
+            pgb.pgb_grad(ctx, x, 0, 0, pgb.PGB_FP64, 1e-8, 100, 50)
+    finally:
+        pgb.pgb_destroy(ctx)
