@@ -919,6 +919,87 @@ def run_poses_uneven(args):
         pgb.pgb_destroy(c)
 
 
+def _two_sphere_analytical(case):
+    """(F_int, solvation, surface, isolated molecule, isolated surface) of the
+    analytical two-sphere solution for `case`, and the volts of one internal
+    potential unit, from tests/golden/two_sphere_analytical.txt (written from
+    the series solution of Section 4 by make_two_sphere_analytical.py)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "two_sphere_analytical.txt")
+    volt, row = None, None
+    for line in open(path):
+        if line.startswith("# one internal potential unit"):
+            volt = float(line.split("=")[1].split()[0])
+        elif line.split()[:2] == [case, "60"]:
+            row = [float(v) for v in line.split()[2:]]
+    return row, volt
+
+
+def run_replica(args):
+    """The paper's grid-convergence case (Section 5.1, Table 1): a dielectric
+    sphere r = 5 A (eps 4, unit charge at its centre) and a sphere r = 4 A held
+    at phi0 = 1 internal potential unit, 12 A apart, kappa 0.125, eps 80, at
+    icosphere levels 3..6 (1280 ... 81920 panels per sphere), with the
+    paper's parameters (far rule 3 points, close-by rule `--near` points,
+    9 Gauss points per edge in-element, N_crit 300, P 15, theta 0.5, GMRES tol
+    1e-9; FP32 + refinement with the double-single residual).  Per level the
+    interaction energy F_int = F(pair) - F(molecule alone) - F(surface alone)
+    (Eq. 17) against the analytical value, and the observed order of
+    convergence of the three finest meshes."""
+    import math
+    import torch
+    import synth
+    import paper_1506_03745_gb300 as pgb
+    from paper_1506_03745_gb300.context import context as gpu_context
+    ana, volt = _two_sphere_analytical("paper_5_4_phi1")
+    prm = dict(PARAMS, K=3, K_near=args.near, n_edge=9, leaf_size=300, P=15, theta=0.5)
+    tol = 1e-9
+    levels = [int(v) for v in args.levels.split(",")]
+    rows = []
+    for level in levels:
+        vm, fm = synth.icosphere(level, 5.0)
+        vs, fs = synth.icosphere(level, 4.0)
+        mol = dict(kind="dielectric", verts=vm, tris=fm, eps_in=4.0, qxyz=np.zeros((1, 3)), q=np.array([1.0]), bc=0.0)
+        srf = dict(kind="phi", verts=vs + np.array([12.0, 0.0, 0.0]), tris=fs, eps_in=1.0, qxyz=np.zeros((0, 3)),
+                   q=np.zeros(0), bc=volt)
+        out = {"level": level, "panels_per_sphere": len(fm)}
+        F = {}
+        t_all = 0.0
+        for name, bodies in (("pair", [mol, srf]), ("molecule", [mol]), ("surface", [srf])):
+            ctx = gpu_context(bodies, **prm)
+            n = pgb.pgb_num_unknowns(ctx)
+            x = torch.empty(n, dtype=torch.float64, device="cuda")
+            (code, st), ms = _timed(lambda: pgb.pgb_solve(ctx, pgb.PGB_FP32_REFINE, tol, MAX_ITER, RESTART, x))
+            e = pgb.pgb_energy(ctx, x)
+            pgb.pgb_destroy(ctx)
+            F[name] = e
+            t_all += ms
+            out[name] = {"status": code, "iterations": st["iterations"], "rel_residual": st["rel_residual"],
+                         "solve_ms": ms, "solvation": e["solvation"], "surface": e["surface"]}
+        f_int = (F["pair"]["solvation"] + F["pair"]["surface"]) - F["molecule"]["solvation"] - F["surface"]["surface"]
+        out["F_int_kcal_mol"] = f_int
+        out["rel_error_vs_analytical"] = abs(f_int - ana[0]) / abs(ana[0])
+        out["solve_ms_total"] = t_all
+        rows.append(out)
+        print(json.dumps(out), file=sys.stderr, flush=True)
+    orders = {}
+    for k in range(len(rows) - 1):
+        e0, e1 = rows[k]["rel_error_vs_analytical"], rows[k + 1]["rel_error_vs_analytical"]
+        orders[f"levels_{rows[k]['level']}_{rows[k + 1]['level']}"] = math.log(e0 / e1) / math.log(4.0)
+    richardson = None
+    if len(rows) >= 3:
+        f1, f2, f3 = (r["F_int_kcal_mol"] for r in rows[-3:])
+        if (f1 - f2) * (f2 - f3) > 0:
+            richardson = math.log((f1 - f2) / (f2 - f3)) / math.log(4.0)
+    print(json.dumps({"workload": "paper grid-convergence case: spheres r=5 A (eps 4, central charge 1 e) and r=4 A "
+                                  "(phi0 = 1 internal unit), 12 A apart, kappa 0.125, eps 80",
+                      "params": {k: prm[k] for k in ("K", "K_near", "n_edge", "leaf_size", "P", "theta")},
+                      "tol": tol, "mode": "FP32 + refinement (double-single residual)",
+                      "F_int_analytical_kcal_mol": ana[0], "levels": rows,
+                      "observed_order_vs_analytical": orders,
+                      "observed_order_richardson_three_finest": richardson,
+                      "paper_observed_order": 1.007}), flush=True)
+
+
 def run_scaling(args):
     """The two-sphere configuration at icosphere levels 4..7 (2 x 5120 ... 2 x
     327680 panels): the step (tree + FP32/FP64-refined solve + energies) and
@@ -1079,7 +1160,9 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--mode", default="solve", choices=["solve", "matvec"])
     ap.add_argument("--workload", default="two_sphere", choices=["two_sphere", "star", "gradient", "poses", "poses_uneven", "brick",
-                                                            "scaling", "stern"])
+                                                            "scaling", "stern", "replica"])
+    ap.add_argument("--levels", default="3,4,5,6", help="icosphere levels of --workload replica")
+    ap.add_argument("--near", type=int, default=19, help="close-by rule points of --workload replica (19 or 37)")
     ap.add_argument("--poses", type=int, default=8, help="orientations for --workload poses")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp64_ds"])
     ap.add_argument("--gpus", type=int, default=1)
@@ -1119,6 +1202,8 @@ def main():
         run_scaling(args)
     elif args.workload == "stern":
         run_stern(args)
+    elif args.workload == "replica":
+        run_replica(args)
     elif args.workload == "poses":
         run_poses(args)
     elif args.workload == "poses_uneven":
