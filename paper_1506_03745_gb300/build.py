@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpgb.so")
 SOURCES = ["tree.cu", "matvec.cu", "treecode_f32.cu", "treecode_f64.cu", "solver.cu", "energy.cu", "adjoint.cu",
-           "treecode_ds.cu", "batch.cu", "farfield.cu", "shard.cu", "api.cu"]
+           "treecode_ds.cu", "treecode_ds_hi.cu", "batch.cu", "farfield.cu", "shard.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", "-Xcompiler", "-Wno-deprecated-declarations"]
 

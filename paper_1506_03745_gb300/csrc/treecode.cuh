@@ -19,6 +19,7 @@
 // Moment shift (upward pass): M_k(c') = sum_{j<=k} C(k,j) (c'-c)^{k-j} M_j(c).
 #pragma once
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "ds.cuh"
@@ -271,6 +272,25 @@ struct alignas(16) Vec16 {
 // g_0 = 1, g_1 = -(1 + x), g_p = x^2 g_{p-2} - (2p - 1) g_{p-1}.  The monomials
 // are formed in nested order, one product each, and summed per degree, so
 // that a term costs one product and one multiply-add per kernel.
+// Compile-time loop: f(std::integral_constant<int, I>) for I = B .. E-1, so
+// that array indices formed from I are constants whatever the trip count
+// (a plain unrolled loop nest is left partly rolled by the compiler at the
+// higher orders, which moves the per-degree sums to local memory).
+template <int B, int E, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+// index of S^(a,b,0) in the evaluation order of order P
+__host__ __device__ constexpr int eval_index(int P, int a, int b) {
+    int o = 0;
+    for (int q = 0; q < a; ++q) o += (P - q + 1) * (P - q + 2) / 2;
+    for (int q = 0; q < b; ++q) o += P - a - q + 1;
+    return o;
+}
+
 template <typename real, int P, bool LAP>
 __device__ __forceinline__ void far_eval(real Rx, real Ry, real Rz, real kappa, const real* __restrict__ cL,
                                          const real* __restrict__ cY, real& uL, real& uY) {
@@ -287,28 +307,57 @@ __device__ __forceinline__ void far_eval(real Rx, real Ry, real Rz, real kappa, 
     for (int p = 0; p <= P; ++p) acc[p] = real(0);
     real aL = real(0);
     V qy, ql;
-    int idx = 0;
     real xa = real(1);
+    if constexpr (is_ds<real> && P > 8) {
+        // double-single above order 8: loops the compiler unrolls as it sees
+        // fit (the full unroll of these long double-single bodies takes the
+        // compiler minutes); the FP64-class residual product runs a few times
+        // per solve
+        int idx = 0;
 #pragma unroll
-    for (int a = 0; a <= P; ++a) {
+        for (int a = 0; a <= P; ++a) {
+            real xy = xa;
+#pragma unroll
+            for (int b = 0; b <= P - a; ++b) {
+                real t = xy;
+#pragma unroll
+                for (int c = 0; c <= P - a - b; ++c) {
+                    if (idx % VN == 0) {
+                        qy = *reinterpret_cast<const V*>(cY + idx);
+                        if (LAP) ql = *reinterpret_cast<const V*>(cL + idx);
+                    }
+                    acc[a + b + c] = madd(qy.v[idx % VN], t, acc[a + b + c]);
+                    if (LAP) aL = madd(ql.v[idx % VN], t, aL);
+                    ++idx;
+                    if (c < P - a - b) t = t * sz;
+                }
+                if (b < P - a) xy = xy * sy;
+            }
+            if (a < P) xa = xa * sx;
+        }
+    } else {
+    static_for<0, P + 1>([&](auto A) {
+        constexpr int a = decltype(A)::value;
         real xy = xa;
-#pragma unroll
-        for (int b = 0; b <= P - a; ++b) {
+        static_for<0, P - a + 1>([&](auto Bc) {
+            constexpr int b = decltype(Bc)::value;
+            constexpr int i0 = eval_index(P, a, b);
             real t = xy;
-#pragma unroll
-            for (int c = 0; c <= P - a - b; ++c) {
-                if (idx % VN == 0) {
+            static_for<0, P - a - b + 1>([&](auto Cc) {
+                constexpr int c = decltype(Cc)::value;
+                constexpr int idx = i0 + c;
+                if constexpr (idx % VN == 0) {
                     qy = *reinterpret_cast<const V*>(cY + idx);
-                    if (LAP) ql = *reinterpret_cast<const V*>(cL + idx);
+                    if constexpr (LAP) ql = *reinterpret_cast<const V*>(cL + idx);
                 }
                 acc[a + b + c] = madd(qy.v[idx % VN], t, acc[a + b + c]);
-                if (LAP) aL = madd(ql.v[idx % VN], t, aL);
-                ++idx;
-                if (c < P - a - b) t = t * sz;
-            }
-            if (b < P - a) xy = xy * sy;
-        }
-        if (a < P) xa = xa * sx;
+                if constexpr (LAP) aL = madd(ql.v[idx % VN], t, aL);
+                if constexpr (c < P - a - b) t = t * sz;
+            });
+            if constexpr (b < P - a) xy = xy * sy;
+        });
+        if constexpr (a < P) xa = xa * sx;
+    });
     }
     const real r = r2 * ri;
     const real x = kappa * r;
