@@ -1162,7 +1162,7 @@ def main():
     ap.add_argument("--workload", default="two_sphere", choices=["two_sphere", "star", "gradient", "poses", "poses_uneven", "brick",
                                                             "scaling", "stern", "replica"])
     ap.add_argument("--levels", default="3,4,5,6", help="icosphere levels of --workload replica")
-    ap.add_argument("--near", type=int, default=19, help="close-by rule points of --workload replica (19 or 37)")
+    ap.add_argument("--near", type=int, default=37, help="close-by rule points of --workload replica (19 or 37)")
     ap.add_argument("--poses", type=int, default=8, help="orientations for --workload poses")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp64_ds"])
     ap.add_argument("--gpus", type=int, default=1)

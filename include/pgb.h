@@ -63,7 +63,7 @@ extern "C" {
  * the target group size of the interaction lists. */
 typedef struct pgb_params {
     int32_t K;            /* far-field points per panel: 1, 3, 4 or 7 (Section 3.1) */
-    int32_t K_near;       /* fine rule inside 2L: 19 (Section 3.1) */
+    int32_t K_near;       /* fine rule inside 2L: 19 or 37 (Section 3.1; Table 1 uses 37) */
     int32_t n_edge;       /* Gauss points per edge for the self panel: 3, 6, 9 or 12 */
     int32_t P;            /* Taylor order: 0..8, 10, 12 or 15 (Section 3.2; Tables 1
                              and 2 use 15); pgb_grad takes 0..8 */

@@ -5,7 +5,8 @@ The paper integrates far panels with 1, 3, 4 or 7 Gauss points, close panels
 collocation point semi-analytically with Gauss points along its edges.  It does
 not print the rules.  The oracle's reading: fully symmetric rules with the
 fewest orbits that reach the degrees 1 (K=1), 2 (K=3), 3 (K=4), 5 (K=7) and
-9 (K=19).  Each rule is *derived here* by solving its moment equations
+9 (K=19), and for the 37-point close-by rule of Table 1 the fully symmetric
+rule of degree 13 whose orbit count matches its moment conditions.  Each rule is *derived here* by solving its moment equations
 sum_m w_m x_m^i y_m^j = 2 i! j!/(i+j+2)!  (exact monomial integrals over the
 reference triangle, normalised to unit area) for the weights and orbit
 parameters, from a rough starting point, with Levenberg-Marquardt.
@@ -30,7 +31,17 @@ _RULES = {
     7: (5, [("c", (0.22,)), ("a", (0.13, 0.47)), ("a", (0.13, 0.10))]),
     19: (9, [("c", (0.097,)), ("a", (0.031, 0.49)), ("a", (0.078, 0.44)),
              ("a", (0.080, 0.19)), ("a", (0.026, 0.045)), ("b", (0.043, 0.037, 0.22))]),
+    # degree 13: the fully symmetric moment conditions up to degree 13 are
+    # 21 (the symmetric polynomials e2^a e3^b, 2a + 3b <= 13), met by the
+    # centroid, four 3-point and four 6-point orbits (21 unknowns, 37 points)
+    37: (13, [("c", (0.068,)), ("a", (0.058, 0.22)), ("a", (0.024, 0.49)), ("a", (0.0061, 0.022)),
+              ("a", (0.056, 0.43)), ("b", (0.015, 0.024, 0.86)), ("b", (0.0096, 0.27, 0.72)),
+              ("b", (0.035, 0.068, 0.62)), ("b", (0.024, 0.16, 0.75))]),
 }
+# rules whose moment equations are solved relative to the exact moments: the
+# degree-13 moments span many orders of magnitude, and unscaled equations leave
+# the orbit parameters undetermined beyond about 1e-6
+_RELATIVE = {37}
 
 
 def _expand(params, struct):
@@ -51,13 +62,15 @@ def _expand(params, struct):
     return np.array(lam), np.array(w)
 
 
-def _moment_residual(params, struct, deg):
+def _moment_residual(params, struct, deg, relative=False):
     lam, w = _expand(params, struct)
     x, y = lam[:, 0], lam[:, 1]
     res = []
     for i in range(deg + 1):
         for j in range(deg + 1 - i):
-            res.append(np.sum(w * x ** i * y ** j) - 2.0 * factorial(i) * factorial(j) / factorial(i + j + 2))
+            exact = 2.0 * factorial(i) * factorial(j) / factorial(i + j + 2)
+            r = np.sum(w * x ** i * y ** j) - exact
+            res.append(r / exact if relative else r)
     return np.array(res)
 
 
@@ -71,8 +84,8 @@ def triangle_rule(K: int):
     if K == 1:
         params = np.array([1.0])
     else:
-        sol = least_squares(_moment_residual, x0, args=(struct, deg), method="lm",
-                            xtol=1e-15, ftol=1e-15, gtol=1e-15, max_nfev=2000)
+        sol = least_squares(_moment_residual, x0, args=(struct, deg, K in _RELATIVE), method="lm",
+                            xtol=1e-15, ftol=1e-15, gtol=1e-15, max_nfev=20000)
         params = sol.x
     lam, w = _expand(params, struct)
     mu = lam - 1.0 / 3.0

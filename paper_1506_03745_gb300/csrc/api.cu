@@ -101,7 +101,7 @@ static int guard(pgb_ctx* c, F f) {
 
 static int check_params(const pgb_params* p, std::string& why) {
     if (!(p->K == 1 || p->K == 3 || p->K == 4 || p->K == 7)) why = "K must be 1, 3, 4 or 7";
-    else if (p->K_near != 19) why = "K_near must be 19";
+    else if (p->K_near != 19 && p->K_near != 37) why = "K_near must be 19 or 37";
     else if (!(p->n_edge == 3 || p->n_edge == 6 || p->n_edge == 9 || p->n_edge == 12)) why = "n_edge must be 3, 6, 9 or 12";
     else if (!p_supported(p->P)) why = "P must be in 0..8, or 10, 12 or 15";
     else if (!(p->theta >= 0 && p->theta < 1)) why = "theta must be in [0, 1)";

@@ -14,7 +14,7 @@ namespace pgb {
 struct Rules {
     int K, Kn, ne;
     double mu[7][3], w[7];
-    double mun[19][3], wn[19];
+    double mun[37][3], wn[37];  // close-by rule: 19 or 37 points
     double ex[12], ew[12];
 };
 

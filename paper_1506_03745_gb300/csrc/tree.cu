@@ -30,10 +30,16 @@ Rules make_rules(int K, int Kn, int ne) {
         for (int a = 0; a < 3; ++a) r.mu[i][a] = mu[i][a];
         r.w[i] = w[i];
     }
-    if (Kn != 19) fail(PGB_EINVAL, "K_near must be 19");
-    for (int i = 0; i < 19; ++i) {
-        for (int a = 0; a < 3; ++a) r.mun[i][a] = PGB_TRI19_MU[i][a];
-        r.wn[i] = PGB_TRI19_W[i];
+    const double(*mun)[3] = nullptr;
+    const double* wn = nullptr;
+    switch (Kn) {
+        case 19: mun = PGB_TRI19_MU; wn = PGB_TRI19_W; break;
+        case 37: mun = PGB_TRI37_MU; wn = PGB_TRI37_W; break;
+        default: fail(PGB_EINVAL, "K_near must be 19 or 37");
+    }
+    for (int i = 0; i < Kn; ++i) {
+        for (int a = 0; a < 3; ++a) r.mun[i][a] = mun[i][a];
+        r.wn[i] = wn[i];
     }
     const double *ex = nullptr, *ew = nullptr;
     switch (ne) {
@@ -1336,7 +1342,7 @@ __global__ void k_corr_compact(int64_t n, const int64_t* off, const int32_t* tmp
     for (int64_t k = b; k < e; ++k) cj[k] = tmp[i * cap + (k - b)];
 }
 
-// Fine-rule (19-point) nodes of every panel, mapped like the K-point nodes.
+// Fine-rule (19- or 37-point) nodes of every panel, mapped like the K-point nodes.
 __global__ void k_fine_nodes(int64_t n, const double* V, const double* C, Rules r, double* YF) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n * r.Kn) return;
@@ -1400,7 +1406,7 @@ __device__ __forceinline__ int64_t owner_row(const int64_t* off, int64_t n, int6
     return lo;
 }
 
-// Correction entries (i, j), j != i: 19-point rule minus the K-point sum,
+// Correction entries (i, j), j != i: fine rule minus the K-point sum,
 // for V_L, K_L, V_Y, K_Y (Section 3.1), one thread per entry, in
 // double-single arithmetic from the nodes split once per build (YF, Y); the
 // Laplace pair only where it enters a row (same dielectric body).  The

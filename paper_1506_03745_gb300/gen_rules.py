@@ -2,9 +2,10 @@
 write them to csrc/pgb_rules.h.
 
 Section 3.1 of the paper integrates far panels with 1, 3, 4 or 7 Gauss
-points, panels closer than 2L with 19 points and the self panel with Gauss
-points along its edges, without printing the rules.  This library uses the
-fully symmetric rules of degree 1, 2, 3, 5 and 9 with the fewest orbits.
+points, panels closer than 2L with 19 points (37 in Table 1) and the self
+panel with Gauss points along its edges, without printing the rules.  This
+library uses the fully symmetric rules of degree 1, 2, 3, 5, 9 and 13 with the
+fewest orbits.
 Each is found here by Newton's method on its moment equations (the exact
 integrals of x^i y^j over the unit right triangle, normalised to unit area),
 starting from a rough guess; the edge rule is Gauss-Legendre on [0, 1],
@@ -27,7 +28,15 @@ SPECS = {
     7: (5, [("c", [0.2]), ("a", [0.12, 0.46]), ("a", [0.14, 0.11])]),
     19: (9, [("c", [0.1]), ("a", [0.03, 0.49]), ("a", [0.08, 0.44]),
              ("a", [0.08, 0.19]), ("a", [0.025, 0.045]), ("b", [0.045, 0.035, 0.22])]),
+    # degree 13 with 21 parameters: the count of fully symmetric moment
+    # conditions of degree <= 13 (one per e2^a e3^b with 2a + 3b <= 13)
+    37: (13, [("c", [0.07]), ("a", [0.06, 0.22]), ("a", [0.024, 0.49]), ("a", [0.006, 0.022]),
+              ("a", [0.055, 0.43]), ("b", [0.015, 0.024, 0.86]), ("b", [0.0096, 0.27, 0.72]),
+              ("b", [0.035, 0.07, 0.62]), ("b", [0.024, 0.16, 0.75])]),
 }
+# rules solved for relative moment errors (each equation divided by its exact
+# moment): the degree-13 moments span many orders of magnitude
+RELATIVE = {37}
 EDGE_POINTS = (3, 6, 9, 12)
 
 
@@ -55,26 +64,27 @@ def points(params, orbits):
     return np.array(bary), np.array(wts)
 
 
-def residual(params, orbits, degree):
+def residual(params, orbits, degree, relative=False):
     bary, w = points(params, orbits)
     out = []
     for i in range(degree + 1):
         for j in range(degree + 1 - i):
             exact = 2.0 * math.factorial(i) * math.factorial(j) / math.factorial(i + j + 2)
-            out.append(np.dot(w, bary[:, 0] ** i * bary[:, 1] ** j) - exact)
+            r = np.dot(w, bary[:, 0] ** i * bary[:, 1] ** j) - exact
+            out.append(r / exact if relative else r)
     return np.array(out)
 
 
-def newton(orbits, degree, x0, iters=60):
+def newton(orbits, degree, x0, iters=60, relative=False):
     """Gauss-Newton with a complex-step Jacobian (exact to rounding)."""
     x = np.array(x0, dtype=np.float64)
     for _ in range(iters):
-        f = residual(x, orbits, degree).real
+        f = residual(x, orbits, degree, relative).real
         J = np.empty((len(f), len(x)))
         for k in range(len(x)):
             e = np.zeros(len(x), dtype=np.complex128)
             e[k] = 1e-30j
-            J[:, k] = residual(x + e, orbits, degree).imag / 1e-30
+            J[:, k] = residual(x + e, orbits, degree, relative).imag / 1e-30
         step = np.linalg.lstsq(J, -f, rcond=None)[0]
         x = x + step
         if np.max(np.abs(step)) < 1e-17:
@@ -87,7 +97,8 @@ def newton(orbits, degree, x0, iters=60):
 def triangle_rule(K):
     degree, orbits = SPECS[K]
     x0 = [v for _, vals in orbits for v in vals]
-    x = np.array([1.0]) if K == 1 else newton(orbits, degree, x0)
+    x = np.array([1.0]) if K == 1 else newton(orbits, degree, x0, iters=200 if K in RELATIVE else 60,
+                                              relative=K in RELATIVE)
     bary, w = points(x, orbits)
     return np.real(bary) - 1.0 / 3.0, np.real(w)
 

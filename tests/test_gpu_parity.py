@@ -376,3 +376,28 @@ def test_orders_without_kernels_are_rejected():
             pgb.pgb_grad(ctx, x, 0, 0, pgb.PGB_FP64, 1e-8, 100, 50)
     finally:
         pgb.pgb_destroy(ctx)
+
+
+@pytest.mark.parametrize("case", ["sigma_pair", "phi_pair"])
+def test_direct_sum_with_37_point_close_by_rule(case):
+    """Table 1's close-by rule (37 points, degree 13) in the near-field
+    corrections: the direct-sum product matches the oracle's with the same
+    rule (each side derives the rule on its own from the moment equations),
+    and differs from the 19-point product by the quadrature error."""
+    bodies = spheres(**CASES[case])
+    so = oracle_system(bodies, theta=0.0, K_near=37)
+    ctx = gpu_context(bodies, theta=0.0, leaf_size=16, K_near=37)
+    c19 = gpu_context(bodies, theta=0.0, leaf_size=16)
+    try:
+        x = np.random.default_rng(4).normal(size=so.n)
+        ref = so.apply(x)
+        scale = np.abs(ref).max()
+        y64 = _matvec(ctx, x, pgb.PGB_FP64)
+        assert np.abs(y64 - ref).max() / scale < 1e-11
+        y32 = _matvec(ctx, x, pgb.PGB_FP32)
+        assert np.abs(y32 - ref).max() / scale < 2e-6
+        d = np.abs(_matvec(c19, x, pgb.PGB_FP64) - y64).max() / scale
+        assert 1e-12 < d < 1e-3
+    finally:
+        pgb.pgb_destroy(ctx)
+        pgb.pgb_destroy(c19)

@@ -1,5 +1,5 @@
-"""The paper's grid-convergence case (Section 5.1, Table 1 parameters but the
-close-by rule: far rule 3 points, 9 Gauss points per edge in-element,
+"""The paper's grid-convergence case (Section 5.1, Table 1 parameters: far
+rule 3 points, close-by rule 37 points, 9 Gauss points per edge in-element,
 N_crit 300, P 15, theta 0.5, GMRES tol 1e-9): spheres r = 5 A (eps 4, central
 unit charge) and r = 4 A held at phi0 = 1 internal unit, 12 A apart, kappa
 0.125, eps 80.  The interaction energy of Eq. 17 approaches the analytical
@@ -41,7 +41,7 @@ def _f_int(level, volt):
     mol = dict(kind="dielectric", verts=vm, tris=fm, eps_in=4.0, qxyz=np.zeros((1, 3)), q=np.array([1.0]), bc=0.0)
     srf = dict(kind="phi", verts=vs + np.array([12.0, 0.0, 0.0]), tris=fs, eps_in=1.0, qxyz=np.zeros((0, 3)),
                q=np.zeros(0), bc=volt)
-    prm = dict(K=3, n_edge=9, leaf_size=300, P=15, theta=0.5)
+    prm = dict(K=3, K_near=37, n_edge=9, leaf_size=300, P=15, theta=0.5)
     e = {}
     for name, bodies in (("pair", [mol, srf]), ("molecule", [mol]), ("surface", [srf])):
         ctx = gpu_context(bodies, **prm)
