@@ -372,6 +372,39 @@ def reduce_across_ranks(dist, total_ms, matvecs, device):
 
 
 # ------------------------------------------------------------------ GPU arm
+def rank_chunks(n_poses, batch, rank, world):
+    """Contiguous pose range [lo, hi) of `rank`: whole chunks of `batch` poses
+    (the unions the sweep solves), as even as the chunk count allows."""
+    chunks = (n_poses + batch - 1) // batch
+    c0 = chunks * rank // world
+    c1 = chunks * (rank + 1) // world
+    return min(n_poses, c0 * batch), min(n_poses, c1 * batch)
+
+
+def gather_rows(dist, F, lo, hi, n, width, device):
+    """Rows [lo, hi) of the (n, k) array F from every rank (at most `width`
+    rows each), assembled in order (rank 0 receives; others return None).
+    Result collection after the timed region: no exchange inside a solve."""
+    import torch
+    world = dist.get_world_size()
+    k = F.shape[1]
+    width = max(width, 1)
+    buf = torch.zeros((width, k), dtype=torch.float64, device=device)
+    buf[:hi - lo] = torch.as_tensor(F[lo:hi], dtype=torch.float64, device=device)
+    meta = torch.tensor([lo, hi], dtype=torch.int64, device=device)
+    bufs = [torch.zeros_like(buf) for _ in range(world)]
+    metas = [torch.zeros_like(meta) for _ in range(world)]
+    dist.all_gather(bufs, buf)
+    dist.all_gather(metas, meta)
+    if dist.get_rank() != 0:
+        return None
+    out = np.zeros((n, k))
+    for b, m in zip(bufs, metas):
+        a, c = int(m[0]), int(m[1])
+        out[a:c] = b[:c - a].cpu().numpy()
+    return out
+
+
 def run_gpu(args):
     import torch
     import paper_1506_03745_gb300 as pgb
@@ -813,11 +846,24 @@ def run_poses_uneven(args):
     beside it the same poses molecule by molecule through pgb_solve_batch
     with 4 lanes.  The batched FP64 solve (tol 1e-9) is timed beside the
     batched FP32 + refinement solve on the leading 8 chunks: speedup and
-    per-pose energy error."""
+    per-pose energy error.  Under torchrun the poses are split across the
+    ranks in contiguous runs of whole chunks (independent problems: no
+    exchange inside a solve); rank 0 tunes the parameters for all, the time
+    is the slowest rank's, and the energies are gathered after the timed
+    region."""
     import torch
     import synth
     import paper_1506_03745_gb300 as pgb
     from paper_1506_03745_gb300.context import context as gpu_context
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
     batch = PARAMS["batch"] if PARAMS["batch"] > 1 else 8
     sizes = np.geomspace(5000, 40000, 8)
     srf = sphere_body()
@@ -837,7 +883,7 @@ def run_poses_uneven(args):
     # is within 1e-5 of the most accurate candidate's (theta 0.5, P 7)
     prm = dict(PARAMS)
     tune = None
-    if not args.no_autotune:
+    if not args.no_autotune and rank == 0:
         m0 = dict(mols[0], R=np.eye(3), t=np.array([place_for_gap(verts[0], np.eye(3), 40.0, 8.0), 0.0, 0.0]))
         ct = gpu_context([m0, srf], **PARAMS)
         thetas, Ps, leaves = [0.5, 0.6, 0.7], [5, 6, 7], [32, 64]
@@ -852,6 +898,10 @@ def run_poses_uneven(args):
                                for i, (t_, p_, l_) in enumerate((t_, p_, l_) for t_ in thetas for p_ in Ps
                                                                  for l_ in leaves)],
                 "ms": t_ms}
+    if dist is not None:  # every rank solves with rank 0's parameters
+        box = [prm]
+        dist.broadcast_object_list(box, src=0)
+        prm = box[0]
     ctxs = [gpu_context([mols[k], srf], **dict(prm, batch=batch if k == 0 else 1)) for k in range(8)]
     Rs = synth.random_rotations(17, args.poses)
     R, t, pc = [], [], []
@@ -865,14 +915,47 @@ def run_poses_uneven(args):
     B = len(R)
     tol = 1e-5
     mode = pgb.PGB_FP32_REFINE
+    lo, hi = rank_chunks(B, batch, rank, world)
     pgb.pgb_solve_poses(ctxs, pc[:batch], 0, R[:batch], t[:batch], mode, tol, MAX_ITER, RESTART)  # warm-up
     pgb.pgb_timing(ctxs[0], True, read=True)
-    (code, F, st), ms = _timed(lambda: pgb.pgb_solve_poses(ctxs, pc, 0, R, t, mode, tol, MAX_ITER, RESTART))
+    if dist is not None:
+        torch.cuda.synchronize(dev)
+        dist.barrier()
+    code, F, st, ms = 0, np.zeros((0, 4)), [], 0.0
+    if hi > lo:
+        (code, F, st), ms = _timed(lambda: pgb.pgb_solve_poses(ctxs, pc[lo:hi], 0, R[lo:hi], t[lo:hi], mode, tol,
+                                                               MAX_ITER, RESTART))
     tim = pgb.pgb_timing(ctxs[0], False, read=True)
+    n_local = hi - lo
+    if dist is not None:
+        torch.cuda.synchronize(dev)
+        dist.barrier()
+        tm = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        ms = float(tm.item())
+        chunks = (B + batch - 1) // batch
+        width = ((chunks + world - 1) // world) * batch
+        Fl = np.zeros((B, 4))
+        Fl[lo:hi] = F
+        its_l = np.zeros((B, 2))
+        its_l[lo:hi, 0] = [s_["iterations"] for s_ in st]
+        its_l[lo:hi, 1] = [s_["rel_residual"] for s_ in st]
+        cd = torch.tensor([abs(code)], dtype=torch.float64, device=dev)
+        dist.all_reduce(cd, op=dist.ReduceOp.MAX)
+        Fg = gather_rows(dist, Fl, lo, hi, B, width, dev)
+        Ig = gather_rows(dist, its_l, lo, hi, B, width, dev)
+        if rank != 0:
+            for c in ctxs:
+                pgb.pgb_destroy(c)
+            dist.destroy_process_group()
+            return
+        F = Fg
+        st = [{"iterations": int(v[0]), "rel_residual": float(v[1])} for v in Ig]
+        code = -int(cd.item()) if cd.item() else 0
     # the same poses molecule by molecule with concurrent lanes (molecule 0
     # needs a context of its own without the batch parameter)
     lanes = None
-    if not args.no_lanes:
+    if not args.no_lanes and world == 1:
         c0 = gpu_context([mols[0], srf], **dict(prm, batch=1))
         F_l = np.zeros_like(F)
         ms_l = 0.0
@@ -902,21 +985,26 @@ def run_poses_uneven(args):
     its = np.array([s["iterations"] for s in st])
     print(json.dumps({"workload": f"8 molecules ({min(npan)}-{max(npan)} panels, 900 charges each) x {args.poses} "
                                   f"orientations x 4 gaps near a sphere r=40 A (30420 panels)",
-                      "poses": B, "batch": batch, "ms": ms, "poses_per_s": B / (ms / 1e3),
+                      "poses": B, "batch": batch, "n_gpus": world,
+                      "split": "contiguous whole chunks per rank, slowest rank's time" if world > 1 else None,
+                      "ms": ms, "poses_per_s": B / (ms / 1e3),
                       "lanes_4_per_molecule": lanes, "mode": "FP32 + refinement (double-single residual)",
                       "max_rel_residual": float(max(s_["rel_residual"] for s_ in st)),
                       "molecule_panels": npan, "mean_iterations": float(its.mean()), "autotune": tune,
                       "iterations_range": [int(its.min()), int(its.max())], "status": code,
                       "batched_vs_fp64": vs64,
-                      "stage_ms_per_pose": {k: v[0] / B for k, v in tim.items() if k not in ("kernel_launches", "host_launches") and v[0]},
-                      "kernel_launches_per_pose": tim["kernel_launches"] / B,
-                      "host_launch_calls_per_pose": tim["host_launches"] / B,
+                      # rank 0's own poses
+                      "stage_ms_per_pose": {k: v[0] / max(n_local, 1) for k, v in tim.items() if k not in ("kernel_launches", "host_launches") and v[0]},
+                      "kernel_launches_per_pose": tim["kernel_launches"] / max(n_local, 1),
+                      "host_launch_calls_per_pose": tim["host_launches"] / max(n_local, 1),
                       # per molecule, per gap: Boltzmann weights over the orientations (poses are
                       # ordered orientation, gap, molecule)
                       "orientation_landscape": {f"molecule_{k}": orientation_landscape(F[k::8, 3], args.poses, 4)
                                                 for k in range(8)}}), flush=True)
     for c in ctxs:
         pgb.pgb_destroy(c)
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 def _two_sphere_analytical(case):
