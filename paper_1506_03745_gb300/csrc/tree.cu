@@ -338,39 +338,51 @@ __device__ int64_t lower_oct(const uint32_t* key, int64_t s, int64_t e, int chil
     return s;
 }
 
+// One warp per node: lane o <= 8 finds the first panel of octant o (lane 8:
+// the node's end), so the octants' bounds are the differences of neighbour
+// lanes; the nonempty ones are counted (k_split_count) or written in octant
+// order (k_split_write).  blockDim a multiple of 32.
+__device__ __forceinline__ unsigned split_bounds(const int32_t* start, const int32_t* end, int64_t i, int level,
+                                                 int leaf_size, bool always, const uint32_t* key, int64_t& lo,
+                                                 int64_t& hi) {
+    const int lane = threadIdx.x & 31;
+    const int64_t s = start[i], e = end[i];
+    const bool split = always || (e - s > leaf_size && level < 10);
+    int64_t b = 0;
+    if (split && lane <= 8) b = lane == 8 ? e : lower_oct(key, s, e, level + 1, lane);
+    const int64_t nb = __shfl_down_sync(0xffffffffu, b, 1);
+    lo = b;
+    hi = nb;
+    return __ballot_sync(0xffffffffu, split && lane < 8 && nb > b);
+}
+
 __global__ void k_split_count(const int32_t* start, const int32_t* end, int64_t n, int level, int leaf_size,
                               const uint32_t* key, int64_t* nchild) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int64_t s = start[i], e = end[i];
-    int64_t cnt = 0;
-    if (e - s > leaf_size && level < 10) {
-        for (int o = 0; o < 8; ++o) {
-            int64_t a = lower_oct(key, s, e, level + 1, o), b = lower_oct(key, s, e, level + 1, o + 1);
-            cnt += (b > a);
-        }
-    }
-    nchild[i] = cnt;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;  // warp-uniform
+    int64_t lo, hi;
+    const unsigned ne = split_bounds(start, end, i, level, leaf_size, false, key, lo, hi);
+    if ((threadIdx.x & 31) == 0) nchild[i] = __popc(ne);
 }
 
 __global__ void k_split_write(const int32_t* start, const int32_t* end, const int32_t* body, int64_t n, int level,
                               const uint32_t* key, const int64_t* nchild, const int64_t* coff, int64_t child_base,
                               int32_t* first_child, int32_t* nch, int32_t* cstart, int32_t* cend, int32_t* cbody) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    nch[i] = (int32_t)nchild[i];
-    first_child[i] = nchild[i] ? (int32_t)(child_base + coff[i]) : -1;
-    if (!nchild[i]) return;
-    int64_t s = start[i], e = end[i];
-    int64_t k = coff[i];
-    for (int o = 0; o < 8; ++o) {
-        int64_t a = lower_oct(key, s, e, level + 1, o), b = lower_oct(key, s, e, level + 1, o + 1);
-        if (b > a) {
-            cstart[k] = (int32_t)a;
-            cend[k] = (int32_t)b;
-            cbody[k] = body[i];
-            ++k;
-        }
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;  // warp-uniform
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) {
+        nch[i] = (int32_t)nchild[i];
+        first_child[i] = nchild[i] ? (int32_t)(child_base + coff[i]) : -1;
+    }
+    if (!nchild[i]) return;  // warp-uniform
+    int64_t lo, hi;
+    const unsigned ne = split_bounds(start, end, i, level, 0, true, key, lo, hi);
+    if ((ne >> lane) & 1u) {
+        const int64_t k = coff[i] + __popc(ne & ((1u << lane) - 1u));
+        cstart[k] = (int32_t)lo;
+        cend[k] = (int32_t)hi;
+        cbody[k] = body[i];
     }
 }
 
@@ -500,14 +512,14 @@ void build_order(pgb_ctx* c) {
         int64_t m = lv_n[level];
         nchild.resize(m);
         coff.resize(m);
-        k_split_count<<<nblk(m, 128), 128, 0, s>>>(*lv_start[level], *lv_end[level], m, level, c->p.leaf_size,
-                                                   c->d_key, nchild);
+        k_split_count<<<nblk(32 * m, 128), 128, 0, s>>>(*lv_start[level], *lv_end[level], m, level,
+                                                        c->p.leaf_size, c->d_key, nchild);
         PGB_CUDA(cudaGetLastError());
         int64_t total = 0;
         exclusive_scan_i64(nchild, coff, m, s, &total);
         alloc(std::max<int64_t>(total, 1));
         lv_n.back() = total;
-        k_split_write<<<nblk(m, 128), 128, 0, s>>>(*lv_start[level], *lv_end[level], *lv_body[level], m, level,
+        k_split_write<<<nblk(32 * m, 128), 128, 0, s>>>(*lv_start[level], *lv_end[level], *lv_body[level], m, level,
                                                    c->d_key, nchild, coff, base, *lv_fc[level], *lv_nch[level],
                                                    *lv_start[level + 1], *lv_end[level + 1], *lv_body[level + 1]);
         PGB_CUDA(cudaGetLastError());
