@@ -94,35 +94,53 @@ __device__ __forceinline__ ds ds_rsqrt(ds x) {
     return two_sum(y, __fmul_rn(__fmul_rn(0.5f, y), e.hi));
 }
 
-// 2^t for t < 127 (results below 2^-126 are returned as 0): t = n + f with
-// n = rint(t.hi) and f = t - n, |f| <= 1/2 (t.hi - n is exact); 2^f from its
-// Taylor series sum_k (ln 2)^k f^k / k!: the terms k = 7..12 in FP32 (they
-// are below 1.3e-7 in all, so FP32 leaves them an error below 1e-14), k = 0..6
-// by Horner steps in double-single; the truncation after k = 12 is below
-// 0.347^13 / 13! < 2e-16.  Then 2^n is applied to both parts (exact).
+// 2^t for t < 127 (results below 2^-126 are returned as 0), table-driven
+// (Tang's reduction, ACM TOMS 15, 1989): t = m / 64 + f with m = rint(64 t.hi)
+// and |f| <= 1/128 (t.hi - m/64 is exact), so 2^t = 2^(m >> 6) 2^(j/64) 2^f
+// with j = m & 63.  2^(j/64) comes from a 64-entry double-single table
+// computed at compile time from the exponential series; 2^f from its Taylor
+// series sum_k (ln 2)^k f^k / k!: the terms k = 3..5 in FP32 (they are below
+// 2.7e-8 in all, so FP32 leaves them an error below 2e-15), k = 0..2 by
+// Horner steps in double-single; the truncation after k = 5 is below
+// 0.0055^6 / 720 < 4e-17.  Then 2^(m >> 6) is applied to both parts (exact).
 template <int K>
 struct DsCoef {
     static constexpr ds v = ds_const(Exp2Coef<K>::v);
 };
+// e^x by its series, for the compile-time table (|x| < 1: 30 terms reach
+// double rounding)
+__host__ __device__ constexpr double exp_series(double x) {
+    double s = 1.0, t = 1.0;
+    for (int k = 1; k < 30; ++k) {
+        t = t * x / k;
+        s += t;
+    }
+    return s;
+}
+struct Exp2Table {
+    ds v[64];
+    __host__ __device__ constexpr Exp2Table() : v() {
+        for (int j = 0; j < 64; ++j) v[j] = ds_const(exp_series(j * PGB_LN2 / 64.0));
+    }
+};
+__device__ const Exp2Table kExp2Table = Exp2Table();
+
 __device__ __forceinline__ ds ds_exp2(ds t) {
-    const float n = rintf(t.hi);
-    const ds f = two_sum(__fsub_rn(t.hi, n), t.lo);
-    // tail k = 7..12 in FP32 (Horner), as the coefficient of f^7
-    float q = (float)Exp2Coef<12>::v;
-    q = __fmaf_rn(q, f.hi, (float)Exp2Coef<11>::v);
-    q = __fmaf_rn(q, f.hi, (float)Exp2Coef<10>::v);
-    q = __fmaf_rn(q, f.hi, (float)Exp2Coef<9>::v);
-    q = __fmaf_rn(q, f.hi, (float)Exp2Coef<8>::v);
-    q = __fmaf_rn(q, f.hi, (float)Exp2Coef<7>::v);
-    ds p = DsCoef<6>::v + mul_f(f, q);
-    p = ds_fma(p, f, DsCoef<5>::v);
-    p = ds_fma(p, f, DsCoef<4>::v);
-    p = ds_fma(p, f, DsCoef<3>::v);
-    p = ds_fma(p, f, DsCoef<2>::v);
+    const float mf = rintf(__fmul_rn(t.hi, 64.f));
+    const int m = (int)mf;
+    const ds f = two_sum(__fsub_rn(t.hi, __fmul_rn(mf, 0.015625f)), t.lo);
+    // tail k = 3..5 in FP32 (Horner), as the coefficient of f^3
+    float q = (float)Exp2Coef<5>::v;
+    q = __fmaf_rn(q, f.hi, (float)Exp2Coef<4>::v);
+    q = __fmaf_rn(q, f.hi, (float)Exp2Coef<3>::v);
+    ds p = DsCoef<2>::v + mul_f(f, q);
     p = ds_fma(p, f, DsCoef<1>::v);
     p = ds_fma(p, f, ds(1));
-    if (n < -126.f) return ds(0);
-    const float sc = __int_as_float((127 + (int)n) << 23);
+    const float2 tv = __ldg(reinterpret_cast<const float2*>(&kExp2Table.v[m & 63]));
+    p = p * ds(tv.x, tv.y);
+    const int n = m >> 6;  // floor(m / 64)
+    if (n < -126) return ds(0);
+    const float sc = __int_as_float((127 + n) << 23);
     return ds(__fmul_rn(p.hi, sc), __fmul_rn(p.lo, sc));
 }
 
