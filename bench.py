@@ -141,22 +141,31 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ profile
+def kernel_source_hash():
+    """First 16 hex digits of the SHA-256 of the treecode kernels' sources
+    (treecode.cuh, then ds.cuh): the key under which a committed ncu summary
+    records the source it was taken on."""
+    h = hashlib.sha256()
+    for f in ("treecode.cuh", "ds.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1506_03745_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def recorded_traffic(kernel):
     """dram bytes per launch of `kernel` from the committed ncu summary
     (profiles/<kernel>_two_sphere.txt), if it was taken on the current kernel
     source."""
     name = kernel.split("<")[0]
     path = os.path.join(ROOT, "profiles", f"{name}_fp32_two_sphere.txt")
-    src = os.path.join(ROOT, "paper_1506_03745_gb300", "csrc", "treecode.cuh")
     if not os.path.exists(path):
         return None
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = kernel_source_hash()
     kv = {}
     for line in open(path):
         if "=" in line and not line.startswith("#"):
             k, v = line.split("=", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("treecode_cuh_sha256_16") != h or "dram_bytes_per_launch_full" not in kv:
+    if kv.get("kernel_sources_sha256_16") != h or "dram_bytes_per_launch_full" not in kv:
         return None
     return float(kv["dram_bytes_per_launch_full"])
 
@@ -165,16 +174,15 @@ def recorded_counters(fname):
     """key = value lines of a committed ncu summary (profiles/fname) when its
     recorded source hash matches the current kernels (else empty)."""
     path = os.path.join(ROOT, "profiles", fname)
-    src = os.path.join(ROOT, "paper_1506_03745_gb300", "csrc", "treecode.cuh")
     if not os.path.exists(path):
         return {}
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = kernel_source_hash()
     kv = {}
     for line in open(path):
         if "=" in line and not line.startswith("#"):
             k, v = line.split("=", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("treecode_cuh_sha256_16") != h:
+    if kv.get("kernel_sources_sha256_16") != h:
         return {}
     out = {}
     for k, v in kv.items():
