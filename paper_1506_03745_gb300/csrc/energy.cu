@@ -68,6 +68,29 @@ __device__ __forceinline__ double phi_panel(const Geo& g, const BodyDev& bd, con
 // body enclosing it (a cavity's panels bound the molecule's interior): its
 // second pair of weights takes that body's charges.  One warp per panel,
 // lanes over the charges.  w[j] = {wV own, wK own, wV enclosing, wK enclosing}.
+// The same weights with one thread per panel over all its charges in order,
+// for bodies of fewer than 32 charges (a warp per panel would leave most
+// lanes idle, and the FP64 pipe takes whole warps).
+__global__ void k_charge_weights_1t(Geo g, BodyDev bd, Rules r, const double* qxyz, const double* qv,
+                                    const int64_t* qoff, dbl4* w) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= g.n_pan) return;
+    const int b = g.pbody[j];
+    double sv[2] = {0, 0}, sk[2] = {0, 0};
+    for (int side = 0; side < 2; ++side) {
+        const int src = side == 0 ? (bd.kind[b] == PGB_DIELECTRIC ? b : -1) : bd.parent[b];
+        if (src < 0) continue;
+        for (int64_t k = qoff[src]; k < qoff[src + 1]; ++k) {
+            const double xq[3] = {qxyz[3 * k], qxyz[3 * k + 1], qxyz[3 * k + 2]};
+            double vl, kl;
+            panel_vk(g, r, xq, j, vl, kl);
+            sv[side] += qv[k] * vl;
+            sk[side] += qv[k] * kl;
+        }
+    }
+    w[j] = dbl4{sv[0], sk[0], sv[1], sk[1]};
+}
+
 __global__ void k_charge_weights(Geo g, BodyDev bd, Rules r, const double* qxyz, const double* qv,
                                  const int64_t* qoff, dbl4* w) {
     const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -192,6 +215,49 @@ __global__ void k_body_sums(Geo g, BodyDev bd, const double* qxyz, const double*
     }
 }
 
+// k_body_sums over BODY_PARTS blocks per body (blockIdx.y = body, blockIdx.x
+// = part, panels strided over the parts), partial sums part[(b * BODY_PARTS +
+// x) * 3 + {0, 1, 2}] reduced in part order by k_body_sums_final; the
+// charge-weight path only (energies()).
+#define BODY_PARTS 64
+__global__ void k_body_sums_part(Geo g, BodyDev bd, const dbl4* w, const double* x, double* part) {
+    __shared__ double sh[32];
+    const int b = blockIdx.y;
+    double s0 = 0, s1 = 0, s2 = 0;
+    const int64_t p0 = bd.pan_off[b], p1 = bd.pan_off[b + 1], N = p1 - p0, o = bd.unk_off[b];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t first = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (w && bd.kind[b] == PGB_DIELECTRIC) {
+        const int pb = bd.parent[b];
+        const double f = pb >= 0 ? bd.eps_ratio[b] / bd.eps_ratio[pb] : 0.0;
+        for (int64_t j = first; j < p1; j += stride) {
+            const int64_t loc = g.perm[j] - p0;
+            const double phi = x[o + loc], dphi = x[o + N + loc];
+            s0 += w[j].x * dphi - w[j].y * phi;
+            if (pb >= 0) s1 -= w[j].z * f * dphi - w[j].w * phi;
+        }
+    }
+    if (bd.kind[b] != PGB_DIELECTRIC)
+        for (int64_t j = first; j < p1; j += stride) s2 += x[o + (g.perm[j] - p0)] * g.A[j];
+    s0 = block_sum(s0, sh);
+    s1 = block_sum(s1, sh);
+    s2 = block_sum(s2, sh);
+    if (threadIdx.x == 0) {
+        double* q = part + 3 * ((int64_t)b * gridDim.x + blockIdx.x);
+        q[0] = s0;
+        q[1] = s1;
+        q[2] = s2;
+    }
+}
+__global__ void k_body_sums_final(const double* part, int nparts, double* out) {
+    if (threadIdx.x >= 3) return;
+    const int b = blockIdx.x;
+    double t = 0;
+    for (int k = 0; k < nparts; ++k) t += part[3 * ((int64_t)b * nparts + k) + threadIdx.x];
+    // the charge-weight sums carry the 1/4pi of phi_reac (Eq. 13)
+    out[3 * b + threadIdx.x] = threadIdx.x < 2 ? t * (1.0 / PGB_FOUR_PI) : t;
+}
+
 // Coulomb sum_{l>k} q_k q_l / r_kl of each body: one block per charge k,
 // partial sums pair[k], then a per-body reduction.
 __global__ void k_coulomb_pairs(const double* qxyz, const double* qv, const int32_t* qbody, const int64_t* qoff,
@@ -241,15 +307,27 @@ void energies(pgb_ctx* c, const double* x, pgb_energies* e, pgb_energies* per_bo
         const uint64_t key[4] = {c->tree_gen, c->config_gen, (uint64_t)c->p.K, (uint64_t)c->p.K_near};
         if (memcmp(key, c->qw_key, sizeof(key))) {
             c->d_qw.resize(c->n_pan);
-            k_charge_weights<<<(unsigned)((c->n_pan * 32 + 127) / 128), 128, 0, s>>>(
-                geo(c), body_dev(c), r, c->d_qxyz, c->d_qval, qoff, c->d_qw);
+            int64_t qmax = 0;
+            for (const auto& bo : c->bodies) qmax = std::max<int64_t>(qmax, bo.nq);
+            if (qmax < 32)
+                k_charge_weights_1t<<<(unsigned)((c->n_pan + 127) / 128), 128, 0, s>>>(
+                    geo(c), body_dev(c), r, c->d_qxyz, c->d_qval, qoff, c->d_qw);
+            else
+                k_charge_weights<<<(unsigned)((c->n_pan * 32 + 127) / 128), 128, 0, s>>>(
+                    geo(c), body_dev(c), r, c->d_qxyz, c->d_qval, qoff, c->d_qw);
             PGB_CUDA(cudaGetLastError());
             PGB_LAUNCHED(c, 1);
             memcpy(c->qw_key, key, sizeof(key));
         }
     }
-    k_body_sums<<<nb, 128, 0, s>>>(geo(c), body_dev(c), c->d_qxyz, c->d_qval, qoff, nullptr,
-                                   c->n_q ? c->d_qw.p : nullptr, x, sums);
+    {
+        DBuf<double> part;
+        part.resize((size_t)3 * BODY_PARTS * nb);
+        k_body_sums_part<<<dim3(BODY_PARTS, nb), 128, 0, s>>>(geo(c), body_dev(c), c->n_q ? c->d_qw.p : nullptr, x,
+                                                             part);
+        k_body_sums_final<<<nb, 32, 0, s>>>(part, BODY_PARTS, sums);
+        PGB_LAUNCHED(c, 1);
+    }
     // the cavities' share of each body's reaction potential, before the
     // Coulomb reduction reuses slot [1]
     DBuf<double> inner;
