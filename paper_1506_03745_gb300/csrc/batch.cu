@@ -444,7 +444,13 @@ int solve_seg(pgb_ctx* c, int mode, double tol, int max_iter, int restart, doubl
     c->d_r.resize(n);
     c->d_xs.resize(n);
     const int rhs_prec = mode == PGB_FP64 ? PGB_FP64 : PGB_FP32;
-    build_rhs(c, c->d_b, rhs_prec);
+    if (mode == PGB_FP32_REFINE) {  // Coulomb rows once: the outer residual's and the right-hand side's
+        c->d_bc.resize(n);
+        coulomb_rows(c, c->d_bc);
+        build_rhs(c, c->d_b, rhs_prec, c->d_bc);
+    } else {
+        build_rhs(c, c->d_b, rhs_prec);
+    }
     precond_prepare(c);
     int known_mv = 0;
     for (auto& b : c->bodies)
@@ -479,8 +485,6 @@ int solve_seg(pgb_ctx* c, int mode, double tol, int max_iter, int restart, doubl
         // refinement as in solve(), per problem: inner FP32 solves aimed at
         // the final tolerance, the outer residual b_Coulomb - A64(x +
         // imposed) in FP64; a problem leaves when it meets tol or stalls
-        c->d_bc.resize(n);
-        coulomb_rows(c, c->d_bc);
         PGB_CUDA(cudaMemcpyAsync(c->d_r.p, c->d_b.p, 8 * n, cudaMemcpyDeviceToDevice, s));
         std::vector<double> rn = bn;
         std::vector<char> done(B);

@@ -481,7 +481,7 @@ void arnoldi_step(pgb_ctx* c, int j, double* w, double* h, double* hc, double* c
 double energy_unit_kcal();
 void phi_reac(pgb_ctx* c, const double* x, double* out);
 // solver (solver.cu)
-void build_rhs(pgb_ctx* c, double* b, int precision);
+void build_rhs(pgb_ctx* c, double* b, int precision, const double* bc = nullptr);
 int solve(pgb_ctx* c, int mode, double tol, int max_iter, int restart, double* x, pgb_solve_stats* st);
 void precond_prepare(pgb_ctx* c);
 void precond_apply(pgb_ctx* c, const double* v, double* z, bool transpose, bool add);

@@ -385,8 +385,8 @@ int pgb_solve_shard(pgb_ctx* c, int32_t rank, int32_t world, double* xs, double*
         c->d_b.resize(n);
         c->d_bc.resize(n);
         c->d_shard_tmp.resize(n);
-        build_rhs(c, c->d_b, mode == PGB_FP64 ? PGB_FP64 : PGB_FP32);
         coulomb_rows(c, c->d_bc);
+        build_rhs(c, c->d_b, mode == PGB_FP64 ? PGB_FP64 : PGB_FP32, c->d_bc);
         c->d_shard_b.resize(std::max<int64_t>(nl, 1));
         c->d_shard_bc.resize(std::max<int64_t>(nl, 1));
         c->d_shard_x.resize(std::max<int64_t>(nl, 1));

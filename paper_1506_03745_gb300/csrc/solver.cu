@@ -34,7 +34,7 @@ __global__ void k_coulomb_rows(Geo g, BodyDev bd, const double* qxyz, const doub
         double s = 0;
         for (int64_t k = qoff[src]; k < qoff[src + 1]; ++k) {
             double dx = x - qxyz[3 * k], dy = y - qxyz[3 * k + 1], dz = z - qxyz[3 * k + 2];
-            s += qv[k] / sqrt(dx * dx + dy * dy + dz * dz);
+            s += qv[k] * rsqrt_nr<2>(dx * dx + dy * dy + dz * dz);  // FP64 rounding (common.cuh)
         }
         if (side == 0) b[bd.unk_off[bi] + loc] = s / (PGB_FOUR_PI * eps_in[bi]);
         else b[bd.unk_off[bi] + N + loc] += s / (PGB_FOUR_PI * eps_in[src]);
@@ -64,13 +64,24 @@ void coulomb_rows(pgb_ctx* c, double* b) {
     PGB_LAUNCHED(c, 1);
 }
 
-void build_rhs(pgb_ctx* c, double* b, int precision) {
+__global__ void k_axpby(double a, const double* x, double b, const double* y, double* out, int64_t n);
+
+// bc: the Coulomb rows already formed (coulomb_rows), added to the imposed
+// terms instead of being computed again (the imposed terms of a molecule's
+// interior rows are zero: Laplace couples a body only to itself).
+void build_rhs(pgb_ctx* c, double* b, int precision, const double* bc) {
     cudaStream_t s = c->stream;
     StageTimer tm(c, PGB_STAGE_RHS);
     PGB_CUDA(cudaMemsetAsync(b, 0, 8 * c->n_unk, s));
     bool any_known = false;
     for (auto& bd : c->bodies) any_known |= bd.kind != PGB_DIELECTRIC;
     if (any_known) apply_operator(c, nullptr, b, precision, true);
+    if (bc) {
+        k_axpby<<<nblk(c->n_unk, 256), 256, 0, s>>>(1.0, b, 1.0, bc, b, c->n_unk);
+        PGB_CUDA(cudaGetLastError());
+        PGB_LAUNCHED(c, 1);
+        return;
+    }
     std::vector<int64_t> qoff(c->bodies.size() + 1, 0);
     std::vector<double> eps(c->bodies.size());
     for (size_t i = 0; i < c->bodies.size(); ++i) {
@@ -907,7 +918,13 @@ int solve(pgb_ctx* c, int mode, double tol, int max_iter, int restart, double* x
     if (mode != PGB_FP64 && mode != PGB_FP32_REFINE && mode != PGB_FP32)
         fail(PGB_EINVAL, "mode must be PGB_FP64, PGB_FP32_REFINE or PGB_FP32");
     const int rhs_prec = mode == PGB_FP64 ? PGB_FP64 : PGB_FP32;
-    build_rhs(c, c->d_b, rhs_prec);
+    if (mode == PGB_FP32_REFINE) {  // the outer residual's Coulomb rows, also the inner right-hand side's
+        c->d_bc.resize(n);
+        coulomb_rows(c, c->d_bc);
+        build_rhs(c, c->d_b, rhs_prec, c->d_bc);
+    } else {
+        build_rhs(c, c->d_b, rhs_prec);
+    }
     precond_prepare(c);
     pgb_solve_stats z{};
     int known_mv = 0;
@@ -947,8 +964,6 @@ int solve(pgb_ctx* c, int mode, double tol, int max_iter, int restart, double* x
         // serves the FP32 chain first and the FP64 work fills the rest.
         StreamSwap swap(c, c->p.overlap != 0);
         s = c->stream;
-        c->d_bc.resize(n);
-        coulomb_rows(c, c->d_bc);
         PGB_CUDA(cudaMemcpyAsync(c->d_r.p, c->d_b.p, 8 * n, cudaMemcpyDeviceToDevice, s));
         double rn = bnorm;
         while (rel > tol && z.iterations < max_iter && z.outer_steps < 50) {
