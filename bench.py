@@ -848,7 +848,9 @@ def run_poses_uneven(args):
     panels in geometric steps, 900 charges each) near a sphere r = 40 A
     (30420 panels, sigma -0.05 C/m^2): `--poses` orientations x 4 gaps (6, 8,
     10, 14 A) per molecule, FP32 + refinement with the double-single
-    residual (tol 1e-5).  Batched: pgb_solve_poses
+    residual and the block-diagonal preconditioner (tol 1e-6: every pose's
+    energy within 1e-5 of FP64; `--precond 0` gives the plain GMRES at tol
+    1e-5).  Batched: pgb_solve_poses
     with chunks of `batch` poses (default 8, one pose of every molecule per
     chunk: one launch per stage over eight molecules of different sizes);
     beside it the same poses molecule by molecule through pgb_solve_batch
@@ -889,13 +891,21 @@ def run_poses_uneven(args):
     # treecode parameters and work-item sizes by the autotuner, on the first
     # molecule 8 A from the sphere: the fastest FP32 solve whose total energy
     # is within 1e-5 of the most accurate candidate's (theta 0.5, P 7)
+    # the block-diagonal preconditioner halves the iterations (55 -> 27 per
+    # pose); with it the relative-residual tolerance that keeps every pose's
+    # energy within 1e-5 of the FP64 solve is tighter (on the leading 64 poses
+    # 1e-5 left 2.6e-5, 3e-6 left 6.5e-6, 2e-6 left 8.9e-6 on another pose
+    # set, 1e-6 left 4.9e-6): 1e-6 by default
     prm = dict(PARAMS)
+    if args.precond is None:
+        prm["precond"] = 1
+    tol = args.pose_tol if args.pose_tol is not None else (1e-6 if prm["precond"] else 1e-5)
     tune = None
     if not args.no_autotune and rank == 0:
         m0 = dict(mols[0], R=np.eye(3), t=np.array([place_for_gap(verts[0], np.eye(3), 40.0, 8.0), 0.0, 0.0]))
-        ct = gpu_context([m0, srf], **PARAMS)
+        ct = gpu_context([m0, srf], **prm)
         thetas, Ps, leaves = [0.5, 0.6, 0.7], [5, 6, 7], [32, 64]
-        (chosen, rep), t_ms = _timed(lambda: pgb.pgb_autotune(ct, thetas, Ps, leaves, reps=3, tol=1e-5,
+        (chosen, rep), t_ms = _timed(lambda: pgb.pgb_autotune(ct, thetas, Ps, leaves, reps=3, tol=tol,
                                                               target_rel_err=1e-5))
         pgb.pgb_destroy(ct)
         for k in ("theta", "P", "leaf_size", "p2p_item", "m2p_item"):
@@ -921,7 +931,6 @@ def run_poses_uneven(args):
                 pc.append(k)
     R, t, pc = np.array(R), np.array(t), np.array(pc, dtype=np.int32)
     B = len(R)
-    tol = 1e-5
     mode = pgb.PGB_FP32_REFINE
     lo, hi = rank_chunks(B, batch, rank, world)
     pgb.pgb_solve_poses(ctxs, pc[:batch], 0, R[:batch], t[:batch], mode, tol, MAX_ITER, RESTART)  # warm-up
@@ -993,7 +1002,7 @@ def run_poses_uneven(args):
     its = np.array([s["iterations"] for s in st])
     print(json.dumps({"workload": f"8 molecules ({min(npan)}-{max(npan)} panels, 900 charges each) x {args.poses} "
                                   f"orientations x 4 gaps near a sphere r=40 A (30420 panels)",
-                      "poses": B, "batch": batch, "n_gpus": world,
+                      "poses": B, "batch": batch, "n_gpus": world, "tol": tol, "precond": prm.get("precond", 0),
                       "split": "contiguous whole chunks per rank, slowest rank's time" if world > 1 else None,
                       "ms": ms, "poses_per_s": B / (ms / 1e3),
                       "lanes_4_per_molecule": lanes, "mode": "FP32 + refinement (double-single residual)",
@@ -1279,6 +1288,9 @@ def main():
     ap.add_argument("--residual", type=int, default=None, help="0: native FP64 outer residual, 1: double-single")
     ap.add_argument("--no-autotune", action="store_true", help="pose sweep over 8 molecules: library parameters")
     ap.add_argument("--no-lanes", action="store_true", help="pose sweep over 8 molecules: skip the lanes comparison")
+    ap.add_argument("--pose-tol", type=float, default=None,
+                    help="GMRES relative-residual tolerance of the 8-molecule pose sweep (default 1e-6 with its "
+                         "preconditioner, 1e-5 without)")
     args = ap.parse_args()
     for k, v in (("leaf_size", args.leaf), ("P", args.P), ("theta", args.theta), ("p2p_item", args.p2p_item),
                  ("m2p_item", args.m2p_item), ("precond", args.precond),
