@@ -337,8 +337,9 @@ int pgb_set_region(struct pgb_ctx* ctx, int32_t id, int32_t parent, double kappa
 /* Treecode parameter autotuner (a library feature; the paper fixes its
  * parameters by hand, Tables 1, 2, 4).  For every candidate (theta, P,
  * leaf_size) of the given lists it builds the tree, times `reps` FP32
- * matvecs with CUDA events and solves in PGB_FP32 mode to `tol` for the total
- * energy.  The reference is the candidate with the smallest theta, largest P
+ * matvecs with CUDA events and solves in PGB_FP32_REFINE mode to `tol` for
+ * the total energy (so the FP64-class residual product, whose near field
+ * grows with the leaf size, is in the time).  The reference is the candidate with the smallest theta, largest P
  * and first leaf size; among the candidates whose total energy is within
  * target_rel_err of the reference, the one with the shortest solve time
  * (tree build + solve) is chosen.  With it, the work-item sizes p2p_item and

@@ -870,7 +870,7 @@ int pgb_autotune(pgb_ctx* c, const double* thetas, int32_t n_theta, const int32_
             x.resize(c->n_unk);
             y.resize(c->n_unk);
             pgb_solve_stats st{};
-            r = solve(c, PGB_FP32, tol, 5000, 100, x, &st);
+            r = solve(c, PGB_FP32_REFINE, tol, 5000, 100, x, &st);  // the refinement residual counts too
             if (r != PGB_OK && r != PGB_ENOCONV) fail(r, c->err);
             PGB_CUDA(cudaEventRecord(e1, c->stream));
             PGB_CUDA(cudaEventSynchronize(e1));
