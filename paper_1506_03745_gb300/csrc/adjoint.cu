@@ -101,7 +101,7 @@ __global__ void k_tn_sort(int64_t nn, const int64_t* toff, int64_t* te) {  // in
 static void build_adjoint(pgb_ctx* c) {
     if (c->adj_valid) return;
     cudaStream_t s = c->stream;
-    const int64_t n = c->n_pan, ng = c->n_groups, K = c->p.K;
+    const int64_t n = c->n_pan, ng = c->n_groups;
     c->d_n32.resize(n); c->d_n64.resize(n); c->d_cT32.resize(n); c->d_cT64.resize(n);
     k_adj_panels<<<nblk(n, 128), 128, 0, s>>>(n, c->d_c, c->d_n, c->d_pan_leaf, c->d_leaf_node, c->d_node_center,
                                              c->d_n32, c->d_n64, c->d_cT32, c->d_cT64);

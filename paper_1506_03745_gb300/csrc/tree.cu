@@ -629,7 +629,6 @@ __global__ void k_node_geometry(const int32_t* nstart, const int32_t* nend, cons
                                 const double* pose, const double* Y, const double* C, const double* A, int K,
                                 double* center, double* r2, double* clo, double* chi, double* a8) {
     __shared__ double cw[3];
-    __shared__ double sh[32];
     int nd = blockIdx.x;
     int64_t s = nstart[nd], e = nend[nd];
     int b = nbody[nd], l = nlevel[nd];

@@ -812,11 +812,13 @@ __global__ void __launch_bounds__(128) k_far_big(UpArgs a, const real* __restric
             const int i = q / (2 * T), k = q - i * 2 * T;
             sm[i][k] = act[i] ? mom[(n0 + i) * 2 * T + k] : real(0);
         }
-        for (int q = threadIdx.x; q < NB * (TP - T); q += blockDim.x) {  // padding
-            const int i = q / (TP - T), k = T + q - i * (TP - T);
-            if (act[i]) {
-                far[(n0 + i) * 2 * TP + k] = real(0);
-                far[(n0 + i) * 2 * TP + TP + k] = real(0);
+        if constexpr (TP > T) {
+            for (int q = threadIdx.x; q < NB * (TP - T); q += blockDim.x) {  // padding
+                const int i = q / (TP - T), k = T + q - i * (TP - T);
+                if (act[i]) {
+                    far[(n0 + i) * 2 * TP + k] = real(0);
+                    far[(n0 + i) * 2 * TP + TP + k] = real(0);
+                }
             }
         }
         __syncthreads();
