@@ -85,6 +85,61 @@ __global__ void k_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* 
     if (t == blockDim.x - 1) *total = sh[t];
 }
 
+// Exclusive scan of long arrays over many blocks: each block of SCAN_T
+// threads takes SCAN_CHUNK consecutive values; k_scan_part sums every chunk,
+// the chunk sums are scanned by k_scan_i64, and k_scan_chunk scans each chunk
+// in shared memory from its offset.  (Integer sums: the same result as the
+// one-block scan.)
+#define SCAN_T 256
+#define SCAN_PER 16
+#define SCAN_CHUNK (SCAN_T * SCAN_PER)
+__global__ void __launch_bounds__(SCAN_T) k_scan_part(const int64_t* __restrict__ in, int64_t n, int64_t* part) {
+    __shared__ int64_t sh[SCAN_T / 32];
+    const int64_t b0 = (int64_t)blockIdx.x * SCAN_CHUNK;
+    int64_t t = 0;
+    for (int k = threadIdx.x; k < SCAN_CHUNK; k += SCAN_T)
+        if (b0 + k < n) t += in[b0 + k];
+    t = warp_sum(t);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t u = 0;
+        for (int w = 0; w < SCAN_T / 32; ++w) u += sh[w];
+        part[blockIdx.x] = u;
+    }
+}
+__global__ void __launch_bounds__(SCAN_T) k_scan_chunk(const int64_t* __restrict__ in, int64_t* out, int64_t n,
+                                                       const int64_t* __restrict__ poff) {
+    __shared__ int64_t v[SCAN_CHUNK];
+    __shared__ int64_t wsum[SCAN_T / 32];
+    const int64_t b0 = (int64_t)blockIdx.x * SCAN_CHUNK;
+    for (int k = threadIdx.x; k < SCAN_CHUNK; k += SCAN_T) v[k] = b0 + k < n ? in[b0 + k] : 0;
+    __syncthreads();
+    // each thread its SCAN_PER consecutive values, then the threads' totals
+    int64_t own = 0;
+    for (int q = 0; q < SCAN_PER; ++q) own += v[threadIdx.x * SCAN_PER + q];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t inc = own;  // inclusive scan over the warp
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    int64_t before = poff[blockIdx.x] + inc - own;
+    for (int k = 0; k < w; ++k) before += wsum[k];
+    __syncthreads();
+    for (int q = 0; q < SCAN_PER; ++q) {
+        const int idx = threadIdx.x * SCAN_PER + q;
+        const int64_t x = v[idx];
+        v[idx] = before;
+        before += x;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < SCAN_CHUNK; k += SCAN_T)
+        if (b0 + k < n) out[b0 + k] = v[k];
+}
+
 void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s, int64_t* total_host) {
     // one total slot per host thread, outside any stream order, freed when the thread ends
     struct Slot {
@@ -99,7 +154,17 @@ void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t
         PGB_CUDA(cudaMalloc(&slot.p, sizeof(int64_t)));
     }
     int64_t* tot = slot.p;
-    k_scan_i64<<<1, 1024, 0, s>>>(in, out, n, tot);
+    if (n > 4 * SCAN_CHUNK) {
+        const int64_t nb = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
+        DBuf<int64_t> part, poff;
+        part.resize(nb);
+        poff.resize(nb);
+        k_scan_part<<<(unsigned)nb, SCAN_T, 0, s>>>(in, n, part);
+        k_scan_i64<<<1, 1024, 0, s>>>(part, poff, nb, tot);
+        k_scan_chunk<<<(unsigned)nb, SCAN_T, 0, s>>>(in, out, n, poff);
+    } else {
+        k_scan_i64<<<1, 1024, 0, s>>>(in, out, n, tot);
+    }
     PGB_CUDA(cudaGetLastError());
     if (total_host) {
         PGB_CUDA(cudaMemcpyAsync(total_host, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -324,66 +389,94 @@ __global__ void k_key30(const uint64_t* k64, int64_t n, uint32_t* k32) {
     if (i < n) k32[i] = (uint32_t)(k64[i] & 0x3fffffffull);
 }
 
-// Octree split: a node at depth l with more than leaf_size panels splits into
-// its non-empty octants (key order), depth limited to 10.
-__device__ __forceinline__ int octant_of(const uint32_t* key, int64_t i, int child_level) {
-    return (int)((key[i] >> (3 * (10 - child_level))) & 7u);
+// Octree in one pass.  A node at depth l with more than leaf_size panels
+// splits into its non-empty octants, depth limited to 10.  With the panels in
+// key order the cells of a level are runs of equal key prefixes within a
+// body, and the counts only shrink going down, so a level-l cell (l >= 1) is
+// a node exactly when its parent cell holds more than leaf_size panels (its
+// ancestors then hold more too).  Every (level, panel) pair is tested at once
+// and one scan numbers the nodes level by level in key order.
+#define OCT_LEVELS 11  // levels 0 (a body's root) .. 10
+
+// body of sorted panel i (bodies are contiguous ranges off[b] .. off[b+1])
+__device__ __forceinline__ int sorted_body(const int64_t* off, int nb, int64_t i) {
+    int lo = 0, hi = nb;
+    while (hi - lo > 1) {
+        const int m = (lo + hi) >> 1;
+        if (off[m] <= i) lo = m;
+        else hi = m;
+    }
+    return lo;
 }
-__device__ int64_t lower_oct(const uint32_t* key, int64_t s, int64_t e, int child_level, int o) {
+// first j in [s, e) with (key[j] >> sh) >= p (keys ascending within a body)
+__device__ __forceinline__ int64_t key_lower(const uint32_t* key, int64_t s, int64_t e, int sh, uint64_t p) {
     while (s < e) {
-        int64_t m = (s + e) >> 1;
-        if (octant_of(key, m, child_level) < o) s = m + 1;
+        const int64_t m = (s + e) >> 1;
+        if ((uint64_t)(key[m] >> sh) < p) s = m + 1;
         else e = m;
     }
     return s;
 }
 
-// One warp per node: lane o <= 8 finds the first panel of octant o (lane 8:
-// the node's end), so the octants' bounds are the differences of neighbour
-// lanes; the nonempty ones are counted (k_split_count) or written in octant
-// order (k_split_write).  blockDim a multiple of 32.
-__device__ __forceinline__ unsigned split_bounds(const int32_t* start, const int32_t* end, int64_t i, int level,
-                                                 int leaf_size, bool always, const uint32_t* key, int64_t& lo,
-                                                 int64_t& hi) {
-    const int lane = threadIdx.x & 31;
-    const int64_t s = start[i], e = end[i];
-    const bool split = always || (e - s > leaf_size && level < 10);
-    int64_t b = 0;
-    if (split && lane <= 8) b = lane == 8 ? e : lower_oct(key, s, e, level + 1, lane);
-    const int64_t nb = __shfl_down_sync(0xffffffffu, b, 1);
-    lo = b;
-    hi = nb;
-    return __ballot_sync(0xffffffffu, split && lane < 8 && nb > b);
+// M[l n + i] = 1 when sorted panel i starts a node of level l; M[11 n] = 0
+// (the scan's total lands after it).
+__global__ void k_oct_marks(const uint32_t* key, const int64_t* off, int nb, int64_t n, int leaf_size, int64_t* M) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t > OCT_LEVELS * n) return;
+    if (t == OCT_LEVELS * n) {
+        M[t] = 0;
+        return;
+    }
+    const int l = (int)(t / n);
+    const int64_t i = t - l * n;
+    const int b = sorted_body(off, nb, i);
+    const bool body_first = i == off[b];
+    int64_t m = 0;
+    if (l == 0) {
+        m = body_first;
+    } else {
+        const int sh = 3 * (10 - l);
+        if (body_first || (key[i] >> sh) != (key[i - 1] >> sh)) {
+            const int ps = sh + 3;  // the parent's level
+            const uint64_t pp = key[i] >> ps;
+            const int64_t a = key_lower(key, off[b], off[b + 1], ps, pp);
+            const int64_t e = key_lower(key, off[b], off[b + 1], ps, pp + 1);
+            m = (e - a) > leaf_size;
+        }
+    }
+    M[t] = m;
 }
 
-__global__ void k_split_count(const int32_t* start, const int32_t* end, int64_t n, int level, int leaf_size,
-                              const uint32_t* key, int64_t* nchild) {
-    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (i >= n) return;  // warp-uniform
-    int64_t lo, hi;
-    const unsigned ne = split_bounds(start, end, i, level, leaf_size, false, key, lo, hi);
-    if ((threadIdx.x & 31) == 0) nchild[i] = __popc(ne);
+// Node S[t] of every mark t = l n + i: its panel range, body, level and
+// children (the level-(l+1) nodes that start inside its range).
+__global__ void k_oct_nodes(const uint32_t* key, const int64_t* off, int nb, int64_t n, const int64_t* M,
+                            const int64_t* S, int32_t* nstart, int32_t* nend, int32_t* nbody, int32_t* nlevel,
+                            int32_t* first_child, int32_t* nch) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= OCT_LEVELS * n || !M[t]) return;
+    const int l = (int)(t / n);
+    const int64_t i = t - l * n;
+    const int b = sorted_body(off, nb, i);
+    const int sh = 3 * (10 - l);
+    const int64_t end = l == 0 ? off[b + 1] : key_lower(key, i, off[b + 1], sh, (uint64_t)(key[i] >> sh) + 1);
+    const int64_t id = S[t];
+    nstart[id] = (int32_t)i;
+    nend[id] = (int32_t)end;
+    nbody[id] = b;
+    nlevel[id] = l;
+    int64_t c0 = 0, c1 = 0;
+    if (l < OCT_LEVELS - 1) {
+        c0 = S[(int64_t)(l + 1) * n + i];
+        c1 = S[(int64_t)(l + 1) * n + end];
+    }
+    nch[id] = (int32_t)(c1 - c0);
+    first_child[id] = c1 > c0 ? (int32_t)c0 : -1;
 }
 
-__global__ void k_split_write(const int32_t* start, const int32_t* end, const int32_t* body, int64_t n, int level,
-                              const uint32_t* key, const int64_t* nchild, const int64_t* coff, int64_t child_base,
-                              int32_t* first_child, int32_t* nch, int32_t* cstart, int32_t* cend, int32_t* cbody) {
-    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (i >= n) return;  // warp-uniform
-    const int lane = threadIdx.x & 31;
-    if (lane == 0) {
-        nch[i] = (int32_t)nchild[i];
-        first_child[i] = nchild[i] ? (int32_t)(child_base + coff[i]) : -1;
-    }
-    if (!nchild[i]) return;  // warp-uniform
-    int64_t lo, hi;
-    const unsigned ne = split_bounds(start, end, i, level, 0, true, key, lo, hi);
-    if ((ne >> lane) & 1u) {
-        const int64_t k = coff[i] + __popc(ne & ((1u << lane) - 1u));
-        cstart[k] = (int32_t)lo;
-        cend[k] = (int32_t)hi;
-        cbody[k] = body[i];
-    }
+// the first node id of every level (lb[l] = S[l n], lb[11] = the total)
+__global__ void k_oct_levels(const int64_t* S, int64_t n, int64_t* lb) {
+    const int l = threadIdx.x;
+    if (l <= OCT_LEVELS) lb[l] = S[(int64_t)l * n];
 }
 
 __global__ void k_parents(const int32_t* child, const int32_t* nch, int64_t n, int32_t* parent) {
@@ -482,78 +575,33 @@ void build_order(pgb_ctx* c) {
     k_invert<<<nblk(n, 256), 256, 0, s>>>(c->d_perm, n, c->d_inv);
     PGB_CUDA(cudaGetLastError());
 
-    // octree, level by level (all bodies together); roots first
-    std::vector<DBuf<int32_t>*> lv_start, lv_end, lv_body, lv_fc, lv_nch;
-    std::vector<int64_t> lv_n;
-    auto alloc = [&](int64_t m) {
-        lv_start.push_back(new DBuf<int32_t>); lv_start.back()->resize(m);
-        lv_end.push_back(new DBuf<int32_t>); lv_end.back()->resize(m);
-        lv_body.push_back(new DBuf<int32_t>); lv_body.back()->resize(m);
-        lv_fc.push_back(new DBuf<int32_t>); lv_fc.back()->resize(m);
-        lv_nch.push_back(new DBuf<int32_t>); lv_nch.back()->resize(m);
-        lv_n.push_back(m);
-    };
-    alloc(nb);
-    {
-        std::vector<int32_t> rs(nb), re(nb), rb(nb);
-        for (int b = 0; b < nb; ++b) {
-            rs[b] = (int32_t)off[b];
-            re[b] = (int32_t)off[b + 1];
-            rb[b] = b;
-        }
-        PGB_CUDA(cudaMemcpyAsync(lv_start[0]->p, rs.data(), 4 * nb, cudaMemcpyHostToDevice, s));
-        PGB_CUDA(cudaMemcpyAsync(lv_end[0]->p, re.data(), 4 * nb, cudaMemcpyHostToDevice, s));
-        PGB_CUDA(cudaMemcpyAsync(lv_body[0]->p, rb.data(), 4 * nb, cudaMemcpyHostToDevice, s));
-        PGB_CUDA(cudaStreamSynchronize(s));
-    }
-    int64_t base = nb;
-    DBuf<int64_t> nchild, coff;
-    for (int level = 0; level <= 10; ++level) {
-        int64_t m = lv_n[level];
-        nchild.resize(m);
-        coff.resize(m);
-        k_split_count<<<nblk(32 * m, 128), 128, 0, s>>>(*lv_start[level], *lv_end[level], m, level,
-                                                        c->p.leaf_size, c->d_key, nchild);
-        PGB_CUDA(cudaGetLastError());
-        int64_t total = 0;
-        exclusive_scan_i64(nchild, coff, m, s, &total);
-        alloc(std::max<int64_t>(total, 1));
-        lv_n.back() = total;
-        k_split_write<<<nblk(32 * m, 128), 128, 0, s>>>(*lv_start[level], *lv_end[level], *lv_body[level], m, level,
-                                                   c->d_key, nchild, coff, base, *lv_fc[level], *lv_nch[level],
-                                                   *lv_start[level + 1], *lv_end[level + 1], *lv_body[level + 1]);
-        PGB_CUDA(cudaGetLastError());
-        base += total;
-        if (total == 0) break;
-    }
+    // octree: every level at once (roots first, then each level in key order)
+    DBuf<int64_t> M, S, lb;
+    M.resize(OCT_LEVELS * n + 1);
+    S.resize(OCT_LEVELS * n + 1);
+    lb.resize(OCT_LEVELS + 1);
+    k_oct_marks<<<nblk(OCT_LEVELS * n + 1, 256), 256, 0, s>>>(c->d_key, d_off, nb, n, c->p.leaf_size, M);
+    PGB_CUDA(cudaGetLastError());
+    exclusive_scan_i64(M, S, OCT_LEVELS * n + 1, s, nullptr);
+    k_oct_levels<<<1, 32, 0, s>>>(S, n, lb);
+    PGB_CUDA(cudaGetLastError());
+    std::vector<int64_t> hl(OCT_LEVELS + 1);
+    PGB_CUDA(cudaMemcpyAsync(hl.data(), lb.p, 8 * (OCT_LEVELS + 1), cudaMemcpyDeviceToHost, s));
+    PGB_CUDA(cudaStreamSynchronize(s));
     int nlev = 0;
-    while (nlev < (int)lv_n.size() && lv_n[nlev] > 0) ++nlev;
-    int64_t nn = 0;
-    c->level_begin.assign(nlev + 1, 0);
-    for (int l = 0; l < nlev; ++l) {
-        c->level_begin[l] = nn;
-        nn += lv_n[l];
-    }
-    c->level_begin[nlev] = nn;
+    while (nlev < OCT_LEVELS && hl[nlev + 1] > hl[nlev]) ++nlev;
+    const int64_t nn = hl[nlev];
+    c->level_begin.assign(hl.begin(), hl.begin() + nlev + 1);
     c->n_nodes = nn;
     c->d_node_start.resize(nn); c->d_node_end.resize(nn); c->d_node_body.resize(nn);
     c->d_node_child.resize(nn); c->d_node_nchild.resize(nn); c->d_node_level.resize(nn);
-    c->h_node_level.assign(nn, 0);
-    for (int l = 0; l < nlev; ++l) {
-        int64_t o = c->level_begin[l], m = lv_n[l];
-        PGB_CUDA(cudaMemcpyAsync(c->d_node_start.p + o, lv_start[l]->p, 4 * m, cudaMemcpyDeviceToDevice, s));
-        PGB_CUDA(cudaMemcpyAsync(c->d_node_end.p + o, lv_end[l]->p, 4 * m, cudaMemcpyDeviceToDevice, s));
-        PGB_CUDA(cudaMemcpyAsync(c->d_node_body.p + o, lv_body[l]->p, 4 * m, cudaMemcpyDeviceToDevice, s));
-        PGB_CUDA(cudaMemcpyAsync(c->d_node_child.p + o, lv_fc[l]->p, 4 * m, cudaMemcpyDeviceToDevice, s));
-        PGB_CUDA(cudaMemcpyAsync(c->d_node_nchild.p + o, lv_nch[l]->p, 4 * m, cudaMemcpyDeviceToDevice, s));
-        k_fill_i32<<<nblk(m, 256), 256, 0, s>>>(c->d_node_level.p + o, m, l);
-        for (int64_t i = o; i < o + m; ++i) c->h_node_level[i] = l;
-    }
+    k_oct_nodes<<<nblk(OCT_LEVELS * n, 256), 256, 0, s>>>(c->d_key, d_off, nb, n, M, S, c->d_node_start,
+                                                          c->d_node_end, c->d_node_body, c->d_node_level,
+                                                          c->d_node_child, c->d_node_nchild);
     PGB_CUDA(cudaGetLastError());
-    PGB_CUDA(cudaStreamSynchronize(s));
-    for (size_t l = 0; l < lv_start.size(); ++l) {
-        delete lv_start[l]; delete lv_end[l]; delete lv_body[l]; delete lv_fc[l]; delete lv_nch[l];
-    }
+    c->h_node_level.assign(nn, 0);
+    for (int l = 0; l < nlev; ++l)
+        for (int64_t k = c->level_begin[l]; k < c->level_begin[l + 1]; ++k) c->h_node_level[k] = l;
     for (int b = 0; b < nb; ++b) c->bodies[b].root = b;
     c->d_node_parent.resize(nn);
     k_fill_i32<<<nblk(nn, 256), 256, 0, s>>>(c->d_node_parent, nn, -1);
