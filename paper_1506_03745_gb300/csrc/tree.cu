@@ -1505,24 +1505,33 @@ __global__ void k_corr_self(int64_t n, const int64_t* off, const int32_t* cj, co
     if (e < 0) return;
     const double* x = C + 3 * i;
     const double* v = V + 9 * i;
+    // square roots and reciprocals by rsqrt_nr<2> (FP64 rounding, common.cuh):
+    // the FP64 pipe runs at 1/64 of the FP32 rate and the library's sqrt and
+    // division cost several times as much
+    const double inv_kappa = kappa > 0 ? 1.0 / kappa : 0.0;
     double vl = 0, vy = 0;
     for (int ed = 0; ed < 3; ++ed) {
         const double* pa = v + 3 * ed;
         const double* pb = v + 3 * ((ed + 1) % 3);
         double ev[3] = {pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2]};
-        double ell = sqrt(ev[0] * ev[0] + ev[1] * ev[1] + ev[2] * ev[2]);
-        double u[3] = {ev[0] / ell, ev[1] / ell, ev[2] / ell};
+        const double ell2 = ev[0] * ev[0] + ev[1] * ev[1] + ev[2] * ev[2];
+        const double il = rsqrt_nr<2>(ell2);
+        const double ell = ell2 * il;
+        double u[3] = {ev[0] * il, ev[1] * il, ev[2] * il};
         double cpa[3] = {x[0] - pa[0], x[1] - pa[1], x[2] - pa[2]};
         double proj = cpa[0] * u[0] + cpa[1] * u[1] + cpa[2] * u[2];
         double hv[3] = {cpa[0] - proj * u[0], cpa[1] - proj * u[1], cpa[2] - proj * u[2]};
-        double h = sqrt(hv[0] * hv[0] + hv[1] * hv[1] + hv[2] * hv[2]);
+        const double h2 = hv[0] * hv[0] + hv[1] * hv[1] + hv[2] * hv[2];
+        const double h = h2 * rsqrt_nr<2>(h2);
         for (int g = 0; g < r.ne; ++g) {
             double sg = r.ex[g] * ell;
             double p[3] = {pa[0] + sg * u[0] - x[0], pa[1] + sg * u[1] - x[1], pa[2] + sg * u[2] - x[2]};
-            double rho = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
-            double jac = h / (rho * rho) * ell * r.ew[g];
+            const double rho2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+            const double ri = rsqrt_nr<2>(rho2);
+            const double rho = rho2 * ri;
+            double jac = h * (ri * ri) * ell * r.ew[g];
             vl += rho * jac;
-            vy += (kappa > 0 ? (1.0 - exp(-kappa * rho)) / kappa : rho) * jac;
+            vy += (kappa > 0 ? (1.0 - exp(-kappa * rho)) * inv_kappa : rho) * jac;
         }
     }
     const int bi = pbody[i];
