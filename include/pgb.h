@@ -77,7 +77,9 @@ typedef struct pgb_params {
                              self terms, applied on the right so the residual test is unchanged */
     int32_t graphs;       /* 2 (default): the GMRES iterations after the first column of each restart
                              cycle are replayed from one CUDA graph whose device-side loop stops on
-                             the residual estimate (no host round trip per iteration), and the
+                             the residual estimate (no host round trip per iteration; for pose
+                             batches the loop also tracks every pose's estimate and leaves finished
+                             poses out of the products), and the
                              upward pass of every other product (P2M, moment shifts, far-field
                              coefficients) is captured once per tree and replayed; 1: the upward
                              pass only; 0: plain launches */
