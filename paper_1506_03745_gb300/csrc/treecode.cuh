@@ -686,13 +686,17 @@ __device__ __forceinline__ bool body_on(const UpArgs& a, int b) {
 }
 
 
-// C(n, m) (0 for m > n), exact in double for the orders used here
-__device__ __forceinline__ double binom_exact(int n, int m) {
-    if (m > n) return 0.0;
-    double b = 1.0;
-    for (int i = 1; i <= m; ++i) b = b * (n - m + i) / i;
-    return b;
-}
+// C(n, m) for n, m <= 15 (0 for m > n), by Pascal's rule at compile time
+struct BinomTable {
+    double v[16][16];
+    __host__ __device__ constexpr BinomTable() : v() {
+        for (int n = 0; n < 16; ++n) {
+            v[n][0] = 1.0;
+            for (int m = 1; m <= n; ++m) v[n][m] = v[n - 1][m - 1] + (m < n ? v[n - 1][m] : 0.0);
+        }
+    }
+};
+__device__ const BinomTable kBinomTable = BinomTable();
 
 __device__ __constant__ const int kBinom[9][9] = {
     {1, 0, 0, 0, 0, 0, 0, 0, 0},      {1, 1, 0, 0, 0, 0, 0, 0, 0},      {1, 2, 1, 0, 0, 0, 0, 0, 0},
@@ -1120,7 +1124,7 @@ __global__ void __launch_bounds__(128) k_upward(UpArgs a, const typename V4<real
     }
     for (int q = tid; q < (P + 1) * (P + 1); q += blockDim.x) {
         const int n = q / (P + 1), m = q - n * (P + 1);
-        sh.binom[n][m] = from_dbl<real>(binom_exact(n, m));
+        sh.binom[n][m] = from_dbl<real>(kBinomTable.v[n][m]);
     }
     __syncthreads();
     for (int64_t leaf = blockIdx.x; leaf < a.n_leaves; leaf += gridDim.x) {
@@ -1157,8 +1161,9 @@ constexpr int m2p_warps() {
     return nw;
 }
 
-// Nodes per block of k_far_big.
-constexpr int FAR_BIG_NB = 4;
+// Nodes per block of k_far_big: 8 in FP32, 4 in the 8-byte types (shared memory).
+template <typename real>
+constexpr int far_big_nb() { return sizeof(real) == sizeof(float) ? 8 : 4; }
 
 // The upward pass of one product: P2M and the moment shifts in one launch
 // (k_upward), then the far-field coefficients (orders up to 8: k_far_f32 in
@@ -1181,16 +1186,17 @@ void launch_upward(const UpArgs& up, const void* src, void* mom, cudaStream_t s)
     PGB_CUDA(cudaGetDevice(&dev));
     PGB_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     if constexpr (P > 8) {
-        constexpr size_t smem = sizeof(real) * FAR_BIG_NB * 2 * MI<P>::T;
+        constexpr int NB = far_big_nb<real>();
+        constexpr size_t smem = sizeof(real) * NB * 2 * MI<P>::T;
         static bool attr = false;
         if (!attr) {
-            PGB_CUDA(cudaFuncSetAttribute(k_far_big<real, P, FAR_BIG_NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            PGB_CUDA(cudaFuncSetAttribute(k_far_big<real, P, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
             attr = true;
         }
-        int64_t gf = (up.n_nodes + FAR_BIG_NB - 1) / FAR_BIG_NB;
+        int64_t gf = (up.n_nodes + NB - 1) / NB;
         if (up.p2m_grid > 0) gf = std::min<int64_t>(gf, up.p2m_grid);
-        k_far_big<real, P, FAR_BIG_NB><<<(unsigned)std::max<int64_t>(gf, 1), 128, smem, s>>>(up, (const real*)mom);
+        k_far_big<real, P, NB><<<(unsigned)std::max<int64_t>(gf, 1), 128, smem, s>>>(up, (const real*)mom);
     } else if constexpr (sizeof(real) == sizeof(float)) {
         // FP32: a block per (node, table), a thread per output
         k_far_f32<P><<<dim3((unsigned)up.n_nodes, 2), far_tr(P), 0, s>>>(up, (const float*)mom);
